@@ -1,0 +1,290 @@
+"""FP64 CPU oracle of the open-loop Shack-Hartmann measurement.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with
+the CUDA library (``paper_1408_0698_gb300``); both are written from the paper
+(Arcidiacono et al. 2014, Sec. 4 "Open Loop generation" and "LGS Shack Hartmann
+wavefront sensor") and compared element by element.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, brute-force definitions);
+this module only builds it and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (OpenMP, no FP contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    hdr = os.path.join(_HERE, "oracle.h")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+           src, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Geom(C.Structure):
+    _fields_ = [("diameter_m", C.c_double), ("obstruction", C.c_double), ("n_sub", C.c_int),
+                ("n", C.c_int), ("N", C.c_int), ("n_det", C.c_int), ("valid_fill", C.c_double)]
+
+
+class _Star(C.Structure):
+    _fields_ = [("is_lgs", C.c_int), ("theta_x", C.c_double), ("theta_y", C.c_double),
+                ("range_m", C.c_double), ("wavelength_m", C.c_double), ("launch_x", C.c_double),
+                ("launch_y", C.c_double), ("spot_fwhm_rad", C.c_double), ("photons", C.c_double),
+                ("read_noise", C.c_double), ("n_na", C.c_int),
+                ("na_alt", C.POINTER(C.c_double)), ("na_weight", C.POINTER(C.c_double))]
+
+
+class _Layers(C.Structure):
+    _fields_ = [("n_layers", C.c_int), ("S", C.c_int), ("dx", C.c_double),
+                ("alt", C.POINTER(C.c_double)), ("vx", C.POINTER(C.c_double)),
+                ("vy", C.POINTER(C.c_double)), ("x0", C.POINTER(C.c_double)),
+                ("y0", C.POINTER(C.c_double))]
+
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint32)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            L = _lib
+            L.orc_pupil_mask.argtypes = [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_uint8)]
+            L.orc_valid_subaps.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, _ip, _dp]
+            L.orc_valid_subaps.restype = C.c_int
+            L.orc_bilinear.argtypes = [_fp, C.c_int, C.c_double, C.c_double]
+            L.orc_bilinear.restype = C.c_double
+            L.orc_opd.argtypes = [C.POINTER(_Layers), _fp, C.POINTER(_Star), C.c_double, C.c_double, C.c_double]
+            L.orc_opd.restype = C.c_double
+            L.orc_project_grid.argtypes = [C.c_double, C.c_int, C.POINTER(_Layers), _fp, C.POINTER(_Star), C.c_double, _dp]
+            L.orc_dft2.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+            L.orc_elong_kernel.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(_Star), _dp]
+            L.orc_convolve.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.orc_bin.argtypes = [C.c_int, C.c_int, _dp, _dp]
+            L.orc_philox.argtypes = [_up, _up, _up]
+            L.orc_noise_pixel.argtypes = [C.c_float, C.c_float, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, _ip]
+            L.orc_noise_pixel.restype = C.c_double
+            L.orc_noise_image.argtypes = [C.c_int, _fp, C.c_float, C.c_uint64, C.c_uint32, C.c_double, C.c_uint32, _dp, _ip]
+            L.orc_cog.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.orc_measure_wfs.argtypes = [C.POINTER(_Geom), C.POINTER(_Star), C.c_int, C.POINTER(_Layers), _fp,
+                                          C.c_double, C.c_uint64, C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_measure_wfs.restype = C.c_int
+            L.orc_num_threads.restype = C.c_int
+        return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _Keep:
+    """Holds the numpy arrays that ctypes structs point into."""
+
+    def __init__(self):
+        self.refs = []
+
+    def d(self, a):
+        a = _f64(a)
+        self.refs.append(a)
+        return _ptr(a, _dp)
+
+
+def _star(gs, keep):
+    s = _Star()
+    s.is_lgs = int(bool(gs.is_lgs))
+    s.theta_x, s.theta_y = gs.theta_x_rad, gs.theta_y_rad
+    s.range_m = gs.range_m if gs.is_lgs else math.inf
+    s.wavelength_m = gs.wavelength_m
+    s.launch_x, s.launch_y = gs.launch_x_m, gs.launch_y_m
+    s.spot_fwhm_rad = gs.spot_fwhm_rad
+    s.photons, s.read_noise = gs.photons_per_subap, gs.read_noise_e
+    s.n_na = len(gs.na_alt_m) if gs.is_lgs else 0
+    s.na_alt = keep.d(gs.na_alt_m if len(gs.na_alt_m) else [0.0])
+    s.na_weight = keep.d(gs.na_weight if len(gs.na_weight) else [0.0])
+    return s
+
+
+def _layers(lay, keep):
+    L = _Layers()
+    L.n_layers, L.S, L.dx = lay.n_layers, lay.screen_size, lay.screen_dx_m
+    L.alt, L.vx, L.vy = keep.d(lay.alt_m), keep.d(lay.wind_vx_mps), keep.d(lay.wind_vy_mps)
+    L.x0, L.y0 = keep.d(lay.x0_m), keep.d(lay.y0_m)
+    return L
+
+
+def _geom(tel, g):
+    G = _Geom()
+    G.diameter_m, G.obstruction = tel.diameter_m, tel.obstruction
+    G.n_sub, G.n, G.N, G.n_det, G.valid_fill = g.n_sub, g.n_pix_sub, g.n_fft, g.n_det, g.valid_fill
+    return G
+
+
+# ---------------------------------------------------------------- public wrappers
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def pupil_mask(D, eps, Np):
+    m = np.zeros((Np, Np), dtype=np.uint8)
+    lib().orc_pupil_mask(D, eps, Np, m.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return m
+
+
+def valid_subaps(D, eps, n_sub, n, thr=0.5):
+    cap = n_sub * n_sub
+    idx = np.zeros(cap, dtype=np.int32)
+    fill = np.zeros(cap, dtype=np.float64)
+    c = lib().orc_valid_subaps(D, eps, n_sub, n, thr, _ptr(idx, _ip), _ptr(fill, _dp))
+    return idx[:c].copy(), fill[:c].copy()
+
+
+def bilinear(screen, u, v):
+    s = np.ascontiguousarray(screen, dtype=np.float32)
+    return lib().orc_bilinear(_ptr(s, _fp), s.shape[0], float(u), float(v))
+
+
+def opd(cfg, screens, star_index, x, y, t):
+    keep = _Keep()
+    L = _layers(cfg.layers, keep)
+    s = _star(cfg.stars[star_index], keep)
+    sc = np.ascontiguousarray(screens, dtype=np.float32)
+    return lib().orc_opd(C.byref(L), _ptr(sc, _fp), C.byref(s), x, y, t)
+
+
+def project_grid(cfg, screens, star_index, t):
+    gs = cfg.stars[star_index]
+    g = cfg.geometries[gs.geometry_index]
+    Np = g.n_sub * g.n_pix_sub
+    keep = _Keep()
+    L = _layers(cfg.layers, keep)
+    s = _star(gs, keep)
+    sc = np.ascontiguousarray(screens, dtype=np.float32)
+    out = np.zeros((Np, Np), dtype=np.float64)
+    lib().orc_project_grid(cfg.telescope.diameter_m, Np, C.byref(L), _ptr(sc, _fp), C.byref(s), t,
+                           _ptr(out, _dp))
+    return out
+
+
+def dft2(X, N):
+    X = np.asarray(X, dtype=np.complex128)
+    n = X.shape[0]
+    xr, xi = _f64(X.real), _f64(X.imag)
+    yr = np.zeros((N, N)); yi = np.zeros((N, N))
+    lib().orc_dft2(n, N, _ptr(xr, _dp), _ptr(xi, _dp), _ptr(yr, _dp), _ptr(yi, _dp))
+    return yr + 1j * yi
+
+
+def elong_kernel(N, pix_rad, rbx, rby, star):
+    keep = _Keep()
+    s = _star(star, keep)
+    K = np.zeros((N, N))
+    lib().orc_elong_kernel(N, pix_rad, rbx, rby, C.byref(s), _ptr(K, _dp))
+    return K
+
+
+def convolve(I, K):
+    I, K = _f64(I), _f64(K)
+    out = np.zeros_like(I)
+    lib().orc_convolve(I.shape[0], _ptr(I, _dp), _ptr(K, _dp), _ptr(out, _dp))
+    return out
+
+
+def bin_image(I, nd):
+    I = _f64(I)
+    B = np.zeros((nd, nd))
+    lib().orc_bin(I.shape[0], nd, _ptr(I, _dp), _ptr(B, _dp))
+    return B
+
+
+def philox(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox(_ptr(c, _up), _ptr(k, _up), _ptr(o, _up))
+    return o
+
+
+def noise_image(E, read_noise, seed, wfs, t, pixel0=0):
+    E = np.ascontiguousarray(E, dtype=np.float32).ravel()
+    Cc = np.zeros(E.size, dtype=np.float64)
+    K = np.zeros(E.size, dtype=np.int32)
+    lib().orc_noise_image(E.size, _ptr(E, _fp), float(read_noise), int(seed), int(wfs), float(t),
+                          int(pixel0), _ptr(Cc, _dp), _ptr(K, _ip))
+    return Cc, K
+
+
+def cog(Cimg):
+    Cimg = _f64(Cimg)
+    sx, sy = C.c_double(), C.c_double()
+    lib().orc_cog(Cimg.shape[0], _ptr(Cimg, _dp), C.byref(sx), C.byref(sy))
+    return sx.value, sy.value
+
+
+def measure_wfs(cfg, screens, star_index, t, seed=0, noise=False, sel=None, stages=False):
+    """Measure one WFS; returns a dict with 'slopes' [n_sel, 2] and, with
+    stages=True, 'opd', 'I', 'Ie', 'E', 'C' per selected subap."""
+    gs = cfg.stars[star_index]
+    g = cfg.geometries[gs.geometry_index]
+    keep = _Keep()
+    G = _geom(cfg.telescope, g)
+    L = _layers(cfg.layers, keep)
+    s = _star(gs, keep)
+    sc = np.ascontiguousarray(screens, dtype=np.float32)
+    if sel is None:
+        nv = len(valid_subaps(cfg.telescope.diameter_m, cfg.telescope.obstruction, g.n_sub,
+                              g.n_pix_sub, g.valid_fill)[0])
+        n_sel, selp = nv, None
+    else:
+        sel = np.ascontiguousarray(sel, dtype=np.int32)
+        n_sel, selp = len(sel), _ptr(sel, _ip)
+    n, N, nd = g.n_pix_sub, g.n_fft, g.n_det
+    out = {"slopes": np.zeros((n_sel, 2))}
+    if stages:
+        out["opd"] = np.zeros((n_sel, n, n))
+        out["I"] = np.zeros((n_sel, N, N))
+        out["Ie"] = np.zeros((n_sel, N, N))
+        out["E"] = np.zeros((n_sel, nd, nd))
+        out["C"] = np.zeros((n_sel, nd, nd))
+    gp = lambda k: _ptr(out[k], _dp) if k in out else None
+    rc = lib().orc_measure_wfs(C.byref(G), C.byref(s), star_index, C.byref(L), _ptr(sc, _fp), t,
+                               int(seed), int(bool(noise)), n_sel, selp, gp("slopes"), gp("opd"),
+                               gp("I"), gp("Ie"), gp("E"), gp("C"))
+    if rc < 0:
+        raise ValueError("oracle: bad geometry")
+    return out
+
+
+def measure(cfg, screens, t, seed=0, noise=False):
+    """All guide stars of a configuration: slopes concatenated [sum_w n_valid_w, 2]."""
+    return np.concatenate([measure_wfs(cfg, screens, w, t, seed, noise)["slopes"]
+                           for w in range(len(cfg.stars))], axis=0)

@@ -1,0 +1,460 @@
+/*
+ * oracle.c -- FP64 CPU reference of the open-loop Shack-Hartmann measurement.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the library.  Independent of the
+ * CUDA path (no shared code, header, table or constant).
+ *
+ * Paper: Arcidiacono et al. 2014 (MAORY E2E simulation).
+ *   Sec. 4 "Open Loop generation": layers piled up, shifted for the star
+ *     direction and the temporal evolution; for an LGS the pupil footprint
+ *     shrinks with altitude (cone effect).
+ *   Sec. 4 "LGS Shack Hartmann wavefront sensor": the WF is split into
+ *     subapertures, each spot computed by FFT (Sec. 2: "FFT (actually DFT)"),
+ *     sodium sub-layers with their tip-tilt shift weighted by the sodium
+ *     profile, a Gaussian convolution for the physical spot extent, the
+ *     sub-layers piled up, noise added, centroid taken to give X/Y slopes.
+ *
+ * Readings where the paper is silent are fixed in the design notes
+ * (pixel-centre pupil, 0.5 fill threshold, centred DFT, periodic
+ * minimum-image Gaussian kernel, periodic convolution, Philox/Poisson/
+ * Box-Muller noise, CoG in detector pixels).
+ *
+ * Build with -ffp-contract=off: the Poisson decisions are taken in FP32 with
+ * the same operation order as the GPU kernel, so no fused multiply-adds.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---- pupil and subapertures (Sec. 2 pupil sampling; Sec. 4 subaperture split) ---- */
+
+static int lit(double D, double eps, int Np, int i, int j)
+{
+    double dx = D / Np;
+    double x = (j - (Np - 1) / 2.0) * dx;
+    double y = (i - (Np - 1) / 2.0) * dx;
+    double r2 = x * x + y * y;
+    double ro = D / 2.0, ri = eps * D / 2.0;
+    return (r2 <= ro * ro) && (r2 >= ri * ri);
+}
+
+void orc_pupil_mask(double D, double eps, int Np, uint8_t *mask)
+{
+    for (int i = 0; i < Np; ++i)
+        for (int j = 0; j < Np; ++j)
+            mask[(size_t)i * Np + j] = (uint8_t)lit(D, eps, Np, i, j);
+}
+
+int orc_valid_subaps(double D, double eps, int n_sub, int n, double thr, int32_t *idx,
+                     double *fill)
+{
+    int Np = n_sub * n, count = 0;
+    for (int sy = 0; sy < n_sub; ++sy)
+        for (int sx = 0; sx < n_sub; ++sx) {
+            int c = 0;
+            for (int p = 0; p < n; ++p)
+                for (int q = 0; q < n; ++q) c += lit(D, eps, Np, sy * n + p, sx * n + q);
+            double f = (double)c / ((double)n * n);
+            if (f >= thr) {
+                if (idx) idx[count] = sy * n_sub + sx;
+                if (fill) fill[count] = f;
+                ++count;
+            }
+        }
+    return count;
+}
+
+/* ---- projection (Sec. 4 Open Loop generation) ---- */
+
+static int wrap(long long i, int S)
+{
+    long long r = i % S;
+    return (int)(r < 0 ? r + S : r);
+}
+
+double orc_bilinear(const float *scr, int S, double u, double v)
+{
+    double iu = floor(u), iv = floor(v);
+    double f = u - iu, g = v - iv;
+    int i0 = wrap((long long)iu, S), i1 = wrap((long long)iu + 1, S);
+    int j0 = wrap((long long)iv, S), j1 = wrap((long long)iv + 1, S);
+    double s00 = scr[(size_t)j0 * S + i0], s01 = scr[(size_t)j0 * S + i1];
+    double s10 = scr[(size_t)j1 * S + i0], s11 = scr[(size_t)j1 * S + i1];
+    return (1 - f) * (1 - g) * s00 + f * (1 - g) * s01 + (1 - f) * g * s10 + f * g * s11;
+}
+
+double orc_opd(const orc_layers *L, const float *screens, const orc_star *gs, double x,
+               double y, double t)
+{
+    double sum = 0.0;
+    for (int l = 0; l < L->n_layers; ++l) {
+        double h = L->alt[l];
+        /* cone: a source at finite range sees the layer through a footprint
+           shrunk by (1 - h / range) */
+        double c = gs->is_lgs ? 1.0 - h / gs->range_m : 1.0;
+        /* frozen flow: the screen moves by +v t, so the sample point moves by -v t */
+        double u = L->S / 2.0 + (c * x + gs->theta_x * h - (L->x0[l] + L->vx[l] * t)) / L->dx;
+        double v = L->S / 2.0 + (c * y + gs->theta_y * h - (L->y0[l] + L->vy[l] * t)) / L->dx;
+        sum += orc_bilinear(screens + (size_t)l * L->S * L->S, L->S, u, v);
+    }
+    return sum;
+}
+
+void orc_project_grid(double D, int Np, const orc_layers *L, const float *screens,
+                      const orc_star *gs, double t, double *opd)
+{
+    double dx = D / Np;
+    for (int i = 0; i < Np; ++i)
+        for (int j = 0; j < Np; ++j) {
+            double x = (j - (Np - 1) / 2.0) * dx, y = (i - (Np - 1) / 2.0) * dx;
+            opd[(size_t)i * Np + j] = orc_opd(L, screens, gs, x, y, t);
+        }
+}
+
+/* ---- spot by DFT (Sec. 4 LGS SH; Sec. 2 DFT) ---- */
+
+/* F[k][p] = exp(-2 pi i (k - cN)(p - cn) / N), cN = (N-1)/2, cn = (n-1)/2 */
+static void dft_matrix(int n, int N, double *fr, double *fi)
+{
+    double cN = (N - 1) / 2.0, cn = (n - 1) / 2.0;
+    for (int k = 0; k < N; ++k)
+        for (int p = 0; p < n; ++p) {
+            double a = (k - cN) * (p - cn);     /* a multiple of 1/4: exact */
+            a = fmod(a, (double)N);             /* exact reduction */
+            double ang = -2.0 * M_PI * a / N;
+            fr[k * n + p] = cos(ang);
+            fi[k * n + p] = sin(ang);
+        }
+}
+
+void orc_dft2(int n, int N, const double *xr, const double *xi, double *yr, double *yi)
+{
+    double *fr = malloc(sizeof(double) * N * n), *fi = malloc(sizeof(double) * N * n);
+    double *ur = malloc(sizeof(double) * N * n), *ui = malloc(sizeof(double) * N * n);
+    dft_matrix(n, N, fr, fi);
+    /* U = F X  (N x n) */
+    for (int k = 0; k < N; ++k)
+        for (int q = 0; q < n; ++q) {
+            double sr = 0, si = 0;
+            for (int p = 0; p < n; ++p) {
+                double a = fr[k * n + p], b = fi[k * n + p];
+                double c = xr[p * n + q], d = xi[p * n + q];
+                sr += a * c - b * d;
+                si += a * d + b * c;
+            }
+            ur[k * n + q] = sr;
+            ui[k * n + q] = si;
+        }
+    /* Y = U F^T  (N x N) */
+    for (int k = 0; k < N; ++k)
+        for (int m = 0; m < N; ++m) {
+            double sr = 0, si = 0;
+            for (int q = 0; q < n; ++q) {
+                double a = ur[k * n + q], b = ui[k * n + q];
+                double c = fr[m * n + q], d = fi[m * n + q];
+                sr += a * c - b * d;
+                si += a * d + b * c;
+            }
+            yr[k * N + m] = sr;
+            yi[k * N + m] = si;
+        }
+    free(fr); free(fi); free(ur); free(ui);
+}
+
+/* ---- elongation (Sec. 4 LGS SH: sub-layer tip-tilt, profile weight, Gaussian) ---- */
+
+static double min_image(double d, int N)
+{
+    return d - N * floor(d / N + 0.5);
+}
+
+void orc_elong_kernel(int N, double pix_rad, double rbx, double rby, const orc_star *gs,
+                      double *K)
+{
+    double sigma = gs->spot_fwhm_rad / (2.0 * sqrt(2.0 * log(2.0))) / pix_rad;
+    double h0 = gs->range_m, tot = 0.0;
+    memset(K, 0, sizeof(double) * N * N);
+    for (int s = 0; s < gs->n_na; ++s) {
+        /* slice at h_s seen from the subaperture, relative to the focus at h0 */
+        double k = 1.0 / h0 - 1.0 / gs->na_alt[s];
+        double shx = (rbx - gs->launch_x) * k / pix_rad;
+        double shy = (rby - gs->launch_y) * k / pix_rad;
+        for (int p = 0; p < N; ++p)
+            for (int q = 0; q < N; ++q) {
+                double dy = min_image(p - shy, N), dx = min_image(q - shx, N);
+                K[p * N + q] += gs->na_weight[s] * exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma));
+            }
+    }
+    for (int i = 0; i < N * N; ++i) tot += K[i];
+    for (int i = 0; i < N * N; ++i) K[i] /= tot;
+}
+
+void orc_convolve(int N, const double *I, const double *K, double *out)
+{
+    for (int k = 0; k < N; ++k)
+        for (int m = 0; m < N; ++m) {
+            double s = 0.0;
+            for (int p = 0; p < N; ++p)
+                for (int q = 0; q < N; ++q)
+                    s += I[p * N + q] * K[((k - p + N) % N) * N + ((m - q + N) % N)];
+            out[k * N + m] = s;
+        }
+}
+
+void orc_bin(int N, int nd, const double *I, double *B)
+{
+    int b = N / nd;
+    for (int i = 0; i < nd; ++i)
+        for (int j = 0; j < nd; ++j) {
+            double s = 0.0;
+            for (int r = 0; r < b; ++r)
+                for (int c = 0; c < b; ++c) s += I[(b * i + r) * N + (b * j + c)];
+            B[i * nd + j] = s;
+        }
+}
+
+/* ---- noise (Sec. 4: "final noise-added image") ---- */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64
+   multiplies; the key advances by the Weyl constants between rounds. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 23 random bits + 1/2, scaled: exactly representable, strictly inside (0, 1) */
+static float unit_float(uint32_t x)
+{
+    return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+typedef struct {
+    uint32_t key[2], ctr[4], buf[4];
+    int pos;
+} ustream;
+
+static void us_block(ustream *s, uint32_t block)
+{
+    s->ctr[1] = (s->ctr[1] & 0xFFFF0000u) | (block & 0xFFFFu);
+    orc_philox(s->ctr, s->key, s->buf);
+}
+
+static float us_next(ustream *s)
+{
+    if (s->pos == 4) {
+        us_block(s, (s->ctr[1] & 0xFFFFu) + 1u);
+        s->pos = 0;
+    }
+    return unit_float(s->buf[s->pos++]);
+}
+
+/* log(k!) in FP32: exact sum of logs below 10, Stirling's series above. */
+static float log_factorial(float k)
+{
+    if (k < 10.0f) {
+        float s = 0.0f;
+        for (int j = 2; j <= (int)k; ++j) s = s + logf((float)j);
+        return s;
+    }
+    float x = k + 1.0f;
+    float r = 1.0f / x;
+    float corr = r * (1.0f / 12.0f - (r * r) * (1.0f / 360.0f));
+    return (x - 0.5f) * logf(x) - x + 0.918938533f + corr;
+}
+
+/* Poisson(E) in FP32: sequential-search inversion for E < 16, Hormann's
+   transformed rejection (PTRS, 1993) for E >= 16. */
+static int32_t poisson_f32(float E, ustream *s)
+{
+    if (!(E > 0.0f)) return 0;
+    if (E < 16.0f) {
+        float u = us_next(s);
+        float p = expf(-E);
+        float F = p;
+        int32_t k = 0;
+        while (u > F) {
+            k = k + 1;
+            p = p * E / (float)k;
+            float Fn = F + p;
+            if (Fn == F) break;
+            F = Fn;
+        }
+        return k;
+    }
+    float slam = sqrtf(E);
+    float logE = logf(E);
+    float b = 0.931f + 2.53f * slam;
+    float a = -0.059f + 0.02483f * b;
+    float inv_alpha = 1.1239f + 1.1328f / (b - 3.4f);
+    float vr = 0.9277f - 3.6224f / (b - 2.0f);
+    for (int tries = 0; tries < 1024; ++tries) {
+        float U = us_next(s) - 0.5f;
+        float V = us_next(s);
+        float us = 0.5f - fabsf(U);
+        float kf = floorf((2.0f * a / us + b) * U + E + 0.43f);
+        if (us >= 0.07f && V <= vr) return (int32_t)kf;
+        if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+        float lhs = logf(V) + logf(inv_alpha) - logf(a / (us * us) + b);
+        float rhs = -E + kf * logE - log_factorial(kf);
+        if (lhs <= rhs) return (int32_t)kf;
+    }
+    return (int32_t)floorf(E);
+}
+
+double orc_noise_pixel(float E, float read_noise, uint64_t seed, uint32_t pixel, uint32_t wfs,
+                       double t, int32_t *k_out)
+{
+    ustream s;
+    uint64_t tb;
+    memcpy(&tb, &t, sizeof tb);
+    s.key[0] = (uint32_t)seed;
+    s.key[1] = (uint32_t)(seed >> 32);
+    s.ctr[0] = pixel;
+    s.ctr[1] = wfs << 16;
+    s.ctr[2] = (uint32_t)tb;
+    s.ctr[3] = (uint32_t)(tb >> 32);
+    us_block(&s, 0);
+    /* draws 0 and 1 feed the read noise; the Poisson sampler starts at draw 2 */
+    float u1 = unit_float(s.buf[0]), u2 = unit_float(s.buf[1]);
+    s.pos = 2;
+    int32_t k = poisson_f32(E, &s);
+    if (k_out) *k_out = k;
+    double z = sqrt(-2.0 * log((double)u1)) * cos(2.0 * M_PI * (double)u2);
+    return (double)k + (double)read_noise * z;
+}
+
+void orc_noise_image(int n, const float *E, float read_noise, uint64_t seed, uint32_t wfs,
+                     double t, uint32_t pixel0, double *C, int32_t *K)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        C[i] = orc_noise_pixel(E[i], read_noise, seed, pixel0 + (uint32_t)i, wfs, t,
+                               K ? &K[i] : NULL);
+}
+
+/* ---- centroid (Sec. 3 closed loop: X and Y slopes; Sec. 4: centroid of the image) ---- */
+
+void orc_cog(int nd, const double *C, double *sx, double *sy)
+{
+    double c = (nd - 1) / 2.0, s = 0.0, mx = 0.0, my = 0.0;
+    for (int i = 0; i < nd; ++i)
+        for (int j = 0; j < nd; ++j) {
+            double v = C[i * nd + j];
+            s += v;
+            mx += (j - c) * v;
+            my += (i - c) * v;
+        }
+    if (s > 0.0) {
+        *sx = mx / s;
+        *sy = my / s;
+    } else {
+        *sx = 0.0;
+        *sy = 0.0;
+    }
+}
+
+/* ---- one wavefront sensor ---- */
+
+int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
+                    const orc_layers *L, const float *screens, double t, uint64_t seed,
+                    int noise, int n_sel, const int32_t *sel, double *slopes, double *opd_out,
+                    double *I_out, double *Ie_out, double *E_out, double *C_out)
+{
+    if (g->n <= 0 || g->N < g->n || g->n_det <= 0 || g->N % g->n_det) return -1;
+    int n = g->n, N = g->N, nd = g->n_det, Np = g->n_sub * g->n;
+    int nv = orc_valid_subaps(g->diameter_m, g->obstruction, g->n_sub, n, g->valid_fill, NULL, NULL);
+    int32_t *idx = malloc(sizeof(int32_t) * (nv > 0 ? nv : 1));
+    double *fill = malloc(sizeof(double) * (nv > 0 ? nv : 1));
+    orc_valid_subaps(g->diameter_m, g->obstruction, g->n_sub, n, g->valid_fill, idx, fill);
+    if (!sel) n_sel = nv;
+    double dx = g->diameter_m / Np;
+    double pix_rad = gs->wavelength_m / (N * dx);
+
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < n_sel; ++s) {
+        int v = sel ? sel[s] : s;
+        if (v < 0 || v >= nv) continue;
+        int sy = idx[v] / g->n_sub, sx = idx[v] % g->n_sub;
+        double *xr = calloc((size_t)n * n, sizeof(double)), *xi = calloc((size_t)n * n, sizeof(double));
+        double *yr = malloc(sizeof(double) * N * N), *yi = malloc(sizeof(double) * N * N);
+        double *I = malloc(sizeof(double) * N * N), *Ie = malloc(sizeof(double) * N * N);
+        double *B = malloc(sizeof(double) * nd * nd), *C = malloc(sizeof(double) * nd * nd);
+        /* field of the subaperture: a exp(i 2 pi OPD / lambda) */
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                int i = sy * n + p, j = sx * n + q;
+                double x = (j - (Np - 1) / 2.0) * dx, y = (i - (Np - 1) / 2.0) * dx;
+                double o = orc_opd(L, screens, gs, x, y, t);
+                if (opd_out) opd_out[(size_t)s * n * n + p * n + q] = o;
+                if (lit(g->diameter_m, g->obstruction, Np, i, j)) {
+                    double phi = 2.0 * M_PI * o / gs->wavelength_m;
+                    xr[p * n + q] = cos(phi);
+                    xi[p * n + q] = sin(phi);
+                }
+            }
+        orc_dft2(n, N, xr, xi, yr, yi);
+        for (int k = 0; k < N * N; ++k) I[k] = yr[k] * yr[k] + yi[k] * yi[k];
+        if (gs->is_lgs) {
+            double *K = malloc(sizeof(double) * N * N);
+            double rbx = ((sx + 0.5) * n) * dx - g->diameter_m / 2.0;
+            double rby = ((sy + 0.5) * n) * dx - g->diameter_m / 2.0;
+            orc_elong_kernel(N, pix_rad, rbx, rby, gs, K);
+            orc_convolve(N, I, K, Ie);
+            free(K);
+        } else {
+            memcpy(Ie, I, sizeof(double) * N * N);
+        }
+        orc_bin(N, nd, Ie, B);
+        double sumB = 0.0;
+        for (int k = 0; k < nd * nd; ++k) sumB += B[k];
+        for (int k = 0; k < nd * nd; ++k)
+            B[k] = sumB > 0.0 ? gs->photons * fill[v] * B[k] / sumB : 0.0;
+        for (int k = 0; k < nd * nd; ++k) {
+            if (noise)
+                C[k] = orc_noise_pixel((float)B[k], (float)gs->read_noise, seed,
+                                       (uint32_t)(v * nd * nd + k), (uint32_t)wfs_index, t, NULL);
+            else
+                C[k] = B[k];
+        }
+        orc_cog(nd, C, &slopes[2 * s], &slopes[2 * s + 1]);
+        if (I_out) memcpy(I_out + (size_t)s * N * N, I, sizeof(double) * N * N);
+        if (Ie_out) memcpy(Ie_out + (size_t)s * N * N, Ie, sizeof(double) * N * N);
+        if (E_out) memcpy(E_out + (size_t)s * nd * nd, B, sizeof(double) * nd * nd);
+        if (C_out) memcpy(C_out + (size_t)s * nd * nd, C, sizeof(double) * nd * nd);
+        free(xr); free(xi); free(yr); free(yi); free(I); free(Ie); free(B); free(C);
+    }
+    free(idx);
+    free(fill);
+    return nv;
+}

@@ -1,0 +1,96 @@
+/*
+ * oracle.h -- plain, slow FP64 CPU reference of the open-loop Shack-Hartmann
+ * measurement (Arcidiacono et al., "End to end numerical simulations of the
+ * MAORY multiconjugate adaptive optics system", SPIE 2014, Sec. 4 "Open Loop
+ * generation" and "LGS Shack Hartmann wavefront sensor").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; the two are written
+ * independently from the paper and compared element by element.
+ *
+ * Every function is a direct transcription of a definition: brute-force
+ * matrix DFT, direct periodic convolution, natural-order FP64 sums.  No
+ * blocking, fusion or reordering.
+ *
+ * Parity pins: every function here is pinned by a test against a closed form,
+ * an invariant or a brute-force computation (see tests/test_oracle_pins.py).
+ */
+#ifndef GBWFS_ORACLE_H
+#define GBWFS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double diameter_m, obstruction;   /* telescope */
+    int n_sub, n, N, n_det;           /* subaps across, px/subap, DFT size, det px/subap */
+    double valid_fill;
+} orc_wfs_geom;
+
+typedef struct {
+    int is_lgs;
+    double theta_x, theta_y, range_m, wavelength_m;
+    double launch_x, launch_y, spot_fwhm_rad, photons, read_noise;
+    int n_na;
+    const double *na_alt, *na_weight;
+} orc_star;
+
+typedef struct {
+    int n_layers, S;
+    double dx;
+    const double *alt, *vx, *vy, *x0, *y0;
+} orc_layers;
+
+/* Pupil: binary mask from the pixel-centre test eps*D/2 <= r <= D/2. */
+void orc_pupil_mask(double D, double eps, int Np, uint8_t *mask);
+/* Valid subapertures (fill >= thr), row-major (y then x); returns the count. */
+int orc_valid_subaps(double D, double eps, int n_sub, int n, double thr,
+                     int32_t *idx, double *fill);
+/* Periodic bilinear sample of one S x S screen at (u = column, v = row). */
+double orc_bilinear(const float *scr, int S, double u, double v);
+/* Layered, cone-compressed OPD along the star's line of sight at pupil (x, y), time t. */
+double orc_opd(const orc_layers *L, const float *screens, const orc_star *gs,
+               double x, double y, double t);
+/* OPD on the whole Np x Np pupil grid of a geometry. */
+void orc_project_grid(double D, int Np, const orc_layers *L, const float *screens,
+                      const orc_star *gs, double t, double *opd);
+/* Centred 2-D DFT of an n x n field into N x N: Y = F X F^T. */
+void orc_dft2(int n, int N, const double *xr, const double *xi, double *yr, double *yi);
+/* Sodium elongation kernel (N x N, sums to one) of the subaperture centred at (rbx, rby). */
+void orc_elong_kernel(int N, double pix_rad, double rbx, double rby, const orc_star *gs,
+                      double *K);
+/* Periodic convolution out = I (*) K on an N x N grid. */
+void orc_convolve(int N, const double *I, const double *K, double *out);
+/* b x b binning, b = N / nd. */
+void orc_bin(int N, int nd, const double *I, double *B);
+/* Philox4x32-10 block function. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* One detector pixel's noisy count; *k_out receives the Poisson draw. */
+double orc_noise_pixel(float E, float read_noise, uint64_t seed, uint32_t pixel,
+                       uint32_t wfs, double t, int32_t *k_out);
+void orc_noise_image(int n, const float *E, float read_noise, uint64_t seed, uint32_t wfs,
+                     double t, uint32_t pixel0, double *C, int32_t *K);
+/* Centre of gravity in detector pixels. */
+void orc_cog(int nd, const double *C, double *sx, double *sy);
+
+/*
+ * One wavefront sensor, one time t.  sel lists indices into the valid-subap
+ * list (NULL = all); every output is per selected subap and may be NULL
+ * except slopes:  slopes[n_sel][2], opd[n_sel][n*n], I[n_sel][N*N],
+ * Ie[n_sel][N*N] (after elongation), E[n_sel][nd*nd], C[n_sel][nd*nd].
+ * Returns the number of valid subaps, or -1 on a bad argument.
+ */
+int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
+                    const orc_layers *L, const float *screens, double t, uint64_t seed,
+                    int noise, int n_sel, const int32_t *sel, double *slopes,
+                    double *opd, double *I, double *Ie, double *E, double *C);
+
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

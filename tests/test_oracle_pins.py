@@ -1,0 +1,452 @@
+"""Pins of the FP64 oracle against what the mathematics and the physics fix.
+
+Each test checks one oracle function against something other than itself: a
+closed form (Dirichlet kernel), an independent library routine (numpy FFT), an
+invariant (Parseval, energy conservation, mirror symmetry), an exact special case
+(integer shifts, linear screens) or statistics.  Each is chosen so that a plausible
+slip (dropped term, wrong sign or index, transposed operand) fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1408_0698_gb300 import inputs
+
+RNG = np.random.default_rng(12345)
+
+
+def centred_dft_via_fft(X, N):
+    """Centred DFT through numpy's FFT: Y[k] = e^{i..} FFT(X[p] w^{-cN p})[k] per axis."""
+    n = X.shape[0]
+    cN, cn = (N - 1) / 2.0, (n - 1) / 2.0
+    p = np.arange(n)
+    k = np.arange(N)
+    mod = np.exp(2j * np.pi * cN * p / N)           # w^{-cN p}, w = e^{-2 pi i / N}
+    Xm = X * mod[:, None] * mod[None, :]
+    P = np.zeros((N, N), complex)
+    P[:n, :n] = Xm
+    F = np.fft.fft2(P)
+    ph = np.exp(2j * np.pi * (k * cn - cN * cn) / N)  # w^{-k cn} w^{cN cn}
+    return F * ph[:, None] * ph[None, :]
+
+
+def dirichlet(u, n, N):
+    """|sum_{q<n} e^{-2 pi i (q - cn) u / N}| for real u (closed form)."""
+    u = np.asarray(u, float)
+    s = np.sin(np.pi * u / N)
+    out = np.where(np.abs(s) < 1e-300, float(n), np.sin(np.pi * n * u / N) / np.where(s == 0, 1, s))
+    return out
+
+
+# ---------------------------------------------------------------- P1, P2: the DFT
+
+@pytest.mark.parametrize("n,N", [(2, 4), (3, 8), (4, 8), (5, 12), (8, 16), (6, 24)])
+def test_dft_matches_numpy_fft(n, N):
+    X = RNG.standard_normal((n, n)) + 1j * RNG.standard_normal((n, n))
+    Y = oracle.dft2(X, N)
+    Yf = centred_dft_via_fft(X, N)
+    assert np.max(np.abs(Y - Yf)) <= 1e-12 * np.max(np.abs(Yf))
+
+
+def test_dft_brute_force_tiny():
+    n, N = 3, 5
+    X = RNG.standard_normal((n, n)) + 1j * RNG.standard_normal((n, n))
+    Y = oracle.dft2(X, N)
+    # brute force with integer-shifted indices: (k-cN)(p-cn) expanded term by term
+    cN, cn = (N - 1) / 2, (n - 1) / 2
+    B = np.zeros((N, N), complex)
+    for k in range(N):
+        for m in range(N):
+            acc = 0j
+            for p in range(n):
+                for q in range(n):
+                    acc += X[p, q] * np.exp(-2j * np.pi * ((k - cN) * (p - cn) + (m - cN) * (q - cn)) / N)
+            B[k, m] = acc
+    assert np.allclose(Y, B, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,N", [(4, 8), (6, 24), (10, 32), (8, 16)])
+def test_parseval(n, N):
+    X = np.exp(1j * RNG.uniform(0, 2 * np.pi, (n, n))) * (RNG.uniform(size=(n, n)) > 0.3)
+    Y = oracle.dft2(X, N)
+    assert abs(np.sum(np.abs(Y) ** 2) - N * N * np.sum(np.abs(X) ** 2)) <= 1e-12 * N * N * n * n
+
+
+# ---------------------------------------------------------------- P3, P4: flat and tilt
+
+@pytest.mark.parametrize("n,N", [(8, 16), (10, 32), (6, 24)])
+def test_flat_square_subap_is_dirichlet(n, N):
+    X = np.ones((n, n), complex)
+    I = np.abs(oracle.dft2(X, N)) ** 2
+    u = np.arange(N) - (N - 1) / 2
+    d = dirichlet(u, n, N) ** 2
+    ref = d[:, None] * d[None, :]
+    assert np.max(np.abs(I - ref)) <= 1e-10 * ref.max()
+
+
+@pytest.mark.parametrize("ax,ay", [(0.37, -1.21), (2.0, 0.0), (-3.0, 1.0)])
+def test_tilt_shifts_dirichlet(ax, ay):
+    """phi = 2 pi (ax q + ay p)/N shifts the spot by (ax, ay) FFT px: closed form."""
+    n, N = 8, 16
+    p = np.arange(n)
+    X = np.exp(2j * np.pi * (ay * p[:, None] + ax * p[None, :]) / N)
+    I = np.abs(oracle.dft2(X, N)) ** 2
+    u = np.arange(N) - (N - 1) / 2
+    ref = (dirichlet(u - ay, n, N) ** 2)[:, None] * (dirichlet(u - ax, n, N) ** 2)[None, :]
+    assert np.max(np.abs(I - ref)) <= 1e-10 * ref.max()
+    if float(ax).is_integer() and float(ay).is_integer():
+        I0 = np.abs(oracle.dft2(np.ones((n, n)), N)) ** 2
+        assert np.allclose(I, np.roll(I0, (int(ay), int(ax)), axis=(0, 1)), rtol=0, atol=1e-10 * I0.max())
+
+
+def test_flat_phase_gives_zero_slope_any_mask():
+    cfg = inputs.config1()
+    S = cfg.layers.screen_size
+    r = oracle.measure_wfs(cfg, np.zeros((1, S, S), np.float32), 0, 0.0)
+    assert np.max(np.abs(r["slopes"])) <= 1e-12
+
+
+def _tilt_screen(S, ds, ax, ay):
+    i = np.arange(S) * ds
+    return (ax * i[None, :] + ay * i[:, None]).astype(np.float32)[None]
+
+
+def test_tilt_slope_is_analytic_centroid():
+    """End to end: a tilted wavefront on an interior (fully lit) NGS subap gives the CoG of
+    the binned, shifted Dirichlet spot."""
+    cfg = inputs.config1()
+    g = cfg.geometries[0]
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    lam = cfg.stars[0].wavelength_m
+    n, N, nd = g.n_pix_sub, g.n_fft, g.n_det
+    dx = cfg.telescope.diameter_m / (g.n_sub * n)
+    alpha_x, alpha_y = 0.8 * lam / (N * dx), -0.45 * lam / (N * dx)  # radians of tilt
+    scr = _tilt_screen(S, ds, alpha_x, alpha_y)
+    idx, fill = oracle.valid_subaps(cfg.telescope.diameter_m, 0.0, g.n_sub, n)
+    interior = np.where(fill == 1.0)[0]
+    r = oracle.measure_wfs(cfg, scr, 0, 0.0, sel=interior)
+    ax, ay = alpha_x * N * dx / lam, alpha_y * N * dx / lam
+    u = np.arange(N) - (N - 1) / 2
+    I = (dirichlet(u - ay, n, N) ** 2)[:, None] * (dirichlet(u - ax, n, N) ** 2)[None, :]
+    b = N // nd
+    B = I.reshape(nd, b, nd, b).sum(axis=(1, 3))
+    c = (nd - 1) / 2
+    sx = np.sum((np.arange(nd)[None, :] - c) * B) / B.sum()
+    sy = np.sum((np.arange(nd)[:, None] - c) * B) / B.sum()
+    assert np.max(np.abs(r["slopes"][:, 0] - sx)) < 2e-6
+    assert np.max(np.abs(r["slopes"][:, 1] - sy)) < 2e-6
+    assert sx > 0 and sy < 0
+
+
+# ---------------------------------------------------------------- P5: mirror symmetry
+
+def test_mirror_and_transpose_symmetry():
+    cfg = inputs.config1()
+    g = cfg.geometries[0]
+    S = cfg.layers.screen_size
+    scr = inputs.make_screens(cfg.layers, 77)
+    base = oracle.measure_wfs(cfg, scr, 0, 0.0)["slopes"]
+    idx, _ = oracle.valid_subaps(cfg.telescope.diameter_m, 0.0, g.n_sub, g.n_pix_sub)
+    pos = {int(v): k for k, v in enumerate(idx)}
+    ns = g.n_sub
+    # x -> -x: column i -> S - i (pixel centres sit half way between screen samples)
+    mir = scr[:, :, (S - np.arange(S)) % S].copy()
+    sm = oracle.measure_wfs(cfg, mir, 0, 0.0)["slopes"]
+    for k, v in enumerate(idx):
+        sy, sx = divmod(int(v), ns)
+        j = pos[sy * ns + (ns - 1 - sx)]
+        assert abs(sm[j, 0] + base[k, 0]) < 1e-9 and abs(sm[j, 1] - base[k, 1]) < 1e-9
+    # transpose: swap x and y
+    tr = np.ascontiguousarray(np.transpose(scr, (0, 2, 1)))
+    st = oracle.measure_wfs(cfg, tr, 0, 0.0)["slopes"]
+    for k, v in enumerate(idx):
+        sy, sx = divmod(int(v), ns)
+        j = pos[sx * ns + sy]
+        assert abs(st[j, 0] - base[k, 1]) < 1e-9 and abs(st[j, 1] - base[k, 0]) < 1e-9
+
+
+# ---------------------------------------------------------------- P6: elongation
+
+def _one_slice_star(h0, h1, fwhm, launch=(0.0, 0.0)):
+    return inputs.GuideStar(is_lgs=True, theta_x_rad=0, theta_y_rad=0, range_m=h0,
+                            wavelength_m=589e-9, geometry_index=0, launch_x_m=launch[0],
+                            launch_y_m=launch[1], spot_fwhm_rad=fwhm,
+                            na_alt_m=np.array([h1]), na_weight=np.array([1.0]))
+
+
+def test_elongation_integer_shift_is_roll():
+    N = 16
+    h0, h1 = 90e3, 100e3
+    k = 1.0 / h0 - 1.0 / h1
+    pix = 1e-6
+    # choose subap centre so the shift is exactly (3, -2) FFT px
+    rbx, rby = 3 * pix / k, -2 * pix / k
+    star = _one_slice_star(h0, h1, 1e-3 * pix)  # sigma ~ 4e-4 px: a delta
+    K = oracle.elong_kernel(N, pix, rbx, rby, star)
+    assert abs(K.sum() - 1) < 1e-12
+    I = RNG.uniform(size=(N, N))
+    out = oracle.convolve(I, K)
+    assert np.allclose(out, np.roll(I, (-2, 3), axis=(0, 1)), atol=1e-9)
+
+
+def test_convolution_matches_fft_and_conserves_energy():
+    N = 24
+    cfg = inputs.config2()
+    star = cfg.stars[1]
+    K = oracle.elong_kernel(N, 7.36e-7, 2.5, -1.7, star)
+    assert abs(K.sum() - 1) < 1e-12 and K.min() >= 0
+    I = RNG.uniform(size=(N, N))
+    out = oracle.convolve(I, K)
+    ref = np.real(np.fft.ifft2(np.fft.fft2(I) * np.fft.fft2(K)))
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.abs(ref).max()
+    assert abs(out.sum() - I.sum()) < 1e-11 * I.sum()
+
+
+def test_elongation_centroid_and_antisymmetry():
+    """Narrow slices, small shifts: the kernel's first moment is sum_s w_s Delta_s, and
+    mirroring the subap about the launch point mirrors the kernel."""
+    N = 32
+    pix = 4e-7
+    h, w = inputs.sodium_slices(90e3, 10e3, 8)
+    star = inputs.GuideStar(True, 0, 0, 90e3, 589e-9, 0, launch_x_m=5.0, launch_y_m=0.0,
+                            spot_fwhm_rad=4.0 * pix, na_alt_m=h, na_weight=w)
+    rb = (4.0, 0.5)
+    K = oracle.elong_kernel(N, pix, rb[0], rb[1], star)
+    d = np.arange(N) - N * np.floor(np.arange(N) / N + 0.5)
+    mx = np.sum(d[None, :] * K)
+    my = np.sum(d[:, None] * K)
+    kk = 1 / 90e3 - 1 / h
+    ex = np.sum(w * (rb[0] - 5.0) * kk / pix)
+    ey = np.sum(w * (rb[1] - 0.0) * kk / pix)
+    assert abs(mx - ex) < 1e-6 and abs(my - ey) < 1e-6
+    assert abs(ex) > 0.05  # the slices really are spread
+    K2 = oracle.elong_kernel(N, pix, 2 * 5.0 - rb[0], -rb[1], star)
+    flip = np.roll(K[::-1, ::-1], (1, 1), axis=(0, 1))  # index j -> -j mod N
+    assert np.allclose(K2, flip, atol=1e-14)
+
+
+# ---------------------------------------------------------------- P7: binning / photometry
+
+def test_binning_and_photometry():
+    I = RNG.uniform(size=(32, 32))
+    B = oracle.bin_image(I, 16)
+    assert np.allclose(B, I.reshape(16, 2, 16, 2).sum(axis=(1, 3)), atol=1e-13)
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, 5)
+    g = cfg.geometries[0]
+    _, fill = oracle.valid_subaps(8.0, 0.0, g.n_sub, g.n_pix_sub)
+    for w in (0, 3):
+        r = oracle.measure_wfs(cfg, scr, w, 0.01, stages=True)
+        tot = r["E"].sum(axis=(1, 2))
+        assert np.allclose(tot, cfg.stars[w].photons_per_subap * fill, rtol=1e-12)
+        # Parseval through elongation: sum I' = sum I = N^2 * lit pixels
+        lit = np.round(fill * g.n_pix_sub ** 2)
+        assert np.allclose(r["Ie"].sum(axis=(1, 2)), g.n_fft ** 2 * lit, rtol=1e-11)
+
+
+# ---------------------------------------------------------------- P8, P9, P12: projection
+
+def _layers1(alt, S, ds, vx=0.0, vy=0.0):
+    return inputs.Layers(alt_m=np.array([alt]), wind_vx_mps=np.array([vx]), wind_vy_mps=np.array([vy]),
+                         x0_m=np.zeros(1), y0_m=np.zeros(1), screen_size=S, screen_dx_m=ds)
+
+
+def test_projection_integer_offsets_copy_screen():
+    cfg = inputs.config1()
+    S = 256
+    scr = RNG.standard_normal((1, S, S)).astype(np.float32)
+    # pupil pixel centres sit at half-integer screen coordinates: shift the layer by half a px
+    cfg.layers = _layers1(0.0, S, 0.05)
+    cfg.layers.x0_m[:] = -0.025
+    cfg.layers.y0_m[:] = -0.025
+    opd = oracle.project_grid(cfg, scr, 0, 0.0)
+    # u = 128 + (j - 79.5) + 0.5 = j + 49
+    win = scr[0, 49:49 + 160, 49:49 + 160].astype(np.float64)
+    assert np.max(np.abs(opd - win)) <= 1e-12 * np.abs(win).max()
+    # periodic wrap: moving by a whole screen changes nothing
+    cfg.layers.x0_m[:] = -0.025 + S * 0.05
+    opd2 = oracle.project_grid(cfg, scr, 0, 0.0)
+    assert np.max(np.abs(opd - opd2)) <= 1e-12 * np.abs(win).max()
+
+
+def test_bilinear_exact_on_linear_screen():
+    S = 64
+    i = np.arange(S, dtype=np.float64)
+    scr = (0.25 * i[None, :] - 0.5 * i[:, None] + 3.0).astype(np.float32)
+    for u, v in [(10.3, 20.7), (33.01, 5.99), (0.5, 0.25)]:
+        assert abs(oracle.bilinear(scr, u, v) - (0.25 * u - 0.5 * v + 3.0)) < 1e-12
+
+
+def test_cone_scales_gradient():
+    """A constant-gradient layer at altitude h seen from an LGS at range H: the sampled
+    gradient is the screen's times c = 1 - h/H (closed form)."""
+    S, ds, h, H = 512, 0.05, 8e3, 90e3
+    g = 2e-7
+    i = np.arange(S, dtype=np.float64) * ds
+    scr = np.ascontiguousarray(np.broadcast_to(g * i[None, :], (S, S))).astype(np.float32)[None]
+    cfg = inputs.config2()
+    cfg.layers = _layers1(h, S, ds)
+    star = cfg.stars[0]
+    star.theta_x_rad = star.theta_y_rad = 0.0
+    o1 = oracle.opd(cfg, scr, 0, -2.0, 0.3, 0.0)
+    o2 = oracle.opd(cfg, scr, 0, 2.0, 0.3, 0.0)
+    assert abs((o2 - o1) / 4.0 - g * (1 - h / H)) < 1e-6 * g
+    ngs = cfg.stars[3]
+    o1 = oracle.opd(cfg, scr, 3, -2.0, 0.3, 0.0)
+    o2 = oracle.opd(cfg, scr, 3, 2.0, 0.3, 0.0)
+    assert abs((o2 - o1) / 4.0 - g) < 1e-6 * g
+    # direction: theta * h moves the footprint
+    o2 = oracle.opd(cfg, scr, 0, 2.0, 0.3, 0.0)
+    star.theta_x_rad = 1e-4
+    o3 = oracle.opd(cfg, scr, 0, 2.0, 0.3, 0.0)
+    assert abs((o3 - o2) - g * 1e-4 * h) < 1e-5 * g * 1e-4 * h
+
+
+def test_frozen_flow_long_run_exact():
+    """At t = 2 s with v = 10 m/s and 0.05 m px the footprint has moved by exactly 400 px:
+    the OPD equals that of the screen rolled by 400 px."""
+    cfg = inputs.config1()
+    S = 1024
+    cfg.layers = _layers1(0.0, S, 0.05, vx=10.0, vy=-5.0)
+    scr = RNG.standard_normal((1, S, S)).astype(np.float32)
+    o_t = oracle.project_grid(cfg, scr, 0, 2.0)
+    rolled = np.roll(scr, (-200, 400), axis=(1, 2))
+    o_0 = oracle.project_grid(cfg, rolled, 0, 0.0)
+    assert np.max(np.abs(o_t - o_0)) <= 1e-12 * np.abs(o_0).max()
+
+
+# ---------------------------------------------------------------- P10: noise
+
+def test_philox_uniformity_and_independence():
+    n = 1 << 16
+    vals = np.zeros((n, 4), np.uint32)
+    for i in range(n):
+        vals[i] = oracle.philox([i, 7, 0, 0], [0x1234, 0xABCD])
+    u = (vals >> 9).astype(np.float64) / 2 ** 23
+    h, _ = np.histogram(u.ravel(), bins=64, range=(0, 1))
+    chi2 = np.sum((h - h.mean()) ** 2 / h.mean())
+    assert chi2 < 130  # 63 dof, p ~ 1e-6
+    # lanes uncorrelated; counter increments decorrelate
+    cc = np.corrcoef(u.T)
+    assert np.max(np.abs(cc - np.eye(4))) < 0.02
+    assert abs(np.corrcoef(u[:-1, 0], u[1:, 0])[0, 1]) < 0.02
+    # bits balanced
+    bits = np.unpackbits(vals.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.002
+
+
+@pytest.mark.parametrize("E", [0.3, 3.0, 12.0, 16.0, 40.0, 250.0])
+def test_poisson_moments(E):
+    n = 40000
+    Earr = np.full(n, E, np.float32)
+    C, K = oracle.noise_image(Earr, 0.0, 99, 1, 0.5)
+    assert np.array_equal(C, K.astype(float))  # no read noise
+    m, v = K.mean(), K.var()
+    se = math.sqrt(E / n)
+    assert abs(m - E) < 5 * se
+    assert abs(v / E - 1) < 5 * math.sqrt(2.0 / n) + 0.01
+    # pmf against the exact Poisson pmf (chi-square over the bulk)
+    ks = np.arange(max(0, int(E - 4 * math.sqrt(E))), int(E + 4 * math.sqrt(E)) + 2)
+    logp = np.array([-E + k * math.log(E) - math.lgamma(k + 1) for k in ks])
+    expct = n * np.exp(logp)
+    obs = np.array([(K == k).sum() for k in ks])
+    keep = expct > 20
+    chi2 = np.sum((obs[keep] - expct[keep]) ** 2 / expct[keep])
+    assert chi2 < keep.sum() + 6 * math.sqrt(2 * keep.sum()) + 10
+
+
+def test_read_noise_gaussian():
+    n = 50000
+    C, K = oracle.noise_image(np.zeros(n, np.float32), 3.0, 5, 2, 0.0)
+    assert np.all(K == 0)
+    assert abs(C.mean()) < 5 * 3 / math.sqrt(n)
+    assert abs(C.std() / 3.0 - 1) < 0.02
+    # fourth moment of a Gaussian
+    z = C / 3.0
+    assert abs(np.mean(z ** 4) - 3) < 0.1
+
+
+def test_noise_is_counter_based():
+    E = inputs.random_expected_image(4096, 3)
+    C1, _ = oracle.noise_image(E, 3.0, 11, 4, 0.125)
+    C2, _ = oracle.noise_image(E, 3.0, 11, 4, 0.125)
+    C3, _ = oracle.noise_image(E, 3.0, 11, 4, 0.126)
+    C4, _ = oracle.noise_image(E, 3.0, 11, 5, 0.125)
+    assert np.array_equal(C1, C2)
+    assert not np.array_equal(C1, C3) and not np.array_equal(C1, C4)
+
+
+def test_slope_noise_variance_delta_method():
+    """Photon + read noise on a fixed spot: the CoG variance matches the delta-method
+    prediction sum((x - s)^2 (E + ron^2)) / (sum E)^2."""
+    nd = 8
+    rng = np.random.default_rng(0)
+    y, x = np.mgrid[0:nd, 0:nd] - (nd - 1) / 2
+    E = 500.0 * np.exp(-((x - 0.4) ** 2 + (y + 0.2) ** 2) / 2.0)
+    E = (E / E.sum() * 500.0).astype(np.float32)
+    ron = 1.0
+    sx = []
+    for rep in range(3000):
+        C, _ = oracle.noise_image(E.ravel(), ron, 1, 0, float(rep) * 1e-3)
+        sx.append(oracle.cog(C.reshape(nd, nd))[0])
+    sx = np.array(sx)
+    Ed = E.astype(float)
+    s0 = np.sum(x * Ed) / Ed.sum()
+    pred = np.sum((x - s0) ** 2 * (Ed + ron ** 2)) / Ed.sum() ** 2
+    assert abs(sx.var() / pred - 1) < 0.1
+    assert abs(sx.mean() - s0) < 5 * math.sqrt(pred / len(sx)) + 2e-3
+
+
+# ---------------------------------------------------------------- subaperture counts
+
+def test_valid_subap_counts():
+    """Pupil split: valid-subaperture counts of the configured geometries (fill >= 0.5)."""
+    assert len(oracle.valid_subaps(8.0, 0.0, 20, 8)[0]) == 316
+    assert len(oracle.valid_subaps(8.0, 0.0, 40, 6)[0]) == 1264
+    assert len(oracle.valid_subaps(39.0, 0.28, 80, 10)[0]) == 4632
+    assert len(oracle.valid_subaps(39.0, 0.28, 2, 32)[0]) == 4
+    # the pupil mask: area within one pixel ring of pi (D/2)^2 (1 - eps^2)
+    m = oracle.pupil_mask(39.0, 0.28, 800)
+    area = m.sum() * (39.0 / 800) ** 2
+    exact = np.pi * (19.5 ** 2) * (1 - 0.28 ** 2)
+    assert abs(area - exact) < 2 * np.pi * 19.5 * (39.0 / 800) * 1.3
+    assert np.array_equal(m, m[::-1, :]) and np.array_equal(m, m.T)
+
+
+# ---------------------------------------------------------------- golden fixtures
+
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def _paper_sizes():
+    out = {}
+    for line in open(f"{GOLDEN}/paper_sizes.txt"):
+        line = line.split("#")[0].split()
+        if len(line) == 2:
+            out[line[0]] = float(line[1])
+    return out
+
+
+def test_elt_workload_uses_the_paper_sizes():
+    p = _paper_sizes()
+    c3 = inputs.config3()
+    g = c3.geometries[0]
+    assert g.n_sub * g.n_pix_sub == p["pupil_px"] and g.n_sub == p["lgs_subaps"]
+    assert abs(c3.telescope.diameter_m / (g.n_sub * g.n_pix_sub) - p["pupil_dx_m"]) < 1e-15
+    assert sum(s.is_lgs for s in c3.stars) == p["n_lgs"]
+    assert sum(not s.is_lgs for s in c3.stars) == p["n_ngs"]
+
+
+def test_oracle_regression_fixtures():
+    cfg = inputs.config1()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    ref = np.loadtxt(f"{GOLDEN}/config1_t0.003_slopes.txt")
+    s = oracle.measure_wfs(cfg, scr, 0, 0.003)["slopes"]
+    assert np.allclose(s, ref, rtol=0, atol=1e-12)
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    ref = np.loadtxt(f"{GOLDEN}/config2_lgs1_t0.01_slopes.txt")
+    s = oracle.measure_wfs(cfg, scr, 1, 0.01, sel=ref[:, 0].astype(np.int32))["slopes"]
+    assert np.allclose(s, ref[:, 1:], rtol=0, atol=1e-12)
