@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the Shack-Hartmann measurement on the ELT workload.
+
+One step = one frame of the ELT-class system (800x800 px pupil at 4.875e-2 m,
+obstruction 0.28; 6 LGS 80x80 WFSs with 10-px subapertures padded to 32,
+16x16 detector px, 8 sodium slices; 3 H-band NGS 2x2 WFSs; 10 layers): 27,804
+subaperture spots, projected, imaged, elongated, binned, made noisy and reduced
+to slopes.  Inputs (2048^2 x 10 FP32 screens) are resident in HBM; L2 is
+flushed (256 MB write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun), each rank measures its own
+independent Monte-Carlo run (replicas; no collective on the data path) and the
+value is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SH-WFS spots/s & ELT 6-LGS frames/s at ≤1e-3 px slope err; served p50/p99"
+UNIT = "spots/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def spot_flops(n, N, nd, lgs):
+    """FP32 flops (FMA = 2) of one subaperture in the CUDA-core spot kernel:
+    DFT 8Nn(n+N) + |.|^2 3N^2; LGS elongation+binning through the transfer function
+    4N^2 n + (2n-1) n (8N+6) + 8 (2n-1) nd n + 4 nd^2 (2n-1); NGS binning N^2; the
+    photometry and centroid 6 nd^2."""
+    f = 8 * N * n * (n + N) + 3 * N * N + 6 * nd * nd
+    if lgs:
+        f += 4 * N * N * n + (2 * n - 1) * n * (8 * N + 6) + 8 * (2 * n - 1) * nd * n + 4 * nd * nd * (2 * n - 1)
+    else:
+        f += N * N
+    return f
+
+
+def source_sha(names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1408_0698_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "internal.h"],
+                  "project": ["k_project.cu", "internal.h"]}
+
+
+def ncu_traffic(kernel_key):
+    """Per-launch DRAM bytes of a kernel from profiles/traffic.txt, if the kernel's
+    sources still hash to what was profiled; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = source_sha(KERNEL_SOURCES[kernel_key])
+    for line in open(p):
+        parts = line.split("#")[0].split()
+        if len(parts) == 3 and parts[0] == kernel_key and parts[2] == want:
+            return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(cfg, scr, t, target_s=12.0):
+    """The FP64 oracle, as it stands, on this host's cores, over a bounded sample of the
+    ELT frame: every k-th subaperture of each LGS WFS plus all NGS subapertures."""
+    import oracle
+    nthreads = oracle.num_threads()
+    t0 = time.perf_counter()
+    oracle.measure_wfs(cfg, scr, 0, t, sel=np.arange(0, 4632, 97, dtype=np.int32))
+    per = (time.perf_counter() - t0) / len(range(0, 4632, 97))
+    n_lgs_per_wfs = max(1, int(target_s / per / 6))
+    stride = max(1, 4632 // n_lgs_per_wfs)
+    spots = 0
+    t0 = time.perf_counter()
+    for w, s in enumerate(cfg.stars):
+        if s.is_lgs:
+            sel = np.arange(w % stride, 4632, stride, dtype=np.int32)
+            oracle.measure_wfs(cfg, scr, w, t, sel=sel)
+            spots += len(sel)
+        else:
+            spots += len(oracle.measure_wfs(cfg, scr, w, t)["slopes"])
+    dt = time.perf_counter() - t0
+    return {"value": spots / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"{spots} spots of one ELT frame (every {stride}th LGS subaperture of 6 WFSs "
+                      f"+ all 12 NGS subapertures), FP64, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    """The oracle on the host cores, on bounded samples of the ELT frame (one per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1408_0698_gb300 import inputs
+    cfg = inputs.config3(inputs.PREC_FP32)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    t0 = time.perf_counter()
+    oracle.measure_wfs(cfg, scr, 0, 0.0, sel=np.arange(0, 4632, 193, dtype=np.int32))
+    per = (time.perf_counter() - t0) / len(range(0, 4632, 193))
+    per_step = max(1, min(4632 * 6, int(budget / per)))
+    rng = np.random.default_rng(0)
+
+    def step(k):
+        w = k % 6
+        sel = np.sort(rng.choice(4632, size=min(per_step, 4632), replace=False)).astype(np.int32)
+        oracle.measure_wfs(cfg, scr, w, k * cfg.dt_s, sel=sel)
+        return len(sel)
+
+    for k in range(args.warmup):
+        step(k)
+    spots = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        spots += step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    v = spots / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "ELT frame sample (config3: 6 LGS 80x80 + 3 NGS 2x2, 10 layers)",
+                       "spots_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{per_step} LGS subapertures per step, FP64 oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1408_0698_gb300 import inputs, native
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    prec = inputs.PREC_FP32 if args.precision == "fp32" else inputs.PREC_BF16X3
+    cfg = inputs.config3(prec)
+    scr = inputs.make_screens(cfg.layers, cfg.seed + 17 * rank)   # one MC run per rank
+    w = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
+    spots = w.total
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    s_d = torch.as_tensor(scr).to(dev)
+    slopes = torch.empty((spots, 2), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    dt = cfg.dt_s
+
+    for k in range(args.warmup):
+        native.wfs_measure(w.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
+    torch.cuda.synchronize()
+    native.wfs_sync_status(w.h)
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    native.wfs_timing_enable(w.h, True)
+    native.wfs_timing_read(w.h)
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        native.wfs_measure(w.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    native.wfs_timing_enable(w.h, False)
+    ktimes = native.wfs_timing_read(w.h)
+    native.wfs_sync_status(w.h)
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * spots * args.steps / (ms_max / 1e3)
+    frames = world * args.steps / (ms_max / 1e3)
+
+    # e2e: host buffers through wfs_measure_host, copies inside the timed region
+    host_scr = torch.as_tensor(scr).pin_memory()
+    host_sl = torch.empty((spots, 2)).pin_memory()
+    ke = max(3, min(args.e2e_steps, args.steps))
+    for k in range(3):
+        native.wfs_measure_host(w.h, host_scr.data_ptr(), k * dt, host_sl.data_ptr(), sp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for k in range(ke):
+        native.wfs_measure_host(w.h, host_scr.data_ptr(), k * dt, host_sl.data_ptr(), sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * spots * ke / (float(e_ms.item()) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(host_scr.numel() * 4), "d2h_bytes_per_step": int(host_sl.numel() * 4),
+           "steps": ke}
+
+    # roofline of the dominant kernel, from the live per-kernel events
+    pk, kind = peaks()
+    name, (launches, tot_ms) = max(ktimes.items(), key=lambda kv: kv[1][1])
+    avg_s = tot_ms / launches / 1e3
+    roof = None
+    if name.startswith("spot_fp32"):
+        N = int(name.split("N")[-1])
+        flops = 0
+        for s in cfg.stars:
+            g = cfg.geometries[s.geometry_index]
+            if g.n_fft == N:
+                nv = w.layouts[cfg.stars.index(s)].n_valid
+                flops += nv * spot_flops(g.n_pix_sub, g.n_fft, g.n_det, s.is_lgs)
+        ach = flops / avg_s / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": ncu_traffic("spot"),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3}
+    elif name == "project":
+        nbytes = sum(l.n_valid * l.n * l.n for l in w.layouts) * 4 + 10 * 4 * (1000 ** 2)
+        ach = nbytes / avg_s / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic("project"), "peak_source": kind,
+                "avg_launch_ms": avg_s * 1e3}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "config3 ELT frame: 800x800 px pupil (4.875e-2 m), 6 LGS 80x80 "
+                                   "(n=10, N=32, 16x16 det px, 8 Na slices) + 3 NGS 2x2 (n=32, N=64), "
+                                   "10 layers, noise on",
+                       "spots_per_frame": spots, "dft_precision": args.precision,
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                       "replicas": world},
+            "frames_per_s": frames,
+            "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in ktimes.items()},
+            "gpu_launches": int(sum(v[0] for v in ktimes.values())),
+            "roofline": roof, "e2e": e2e, "clocks": clk, "wall_s_timed": wall}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, scr, 0.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    w.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

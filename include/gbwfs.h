@@ -1,0 +1,267 @@
+/*
+ * gbwfs.h -- C ABI of the GB300-native Shack-Hartmann wavefront-sensor
+ * measurement library (libgbwfs.so).
+ *
+ * The library computes, on one GPU, the open-loop Shack-Hartmann measurement
+ * of Arcidiacono et al., "End to end numerical simulations of the MAORY
+ * multiconjugate adaptive optics system" (SPIE 2014):
+ *
+ *   Sec. 4 "Open Loop generation": the phase screens of the turbulent layers
+ *     are piled up, each shifted for the star direction and for the temporal
+ *     evolution (frozen flow); for a laser guide star the pupil footprint
+ *     shrinks with layer altitude (cone effect).  No Fresnel propagation.
+ *   Sec. 4 "LGS Shack Hartmann wavefront sensor": the wavefront is split into
+ *     subapertures, each spot computed by FFT (a DFT, Sec. 2), the sodium
+ *     layer's sub-layers shift the spot (tip-tilt) and are weighted by the
+ *     sodium profile, the physical extent is a Gaussian convolution, the
+ *     sub-layers are piled up, noise is added and the centroid gives the X and
+ *     Y slopes (Sec. 3, closed-loop block: slopes are the WFS output).
+ *
+ * Conventions (all entry points):
+ *   - Units: lengths in metres, angles in radians, time in seconds, OPD in
+ *     metres, slopes in detector pixels.
+ *   - Images: row index = y, column index = x, row-major.  Valid
+ *     subapertures are ordered row-major (y, then x) over the n_sub x n_sub
+ *     grid; a subaperture is valid when its lit-pixel fraction >= valid_fill.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device pointers are plain CUDA device addresses (for example
+ *     torch.Tensor.data_ptr()); the caller keeps ownership of every buffer it
+ *     passes and must keep it alive until the stream work completes.
+ *   - Errors: argument errors are detected on the host before anything is
+ *     enqueued and returned synchronously; the message is available from
+ *     wfs_last_error().  Errors found by a kernel are written to a device
+ *     status word that wfs_sync_status() reads back.
+ *   - Threading: a handle may be used by one host thread at a time
+ *     (thread-compatible, not thread-safe).  Different handles are
+ *     independent.
+ */
+#ifndef GBWFS_H
+#define GBWFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wfs_ctx *wfs_handle;
+typedef struct wfs_batch_ctx *wfs_batch;
+
+typedef enum {
+    WFS_OK = 0,
+    WFS_EINVAL = 1,       /* bad argument (see wfs_last_error) */
+    WFS_ENOMEM = 2,       /* device or host allocation failed */
+    WFS_ECUDA = 3,        /* a CUDA runtime call failed */
+    WFS_EBUSY = 4,        /* handle in use */
+    WFS_ETIMEOUT = 5,     /* a bounded device wait gave up */
+    WFS_EUNSUPPORTED = 6  /* valid request this build does not implement */
+} wfs_status;
+
+/* DFT arithmetic of a geometry (the rest of the path is FP32 throughout). */
+enum {
+    WFS_PREC_FP32 = 0,    /* plain FP32 on the CUDA cores */
+    WFS_PREC_BF16X3 = 1,  /* tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
+    WFS_PREC_FP16S = 2    /* reserved: FP16 with scaling */
+};
+
+/* Telescope pupil: circular, diameter D, central obstruction eps (fraction of D). */
+typedef struct {
+    double diameter_m;
+    double obstruction;
+} wfs_telescope;
+
+/*
+ * Shack-Hartmann geometry (Sec. 4 LGS SH: the WF is split into subapertures
+ * and each spot is computed by a DFT).  The pupil is sampled on an
+ * (n_sub*n_pix_sub)^2 grid of pitch D/(n_sub*n_pix_sub); each subaperture's
+ * n_pix_sub^2 field is zero-padded to an n_fft^2 DFT and the intensity binned
+ * to n_det^2 detector pixels.  Requires n_fft >= n_pix_sub, n_fft % n_det == 0,
+ * n_pix_sub <= 32, n_fft <= 64; an LGS geometry also needs
+ * n_fft >= 2*n_pix_sub - 1.
+ */
+typedef struct {
+    int n_sub;
+    int n_pix_sub;
+    int n_fft;
+    int n_det;
+    double valid_fill;  /* valid-subaperture threshold on the lit fraction */
+    int precision;      /* WFS_PREC_* */
+} wfs_geometry;
+
+/*
+ * One guide star and its wavefront sensor.
+ *   theta_*: direction of the star.  range_m: LGS focus / sodium centroid
+ *   altitude (ignored for an NGS, which is at infinity).  launch_*: position
+ *   of the LGS launch telescope in the pupil plane.  spot_fwhm_rad: FWHM of
+ *   the Gaussian physical extent of the LGS spot (Sec. 4, must be > 0 for an
+ *   LGS).  photons_per_subap: photons in a fully lit subaperture per frame.
+ *   read_noise_e: detector read-noise sigma in electrons.  n_na sodium
+ *   slices at altitudes na_alt_m with weights na_weight (the sodium profile,
+ *   normalised by the library).  Arrays are copied by wfs_create.
+ */
+typedef struct {
+    int is_lgs;
+    double theta_x_rad, theta_y_rad;
+    double range_m;
+    double wavelength_m;
+    double launch_x_m, launch_y_m;
+    double spot_fwhm_rad;
+    double photons_per_subap;
+    double read_noise_e;
+    int geometry_index;
+    int n_na;
+    const double *na_alt_m;
+    const double *na_weight;
+} wfs_guide_star;
+
+/*
+ * Turbulent layers (Sec. 4 Open Loop generation).  Each layer is a periodic
+ * screen_size^2 OPD screen of pitch screen_dx_m at altitude alt_m, moving
+ * with wind (vx, vy) from initial offset (x0, y0): at time t the point
+ * sampled for pupil position x is screen position c*x + theta*h - (x0 + v t),
+ * with c = 1 - h/range for an LGS and 1 for an NGS, relative to the screen
+ * centre.  Arrays are copied by wfs_create.
+ */
+typedef struct {
+    int n_layers;
+    int screen_size;
+    double screen_dx_m;
+    const double *alt_m;
+    const double *wind_vx_mps, *wind_vy_mps;
+    const double *x0_m, *y0_m;
+} wfs_layers;
+
+/*
+ * Optional per-stage device outputs of wfs_measure_stages (any may be NULL).
+ * Each is the concatenation over guide stars, in guide-star order, of
+ * n_valid_w blocks (offsets from wfs_layout):
+ *   opd[n_valid][n*n]        projected OPD of each subaperture (m)
+ *   intensity[n_valid][N*N]  spot |DFT|^2 before elongation
+ *   expected[n_valid][nd*nd] expected detector counts (after elongation,
+ *                            binning and photometry, before noise)
+ *   counts[n_valid][nd*nd]   noisy counts (equal to expected without noise)
+ */
+typedef struct {
+    float *opd;
+    float *intensity;
+    float *expected;
+    float *counts;
+} wfs_stage_out;
+
+typedef struct {
+    int n_valid, n, n_fft, n_det, is_lgs;
+    size_t slope_offset;      /* in floats, into slopes_out (2 per subaperture) */
+    size_t opd_offset;        /* in floats, into wfs_stage_out.opd */
+    size_t intensity_offset;  /* in floats, into wfs_stage_out.intensity */
+    size_t det_offset;        /* in floats, into wfs_stage_out.expected / counts */
+} wfs_layout_info;
+
+/*
+ * wfs_create -- validate the description, build the valid-subaperture tables,
+ * the pupil mask bits, the DFT and elongation tables, and allocate the
+ * handle's device memory (cudaMalloc on the current device).  Host arrays are
+ * copied.  seed keys the noise generator; noise_enable = 0 gives the expected
+ * image (noise-free slopes).  On success *out owns all of it until
+ * wfs_destroy.  Returns WFS_EINVAL (bad description), WFS_EUNSUPPORTED,
+ * WFS_ENOMEM or WFS_ECUDA.
+ */
+wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs,
+                      int n_geom, const wfs_geometry *geom, const wfs_layers *layers,
+                      uint64_t seed, int noise_enable, wfs_handle *out);
+
+/* Release everything the handle owns (synchronises the device first). */
+wfs_status wfs_destroy(wfs_handle h);
+
+/*
+ * wfs_measure -- one frame at time t_s for every guide star of the handle.
+ *   screens: device, float [n_layers][screen_size][screen_size], OPD (m).
+ *   slopes_out: device, float [sum_w n_valid_w][2], (x, y) in detector pixels,
+ *     guide stars concatenated in order.
+ * Asynchronous on `stream`; no allocation, no host synchronisation; inputs
+ * are not modified.  Two calls on one handle must not overlap in time on
+ * different streams (they share the handle's device scratch).
+ */
+wfs_status wfs_measure(wfs_handle h, const float *screens, double t_s, float *slopes_out,
+                       void *stream);
+
+/* As wfs_measure, also writing the intermediate stages selected in *stages. */
+wfs_status wfs_measure_stages(wfs_handle h, const float *screens, double t_s,
+                              float *slopes_out, const wfs_stage_out *stages, void *stream);
+
+/*
+ * wfs_measure_host -- the same frame with HOST buffers: copies screens_host
+ * (host, same layout as `screens`; pinned memory for asynchronous copies) to
+ * the device, measures, and copies the slopes back to slopes_host.  The first
+ * call allocates the device staging buffers (screens and slopes) that later
+ * calls reuse.  Asynchronous on `stream`: slopes_host is valid after the
+ * stream is synchronised.
+ */
+wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
+                            float *slopes_host, void *stream);
+
+/* Switch the noise stage on or off for later calls. */
+wfs_status wfs_set_noise(wfs_handle h, int enable);
+
+/* Number of valid subapertures of guide star gs, and of all guide stars. */
+wfs_status wfs_num_valid(wfs_handle h, int gs, int *n);
+wfs_status wfs_total_valid(wfs_handle h, int *n);
+/* Valid subaperture ids (sy * n_sub + sx) of guide star gs into host_idx[n_valid]. */
+wfs_status wfs_valid_map(wfs_handle h, int gs, int32_t *host_idx);
+/* Sizes and buffer offsets of guide star gs. */
+wfs_status wfs_layout(wfs_handle h, int gs, wfs_layout_info *out);
+/*
+ * Synchronise the handle's last stream and read the device status word
+ * (WFS_OK, or the first error a kernel recorded), then clear it.
+ */
+wfs_status wfs_sync_status(wfs_handle h);
+/* Last error message of the handle (or, for h == NULL, of the calling thread). */
+const char *wfs_last_error(wfs_handle h);
+
+/*
+ * wfs_noise_apply -- the noise stage alone (Sec. 4: "final noise-added
+ * image"), the same device function the measurement uses:
+ *   counts[i] = Poisson(expected[i]) + read_noise_e * z
+ * with the uniforms drawn from Philox4x32-10 keyed by seed, counter
+ * (pixel0 + i, wfs_index << 16 | block, bits of t_s).  expected and counts
+ * are device float[n]; expected >= 0.
+ */
+wfs_status wfs_noise_apply(const float *expected, int n, float read_noise_e, uint64_t seed,
+                           uint32_t wfs_index, double t_s, uint32_t pixel0, float *counts,
+                           void *stream);
+
+/*
+ * Batching: several handles (uneven geometries) measured by one call.
+ * wfs_batch_create keeps the handle pointers (they must outlive the batch);
+ * wfs_batch_measure takes per-handle screens, times and slope buffers
+ * (host arrays of n device pointers / times).
+ */
+wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out);
+wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const double *t_s,
+                             float *const *slopes_out, void *stream);
+wfs_status wfs_batch_destroy(wfs_batch b);
+
+/*
+ * Kernel timing (measurement aid).  While enabled, every kernel launch of the
+ * handle's later calls is bracketed by CUDA events recorded on the launch
+ * stream.  wfs_timing_read synchronises those events, writes up to `max`
+ * per-kernel totals (launch count and summed event time in milliseconds) to
+ * out, sets *n_out to the number of distinct kernels, and resets the totals.
+ * At most 65536 launches are recorded between two reads (WFS_EBUSY beyond).
+ */
+typedef struct {
+    char name[48];
+    int launches;
+    double total_ms;
+} wfs_kernel_time;
+
+wfs_status wfs_timing_enable(wfs_handle h, int enable);
+wfs_status wfs_timing_read(wfs_handle h, int max, wfs_kernel_time *out, int *n_out);
+
+/* Library version string. */
+const char *wfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBWFS_H */

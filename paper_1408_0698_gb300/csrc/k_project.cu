@@ -1,0 +1,89 @@
+// k_project.cu -- layered frozen-flow projection (Sec. 4 "Open Loop
+// generation": the layers' screens are piled up, each shifted for the star's
+// direction and for the temporal evolution; for an LGS the pupil projection
+// shrinks with altitude, c = 1 - h / range).  No Fresnel propagation.
+//
+// For pupil pixel x (metres from the pupil centre) and layer l the sampled
+// screen coordinate, in screen pixels from the screen origin, is
+//     u = S/2 + (c_l x + theta h_l - (x0_l + v_l t)) / ds
+// split as  u = [S/2 + (theta h_l - x0_l - v_l t)/ds]  +  c_l (dx/ds) j'
+// where j' is the pixel's half-integer column offset from the pupil centre.
+// The first (time-dependent, possibly large) term is evaluated once per CTA
+// in FP64 and split into an integer base (mod S) and an FP32 fraction; the
+// per-pixel term is FP32.  This keeps long runs (large v t) exact to FP64
+// rounding while every pixel stays in FP32.
+//
+// Output layout: per WFS, [n_valid][n][n] (subaperture-tiled), so the spot
+// kernel reads each subaperture's n*n OPD as one contiguous block.
+#include "internal.h"
+
+namespace gbwfs {
+
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ ProjArgs a) {
+    __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
+    __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers];
+
+    int w = 0;
+    while (w + 1 < a.n_wfs && (int)blockIdx.x >= a.w[w + 1].block_begin) ++w;
+    const ProjWfs &W = a.w[w];
+    const int S = a.S;
+
+    if ((int)threadIdx.x < a.n_layers) {
+        const int l = threadIdx.x;
+        const double h = a.alt[l];
+        const double c = W.is_lgs ? 1.0 - h / W.range_m : 1.0;
+        const double ou = 0.5 * S + (W.theta_x * h - (a.x0[l] + a.vx[l] * a.t)) / a.ds;
+        const double ov = 0.5 * S + (W.theta_y * h - (a.y0[l] + a.vy[l] * a.t)) / a.ds;
+        const double bu = floor(ou), bv = floor(ov);
+        s_fu[l] = (float)(ou - bu);
+        s_fv[l] = (float)(ov - bv);
+        double mu = fmod(bu, (double)S), mv = fmod(bv, (double)S);
+        if (mu < 0) mu += S;
+        if (mv < 0) mv += S;
+        s_bu[l] = (int)mu;
+        s_bv[l] = (int)mv;
+        s_c[l] = (float)(c * W.pupil_dx_over_ds);
+    }
+    __syncthreads();
+
+    const int n = W.n, nn = n * n;
+    const int pix = ((int)blockIdx.x - W.block_begin) * blockDim.x + threadIdx.x;
+    if (pix >= W.n_valid * nn) return;
+    const int v = pix / nn, r = pix - v * nn, p = r / n, q = r - p * n;
+    const int id = __ldg(W.subap + v);
+    const int sy = id / W.n_sub, sx = id - sy * W.n_sub;
+    const float half = 0.5f * (float)(W.n_sub * n - 1);
+    const float xr = (float)(sx * n + q) - half;  // exact half-integers
+    const float yr = (float)(sy * n + p) - half;
+
+    float acc = 0.0f;
+    for (int l = 0; l < a.n_layers; ++l) {
+        const float u = fmaf(s_c[l], xr, s_fu[l]);
+        const float vv = fmaf(s_c[l], yr, s_fv[l]);
+        const float fu0 = floorf(u), fv0 = floorf(vv);
+        const float f = u - fu0, g = vv - fv0;
+        int i0 = s_bu[l] + (int)fu0, j0 = s_bv[l] + (int)fv0;
+        // |c x / ds| < S is enforced when the handle is created: one wrap suffices
+        i0 += (i0 < 0) ? S : 0;
+        i0 -= (i0 >= S) ? S : 0;
+        j0 += (j0 < 0) ? S : 0;
+        j0 -= (j0 >= S) ? S : 0;
+        const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
+        const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+        const float *scr = a.screens + (size_t)l * S * S;
+        const float s00 = __ldg(scr + (size_t)j0 * S + i0), s01 = __ldg(scr + (size_t)j0 * S + i1);
+        const float s10 = __ldg(scr + (size_t)j1 * S + i0), s11 = __ldg(scr + (size_t)j1 * S + i1);
+        const float top = fmaf(f, s01 - s00, s00);
+        const float bot = fmaf(f, s11 - s10, s10);
+        acc += fmaf(g, bot - top, top);
+    }
+    W.opd[pix] = acc;
+}
+
+cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) {
+    if (total_blocks <= 0) return cudaSuccess;
+    k_project<<<total_blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace gbwfs

@@ -1,0 +1,58 @@
+"""Helpers for the GPU tests: run a configuration through the C ABI with stage outputs."""
+import numpy as np
+import torch
+
+from paper_1408_0698_gb300 import native
+
+
+def run_library(cfg, screens, t, seed=0, noise=False, stages=True, handle=None):
+    """Returns (per-WFS dict list, Wfs).  Everything goes through wfs_measure_stages."""
+    dev = torch.device("cuda:0")
+    w = handle or native.Wfs(cfg, seed=seed, noise=noise)
+    if handle is not None:
+        native.wfs_set_noise(w.h, noise)
+    scr = torch.as_tensor(np.ascontiguousarray(screens, dtype=np.float32)).to(dev)
+    slopes = torch.full((w.total, 2), float("nan"), device=dev)
+    tot_opd = sum(l.n_valid * l.n * l.n for l in w.layouts)
+    tot_int = sum(l.n_valid * l.n_fft * l.n_fft for l in w.layouts)
+    tot_det = sum(l.n_valid * l.n_det * l.n_det for l in w.layouts)
+    if stages:
+        opd = torch.full((max(tot_opd, 1),), float("nan"), device=dev)
+        inten = torch.full((max(tot_int, 1),), float("nan"), device=dev)
+        E = torch.full((max(tot_det, 1),), float("nan"), device=dev)
+        Cc = torch.full((max(tot_det, 1),), float("nan"), device=dev)
+        native.wfs_measure_stages(w.h, scr.data_ptr(), t, slopes.data_ptr(), opd.data_ptr(),
+                                  inten.data_ptr(), E.data_ptr(), Cc.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    else:
+        native.wfs_measure(w.h, scr.data_ptr(), t, slopes.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    native.wfs_sync_status(w.h)
+    out = []
+    s_all = slopes.cpu().numpy()
+    if stages:
+        o_all, i_all, e_all, c_all = (x.cpu().numpy() for x in (opd, inten, E, Cc))
+    for L in w.layouts:
+        d = {"slopes": s_all[L.slope_offset // 2: L.slope_offset // 2 + L.n_valid]}
+        if stages:
+            nv, n, N, nd = L.n_valid, L.n, L.n_fft, L.n_det
+            d["opd"] = o_all[L.opd_offset: L.opd_offset + nv * n * n].reshape(nv, n, n)
+            d["I"] = i_all[L.intensity_offset: L.intensity_offset + nv * N * N].reshape(nv, N, N)
+            d["E"] = e_all[L.det_offset: L.det_offset + nv * nd * nd].reshape(nv, nd, nd)
+            d["C"] = c_all[L.det_offset: L.det_offset + nv * nd * nd].reshape(nv, nd, nd)
+        out.append(d)
+    return out, w
+
+
+def rel_per_subap(a, b):
+    """max over subaps of ||a - b||_2 / ||b||_2."""
+    a = a.reshape(a.shape[0], -1).astype(np.float64)
+    b = b.reshape(b.shape[0], -1).astype(np.float64)
+    num = np.linalg.norm(a - b, axis=1)
+    den = np.linalg.norm(b, axis=1)
+    return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+def slope_rms(a, b):
+    return float(np.sqrt(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2)))

@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared symbol, and
+rejects bad descriptions synchronously, before any device work."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+from paper_1408_0698_gb300 import inputs, native
+
+
+def test_library_exports_every_header_symbol():
+    L = native.lib()
+    names = native.header_symbols()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(names) == set(native._SIGS), "binding and header disagree"
+    assert "sm_103a" in native.wfs_version()
+
+
+def _create(cfg, **kw):
+    tel, stars, geoms, lay, keep = native.marshal(cfg)
+    for k, v in kw.items():
+        obj, field, val = v
+        setattr({"tel": tel, "lay": lay, "g0": geoms[0], "s0": stars[0]}[obj], field, val)
+    h = native._H()
+    st = native.lib().wfs_create(C.byref(tel), len(stars), (native.wfs_guide_star * len(stars))(*stars),
+                                 len(geoms), (native.wfs_geometry * len(geoms))(*geoms), C.byref(lay),
+                                 0, 0, C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("edit,expect", [
+    (("tel", "diameter_m", -1.0), native.WFS_EINVAL),
+    (("tel", "obstruction", 1.0), native.WFS_EINVAL),
+    (("g0", "n_pix_sub", 40), native.WFS_EINVAL),
+    (("g0", "n_fft", 4), native.WFS_EINVAL),
+    (("g0", "n_det", 7), native.WFS_EINVAL),
+    (("g0", "n_fft", 128), native.WFS_EINVAL),
+    (("g0", "valid_fill", 0.0), native.WFS_EINVAL),
+    (("g0", "precision", 9), native.WFS_EINVAL),
+    (("s0", "wavelength_m", 0.0), native.WFS_EINVAL),
+    (("s0", "geometry_index", 3), native.WFS_EINVAL),
+    (("s0", "spot_fwhm_rad", 0.0), native.WFS_EINVAL),
+    (("s0", "range_m", math.inf), native.WFS_EINVAL),
+    (("s0", "n_na", 0), native.WFS_EINVAL),
+    (("lay", "n_layers", 0), native.WFS_EINVAL),
+    (("lay", "screen_size", 64), native.WFS_EINVAL),   # footprint larger than the screen
+    (("lay", "screen_dx_m", math.nan), native.WFS_EINVAL),
+])
+def test_bad_descriptions_rejected(edit, expect):
+    cfg = inputs.config2()
+    st, h = _create(cfg, e=edit)
+    assert st == expect
+    assert not h.value
+    assert native.wfs_last_error(None)
+
+
+def test_lgs_needs_band_limited_dft():
+    cfg = inputs.config2()
+    st, _ = _create(cfg, e1=("g0", "n_fft", 10), e2=("g0", "n_det", 5))   # 10 < 2*6-1
+    assert st == native.WFS_EUNSUPPORTED
+
+
+def test_null_arguments():
+    L = native.lib()
+    assert L.wfs_measure(None, None, 0.0, None, None) == native.WFS_EINVAL
+    assert L.wfs_destroy(None) == native.WFS_EINVAL
+    assert L.wfs_create(None, 1, None, 1, None, None, 0, 0, None) == native.WFS_EINVAL
+    assert L.wfs_noise_apply(None, 10, 1.0, 0, 0, 0.0, 0, None, None) == native.WFS_EINVAL
+    n = C.c_int()
+    assert L.wfs_num_valid(None, 0, C.byref(n)) == native.WFS_EINVAL
+
+
+def test_no_silent_cpu_path_without_gpu():
+    """On a machine without a GPU a valid description fails with a CUDA error: the library
+    has no host fallback."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    st, h = _create(inputs.config1())
+    assert st in (native.WFS_ECUDA, native.WFS_ENOMEM)
+    assert not h.value

@@ -1,0 +1,268 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Bars: noise-free slopes <= 1e-3 detector-pixel RMS; spot intensities and expected
+detector images <= 1e-4 relative (||a - b||_2 / ||b||_2 per subaperture, max over
+subaperture); projected OPD <= 1e-6 relative; valid-subaperture maps and integer
+Poisson draws bit-exact (draws up to FP32-vs-FP64 rounding of the mean).
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1408_0698_gb300 import inputs, native
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from _gpu import rel_per_subap, run_library, slope_rms  # noqa: E402
+
+SLOPE_RMS = 1e-3
+INT_REL = 1e-4
+OPD_REL = 1e-6
+
+
+def _check_wfs(cfg, scr, t, gpu, sel=None, noise=False, seed=0):
+    for w, d in enumerate(gpu):
+        sel_w = sel[w] if sel is not None else None
+        ref = oracle.measure_wfs(cfg, scr, w, t, seed=seed, noise=noise, sel=sel_w, stages=True)
+        pick = (lambda a: a[sel_w]) if sel_w is not None else (lambda a: a)
+        assert rel_per_subap(pick(d["opd"]), ref["opd"]) < OPD_REL, f"wfs {w} opd"
+        assert rel_per_subap(pick(d["I"]), ref["I"]) < INT_REL, f"wfs {w} intensity"
+        assert rel_per_subap(pick(d["E"]), ref["E"]) < INT_REL, f"wfs {w} expected image"
+        if not noise:
+            assert slope_rms(pick(d["slopes"]), ref["slopes"]) < SLOPE_RMS, f"wfs {w} slopes"
+            assert np.max(np.abs(pick(d["slopes"]) - ref["slopes"])) < 5 * SLOPE_RMS
+        # photometry closed form: sum E = photons * fill
+        g = cfg.geometries[cfg.stars[w].geometry_index]
+        tot = pick(d["E"]).reshape(len(ref["E"]), -1).sum(axis=1)
+        assert np.allclose(tot, ref["E"].reshape(len(ref["E"]), -1).sum(axis=1), rtol=1e-5)
+
+
+def test_valid_maps_bit_exact():
+    for cfg in (inputs.config1(), inputs.config2(), inputs.config3(inputs.PREC_FP32)):
+        w = native.Wfs(cfg)
+        for k, s in enumerate(cfg.stars):
+            g = cfg.geometries[s.geometry_index]
+            idx, _ = oracle.valid_subaps(cfg.telescope.diameter_m, cfg.telescope.obstruction,
+                                         g.n_sub, g.n_pix_sub, g.valid_fill)
+            assert np.array_equal(native.wfs_valid_map(w.h, k), idx)
+        w.close()
+
+
+def test_config1_full_parity():
+    cfg = inputs.config1()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    for t in (0.0, 0.003, 0.009):
+        gpu, w = run_library(cfg, scr, t)
+        _check_wfs(cfg, scr, t, gpu)
+        w.close()
+
+
+def test_config2_full_parity():
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    gpu, w = run_library(cfg, scr, 0.05)
+    _check_wfs(cfg, scr, 0.05, gpu)
+    w.close()
+
+
+def test_config3_sampled_parity_full_launch():
+    """The ELT frame at full size in the benchmark's launch configuration; sampled
+    subapertures (every 29th LGS subaperture, all NGS) checked against the oracle."""
+    cfg = inputs.config3(inputs.PREC_FP32)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    t = 0.137
+    gpu, w = run_library(cfg, scr, t)
+    sel = []
+    for k, d in enumerate(gpu):
+        nv = len(d["slopes"])
+        sel.append(np.arange(k, nv, 29, dtype=np.int32) if cfg.stars[k].is_lgs else np.arange(nv, dtype=np.int32))
+    _check_wfs(cfg, scr, t, gpu, sel=sel)
+    # every subaperture's expected image sums to photons * fill (property at any size)
+    for k, d in enumerate(gpu):
+        g = cfg.geometries[cfg.stars[k].geometry_index]
+        _, fill = oracle.valid_subaps(cfg.telescope.diameter_m, cfg.telescope.obstruction, g.n_sub, g.n_pix_sub)
+        assert np.allclose(d["E"].reshape(len(fill), -1).sum(axis=1), cfg.stars[k].photons_per_subap * fill, rtol=2e-5)
+        assert np.all(np.isfinite(d["slopes"]))
+    w.close()
+
+
+def test_noise_stage_bit_exact_poisson():
+    E = inputs.random_expected_image(1 << 18, 11, max_mean=80.0)
+    dev = torch.device("cuda:0")
+    e_d = torch.as_tensor(E).to(dev)
+    c_d = torch.empty_like(e_d)
+    native.wfs_noise_apply(e_d.data_ptr(), E.size, 0.0, 1234, 5, 0.25, 77, c_d.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    C_gpu = c_d.cpu().numpy()
+    C_orc, K = oracle.noise_image(E, 0.0, 1234, 5, 0.25, 77)
+    assert np.all(C_gpu == np.round(C_gpu))
+    match = np.mean(C_gpu == K)
+    assert match >= 0.9999, match
+    assert np.all(np.abs(C_gpu - K)[C_gpu != K] <= 1)
+    # read noise only: Gaussian values agree to FP32 rounding
+    Z = np.zeros(1 << 16, np.float32)
+    z_d = torch.as_tensor(Z).to(dev)
+    native.wfs_noise_apply(z_d.data_ptr(), Z.size, 3.0, 99, 1, 1.5, 0, c_d.data_ptr(),
+                           torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    Cz, _ = oracle.noise_image(Z, 3.0, 99, 1, 1.5, 0)
+    assert np.max(np.abs(c_d.cpu().numpy()[:Z.size] - Cz)) < 1e-4
+
+
+def test_noisy_frame_matches_oracle():
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    t = 0.02
+    gpu, w = run_library(cfg, scr, t, seed=42, noise=True)
+    for k in (0, 3):
+        ref = oracle.measure_wfs(cfg, scr, k, t, seed=42, noise=True, stages=True)
+        same = np.abs(gpu[k]["C"] - ref["C"]) < 1e-3
+        assert same.mean() >= 0.999, same.mean()
+        ok = np.all(same.reshape(len(same), -1), axis=1)
+        assert slope_rms(gpu[k]["slopes"][ok], ref["slopes"][ok]) < SLOPE_RMS
+    w.close()
+
+
+def test_noise_statistics_on_gpu():
+    """Counts over many frames of a frozen screen: per-pixel mean E and variance
+    E + ron^2 (P10)."""
+    cfg = inputs.config1()
+    cfg.stars[0].read_noise_e = 2.0
+    cfg.layers = dataclasses.replace(cfg.layers, wind_vx_mps=np.zeros(1), wind_vy_mps=np.zeros(1))
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    w = native.Wfs(cfg, seed=7, noise=True)
+    dev = torch.device("cuda:0")
+    s_d = torch.as_tensor(scr).to(dev)
+    nd = cfg.geometries[0].n_det
+    slopes = torch.empty((w.total, 2), device=dev)
+    E = torch.empty(w.total * nd * nd, device=dev)
+    C = torch.empty(w.total * nd * nd, device=dev)
+    acc1 = torch.zeros_like(C, dtype=torch.float64)
+    acc2 = torch.zeros_like(C, dtype=torch.float64)
+    reps = 400
+    for r in range(reps):
+        native.wfs_measure_stages(w.h, s_d.data_ptr(), 1e-3 * r, slopes.data_ptr(), 0, 0, E.data_ptr(),
+                                  C.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        acc1 += C.double()
+        acc2 += C.double() ** 2
+    torch.cuda.synchronize()
+    m = (acc1 / reps).cpu().numpy()
+    v = (acc2 / reps).cpu().numpy() - m ** 2
+    e = E.cpu().numpy().astype(np.float64)
+    z_mean = (m - e) / np.sqrt((e + 4.0) / reps)
+    assert abs(z_mean.mean()) < 0.05 and 0.9 < z_mean.std() < 1.1
+    big = e > 5
+    ratio = v[big] / (e[big] + 4.0)
+    assert abs(np.mean(ratio) - 1) < 0.02
+    w.close()
+
+
+def test_long_run_offsets_fp64():
+    """Frozen-flow offsets are formed in FP64: OPD at t = 2 s and at t = 1e4 s match the
+    FP64 oracle (an FP32 offset would be off by ~1e-3 px after 1e4 s at 10 m/s)."""
+    cfg = inputs.config1()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    for t in (2.0, 1.0e4 + 0.0123):
+        gpu, w = run_library(cfg, scr, t)
+        ref = oracle.measure_wfs(cfg, scr, 0, t, stages=True)
+        assert rel_per_subap(gpu[0]["opd"], ref["opd"]) < OPD_REL
+        w.close()
+
+
+def test_deterministic_and_time_dependent():
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    a, w = run_library(cfg, scr, 0.01, seed=3, noise=True, stages=False)
+    b, _ = run_library(cfg, scr, 0.01, seed=3, noise=True, stages=False, handle=w)
+    c, _ = run_library(cfg, scr, 0.011, seed=3, noise=True, stages=False, handle=w)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x["slopes"], y["slopes"])
+        assert not np.array_equal(x["slopes"], z["slopes"])
+    w.close()
+
+
+def _small_cfg(n_sub, n, N, nd, lgs, eps=0.0, fill=0.5, photons=500.0, D=4.0):
+    dx = D / (n_sub * n)
+    S = 1 << int(math.ceil(math.log2(1.5 * n_sub * n + 16)))
+    lay = inputs._layers([0.0, 3e3], [0.7, 0.3], 0.1, 20.0, S, dx)
+    if lgs:
+        star = inputs._lgs(10 * inputs.ARCSEC, -5 * inputs.ARCSEC, 0.7, 0, photons=photons)
+        # keep the sodium slices' shifts small enough to stay inside small grids
+        star.spot_fwhm_rad = 1.5 * 589e-9 / (N * dx)
+    else:
+        star = inputs._ngs(3 * inputs.ARCSEC, 0.0, 700e-9, 0, photons=photons)
+    return inputs.Config("small", inputs.Telescope(D, eps), [inputs.Geometry(n_sub, n, N, nd, fill)],
+                         [star], lay, seed=9)
+
+
+@pytest.mark.parametrize("n_sub,n,N,nd,lgs", [
+    (7, 5, 12, 4, True),     # ragged: odd n, N not a power of two
+    (9, 3, 6, 3, False),     # tiny subapertures, odd detector
+    (5, 1, 2, 1, False),     # one pupil pixel per subaperture, one detector pixel
+    (2, 32, 64, 32, True),   # largest LGS geometry (multi-warp teams)
+    (3, 32, 64, 16, False),  # largest NGS geometry, b = 4
+    (33, 4, 8, 2, True),     # more subapertures than one CTA covers, ragged tail
+])
+def test_edge_geometries(n_sub, n, N, nd, lgs):
+    cfg = _small_cfg(n_sub, n, N, nd, lgs)
+    scr = inputs.make_screens(cfg.layers, 5)
+    gpu, w = run_library(cfg, scr, 0.004)
+    _check_wfs(cfg, scr, 0.004, gpu)
+    w.close()
+
+
+def test_zero_photons_and_no_valid_subaps():
+    cfg = _small_cfg(6, 6, 12, 6, False, photons=0.0)
+    scr = inputs.make_screens(cfg.layers, 1)
+    gpu, w = run_library(cfg, scr, 0.0)
+    assert np.all(gpu[0]["slopes"] == 0) and np.all(gpu[0]["E"] == 0)
+    w.close()
+    cfg = _small_cfg(2, 8, 16, 8, False, eps=0.95, fill=0.99)
+    w = native.Wfs(cfg)
+    assert w.total == 0
+    dev = torch.device("cuda:0")
+    s_d = torch.as_tensor(inputs.make_screens(cfg.layers, 1)).to(dev)
+    out = torch.empty(1, device=dev)
+    native.wfs_measure(w.h, s_d.data_ptr(), 0.0, out.data_ptr(), 0)
+    native.wfs_sync_status(w.h)
+    w.close()
+
+
+def test_flat_screen_zero_slopes_ngs():
+    cfg = inputs.config1()
+    S = cfg.layers.screen_size
+    gpu, w = run_library(cfg, np.zeros((1, S, S), np.float32), 0.0)
+    assert np.max(np.abs(gpu[0]["slopes"])) < 1e-5
+    w.close()
+
+
+def test_host_buffer_path_and_batch_match_device_path():
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    ref, w = run_library(cfg, scr, 0.03, stages=False)
+    ref_s = np.concatenate([d["slopes"] for d in ref])
+    host_scr = torch.as_tensor(scr).pin_memory()
+    host_out = torch.empty((w.total, 2)).pin_memory()
+    native.wfs_measure_host(w.h, host_scr.data_ptr(), 0.03, host_out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(host_out.numpy(), ref_s)
+    cfg1 = inputs.config1()
+    scr1 = inputs.make_screens(cfg1.layers, cfg1.seed)
+    w1 = native.Wfs(cfg1)
+    b = native.wfs_batch_create([w.h, w1.h])
+    dev = torch.device("cuda:0")
+    s0, s1 = torch.as_tensor(scr).to(dev), torch.as_tensor(scr1).to(dev)
+    o0, o1 = torch.empty((w.total, 2), device=dev), torch.empty((w1.total, 2), device=dev)
+    native.wfs_batch_measure(b, [s0.data_ptr(), s1.data_ptr()], [0.03, 0.002], [o0.data_ptr(), o1.data_ptr()], 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(o0.cpu().numpy(), ref_s)
+    r1, _ = run_library(cfg1, scr1, 0.002, stages=False, handle=w1)
+    assert np.array_equal(o1.cpu().numpy(), r1[0]["slopes"])
+    native.wfs_batch_destroy(b)
+    w.close()
+    w1.close()
