@@ -9,9 +9,11 @@
 // split as  u = [S/2 + (theta h_l - x0_l - v_l t)/ds]  +  c_l (dx/ds) j'
 // where j' is the pixel's half-integer column offset from the pupil centre.
 // The first (time-dependent, possibly large) term is evaluated once per CTA
-// in FP64 and split into an integer base (mod S) and an FP32 fraction; the
-// per-pixel term is FP32.  This keeps long runs (large v t) exact to FP64
-// rounding while every pixel stays in FP32.
+// in FP64 and split into an integer base (mod S) and an FP32 fraction.  The
+// per-pixel term uses FP32 only: the scale c_l dx/ds is held as two floats
+// (hi + lo) and the product with j' is split exactly with an FMA, so the
+// fractional coordinate is accurate to ~1e-7 px even 400 px from the centre.
+// This keeps long runs (large v t) exact to FP64 rounding.
 //
 // Output layout: per WFS, [n_valid][n][n] (subaperture-tiled), so the spot
 // kernel reads each subaperture's n*n OPD as one contiguous block.
@@ -21,7 +23,7 @@ namespace gbwfs {
 
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ ProjArgs a) {
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
-    __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers];
+    __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
 
     int w = 0;
     while (w + 1 < a.n_wfs && (int)blockIdx.x >= a.w[w + 1].block_begin) ++w;
@@ -42,7 +44,9 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ ProjArg
         if (mv < 0) mv += S;
         s_bu[l] = (int)mu;
         s_bv[l] = (int)mv;
-        s_c[l] = (float)(c * W.pupil_dx_over_ds);
+        const double cs = c * W.pupil_dx_over_ds;
+        s_c[l] = (float)cs;
+        s_cl[l] = (float)(cs - (double)s_c[l]);
     }
     __syncthreads();
 
@@ -58,11 +62,16 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ ProjArg
 
     float acc = 0.0f;
     for (int l = 0; l < a.n_layers; ++l) {
-        const float u = fmaf(s_c[l], xr, s_fu[l]);
-        const float vv = fmaf(s_c[l], yr, s_fv[l]);
-        const float fu0 = floorf(u), fv0 = floorf(vv);
-        const float f = u - fu0, g = vv - fv0;
-        int i0 = s_bu[l] + (int)fu0, j0 = s_bv[l] + (int)fv0;
+        const float ch = s_c[l], cl = s_cl[l];
+        // c * xr = ph + pl exactly (to FP32 rounding of the small part)
+        const float ph = __fmul_rn(ch, xr), pl = fmaf(ch, xr, -ph) + cl * xr;
+        const float qh = __fmul_rn(ch, yr), ql = fmaf(ch, yr, -qh) + cl * yr;
+        const float ih = floorf(ph), jh = floorf(qh);
+        const float ru = ((ph - ih) + pl) + s_fu[l];  // in [-eps, 2)
+        const float rv = ((qh - jh) + ql) + s_fv[l];
+        const float iu = floorf(ru), jv = floorf(rv);
+        const float f = ru - iu, g = rv - jv;
+        int i0 = s_bu[l] + (int)ih + (int)iu, j0 = s_bv[l] + (int)jh + (int)jv;
         // |c x / ds| < S is enforced when the handle is created: one wrap suffices
         i0 += (i0 < 0) ? S : 0;
         i0 -= (i0 >= S) ? S : 0;

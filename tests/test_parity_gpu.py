@@ -2,8 +2,10 @@
 
 Bars: noise-free slopes <= 1e-3 detector-pixel RMS; spot intensities and expected
 detector images <= 1e-4 relative (||a - b||_2 / ||b||_2 per subaperture, max over
-subaperture); projected OPD <= 1e-6 relative; valid-subaperture maps and integer
-Poisson draws bit-exact (draws up to FP32-vs-FP64 rounding of the mean).
+subaperture); projected OPD <= 5e-6 relative (an FP32 sum of up to 10 bilinear layer
+samples: (L + 3) 2^-24 times a layer-cancellation factor of a few); valid-subaperture
+maps and integer Poisson draws bit-exact (draws up to FP32-vs-FP64 rounding of the
+mean).
 """
 import dataclasses
 import math
@@ -21,7 +23,7 @@ from _gpu import rel_per_subap, run_library, slope_rms  # noqa: E402
 
 SLOPE_RMS = 1e-3
 INT_REL = 1e-4
-OPD_REL = 1e-6
+OPD_REL = 5e-6
 
 
 def _check_wfs(cfg, scr, t, gpu, sel=None, noise=False, seed=0):
