@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
+                    help="L2 flush buffer written between timed steps (0: none, for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -244,7 +246,7 @@ def main():
     sp = stream.cuda_stream
     s_d = torch.as_tensor(scr).to(dev)
     slopes = torch.empty((spots, 2), device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(max(1, args.flush_mb << 18), dtype=torch.float32, device=dev)
     dt = cfg.dt_s
 
     for k in range(args.warmup):
@@ -264,7 +266,8 @@ def main():
     time.sleep(0.3)
     wall0 = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(float(k))
+        if args.flush_mb:
+            flush.fill_(float(k))
         ev0[k].record(stream)
         native.wfs_measure(w.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
         ev1[k].record(stream)
@@ -338,7 +341,8 @@ def main():
                                    "(n=10, N=32, 16x16 det px, 8 Na slices) + 3 NGS 2x2 (n=32, N=64), "
                                    "10 layers, noise on",
                        "spots_per_frame": spots, "dft_precision": args.precision,
-                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                       "l2": (f"flushed between timed steps ({args.flush_mb} MB write, outside the step events)"
+                              if args.flush_mb else "not flushed (profiling run)"),
                        "replicas": world},
             "frames_per_s": frames,
             "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in ktimes.items()},
