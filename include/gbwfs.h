@@ -258,6 +258,44 @@ typedef struct {
 wfs_status wfs_timing_enable(wfs_handle h, int enable);
 wfs_status wfs_timing_read(wfs_handle h, int max, wfs_kernel_time *out, int *n_out);
 
+/*
+ * wfs_measure_one_static -- one guide star's measurement without any device
+ * allocation.  The paper has no counterpart; this entry point exists for
+ * callers that cannot call cudaMalloc: a real-time control loop that must
+ * not block on the allocator, a host program that gives the library a fixed
+ * device budget, or a plugin that only receives buffers.  Such callers cannot
+ * create a handle, because wfs_create allocates.
+ *
+ * Everything kept between the kernels (subaperture tables, DFT and binning
+ * matrices, the LGS elongation table, the projected OPD) lives in one
+ * file-scope device array of WFS_STATIC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits.  No cudaMalloc, cudaFree or
+ * other allocating routine is called; host staging uses fixed static arrays.
+ * A guide star whose tables would not fit, or with more than 8192 valid
+ * subapertures, is rejected with WFS_EINVAL and a message from
+ * wfs_last_error(NULL).  Only WFS_PREC_FP32 geometries are accepted.
+ *
+ * Inputs and outputs as for wfs_measure with one guide star: screens (device
+ * [n_layers][S][S]), slopes_out (device, room for slopes_capacity (x, y)
+ * pairs); *n_valid_out receives the number of valid subapertures written.
+ * wfs_index is the guide-star index used in the noise counter, so the result
+ * equals that of a handle whose guide star wfs_index is *gs.
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current: make it before any
+ * stream capture.  All calls share the array and the host staging, which keep
+ * the last call's contents: calls from several host threads, or calls whose
+ * GPU work overlaps on different streams, race.  Calls on one stream are
+ * ordered.  Asynchronous on `stream`.
+ */
+#define WFS_STATIC_SCRATCH_BYTES (16u << 20)
+
+wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs_geometry *geom,
+                                  const wfs_guide_star *gs, const wfs_layers *layers,
+                                  const float *screens, double t_s, uint64_t seed,
+                                  uint32_t wfs_index, int noise_enable, float *slopes_out,
+                                  int slopes_capacity, int *n_valid_out, void *stream);
+
 /* Library version string. */
 const char *wfs_version(void);
 

@@ -371,6 +371,8 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
 
 }  // namespace
 
+void gbwfs::set_thread_error(const char *msg) { tl_error = msg ? msg : ""; }
+
 extern "C" {
 
 const char *wfs_version(void) { return "gbwfs 0.1 (sm_103a)"; }

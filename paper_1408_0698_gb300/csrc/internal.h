@@ -74,5 +74,7 @@ cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
 cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
                          uint32_t pixel0, float *C, cudaStream_t s);
 size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_per_cta);
+// Sets the calling thread's message returned by wfs_last_error(NULL).
+void set_thread_error(const char *msg);
 
 }  // namespace gbwfs

@@ -100,6 +100,10 @@ _SIGS = {
     "wfs_batch_destroy": (C.c_int, [_H]),
     "wfs_version": (C.c_char_p, []),
     "wfs_timing_enable": (C.c_int, [_H, C.c_int]),
+    "wfs_measure_one_static": (C.c_int, [C.POINTER(wfs_telescope), C.POINTER(wfs_geometry),
+                                         C.POINTER(wfs_guide_star), C.POINTER(wfs_layers), C.c_void_p,
+                                         C.c_double, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p, C.c_int,
+                                         C.POINTER(C.c_int), C.c_void_p]),
     "wfs_timing_read": (C.c_int, [_H, C.c_int, C.POINTER(wfs_kernel_time), C.POINTER(C.c_int)]),
 }
 
@@ -224,6 +228,17 @@ def wfs_timing_read(h):
     n = C.c_int()
     _check(lib().wfs_timing_read(h, 64, arr, C.byref(n)), h)
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(n.value, 64))}
+
+
+def wfs_measure_one_static(tel, geom, star, layers, screens_ptr, t, seed, wfs_index, noise,
+                           slopes_ptr, slopes_capacity, stream=0):
+    """One guide star without device allocation (scratch in the library's static array);
+    returns the number of valid subapertures written."""
+    nv = C.c_int()
+    _check(lib().wfs_measure_one_static(C.byref(tel), C.byref(geom), C.byref(star), C.byref(layers),
+                                        screens_ptr, float(t), int(seed), int(wfs_index), int(bool(noise)),
+                                        slopes_ptr, int(slopes_capacity), C.byref(nv), stream))
+    return nv.value
 
 
 def wfs_batch_create(handles):
