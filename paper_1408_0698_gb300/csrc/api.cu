@@ -67,6 +67,10 @@ struct wfs_ctx {
     float *d_slopes_stage = nullptr;
     cudaStream_t last_stream = nullptr;
     std::string err;
+    // side streams for the spot launches of the second and later geometries
+    std::vector<cudaStream_t> side;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
     // kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;      // pool of event pairs
@@ -209,6 +213,12 @@ void release(wfs_ctx *h) {
     cudaFree(h->d_slopes_stage);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
+    for (cudaStream_t st : h->side) cudaStreamDestroy(st);
+    h->side.clear();
+    for (cudaEvent_t e : h->ev_join) cudaEventDestroy(e);
+    h->ev_join.clear();
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    h->ev_fork = nullptr;
 }
 
 wfs_status validate(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs, int n_geom,
@@ -314,13 +324,18 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         P.theta_y = s.gs.theta_y_rad;
         P.pupil_dx_over_ds = (h->tel.diameter_m / (g.n_sub * g.n_pix_sub)) / h->ds;
         P.block_begin = blocks;
-        blocks += (s.n_valid * g.n_pix_sub * g.n_pix_sub + 255) / 256;
+        blocks += project_blocks(s.n_valid * g.n_pix_sub * g.n_pix_sub);
     }
     long slot = blocks > 0 ? timed_begin(h, "project", stream) : -1;
     cudaError_t e = launch_project(pa, blocks, stream);
     timed_end(h, slot, stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "projection launch");
 
+    // The largest geometry runs on the caller's stream, launched last; the others run on side
+    // streams forked after the projection (launched first, so their few CTAs are resident
+    // before the large launch fills the GPU) and joined before the call returns.
+    std::vector<ShArgs> jobs;
+    jobs.reserve(h->geoms.size());
     for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
         const GeomDev &G = h->geoms[gi];
         ShArgs sa;
@@ -358,14 +373,40 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
             W.read_noise = (float)s.gs.read_noise_e;
             total += s.n_valid;
         }
-        if (!nw) continue;
+        if (!nw || !total) continue;
         sa.n_wfs = nw;
         sa.total = total;
-        slot = timed_begin(h, "spot_fp32_N" + std::to_string(sa.N), stream);
-        e = launch_sh_fp32(sa, stream);
-        timed_end(h, slot, stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "spot launch");
+        jobs.push_back(sa);
     }
+    if (jobs.empty()) return WFS_OK;
+    size_t big = 0;
+    for (size_t j = 1; j < jobs.size(); ++j)
+        if (jobs[j].total > jobs[big].total) big = j;
+    auto prec_of = [&](const ShArgs &sa) {
+        for (const GeomDev &G : h->geoms)
+            if (G.F == sa.F) return G.g.precision;
+        return (int)WFS_PREC_FP32;
+    };
+    auto launch_job = [&](const ShArgs &sa, cudaStream_t ls) -> cudaError_t {
+        const bool fast = prec_of(sa) == WFS_PREC_FP32 && sh_n32_supported(sa.n, sa.N, sa.nd);
+        long sl = timed_begin(h, std::string(fast ? "spot_n32_fp32_N" : "spot_fp32_N") + std::to_string(sa.N), ls);
+        cudaError_t err = fast ? launch_sh_n32(sa, ls) : launch_sh_fp32(sa, ls);
+        timed_end(h, sl, ls);
+        return err;
+    };
+    size_t k = 0;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        if (j == big) continue;
+        if (k >= h->side.size()) return fail(h, WFS_EINVAL, "internal: missing side stream");
+        if (k == 0 && (e = cudaEventRecord(h->ev_fork, stream)) != cudaSuccess) return cuda_fail(h, e, "fork");
+        if ((e = cudaStreamWaitEvent(h->side[k], h->ev_fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork wait");
+        if ((e = launch_job(jobs[j], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+        if ((e = cudaEventRecord(h->ev_join[k], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "join");
+        ++k;
+    }
+    if ((e = launch_job(jobs[big], stream)) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+    for (size_t j = 0; j < k; ++j)
+        if ((e = cudaStreamWaitEvent(stream, h->ev_join[j], 0)) != cudaSuccess) return cuda_fail(h, e, "join wait");
     return WFS_OK;
 }
 
@@ -499,6 +540,24 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 return cuda_fail(nullptr, e, "elongation table launch");
             }
         }
+    }
+    for (int i = 1; i < n_geom; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            if (st) cudaStreamDestroy(st);
+            release(h);
+            delete h;
+            return cuda_fail(nullptr, e, "side stream creation");
+        }
+        h->side.push_back(st);
+        h->ev_join.push_back(ev);
+    }
+    if (n_geom > 1 && (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
+        release(h);
+        delete h;
+        return cuda_fail(nullptr, e, "fork event creation");
     }
     h->total_valid = (int)(slope / 2);
     h->opd_total = opd;

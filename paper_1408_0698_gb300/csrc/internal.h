@@ -69,8 +69,13 @@ struct KtilArgs {
 
 // Launchers (return the cudaGetLastError() of the launch).
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s);
+// CTAs the projection needs for `pixels` pupil pixels of one WFS.
+int project_blocks(int pixels);
 cudaError_t launch_sh_fp32(const ShArgs &a, cudaStream_t s);
 cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
+// Compile-time specialised FP32 spot kernel for N = 32 geometries.
+bool sh_n32_supported(int n, int N, int nd);
+cudaError_t launch_sh_n32(const ShArgs &a, cudaStream_t s);
 cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
                          uint32_t pixel0, float *C, cudaStream_t s);
 size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_per_cta);

@@ -21,7 +21,10 @@
 
 namespace gbwfs {
 
-__global__ void __launch_bounds__(256) k_project(const __grid_constant__ ProjArgs a) {
+constexpr int kProjThreads = 256;
+constexpr int kProjPix = 4;  // pixels per thread (strided by the block size: coalesced)
+
+__global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
     __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
 
@@ -34,64 +37,89 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ ProjArg
         const int l = threadIdx.x;
         const double h = a.alt[l];
         const double c = W.is_lgs ? 1.0 - h / W.range_m : 1.0;
-        const double ou = 0.5 * S + (W.theta_x * h - (a.x0[l] + a.vx[l] * a.t)) / a.ds;
-        const double ov = 0.5 * S + (W.theta_y * h - (a.y0[l] + a.vy[l] * a.t)) / a.ds;
+        const double inv_ds = 1.0 / a.ds;
+        const double ou = 0.5 * S + (W.theta_x * h - (a.x0[l] + a.vx[l] * a.t)) * inv_ds;
+        const double ov = 0.5 * S + (W.theta_y * h - (a.y0[l] + a.vy[l] * a.t)) * inv_ds;
         const double bu = floor(ou), bv = floor(ov);
         s_fu[l] = (float)(ou - bu);
         s_fv[l] = (float)(ov - bv);
-        double mu = fmod(bu, (double)S), mv = fmod(bv, (double)S);
-        if (mu < 0) mu += S;
-        if (mv < 0) mv += S;
-        s_bu[l] = (int)mu;
-        s_bv[l] = (int)mv;
+        // base index mod S (exact: bu, bv are integers well inside 2^53)
+        long long iu = (long long)bu % S, iv = (long long)bv % S;
+        if (iu < 0) iu += S;
+        if (iv < 0) iv += S;
+        s_bu[l] = (int)iu;
+        s_bv[l] = (int)iv;
         const double cs = c * W.pupil_dx_over_ds;
         s_c[l] = (float)cs;
         s_cl[l] = (float)(cs - (double)s_c[l]);
     }
     __syncthreads();
 
-    const int n = W.n, nn = n * n;
-    const int pix = ((int)blockIdx.x - W.block_begin) * blockDim.x + threadIdx.x;
-    if (pix >= W.n_valid * nn) return;
-    const int v = pix / nn, r = pix - v * nn, p = r / n, q = r - p * n;
-    const int id = __ldg(W.subap + v);
-    const int sy = id / W.n_sub, sx = id - sy * W.n_sub;
+    const int n = W.n, nn = n * n, total = W.n_valid * nn;
+    const int pix0 = ((int)blockIdx.x - W.block_begin) * (kProjThreads * kProjPix) + threadIdx.x;
     const float half = 0.5f * (float)(W.n_sub * n - 1);
-    const float xr = (float)(sx * n + q) - half;  // exact half-integers
-    const float yr = (float)(sy * n + p) - half;
-
-    float acc = 0.0f;
-    for (int l = 0; l < a.n_layers; ++l) {
-        const float ch = s_c[l], cl = s_cl[l];
-        // c * xr = ph + pl exactly (to FP32 rounding of the small part)
-        const float ph = __fmul_rn(ch, xr), pl = fmaf(ch, xr, -ph) + cl * xr;
-        const float qh = __fmul_rn(ch, yr), ql = fmaf(ch, yr, -qh) + cl * yr;
-        const float ih = floorf(ph), jh = floorf(qh);
-        const float ru = ((ph - ih) + pl) + s_fu[l];  // in [-eps, 2)
-        const float rv = ((qh - jh) + ql) + s_fv[l];
-        const float iu = floorf(ru), jv = floorf(rv);
-        const float f = ru - iu, g = rv - jv;
-        int i0 = s_bu[l] + (int)ih + (int)iu, j0 = s_bv[l] + (int)jh + (int)jv;
-        // |c x / ds| < S is enforced when the handle is created: one wrap suffices
-        i0 += (i0 < 0) ? S : 0;
-        i0 -= (i0 >= S) ? S : 0;
-        j0 += (j0 < 0) ? S : 0;
-        j0 -= (j0 >= S) ? S : 0;
-        const int i1 = (i0 + 1 == S) ? 0 : i0 + 1;
-        const int j1 = (j0 + 1 == S) ? 0 : j0 + 1;
-        const float *scr = a.screens + (size_t)l * S * S;
-        const float s00 = __ldg(scr + (size_t)j0 * S + i0), s01 = __ldg(scr + (size_t)j0 * S + i1);
-        const float s10 = __ldg(scr + (size_t)j1 * S + i0), s11 = __ldg(scr + (size_t)j1 * S + i1);
-        const float top = fmaf(f, s01 - s00, s00);
-        const float bot = fmaf(f, s11 - s10, s10);
-        acc += fmaf(g, bot - top, top);
+    float xr[kProjPix], yr[kProjPix], acc[kProjPix];
+#pragma unroll
+    for (int j = 0; j < kProjPix; ++j) {
+        const int pix = min(pix0 + j * kProjThreads, total - 1);
+        const int v = pix / nn, r = pix - v * nn, p = r / n, q = r - p * n;
+        const int id = __ldg(W.subap + v);
+        const int sy = id / W.n_sub, sx = id - sy * W.n_sub;
+        xr[j] = (float)(sx * n + q) - half;  // exact half-integers
+        yr[j] = (float)(sy * n + p) - half;
+        acc[j] = 0.0f;
     }
-    W.opd[pix] = acc;
+    const bool pow2 = (S & (S - 1)) == 0;
+    for (int l = 0; l < a.n_layers; ++l) {
+        const float ch = s_c[l], cl = s_cl[l], fu = s_fu[l], fv = s_fv[l];
+        const int bu = s_bu[l], bv = s_bv[l];
+        const float *scr = a.screens + (size_t)l * S * S;
+#pragma unroll
+        for (int j = 0; j < kProjPix; ++j) {
+            // c * xr = ph + pl exactly (to FP32 rounding of the small part)
+            const float ph = __fmul_rn(ch, xr[j]), pl = fmaf(ch, xr[j], -ph) + cl * xr[j];
+            const float qh = __fmul_rn(ch, yr[j]), ql = fmaf(ch, yr[j], -qh) + cl * yr[j];
+            const float ih = floorf(ph), jh = floorf(qh);
+            const float ru = ((ph - ih) + pl) + fu;  // in [-eps, 2)
+            const float rv = ((qh - jh) + ql) + fv;
+            const float iu = floorf(ru), jv = floorf(rv);
+            const float f = ru - iu, g = rv - jv;
+            int i0 = bu + (int)ih + (int)iu, j0 = bv + (int)jh + (int)jv;
+            int i1, j1;
+            if (pow2) {
+                i0 &= S - 1;
+                j0 &= S - 1;
+                i1 = (i0 + 1) & (S - 1);
+                j1 = (j0 + 1) & (S - 1);
+            } else {
+                // |c x / ds| < S is enforced when the handle is created: one wrap suffices
+                i0 += (i0 < 0) ? S : 0;
+                i0 -= (i0 >= S) ? S : 0;
+                j0 += (j0 < 0) ? S : 0;
+                j0 -= (j0 >= S) ? S : 0;
+                i1 = (i0 + 1 == S) ? 0 : i0 + 1;
+                j1 = (j0 + 1 == S) ? 0 : j0 + 1;
+            }
+            const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
+            const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+            const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+            const float top = fmaf(f, s01 - s00, s00);
+            const float bot = fmaf(f, s11 - s10, s10);
+            acc[j] += fmaf(g, bot - top, top);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kProjPix; ++j) {
+        const int pix = pix0 + j * kProjThreads;
+        if (pix < total) W.opd[pix] = acc[j];
+    }
 }
+
+int project_blocks(int pixels) { return (pixels + kProjThreads * kProjPix - 1) / (kProjThreads * kProjPix); }
 
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) {
     if (total_blocks <= 0) return cudaSuccess;
-    k_project<<<total_blocks, 256, 0, s>>>(a);
+    k_project<<<total_blocks, kProjThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

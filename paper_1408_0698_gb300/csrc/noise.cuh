@@ -68,7 +68,7 @@ __device__ __forceinline__ float log_factorial_f32(float k) {
     return __fadd_rn(__fadd_rn(v, 0.918938533f), corr);
 }
 
-__device__ __noinline__ int poisson_f32(float E, Philox &g) {
+static __device__ __noinline__ int poisson_f32(float E, Philox &g) {
     if (!(E > 0.0f)) return 0;
     if (E < 16.0f) {
         float u = g.next();

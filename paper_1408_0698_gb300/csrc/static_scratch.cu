@@ -250,7 +250,7 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
     P.theta_y = gs->theta_y_rad;
     P.pupil_dx_over_ds = dx / L->screen_dx_m;
     P.block_begin = 0;
-    if ((e = launch_project(pa, (nv * n * n + 255) / 256, s)) != cudaSuccess)
+    if ((e = launch_project(pa, project_blocks(nv * n * n), s)) != cudaSuccess)
         return st_fail(WFS_ECUDA, "wfs_measure_one_static: projection launch");
 
     ShArgs sa;
