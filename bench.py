@@ -70,6 +70,7 @@ def source_sha(names):
 
 KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "internal.h"],
                   "spot_n32": ["k_sh_n32.cu", "noise.cuh", "internal.h"],
+                  "spot_tc": ["k_sh_tc.cu", "noise.cuh", "internal.h"],
                   "project": ["k_project.cu", "internal.h"]}
 
 
@@ -334,9 +335,18 @@ def main():
         ach = flops / avg_s / 1e12
         roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": ncu_traffic("spot_n32" if name.startswith("spot_n32") else "spot"),
+                "traffic": ncu_traffic("spot_n32" if name.startswith("spot_n32") else
+                                       "spot_tc" if name.startswith("spot_tc") else "spot"),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3}
+        if name.startswith("spot_tc"):
+            # the two tensor-core contractions: M = 32 rows per subaperture, N x K = 64 x 64 and
+            # 32 x 128 BF16 issued per row (three split products included)
+            nv = sum(w.layouts[k].n_valid for k, s in enumerate(cfg.stars)
+                     if cfg.geometries[s.geometry_index].n_fft == 32)
+            tflops = nv * 2 * 32 * (64 * 64 + 32 * 128) / avg_s / 1e12
+            roof["tensor_pipe"] = {"achieved": tflops, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                                   "frac": tflops / pk["bf16_tflops"], "peak_source": kind}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

@@ -32,6 +32,7 @@ struct GeomDev {
     wfs_geometry g{};
     int mask_words = 0;
     float2 *F = nullptr, *Ga = nullptr, *G = nullptr;
+    uint8_t *tcB1 = nullptr, *tcB2h = nullptr, *tcB2l = nullptr;  // BF16X3 operand tiles
 };
 
 struct GsDev {
@@ -153,23 +154,29 @@ void cexp_minus(double a, int N, double *re, double *im) {
 }
 
 void build_geom_tables(const wfs_geometry &g, std::vector<float2> &F, std::vector<float2> &Ga,
-                       std::vector<float2> &G) {
+                       std::vector<float2> &G, std::vector<double> &F64, std::vector<double> &Ga64) {
     const int n = g.n_pix_sub, N = g.n_fft, nd = g.n_det, b = N / nd;
     const double cN = (N - 1) / 2.0, cn = (n - 1) / 2.0;
     F.resize((size_t)n * N);
     Ga.resize((size_t)n * N);
     G.resize((size_t)n * nd);
+    F64.resize((size_t)2 * n * N);   // re block then im block, [q][m]
+    Ga64.resize((size_t)2 * n * N);  // re block then im block, [d][k]
     for (int q = 0; q < n; ++q)
         for (int m = 0; m < N; ++m) {
             double re, im;
             cexp_minus((m - cN) * (q - cn), N, &re, &im);
             F[(size_t)q * N + m] = make_float2((float)re, (float)im);
+            F64[(size_t)q * N + m] = re;
+            F64[(size_t)n * N + q * N + m] = im;
         }
     for (int d = 0; d < n; ++d)
         for (int k = 0; k < N; ++k) {
             double re, im;
             cexp_minus(-(k - cN) * d, N, &re, &im);  // exp(+2 pi i (k - cN) d / N)
             Ga[(size_t)d * N + k] = make_float2((float)re, (float)im);
+            Ga64[(size_t)d * N + k] = re;
+            Ga64[(size_t)n * N + d * N + k] = im;
         }
     for (int d = 0; d < n; ++d)
         for (int i = 0; i < nd; ++i) {
@@ -200,6 +207,9 @@ void release(wfs_ctx *h) {
         cudaFree(g.F);
         cudaFree(g.Ga);
         cudaFree(g.G);
+        cudaFree(g.tcB1);
+        cudaFree(g.tcB2h);
+        cudaFree(g.tcB2l);
     }
     for (auto &s : h->gs) {
         cudaFree(s.d_ids);
@@ -347,6 +357,9 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.F = G.F;
         sa.Ga = G.Ga;
         sa.G = G.G;
+        sa.tc_B1 = G.tcB1;
+        sa.tc_B2h = G.tcB2h;
+        sa.tc_B2l = G.tcB2l;
         sa.seed = h->seed;
         sa.noise = h->noise;
         sa.t = t;
@@ -388,9 +401,20 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         return (int)WFS_PREC_FP32;
     };
     auto launch_job = [&](const ShArgs &sa, cudaStream_t ls) -> cudaError_t {
-        const bool fast = prec_of(sa) == WFS_PREC_FP32 && sh_n32_supported(sa.n, sa.N, sa.nd);
-        long sl = timed_begin(h, std::string(fast ? "spot_n32_fp32_N" : "spot_fp32_N") + std::to_string(sa.N), ls);
-        cudaError_t err = fast ? launch_sh_n32(sa, ls) : launch_sh_fp32(sa, ls);
+        const int prec = prec_of(sa);
+        std::string name;
+        cudaError_t err;
+        long sl;
+        if (prec == WFS_PREC_BF16X3) {
+            sl = timed_begin(h, "spot_tc_bf16x3_N" + std::to_string(sa.N), ls);
+            err = launch_sh_tc(sa, ls);
+        } else if (sh_n32_supported(sa.n, sa.N, sa.nd)) {
+            sl = timed_begin(h, "spot_n32_fp32_N" + std::to_string(sa.N), ls);
+            err = launch_sh_n32(sa, ls);
+        } else {
+            sl = timed_begin(h, "spot_fp32_N" + std::to_string(sa.N), ls);
+            err = launch_sh_fp32(sa, ls);
+        }
         timed_end(h, sl, ls);
         return err;
     };
@@ -427,9 +451,15 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
     *out = nullptr;
     wfs_status st = validate(tel, n_gs, gs, n_geom, geom, layers);
     if (st != WFS_OK) return st;
-    for (int i = 0; i < n_geom; ++i)
-        if (geom[i].precision != WFS_PREC_FP32)
-            return fail(nullptr, WFS_EUNSUPPORTED, "geometry " + std::to_string(i) + ": precision not built yet");
+    for (int i = 0; i < n_geom; ++i) {
+        const wfs_geometry &g = geom[i];
+        if (g.precision == WFS_PREC_FP16S)
+            return fail(nullptr, WFS_EUNSUPPORTED, "geometry " + std::to_string(i) + ": WFS_PREC_FP16S is not built");
+        if (g.precision == WFS_PREC_BF16X3 && !sh_tc_supported(g.n_pix_sub, g.n_fft, g.n_det))
+            return fail(nullptr, WFS_EUNSUPPORTED,
+                        "geometry " + std::to_string(i) +
+                            ": WFS_PREC_BF16X3 is built for n_fft = 32 with (n_pix_sub, n_det) = (10, 16) or (8, 16)");
+    }
 
     wfs_ctx *h = new wfs_ctx();
     h->tel = *tel;
@@ -452,12 +482,25 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
         G.g = geom[i];
         G.mask_words = (geom[i].n_pix_sub * geom[i].n_pix_sub + 31) / 32;
         std::vector<float2> F, Ga, Gb;
-        build_geom_tables(geom[i], F, Ga, Gb);
+        std::vector<double> F64, Ga64;
+        build_geom_tables(geom[i], F, Ga, Gb, F64, Ga64);
         if ((e = upload(&G.F, F)) != cudaSuccess || (e = upload(&G.Ga, Ga)) != cudaSuccess ||
             (e = upload(&G.G, Gb)) != cudaSuccess) {
             release(h);
             delete h;
             return cuda_fail(nullptr, e, "table upload");
+        }
+        if (geom[i].precision == WFS_PREC_BF16X3) {
+            const int n = geom[i].n_pix_sub, N = geom[i].n_fft;
+            std::vector<uint8_t> b1, b2h, b2l;
+            build_tc_tiles(n, N, F64.data(), F64.data() + (size_t)n * N, Ga64.data(), Ga64.data() + (size_t)n * N,
+                           b1, b2h, b2l);
+            if ((e = upload(&G.tcB1, b1)) != cudaSuccess || (e = upload(&G.tcB2h, b2h)) != cudaSuccess ||
+                (e = upload(&G.tcB2l, b2l)) != cudaSuccess) {
+                release(h);
+                delete h;
+                return cuda_fail(nullptr, e, "tensor-core tile upload");
+            }
         }
     }
     h->gs.resize(n_gs);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace gbwfs {
 
 constexpr int kMaxGuideStars = 32;
@@ -55,6 +57,8 @@ struct ShArgs {
     int noise;
     double t;
     int *status;
+    // tensor-core operand tiles (BF16, pre-swizzled), used by the BF16X3 kernel only
+    const void *tc_B1, *tc_B2h, *tc_B2l;
     ShWfs w[kMaxGuideStars];
 };
 
@@ -76,6 +80,14 @@ cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
 // Compile-time specialised FP32 spot kernel for N = 32 geometries.
 bool sh_n32_supported(int n, int N, int nd);
 cudaError_t launch_sh_n32(const ShArgs &a, cudaStream_t s);
+// Tensor-core (tcgen05, BF16 x3) spot kernel for N = 32 geometries with n <= 10.
+bool sh_tc_supported(int n, int N, int nd);
+cudaError_t launch_sh_tc(const ShArgs &a, cudaStream_t s);
+// Swizzled BF16 operand tiles of the two constant matrices (F^T blocks, Ga blocks),
+// from FP64 tables laid out [q][m] (F) and [d][k] (Ga).
+void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
+                    const double *Ga_im64, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
+                    std::vector<uint8_t> &B2l);
 cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
                          uint32_t pixel0, float *C, cudaStream_t s);
 size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_per_cta);

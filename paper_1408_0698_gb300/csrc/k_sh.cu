@@ -86,7 +86,7 @@ __device__ __forceinline__ float2 cmac(float2 acc, float2 a, float2 b) {
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 template <int TEAM>
-__global__ void __launch_bounds__(256) k_sh_fp32(const __grid_constant__ ShArgs a) {
+__global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __grid_constant__ ShArgs a) {
     extern __shared__ __align__(16) float smem[];
     const int n = a.n, N = a.N, nd = a.nd, nn = n * n, D2 = 2 * n - 1, no = odd_up(n);
     float2 *sF = reinterpret_cast<float2 *>(smem);  // [q][m]
@@ -253,10 +253,11 @@ __global__ void __launch_bounds__(256) k_sh_fp32(const __grid_constant__ ShArgs 
 }
 
 size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_per_cta) {
-    const int team = N > 32 ? 128 : 32;
+    // a warp per subaperture up to 32-point DFTs; larger DFTs get a 512-thread team each
+    const int team = N > 32 ? 512 : 32;
     const size_t consts = (size_t)(2 * n * N + n * nd) * sizeof(float2);
     const size_t per = (size_t)team_floats(n, N, nd, team) * sizeof(float);
-    int teams = 256 / team;
+    int teams = team >= 256 ? 1 : 256 / team;
     while (teams > 1 && consts + teams * per > 200 * 1024) --teams;
     if (team_threads) *team_threads = team;
     if (teams_per_cta) *teams_per_cta = teams;
@@ -275,9 +276,9 @@ cudaError_t launch_sh_fp32(const ShArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         k_sh_fp32<32><<<blocks, team * teams, smem, s>>>(a);
     } else {
-        e = cudaFuncSetAttribute(k_sh_fp32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sh_fp32<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sh_fp32<128><<<blocks, team * teams, smem, s>>>(a);
+        k_sh_fp32<512><<<blocks, team * teams, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

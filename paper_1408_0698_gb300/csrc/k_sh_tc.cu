@@ -1,0 +1,562 @@
+// k_sh_tc.cu -- the spot kernel with the DFT contraction on the 5th-generation
+// tensor cores (tcgen05, BF16 hi/lo split with three products, FP32
+// accumulation in tensor memory), for 32-point DFT geometries with n <= 10.
+//
+// Arithmetic (Sec. 4 LGS SH: spot by DFT, sodium elongation, binning, noise,
+// centroid) is that of k_sh.cu; only the two contractions whose second operand
+// is a constant matrix shared by all subapertures run on the tensor cores:
+//
+//   Y = U F^T   rows (subaperture b, DFT row k): M = 4 x 32 = 128, N = 64
+//               (re/im x 32 columns), K = [U_hi | U_lo | U_hi] x [F_hi; F_hi; F_lo]
+//               = 3 x 2n (complex as real pairs), zero-padded to 64
+//   Ta = I Ga^T rows (b, k): M = 128, N = 32 (re/im x 16 dx), K = [I_hi | I_lo]
+//               x [Ga_hi; Ga_hi] (64) then [I_hi | I_lo] x [Ga_lo; 0] (64)
+//
+// Each BF16 pair (x_hi, x_lo = bf16(x - x_hi)) carries ~16 significant bits; the
+// dropped lo*lo products are ~2^-16 of each term.  Operands live in shared memory
+// in the 128-byte-swizzled K-major layout (8-row x 128-byte atoms); one elected
+// thread issues the MMAs and commits them to an mbarrier; every wait is bounded
+// and a timeout is reported in the status word (the kernel then frees its tensor
+// memory and returns).  U = F X, the column transform, binning, photometry,
+// noise and the centroid run on the CUDA cores exactly as in the FP32 kernels.
+//
+// CTA = one warpgroup (4 warps); warp w owns subaperture 4g + w of group g and its
+// lane k owns DFT row k, which is also TMEM lane 32 w + k of both accumulators.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+#include "noise.cuh"
+
+namespace gbwfs {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 128;      // D1: columns [0, 64), D2: [64, 96)
+constexpr int kWaitLimit = 1 << 24;      // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 x BF16 -> F32, both K-major.
+__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+#define GBWFS_TMEM_LD32(r, addr)                                                                          \
+    asm volatile(                                                                                         \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                         \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),        \
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),      \
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),      \
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                           \
+        : "r"(addr))
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// byte offset of element k of row r in a 128-row x 64-element BF16 swizzled tile
+__host__ __device__ inline uint32_t sw128_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void split_bf16(float x, float &hi, float &lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(x));
+    lo = x - hi;
+}
+
+__device__ __forceinline__ void cmacc(float2 &acc, const float2 a, const float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+__device__ __forceinline__ float wsum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int n, int nd>
+struct TcLayout {
+    static constexpr int N = 32, D2 = 2 * n - 1, NO = n | 1, GAK = 33;
+    // byte offsets; tensor-core tiles first (1024-aligned)
+    static constexpr int oB1 = 0;                  // 64 rows x 128 B: [F_hi; F_hi; F_lo] blocks
+    static constexpr int oB2h = oB1 + 8192;        // 32 rows x 128 B: [Ga_hi; Ga_hi]
+    static constexpr int oB2l = oB2h + 4096;       // 32 rows x 128 B: [Ga_lo; 0]
+    // 128 rows x 128 B: [U_hi | U_lo | U_hi] for the first MMA, then (after it has
+    // completed) [I_hi | I_lo] for the second
+    static constexpr int oA = oB2l + 4096;
+    static constexpr int oTab = oA + 16384;        // CUDA-core tables (float2)
+    static constexpr int tFk = 0;                  // [p][k]  F[k][p]
+    static constexpr int tGak = tFk + n * N;       // [dyi][GAK] Ga(dy, k), conjugated rows for dy < 0
+    static constexpr int tG = tGak + D2 * GAK;     // [d][nd] G[d][i]
+    static constexpr int tEnd = tG + n * nd;
+    static constexpr int oWarp = oTab + tEnd * 8;  // per-warp scratch (float2)
+    // the NGS image rows (wI) alias the LGS transfer-domain scratch (wTa, wM)
+    static constexpr int wX = 0, wTa = wX + n * n, wM = wTa + N * NO, wI = wTa;
+    static constexpr int lgs_end = wM + D2 * n, ngs_end = wI + (N * (N + 1) + 1) / 2;
+    static constexpr int warp = lgs_end > ngs_end ? lgs_end : ngs_end;
+    static constexpr int oMisc = oWarp + 4 * warp * 8;  // mbarriers, TMEM address, flags
+    static constexpr int bytes = oMisc + 64;
+};
+
+}  // namespace
+
+template <int n, int nd>
+__global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__ ShArgs a) {
+    using Lay = TcLayout<n, nd>;
+    constexpr int N = 32, D2 = Lay::D2, NO = Lay::NO, GAK = Lay::GAK, b = N / nd, nd2 = nd * nd;
+    static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
+    static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sB1 = smem + Lay::oB1, *sB2h = smem + Lay::oB2h, *sB2l = smem + Lay::oB2l;
+    uint8_t *sA1 = smem + Lay::oA, *sA2 = smem + Lay::oA;
+    float2 *tab = reinterpret_cast<float2 *>(smem + Lay::oTab);
+    float2 *Fk = tab + Lay::tFk, *Gak = tab + Lay::tGak, *Gt = tab + Lay::tG;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + 16);
+    int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 20);
+
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    // constant operand tiles (pre-swizzled on the host) and CUDA-core tables
+    {
+        const uint4 *src1 = reinterpret_cast<const uint4 *>(a.tc_B1);
+        const uint4 *src2 = reinterpret_cast<const uint4 *>(a.tc_B2h);
+        const uint4 *src3 = reinterpret_cast<const uint4 *>(a.tc_B2l);
+        for (int i = tid; i < 8192 / 16; i += kTcThreads) reinterpret_cast<uint4 *>(sB1)[i] = src1[i];
+        for (int i = tid; i < 4096 / 16; i += kTcThreads) {
+            reinterpret_cast<uint4 *>(sB2h)[i] = src2[i];
+            reinterpret_cast<uint4 *>(sB2l)[i] = src3[i];
+        }
+        for (int i = tid; i < n * N; i += kTcThreads) {
+            const int p = i / N, k = i - p * N;
+            Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
+        }
+        for (int i = tid; i < D2 * N; i += kTcThreads) {
+            const int dyi = i / N, k = i - dyi * N, dy = dyi - (n - 1);
+            float2 g = a.Ga[(dy >= 0 ? dy : -dy) * N + k];
+            if (dy < 0) g.y = -g.y;
+            Gak[dyi * GAK + k] = g;
+        }
+        for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
+    }
+    if (wib == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *sflag = 0;
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t t_row = tmem + ((uint32_t)(wib * 32) << 16);
+    constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
+
+    float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
+    float2 *Ta = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wTa;
+    float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
+    float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
+    const uint32_t tlo = (uint32_t)__double_as_longlong(a.t);
+    const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(a.t) >> 32);
+    const float cd = 0.5f * (float)(nd - 1);
+    const int ix = lane & 15, half = lane >> 4;
+    const int row = wib * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
+    const int groups = (a.total + 3) / 4;
+    uint32_t phase = 0;
+
+    for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+        const int g = 4 * grp + wib;
+        const bool active = g < a.total;
+        int w = 0;
+        if (active)
+            while (w + 1 < a.n_wfs && g >= a.w[w + 1].subap_begin) ++w;
+        const ShWfs &W = a.w[w];
+        const int v = active ? g - W.subap_begin : 0;
+
+        // field and U = F X (CUDA cores)
+        float2 U[n];
+#pragma unroll
+        for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
+        if (active) {
+            const float *opd = W.opd + (size_t)v * (n * n);
+            const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
+            const float ref = __ldg(opd);
+            for (int i = lane; i < n * n; i += 32) {
+                const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
+                float s, c;
+                sincosf(W.k_phase * (__ldg(opd + i) - ref), &s, &c);
+                X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                const float2 f = Fk[p * N + lane];
+#pragma unroll
+                for (int q = 0; q < n; ++q) cmacc(U[q], f, X[p * n + q]);
+            }
+        }
+        // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
+        {
+            float hv[2 * n], lv[2 * n];
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+                split_bf16(U[q].x, hv[q], lv[q]);
+                split_bf16(U[q].y, hv[n + q], lv[n + q]);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+                uint32_t wds[4];
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    float vv[2];
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int e = ch * 8 + e2 * 2 + h2;
+                        const int t = e / (2 * n), j = e % (2 * n);
+                        vv[h2] = e >= 6 * n ? 0.0f : (t == 1 ? lv[j] : hv[j]);
+                    }
+                    wds[e2] = pack_bf16(vv[0], vv[1]);
+                }
+                *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+            }
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (*sflag) break;  // a previous wait timed out (uniform: read after the barrier)
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
+            mma_commit(&mbar[0]);
+        }
+        if (!mbar_wait(&mbar[0], phase)) *sflag = 1;
+        fence_after_sync();
+        // Y row from TMEM -> I
+        float I[N];
+        {
+            uint32_t r[32];
+            GBWFS_TMEM_LD32(r, t_row + 0);
+            tmem_wait_ld();
+            uint32_t r2[32];
+            GBWFS_TMEM_LD32(r2, t_row + 32);
+            tmem_wait_ld();
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
+                I[m] = fmaf(yr, yr, yi * yi);
+            }
+        }
+        if (active && W.st_I) {
+            float *dst = W.st_I + (size_t)v * (N * N) + lane * N;
+#pragma unroll
+            for (int m = 0; m < N; ++m) dst[m] = I[m];
+        }
+        if (active && !W.is_lgs) {
+#pragma unroll
+            for (int m = 0; m < N; ++m) Iw[lane * (N + 1) + m] = I[m];
+        }
+        // A2 row: [I_hi | I_lo]
+        {
+#pragma unroll
+            for (int ch = 0; ch < 8; ++ch) {
+                uint32_t wds[4];
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    float vv[2];
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int e = ch * 8 + e2 * 2 + h2;
+                        float hi, lo;
+                        split_bf16(I[e & 31], hi, lo);
+                        vv[h2] = e < 32 ? hi : lo;
+                    }
+                    wds[e2] = pack_bf16(vv[0], vv[1]);
+                }
+                *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+            }
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (*sflag) break;
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2l) + 32 * s), idesc2, 1);
+            mma_commit(&mbar[1]);
+        }
+        if (!mbar_wait(&mbar[1], phase)) *sflag = 1;
+        fence_after_sync();
+        {
+            uint32_t r[32];
+            GBWFS_TMEM_LD32(r, t_row + 64);
+            tmem_wait_ld();
+            if (active && W.is_lgs) {
+#pragma unroll
+                for (int d = 0; d < n; ++d) Ta[lane * NO + d] = make_float2(__uint_as_float(r[d]), __uint_as_float(r[16 + d]));
+            }
+        }
+        phase ^= 1u;
+        fence_before_sync();  // TMEM reads of this group precede the next group's MMAs
+        if (!active) continue;
+        __syncwarp();
+
+        // remaining stages on the CUDA cores (per warp)
+        float Bv[nd / 2];
+        if (W.is_lgs) {
+            const float2 *kt = W.ktil + (size_t)v * (D2 * n);
+            constexpr int DYP = (D2 + 1) / 2, DXP = (n + 1) / 2, TASKS = DYP * DXP;
+            for (int task = lane; task < TASKS; task += 32) {
+                const int dyp = task / DXP, dxp = task - dyp * DXP;
+                const int dyi0 = 2 * dyp, dx0 = 2 * dxp;
+                const bool has_dy1 = dyi0 + 1 < D2, has_dx1 = dx0 + 1 < n;
+                const float2 *g0 = Gak + dyi0 * GAK;
+                const float2 *g1 = Gak + (has_dy1 ? dyi0 + 1 : dyi0) * GAK;
+                float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;
+#pragma unroll 4
+                for (int k = 0; k < N; ++k) {
+                    const float2 ga0 = g0[k], ga1 = g1[k];
+                    const float2 t0 = Ta[k * NO + dx0];
+                    const float2 t1 = has_dx1 ? Ta[k * NO + dx0 + 1] : make_float2(0.f, 0.f);
+                    cmacc(c00, ga0, t0);
+                    cmacc(c01, ga0, t1);
+                    cmacc(c10, ga1, t0);
+                    cmacc(c11, ga1, t1);
+                }
+                auto put = [&](int dyi, int dx, float2 c) {
+                    const float2 kv = __ldg(kt + dyi * n + dx);
+                    Mw[dyi * n + dx] = make_float2(c.x * kv.x - c.y * kv.y, c.x * kv.y + c.y * kv.x);
+                };
+                put(dyi0, dx0, c00);
+                if (has_dx1) put(dyi0, dx0 + 1, c01);
+                if (has_dy1) {
+                    put(dyi0 + 1, dx0, c10);
+                    if (has_dx1) put(dyi0 + 1, dx0 + 1, c11);
+                }
+            }
+            __syncwarp();
+            constexpr int HALF_DY = (D2 + 1) / 2;
+            const int dyi_begin = half * HALF_DY;
+            float2 Gc[n];
+#pragma unroll
+            for (int d = 0; d < n; ++d) Gc[d] = ix < nd ? Gt[d * nd + ix] : make_float2(0.f, 0.f);
+            float Bp[nd];
+#pragma unroll
+            for (int i = 0; i < nd; ++i) Bp[i] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < HALF_DY; ++j) {
+                const int dyi = dyi_begin + j;
+                if (dyi < D2) {
+                    float2 p = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < n; ++d) cmacc(p, Mw[dyi * n + d], Gc[d]);
+                    const int dy = dyi - (n - 1);
+                    const float2 *gr = Gt + (dy >= 0 ? dy : -dy) * nd;
+                    const float sg = dy >= 0 ? 1.0f : -1.0f;
+#pragma unroll
+                    for (int i = 0; i < nd; ++i) {
+                        const float2 gv = gr[i];
+                        Bp[i] = fmaf(gv.x, p.x, fmaf(-sg * gv.y, p.y, Bp[i]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < nd; ++i) Bp[i] += __shfl_xor_sync(0xffffffffu, Bp[i], 16);
+#pragma unroll
+            for (int j = 0; j < nd / 2; ++j) Bv[j] = half ? Bp[nd / 2 + j] : Bp[j];
+        } else {
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < nd / 2; ++j) {
+                const int iy = half * (nd / 2) + j;
+                float s = 0.0f;
+#pragma unroll
+                for (int r = 0; r < b; ++r)
+#pragma unroll
+                    for (int c = 0; c < b; ++c) s += Iw[(b * iy + r) * (N + 1) + b * ix + c];
+                Bv[j] = s;
+            }
+        }
+        float sb = 0.0f;
+        if (ix < nd) {
+#pragma unroll
+            for (int j = 0; j < nd / 2; ++j) sb += Bv[j];
+        }
+        sb = wsum(sb);
+        const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
+        float sc = 0.0f, sx = 0.0f, sy = 0.0f;
+        if (ix < nd) {
+#pragma unroll
+            for (int j = 0; j < nd / 2; ++j) {
+                const int iy = half * (nd / 2) + j, o = iy * nd + ix;
+                const float e = scale * Bv[j];
+                const float c = a.noise ? noise_pixel(e, W.read_noise, a.seed, (uint32_t)(v * nd2 + o),
+                                                      (uint32_t)W.gs_index, tlo, thi)
+                                        : e;
+                if (W.st_E) W.st_E[(size_t)v * nd2 + o] = e;
+                if (W.st_C) W.st_C[(size_t)v * nd2 + o] = c;
+                sc += c;
+                sx = fmaf((float)ix - cd, c, sx);
+                sy = fmaf((float)iy - cd, c, sy);
+            }
+        }
+        sc = wsum(sc);
+        sx = wsum(sx);
+        sy = wsum(sy);
+        if (lane == 0) {
+            const bool okc = sc > 0.0f;
+            W.slopes[2 * v] = okc ? sx / sc : 0.0f;
+            W.slopes[2 * v + 1] = okc ? sy / sc : 0.0f;
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (*sflag && tid == 0 && a.status) atomicCAS(a.status, 0, 5 /* WFS_ETIMEOUT */);
+    fence_after_sync();
+    if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+uint16_t bf16_bits(float f) {  // round to nearest even (finite inputs)
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_float(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+template <int n, int nd>
+cudaError_t launch_tc(const ShArgs &a, cudaStream_t s) {
+    using Lay = TcLayout<n, nd>;
+    const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
+    cudaError_t e = cudaFuncSetAttribute(k_sh_tc<n, nd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int groups = (a.total + 3) / 4;
+    int blocks = groups < 152 * 3 ? groups : 152 * 3;
+    k_sh_tc<n, nd><<<blocks, kTcThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool sh_tc_supported(int n, int N, int nd) { return N == 32 && ((n == 10 && nd == 16) || (n == 8 && nd == 16)); }
+
+// Operand tiles of the two constant matrices, already in the swizzled shared layout.
+void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
+                    const double *Ga_im64, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
+                    std::vector<uint8_t> &B2l) {
+    B1.assign(8192, 0);
+    B2h.assign(4096, 0);
+    B2l.assign(4096, 0);
+    auto put = [](std::vector<uint8_t> &t, int r, int k, float v) {
+        const uint16_t h = bf16_bits(v);
+        memcpy(t.data() + sw128_off(r, k), &h, 2);
+    };
+    // B1[row = c' * 32 + m][K = t * 2n + c * n + q]
+    for (int cp = 0; cp < 2; ++cp)
+        for (int m = 0; m < N; ++m)
+            for (int t = 0; t < 3; ++t)
+                for (int c = 0; c < 2; ++c)
+                    for (int q = 0; q < n; ++q) {
+                        const double fr = F_re64[q * N + m], fi = F_im64[q * N + m];
+                        double val;
+                        if (c == 0 && cp == 0) val = fr;
+                        else if (c == 1 && cp == 0) val = -fi;
+                        else if (c == 0 && cp == 1) val = fi;
+                        else val = fr;
+                        const float hi = bf16_float(bf16_bits((float)val));
+                        const float lo = (float)(val - (double)hi);
+                        put(B1, cp * 32 + m, t * 2 * n + c * n + q, t == 2 ? lo : hi);
+                    }
+    // B2h[row = c'' * 16 + dx][K = h * 32 + m] = Ga_hi, B2l = [Ga_lo; 0]
+    for (int cpp = 0; cpp < 2; ++cpp)
+        for (int dx = 0; dx < n; ++dx)
+            for (int m = 0; m < N; ++m) {
+                const double val = cpp == 0 ? Ga_re64[dx * N + m] : Ga_im64[dx * N + m];
+                const float hi = bf16_float(bf16_bits((float)val));
+                const float lo = (float)(val - (double)hi);
+                put(B2h, cpp * 16 + dx, m, hi);
+                put(B2h, cpp * 16 + dx, 32 + m, hi);
+                put(B2l, cpp * 16 + dx, m, lo);
+            }
+}
+
+cudaError_t launch_sh_tc(const ShArgs &a, cudaStream_t s) {
+    if (a.total <= 0) return cudaSuccess;
+    if (a.n == 10 && a.nd == 16) return launch_tc<10, 16>(a, s);
+    if (a.n == 8 && a.nd == 16) return launch_tc<8, 16>(a, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gbwfs

@@ -268,3 +268,60 @@ def test_host_buffer_path_and_batch_match_device_path():
     native.wfs_batch_destroy(b)
     w.close()
     w1.close()
+
+
+# ---------------------------------------------------------------- split-BF16 tensor-core DFT
+
+def test_config3_bf16x3_sampled_parity_full_launch():
+    """The ELT frame with the LGS DFT on the tensor cores (BF16 x3, FP32 accumulation), full
+    launch, sampled subapertures against the FP64 oracle at the same bars as the FP32 path."""
+    cfg = inputs.config3(inputs.PREC_BF16X3)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    t = 0.071
+    gpu, w = run_library(cfg, scr, t)
+    sel = []
+    for k, d in enumerate(gpu):
+        nv = len(d["slopes"])
+        sel.append(np.arange(k + 3, nv, 31, dtype=np.int32) if cfg.stars[k].is_lgs else np.arange(nv, dtype=np.int32))
+    _check_wfs(cfg, scr, t, gpu, sel=sel)
+    for k, d in enumerate(gpu):
+        assert np.all(np.isfinite(d["slopes"])) and np.all(np.isfinite(d["E"]))
+    w.close()
+
+
+def test_bf16x3_matches_fp32_path_everywhere():
+    """Full ELT frame: every subaperture of the tensor-core path against the FP32 path."""
+    scr = inputs.make_screens(inputs.config3().layers, 3000)
+    a, wa = run_library(inputs.config3(inputs.PREC_FP32), scr, 0.2, stages=True)
+    b, wb = run_library(inputs.config3(inputs.PREC_BF16X3), scr, 0.2, stages=True)
+    for x, y in zip(a, b):
+        assert slope_rms(y["slopes"], x["slopes"]) < SLOPE_RMS
+        assert rel_per_subap(y["E"], x["E"]) < INT_REL
+        assert rel_per_subap(y["I"], x["I"]) < INT_REL
+    wa.close()
+    wb.close()
+
+
+@pytest.mark.parametrize("n_sub,n,lgs,noise", [(13, 10, True, False), (11, 8, True, True),
+                                               (9, 10, False, False), (7, 8, False, True)])
+def test_bf16x3_edge_geometries(n_sub, n, lgs, noise):
+    """Ragged groups (valid count not a multiple of 4), NGS spots through the tensor-core
+    kernel's binning branch, n = 8 and 10, noise on and off."""
+    cfg = _small_cfg(n_sub, n, 32, 16, lgs)
+    cfg.geometries[0].precision = inputs.PREC_BF16X3
+    scr = inputs.make_screens(cfg.layers, 8)
+    gpu, w = run_library(cfg, scr, 0.003, seed=4, noise=noise)
+    assert w.total % 4 != 0 or n_sub == 9
+    _check_wfs(cfg, scr, 0.003, gpu, noise=noise, seed=4)
+    if noise:
+        ref = oracle.measure_wfs(cfg, scr, 0, 0.003, seed=4, noise=True, stages=True)
+        same = np.abs(gpu[0]["C"] - ref["C"]) < 1e-3
+        assert same.mean() >= 0.999
+    w.close()
+
+
+def test_bf16x3_unsupported_geometry_is_refused():
+    cfg = inputs.config2(inputs.PREC_BF16X3)
+    with pytest.raises(native.WfsError) as ei:
+        native.Wfs(cfg)
+    assert ei.value.status == native.WFS_EUNSUPPORTED
