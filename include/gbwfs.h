@@ -231,14 +231,37 @@ wfs_status wfs_noise_apply(const float *expected, int n, float read_noise_e, uin
                            void *stream);
 
 /*
- * Batching: several handles (uneven geometries) measured by one call.
- * wfs_batch_create keeps the handle pointers (they must outlive the batch);
- * wfs_batch_measure takes per-handle screens, times and slope buffers
- * (host arrays of n device pointers / times).
+ * Batching: several handles (uneven geometries, precisions, layer counts) measured
+ * by one call.  wfs_batch_create keeps the handle pointers (they must outlive the
+ * batch; at most 64, all on the current device, each at most once) and merges their
+ * work tables: one projection launch covers every wavefront sensor of every
+ * instance, and one persistent spot launch per kernel class (kernel kind, n_pix_sub,
+ * n_fft, n_det) covers all subapertures of that class across instances.
+ * wfs_batch_measure takes host arrays of n device screen pointers, n times and n
+ * device slope buffers (laid out as for wfs_measure of each handle).  The first call
+ * builds a CUDA graph (projection node, then the class nodes in parallel); later
+ * calls rewrite the nodes' parameters and replay it (GBWFS_BATCH_GRAPH=0 in the
+ * environment launches directly instead).  Results equal those of wfs_measure on
+ * each handle.  The instances' projected OPD goes to each handle's own scratch, so
+ * calls that involve the same handle must not overlap in time.  Asynchronous.
  */
 wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out);
 wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const double *t_s,
                              float *const *slopes_out, void *stream);
+/*
+ * Autotuner: times the candidate launch shapes of every kernel class on these inputs
+ * (persistent grid size; warps per CTA for the FP32 32-point kernel), keeps the
+ * fastest for later calls, and appends it to the file named by the environment
+ * variable GBWFS_TUNE_CACHE (if set), from which wfs_batch_create reads earlier
+ * choices.  Synchronises `stream`; leaves the slopes of one measurement in slopes_out.
+ */
+wfs_status wfs_batch_tune(wfs_batch b, const float *const *screens, const double *t_s,
+                          float *const *slopes_out, void *stream);
+/* Kernel classes of a batch (kind: 0 generic FP32, 1 FP32 N = 32, 2 tensor-core BF16x3). */
+typedef struct {
+    int kind, n_pix_sub, n_fft, n_det, n_wfs, n_subaps, grid_cap, cta_warps;
+} wfs_batch_class;
+wfs_status wfs_batch_info(wfs_batch b, int max, wfs_batch_class *out, int *n_out);
 wfs_status wfs_batch_destroy(wfs_batch b);
 
 /*

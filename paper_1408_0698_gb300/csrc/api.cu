@@ -14,7 +14,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -35,6 +37,19 @@ struct GeomDev {
     uint8_t *tcB1 = nullptr, *tcB2h = nullptr, *tcB2l = nullptr;  // BF16X3 operand tiles
 };
 
+// One spot launch: consecutive entries of a WFS table sharing a kernel class.
+struct SpotGroup {
+    int geom = 0;            // geometry index (in the owning handle)
+    int first = 0, count = 0, total = 0;
+    int kind = 0;            // SpotKind
+    int grid_cap = 0, cta_warps = 0;
+};
+
+int spot_kind(const wfs_geometry &g) {
+    if (g.precision == WFS_PREC_BF16X3) return kSpotTc;
+    return sh_n32_supported(g.n_pix_sub, g.n_fft, g.n_det) ? kSpotN32 : kSpotGeneric;
+}
+
 struct GsDev {
     wfs_guide_star gs{};
     std::vector<double> na_alt, na_w;
@@ -51,6 +66,13 @@ struct GsDev {
 }  // namespace
 
 struct wfs_ctx {
+    // work tables: one instance, WFS entries grouped by geometry
+    InstDesc inst_host{};
+    InstDesc *d_inst = nullptr;
+    std::vector<WfsDesc> wfs_host;
+    WfsDesc *d_wfs = nullptr;
+    std::vector<SpotGroup> groups;
+    int proj_blocks = 0;
     wfs_telescope tel{};
     std::vector<GeomDev> geoms;
     std::vector<GsDev> gs;
@@ -81,8 +103,32 @@ struct wfs_ctx {
     bool ev_overflow = false;
 };
 
+// A batch: the instances' work tables merged, WFS entries grouped by kernel class
+// (kind, n, N, nd) across instances, replayed as one CUDA graph (projection node, then one
+// spot node per class in parallel) whose kernel parameters are rewritten per call.
+struct BatchClass {
+    int kind = 0;
+    const GeomDev *geom = nullptr;   // geometry tables (those of the first handle in the class)
+    int first = 0, count = 0, total = 0;
+    int grid_cap = 0, cta_warps = 0;
+    std::string key;
+};
+
 struct wfs_batch_ctx {
     std::vector<wfs_handle> hs;
+    int device = 0;
+    InstDesc *d_inst = nullptr;
+    WfsDesc *d_wfs = nullptr;
+    std::vector<WfsDesc> wfs_host;
+    std::vector<BatchClass> classes;
+    int proj_blocks = 0;
+    ProjArgs *pa = nullptr;          // parameter blocks the graph nodes point to
+    std::vector<ShArgs *> sa;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t proj_node = nullptr;
+    std::vector<cudaGraphNode_t> spot_nodes;  // per class (null when the class is empty)
+    int use_graph = 1;
 };
 
 namespace {
@@ -219,6 +265,8 @@ void release(wfs_ctx *h) {
     }
     cudaFree(h->d_opd);
     cudaFree(h->d_status);
+    cudaFree(h->d_inst);
+    cudaFree(h->d_wfs);
     cudaFree(h->d_screens_stage);
     cudaFree(h->d_slopes_stage);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -292,6 +340,24 @@ wfs_status validate(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs
     return WFS_OK;
 }
 
+// Geometry tables of a spot launch.
+void fill_geom_args(ShArgs &sa, const GeomDev &G) {
+    sa.n = G.g.n_pix_sub;
+    sa.N = G.g.n_fft;
+    sa.nd = G.g.n_det;
+    sa.mask_words = G.mask_words;
+    sa.F = G.F;
+    sa.Ga = G.Ga;
+    sa.G = G.G;
+    sa.tc_B1 = G.tcB1;
+    sa.tc_B2h = G.tcB2h;
+    sa.tc_B2l = G.tcB2l;
+}
+
+const char *kind_name(int kind) {
+    return kind == kSpotTc ? "spot_tc_bf16x3_N" : kind == kSpotN32 ? "spot_n32_fp32_N" : "spot_fp32_N";
+}
+
 wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slopes,
                         const wfs_stage_out *st, cudaStream_t stream) {
     if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
@@ -301,134 +367,67 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     cudaGetDevice(&dev);
     if (dev != h->device) return fail(h, WFS_EINVAL, "current device differs from the handle's device");
     h->last_stream = stream;
-    float *opd = (st && st->opd) ? st->opd : h->d_opd;
+    InstDyn dyn;
+    memset(&dyn, 0, sizeof dyn);
+    dyn.screens = screens;
+    dyn.opd = (st && st->opd) ? st->opd : h->d_opd;
+    dyn.slopes = slopes;
+    dyn.st_I = st ? st->intensity : nullptr;
+    dyn.st_E = st ? st->expected : nullptr;
+    dyn.st_C = st ? st->counts : nullptr;
+    dyn.t = t;
+    dyn.noise = h->noise;
 
-    ProjArgs pa;
-    memset(&pa, 0, sizeof pa);
-    pa.screens = screens;
-    pa.n_layers = h->n_layers;
-    pa.S = h->S;
-    pa.ds = h->ds;
-    pa.t = t;
-    for (int l = 0; l < h->n_layers; ++l) {
-        pa.alt[l] = h->alt[l];
-        pa.vx[l] = h->vx[l];
-        pa.vy[l] = h->vy[l];
-        pa.x0[l] = h->x0[l];
-        pa.y0[l] = h->y0[l];
+    static thread_local ProjArgs pa;
+    pa.inst = h->d_inst;
+    pa.wfs = h->d_wfs;
+    pa.n_wfs = (int)h->wfs_host.size();
+    pa.n_inst = 1;
+    pa.dyn[0] = dyn;
+    cudaError_t e;
+    if (h->proj_blocks > 0) {
+        long slot = timed_begin(h, "project", stream);
+        e = launch_project(pa, h->proj_blocks, stream);
+        timed_end(h, slot, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "projection launch");
     }
-    int blocks = 0;
-    pa.n_wfs = (int)h->gs.size();
-    for (size_t w = 0; w < h->gs.size(); ++w) {
-        const GsDev &s = h->gs[w];
-        const wfs_geometry &g = h->geoms[s.gs.geometry_index].g;
-        ProjWfs &P = pa.w[w];
-        P.subap = s.d_ids;
-        P.opd = opd + s.opd_off;
-        P.n = g.n_pix_sub;
-        P.n_sub = g.n_sub;
-        P.n_valid = s.n_valid;
-        P.is_lgs = s.gs.is_lgs;
-        P.range_m = s.gs.range_m;
-        P.theta_x = s.gs.theta_x_rad;
-        P.theta_y = s.gs.theta_y_rad;
-        P.pupil_dx_over_ds = (h->tel.diameter_m / (g.n_sub * g.n_pix_sub)) / h->ds;
-        P.block_begin = blocks;
-        blocks += project_blocks(s.n_valid * g.n_pix_sub * g.n_pix_sub);
-    }
-    long slot = blocks > 0 ? timed_begin(h, "project", stream) : -1;
-    cudaError_t e = launch_project(pa, blocks, stream);
-    timed_end(h, slot, stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "projection launch");
 
-    // The largest geometry runs on the caller's stream, launched last; the others run on side
+    // The largest group runs on the caller's stream, launched last; the others run on side
     // streams forked after the projection (launched first, so their few CTAs are resident
     // before the large launch fills the GPU) and joined before the call returns.
-    std::vector<ShArgs> jobs;
-    jobs.reserve(h->geoms.size());
-    for (size_t gi = 0; gi < h->geoms.size(); ++gi) {
-        const GeomDev &G = h->geoms[gi];
-        ShArgs sa;
-        memset(&sa, 0, sizeof sa);
-        sa.n = G.g.n_pix_sub;
-        sa.N = G.g.n_fft;
-        sa.nd = G.g.n_det;
-        sa.mask_words = G.mask_words;
-        sa.F = G.F;
-        sa.Ga = G.Ga;
-        sa.G = G.G;
-        sa.tc_B1 = G.tcB1;
-        sa.tc_B2h = G.tcB2h;
-        sa.tc_B2l = G.tcB2l;
-        sa.seed = h->seed;
-        sa.noise = h->noise;
-        sa.t = t;
-        sa.status = h->d_status;
-        int total = 0, nw = 0;
-        for (size_t w = 0; w < h->gs.size(); ++w) {
-            const GsDev &s = h->gs[w];
-            if (s.gs.geometry_index != (int)gi) continue;
-            ShWfs &W = sa.w[nw++];
-            W.opd = opd + s.opd_off;
-            W.mask = s.d_mask;
-            W.fill = s.d_fill;
-            W.ktil = s.d_ktil;
-            W.slopes = slopes + s.slope_off;
-            W.st_I = (st && st->intensity) ? st->intensity + s.int_off : nullptr;
-            W.st_E = (st && st->expected) ? st->expected + s.det_off : nullptr;
-            W.st_C = (st && st->counts) ? st->counts + s.det_off : nullptr;
-            W.n_valid = s.n_valid;
-            W.is_lgs = s.gs.is_lgs;
-            W.gs_index = (int)w;
-            W.subap_begin = total;
-            W.k_phase = (float)(2.0 * M_PI / s.gs.wavelength_m);
-            W.photons = (float)s.gs.photons_per_subap;
-            W.read_noise = (float)s.gs.read_noise_e;
-            total += s.n_valid;
-        }
-        if (!nw || !total) continue;
-        sa.n_wfs = nw;
-        sa.total = total;
-        jobs.push_back(sa);
-    }
-    if (jobs.empty()) return WFS_OK;
     size_t big = 0;
-    for (size_t j = 1; j < jobs.size(); ++j)
-        if (jobs[j].total > jobs[big].total) big = j;
-    auto prec_of = [&](const ShArgs &sa) {
-        for (const GeomDev &G : h->geoms)
-            if (G.F == sa.F) return G.g.precision;
-        return (int)WFS_PREC_FP32;
-    };
-    auto launch_job = [&](const ShArgs &sa, cudaStream_t ls) -> cudaError_t {
-        const int prec = prec_of(sa);
-        std::string name;
-        cudaError_t err;
-        long sl;
-        if (prec == WFS_PREC_BF16X3) {
-            sl = timed_begin(h, "spot_tc_bf16x3_N" + std::to_string(sa.N), ls);
-            err = launch_sh_tc(sa, ls);
-        } else if (sh_n32_supported(sa.n, sa.N, sa.nd)) {
-            sl = timed_begin(h, "spot_n32_fp32_N" + std::to_string(sa.N), ls);
-            err = launch_sh_n32(sa, ls);
-        } else {
-            sl = timed_begin(h, "spot_fp32_N" + std::to_string(sa.N), ls);
-            err = launch_sh_fp32(sa, ls);
-        }
+    for (size_t j = 1; j < h->groups.size(); ++j)
+        if (h->groups[j].total > h->groups[big].total) big = j;
+    static thread_local ShArgs sa;
+    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls) -> cudaError_t {
+        memset(&sa, 0, offsetof(ShArgs, dyn));
+        fill_geom_args(sa, h->geoms[G.geom]);
+        sa.inst = h->d_inst;
+        sa.wfs = h->d_wfs + G.first;
+        sa.n_wfs = G.count;
+        sa.total = G.total;
+        sa.status = h->d_status;
+        sa.grid_cap = G.grid_cap;
+        sa.cta_warps = G.cta_warps;
+        sa.n_inst = 1;
+        sa.dyn[0] = dyn;
+        long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
+        cudaError_t err = launch_spot(G.kind, sa, ls);
         timed_end(h, sl, ls);
         return err;
     };
     size_t k = 0;
-    for (size_t j = 0; j < jobs.size(); ++j) {
-        if (j == big) continue;
+    for (size_t j = 0; j < h->groups.size(); ++j) {
+        if (j == big || h->groups[j].total == 0) continue;
         if (k >= h->side.size()) return fail(h, WFS_EINVAL, "internal: missing side stream");
         if (k == 0 && (e = cudaEventRecord(h->ev_fork, stream)) != cudaSuccess) return cuda_fail(h, e, "fork");
         if ((e = cudaStreamWaitEvent(h->side[k], h->ev_fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork wait");
-        if ((e = launch_job(jobs[j], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+        if ((e = launch_group(h->groups[j], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "spot launch");
         if ((e = cudaEventRecord(h->ev_join[k], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "join");
         ++k;
     }
-    if ((e = launch_job(jobs[big], stream)) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+    if (!h->groups.empty() && h->groups[big].total > 0)
+        if ((e = launch_group(h->groups[big], stream)) != cudaSuccess) return cuda_fail(h, e, "spot launch");
     for (size_t j = 0; j < k; ++j)
         if ((e = cudaStreamWaitEvent(stream, h->ev_join[j], 0)) != cudaSuccess) return cuda_fail(h, e, "join wait");
     return WFS_OK;
@@ -582,6 +581,72 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 delete h;
                 return cuda_fail(nullptr, e, "elongation table launch");
             }
+        }
+    }
+    // work tables: the instance (layers, seed) and the WFS entries grouped by geometry
+    {
+        InstDesc &I = h->inst_host;
+        memset(&I, 0, sizeof I);
+        I.n_layers = h->n_layers;
+        I.S = h->S;
+        I.ds = h->ds;
+        for (int l = 0; l < h->n_layers; ++l) {
+            I.alt[l] = h->alt[l];
+            I.vx[l] = h->vx[l];
+            I.vy[l] = h->vy[l];
+            I.x0[l] = h->x0[l];
+            I.y0[l] = h->y0[l];
+        }
+        I.seed = seed;
+        int blocks = 0;
+        for (int gi = 0; gi < n_geom; ++gi) {
+            SpotGroup G;
+            G.geom = gi;
+            G.first = (int)h->wfs_host.size();
+            G.kind = spot_kind(geom[gi]);
+            for (int w = 0; w < n_gs; ++w) {
+                const GsDev &s = h->gs[w];
+                if (s.gs.geometry_index != gi) continue;
+                const wfs_geometry &g = geom[gi];
+                WfsDesc d;
+                memset(&d, 0, sizeof d);
+                d.inst = 0;
+                d.gs_index = w;
+                d.n = g.n_pix_sub;
+                d.n_sub = g.n_sub;
+                d.n_valid = s.n_valid;
+                d.is_lgs = s.gs.is_lgs;
+                d.range_m = s.gs.range_m;
+                d.theta_x = s.gs.theta_x_rad;
+                d.theta_y = s.gs.theta_y_rad;
+                d.pupil_dx_over_ds = (tel->diameter_m / (g.n_sub * g.n_pix_sub)) / h->ds;
+                d.k_phase = (float)(2.0 * M_PI / s.gs.wavelength_m);
+                d.photons = (float)s.gs.photons_per_subap;
+                d.read_noise = (float)s.gs.read_noise_e;
+                d.subap = s.d_ids;
+                d.mask = s.d_mask;
+                d.fill = s.d_fill;
+                d.ktil = s.d_ktil;
+                d.opd_off = (long long)s.opd_off;
+                d.slope_off = (long long)s.slope_off;
+                d.int_off = (long long)s.int_off;
+                d.det_off = (long long)s.det_off;
+                d.proj_block_begin = blocks;
+                blocks += project_blocks(s.n_valid * g.n_pix_sub * g.n_pix_sub);
+                d.subap_begin = G.total;
+                G.total += s.n_valid;
+                h->wfs_host.push_back(d);
+                ++G.count;
+            }
+            if (G.count) h->groups.push_back(G);
+        }
+        h->proj_blocks = blocks;
+        if ((e = cudaMalloc(&h->d_inst, sizeof(InstDesc))) != cudaSuccess ||
+            (e = cudaMemcpy(h->d_inst, &h->inst_host, sizeof(InstDesc), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = upload(&h->d_wfs, h->wfs_host)) != cudaSuccess) {
+            release(h);
+            delete h;
+            return cuda_fail(nullptr, e, "work table upload");
         }
     }
     for (int i = 1; i < n_geom; ++i) {
@@ -765,12 +830,255 @@ wfs_status wfs_noise_apply(const float *expected, int n, float read_noise_e, uin
     return WFS_OK;
 }
 
+namespace {
+
+void batch_free(wfs_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_wfs);
+    delete b->pa;
+    for (ShArgs *p : b->sa) delete p;
+    delete b;
+}
+
+void batch_drop_graph(wfs_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->proj_node = nullptr;
+    b->spot_nodes.clear();
+}
+
+// Per-call parameters of every node.
+wfs_status batch_fill(wfs_batch b, const float *const *screens, const double *t, float *const *slopes) {
+    const int n = (int)b->hs.size();
+    for (int i = 0; i < n; ++i) {
+        if (!screens[i] || !slopes[i] || !is_finite(t[i]))
+            return fail(nullptr, WFS_EINVAL, "batch: null buffer or non-finite time for instance " + std::to_string(i));
+        InstDyn &d = b->pa->dyn[i];
+        memset(&d, 0, sizeof d);
+        d.screens = screens[i];
+        d.opd = b->hs[i]->d_opd;
+        d.slopes = slopes[i];
+        d.t = t[i];
+        d.noise = b->hs[i]->noise;
+        b->hs[i]->last_stream = nullptr;
+    }
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        ShArgs &a = *b->sa[c];
+        memcpy(a.dyn, b->pa->dyn, sizeof(InstDyn) * n);
+        a.grid_cap = b->classes[c].grid_cap;
+        a.cta_warps = b->classes[c].cta_warps;
+    }
+    return WFS_OK;
+}
+
+cudaError_t batch_build_graph(wfs_batch b) {
+    cudaError_t e;
+    if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess) return e;
+    LaunchShape ps;
+    project_launch_shape(b->proj_blocks, &ps);
+    void *pargs[] = {(void *)b->pa};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = (void *)ps.func;
+    kp.gridDim = ps.grid;
+    kp.blockDim = ps.block;
+    kp.sharedMemBytes = (unsigned)ps.smem;
+    kp.kernelParams = pargs;
+    if ((e = cudaGraphAddKernelNode(&b->proj_node, b->graph, nullptr, 0, &kp)) != cudaSuccess) return e;
+    b->spot_nodes.assign(b->classes.size(), nullptr);
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        if (b->classes[c].total <= 0) continue;
+        LaunchShape sh;
+        if ((e = spot_launch_shape(b->classes[c].kind, *b->sa[c], &sh)) != cudaSuccess) return e;
+        void *sargs[] = {(void *)b->sa[c]};
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)sh.func;
+        kp.gridDim = sh.grid;
+        kp.blockDim = sh.block;
+        kp.sharedMemBytes = (unsigned)sh.smem;
+        kp.kernelParams = sargs;
+        if ((e = cudaGraphAddKernelNode(&b->spot_nodes[c], b->graph, &b->proj_node, 1, &kp)) != cudaSuccess) return e;
+    }
+    return cudaGraphInstantiate(&b->exec, b->graph, 0);
+}
+
+cudaError_t batch_update_graph(wfs_batch b) {
+    cudaError_t e;
+    LaunchShape ps;
+    project_launch_shape(b->proj_blocks, &ps);
+    void *pargs[] = {(void *)b->pa};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = (void *)ps.func;
+    kp.gridDim = ps.grid;
+    kp.blockDim = ps.block;
+    kp.sharedMemBytes = (unsigned)ps.smem;
+    kp.kernelParams = pargs;
+    if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->proj_node, &kp)) != cudaSuccess) return e;
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        if (!b->spot_nodes[c]) continue;
+        LaunchShape sh;
+        if ((e = spot_launch_shape(b->classes[c].kind, *b->sa[c], &sh)) != cudaSuccess) return e;
+        void *sargs[] = {(void *)b->sa[c]};
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)sh.func;
+        kp.gridDim = sh.grid;
+        kp.blockDim = sh.block;
+        kp.sharedMemBytes = (unsigned)sh.smem;
+        kp.kernelParams = sargs;
+        if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->spot_nodes[c], &kp)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t batch_launch_direct(wfs_batch b, cudaStream_t s) {
+    cudaError_t e = launch_project(*b->pa, b->proj_blocks, s);
+    if (e != cudaSuccess) return e;
+    for (size_t c = 0; c < b->classes.size(); ++c)
+        if ((e = launch_spot(b->classes[c].kind, *b->sa[c], s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// ---- tuning cache: lines "key grid_cap cta_warps" in the file named by GBWFS_TUNE_CACHE
+std::string class_key(const BatchClass &c, int total) {
+    int bucket = 1;
+    while (bucket < total) bucket <<= 1;
+    cudaDeviceProp p;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&p, dev);
+    std::string name = p.name;
+    for (char &ch : name)
+        if (ch == ' ') ch = '_';
+    return "kind" + std::to_string(c.kind) + "_n" + std::to_string(c.geom->g.n_pix_sub) + "_N" +
+           std::to_string(c.geom->g.n_fft) + "_nd" + std::to_string(c.geom->g.n_det) + "_sub" +
+           std::to_string(bucket) + "_" + name;
+}
+
+bool cache_lookup(const std::string &key, int *cap, int *warps) {
+    const char *path = getenv("GBWFS_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char k[256];
+    int a = 0, b = 0;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d", k, &a, &b) == 3)
+        if (key == k) {
+            *cap = a;
+            *warps = b;
+            found = true;
+        }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, int cap, int warps) {
+    const char *path = getenv("GBWFS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d\n", key.c_str(), cap, warps);
+    fclose(f);
+}
+
+}  // namespace
+
 wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     if (!out || !hs || n < 1) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
-    for (int i = 0; i < n; ++i)
+    *out = nullptr;
+    if (n > kMaxInstances) return fail(nullptr, WFS_EINVAL, "batch: more than 64 instances");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < n; ++i) {
         if (!hs[i]) return fail(nullptr, WFS_EINVAL, "null handle in batch");
+        if (hs[i]->device != dev) return fail(nullptr, WFS_EINVAL, "batch handles must live on the current device");
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return fail(nullptr, WFS_EINVAL, "a handle appears twice in the batch");
+    }
     wfs_batch b = new wfs_batch_ctx();
     b->hs.assign(hs, hs + n);
+    b->device = dev;
+    // classes in order of first appearance; WFS entries of each class contiguous
+    for (int i = 0; i < n; ++i)
+        for (const SpotGroup &G : hs[i]->groups) {
+            const wfs_geometry &g = hs[i]->geoms[G.geom].g;
+            const std::string key = std::to_string(G.kind) + ":" + std::to_string(g.n_pix_sub) + ":" +
+                                    std::to_string(g.n_fft) + ":" + std::to_string(g.n_det);
+            size_t c = 0;
+            while (c < b->classes.size() && b->classes[c].key != key) ++c;
+            if (c == b->classes.size()) {
+                BatchClass bc;
+                bc.kind = G.kind;
+                bc.geom = &hs[i]->geoms[G.geom];
+                bc.key = key;
+                b->classes.push_back(bc);
+            }
+        }
+    std::vector<std::vector<WfsDesc>> per(b->classes.size());
+    for (int i = 0; i < n; ++i)
+        for (const SpotGroup &G : hs[i]->groups) {
+            const wfs_geometry &g = hs[i]->geoms[G.geom].g;
+            const std::string key = std::to_string(G.kind) + ":" + std::to_string(g.n_pix_sub) + ":" +
+                                    std::to_string(g.n_fft) + ":" + std::to_string(g.n_det);
+            size_t c = 0;
+            while (b->classes[c].key != key) ++c;
+            for (int k = 0; k < G.count; ++k) {
+                WfsDesc d = hs[i]->wfs_host[G.first + k];
+                d.inst = i;
+                per[c].push_back(d);
+            }
+        }
+    int blocks = 0;
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        BatchClass &bc = b->classes[c];
+        bc.first = (int)b->wfs_host.size();
+        for (WfsDesc d : per[c]) {
+            d.subap_begin = bc.total;
+            bc.total += d.n_valid;
+            d.proj_block_begin = blocks;
+            blocks += project_blocks(d.n_valid * d.n * d.n);
+            b->wfs_host.push_back(d);
+            ++bc.count;
+        }
+        int cap = 0, warps = 0;
+        if (cache_lookup(class_key(bc, bc.total), &cap, &warps)) {
+            bc.grid_cap = cap;
+            bc.cta_warps = warps;
+        }
+    }
+    b->proj_blocks = blocks;
+    std::vector<InstDesc> inst(n);
+    for (int i = 0; i < n; ++i) inst[i] = hs[i]->inst_host;
+    cudaError_t e;
+    if ((e = upload(&b->d_inst, inst)) != cudaSuccess || (e = upload(&b->d_wfs, b->wfs_host)) != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(nullptr, e, "batch table upload");
+    }
+    b->pa = new ProjArgs();
+    memset(b->pa, 0, sizeof(ProjArgs));
+    b->pa->inst = b->d_inst;
+    b->pa->wfs = b->d_wfs;
+    b->pa->n_wfs = (int)b->wfs_host.size();
+    b->pa->n_inst = n;
+    for (const BatchClass &bc : b->classes) {
+        ShArgs *a = new ShArgs();
+        memset(a, 0, sizeof(ShArgs));
+        fill_geom_args(*a, *bc.geom);
+        a->inst = b->d_inst;
+        a->wfs = b->d_wfs + bc.first;
+        a->n_wfs = bc.count;
+        a->total = bc.total;
+        a->status = hs[0]->d_status;
+        a->n_inst = n;
+        b->sa.push_back(a);
+    }
+    const char *g = getenv("GBWFS_BATCH_GRAPH");
+    b->use_graph = !(g && g[0] == '0');
     *out = b;
     return WFS_OK;
 }
@@ -778,16 +1086,113 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
 wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const double *t_s,
                              float *const *slopes_out, void *stream) {
     if (!b || !screens || !t_s || !slopes_out) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
-    for (size_t i = 0; i < b->hs.size(); ++i) {
-        wfs_status st = measure_impl(b->hs[i], screens[i], t_s[i], slopes_out[i], nullptr, (cudaStream_t)stream);
-        if (st != WFS_OK) return st;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(nullptr, WFS_EINVAL, "current device differs from the batch's device");
+    wfs_status st = batch_fill(b, screens, t_s, slopes_out);
+    if (st != WFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (!b->use_graph) {
+        if ((e = batch_launch_direct(b, s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
+        return WFS_OK;
     }
+    if (!b->exec) {
+        if ((e = batch_build_graph(b)) != cudaSuccess) {
+            batch_drop_graph(b);
+            return cuda_fail(nullptr, e, "batch graph build");
+        }
+    } else if ((e = batch_update_graph(b)) != cudaSuccess) {
+        return cuda_fail(nullptr, e, "batch graph update");
+    }
+    if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
+    return WFS_OK;
+}
+
+wfs_status wfs_batch_tune(wfs_batch b, const float *const *screens, const double *t_s, float *const *slopes_out,
+                          void *stream) {
+    if (!b || !screens || !t_s || !slopes_out) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
+    wfs_status st = batch_fill(b, screens, t_s, slopes_out);
+    if (st != WFS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = launch_project(*b->pa, b->proj_blocks, s)) != cudaSuccess) return cuda_fail(nullptr, e, "tune projection");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        BatchClass &bc = b->classes[c];
+        if (bc.total <= 0) continue;
+        std::vector<std::pair<int, int>> cand;  // (grid cap, warps per CTA)
+        if (bc.kind == kSpotN32) {
+            for (int w : {4, 8})
+                for (int m : {2, 4, 8, 16}) cand.push_back({152 * m * (8 / w), w});
+        } else if (bc.kind == kSpotTc) {
+            for (int m : {1, 2, 3}) cand.push_back({152 * m, 0});
+        } else {
+            for (int m : {2, 4, 8, 32}) cand.push_back({152 * m, 0});
+        }
+        float best = 1e30f;
+        std::pair<int, int> pick = cand[0];
+        for (const auto &cw : cand) {
+            ShArgs &a = *b->sa[c];
+            a.grid_cap = cw.first;
+            a.cta_warps = cw.second;
+            if ((e = launch_spot(bc.kind, a, s)) != cudaSuccess) break;  // warm-up
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; ++r)
+                if ((e = launch_spot(bc.kind, a, s)) != cudaSuccess) break;
+            cudaEventRecord(e1, s);
+            if (e != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                pick = cw;
+            }
+        }
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(nullptr, e, "tune launch");
+        }
+        bc.grid_cap = pick.first;
+        bc.cta_warps = pick.second;
+        b->sa[c]->grid_cap = pick.first;
+        b->sa[c]->cta_warps = pick.second;
+        cache_store(class_key(bc, bc.total), pick.first, pick.second);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    batch_drop_graph(b);  // the next measure captures the tuned shapes
+    return WFS_OK;
+}
+
+wfs_status wfs_batch_info(wfs_batch b, int max, wfs_batch_class *out, int *n_out) {
+    if (!b || !n_out || (max > 0 && !out)) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
+    int k = 0;
+    for (const BatchClass &bc : b->classes) {
+        if (k < max) {
+            wfs_batch_class &o = out[k];
+            o.kind = bc.kind;
+            o.n_pix_sub = bc.geom->g.n_pix_sub;
+            o.n_fft = bc.geom->g.n_fft;
+            o.n_det = bc.geom->g.n_det;
+            o.n_wfs = bc.count;
+            o.n_subaps = bc.total;
+            o.grid_cap = bc.grid_cap;
+            o.cta_warps = bc.cta_warps;
+        }
+        ++k;
+    }
+    *n_out = k;
     return WFS_OK;
 }
 
 wfs_status wfs_batch_destroy(wfs_batch b) {
     if (!b) return fail(nullptr, WFS_EINVAL, "null batch");
-    delete b;
+    cudaDeviceSynchronize();
+    batch_free(b);
     return WFS_OK;
 }
 

@@ -1,5 +1,13 @@
-// internal.h -- kernel argument blocks and launchers shared by the library's
-// translation units (never installed; the public ABI is include/gbwfs.h).
+// internal.h -- work tables, kernel argument blocks and launchers shared by the
+// library's translation units (never installed; the public ABI is include/gbwfs.h).
+//
+// Every launch reads two device work tables: one InstDesc per instance (a handle:
+// its turbulence layers and noise seed) and one WfsDesc per wavefront sensor (its
+// static subaperture tables and its offsets into the instance's buffers).  Only the
+// per-call values -- screens, output buffers, time, noise switch -- travel in the
+// kernel parameters (InstDyn, one per instance), so a batch of uneven instances is
+// one projection launch plus one spot launch per kernel class, and a captured graph
+// is replayed by rewriting those parameters.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,54 +20,66 @@ namespace gbwfs {
 constexpr int kMaxGuideStars = 32;
 constexpr int kMaxLayers = 32;
 constexpr int kMaxNaSlices = 16;
-constexpr int kMaxN = 64;       // largest DFT size
-constexpr int kMaxNPix = 32;    // largest subaperture side in pupil pixels
+constexpr int kMaxN = 64;           // largest DFT size
+constexpr int kMaxNPix = 32;        // largest subaperture side in pupil pixels
+constexpr int kMaxInstances = 64;   // instances per launch (batch size limit)
 
-// ---------------------------------------------------------------- projection
-struct ProjWfs {
-    const int32_t *subap;   // valid subaperture ids, sy * n_sub + sx
-    float *opd;             // [n_valid][n * n] output
-    int n, n_sub, n_valid, is_lgs;
-    double range_m, theta_x, theta_y;
-    double pupil_dx_over_ds;  // pupil pitch / screen pitch
-    int block_begin;          // first CTA of this WFS in the launch
+struct InstDesc {                   // static per instance
+    int n_layers, S;
+    double ds;
+    double alt[kMaxLayers], vx[kMaxLayers], vy[kMaxLayers], x0[kMaxLayers], y0[kMaxLayers];
+    uint64_t seed;
 };
 
+struct WfsDesc {                    // static per wavefront sensor
+    int inst;                       // index into the launch's instance tables
+    int gs_index;                   // guide-star index within its handle (noise counter)
+    int n, n_sub, n_valid, is_lgs;
+    double range_m, theta_x, theta_y;
+    double pupil_dx_over_ds;        // pupil pitch / screen pitch
+    float k_phase;                  // 2 pi / lambda
+    float photons, read_noise;
+    const int32_t *subap;           // [n_valid] ids sy * n_sub + sx
+    const uint32_t *mask;           // [n_valid][mask_words] lit-pixel bits, bit p*n+q
+    const float *fill;              // [n_valid]
+    const float2 *ktil;             // [n_valid][(2n-1)*n] elongation transfer (LGS only)
+    long long opd_off, slope_off, int_off, det_off;  // into the instance's buffers (floats)
+    int proj_block_begin;           // first CTA of this WFS in the projection launch
+    int subap_begin;                // first subaperture of this WFS in its spot launch
+};
+
+struct InstDyn {                    // per call, per instance
+    const float *screens;           // [L][S][S]
+    float *opd;                     // projected OPD, subaperture-tiled
+    float *slopes;                  // [sum n_valid][2]
+    float *st_I, *st_E, *st_C;      // optional stage outputs (null = not written)
+    double t;
+    int noise;
+};
+
+// ---------------------------------------------------------------- projection
 struct ProjArgs {
-    const float *screens;     // [L][S][S]
-    int n_layers, S;
-    double ds, t;
-    double alt[kMaxLayers], vx[kMaxLayers], vy[kMaxLayers], x0[kMaxLayers], y0[kMaxLayers];
-    int n_wfs;
-    ProjWfs w[kMaxGuideStars];
+    const InstDesc *inst;
+    const WfsDesc *wfs;
+    int n_wfs, n_inst;
+    InstDyn dyn[kMaxInstances];
 };
 
 // ---------------------------------------------------------------- spot / slopes
-struct ShWfs {
-    const float *opd;         // [n_valid][n*n]
-    const uint32_t *mask;     // [n_valid][mask_words] lit-pixel bits, bit p*n+q
-    const float *fill;        // [n_valid]
-    const float2 *ktil;       // [n_valid][(2n-1)*n] elongation transfer (LGS only)
-    float *slopes;            // [n_valid][2]
-    float *st_I, *st_E, *st_C;  // optional stage outputs
-    int n_valid, is_lgs, gs_index, subap_begin;
-    float k_phase;            // 2 pi / lambda
-    float photons, read_noise;
-};
-
 struct ShArgs {
     int n, N, nd, mask_words;
     const float2 *F;    // [n][N]  F^T: F[q*N + m] = exp(-2 pi i (m-cN)(q-cn)/N)
     const float2 *Ga;   // [n][N]  Ga[d*N + k] = exp(+2 pi i (k-cN) d / N), d = 0..n-1
     const float2 *G;    // [n][nd] G[d*nd + i] = sum_{r<b} exp(-2 pi i (b i + r - cN) d / N)
+    const void *tc_B1, *tc_B2h, *tc_B2l;  // BF16X3 operand tiles (pre-swizzled)
+    const InstDesc *inst;
+    const WfsDesc *wfs;  // this launch's WFS entries (subap_begin relative to them)
     int n_wfs, total;
-    uint64_t seed;
-    int noise;
-    double t;
     int *status;
-    // tensor-core operand tiles (BF16, pre-swizzled), used by the BF16X3 kernel only
-    const void *tc_B1, *tc_B2h, *tc_B2l;
-    ShWfs w[kMaxGuideStars];
+    int grid_cap;        // maximum CTAs (0 = the launcher's default)
+    int cta_warps;       // warps per CTA where the kernel allows a choice (0 = default)
+    int n_inst;
+    InstDyn dyn[kMaxInstances];
 };
 
 // ---------------------------------------------------------------- elongation tables
@@ -71,26 +91,47 @@ struct KtilArgs {
     double alt[kMaxNaSlices], w[kMaxNaSlices];
 };
 
+#ifdef __CUDACC__
+// The WFS of a launch that owns global subaperture g (binary search on subap_begin).
+__device__ __forceinline__ int find_wfs(const WfsDesc *w, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&w[mid].subap_begin) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+#endif
+
+// A launch as a graph kernel node: function, grid, block, dynamic shared memory.
+struct LaunchShape {
+    const void *func;
+    dim3 grid, block;
+    size_t smem;
+};
+
 // Launchers (return the cudaGetLastError() of the launch).
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s);
+cudaError_t project_launch_shape(int total_blocks, LaunchShape *out);
 // CTAs the projection needs for `pixels` pupil pixels of one WFS.
 int project_blocks(int pixels);
-cudaError_t launch_sh_fp32(const ShArgs &a, cudaStream_t s);
 cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
-// Compile-time specialised FP32 spot kernel for N = 32 geometries.
+cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
+                         uint32_t pixel0, float *C, cudaStream_t s);
+// Spot kernels: kind 0 = generic FP32 (any geometry), 1 = FP32 specialised for N = 32,
+// 2 = tensor core (BF16 x3) for N = 32.
+enum SpotKind { kSpotGeneric = 0, kSpotN32 = 1, kSpotTc = 2 };
 bool sh_n32_supported(int n, int N, int nd);
-cudaError_t launch_sh_n32(const ShArgs &a, cudaStream_t s);
-// Tensor-core (tcgen05, BF16 x3) spot kernel for N = 32 geometries with n <= 10.
 bool sh_tc_supported(int n, int N, int nd);
-cudaError_t launch_sh_tc(const ShArgs &a, cudaStream_t s);
+// Shape of the launch (sets the kernel's dynamic shared-memory attribute).
+cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out);
+cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s);
 // Swizzled BF16 operand tiles of the two constant matrices (F^T blocks, Ga blocks),
 // from FP64 tables laid out [q][m] (F) and [d][k] (Ga).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
                     const double *Ga_im64, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
                     std::vector<uint8_t> &B2l);
-cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
-                         uint32_t pixel0, float *C, cudaStream_t s);
-size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_per_cta);
 // Sets the calling thread's message returned by wfs_last_error(NULL).
 void set_thread_error(const char *msg);
 

@@ -28,18 +28,25 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
     __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
 
-    int w = 0;
-    while (w + 1 < a.n_wfs && (int)blockIdx.x >= a.w[w + 1].block_begin) ++w;
-    const ProjWfs &W = a.w[w];
-    const int S = a.S;
+    // the WFS owning this CTA: last entry whose first CTA is <= blockIdx.x
+    int lo = 0, hi = a.n_wfs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.wfs[mid].proj_block_begin <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const WfsDesc &W = a.wfs[lo];
+    const InstDesc &I = a.inst[W.inst];
+    const InstDyn &D = a.dyn[W.inst];
+    const int S = I.S;
 
-    if ((int)threadIdx.x < a.n_layers) {
+    if ((int)threadIdx.x < I.n_layers) {
         const int l = threadIdx.x;
-        const double h = a.alt[l];
+        const double h = I.alt[l];
         const double c = W.is_lgs ? 1.0 - h / W.range_m : 1.0;
-        const double inv_ds = 1.0 / a.ds;
-        const double ou = 0.5 * S + (W.theta_x * h - (a.x0[l] + a.vx[l] * a.t)) * inv_ds;
-        const double ov = 0.5 * S + (W.theta_y * h - (a.y0[l] + a.vy[l] * a.t)) * inv_ds;
+        const double inv_ds = 1.0 / I.ds;
+        const double ou = 0.5 * S + (W.theta_x * h - (I.x0[l] + I.vx[l] * D.t)) * inv_ds;
+        const double ov = 0.5 * S + (W.theta_y * h - (I.y0[l] + I.vy[l] * D.t)) * inv_ds;
         const double bu = floor(ou), bv = floor(ov);
         s_fu[l] = (float)(ou - bu);
         s_fv[l] = (float)(ov - bv);
@@ -56,7 +63,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     __syncthreads();
 
     const int n = W.n, nn = n * n, total = W.n_valid * nn;
-    const int pix0 = ((int)blockIdx.x - W.block_begin) * (kProjThreads * kProjPix) + threadIdx.x;
+    const int pix0 = ((int)blockIdx.x - W.proj_block_begin) * (kProjThreads * kProjPix) + threadIdx.x;
     const float half = 0.5f * (float)(W.n_sub * n - 1);
     float xr[kProjPix], yr[kProjPix], acc[kProjPix];
 #pragma unroll
@@ -70,10 +77,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
         acc[j] = 0.0f;
     }
     const bool pow2 = (S & (S - 1)) == 0;
-    for (int l = 0; l < a.n_layers; ++l) {
+    float *opd = D.opd + W.opd_off;
+    for (int l = 0; l < I.n_layers; ++l) {
         const float ch = s_c[l], cl = s_cl[l], fu = s_fu[l], fv = s_fv[l];
         const int bu = s_bu[l], bv = s_bv[l];
-        const float *scr = a.screens + (size_t)l * S * S;
+        const float *scr = D.screens + (size_t)l * S * S;
 #pragma unroll
         for (int j = 0; j < kProjPix; ++j) {
             // c * xr = ph + pl exactly (to FP32 rounding of the small part)
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
 #pragma unroll
     for (int j = 0; j < kProjPix; ++j) {
         const int pix = pix0 + j * kProjThreads;
-        if (pix < total) W.opd[pix] = acc[j];
+        if (pix < total) opd[pix] = acc[j];
     }
 }
 
@@ -121,6 +129,14 @@ cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) 
     if (total_blocks <= 0) return cudaSuccess;
     k_project<<<total_blocks, kProjThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t project_launch_shape(int total_blocks, LaunchShape *out) {
+    out->func = (const void *)k_project;
+    out->grid = dim3(total_blocks > 0 ? total_blocks : 1);
+    out->block = dim3(kProjThreads);
+    out->smem = 0;
+    return cudaSuccess;
 }
 
 }  // namespace gbwfs

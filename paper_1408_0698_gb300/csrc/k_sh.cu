@@ -117,20 +117,23 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
     r2 += r2 & 1;
     float *red = tb + ri + r1 + r2;
 
-    const uint32_t tlo = (uint32_t)__double_as_longlong(a.t);
-    const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(a.t) >> 32);
     const int nd2 = nd * nd;
     const float cd = 0.5f * (float)(nd - 1);
 
     for (int g = blockIdx.x * nteams + team; g < a.total; g += gridDim.x * nteams) {
-        int w = 0;
-        while (w + 1 < a.n_wfs && g >= a.w[w + 1].subap_begin) ++w;
-        const ShWfs &W = a.w[w];
+        const WfsDesc &W = a.wfs[find_wfs(a.wfs, a.n_wfs, g)];
+        const InstDyn &D = a.dyn[W.inst];
+        const uint64_t seed = a.inst[W.inst].seed;
+        const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
+        const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
         const int v = g - W.subap_begin;
+        float *st_I = D.st_I ? D.st_I + W.int_off : nullptr;
+        float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
+        float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
         team_sync<TEAM>(team);
 
         // field
-        const float *opd = W.opd + (size_t)v * nn;
+        const float *opd = D.opd + W.opd_off + (size_t)v * nn;
         const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
         const float ref = __ldg(opd);
         for (int i = tid; i < nn; i += TEAM) {
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
             for (int q = 0; q < n; ++q) acc = cmac(acc, U[k * n + q], sF[q * N + m]);
             const float in = fmaf(acc.x, acc.x, acc.y * acc.y);
             I[k * (N + 1) + m] = in;
-            if (W.st_I) W.st_I[(size_t)v * N * N + o] = in;
+            if (st_I) st_I[(size_t)v * N * N + o] = in;
         }
         team_sync<TEAM>(team);
 
@@ -234,11 +237,11 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
         for (int o = tid; o < nd2; o += TEAM) {
             const int iy = o / nd, ix = o - iy * nd;
             const float e = scale * B[o];
-            const float c = a.noise ? noise_pixel(e, W.read_noise, a.seed, (uint32_t)(v * nd2 + o),
+            const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
                                                   (uint32_t)W.gs_index, tlo, thi)
                                     : e;
-            if (W.st_E) W.st_E[(size_t)v * nd2 + o] = e;
-            if (W.st_C) W.st_C[(size_t)v * nd2 + o] = c;
+            if (st_E) st_E[(size_t)v * nd2 + o] = e;
+            if (st_C) st_C[(size_t)v * nd2 + o] = c;
             sc += c;
             sx = fmaf((float)ix - cd, c, sx);
             sy = fmaf((float)iy - cd, c, sy);
@@ -246,8 +249,9 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
         team_sum3<TEAM>(sc, sx, sy, red, tid, team);
         if (tid == 0) {
             const bool ok = sc > 0.0f;
-            W.slopes[2 * v] = ok ? sx / sc : 0.0f;
-            W.slopes[2 * v + 1] = ok ? sy / sc : 0.0f;
+            float *sl = D.slopes + W.slope_off;
+            sl[2 * v] = ok ? sx / sc : 0.0f;
+            sl[2 * v + 1] = ok ? sy / sc : 0.0f;
         }
     }
 }
@@ -264,23 +268,44 @@ size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_pe
     return consts + teams * per;
 }
 
-cudaError_t launch_sh_fp32(const ShArgs &a, cudaStream_t s) {
-    if (a.total <= 0) return cudaSuccess;
+namespace {
+cudaError_t generic_shape(const ShArgs &a, LaunchShape *out) {
     int team = 0, teams = 0;
     const size_t smem = sh_fp32_smem_bytes(a.n, a.N, a.nd, &team, &teams);
     int blocks = (a.total + teams - 1) / teams;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    cudaError_t e;
-    if (team == 32) {
-        e = cudaFuncSetAttribute(k_sh_fp32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sh_fp32<32><<<blocks, team * teams, smem, s>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(k_sh_fp32<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sh_fp32<512><<<blocks, team * teams, smem, s>>>(a);
+    const int cap = a.grid_cap > 0 ? a.grid_cap : 152 * 32;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    const void *f = team == 32 ? (const void *)k_sh_fp32<32> : (const void *)k_sh_fp32<512>;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    out->func = f;
+    out->grid = dim3(blocks);
+    out->block = dim3(team * teams);
+    out->smem = smem;
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t n32_launch_shape(const ShArgs &a, LaunchShape *out);
+cudaError_t tc_launch_shape(const ShArgs &a, LaunchShape *out);
+
+cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out) {
+    switch (kind) {
+        case kSpotGeneric: return generic_shape(a, out);
+        case kSpotN32: return n32_launch_shape(a, out);
+        case kSpotTc: return tc_launch_shape(a, out);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+}
+
+cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s) {
+    if (a.total <= 0) return cudaSuccess;
+    LaunchShape sh;
+    cudaError_t e = spot_launch_shape(kind, a, &sh);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
 }
 
 // ---------------------------------------------------------------------------

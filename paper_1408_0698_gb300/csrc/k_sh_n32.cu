@@ -79,20 +79,22 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float2 *Mw = sm2 + Lay::table + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
 
-    const uint32_t tlo = (uint32_t)__double_as_longlong(a.t);
-    const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(a.t) >> 32);
     const float cd = 0.5f * (float)(nd - 1);
     const int ix = lane & 15, half = lane >> 4;
 
     for (int g = blockIdx.x * nw + wib; g < a.total; g += gridDim.x * nw) {
-        int w = 0;
-        while (w + 1 < a.n_wfs && g >= a.w[w + 1].subap_begin) ++w;
-        const ShWfs &W = a.w[w];
+        const WfsDesc &W = a.wfs[find_wfs(a.wfs, a.n_wfs, g)];
+        const InstDyn &D = a.dyn[W.inst];
+        const uint64_t seed = a.inst[W.inst].seed;
+        const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
+        const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
         const int v = g - W.subap_begin;
+        float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
+        float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
         __syncwarp();
 
         // field, piston-free
-        const float *opd = W.opd + (size_t)v * (n * n);
+        const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
         const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
         const float ref = __ldg(opd);
         for (int i = lane; i < n * n; i += 32) {
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         float2 T[n];
 #pragma unroll
         for (int d = 0; d < n; ++d) T[d] = make_float2(0.0f, 0.0f);
-        float *stI = W.st_I ? W.st_I + (size_t)v * (N * N) + lane * N : nullptr;
+        float *stI = D.st_I ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
 #pragma unroll 2
         for (int m = 0; m < N; ++m) {
             float2 y = make_float2(0.0f, 0.0f);
@@ -237,11 +239,11 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             for (int j = 0; j < nd / 2; ++j) {
                 const int iy = half * (nd / 2) + j, o = iy * nd + ix;
                 const float e = scale * Bv[j];
-                const float c = a.noise ? noise_pixel(e, W.read_noise, a.seed, (uint32_t)(v * nd2 + o),
+                const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
                                                       (uint32_t)W.gs_index, tlo, thi)
                                         : e;
-                if (W.st_E) W.st_E[(size_t)v * nd2 + o] = e;
-                if (W.st_C) W.st_C[(size_t)v * nd2 + o] = c;
+                if (st_E) st_E[(size_t)v * nd2 + o] = e;
+                if (st_C) st_C[(size_t)v * nd2 + o] = c;
                 sc += c;
                 sx = fmaf((float)ix - cd, c, sx);
                 sy = fmaf((float)iy - cd, c, sy);
@@ -252,24 +254,30 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         sy = warp_sum(sy);
         if (lane == 0) {
             const bool ok = sc > 0.0f;
-            W.slopes[2 * v] = ok ? sx / sc : 0.0f;
-            W.slopes[2 * v + 1] = ok ? sy / sc : 0.0f;
+            float *sl = D.slopes + W.slope_off;
+            sl[2 * v] = ok ? sx / sc : 0.0f;
+            sl[2 * v + 1] = ok ? sy / sc : 0.0f;
         }
     }
 }
 
 namespace {
 template <int n, int nd>
-cudaError_t launch_n32(const ShArgs &a, cudaStream_t s) {
+cudaError_t shape_n32(const ShArgs &a, LaunchShape *out) {
     using Lay = N32Layout<n, nd>;
-    constexpr int warps = 8;
+    const int warps = (a.cta_warps == 4 || a.cta_warps == 8) ? a.cta_warps : 8;
     const size_t smem = (size_t)(Lay::table + warps * Lay::warp) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_sh_n32<n, nd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (a.total + warps - 1) / warps;
-    if (blocks > 152 * 2 * 8) blocks = 152 * 2 * 8;
-    k_sh_n32<n, nd><<<blocks, warps * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    const int cap = a.grid_cap > 0 ? a.grid_cap : 152 * 2 * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    out->func = (const void *)k_sh_n32<n, nd>;
+    out->grid = dim3(blocks);
+    out->block = dim3(warps * 32);
+    out->smem = smem;
+    return cudaSuccess;
 }
 }  // namespace
 
@@ -277,10 +285,9 @@ bool sh_n32_supported(int n, int N, int nd) {
     return N == 32 && ((n == 10 && nd == 16) || (n == 8 && nd == 16));
 }
 
-cudaError_t launch_sh_n32(const ShArgs &a, cudaStream_t s) {
-    if (a.total <= 0) return cudaSuccess;
-    if (a.n == 10 && a.nd == 16) return launch_n32<10, 16>(a, s);
-    if (a.n == 8 && a.nd == 16) return launch_n32<8, 16>(a, s);
+cudaError_t n32_launch_shape(const ShArgs &a, LaunchShape *out) {
+    if (a.n == 10 && a.nd == 16) return shape_n32<10, 16>(a, out);
+    if (a.n == 8 && a.nd == 16) return shape_n32<8, 16>(a, out);
     return cudaErrorInvalidValue;
 }
 

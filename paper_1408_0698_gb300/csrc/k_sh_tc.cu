@@ -213,8 +213,6 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
     float2 *Ta = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wTa;
     float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
-    const uint32_t tlo = (uint32_t)__double_as_longlong(a.t);
-    const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(a.t) >> 32);
     const float cd = 0.5f * (float)(nd - 1);
     const int ix = lane & 15, half = lane >> 4;
     const int row = wib * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
@@ -224,10 +222,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
     for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
         const int g = 4 * grp + wib;
         const bool active = g < a.total;
-        int w = 0;
-        if (active)
-            while (w + 1 < a.n_wfs && g >= a.w[w + 1].subap_begin) ++w;
-        const ShWfs &W = a.w[w];
+        const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
+        const InstDyn &D = a.dyn[W.inst];
         const int v = active ? g - W.subap_begin : 0;
 
         // field and U = F X (CUDA cores)
@@ -235,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
 #pragma unroll
         for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
         if (active) {
-            const float *opd = W.opd + (size_t)v * (n * n);
+            const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
             const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
             const float ref = __ldg(opd);
             for (int i = lane; i < n * n; i += 32) {
@@ -305,8 +301,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
                 I[m] = fmaf(yr, yr, yi * yi);
             }
         }
-        if (active && W.st_I) {
-            float *dst = W.st_I + (size_t)v * (N * N) + lane * N;
+        if (active && D.st_I) {
+            float *dst = D.st_I + W.int_off + (size_t)v * (N * N) + lane * N;
 #pragma unroll
             for (int m = 0; m < N; ++m) dst[m] = I[m];
         }
@@ -447,17 +443,22 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
         }
         sb = wsum(sb);
         const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
+        const uint64_t seed = a.inst[W.inst].seed;
+        const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
+        const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
+        float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
+        float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
         float sc = 0.0f, sx = 0.0f, sy = 0.0f;
         if (ix < nd) {
 #pragma unroll
             for (int j = 0; j < nd / 2; ++j) {
                 const int iy = half * (nd / 2) + j, o = iy * nd + ix;
                 const float e = scale * Bv[j];
-                const float c = a.noise ? noise_pixel(e, W.read_noise, a.seed, (uint32_t)(v * nd2 + o),
+                const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
                                                       (uint32_t)W.gs_index, tlo, thi)
                                         : e;
-                if (W.st_E) W.st_E[(size_t)v * nd2 + o] = e;
-                if (W.st_C) W.st_C[(size_t)v * nd2 + o] = c;
+                if (st_E) st_E[(size_t)v * nd2 + o] = e;
+                if (st_C) st_C[(size_t)v * nd2 + o] = c;
                 sc += c;
                 sx = fmaf((float)ix - cd, c, sx);
                 sy = fmaf((float)iy - cd, c, sy);
@@ -468,8 +469,9 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
         sy = wsum(sy);
         if (lane == 0) {
             const bool okc = sc > 0.0f;
-            W.slopes[2 * v] = okc ? sx / sc : 0.0f;
-            W.slopes[2 * v + 1] = okc ? sy / sc : 0.0f;
+            float *sl = D.slopes + W.slope_off;
+            sl[2 * v] = okc ? sx / sc : 0.0f;
+            sl[2 * v + 1] = okc ? sy / sc : 0.0f;
         }
     }
     fence_before_sync();
@@ -497,15 +499,21 @@ float bf16_float(uint16_t h) {
 }
 
 template <int n, int nd>
-cudaError_t launch_tc(const ShArgs &a, cudaStream_t s) {
+cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
     using Lay = TcLayout<n, nd>;
     const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
     cudaError_t e = cudaFuncSetAttribute(k_sh_tc<n, nd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int groups = (a.total + 3) / 4;
-    int blocks = groups < 152 * 3 ? groups : 152 * 3;
-    k_sh_tc<n, nd><<<blocks, kTcThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    // at most 3 CTAs per SM: their tensor memory (3 x 128 columns) always fits
+    const int cap = a.grid_cap > 0 && a.grid_cap < 152 * 3 ? a.grid_cap : 152 * 3;
+    int blocks = groups < cap ? groups : cap;
+    if (blocks < 1) blocks = 1;
+    out->func = (const void *)k_sh_tc<n, nd>;
+    out->grid = dim3(blocks);
+    out->block = dim3(kTcThreads);
+    out->smem = smem;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -552,10 +560,9 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
             }
 }
 
-cudaError_t launch_sh_tc(const ShArgs &a, cudaStream_t s) {
-    if (a.total <= 0) return cudaSuccess;
-    if (a.n == 10 && a.nd == 16) return launch_tc<10, 16>(a, s);
-    if (a.n == 8 && a.nd == 16) return launch_tc<8, 16>(a, s);
+cudaError_t tc_launch_shape(const ShArgs &a, LaunchShape *out) {
+    if (a.n == 10 && a.nd == 16) return shape_tc<10, 16>(a, out);
+    if (a.n == 8 && a.nd == 16) return shape_tc<8, 16>(a, out);
     return cudaErrorInvalidValue;
 }
 

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <string>
 
@@ -52,6 +53,10 @@ int32_t h_ids[kStaticMaxValid];
 float h_fill[kStaticMaxValid];
 uint32_t h_mask[kStaticMaxValid * kStaticMaskWords];
 float2 h_F[kMaxNPix * kMaxN], h_Ga[kMaxNPix * kMaxN], h_G[kMaxNPix * kMaxN];
+InstDesc h_inst;
+WfsDesc h_wfs;
+ProjArgs h_pa;
+ShArgs h_sa;
 wfs_status st_fail(wfs_status st, const char *msg) {
     set_thread_error(msg);
     return st;
@@ -172,6 +177,8 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     const size_t o_status = take(sizeof(int));
+    const size_t o_inst = take(sizeof(InstDesc));
+    const size_t o_wfs = take(sizeof(WfsDesc));
     const size_t o_ids = take((size_t)nv * sizeof(int32_t));
     const size_t o_fill = take((size_t)nv * sizeof(float));
     const size_t o_mask = take((size_t)nv * mw * sizeof(uint32_t));
@@ -223,65 +230,77 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
         if ((e = launch_ktil(ka, s)) != cudaSuccess) return st_fail(WFS_ECUDA, "wfs_measure_one_static: elongation table launch");
     }
 
-    ProjArgs pa;
-    memset(&pa, 0, sizeof pa);
-    pa.screens = screens;
-    pa.n_layers = L->n_layers;
-    pa.S = L->screen_size;
-    pa.ds = L->screen_dx_m;
-    pa.t = t_s;
+    // work tables of this one instance and wavefront sensor
+    memset(&h_inst, 0, sizeof h_inst);
+    h_inst.n_layers = L->n_layers;
+    h_inst.S = L->screen_size;
+    h_inst.ds = L->screen_dx_m;
     for (int l = 0; l < L->n_layers; ++l) {
-        pa.alt[l] = L->alt_m[l];
-        pa.vx[l] = L->wind_vx_mps[l];
-        pa.vy[l] = L->wind_vy_mps[l];
-        pa.x0[l] = L->x0_m[l];
-        pa.y0[l] = L->y0_m[l];
+        h_inst.alt[l] = L->alt_m[l];
+        h_inst.vx[l] = L->wind_vx_mps[l];
+        h_inst.vy[l] = L->wind_vy_mps[l];
+        h_inst.x0[l] = L->x0_m[l];
+        h_inst.y0[l] = L->y0_m[l];
     }
-    pa.n_wfs = 1;
-    ProjWfs &P = pa.w[0];
-    P.subap = d_ids;
-    P.opd = d_opd;
-    P.n = n;
-    P.n_sub = g.n_sub;
-    P.n_valid = nv;
-    P.is_lgs = gs->is_lgs;
-    P.range_m = gs->range_m;
-    P.theta_x = gs->theta_x_rad;
-    P.theta_y = gs->theta_y_rad;
-    P.pupil_dx_over_ds = dx / L->screen_dx_m;
-    P.block_begin = 0;
-    if ((e = launch_project(pa, project_blocks(nv * n * n), s)) != cudaSuccess)
+    h_inst.seed = seed;
+    memset(&h_wfs, 0, sizeof h_wfs);
+    h_wfs.inst = 0;
+    h_wfs.gs_index = (int)wfs_index;
+    h_wfs.n = n;
+    h_wfs.n_sub = g.n_sub;
+    h_wfs.n_valid = nv;
+    h_wfs.is_lgs = gs->is_lgs;
+    h_wfs.range_m = gs->range_m;
+    h_wfs.theta_x = gs->theta_x_rad;
+    h_wfs.theta_y = gs->theta_y_rad;
+    h_wfs.pupil_dx_over_ds = dx / L->screen_dx_m;
+    h_wfs.k_phase = (float)(2.0 * M_PI / gs->wavelength_m);
+    h_wfs.photons = (float)gs->photons_per_subap;
+    h_wfs.read_noise = (float)gs->read_noise_e;
+    h_wfs.subap = d_ids;
+    h_wfs.mask = (const uint32_t *)(base + o_mask);
+    h_wfs.fill = (const float *)(base + o_fill);
+    h_wfs.ktil = gs->is_lgs ? d_kt : nullptr;
+    h_wfs.proj_block_begin = 0;
+    h_wfs.subap_begin = 0;
+    if ((e = cudaMemcpyAsync(base + o_inst, &h_inst, sizeof h_inst, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(base + o_wfs, &h_wfs, sizeof h_wfs, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return st_fail(WFS_ECUDA, "wfs_measure_one_static: work table upload failed");
+    const InstDesc *d_inst = (const InstDesc *)(base + o_inst);
+    const WfsDesc *d_wfs = (const WfsDesc *)(base + o_wfs);
+    InstDyn dyn;
+    memset(&dyn, 0, sizeof dyn);
+    dyn.screens = screens;
+    dyn.opd = d_opd;
+    dyn.slopes = slopes_out;
+    dyn.t = t_s;
+    dyn.noise = noise_enable ? 1 : 0;
+
+    h_pa.inst = d_inst;
+    h_pa.wfs = d_wfs;
+    h_pa.n_wfs = 1;
+    h_pa.n_inst = 1;
+    h_pa.dyn[0] = dyn;
+    if ((e = launch_project(h_pa, project_blocks(nv * n * n), s)) != cudaSuccess)
         return st_fail(WFS_ECUDA, "wfs_measure_one_static: projection launch");
 
-    ShArgs sa;
-    memset(&sa, 0, sizeof sa);
-    sa.n = n;
-    sa.N = N;
-    sa.nd = nd;
-    sa.mask_words = mw;
-    sa.F = (const float2 *)(base + o_F);
-    sa.Ga = (const float2 *)(base + o_Ga);
-    sa.G = (const float2 *)(base + o_G);
-    sa.n_wfs = 1;
-    sa.total = nv;
-    sa.seed = seed;
-    sa.noise = noise_enable ? 1 : 0;
-    sa.t = t_s;
-    sa.status = (int *)(base + o_status);
-    ShWfs &W = sa.w[0];
-    W.opd = d_opd;
-    W.mask = (const uint32_t *)(base + o_mask);
-    W.fill = (const float *)(base + o_fill);
-    W.ktil = gs->is_lgs ? d_kt : nullptr;
-    W.slopes = slopes_out;
-    W.n_valid = nv;
-    W.is_lgs = gs->is_lgs;
-    W.gs_index = (int)wfs_index;
-    W.subap_begin = 0;
-    W.k_phase = (float)(2.0 * M_PI / gs->wavelength_m);
-    W.photons = (float)gs->photons_per_subap;
-    W.read_noise = (float)gs->read_noise_e;
-    if ((e = launch_sh_fp32(sa, s)) != cudaSuccess)
+    memset(&h_sa, 0, offsetof(ShArgs, dyn));
+    h_sa.n = n;
+    h_sa.N = N;
+    h_sa.nd = nd;
+    h_sa.mask_words = mw;
+    h_sa.F = (const float2 *)(base + o_F);
+    h_sa.Ga = (const float2 *)(base + o_Ga);
+    h_sa.G = (const float2 *)(base + o_G);
+    h_sa.inst = d_inst;
+    h_sa.wfs = d_wfs;
+    h_sa.n_wfs = 1;
+    h_sa.total = nv;
+    h_sa.status = (int *)(base + o_status);
+    h_sa.n_inst = 1;
+    h_sa.dyn[0] = dyn;
+    const int kind = sh_n32_supported(n, N, nd) ? kSpotN32 : kSpotGeneric;
+    if ((e = launch_spot(kind, h_sa, s)) != cudaSuccess)
         return st_fail(WFS_ECUDA, "wfs_measure_one_static: spot launch");
     return WFS_OK;
 }

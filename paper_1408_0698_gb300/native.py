@@ -67,6 +67,11 @@ class wfs_layout_info(C.Structure):
                 ("intensity_offset", C.c_size_t), ("det_offset", C.c_size_t)]
 
 
+class wfs_batch_class(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_pix_sub", C.c_int), ("n_fft", C.c_int), ("n_det", C.c_int),
+                ("n_wfs", C.c_int), ("n_subaps", C.c_int), ("grid_cap", C.c_int), ("cta_warps", C.c_int)]
+
+
 class wfs_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int), ("total_ms", C.c_double)]
 
@@ -98,6 +103,9 @@ _SIGS = {
     "wfs_batch_measure": (C.c_int, [_H, C.POINTER(C.c_void_p), C.POINTER(C.c_double),
                                     C.POINTER(C.c_void_p), C.c_void_p]),
     "wfs_batch_destroy": (C.c_int, [_H]),
+    "wfs_batch_tune": (C.c_int, [_H, C.POINTER(C.c_void_p), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_void_p), C.c_void_p]),
+    "wfs_batch_info": (C.c_int, [_H, C.c_int, C.POINTER(wfs_batch_class), C.POINTER(C.c_int)]),
     "wfs_version": (C.c_char_p, []),
     "wfs_timing_enable": (C.c_int, [_H, C.c_int]),
     "wfs_measure_one_static": (C.c_int, [C.POINTER(wfs_telescope), C.POINTER(wfs_geometry),
@@ -254,6 +262,21 @@ def wfs_batch_measure(b, screens_ptrs, ts, slopes_ptrs, stream=0):
     tt = (C.c_double * n)(*[float(t) for t in ts])
     op = (C.c_void_p * n)(*slopes_ptrs)
     _check(lib().wfs_batch_measure(b, sp, tt, op, stream))
+
+
+def wfs_batch_tune(b, screens_ptrs, ts, slopes_ptrs, stream=0):
+    n = len(ts)
+    sp = (C.c_void_p * n)(*screens_ptrs)
+    tt = (C.c_double * n)(*[float(t) for t in ts])
+    op = (C.c_void_p * n)(*slopes_ptrs)
+    _check(lib().wfs_batch_tune(b, sp, tt, op, stream))
+
+
+def wfs_batch_info(b):
+    arr = (wfs_batch_class * 64)()
+    n = C.c_int()
+    _check(lib().wfs_batch_info(b, 64, arr, C.byref(n)))
+    return [dict((f, getattr(arr[i], f)) for f, _ in wfs_batch_class._fields_) for i in range(min(n.value, 64))]
 
 
 def wfs_batch_destroy(b):

@@ -1,0 +1,122 @@
+"""Uneven batches (config-4 style): one projection launch plus one persistent spot launch per
+kernel class, replayed as a CUDA graph, must give the same slopes as measuring every handle
+alone -- bit for bit, with and without the graph, before and after autotuning."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1408_0698_gb300 import inputs, native
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _instances(k, seed=4000, prec=inputs.PREC_FP32):
+    insts = inputs.config4_instances(k, seed, precision=prec)
+    out = []
+    for c in insts:
+        g = c.geometries[0]
+        if prec == inputs.PREC_BF16X3 and not (g.n_fft == 32 and g.n_pix_sub in (8, 10) and g.n_det == 16):
+            g.precision = inputs.PREC_FP32
+        out.append(c)
+    return out
+
+
+def _setup(insts, noise):
+    dev = torch.device("cuda:0")
+    hs, scr, outs = [], [], []
+    for i, c in enumerate(insts):
+        w = native.Wfs(c, seed=c.seed, noise=noise)
+        hs.append(w)
+        scr.append(torch.as_tensor(inputs.make_screens(c.layers, c.seed)).to(dev))
+        outs.append(torch.zeros((max(w.total, 1), 2), device=dev))
+    return hs, scr, outs
+
+
+def _alone(hs, scr, ts):
+    res = []
+    for w, s, t in zip(hs, scr, ts):
+        o = torch.zeros((max(w.total, 1), 2), device="cuda:0")
+        native.wfs_measure(w.h, s.data_ptr(), t, o.data_ptr(), 0)
+        res.append(o)
+    torch.cuda.synchronize()
+    return [r.cpu().numpy() for r in res]
+
+
+@pytest.mark.parametrize("prec,noise", [(inputs.PREC_FP32, True), (inputs.PREC_BF16X3, False)])
+def test_uneven_batch_equals_alone(prec, noise):
+    insts = _instances(24, 4000, prec)
+    hs, scr, outs = _setup(insts, noise)
+    b = native.wfs_batch_create([w.h for w in hs])
+    info = native.wfs_batch_info(b)
+    assert sum(c["n_wfs"] for c in info) == len(hs)
+    assert {c["n_fft"] for c in info} >= {16, 24, 32, 64}
+    for step in range(3):                       # graph build, then two replays
+        ts = [0.003 * step + 1e-4 * i for i in range(len(hs))]
+        native.wfs_batch_measure(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+        torch.cuda.synchronize()
+        ref = _alone(hs, scr, ts)
+        for i, (o, r) in enumerate(zip(outs, ref)):
+            assert np.array_equal(o.cpu().numpy(), r), f"instance {i} step {step}"
+    # tuning changes launch shapes only, never results
+    ts = [0.05 + 1e-4 * i for i in range(len(hs))]
+    native.wfs_batch_tune(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+    info2 = native.wfs_batch_info(b)
+    assert all(c["grid_cap"] > 0 for c in info2)
+    native.wfs_batch_measure(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+    torch.cuda.synchronize()
+    ref = _alone(hs, scr, ts)
+    for o, r in zip(outs, ref):
+        assert np.array_equal(o.cpu().numpy(), r)
+    native.wfs_batch_destroy(b)
+    for w in hs:
+        w.close()
+
+
+def test_batch_direct_launch_matches_graph(monkeypatch):
+    insts = _instances(10, 4100)
+    hs, scr, outs = _setup(insts, True)
+    ts = [0.01 * i for i in range(len(hs))]
+    b = native.wfs_batch_create([w.h for w in hs])
+    native.wfs_batch_measure(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+    torch.cuda.synchronize()
+    g = [o.cpu().numpy() for o in outs]
+    native.wfs_batch_destroy(b)
+    monkeypatch.setenv("GBWFS_BATCH_GRAPH", "0")
+    b = native.wfs_batch_create([w.h for w in hs])
+    for o in outs:
+        o.zero_()
+    native.wfs_batch_measure(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+    torch.cuda.synchronize()
+    for o, r in zip(outs, g):
+        assert np.array_equal(o.cpu().numpy(), r)
+    native.wfs_batch_destroy(b)
+    for w in hs:
+        w.close()
+
+
+def test_tune_cache_round_trip(tmp_path, monkeypatch):
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("GBWFS_TUNE_CACHE", str(path))
+    insts = _instances(6, 4200)
+    hs, scr, outs = _setup(insts, False)
+    ts = [0.0] * len(hs)
+    b = native.wfs_batch_create([w.h for w in hs])
+    native.wfs_batch_tune(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+    tuned = [(c["grid_cap"], c["cta_warps"]) for c in native.wfs_batch_info(b)]
+    native.wfs_batch_destroy(b)
+    assert path.exists() and len(path.read_text().splitlines()) == len(tuned)
+    b = native.wfs_batch_create([w.h for w in hs])
+    assert [(c["grid_cap"], c["cta_warps"]) for c in native.wfs_batch_info(b)] == tuned
+    native.wfs_batch_destroy(b)
+    for w in hs:
+        w.close()
+
+
+def test_batch_rejects_bad_arguments():
+    c = inputs.config1()
+    w = native.Wfs(c)
+    with pytest.raises(native.WfsError):
+        native.wfs_batch_create([w.h, w.h])
+    w.close()
