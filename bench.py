@@ -166,6 +166,23 @@ def cpu_baseline(cfg, scr, t, target_s=12.0):
                       f"+ all 12 NGS subapertures), FP64, {dt:.1f} s"}
 
 
+def served(load=0.8, duration_s=4.0, n_runs=32, budget_gb=150.0, slots=3):
+    """Continuous-batching serving of frame requests from n_runs concurrent MC runs drawn from
+    configs 1-3, device-resident (admitted by HBM footprint), Poisson arrivals at `load` times
+    the measured batched capacity; p50/p99 latency and served throughput."""
+    from paper_1408_0698_gb300 import serving
+    runs = serving.make_runs(n_runs, 5000)
+    budget = int(budget_gb * (1 << 30))
+    cap = serving.capacity(runs, budget, slots)
+    arrivals = serving.poisson_arrivals(runs, load * cap / n_runs, duration_s, seed=11)
+    srv = serving.Server(runs, budget, slots)
+    srv.preadmit()
+    st = srv.serve(arrivals).summary()
+    st.update({"load": load, "capacity_frames_per_s": cap, "runs": n_runs, "budget_gb": budget_gb,
+               "slots": slots, "mix": "configs 1-3 (seeded)"})
+    return st
+
+
 def reference_arm(args):
     """The oracle on the host cores, on bounded samples of the ELT frame (one per step)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -218,6 +235,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-traffic measurement")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (0: none, for profiling runs)")
     args = ap.parse_args()
@@ -362,6 +380,8 @@ def main():
             "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in ktimes.items()},
             "gpu_launches": int(sum(v[0] for v in ktimes.values())),
             "roofline": roof, "e2e": e2e, "clocks": clk, "wall_s_timed": wall}
+    if not args.no_served:
+        line["served"] = served()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, scr, 0.0)
     if rank == 0:

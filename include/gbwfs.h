@@ -249,6 +249,20 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out);
 wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const double *t_s,
                              float *const *slopes_out, void *stream);
 /*
+ * wfs_batch_measure_subset -- continuous batching: measure only the n_active
+ * instances listed in `active` (indices into the batch, each at most once), with
+ * screens, t_s and slopes_out given per listed instance (arrays of n_active).  The
+ * compacted work table is staged in pinned host memory of slot `slot`
+ * (0 <= slot < 8) and copied on `stream`; calls using one slot must be issued on
+ * one stream (they reuse its device table), and an instance must not be in two
+ * calls whose GPU work overlaps (it owns one OPD scratch).  Launches directly
+ * (no graph): one projection and one spot launch per kernel class present.
+ * Results equal those of wfs_measure on each listed handle.
+ */
+wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const int *active,
+                                    const float *const *screens, const double *t_s,
+                                    float *const *slopes_out, void *stream);
+/*
  * Autotuner: times the candidate launch shapes of every kernel class on these inputs
  * (persistent grid size; warps per CTA for the FP32 32-point kernel), keeps the
  * fastest for later calls, and appends it to the file named by the environment

@@ -106,6 +106,8 @@ struct wfs_ctx {
 // A batch: the instances' work tables merged, WFS entries grouped by kernel class
 // (kind, n, N, nd) across instances, replayed as one CUDA graph (projection node, then one
 // spot node per class in parallel) whose kernel parameters are rewritten per call.
+constexpr int kBatchSlots = 8;  // concurrent subset calls per batch (one per stream)
+
 struct BatchClass {
     int kind = 0;
     const GeomDev *geom = nullptr;   // geometry tables (those of the first handle in the class)
@@ -129,6 +131,13 @@ struct wfs_batch_ctx {
     cudaGraphNode_t proj_node = nullptr;
     std::vector<cudaGraphNode_t> spot_nodes;  // per class (null when the class is empty)
     int use_graph = 1;
+    // subset calls: per slot, a pinned staging table, its device copy and a copy-done event
+    struct Slot {
+        WfsDesc *h = nullptr;
+        WfsDesc *d = nullptr;
+        cudaEvent_t copied = nullptr;
+    };
+    std::vector<Slot> slots;
 };
 
 namespace {
@@ -833,6 +842,11 @@ wfs_status wfs_noise_apply(const float *expected, int n, float read_noise_e, uin
 namespace {
 
 void batch_free(wfs_batch b) {
+    for (auto &sl : b->slots) {
+        if (sl.copied) cudaEventDestroy(sl.copied);
+        cudaFreeHost(sl.h);
+        cudaFree(sl.d);
+    }
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_inst);
@@ -1106,6 +1120,99 @@ wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const dou
         return cuda_fail(nullptr, e, "batch graph update");
     }
     if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch graph launch");
+    return WFS_OK;
+}
+
+wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const int *active,
+                                    const float *const *screens, const double *t_s, float *const *slopes_out,
+                                    void *stream) {
+    if (!b || (n_active > 0 && (!active || !screens || !t_s || !slopes_out)) || n_active < 0)
+        return fail(nullptr, WFS_EINVAL, "bad batch subset arguments");
+    if (slot < 0 || slot >= kBatchSlots) return fail(nullptr, WFS_EINVAL, "batch subset slot out of range");
+    const int n = (int)b->hs.size();
+    if (n_active > n) return fail(nullptr, WFS_EINVAL, "more active instances than the batch holds");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(nullptr, WFS_EINVAL, "current device differs from the batch's device");
+    std::vector<int> pos(n, -1);
+    for (int j = 0; j < n_active; ++j) {
+        const int i = active[j];
+        if (i < 0 || i >= n || pos[i] >= 0) return fail(nullptr, WFS_EINVAL, "active instance out of range or repeated");
+        if (!screens[j] || !slopes_out[j] || !is_finite(t_s[j]))
+            return fail(nullptr, WFS_EINVAL, "batch subset: null buffer or non-finite time");
+        pos[i] = j;
+    }
+    if (n_active == 0) return WFS_OK;
+    cudaError_t e;
+    if (b->slots.empty()) {
+        b->slots.resize(kBatchSlots);
+        const size_t cap = b->wfs_host.size() ? b->wfs_host.size() : 1;
+        for (auto &sl : b->slots)
+            if ((e = cudaMallocHost(&sl.h, cap * sizeof(WfsDesc))) != cudaSuccess ||
+                (e = cudaMalloc(&sl.d, cap * sizeof(WfsDesc))) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(nullptr, e, "batch subset slot allocation");
+    }
+    auto &sl = b->slots[slot];
+    // the previous upload from this slot's staging table must have been consumed
+    if ((e = cudaEventSynchronize(sl.copied)) != cudaSuccess) return cuda_fail(nullptr, e, "slot wait");
+    static thread_local ProjArgs pa;
+    static thread_local ShArgs sa;
+    memset(pa.dyn, 0, sizeof(InstDyn) * n);
+    for (int i = 0; i < n; ++i)
+        if (pos[i] >= 0) {
+            InstDyn &d = pa.dyn[i];
+            d.screens = screens[pos[i]];
+            d.opd = b->hs[i]->d_opd;
+            d.slopes = slopes_out[pos[i]];
+            d.t = t_s[pos[i]];
+            d.noise = b->hs[i]->noise;
+        }
+    int count = 0, blocks = 0;
+    std::vector<int> cls_first(b->classes.size()), cls_count(b->classes.size()), cls_total(b->classes.size());
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        const BatchClass &bc = b->classes[c];
+        cls_first[c] = count;
+        cls_total[c] = 0;
+        for (int k = 0; k < bc.count; ++k) {
+            const WfsDesc &src = b->wfs_host[bc.first + k];
+            if (pos[src.inst] < 0) continue;
+            WfsDesc d = src;
+            d.subap_begin = cls_total[c];
+            cls_total[c] += d.n_valid;
+            d.proj_block_begin = blocks;
+            blocks += project_blocks(d.n_valid * d.n * d.n);
+            sl.h[count++] = d;
+        }
+        cls_count[c] = count - cls_first[c];
+    }
+    if ((e = cudaMemcpyAsync(sl.d, sl.h, (size_t)count * sizeof(WfsDesc), cudaMemcpyHostToDevice,
+                             (cudaStream_t)stream)) != cudaSuccess ||
+        (e = cudaEventRecord(sl.copied, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "batch subset table upload");
+    pa.inst = b->d_inst;
+    pa.wfs = sl.d;
+    pa.n_wfs = count;
+    pa.n_inst = n;
+    if (blocks > 0 && (e = launch_project(pa, blocks, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "batch subset projection");
+    for (size_t c = 0; c < b->classes.size(); ++c) {
+        if (!cls_count[c] || !cls_total[c]) continue;
+        const BatchClass &bc = b->classes[c];
+        memset(&sa, 0, offsetof(ShArgs, dyn));
+        fill_geom_args(sa, *bc.geom);
+        sa.inst = b->d_inst;
+        sa.wfs = sl.d + cls_first[c];
+        sa.n_wfs = cls_count[c];
+        sa.total = cls_total[c];
+        sa.status = b->hs[0]->d_status;
+        sa.grid_cap = bc.grid_cap;
+        sa.cta_warps = bc.cta_warps;
+        sa.n_inst = n;
+        memcpy(sa.dyn, pa.dyn, sizeof(InstDyn) * n);
+        if ((e = launch_spot(bc.kind, sa, (cudaStream_t)stream)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "batch subset spot launch");
+    }
     return WFS_OK;
 }
 

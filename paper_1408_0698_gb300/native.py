@@ -105,6 +105,8 @@ _SIGS = {
     "wfs_batch_destroy": (C.c_int, [_H]),
     "wfs_batch_tune": (C.c_int, [_H, C.POINTER(C.c_void_p), C.POINTER(C.c_double),
                                  C.POINTER(C.c_void_p), C.c_void_p]),
+    "wfs_batch_measure_subset": (C.c_int, [_H, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_void_p), C.c_void_p]),
     "wfs_batch_info": (C.c_int, [_H, C.c_int, C.POINTER(wfs_batch_class), C.POINTER(C.c_int)]),
     "wfs_version": (C.c_char_p, []),
     "wfs_timing_enable": (C.c_int, [_H, C.c_int]),
@@ -262,6 +264,15 @@ def wfs_batch_measure(b, screens_ptrs, ts, slopes_ptrs, stream=0):
     tt = (C.c_double * n)(*[float(t) for t in ts])
     op = (C.c_void_p * n)(*slopes_ptrs)
     _check(lib().wfs_batch_measure(b, sp, tt, op, stream))
+
+
+def wfs_batch_measure_subset(b, slot, active, screens_ptrs, ts, slopes_ptrs, stream=0):
+    n = len(active)
+    act = (C.c_int * max(n, 1))(*[int(i) for i in active])
+    sp = (C.c_void_p * max(n, 1))(*screens_ptrs)
+    tt = (C.c_double * max(n, 1))(*[float(t) for t in ts])
+    op = (C.c_void_p * max(n, 1))(*slopes_ptrs)
+    _check(lib().wfs_batch_measure_subset(b, int(slot), n, act, sp, tt, op, stream))
 
 
 def wfs_batch_tune(b, screens_ptrs, ts, slopes_ptrs, stream=0):
