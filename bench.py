@@ -166,6 +166,18 @@ def cpu_baseline(cfg, scr, t, target_s=12.0):
                       f"+ all 12 NGS subapertures), FP64, {dt:.1f} s"}
 
 
+def replica_throughput(local_ms, spots_per_step, steps, world, dev):
+    """Whole-job throughput of `world` replicas: every rank measured `steps` steps of its own
+    run in local_ms; the job's time is the slowest rank's (all-reduce MAX)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return world * spots_per_step * steps / (ms_max / 1e3), world * steps / (ms_max / 1e3), ms_max
+
+
 def served(load=0.8, duration_s=4.0, n_runs=32, budget_gb=150.0, slots=3):
     """Continuous-batching serving of frame requests from n_runs concurrent MC runs drawn from
     configs 1-3, device-resident (admitted by HBM footprint), Poisson arrivals at `load` times
@@ -300,12 +312,7 @@ def main():
     ktimes = native.wfs_timing_read(w.h)
     native.wfs_sync_status(w.h)
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * spots * args.steps / (ms_max / 1e3)
-    frames = world * args.steps / (ms_max / 1e3)
+    value, frames, ms_max = replica_throughput(ms, spots, args.steps, world, dev)
 
     # e2e: host buffers through wfs_measure_host, copies inside the timed region
     host_scr = torch.as_tensor(scr).pin_memory()

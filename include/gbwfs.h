@@ -333,6 +333,15 @@ wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs_geometry *
                                   uint32_t wfs_index, int noise_enable, float *slopes_out,
                                   int slopes_capacity, int *n_valid_out, void *stream);
 
+/*
+ * wfs_check_bounded_wait -- failure-detection check: launches one CTA that waits on an
+ * mbarrier nothing arrives on, for at most `polls` polls (the same bounded wait the
+ * tensor-core spot kernel uses for its MMA completions), and records WFS_ETIMEOUT in the
+ * handle's device status word, which the next wfs_sync_status returns.  The GPU is never
+ * faulted or hung.  The paper has no counterpart (it is a property of this library).
+ */
+wfs_status wfs_check_bounded_wait(wfs_handle h, int polls, void *stream);
+
 /* Library version string. */
 const char *wfs_version(void);
 

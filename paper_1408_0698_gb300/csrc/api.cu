@@ -641,7 +641,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 d.int_off = (long long)s.int_off;
                 d.det_off = (long long)s.det_off;
                 d.proj_block_begin = blocks;
-                blocks += project_blocks(s.n_valid * g.n_pix_sub * g.n_pix_sub);
+                blocks += project_blocks(s.n_valid, g.n_pix_sub);
                 d.subap_begin = G.total;
                 G.total += s.n_valid;
                 h->wfs_host.push_back(d);
@@ -825,6 +825,15 @@ wfs_status wfs_sync_status(wfs_handle h) {
         cudaMemset(h->d_status, 0, sizeof(int));
         return fail(h, (wfs_status)v, "device reported status " + std::to_string(v));
     }
+    return WFS_OK;
+}
+
+wfs_status wfs_check_bounded_wait(wfs_handle h, int polls, void *stream) {
+    if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
+    if (polls < 1 || polls > (1 << 24)) return fail(h, WFS_EINVAL, "polls must be in [1, 2^24]");
+    h->last_stream = (cudaStream_t)stream;
+    cudaError_t e = launch_wait_check(h->d_status, polls, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "wait check launch");
     return WFS_OK;
 }
 
@@ -1055,7 +1064,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
             d.subap_begin = bc.total;
             bc.total += d.n_valid;
             d.proj_block_begin = blocks;
-            blocks += project_blocks(d.n_valid * d.n * d.n);
+            blocks += project_blocks(d.n_valid, d.n);
             b->wfs_host.push_back(d);
             ++bc.count;
         }
@@ -1181,7 +1190,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
             d.subap_begin = cls_total[c];
             cls_total[c] += d.n_valid;
             d.proj_block_begin = blocks;
-            blocks += project_blocks(d.n_valid * d.n * d.n);
+            blocks += project_blocks(d.n_valid, d.n);
             sl.h[count++] = d;
         }
         cls_count[c] = count - cls_first[c];
@@ -1235,7 +1244,7 @@ wfs_status wfs_batch_tune(wfs_batch b, const float *const *screens, const double
             for (int w : {4, 8})
                 for (int m : {2, 4, 8, 16}) cand.push_back({152 * m * (8 / w), w});
         } else if (bc.kind == kSpotTc) {
-            for (int m : {1, 2, 3}) cand.push_back({152 * m, 0});
+            for (int m : {1, 2}) cand.push_back({152 * m, 0});
         } else {
             for (int m : {2, 4, 8, 32}) cand.push_back({152 * m, 0});
         }

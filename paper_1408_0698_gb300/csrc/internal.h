@@ -114,8 +114,8 @@ struct LaunchShape {
 // Launchers (return the cudaGetLastError() of the launch).
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s);
 cudaError_t project_launch_shape(int total_blocks, LaunchShape *out);
-// CTAs the projection needs for `pixels` pupil pixels of one WFS.
-int project_blocks(int pixels);
+// CTAs the projection needs for one WFS (n_valid subapertures of n x n pixels).
+int project_blocks(int n_valid, int n);
 cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
 cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
                          uint32_t pixel0, float *C, cudaStream_t s);
@@ -132,6 +132,8 @@ cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s);
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
                     const double *Ga_im64, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
                     std::vector<uint8_t> &B2l);
+// Bounded mbarrier wait that is never satisfied; writes WFS_ETIMEOUT to *status.
+cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
 // Sets the calling thread's message returned by wfs_last_error(NULL).
 void set_thread_error(const char *msg);
 

@@ -22,7 +22,6 @@
 namespace gbwfs {
 
 constexpr int kProjThreads = 256;
-constexpr int kProjPix = 4;  // pixels per thread (strided by the block size: coalesced)
 
 __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
@@ -62,37 +61,45 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     }
     __syncthreads();
 
-    const int n = W.n, nn = n * n, total = W.n_valid * nn;
-    const int pix0 = ((int)blockIdx.x - W.proj_block_begin) * (kProjThreads * kProjPix) + threadIdx.x;
+    // each thread: one 2x2 block of pupil pixels (rows p, p+1; columns q, q+1) of one subaperture
+    const int n = W.n, nn = n * n, nb = (n + 1) >> 1, nbb = nb * nb;
+    const int blk = ((int)blockIdx.x - W.proj_block_begin) * kProjThreads + threadIdx.x;
+    if (blk >= W.n_valid * nbb) return;
+    const int v = blk / nbb, r = blk - v * nbb, bp = r / nb, bq = r - bp * nb;
+    const int p0 = 2 * bp, q0 = 2 * bq;
+    const int id = __ldg(W.subap + v);
+    const int sy = id / W.n_sub, sx = id - sy * W.n_sub;
     const float half = 0.5f * (float)(W.n_sub * n - 1);
-    float xr[kProjPix], yr[kProjPix], acc[kProjPix];
+    float xr[2], yr[2];
 #pragma unroll
-    for (int j = 0; j < kProjPix; ++j) {
-        const int pix = min(pix0 + j * kProjThreads, total - 1);
-        const int v = pix / nn, r = pix - v * nn, p = r / n, q = r - p * n;
-        const int id = __ldg(W.subap + v);
-        const int sy = id / W.n_sub, sx = id - sy * W.n_sub;
-        xr[j] = (float)(sx * n + q) - half;  // exact half-integers
-        yr[j] = (float)(sy * n + p) - half;
-        acc[j] = 0.0f;
+    for (int j = 0; j < 2; ++j) {
+        xr[j] = (float)(sx * n + q0 + j) - half;  // exact half-integers
+        yr[j] = (float)(sy * n + p0 + j) - half;
     }
+    float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     const bool pow2 = (S & (S - 1)) == 0;
-    float *opd = D.opd + W.opd_off;
     for (int l = 0; l < I.n_layers; ++l) {
-        const float ch = s_c[l], cl = s_cl[l], fu = s_fu[l], fv = s_fv[l];
-        const int bu = s_bu[l], bv = s_bv[l];
+        const float ch = s_c[l], cl = s_cl[l];
         const float *scr = D.screens + (size_t)l * S * S;
+        int ci0[2], ci1[2];
+        float fx[2];
+        const float *row0[2], *row1[2];
+        float gy[2];
 #pragma unroll
-        for (int j = 0; j < kProjPix; ++j) {
-            // c * xr = ph + pl exactly (to FP32 rounding of the small part)
+        for (int j = 0; j < 2; ++j) {
+            // c * x = ph + pl exactly (to FP32 rounding of the small part)
             const float ph = __fmul_rn(ch, xr[j]), pl = fmaf(ch, xr[j], -ph) + cl * xr[j];
+            const float ih = floorf(ph);
+            const float ru = ((ph - ih) + pl) + s_fu[l];  // in [-eps, 2)
+            const float iu = floorf(ru);
+            fx[j] = ru - iu;
+            int i0 = s_bu[l] + (int)ih + (int)iu;
             const float qh = __fmul_rn(ch, yr[j]), ql = fmaf(ch, yr[j], -qh) + cl * yr[j];
-            const float ih = floorf(ph), jh = floorf(qh);
-            const float ru = ((ph - ih) + pl) + fu;  // in [-eps, 2)
-            const float rv = ((qh - jh) + ql) + fv;
-            const float iu = floorf(ru), jv = floorf(rv);
-            const float f = ru - iu, g = rv - jv;
-            int i0 = bu + (int)ih + (int)iu, j0 = bv + (int)jh + (int)jv;
+            const float jh = floorf(qh);
+            const float rv = ((qh - jh) + ql) + s_fv[l];
+            const float jv = floorf(rv);
+            gy[j] = rv - jv;
+            int j0 = s_bv[l] + (int)jh + (int)jv;
             int i1, j1;
             if (pow2) {
                 i0 &= S - 1;
@@ -108,22 +115,34 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
                 i1 = (i0 + 1 == S) ? 0 : i0 + 1;
                 j1 = (j0 + 1 == S) ? 0 : j0 + 1;
             }
-            const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
-            const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
-            const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
-            const float top = fmaf(f, s01 - s00, s00);
-            const float bot = fmaf(f, s11 - s10, s10);
-            acc[j] += fmaf(g, bot - top, top);
+            ci0[j] = i0;
+            ci1[j] = i1;
+            row0[j] = scr + (size_t)j0 * S;
+            row1[j] = scr + (size_t)j1 * S;
         }
-    }
 #pragma unroll
-    for (int j = 0; j < kProjPix; ++j) {
-        const int pix = pix0 + j * kProjThreads;
-        if (pix < total) opd[pix] = acc[j];
+        for (int a2 = 0; a2 < 2; ++a2)      // row of the block
+#pragma unroll
+            for (int b2 = 0; b2 < 2; ++b2) {  // column of the block
+                const float s00 = __ldg(row0[a2] + ci0[b2]), s01 = __ldg(row0[a2] + ci1[b2]);
+                const float s10 = __ldg(row1[a2] + ci0[b2]), s11 = __ldg(row1[a2] + ci1[b2]);
+                const float top = fmaf(fx[b2], s01 - s00, s00);
+                const float bot = fmaf(fx[b2], s11 - s10, s10);
+                acc[a2][b2] += fmaf(gy[a2], bot - top, top);
+            }
     }
+    float *opd = D.opd + W.opd_off + (size_t)v * nn;
+#pragma unroll
+    for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+        for (int b2 = 0; b2 < 2; ++b2)
+            if (p0 + a2 < n && q0 + b2 < n) opd[(p0 + a2) * n + q0 + b2] = acc[a2][b2];
 }
 
-int project_blocks(int pixels) { return (pixels + kProjThreads * kProjPix - 1) / (kProjThreads * kProjPix); }
+int project_blocks(int n_valid, int n) {
+    const int nb = (n + 1) / 2;
+    return (n_valid * nb * nb + kProjThreads - 1) / kProjThreads;
+}
 
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) {
     if (total_blocks <= 0) return cudaSuccess;

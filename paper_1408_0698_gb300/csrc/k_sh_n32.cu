@@ -14,6 +14,7 @@
 // compile-time constants.
 #include "internal.h"
 #include "noise.cuh"
+#include "spot_tail.cuh"
 
 namespace gbwfs {
 
@@ -37,8 +38,8 @@ struct N32Layout {
     static constexpr int oFk = 0;                 // [p][k]   F[k][p]      (lane-k column)
     static constexpr int oFm = oFk + n * N;        // [m][q]   F[m][q]      (broadcast rows)
     static constexpr int oGam = oFm + N * n;       // [m][dx]  Ga[dx][m]    (broadcast rows)
-    static constexpr int oGak = oGam + N * n;      // [d][GAK] Ga[d][k]     (padded rows)
-    static constexpr int oG = oGak + n * GAK;      // [d][nd]  G[d][i]
+    static constexpr int oGak = oGam + N * n;      // [dyi][GAK] Ga(dy, k), conjugated for dy < 0
+    static constexpr int oG = oGak + (2 * n - 1) * GAK;  // [d][nd]  G[d][i]
     static constexpr int table = oG + n * nd;
     // per-warp scratch (float2 units)
     static constexpr int wX = 0;                   // [p][q]
@@ -68,7 +69,8 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         const int d = q, k = m;     // Ga has the same [d][k] shape
         const float2 g = a.Ga[i];
         Gam[k * n + d] = g;
-        Gak[d * GAK + k] = g;
+        Gak[(d + n - 1) * GAK + k] = g;                          // dy = +d
+        if (d > 0) Gak[(n - 1 - d) * GAK + k] = make_float2(g.x, -g.y);  // dy = -d
     }
     for (int i = threadIdx.x; i < n * nd; i += blockDim.x) Gt[i] = a.G[i];
     __syncthreads();
@@ -145,119 +147,12 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 #pragma unroll
             for (int d = 0; d < n; ++d) Ta[lane * NO + d] = T[d];
             __syncwarp();
-            // M = Kt * (Ga_y Ta): 2x2 tiles over (dy pair, dx pair)
-            const float2 *kt = W.ktil + (size_t)v * (D2 * n);
-            constexpr int DYP = (D2 + 1) / 2, DXP = (n + 1) / 2, TASKS = DYP * DXP;
-            for (int task = lane; task < TASKS; task += 32) {
-                const int dyp = task / DXP, dxp = task - dyp * DXP;
-                const int dyi0 = 2 * dyp, dx0 = 2 * dxp;
-                const int dy0 = dyi0 - (n - 1), dy1 = dy0 + 1;
-                const bool has_dy1 = dyi0 + 1 < D2, has_dx1 = dx0 + 1 < n;
-                const float2 *g0 = Gak + (dy0 >= 0 ? dy0 : -dy0) * GAK;
-                const float2 *g1 = Gak + (dy1 >= 0 ? dy1 : -dy1) * GAK;
-                const float s0 = dy0 >= 0 ? 1.0f : -1.0f, s1 = dy1 >= 0 ? 1.0f : -1.0f;
-                float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;
-#pragma unroll 4
-                for (int k = 0; k < N; ++k) {
-                    float2 ga0 = g0[k], ga1 = g1[k];
-                    ga0.y *= s0;
-                    ga1.y *= s1;
-                    const float2 t0 = Ta[k * NO + dx0];
-                    const float2 t1 = has_dx1 ? Ta[k * NO + dx0 + 1] : make_float2(0.f, 0.f);
-                    cmac2(c00, ga0, t0);
-                    cmac2(c01, ga0, t1);
-                    cmac2(c10, ga1, t0);
-                    cmac2(c11, ga1, t1);
-                }
-                auto put = [&](int dyi, int dx, float2 c) {
-                    const float2 kv = __ldg(kt + dyi * n + dx);
-                    Mw[dyi * n + dx] = make_float2(c.x * kv.x - c.y * kv.y, c.x * kv.y + c.y * kv.x);
-                };
-                put(dyi0, dx0, c00);
-                if (has_dx1) put(dyi0, dx0 + 1, c01);
-                if (has_dy1) {
-                    put(dyi0 + 1, dx0, c10);
-                    if (has_dx1) put(dyi0 + 1, dx0 + 1, c11);
-                }
-            }
-            __syncwarp();
-            // P for this half's dy rows, then partial B over those rows
-            constexpr int HALF_DY = (D2 + 1) / 2;
-            const int dyi_begin = half * HALF_DY;
-            float2 Gc[n];
-#pragma unroll
-            for (int d = 0; d < n; ++d) Gc[d] = ix < nd ? Gt[d * nd + ix] : make_float2(0.f, 0.f);
-            float Bp[nd];
-#pragma unroll
-            for (int i = 0; i < nd; ++i) Bp[i] = 0.0f;
-#pragma unroll
-            for (int j = 0; j < HALF_DY; ++j) {
-                const int dyi = dyi_begin + j;
-                if (dyi < D2) {
-                    float2 p = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int d = 0; d < n; ++d) cmac2(p, Mw[dyi * n + d], Gc[d]);
-                    const int dy = dyi - (n - 1);
-                    const float2 *gr = Gt + (dy >= 0 ? dy : -dy) * nd;
-                    const float sg = dy >= 0 ? 1.0f : -1.0f;
-#pragma unroll
-                    for (int i = 0; i < nd; ++i) {
-                        const float2 gv = gr[i];
-                        Bp[i] = fmaf(gv.x, p.x, fmaf(-sg * gv.y, p.y, Bp[i]));
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < nd; ++i) Bp[i] += __shfl_xor_sync(0xffffffffu, Bp[i], 16);
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) Bv[j] = half ? Bp[nd / 2 + j] : Bp[j];
+            tail::lgs_binned<n, nd, NO, GAK>(Ta, Mw, Ta, Gak, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
         } else {
             __syncwarp();
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) {
-                const int iy = half * (nd / 2) + j;
-                float s = 0.0f;
-#pragma unroll
-                for (int r = 0; r < b; ++r)
-#pragma unroll
-                    for (int c = 0; c < b; ++c) s += Iw[(b * iy + r) * (N + 1) + b * ix + c];
-                Bv[j] = s;
-            }
+            tail::ngs_binned<nd>(Iw, lane, Bv);
         }
-
-        // photometry, noise, centroid (lane holds column ix, rows half*nd/2 ...)
-        float sb = 0.0f;
-        if (ix < nd) {
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) sb += Bv[j];
-        }
-        sb = warp_sum(sb);
-        const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
-        float sc = 0.0f, sx = 0.0f, sy = 0.0f;
-        if (ix < nd) {
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) {
-                const int iy = half * (nd / 2) + j, o = iy * nd + ix;
-                const float e = scale * Bv[j];
-                const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
-                                                      (uint32_t)W.gs_index, tlo, thi)
-                                        : e;
-                if (st_E) st_E[(size_t)v * nd2 + o] = e;
-                if (st_C) st_C[(size_t)v * nd2 + o] = c;
-                sc += c;
-                sx = fmaf((float)ix - cd, c, sx);
-                sy = fmaf((float)iy - cd, c, sy);
-            }
-        }
-        sc = warp_sum(sc);
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) {
-            const bool ok = sc > 0.0f;
-            float *sl = D.slopes + W.slope_off;
-            sl[2 * v] = ok ? sx / sc : 0.0f;
-            sl[2 * v + 1] = ok ? sy / sc : 0.0f;
-        }
+        tail::finish<nd>(Bv, W, D, seed, v, lane);
     }
 }
 

@@ -29,13 +29,15 @@
 
 #include "internal.h"
 #include "noise.cuh"
+#include "spot_tail.cuh"
 
 namespace gbwfs {
 
 namespace {
 
-constexpr int kTcThreads = 128;
-constexpr uint32_t kTmemCols = 128;      // D1: columns [0, 64), D2: [64, 96)
+constexpr int kWG = 2;                   // independent warpgroups per CTA
+constexpr int kTcThreads = 128 * kWG;
+constexpr uint32_t kTmemCols = 128 * kWG;  // per warpgroup: D1 columns [0, 64), D2 [64, 96)
 constexpr int kWaitLimit = 1 << 24;      // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -87,6 +89,14 @@ __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+#define GBWFS_TMEM_LD16(r, addr)                                                                          \
+    asm volatile(                                                                                         \
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),        \
+          "=r"(r[15])                                                                                     \
+        : "r"(addr))
+
 #define GBWFS_TMEM_LD32(r, addr)                                                                          \
     asm volatile(                                                                                         \
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"  \
@@ -133,10 +143,10 @@ struct TcLayout {
     static constexpr int oB1 = 0;                  // 64 rows x 128 B: [F_hi; F_hi; F_lo] blocks
     static constexpr int oB2h = oB1 + 8192;        // 32 rows x 128 B: [Ga_hi; Ga_hi]
     static constexpr int oB2l = oB2h + 4096;       // 32 rows x 128 B: [Ga_lo; 0]
-    // 128 rows x 128 B: [U_hi | U_lo | U_hi] for the first MMA, then (after it has
-    // completed) [I_hi | I_lo] for the second
+    // per warpgroup, 128 rows x 128 B: [U_hi | U_lo | U_hi] for the first MMA, then (after
+    // it has completed) [I_hi | I_lo] for the second
     static constexpr int oA = oB2l + 4096;
-    static constexpr int oTab = oA + 16384;        // CUDA-core tables (float2)
+    static constexpr int oTab = oA + 16384 * kWG;  // CUDA-core tables (float2)
     static constexpr int tFk = 0;                  // [p][k]  F[k][p]
     static constexpr int tGak = tFk + n * N;       // [dyi][GAK] Ga(dy, k), conjugated rows for dy < 0
     static constexpr int tG = tGak + D2 * GAK;     // [d][nd] G[d][i]
@@ -146,28 +156,30 @@ struct TcLayout {
     static constexpr int wX = 0, wTa = wX + n * n, wM = wTa + N * NO, wI = wTa;
     static constexpr int lgs_end = wM + D2 * n, ngs_end = wI + (N * (N + 1) + 1) / 2;
     static constexpr int warp = lgs_end > ngs_end ? lgs_end : ngs_end;
-    static constexpr int oMisc = oWarp + 4 * warp * 8;  // mbarriers, TMEM address, flags
-    static constexpr int bytes = oMisc + 64;
+    static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;  // per warpgroup: 2 mbarriers, flag
+    static constexpr int bytes = oMisc + 32 * kWG + 16;
 };
 
 }  // namespace
 
 template <int n, int nd>
-__global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__ ShArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__ ShArgs a) {
     using Lay = TcLayout<n, nd>;
     constexpr int N = 32, D2 = Lay::D2, NO = Lay::NO, GAK = Lay::GAK, b = N / nd, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
     static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB1 = smem + Lay::oB1, *sB2h = smem + Lay::oB2h, *sB2l = smem + Lay::oB2l;
-    uint8_t *sA1 = smem + Lay::oA, *sA2 = smem + Lay::oA;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const int wg = wib >> 2, wq = wib & 3;  // warpgroup, warp within it (= TMEM lane quarter)
+    uint8_t *sA1 = smem + Lay::oA + 16384 * wg, *sA2 = sA1;
     float2 *tab = reinterpret_cast<float2 *>(smem + Lay::oTab);
     float2 *Fk = tab + Lay::tFk, *Gak = tab + Lay::tGak, *Gt = tab + Lay::tG;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + 16);
-    int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 20);
-
-    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + 32 * wg);
+    int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 32 * wg + 16);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + 32 * kWG);
+    const uint32_t bar_id = 1 + wg;
+    auto wg_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(128) : "memory"); };
     // constant operand tiles (pre-swizzled on the host) and CUDA-core tables
     {
         const uint4 *src1 = reinterpret_cast<const uint4 *>(a.tc_B1);
@@ -195,7 +207,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
+    if (wq == 0 && lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -205,8 +217,9 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tmem = *tslot;
-    const uint32_t t_row = tmem + ((uint32_t)(wib * 32) << 16);
+    const uint32_t tmem_all = *tslot;
+    const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
+    const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
     constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
 
     float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
@@ -215,12 +228,13 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
     const float cd = 0.5f * (float)(nd - 1);
     const int ix = lane & 15, half = lane >> 4;
-    const int row = wib * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
+    const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
     const int groups = (a.total + 3) / 4;
+    const bool issuer = wq == 0 && lane == 0;
     uint32_t phase = 0;
 
-    for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
-        const int g = 4 * grp + wib;
+    for (int grp = blockIdx.x * kWG + wg; grp < groups; grp += gridDim.x * kWG) {
+        const int g = 4 * grp + wq;
         const bool active = g < a.total;
         const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
         const InstDyn &D = a.dyn[W.inst];
@@ -275,10 +289,10 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
         }
         fence_async_smem();
         fence_before_sync();
-        __syncthreads();
+        wg_sync();
         fence_after_sync();
         if (*sflag) break;  // a previous wait timed out (uniform: read after the barrier)
-        if (tid == 0) {
+        if (issuer) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
                 mma_bf16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
@@ -286,56 +300,53 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
         }
         if (!mbar_wait(&mbar[0], phase)) *sflag = 1;
         fence_after_sync();
-        // Y row from TMEM -> I
-        float I[N];
+        // Y row from TMEM -> I = |Y|^2 -> second operand row [I_hi | I_lo], 16 columns at a time
         {
-            uint32_t r[32];
-            GBWFS_TMEM_LD32(r, t_row + 0);
-            tmem_wait_ld();
-            uint32_t r2[32];
-            GBWFS_TMEM_LD32(r2, t_row + 32);
-            tmem_wait_ld();
+            float *dstI = (active && D.st_I) ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
 #pragma unroll
-            for (int m = 0; m < N; ++m) {
-                const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
-                I[m] = fmaf(yr, yr, yi * yi);
-            }
-        }
-        if (active && D.st_I) {
-            float *dst = D.st_I + W.int_off + (size_t)v * (N * N) + lane * N;
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t r[16], r2[16];
+                GBWFS_TMEM_LD16(r, t_row + 16 * hh);
+                GBWFS_TMEM_LD16(r2, t_row + 32 + 16 * hh);
+                tmem_wait_ld();
+                float I[16];
 #pragma unroll
-            for (int m = 0; m < N; ++m) dst[m] = I[m];
-        }
-        if (active && !W.is_lgs) {
-#pragma unroll
-            for (int m = 0; m < N; ++m) Iw[lane * (N + 1) + m] = I[m];
-        }
-        // A2 row: [I_hi | I_lo]
-        {
-#pragma unroll
-            for (int ch = 0; ch < 8; ++ch) {
-                uint32_t wds[4];
-#pragma unroll
-                for (int e2 = 0; e2 < 4; ++e2) {
-                    float vv[2];
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int e = ch * 8 + e2 * 2 + h2;
-                        float hi, lo;
-                        split_bf16(I[e & 31], hi, lo);
-                        vv[h2] = e < 32 ? hi : lo;
-                    }
-                    wds[e2] = pack_bf16(vv[0], vv[1]);
+                for (int m = 0; m < 16; ++m) {
+                    const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
+                    I[m] = fmaf(yr, yr, yi * yi);
                 }
-                *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                if (dstI) {
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) dstI[16 * hh + m] = I[m];
+                }
+                if (active && !W.is_lgs) {
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) Iw[lane * (N + 1) + 16 * hh + m] = I[m];
+                }
+#pragma unroll
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        float h0, l0, h1, l1;
+                        split_bf16(I[c2 * 8 + 2 * e2], h0, l0);
+                        split_bf16(I[c2 * 8 + 2 * e2 + 1], h1, l1);
+                        hw[e2] = pack_bf16(h0, h1);
+                        lw[e2] = pack_bf16(l0, l1);
+                    }
+                    *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (2 * hh + c2) * 8)) =
+                        make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (4 + 2 * hh + c2) * 8)) =
+                        make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
             }
         }
         fence_async_smem();
         fence_before_sync();
-        __syncthreads();
+        wg_sync();
         fence_after_sync();
         if (*sflag) break;
-        if (tid == 0) {
+        if (issuer) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
                 mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
@@ -362,123 +373,45 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_sh_tc(const __grid_constant__
 
         // remaining stages on the CUDA cores (per warp)
         float Bv[nd / 2];
-        if (W.is_lgs) {
-            const float2 *kt = W.ktil + (size_t)v * (D2 * n);
-            constexpr int DYP = (D2 + 1) / 2, DXP = (n + 1) / 2, TASKS = DYP * DXP;
-            for (int task = lane; task < TASKS; task += 32) {
-                const int dyp = task / DXP, dxp = task - dyp * DXP;
-                const int dyi0 = 2 * dyp, dx0 = 2 * dxp;
-                const bool has_dy1 = dyi0 + 1 < D2, has_dx1 = dx0 + 1 < n;
-                const float2 *g0 = Gak + dyi0 * GAK;
-                const float2 *g1 = Gak + (has_dy1 ? dyi0 + 1 : dyi0) * GAK;
-                float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;
-#pragma unroll 4
-                for (int k = 0; k < N; ++k) {
-                    const float2 ga0 = g0[k], ga1 = g1[k];
-                    const float2 t0 = Ta[k * NO + dx0];
-                    const float2 t1 = has_dx1 ? Ta[k * NO + dx0 + 1] : make_float2(0.f, 0.f);
-                    cmacc(c00, ga0, t0);
-                    cmacc(c01, ga0, t1);
-                    cmacc(c10, ga1, t0);
-                    cmacc(c11, ga1, t1);
-                }
-                auto put = [&](int dyi, int dx, float2 c) {
-                    const float2 kv = __ldg(kt + dyi * n + dx);
-                    Mw[dyi * n + dx] = make_float2(c.x * kv.x - c.y * kv.y, c.x * kv.y + c.y * kv.x);
-                };
-                put(dyi0, dx0, c00);
-                if (has_dx1) put(dyi0, dx0 + 1, c01);
-                if (has_dy1) {
-                    put(dyi0 + 1, dx0, c10);
-                    if (has_dx1) put(dyi0 + 1, dx0 + 1, c11);
-                }
-            }
-            __syncwarp();
-            constexpr int HALF_DY = (D2 + 1) / 2;
-            const int dyi_begin = half * HALF_DY;
-            float2 Gc[n];
-#pragma unroll
-            for (int d = 0; d < n; ++d) Gc[d] = ix < nd ? Gt[d * nd + ix] : make_float2(0.f, 0.f);
-            float Bp[nd];
-#pragma unroll
-            for (int i = 0; i < nd; ++i) Bp[i] = 0.0f;
-#pragma unroll
-            for (int j = 0; j < HALF_DY; ++j) {
-                const int dyi = dyi_begin + j;
-                if (dyi < D2) {
-                    float2 p = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int d = 0; d < n; ++d) cmacc(p, Mw[dyi * n + d], Gc[d]);
-                    const int dy = dyi - (n - 1);
-                    const float2 *gr = Gt + (dy >= 0 ? dy : -dy) * nd;
-                    const float sg = dy >= 0 ? 1.0f : -1.0f;
-#pragma unroll
-                    for (int i = 0; i < nd; ++i) {
-                        const float2 gv = gr[i];
-                        Bp[i] = fmaf(gv.x, p.x, fmaf(-sg * gv.y, p.y, Bp[i]));
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < nd; ++i) Bp[i] += __shfl_xor_sync(0xffffffffu, Bp[i], 16);
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) Bv[j] = half ? Bp[nd / 2 + j] : Bp[j];
-        } else {
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) {
-                const int iy = half * (nd / 2) + j;
-                float s = 0.0f;
-#pragma unroll
-                for (int r = 0; r < b; ++r)
-#pragma unroll
-                    for (int c = 0; c < b; ++c) s += Iw[(b * iy + r) * (N + 1) + b * ix + c];
-                Bv[j] = s;
-            }
-        }
-        float sb = 0.0f;
-        if (ix < nd) {
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) sb += Bv[j];
-        }
-        sb = wsum(sb);
-        const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
-        const uint64_t seed = a.inst[W.inst].seed;
-        const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
-        const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
-        float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
-        float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
-        float sc = 0.0f, sx = 0.0f, sy = 0.0f;
-        if (ix < nd) {
-#pragma unroll
-            for (int j = 0; j < nd / 2; ++j) {
-                const int iy = half * (nd / 2) + j, o = iy * nd + ix;
-                const float e = scale * Bv[j];
-                const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
-                                                      (uint32_t)W.gs_index, tlo, thi)
-                                        : e;
-                if (st_E) st_E[(size_t)v * nd2 + o] = e;
-                if (st_C) st_C[(size_t)v * nd2 + o] = c;
-                sc += c;
-                sx = fmaf((float)ix - cd, c, sx);
-                sy = fmaf((float)iy - cd, c, sy);
-            }
-        }
-        sc = wsum(sc);
-        sx = wsum(sx);
-        sy = wsum(sy);
-        if (lane == 0) {
-            const bool okc = sc > 0.0f;
-            float *sl = D.slopes + W.slope_off;
-            sl[2 * v] = okc ? sx / sc : 0.0f;
-            sl[2 * v + 1] = okc ? sy / sc : 0.0f;
-        }
+        if (W.is_lgs)
+            tail::lgs_binned<n, nd, NO, GAK>(Ta, Mw, Ta, Gak, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
+        else
+            tail::ngs_binned<nd>(Iw, lane, Bv);
+        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane);
     }
     fence_before_sync();
     __syncthreads();
-    if (*sflag && tid == 0 && a.status) atomicCAS(a.status, 0, 5 /* WFS_ETIMEOUT */);
+    if (*sflag && issuer && a.status) atomicCAS(a.status, 0, 5 /* WFS_ETIMEOUT */);
     fence_after_sync();
-    if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_all), "r"(kTmemCols));
+}
+
+// ---------------------------------------------------------------- wait check
+// One CTA waits on an mbarrier that nothing will ever arrive on, with a short bound, then
+// reports WFS_ETIMEOUT in *status: the same bounded wait the spot kernel uses, exercised
+// without faulting or hanging the GPU.
+__global__ void k_wait_check(int *status, int limit) {
+    __shared__ __align__(8) uint64_t mb;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mb)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(&mb)), "r"(0)
+            : "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) *status = done ? 0 : 5 /* WFS_ETIMEOUT */;
+}
+
+cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s) {
+    k_wait_check<<<1, 32, 0, s>>>(status, limit);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- host side
@@ -505,9 +438,10 @@ cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
     cudaError_t e = cudaFuncSetAttribute(k_sh_tc<n, nd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int groups = (a.total + 3) / 4;
-    // at most 3 CTAs per SM: their tensor memory (3 x 128 columns) always fits
-    const int cap = a.grid_cap > 0 && a.grid_cap < 152 * 3 ? a.grid_cap : 152 * 3;
-    int blocks = groups < cap ? groups : cap;
+    const int cta_groups = (groups + kWG - 1) / kWG;
+    // at most 2 CTAs per SM (shared memory): their tensor memory (2 x 256 columns) always fits
+    const int cap = a.grid_cap > 0 && a.grid_cap < 152 * 2 ? a.grid_cap : 152 * 2;
+    int blocks = cta_groups < cap ? cta_groups : cap;
     if (blocks < 1) blocks = 1;
     out->func = (const void *)k_sh_tc<n, nd>;
     out->grid = dim3(blocks);

@@ -1,0 +1,166 @@
+// spot_tail.cuh -- the stages of the 32-point spot kernels that follow the first
+// transfer-domain stage, on the CUDA cores, for one subaperture owned by one warp
+// (Sec. 4 LGS SH: elongation by the sodium kernel, binning, noise-added image,
+// centroid).  Shared by the FP32 and tensor-core kernels.
+//
+//   M[dy][dx] = Kt[dy][dx] sum_k Ga(dy, k) Ta[k][dx]      (1 x 2 register tiles)
+//   Q[iy][dx] = sum_dy G(dy, iy) M[dy][dx]                 (lane = iy, half-warp = dx half)
+//   B[iy][ix] = Re sum_dx Q[iy][dx] G[dx][ix]              (lane = ix, half-warp = iy half)
+// with Ga(dy, k) = exp(+2 pi i (k - cN) dy / N) and G(dy, i) = sum_{r<b} w^{(b i + r - cN) dy}
+// (conjugated for dy < 0).  Kt carries 1/N^2 and the Hermitian weight c_dx, so B is the
+// binned elongated spot.  Then E = photons fill B / sum B, C = Poisson(E) + ron z (or E),
+// and the centre of gravity.
+#pragma once
+#include "internal.h"
+#include "noise.cuh"
+
+namespace gbwfs {
+namespace tail {
+
+__device__ __forceinline__ void cmac(float2 &acc, const float2 a, const float2 b) {
+    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Ta: [32][NO] (row k), Gak: [2n-1][gak] rows Ga(dy, .) already conjugated for dy < 0,
+// Gt: [n][nd] G[d][i].  M and Q are per-warp scratch ([2n-1][n], [nd][n]).  On return
+// Bv[j] = B[half * nd/2 + j][ix] for lane = half * 16 + ix.
+template <int n, int nd, int NO, int GAK>
+__device__ __forceinline__ void lgs_binned(const float2 *Ta, float2 *M, float2 *Q, const float2 *Gak,
+                                           const float2 *Gt, const float2 *kt, int lane, float (&Bv)[nd / 2]) {
+    constexpr int N = 32, D2 = 2 * n - 1, DXP = (n + 1) / 2, TASKS = D2 * DXP, DXH = (n + 1) / 2;
+    static_assert(nd == 16, "the detector tile maps to 16 lanes x 2 half-warps");
+    // M: tasks (dy, dx pair), three rounds over the warp for n = 10
+    for (int task = lane; task < TASKS; task += 32) {
+        const int dyi = task / DXP, dx0 = 2 * (task - dyi * DXP);
+        const bool has1 = dx0 + 1 < n;
+        const float2 *g = Gak + dyi * GAK;
+        float2 c0 = make_float2(0.f, 0.f), c1 = c0;
+#pragma unroll 8
+        for (int k = 0; k < N; ++k) {
+            const float2 ga = g[k];
+            cmac(c0, ga, Ta[k * NO + dx0]);
+            if (has1) cmac(c1, ga, Ta[k * NO + dx0 + 1]);
+        }
+        const float2 k0 = __ldg(kt + dyi * n + dx0);
+        M[dyi * n + dx0] = make_float2(c0.x * k0.x - c0.y * k0.y, c0.x * k0.y + c0.y * k0.x);
+        if (has1) {
+            const float2 k1 = __ldg(kt + dyi * n + dx0 + 1);
+            M[dyi * n + dx0 + 1] = make_float2(c1.x * k1.x - c1.y * k1.y, c1.x * k1.y + c1.y * k1.x);
+        }
+    }
+    __syncwarp();
+    // Q[iy][dx] for iy = lane & 15, dx in this half
+    const int ix = lane & 15, half = lane >> 4;
+    {
+        const int iy = ix;
+        float2 q[DXH];
+#pragma unroll
+        for (int j = 0; j < DXH; ++j) q[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int dyi = 0; dyi < D2; ++dyi) {
+            const int dy = dyi - (n - 1);
+            float2 gv = Gt[(dy >= 0 ? dy : -dy) * nd + iy];
+            if (dy < 0) gv.y = -gv.y;
+#pragma unroll
+            for (int j = 0; j < DXH; ++j) {
+                const int dx = half * DXH + j;
+                if (dx < n) cmac(q[j], gv, M[dyi * n + dx]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < DXH; ++j) {
+            const int dx = half * DXH + j;
+            if (dx < n) Q[iy * n + dx] = q[j];
+        }
+    }
+    __syncwarp();
+    // B[iy][ix] for iy in this half
+    float2 gc[n];
+#pragma unroll
+    for (int d = 0; d < n; ++d) gc[d] = Gt[d * nd + ix];
+#pragma unroll
+    for (int j = 0; j < nd / 2; ++j) {
+        const int iy = half * (nd / 2) + j;
+        float s = 0.0f;
+#pragma unroll
+        for (int d = 0; d < n; ++d) {
+            const float2 qv = Q[iy * n + d];
+            s = fmaf(qv.x, gc[d].x, fmaf(-qv.y, gc[d].y, s));
+        }
+        Bv[j] = s;
+    }
+}
+
+// NGS: b x b binning of the spot image rows Iw ([32][33] floats).
+template <int nd>
+__device__ __forceinline__ void ngs_binned(const float *Iw, int lane, float (&Bv)[nd / 2]) {
+    constexpr int N = 32, b = N / nd;
+    const int ix = lane & 15, half = lane >> 4;
+#pragma unroll
+    for (int j = 0; j < nd / 2; ++j) {
+        const int iy = half * (nd / 2) + j;
+        float s = 0.0f;
+        if (ix < nd) {
+#pragma unroll
+            for (int r = 0; r < b; ++r)
+#pragma unroll
+                for (int c = 0; c < b; ++c) s += Iw[(b * iy + r) * (N + 1) + b * ix + c];
+        }
+        Bv[j] = s;
+    }
+}
+
+// Photometry, noise and the centroid of subaperture v of WFS W; lane 0 writes the slopes.
+template <int nd>
+__device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc &W, const InstDyn &D,
+                                       uint64_t seed, int v, int lane) {
+    constexpr int nd2 = nd * nd;
+    const int ix = lane & 15, half = lane >> 4;
+    const float cd = 0.5f * (float)(nd - 1);
+    float sb = 0.0f;
+    if (ix < nd) {
+#pragma unroll
+        for (int j = 0; j < nd / 2; ++j) sb += Bv[j];
+    }
+    sb = warp_sum(sb);
+    const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
+    const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
+    const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
+    float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
+    float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
+    float sc = 0.0f, sx = 0.0f, sy = 0.0f;
+    if (ix < nd) {
+#pragma unroll
+        for (int j = 0; j < nd / 2; ++j) {
+            const int iy = half * (nd / 2) + j, o = iy * nd + ix;
+            const float e = scale * Bv[j];
+            const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
+                                                  (uint32_t)W.gs_index, tlo, thi)
+                                    : e;
+            if (st_E) st_E[(size_t)v * nd2 + o] = e;
+            if (st_C) st_C[(size_t)v * nd2 + o] = c;
+            sc += c;
+            sx = fmaf((float)ix - cd, c, sx);
+            sy = fmaf((float)iy - cd, c, sy);
+        }
+    }
+    sc = warp_sum(sc);
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) {
+        const bool ok = sc > 0.0f;
+        float *sl = D.slopes + W.slope_off;
+        sl[2 * v] = ok ? sx / sc : 0.0f;
+        sl[2 * v + 1] = ok ? sy / sc : 0.0f;
+    }
+}
+
+}  // namespace tail
+}  // namespace gbwfs

@@ -110,6 +110,7 @@ _SIGS = {
     "wfs_batch_info": (C.c_int, [_H, C.c_int, C.POINTER(wfs_batch_class), C.POINTER(C.c_int)]),
     "wfs_version": (C.c_char_p, []),
     "wfs_timing_enable": (C.c_int, [_H, C.c_int]),
+    "wfs_check_bounded_wait": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "wfs_measure_one_static": (C.c_int, [C.POINTER(wfs_telescope), C.POINTER(wfs_geometry),
                                          C.POINTER(wfs_guide_star), C.POINTER(wfs_layers), C.c_void_p,
                                          C.c_double, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p, C.c_int,
@@ -226,6 +227,10 @@ def wfs_sync_status(h):
 def wfs_noise_apply(expected_ptr, n, read_noise, seed, wfs_index, t, pixel0, counts_ptr, stream=0):
     _check(lib().wfs_noise_apply(expected_ptr, int(n), float(read_noise), int(seed), int(wfs_index),
                                  float(t), int(pixel0), counts_ptr, stream))
+
+
+def wfs_check_bounded_wait(h, polls, stream=0):
+    _check(lib().wfs_check_bounded_wait(h, int(polls), stream), h)
 
 
 def wfs_timing_enable(h, enable):

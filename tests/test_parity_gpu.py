@@ -325,3 +325,19 @@ def test_bf16x3_unsupported_geometry_is_refused():
     with pytest.raises(native.WfsError) as ei:
         native.Wfs(cfg)
     assert ei.value.status == native.WFS_EUNSUPPORTED
+
+
+def test_bounded_wait_reports_timeout_without_fault():
+    """A wait that nothing satisfies gives up after its bound and reports WFS_ETIMEOUT through
+    the status word; the context stays usable (a measurement right after still works)."""
+    cfg = inputs.config1()
+    w = native.Wfs(cfg)
+    native.wfs_check_bounded_wait(w.h, 2000, 0)
+    with pytest.raises(native.WfsError) as ei:
+        native.wfs_sync_status(w.h)
+    assert ei.value.status == native.WFS_ETIMEOUT
+    native.wfs_sync_status(w.h)          # cleared after being read
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    gpu, _ = run_library(cfg, scr, 0.0, handle=w)
+    assert np.all(np.isfinite(gpu[0]["slopes"]))
+    w.close()
