@@ -60,6 +60,8 @@ struct GsDev {
     uint32_t *d_mask = nullptr;
     float *d_fill = nullptr;
     float2 *d_ktil = nullptr;
+    int4 *d_segs = nullptr;
+    int n_segs = 0, seg_cols = 0, tiled = 0;
     size_t slope_off = 0, opd_off = 0, int_off = 0, det_off = 0;
 };
 
@@ -72,7 +74,7 @@ struct wfs_ctx {
     std::vector<WfsDesc> wfs_host;
     WfsDesc *d_wfs = nullptr;
     std::vector<SpotGroup> groups;
-    int proj_blocks = 0;
+    int proj_blocks = 0, proj_box = 0;
     wfs_telescope tel{};
     std::vector<GeomDev> geoms;
     std::vector<GsDev> gs;
@@ -123,7 +125,7 @@ struct wfs_batch_ctx {
     WfsDesc *d_wfs = nullptr;
     std::vector<WfsDesc> wfs_host;
     std::vector<BatchClass> classes;
-    int proj_blocks = 0;
+    int proj_blocks = 0, proj_box = 0;
     ProjArgs *pa = nullptr;          // parameter blocks the graph nodes point to
     std::vector<ShArgs *> sa;
     cudaGraph_t graph = nullptr;
@@ -271,6 +273,7 @@ void release(wfs_ctx *h) {
         cudaFree(s.d_mask);
         cudaFree(s.d_fill);
         cudaFree(s.d_ktil);
+        cudaFree(s.d_segs);
     }
     cudaFree(h->d_opd);
     cudaFree(h->d_status);
@@ -392,6 +395,8 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     pa.wfs = h->d_wfs;
     pa.n_wfs = (int)h->wfs_host.size();
     pa.n_inst = 1;
+    pa.box_cap = h->proj_box;
+    pa.status = h->d_status;
     pa.dyn[0] = dyn;
     cudaError_t e;
     if (h->proj_blocks > 0) {
@@ -558,6 +563,21 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
             delete h;
             return cuda_fail(nullptr, e, "subaperture table upload");
         }
+        // shared-memory projection tiles when the pupil samples the screens no more coarsely
+        // than one screen pixel (cone factor <= 1)
+        s.tiled = (tel->diameter_m / Np) / layers->screen_dx_m <= 1.0 + 1e-12 && s.n_valid > 0;
+        if (s.tiled) {
+            std::vector<int4> segs;
+            int run = 0;
+            build_segments(s.ids, g.n_sub, segment_max_count(n), segs, &run);
+            s.n_segs = (int)segs.size();
+            s.seg_cols = run * n;
+            if ((e = upload(&s.d_segs, segs)) != cudaSuccess) {
+                release(h);
+                delete h;
+                return cuda_fail(nullptr, e, "projection tile upload");
+            }
+        }
         if (gs[w].is_lgs && s.n_valid > 0) {
             const size_t kt = (size_t)s.n_valid * (2 * n - 1) * n;
             if ((e = cudaMalloc(&s.d_ktil, kt * sizeof(float2))) != cudaSuccess) {
@@ -640,8 +660,13 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 d.slope_off = (long long)s.slope_off;
                 d.int_off = (long long)s.int_off;
                 d.det_off = (long long)s.det_off;
+                d.segs = s.d_segs;
+                d.n_segs = s.n_segs;
+                d.tiled = s.tiled;
+                d.seg_cols = s.seg_cols;
                 d.proj_block_begin = blocks;
-                blocks += project_blocks(s.n_valid, g.n_pix_sub);
+                blocks += project_blocks(d);
+                if (project_box_floats(d) > h->proj_box) h->proj_box = project_box_floats(d);
                 d.subap_begin = G.total;
                 G.total += s.n_valid;
                 h->wfs_host.push_back(d);
@@ -902,7 +927,7 @@ cudaError_t batch_build_graph(wfs_batch b) {
     cudaError_t e;
     if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess) return e;
     LaunchShape ps;
-    project_launch_shape(b->proj_blocks, &ps);
+    project_launch_shape(*b->pa, b->proj_blocks, &ps);
     void *pargs[] = {(void *)b->pa};
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof kp);
@@ -932,7 +957,7 @@ cudaError_t batch_build_graph(wfs_batch b) {
 cudaError_t batch_update_graph(wfs_batch b) {
     cudaError_t e;
     LaunchShape ps;
-    project_launch_shape(b->proj_blocks, &ps);
+    project_launch_shape(*b->pa, b->proj_blocks, &ps);
     void *pargs[] = {(void *)b->pa};
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof kp);
@@ -1064,7 +1089,8 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
             d.subap_begin = bc.total;
             bc.total += d.n_valid;
             d.proj_block_begin = blocks;
-            blocks += project_blocks(d.n_valid, d.n);
+            blocks += project_blocks(d);
+            if (project_box_floats(d) > b->proj_box) b->proj_box = project_box_floats(d);
             b->wfs_host.push_back(d);
             ++bc.count;
         }
@@ -1088,6 +1114,8 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     b->pa->wfs = b->d_wfs;
     b->pa->n_wfs = (int)b->wfs_host.size();
     b->pa->n_inst = n;
+    b->pa->box_cap = b->proj_box;
+    b->pa->status = hs[0]->d_status;
     for (const BatchClass &bc : b->classes) {
         ShArgs *a = new ShArgs();
         memset(a, 0, sizeof(ShArgs));
@@ -1177,7 +1205,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
             d.t = t_s[pos[i]];
             d.noise = b->hs[i]->noise;
         }
-    int count = 0, blocks = 0;
+    int count = 0, blocks = 0, box = 0;
     std::vector<int> cls_first(b->classes.size()), cls_count(b->classes.size()), cls_total(b->classes.size());
     for (size_t c = 0; c < b->classes.size(); ++c) {
         const BatchClass &bc = b->classes[c];
@@ -1190,7 +1218,8 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
             d.subap_begin = cls_total[c];
             cls_total[c] += d.n_valid;
             d.proj_block_begin = blocks;
-            blocks += project_blocks(d.n_valid, d.n);
+            blocks += project_blocks(d);
+            if (project_box_floats(d) > box) box = project_box_floats(d);
             sl.h[count++] = d;
         }
         cls_count[c] = count - cls_first[c];
@@ -1203,6 +1232,8 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
     pa.wfs = sl.d;
     pa.n_wfs = count;
     pa.n_inst = n;
+    pa.box_cap = box;
+    pa.status = b->hs[0]->d_status;
     if (blocks > 0 && (e = launch_project(pa, blocks, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(nullptr, e, "batch subset projection");
     for (size_t c = 0; c < b->classes.size(); ++c) {

@@ -46,6 +46,10 @@ struct WfsDesc {                    // static per wavefront sensor
     long long opd_off, slope_off, int_off, det_off;  // into the instance's buffers (floats)
     int proj_block_begin;           // first CTA of this WFS in the projection launch
     int subap_begin;                // first subaperture of this WFS in its spot launch
+    // projection by shared-memory tiles (pupil pitch <= screen pitch): runs of consecutive
+    // valid subapertures of one subaperture row, {sy, first valid index, count, sx of first}
+    const int4 *segs;
+    int n_segs, tiled, seg_cols;    // seg_cols: largest run width in pupil columns
 };
 
 struct InstDyn {                    // per call, per instance
@@ -62,6 +66,8 @@ struct ProjArgs {
     const InstDesc *inst;
     const WfsDesc *wfs;
     int n_wfs, n_inst;
+    int box_cap;                    // floats of shared memory for tables and screen box
+    int *status;                    // device status word (limit errors)
     InstDyn dyn[kMaxInstances];
 };
 
@@ -113,9 +119,16 @@ struct LaunchShape {
 
 // Launchers (return the cudaGetLastError() of the launch).
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s);
-cudaError_t project_launch_shape(int total_blocks, LaunchShape *out);
-// CTAs the projection needs for one WFS (n_valid subapertures of n x n pixels).
-int project_blocks(int n_valid, int n);
+cudaError_t project_launch_shape(const ProjArgs &a, int total_blocks, LaunchShape *out);
+// CTAs the projection needs for one WFS.
+int project_blocks(const WfsDesc &d);
+// Shared-memory floats the WFS's screen box needs (0 when it is projected by direct gathers).
+int project_box_floats(const WfsDesc &d);
+// Runs of consecutive valid subapertures per subaperture row, at most max_count each.
+void build_segments(const std::vector<int32_t> &ids, int n_sub, int max_count, std::vector<int4> &segs,
+                    int *max_run);
+// Largest run (in subapertures) of one projection tile for n x n-pixel subapertures.
+int segment_max_count(int n);
 cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
 cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
                          uint32_t pixel0, float *C, cudaStream_t s);

@@ -23,6 +23,15 @@ namespace gbwfs {
 
 constexpr int kProjThreads = 256;
 
+constexpr int kTilePixels = 4096;                         // pupil pixels per tiled CTA
+constexpr int kTilePx = kTilePixels / kProjThreads;       // per thread
+
+__device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
+    if (pow2) return i & (S - 1);
+    int r = i % S;
+    return r < 0 ? r + S : r;
+}
+
 __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
     __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
@@ -61,6 +70,129 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     }
     __syncthreads();
 
+    const bool pow2 = (S & (S - 1)) == 0;
+    if (W.tiled) {
+        // one run of consecutive subapertures of one subaperture row; each layer's screen
+        // footprint is staged in shared memory (cp.async, double-buffered so the next layer
+        // streams in while this one is interpolated); coordinates come from per-column and
+        // per-row tables (a pixel's screen column depends on its pupil column only)
+        extern __shared__ float psm[];
+        const int4 sg = W.segs[(int)blockIdx.x - W.proj_block_begin];  // sy, v_first, count, sx0
+        const int n = W.n, nn = n * n, ncol = sg.z * n, npx = sg.z * nn;
+        const int box_floats = ((a.box_cap - ((4 * (ncol + n) + 3) & ~3)) / 2) & ~3;
+        float2 *tab[2] = {reinterpret_cast<float2 *>(psm), reinterpret_cast<float2 *>(psm) + (ncol + n)};
+        const int box_off = (4 * (ncol + n) + 3) & ~3;  // 16-byte aligned boxes
+        float *boxb[2] = {psm + box_off, psm + box_off + (box_floats & ~3)};
+        const float half = 0.5f * (float)(W.n_sub * n - 1);
+        int pj[kTilePx];
+        float acc[kTilePx];
+#pragma unroll
+        for (int k = 0; k < kTilePx; ++k) {
+            const int px = threadIdx.x + k * kProjThreads;
+            const int v = px / nn, rr = px - v * nn, p = rr / n, q = rr - p * n;
+            pj[k] = px < npx ? (p << 16) | (v * n + q) : -1;
+            acc[k] = 0.0f;
+        }
+        auto tables = [&](int l, float2 *t) {
+            const float ch = s_c[l], cl = s_cl[l];
+            for (int j = threadIdx.x; j < ncol + n; j += kProjThreads) {
+                const bool col = j < ncol;
+                const float xr = col ? (float)(sg.w * n + j) - half : (float)(sg.x * n + (j - ncol)) - half;
+                const float ph = __fmul_rn(ch, xr), pl = fmaf(ch, xr, -ph) + cl * xr;
+                const float ih = floorf(ph);
+                const float ru = ((ph - ih) + pl) + (col ? s_fu[l] : s_fv[l]);
+                const float iu = floorf(ru);
+                t[j] = make_float2(__int_as_float((int)ih + (int)iu), ru - iu);
+            }
+        };
+        // Box origin (relative to the layer base) and width, the origin rounded down so that
+        // the box's first screen column is a multiple of 4 (16-byte copies when S % 4 == 0).
+        const bool vec = (S & 3) == 0;
+        auto box_geom = [&](int l, const float2 *t, int &bx0, int &by0, int &bw, int &bh) {
+            bx0 = __float_as_int(t[0].x);
+            by0 = __float_as_int(t[ncol].x);
+            bw = __float_as_int(t[ncol - 1].x) - bx0 + 2;
+            bh = __float_as_int(t[ncol + n - 1].x) - by0 + 2;
+            if (vec) {
+                const int off = wrap_index(s_bu[l] + bx0, S, pow2) & 3;
+                bx0 -= off;
+                bw = (bw + off + 3) & ~3;
+            }
+        };
+        // returns false (for every thread) when the box would not fit
+        auto issue_box = [&](int l, const float2 *t, float *box) -> bool {
+            int bx0, by0, bw, bh;
+            box_geom(l, t, bx0, by0, bw, bh);
+            if (bw * bh > box_floats) return false;
+            const float *scr = D.screens + (size_t)l * S * S;
+            if (vec) {
+                const int cw = bw >> 2;  // 16-byte chunks per box row
+                for (int idx = threadIdx.x; idx < cw * bh; idx += kProjThreads) {
+                    const int r = idx / cw, c4 = idx - r * cw;
+                    const float *src = scr + (size_t)wrap_index(s_bv[l] + by0 + r, S, pow2) * S +
+                                       wrap_index(s_bu[l] + bx0 + 4 * c4, S, pow2);
+                    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(box + r * bw + 4 * c4);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                }
+            } else {
+                for (int r = 0; r < bh; ++r) {
+                    const float *grow = scr + (size_t)wrap_index(s_bv[l] + by0 + r, S, pow2) * S;
+                    for (int c = threadIdx.x; c < bw; c += kProjThreads) {
+                        const float *src = grow + wrap_index(s_bu[l] + bx0 + c, S, pow2);
+                        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(box + r * bw + c);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+                    }
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            return true;
+        };
+        bool fits = true;
+        tables(0, tab[0]);
+        __syncthreads();
+        fits = issue_box(0, tab[0], boxb[0]);
+        for (int l = 0; l < I.n_layers && fits; ++l) {
+            const int cur = l & 1, nxt = cur ^ 1;
+            const bool more = l + 1 < I.n_layers;
+            if (more) tables(l + 1, tab[nxt]);
+            __syncthreads();
+            bool fits_next = true;
+            if (more) fits_next = issue_box(l + 1, tab[nxt], boxb[nxt]);
+            if (more && fits_next)
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            const float2 *t = tab[cur];
+            const float *box = boxb[cur];
+            int bx0, by0, bw, bh;
+            box_geom(l, t, bx0, by0, bw, bh);
+#pragma unroll
+            for (int k = 0; k < kTilePx; ++k) {
+                if (pj[k] < 0) continue;
+                const int j = pj[k] & 0xFFFF, p = pj[k] >> 16;
+                const float2 cj = t[j], rp = t[ncol + p];
+                const int ci = __float_as_int(cj.x) - bx0, ri = __float_as_int(rp.x) - by0;
+                const float *b0 = box + ri * bw + ci;
+                const float s00 = b0[0], s01 = b0[1], s10 = b0[bw], s11 = b0[bw + 1];
+                const float top = fmaf(cj.y, s01 - s00, s00);
+                const float bot = fmaf(cj.y, s11 - s10, s10);
+                acc[k] += fmaf(rp.y, bot - top, top);
+            }
+            __syncthreads();  // this layer's tables and box are free for layer l + 2
+            fits = fits_next;
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (!fits && threadIdx.x == 0 && a.status) atomicCAS(a.status, 0, 6 /* WFS_EUNSUPPORTED */);
+        float *opd = D.opd + W.opd_off + (size_t)sg.y * nn;
+#pragma unroll
+        for (int k = 0; k < kTilePx; ++k) {
+            const int px = threadIdx.x + k * kProjThreads;
+            if (px < npx) opd[px] = acc[k];
+        }
+        return;
+    }
+
     // each thread: one 2x2 block of pupil pixels (rows p, p+1; columns q, q+1) of one subaperture
     const int n = W.n, nn = n * n, nb = (n + 1) >> 1, nbb = nb * nb;
     const int blk = ((int)blockIdx.x - W.proj_block_begin) * kProjThreads + threadIdx.x;
@@ -77,7 +209,6 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
         yr[j] = (float)(sy * n + p0 + j) - half;
     }
     float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    const bool pow2 = (S & (S - 1)) == 0;
     for (int l = 0; l < I.n_layers; ++l) {
         const float ch = s_c[l], cl = s_cl[l];
         const float *scr = D.screens + (size_t)l * S * S;
@@ -139,22 +270,60 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
             if (p0 + a2 < n && q0 + b2 < n) opd[(p0 + a2) * n + q0 + b2] = acc[a2][b2];
 }
 
-int project_blocks(int n_valid, int n) {
-    const int nb = (n + 1) / 2;
-    return (n_valid * nb * nb + kProjThreads - 1) / kProjThreads;
+int segment_max_count(int n) {
+    const int c = kTilePixels / (n * n);
+    return c < 1 ? 1 : c;
+}
+
+int project_blocks(const WfsDesc &d) {
+    if (d.tiled) return d.n_segs;
+    const int nb = (d.n + 1) / 2;
+    return (d.n_valid * nb * nb + kProjThreads - 1) / kProjThreads;
+}
+
+int project_box_floats(const WfsDesc &d) {
+    if (!d.tiled) return 0;
+    // two sets of coordinate tables (2 x (ncol + n) float2) and two boxes of at most
+    // (ncol + 2) x (n + 2) screen pixels (one per layer in flight)
+    return 4 * (d.seg_cols + d.n) + 4 + 2 * ((d.seg_cols + 9) * (d.n + 3) + 4);
+}
+
+void build_segments(const std::vector<int32_t> &ids, int n_sub, int max_count, std::vector<int4> &segs,
+                    int *max_run) {
+    segs.clear();
+    *max_run = 0;
+    for (size_t v = 0; v < ids.size(); ++v) {
+        const int sy = ids[v] / n_sub, sx = ids[v] - sy * n_sub;
+        if (!segs.empty()) {
+            int4 &b = segs.back();
+            if (b.x == sy && b.w + b.z == sx && b.z < max_count) {
+                ++b.z;
+                if (b.z > *max_run) *max_run = b.z;
+                continue;
+            }
+        }
+        segs.push_back(make_int4(sy, (int)v, 1, sx));
+        if (*max_run < 1) *max_run = 1;
+    }
 }
 
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) {
     if (total_blocks <= 0) return cudaSuccess;
-    k_project<<<total_blocks, kProjThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    LaunchShape sh;
+    cudaError_t e = project_launch_shape(a, total_blocks, &sh);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
 }
 
-cudaError_t project_launch_shape(int total_blocks, LaunchShape *out) {
+cudaError_t project_launch_shape(const ProjArgs &a, int total_blocks, LaunchShape *out) {
+    const size_t smem = (size_t)a.box_cap * sizeof(float) + (a.box_cap ? 64 : 0);
+    cudaError_t e = cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     out->func = (const void *)k_project;
     out->grid = dim3(total_blocks > 0 ? total_blocks : 1);
     out->block = dim3(kProjThreads);
-    out->smem = 0;
+    out->smem = smem;
     return cudaSuccess;
 }
 

@@ -280,8 +280,10 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
     h_pa.wfs = d_wfs;
     h_pa.n_wfs = 1;
     h_pa.n_inst = 1;
+    h_pa.box_cap = 0;  // direct gathers: no projection tiles in the static scratch
+    h_pa.status = (int *)(base + o_status);
     h_pa.dyn[0] = dyn;
-    if ((e = launch_project(h_pa, project_blocks(nv, n), s)) != cudaSuccess)
+    if ((e = launch_project(h_pa, project_blocks(h_wfs), s)) != cudaSuccess)
         return st_fail(WFS_ECUDA, "wfs_measure_one_static: projection launch");
 
     memset(&h_sa, 0, offsetof(ShArgs, dyn));
