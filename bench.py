@@ -244,7 +244,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"],
+                    help="DFT arithmetic of the LGS geometry for the headline (the other is timed beside it)")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-traffic measurement")
@@ -387,6 +388,31 @@ def main():
             "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in ktimes.items()},
             "gpu_launches": int(sum(v[0] for v in ktimes.values())),
             "roofline": roof, "e2e": e2e, "clocks": clk, "wall_s_timed": wall}
+    # the other DFT precision, timed the same way on the same inputs (comparison path)
+    other = "fp32" if args.precision == "bf16x3" else "bf16x3"
+    w2 = native.Wfs(inputs.config3(inputs.PREC_FP32 if other == "fp32" else inputs.PREC_BF16X3),
+                    seed=cfg.seed + rank, noise=True)
+    k2 = min(args.steps, 300)
+    for k in range(3):
+        native.wfs_measure(w2.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
+    native.wfs_timing_enable(w2.h, True)
+    native.wfs_timing_read(w2.h)
+    torch.cuda.synchronize()
+    ms2 = 0.0
+    for k in range(k2):
+        if args.flush_mb:
+            flush.fill_(float(k))
+        ev0[k].record(stream)
+        native.wfs_measure(w2.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    ms2 = sum(a.elapsed_time(b) for a, b in zip(ev0[:k2], ev1[:k2]))
+    kt2 = native.wfs_timing_read(w2.h)
+    w2.close()
+    line[f"{other}_path"] = {"value": spots * k2 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / k2,
+                             "steps": k2, "dft_precision": other,
+                             "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])}
+                                         for k, v in kt2.items()}}
     if not args.no_served:
         line["served"] = served()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

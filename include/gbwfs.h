@@ -193,9 +193,11 @@ wfs_status wfs_measure_stages(wfs_handle h, const float *screens, double t_s,
  * wfs_measure_host -- the same frame with HOST buffers: copies screens_host
  * (host, same layout as `screens`; pinned memory for asynchronous copies) to
  * the device, measures, and copies the slopes back to slopes_host.  The first
- * call allocates the device staging buffers (screens and slopes) that later
- * calls reuse.  Asynchronous on `stream`: slopes_host is valid after the
- * stream is synchronised.
+ * call allocates two sets of device staging buffers (screens and slopes) and a
+ * copy stream that later calls reuse: successive calls alternate between the
+ * sets and upload on the copy stream, so the next frame's upload overlaps this
+ * frame's kernels.  Asynchronous on `stream`: slopes_host is valid, and
+ * screens_host may be reused, after the stream is synchronised.
  */
 wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
                             float *slopes_host, void *stream);

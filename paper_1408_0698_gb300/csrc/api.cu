@@ -88,8 +88,12 @@ struct wfs_ctx {
     size_t opd_total = 0, int_total = 0, det_total = 0;
     int total_valid = 0;
     int *d_status = nullptr;
-    float *d_screens_stage = nullptr;
-    float *d_slopes_stage = nullptr;
+    // host-buffer path: two staging buffer sets used alternately, uploads on a copy stream
+    float *d_screens_stage[2] = {nullptr, nullptr};
+    float *d_slopes_stage[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+    unsigned long long host_calls = 0;
     cudaStream_t last_stream = nullptr;
     std::string err;
     // side streams for the spot launches of the second and later geometries
@@ -279,8 +283,13 @@ void release(wfs_ctx *h) {
     cudaFree(h->d_status);
     cudaFree(h->d_inst);
     cudaFree(h->d_wfs);
-    cudaFree(h->d_screens_stage);
-    cudaFree(h->d_slopes_stage);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->d_screens_stage[i]);
+        cudaFree(h->d_slopes_stage[i]);
+        if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+        if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     h->ev.clear();
     for (cudaStream_t st : h->side) cudaStreamDestroy(st);
@@ -740,20 +749,34 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
     if (!screens_host || !slopes_host) return fail(h, WFS_EINVAL, "null host buffer");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nscr = (size_t)h->n_layers * h->S * h->S;
+    const size_t nsl = 2 * (size_t)h->total_valid;
     cudaError_t e;
-    if (!h->d_screens_stage) {
-        if ((e = cudaMalloc(&h->d_screens_stage, nscr * sizeof(float))) != cudaSuccess)
-            return cuda_fail(h, e, "screen staging allocation");
-        if ((e = cudaMalloc(&h->d_slopes_stage, (2 * (size_t)h->total_valid + 1) * sizeof(float))) != cudaSuccess)
-            return cuda_fail(h, e, "slope staging allocation");
+    if (!h->d_screens_stage[0]) {
+        for (int i = 0; i < 2; ++i)
+            if ((e = cudaMalloc(&h->d_screens_stage[i], nscr * sizeof(float))) != cudaSuccess ||
+                (e = cudaMalloc(&h->d_slopes_stage[i], (nsl + 1) * sizeof(float))) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(h, e, "host-path staging allocation");
+        if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(h, e, "host-path copy stream");
     }
-    if ((e = cudaMemcpyAsync(h->d_screens_stage, screens_host, nscr * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    const int i = (int)(h->host_calls & 1);
+    // the staging set is free once the frame that used it two calls ago has finished
+    if (h->host_calls >= 2 && (e = cudaStreamWaitEvent(h->copy_stream, h->ev_done[i], 0)) != cudaSuccess)
+        return cuda_fail(h, e, "host-path wait");
+    if ((e = cudaMemcpyAsync(h->d_screens_stage[i], screens_host, nscr * sizeof(float), cudaMemcpyHostToDevice,
+                             h->copy_stream)) != cudaSuccess ||
+        (e = cudaEventRecord(h->ev_copied[i], h->copy_stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, h->ev_copied[i], 0)) != cudaSuccess)
         return cuda_fail(h, e, "screen upload");
-    wfs_status st = measure_impl(h, h->d_screens_stage, t_s, h->d_slopes_stage, nullptr, s);
+    wfs_status st = measure_impl(h, h->d_screens_stage[i], t_s, h->d_slopes_stage[i], nullptr, s);
     if (st != WFS_OK) return st;
-    if ((e = cudaMemcpyAsync(slopes_host, h->d_slopes_stage, 2 * (size_t)h->total_valid * sizeof(float),
-                             cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(slopes_host, h->d_slopes_stage[i], nsl * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaEventRecord(h->ev_done[i], s)) != cudaSuccess)
         return cuda_fail(h, e, "slope download");
+    ++h->host_calls;
     return WFS_OK;
 }
 

@@ -341,3 +341,21 @@ def test_bounded_wait_reports_timeout_without_fault():
     gpu, _ = run_library(cfg, scr, 0.0, handle=w)
     assert np.all(np.isfinite(gpu[0]["slopes"]))
     w.close()
+
+
+def test_host_path_alternating_buffers():
+    """Successive host-buffer calls alternate staging buffers and overlap uploads with the
+    previous frame; each result equals the device path at its own time."""
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    w = native.Wfs(cfg, seed=5, noise=True)
+    host_scr = torch.as_tensor(scr).pin_memory()
+    outs = [torch.empty((w.total, 2)).pin_memory() for _ in range(5)]
+    ts = [0.001 * k for k in range(5)]
+    for t, o in zip(ts, outs):
+        native.wfs_measure_host(w.h, host_scr.data_ptr(), t, o.data_ptr(), 0)
+    torch.cuda.synchronize()
+    for t, o in zip(ts, outs):
+        ref, _ = run_library(cfg, scr, t, seed=5, noise=True, stages=False, handle=w)
+        assert np.array_equal(o.numpy(), np.concatenate([d["slopes"] for d in ref]))
+    w.close()
