@@ -294,7 +294,10 @@ static float log_factorial(float k)
 }
 
 /* Poisson(E) in FP32: sequential-search inversion for E < 16, Hormann's
-   transformed rejection (PTRS, 1993) for E >= 16. */
+   transformed rejection (PTRS, 1993) for E >= 16.  The inversion recurrence
+   p_k = p_{k-1} E / k is evaluated as (p_{k-1} E) (1/k), 1/k rounded to nearest:
+   three IEEE roundings in a fixed order.  For E < 16 the search stops before
+   k = 43 even at the largest uniform the stream yields. */
 static int32_t poisson_f32(float E, ustream *s)
 {
     if (!(E > 0.0f)) return 0;
@@ -305,7 +308,7 @@ static int32_t poisson_f32(float E, ustream *s)
         int32_t k = 0;
         while (u > F) {
             k = k + 1;
-            p = p * E / (float)k;
+            p = (p * E) * (1.0f / (float)k);
             float Fn = F + p;
             if (Fn == F) break;
             F = Fn;

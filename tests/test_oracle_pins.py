@@ -357,6 +357,29 @@ def test_poisson_moments(E):
     assert chi2 < keep.sum() + 6 * math.sqrt(2 * keep.sum()) + 10
 
 
+def test_inversion_search_length_bound():
+    """The inversion recurrence (p E)(1/k) in FP32 ends (u <= F or F stops growing) before
+    k = 43 for every E < 16, even at the largest uniform ((2^23 - 1 + 1/2) 2^-23): the
+    spot kernels keep 1/k in a 64-entry table."""
+    f = np.float32
+    umax = f((float((1 << 23) - 1) + 0.5) / 8388608.0)
+
+    def search(E):
+        p = f(math.exp(-float(E)))
+        F, k = p, 0
+        while umax > F:
+            k += 1
+            p = f(f(p * E) * f(f(1.0) / f(k)))
+            Fn = f(F + p)
+            if Fn == F:
+                break
+            F = Fn
+        return k
+
+    Es = list(np.linspace(0.01, 15.999, 1600).astype(np.float32)) + [np.nextafter(f(16), f(0))]
+    assert max(search(E) for E in Es) <= 42
+
+
 def test_read_noise_gaussian():
     n = 50000
     C, K = oracle.noise_image(np.zeros(n, np.float32), 3.0, 5, 2, 0.0)
