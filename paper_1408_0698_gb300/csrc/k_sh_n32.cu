@@ -40,7 +40,8 @@ struct N32Layout {
     static constexpr int oGam = oFm + N * n;       // [m][dx]  Ga[dx][m]    (broadcast rows)
     static constexpr int oGak = oGam + N * n;      // [dyi][GAK] Ga(dy, k), conjugated for dy < 0
     static constexpr int oG = oGak + (2 * n - 1) * GAK;  // [d][nd]  G[d][i]
-    static constexpr int table = oG + n * nd;
+    static constexpr int oRk = oG + n * nd;         // RN(1/k) for the Poisson inversion (floats)
+    static constexpr int table = oRk + kRecipTable / 2;
     // per-warp scratch (float2 units)
     static constexpr int wX = 0;                   // [p][q]
     static constexpr int wTa = wX + n * n;         // [k][NO]
@@ -73,6 +74,8 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         if (d > 0) Gak[(n - 1 - d) * GAK + k] = make_float2(g.x, -g.y);  // dy = -d
     }
     for (int i = threadIdx.x; i < n * nd; i += blockDim.x) Gt[i] = a.G[i];
+    float *rk = reinterpret_cast<float *>(sm2 + Lay::oRk);
+    fill_recip_table(rk, threadIdx.x, blockDim.x);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             __syncwarp();
             tail::ngs_binned<nd>(Iw, lane, Bv);
         }
-        tail::finish<nd>(Bv, W, D, seed, v, lane);
+        tail::finish<nd>(Bv, W, D, seed, v, lane, rk);
     }
 }
 

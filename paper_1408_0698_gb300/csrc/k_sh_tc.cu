@@ -150,7 +150,8 @@ struct TcLayout {
     static constexpr int tFk = 0;                  // [p][k]  F[k][p]
     static constexpr int tGak = tFk + n * N;       // [dyi][GAK] Ga(dy, k), conjugated rows for dy < 0
     static constexpr int tG = tGak + D2 * GAK;     // [d][nd] G[d][i]
-    static constexpr int tEnd = tG + n * nd;
+    static constexpr int tRk = tG + n * nd;       // RN(1/k) for the Poisson inversion (floats)
+    static constexpr int tEnd = tRk + kRecipTable / 2;
     static constexpr int oWarp = oTab + tEnd * 8;  // per-warp scratch (float2)
     // the NGS image rows (wI) alias the LGS transfer-domain scratch (wTa, wM)
     static constexpr int wX = 0, wTa = wX + n * n, wM = wTa + N * NO, wI = wTa;
@@ -175,6 +176,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     uint8_t *sA1 = smem + Lay::oA + 16384 * wg, *sA2 = sA1;
     float2 *tab = reinterpret_cast<float2 *>(smem + Lay::oTab);
     float2 *Fk = tab + Lay::tFk, *Gak = tab + Lay::tGak, *Gt = tab + Lay::tG;
+    float *rk = reinterpret_cast<float *>(tab + Lay::tRk);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + 32 * wg);
     int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 32 * wg + 16);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + 32 * kWG);
@@ -201,6 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             Gak[dyi * GAK + k] = g;
         }
         for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
+        fill_recip_table(rk, tid, kTcThreads);
     }
     if (wib == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             tail::lgs_binned<n, nd, NO, GAK>(Ta, Mw, Ta, Gak, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
         else
             tail::ngs_binned<nd>(Iw, lane, Bv);
-        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane);
+        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk);
     }
     fence_before_sync();
     __syncthreads();

@@ -12,48 +12,67 @@
 // Box-Muller read noise; the Poisson sampler starts at its third word and
 // continues with blocks 1, 2, ...
 //
-// Poisson: sequential-search inversion for E < 16; above, Hormann's
-// transformed rejection with squeeze (PTRS, "The transformed rejection method
-// for generating Poisson random variables", 1993).  The integer decisions are
-// taken in FP32 with explicitly rounded operations (no contraction), so the
-// operation order is fixed.
+// Poisson: sequential-search inversion for E < 16 with the recurrence
+// p_k = (p_{k-1} E) * RN(1/k); above, Hormann's transformed rejection with
+// squeeze (PTRS, "The transformed rejection method for generating Poisson
+// random variables", 1993).  The integer decisions are taken in FP32 with
+// explicitly rounded operations (no contraction), so the operation order is
+// fixed.  For E < 16 the search stops before k = 43 even at the largest
+// uniform, so RN(1/k) fits a 64-entry table.
+//
+// Everything here works on values: no generator object lives in memory, so a
+// warp can run the generator blocks of several pixels side by side.
 #pragma once
 #include <stdint.h>
 
 namespace gbwfs {
 
-struct Philox {
-    uint32_t k0, k1, c0, c1, c2, c3;
-    uint32_t r[4];
-    int pos;
+constexpr int kRecipTable = 64;  // RN(1/k), k < 64 (entry 0 unused)
 
-    __device__ __forceinline__ void block(uint32_t b) {
-        uint32_t x0 = c0, x1 = (c1 & 0xFFFF0000u) | (b & 0xFFFFu), x2 = c2, x3 = c3;
-        c1 = x1;
-        uint32_t a0 = k0, a1 = k1;
+// Philox4x32-10 of counter (x0, x1, x2, x3) under key (k0, k1).
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t x0, uint32_t x1, uint32_t x2, uint32_t x3,
+                                               uint32_t k0, uint32_t k1) {
 #pragma unroll
-        for (int i = 0; i < 10; ++i) {
-            uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
-            uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
-            uint32_t y0 = hi1 ^ x1 ^ a0, y2 = hi0 ^ x3 ^ a1;
-            x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
-            a0 += 0x9E3779B9u;
-            a1 += 0xBB67AE85u;
-        }
-        r[0] = x0; r[1] = x1; r[2] = x2; r[3] = x3;
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        const uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
     }
-    __device__ __forceinline__ static float unit(uint32_t x) {
-        // 23 random bits plus one half: exact in FP32, strictly inside (0, 1)
-        return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
-    }
-    __device__ __forceinline__ float next() {
-        if (pos == 4) {
-            block((c1 & 0xFFFFu) + 1u);
-            pos = 0;
-        }
-        return unit(r[pos++]);
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// 23 random bits plus one half: exact in FP32, strictly inside (0, 1).
+__device__ __forceinline__ float philox_unit(uint32_t x) {
+    return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// The stream of one detector pixel.
+struct PixelStream {
+    uint32_t k0, k1, pixel, wfs, tlo, thi;
+    __device__ __forceinline__ uint4 block(uint32_t b) const {
+        return philox4x32_10(pixel, (wfs << 16) | (b & 0xFFFFu), tlo, thi, k0, k1);
     }
 };
+
+__device__ __forceinline__ PixelStream pixel_stream(uint64_t seed, uint32_t pixel, uint32_t wfs,
+                                                    uint32_t tlo, uint32_t thi) {
+    PixelStream q;
+    q.k0 = (uint32_t)seed;
+    q.k1 = (uint32_t)(seed >> 32);
+    q.pixel = pixel;
+    q.wfs = wfs;
+    q.tlo = tlo;
+    q.thi = thi;
+    return q;
+}
+
+// Read-noise deviate from block 0's first two words.
+__device__ __forceinline__ float box_muller(uint32_t w0, uint32_t w1) {
+    return sqrtf(-2.0f * logf(philox_unit(w0))) * cospif(2.0f * philox_unit(w1));
+}
 
 __device__ __forceinline__ float log_factorial_f32(float k) {
     if (k < 10.0f) {
@@ -68,22 +87,39 @@ __device__ __forceinline__ float log_factorial_f32(float k) {
     return __fadd_rn(__fadd_rn(v, 0.918938533f), corr);
 }
 
-static __device__ __noinline__ int poisson_f32(float E, Philox &g) {
-    if (!(E > 0.0f)) return 0;
-    if (E < 16.0f) {
-        float u = g.next();
-        float p = expf(-E);
-        float F = p;
-        int k = 0;
-        while (u > F) {
-            k = k + 1;
-            p = __fdiv_rn(__fmul_rn(p, E), (float)k);
-            float Fn = __fadd_rn(F, p);
-            if (Fn == F) break;
-            F = Fn;
-        }
-        return k;
+// Inversion for 0 < E < 16 with the first Poisson uniform u and p0 = exp(-E).  With
+// TAB, rk[k] holds RN(1/k) (k < kRecipTable); otherwise 1/k is rounded on the spot.
+template <bool TAB>
+__device__ __forceinline__ int poisson_inversion(float E, float u, float p0, const float *rk) {
+    float p = p0, F = p0;
+    int k = 0;
+    while (u > F) {
+        k = k + 1;
+        const float r = TAB ? rk[min(k, kRecipTable - 1)] : __frcp_rn((float)k);
+        p = __fmul_rn(__fmul_rn(p, E), r);
+        const float Fn = __fadd_rn(F, p);
+        if (Fn == F) break;
+        F = Fn;
     }
+    return k;
+}
+
+// PTRS for E >= 16: draws words 2 and 3 of block 0, then blocks 1, 2, ...  Rare for the
+// workloads here, so it recomputes block 0 rather than keep it live.  Inlined: callers give
+// it a single call site (an out-of-line call would make every live register a spill).
+__device__ __forceinline__ int poisson_ptrs(float E, PixelStream q) {
+    uint4 buf = q.block(0);
+    uint32_t blk = 0;
+    int pos = 2;
+    auto next = [&]() {
+        if (pos == 4) {
+            buf = q.block(++blk);
+            pos = 0;
+        }
+        const uint32_t w = pos == 0 ? buf.x : pos == 1 ? buf.y : pos == 2 ? buf.z : buf.w;
+        ++pos;
+        return philox_unit(w);
+    };
     float slam = __fsqrt_rn(E);
     float logE = logf(E);
     float b = __fadd_rn(0.931f, __fmul_rn(2.53f, slam));
@@ -91,8 +127,8 @@ static __device__ __noinline__ int poisson_f32(float E, Philox &g) {
     float inv_alpha = __fadd_rn(1.1239f, __fdiv_rn(1.1328f, __fsub_rn(b, 3.4f)));
     float vr = __fsub_rn(0.9277f, __fdiv_rn(3.6224f, __fsub_rn(b, 2.0f)));
     for (int tries = 0; tries < 1024; ++tries) {
-        float U = __fsub_rn(g.next(), 0.5f);
-        float V = g.next();
+        float U = __fsub_rn(next(), 0.5f);
+        float V = next();
         float us = __fsub_rn(0.5f, fabsf(U));
         float t1 = __fadd_rn(__fdiv_rn(__fmul_rn(2.0f, a), us), b);
         float kf = floorf(__fadd_rn(__fadd_rn(__fmul_rn(t1, U), E), 0.43f));
@@ -106,23 +142,28 @@ static __device__ __noinline__ int poisson_f32(float E, Philox &g) {
     return (int)floorf(E);
 }
 
+// Poisson count of a pixel whose block 0 gave the inversion uniform u (word 2).
+template <bool TAB>
+__device__ __forceinline__ int poisson_count(float E, float u, float p0, const PixelStream &q,
+                                             const float *rk) {
+    if (!(E > 0.0f)) return 0;
+    if (E < 16.0f) return poisson_inversion<TAB>(E, u, p0, rk);
+    return poisson_ptrs(E, q);
+}
+
 // One detector pixel: Poisson photon count plus Gaussian read noise.
 __device__ __forceinline__ float noise_pixel(float E, float read_noise, uint64_t seed,
                                              uint32_t pixel, uint32_t wfs, uint32_t tlo,
                                              uint32_t thi) {
-    Philox g;
-    g.k0 = (uint32_t)seed;
-    g.k1 = (uint32_t)(seed >> 32);
-    g.c0 = pixel;
-    g.c1 = wfs << 16;
-    g.c2 = tlo;
-    g.c3 = thi;
-    g.block(0);
-    float u1 = Philox::unit(g.r[0]), u2 = Philox::unit(g.r[1]);
-    g.pos = 2;
-    int k = poisson_f32(E, g);
-    float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-    return (float)k + read_noise * z;
+    const PixelStream q = pixel_stream(seed, pixel, wfs, tlo, thi);
+    const uint4 r = q.block(0);
+    const int k = poisson_count<false>(E, philox_unit(r.z), expf(-E), q, nullptr);
+    return (float)k + read_noise * box_muller(r.x, r.y);
+}
+
+// Fills rk[0 .. kRecipTable) with RN(1/k) (entry 0 = 1); call from every thread of the block.
+__device__ __forceinline__ void fill_recip_table(float *rk, int tid, int nthreads) {
+    for (int i = tid; i < kRecipTable; i += nthreads) rk[i] = __frcp_rn((float)(i > 0 ? i : 1));
 }
 
 }  // namespace gbwfs

@@ -118,16 +118,20 @@ __device__ __forceinline__ void ngs_binned(const float *Iw, int lane, float (&Bv
 }
 
 // Photometry, noise and the centroid of subaperture v of WFS W; lane 0 writes the slopes.
+// rk: RN(1/k) table (fill_recip_table) in shared memory.  The generator blocks and
+// read-noise deviates of a lane's nd/2 pixels are formed first, side by side; the
+// inversion searches follow, and the rare pixels with E >= 16 go last through one PTRS
+// call site.
 template <int nd>
 __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc &W, const InstDyn &D,
-                                       uint64_t seed, int v, int lane) {
-    constexpr int nd2 = nd * nd;
+                                       uint64_t seed, int v, int lane, const float *rk) {
+    constexpr int nd2 = nd * nd, J = nd / 2;
     const int ix = lane & 15, half = lane >> 4;
     const float cd = 0.5f * (float)(nd - 1);
     float sb = 0.0f;
     if (ix < nd) {
 #pragma unroll
-        for (int j = 0; j < nd / 2; ++j) sb += Bv[j];
+        for (int j = 0; j < J; ++j) sb += Bv[j];
     }
     sb = warp_sum(sb);
     const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
@@ -137,18 +141,60 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
     float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
     float sc = 0.0f, sx = 0.0f, sy = 0.0f;
     if (ix < nd) {
+        float cv[J];
+        if (D.noise) {
+            const uint32_t pix0 = (uint32_t)(v * nd2 + half * J * nd + ix);
+            const PixelStream q0 = pixel_stream(seed, pix0, (uint32_t)W.gs_index, tlo, thi);
+            float z[J], u[J];
 #pragma unroll
-        for (int j = 0; j < nd / 2; ++j) {
-            const int iy = half * (nd / 2) + j, o = iy * nd + ix;
-            const float e = scale * Bv[j];
-            const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o),
-                                                  (uint32_t)W.gs_index, tlo, thi)
-                                    : e;
-            if (st_E) st_E[(size_t)v * nd2 + o] = e;
-            if (st_C) st_C[(size_t)v * nd2 + o] = c;
-            sc += c;
-            sx = fmaf((float)ix - cd, c, sx);
-            sy = fmaf((float)iy - cd, c, sy);
+            for (int j = 0; j < J; ++j) {
+                PixelStream q = q0;
+                q.pixel = pix0 + (uint32_t)(j * nd);
+                const uint4 r = q.block(0);
+                z[j] = box_muller(r.x, r.y);
+                u[j] = philox_unit(r.z);
+            }
+            // inversion for E < 16; pixels at or above it are marked and sampled below
+            uint32_t big = 0;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const float e = scale * Bv[j];
+                int k = 0;
+                if (e >= 16.0f)
+                    big |= 1u << j;
+                else if (e > 0.0f)
+                    k = poisson_inversion<true>(e, u[j], expf(-e), rk);
+                cv[j] = (float)k + W.read_noise * z[j];
+            }
+            while (big) {  // PTRS: one call site, rare
+                const int j = __ffs(big) - 1;
+                big &= big - 1;
+                float e = 0.0f, zj = 0.0f;
+#pragma unroll
+                for (int jj = 0; jj < J; ++jj)
+                    if (jj == j) {
+                        e = scale * Bv[jj];
+                        zj = z[jj];
+                    }
+                PixelStream q = q0;
+                q.pixel = pix0 + (uint32_t)(j * nd);
+                const float c = (float)poisson_ptrs(e, q) + W.read_noise * zj;
+#pragma unroll
+                for (int jj = 0; jj < J; ++jj)
+                    if (jj == j) cv[jj] = c;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < J; ++j) cv[j] = scale * Bv[j];
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int iy = half * J + j, o = iy * nd + ix;
+            if (st_E) st_E[(size_t)v * nd2 + o] = scale * Bv[j];
+            if (st_C) st_C[(size_t)v * nd2 + o] = cv[j];
+            sc += cv[j];
+            sx = fmaf((float)ix - cd, cv[j], sx);
+            sy = fmaf((float)iy - cd, cv[j], sy);
         }
     }
     sc = warp_sum(sc);
