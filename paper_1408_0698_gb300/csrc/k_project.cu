@@ -78,21 +78,20 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
         // per-row tables (a pixel's screen column depends on its pupil column only)
         extern __shared__ float psm[];
         const int4 sg = W.segs[(int)blockIdx.x - W.proj_block_begin];  // sy, v_first, count, sx0
-        const int n = W.n, nn = n * n, ncol = sg.z * n, npx = sg.z * nn;
+        const int n = W.n, nn = n * n, ncol = sg.z * n;
         const int box_floats = ((a.box_cap - ((4 * (ncol + n) + 3) & ~3)) / 2) & ~3;
         float2 *tab[2] = {reinterpret_cast<float2 *>(psm), reinterpret_cast<float2 *>(psm) + (ncol + n)};
         const int box_off = (4 * (ncol + n) + 3) & ~3;  // 16-byte aligned boxes
         float *boxb[2] = {psm + box_off, psm + box_off + (box_floats & ~3)};
         const float half = 0.5f * (float)(W.n_sub * n - 1);
-        int pj[kTilePx];
+        // thread -> (pupil row p, columns ch + k nch, k < kTilePx): lanes of a warp take
+        // consecutive columns of one row, so their table and box reads fall in distinct banks
+        const int nch = (ncol + kTilePx - 1) / kTilePx, ntask = n * nch;  // ntask <= kProjThreads
+        const bool has_task = (int)threadIdx.x < ntask;
+        const int p = has_task ? (int)threadIdx.x / nch : 0, ch = (int)threadIdx.x - p * nch;
         float acc[kTilePx];
 #pragma unroll
-        for (int k = 0; k < kTilePx; ++k) {
-            const int px = threadIdx.x + k * kProjThreads;
-            const int v = px / nn, rr = px - v * nn, p = rr / n, q = rr - p * n;
-            pj[k] = px < npx ? (p << 16) | (v * n + q) : -1;
-            acc[k] = 0.0f;
-        }
+        for (int k = 0; k < kTilePx; ++k) acc[k] = 0.0f;
         auto tables = [&](int l, float2 *t) {
             const float ch = s_c[l], cl = s_cl[l];
             for (int j = threadIdx.x; j < ncol + n; j += kProjThreads) {
@@ -126,13 +125,16 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
             if (bw * bh > box_floats) return false;
             const float *scr = D.screens + (size_t)l * S * S;
             if (vec) {
-                const int cw = bw >> 2;  // 16-byte chunks per box row
-                for (int idx = threadIdx.x; idx < cw * bh; idx += kProjThreads) {
-                    const int r = idx / cw, c4 = idx - r * cw;
-                    const float *src = scr + (size_t)wrap_index(s_bv[l] + by0 + r, S, pow2) * S +
-                                       wrap_index(s_bu[l] + bx0 + 4 * c4, S, pow2);
-                    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(box + r * bw + 4 * c4);
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                // one warp per box row, one lane per 16-byte chunk
+                const int cw = bw >> 2, lane = threadIdx.x & 31, cbase = s_bu[l] + bx0;
+                for (int r = threadIdx.x >> 5; r < bh; r += kProjThreads / 32) {
+                    const float *srow = scr + (size_t)wrap_index(s_bv[l] + by0 + r, S, pow2) * S;
+                    float *drow = box + r * bw;
+                    for (int c4 = lane; c4 < cw; c4 += 32) {
+                        const float *src = srow + wrap_index(cbase + 4 * c4, S, pow2);
+                        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(drow + 4 * c4);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                    }
                 }
             } else {
                 for (int r = 0; r < bh; ++r) {
@@ -167,28 +169,42 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
             const float *box = boxb[cur];
             int bx0, by0, bw, bh;
             box_geom(l, t, bx0, by0, bw, bh);
+            if (has_task) {
+                const float2 rp = t[ncol + p];
+                const float *brow = box + (__float_as_int(rp.x) - by0) * bw - bx0;
 #pragma unroll
-            for (int k = 0; k < kTilePx; ++k) {
-                if (pj[k] < 0) continue;
-                const int j = pj[k] & 0xFFFF, p = pj[k] >> 16;
-                const float2 cj = t[j], rp = t[ncol + p];
-                const int ci = __float_as_int(cj.x) - bx0, ri = __float_as_int(rp.x) - by0;
-                const float *b0 = box + ri * bw + ci;
-                const float s00 = b0[0], s01 = b0[1], s10 = b0[bw], s11 = b0[bw + 1];
-                const float top = fmaf(cj.y, s01 - s00, s00);
-                const float bot = fmaf(cj.y, s11 - s10, s10);
-                acc[k] += fmaf(rp.y, bot - top, top);
+                for (int k = 0; k < kTilePx; ++k) {
+                    const int j = ch + k * nch;
+                    if (j < ncol) {
+                        const float2 cj = t[j];
+                        const float *b0 = brow + __float_as_int(cj.x);
+                        const float s00 = b0[0], s01 = b0[1], s10 = b0[bw], s11 = b0[bw + 1];
+                        const float top = fmaf(cj.y, s01 - s00, s00);
+                        const float bot = fmaf(cj.y, s11 - s10, s10);
+                        acc[k] += fmaf(rp.y, bot - top, top);
+                    }
+                }
             }
             __syncthreads();  // this layer's tables and box are free for layer l + 2
             fits = fits_next;
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         if (!fits && threadIdx.x == 0 && a.status) atomicCAS(a.status, 0, 6 /* WFS_EUNSUPPORTED */);
-        float *opd = D.opd + W.opd_off + (size_t)sg.y * nn;
+        if (has_task) {
+            // column j = v n + q of the segment -> subaperture v, column q; j advances by nch
+            float *opd = D.opd + W.opd_off + (size_t)sg.y * nn + p * n;
+            const int dv = nch / n, dq = nch - dv * n;
+            int v = ch / n, q = ch - v * n;
 #pragma unroll
-        for (int k = 0; k < kTilePx; ++k) {
-            const int px = threadIdx.x + k * kProjThreads;
-            if (px < npx) opd[px] = acc[k];
+            for (int k = 0; k < kTilePx; ++k) {
+                if (ch + k * nch < ncol) opd[v * nn + q] = acc[k];
+                q += dq;
+                v += dv;
+                if (q >= n) {
+                    q -= n;
+                    ++v;
+                }
+            }
         }
         return;
     }
@@ -271,8 +287,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
 }
 
 int segment_max_count(int n) {
-    const int c = kTilePixels / (n * n);
-    return c < 1 ? 1 : c;
+    // a segment of c subaperture columns has n rows x ceil(c n / kTilePx) column sets, one
+    // per thread
+    int c = 1;
+    while (n * (((c + 1) * n + kTilePx - 1) / kTilePx) <= kProjThreads) ++c;
+    return c;
 }
 
 int project_blocks(const WfsDesc &d) {
