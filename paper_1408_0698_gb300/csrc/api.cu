@@ -435,7 +435,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.n_inst = 1;
         sa.dyn[0] = dyn;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
-        cudaError_t err = launch_spot(G.kind, sa, ls);
+        cudaError_t err = launch_spot(G.kind, sa, ls, ls == stream && h->proj_blocks > 0 && !h->timing);
         timed_end(h, sl, ls);
         return err;
     };

@@ -111,6 +111,12 @@ __device__ __forceinline__ int find_wfs(const WfsDesc *w, int n, int g) {
 #endif
 
 // A launch as a graph kernel node: function, grid, block, dynamic shared memory.
+// Programmatic dependent launch: the projection lets the next grid on its stream start
+// early; a spot kernel blocks here until the preceding grid has completed and its writes are
+// visible (a no-op when the launch had no programmatic dependency).
+__device__ __forceinline__ void allow_dependent_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 struct LaunchShape {
     const void *func;
     dim3 grid, block;
@@ -139,7 +145,10 @@ bool sh_n32_supported(int n, int N, int nd);
 bool sh_tc_supported(int n, int N, int nd);
 // Shape of the launch (sets the kernel's dynamic shared-memory attribute).
 cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out);
-cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s);
+// after_project: the launch follows the projection on stream s and may start (prologue only)
+// before the projection has finished (programmatic dependent launch); the spot kernels wait
+// for the preceding grid to complete before they read its output.
+cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s, bool after_project = false);
 // Swizzled BF16 operand tiles of the two constant matrices (F^T blocks, Ga blocks),
 // from FP64 tables laid out [q][m] (F) and [d][k] (Ga).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,

@@ -33,6 +33,7 @@ __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
 }
 
 __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
+    allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
     __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
 

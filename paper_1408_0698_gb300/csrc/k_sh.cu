@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
     }
     for (int i = threadIdx.x; i < n * nd; i += blockDim.x) sG[i] = a.G[i];
     __syncthreads();
+    wait_prior_grid();
 
     const int team = threadIdx.x / TEAM, tid = threadIdx.x % TEAM;
     const int nteams = blockDim.x / TEAM;
@@ -299,13 +300,24 @@ cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out) {
     }
 }
 
-cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s) {
+cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s, bool after_project) {
     if (a.total <= 0) return cudaSuccess;
     LaunchShape sh;
     cudaError_t e = spot_launch_shape(kind, a, &sh);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&a};
-    return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
+    if (!after_project) return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = sh.grid;
+    cfg.blockDim = sh.block;
+    cfg.dynamicSmemBytes = sh.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, sh.func, args);
 }
 
 // ---------------------------------------------------------------------------

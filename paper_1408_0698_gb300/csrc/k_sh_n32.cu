@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float *rk = reinterpret_cast<float *>(sm2 + Lay::oRk);
     fill_recip_table(rk, threadIdx.x, blockDim.x);
     __syncthreads();
+    wait_prior_grid();
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float2 *X = sm2 + Lay::table + wib * Lay::warp + Lay::wX;

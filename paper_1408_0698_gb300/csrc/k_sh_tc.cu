@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem_all = *tslot;
+    wait_prior_grid();
     const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
     constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
