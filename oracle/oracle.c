@@ -259,13 +259,18 @@ static float unit_float(uint32_t x)
     return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
 }
 
+/* The uniforms of one pixel.  Pixels go in pairs (2m, 2m + 1) sharing block 0 of
+   counter (m, wfs << 16 | block, bits(t)); a pixel of parity s draws word 2 + s of
+   block 0 first, then all four words of blocks 1 + s, 3 + s, 5 + s, ... */
 typedef struct {
     uint32_t key[2], ctr[4], buf[4];
-    int pos;
+    int pos, parity;
+    uint32_t block;
 } ustream;
 
 static void us_block(ustream *s, uint32_t block)
 {
+    s->block = block;
     s->ctr[1] = (s->ctr[1] & 0xFFFF0000u) | (block & 0xFFFFu);
     orc_philox(s->ctr, s->key, s->buf);
 }
@@ -273,10 +278,12 @@ static void us_block(ustream *s, uint32_t block)
 static float us_next(ustream *s)
 {
     if (s->pos == 4) {
-        us_block(s, (s->ctr[1] & 0xFFFFu) + 1u);
+        us_block(s, s->block == 0 ? 1u + (uint32_t)s->parity : s->block + 2u);
         s->pos = 0;
     }
-    return unit_float(s->buf[s->pos++]);
+    float u = unit_float(s->buf[s->pos]);
+    s->pos = (s->block == 0) ? 4 : s->pos + 1;
+    return u;
 }
 
 /* log(k!) in FP32: exact sum of logs below 10, Stirling's series above. */
@@ -343,17 +350,20 @@ double orc_noise_pixel(float E, float read_noise, uint64_t seed, uint32_t pixel,
     memcpy(&tb, &t, sizeof tb);
     s.key[0] = (uint32_t)seed;
     s.key[1] = (uint32_t)(seed >> 32);
-    s.ctr[0] = pixel;
+    s.ctr[0] = pixel >> 1;
     s.ctr[1] = wfs << 16;
     s.ctr[2] = (uint32_t)tb;
     s.ctr[3] = (uint32_t)(tb >> 32);
+    s.parity = (int)(pixel & 1u);
     us_block(&s, 0);
-    /* draws 0 and 1 feed the read noise; the Poisson sampler starts at draw 2 */
-    float u1 = unit_float(s.buf[0]), u2 = unit_float(s.buf[1]);
-    s.pos = 2;
+    /* block 0: words 0 and 1 give the pair's two Box-Muller deviates (cos for the even
+       pixel, sin for the odd one); word 2 + parity starts this pixel's Poisson draws */
+    double r = sqrt(-2.0 * log((double)unit_float(s.buf[0])));
+    double th = 2.0 * M_PI * (double)unit_float(s.buf[1]);
+    double z = r * (s.parity ? sin(th) : cos(th));
+    s.pos = 2 + s.parity;
     int32_t k = poisson_f32(E, &s);
     if (k_out) *k_out = k;
-    double z = sqrt(-2.0 * log((double)u1)) * cos(2.0 * M_PI * (double)u2);
     return (double)k + (double)read_noise * z;
 }
 

@@ -68,7 +68,8 @@ void orc_convolve(int N, const double *I, const double *K, double *out);
 void orc_bin(int N, int nd, const double *I, double *B);
 /* Philox4x32-10 block function. */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
-/* One detector pixel's noisy count; *k_out receives the Poisson draw. */
+/* One detector pixel's noisy count; *k_out receives the Poisson draw.  Pixels 2m and 2m + 1
+   share Philox block 0 of counter m (read noise from its words 0-1, Poisson from word 2 or 3). */
 double orc_noise_pixel(float E, float read_noise, uint64_t seed, uint32_t pixel,
                        uint32_t wfs, double t, int32_t *k_out);
 void orc_noise_image(int n, const float *E, float read_noise, uint64_t seed, uint32_t wfs,

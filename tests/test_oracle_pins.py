@@ -380,6 +380,20 @@ def test_inversion_search_length_bound():
     assert max(search(E) for E in Es) <= 42
 
 
+@pytest.mark.parametrize("E", [3.0, 40.0])
+def test_poisson_pair_members_independent(E):
+    """Pixels 2m and 2m + 1 share one generator block (words 2 and 3 start their Poisson
+    draws; above E = 16 their continuation blocks interleave): their counts are
+    uncorrelated and equally distributed."""
+    n = 60000
+    C, K = oracle.noise_image(np.full(n, E, np.float32), 0.0, 17, 3, 0.125)
+    ke, ko = K[0::2].astype(float), K[1::2].astype(float)
+    assert abs(np.corrcoef(ke, ko)[0, 1]) < 0.02
+    se = math.sqrt(E / (n // 2))
+    assert abs(ke.mean() - E) < 5 * se and abs(ko.mean() - E) < 5 * se
+    assert not np.array_equal(ke, ko)
+
+
 def test_read_noise_gaussian():
     n = 50000
     C, K = oracle.noise_image(np.zeros(n, np.float32), 3.0, 5, 2, 0.0)
@@ -389,6 +403,13 @@ def test_read_noise_gaussian():
     # fourth moment of a Gaussian
     z = C / 3.0
     assert abs(np.mean(z ** 4) - 3) < 0.1
+    # the pair's two Box-Muller deviates (cos and sin of one angle): independent, and
+    # z_even^2 + z_odd^2 = -2 ln u is exponential with mean 2
+    ze, zo = z[0::2], z[1::2]
+    assert abs(np.corrcoef(ze, zo)[0, 1]) < 0.02
+    assert abs(ze.std() - 1) < 0.02 and abs(zo.std() - 1) < 0.02
+    r2 = ze ** 2 + zo ** 2
+    assert abs(r2.mean() - 2) < 0.05 and abs(np.median(r2) - 2 * math.log(2)) < 0.05
 
 
 def test_noise_is_counter_based():
