@@ -5,12 +5,13 @@
 //
 // Uniforms come from the counter-based generator Philox4x32-10 (Salmon,
 // Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11),
-// keyed by the 64-bit seed, with counter
-//   (pixel, wfs << 16 | block, low word of bits(t), high word of bits(t)),
+// keyed by the 64-bit seed.  Pixels go in pairs (2m, 2m + 1) that share the
+// counter (m, wfs << 16 | block, low word of bits(t), high word of bits(t)),
 // so a frame's noise depends only on (seed, t, wfs, pixel) and never on the
-// CTA, batch slot or launch that computes it.  Block 0's first two words feed
-// Box-Muller read noise; the Poisson sampler starts at its third word and
-// continues with blocks 1, 2, ...
+// CTA, batch slot or launch that computes it.  Block 0's words 0 and 1 give the
+// pair's two Box-Muller deviates (cos for the even pixel, sin for the odd one);
+// word 2 + parity starts the pixel's Poisson draws, which continue with blocks
+// 1 + parity, 3 + parity, ...
 //
 // Poisson: sequential-search inversion for E < 16 with the recurrence
 // p_k = (p_{k-1} E) * RN(1/k); above, Hormann's transformed rejection with
@@ -49,29 +50,33 @@ __device__ __forceinline__ float philox_unit(uint32_t x) {
     return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f);
 }
 
-// The stream of one detector pixel.
-struct PixelStream {
-    uint32_t k0, k1, pixel, wfs, tlo, thi;
+// The stream of one pixel pair.
+struct PairStream {
+    uint32_t k0, k1, pair, wfs, tlo, thi;
     __device__ __forceinline__ uint4 block(uint32_t b) const {
-        return philox4x32_10(pixel, (wfs << 16) | (b & 0xFFFFu), tlo, thi, k0, k1);
+        return philox4x32_10(pair, (wfs << 16) | (b & 0xFFFFu), tlo, thi, k0, k1);
     }
 };
 
-__device__ __forceinline__ PixelStream pixel_stream(uint64_t seed, uint32_t pixel, uint32_t wfs,
-                                                    uint32_t tlo, uint32_t thi) {
-    PixelStream q;
+__device__ __forceinline__ PairStream pair_stream(uint64_t seed, uint32_t pixel, uint32_t wfs,
+                                                  uint32_t tlo, uint32_t thi) {
+    PairStream q;
     q.k0 = (uint32_t)seed;
     q.k1 = (uint32_t)(seed >> 32);
-    q.pixel = pixel;
+    q.pair = pixel >> 1;
     q.wfs = wfs;
     q.tlo = tlo;
     q.thi = thi;
     return q;
 }
 
-// Read-noise deviate from block 0's first two words.
-__device__ __forceinline__ float box_muller(uint32_t w0, uint32_t w1) {
-    return sqrtf(-2.0f * logf(philox_unit(w0))) * cospif(2.0f * philox_unit(w1));
+// The pair's two read-noise deviates from block 0's first two words.
+__device__ __forceinline__ void box_muller_pair(uint32_t w0, uint32_t w1, float &z_even, float &z_odd) {
+    const float r = sqrtf(-2.0f * logf(philox_unit(w0)));
+    float sn, cs;
+    sincospif(2.0f * philox_unit(w1), &sn, &cs);
+    z_even = r * cs;
+    z_odd = r * sn;
 }
 
 __device__ __forceinline__ float log_factorial_f32(float k) {
@@ -104,20 +109,22 @@ __device__ __forceinline__ int poisson_inversion(float E, float u, float p0, con
     return k;
 }
 
-// PTRS for E >= 16: draws words 2 and 3 of block 0, then blocks 1, 2, ...  Rare for the
-// workloads here, so it recomputes block 0 rather than keep it live.  Inlined: callers give
-// it a single call site (an out-of-line call would make every live register a spill).
-__device__ __forceinline__ int poisson_ptrs(float E, PixelStream q) {
+// PTRS for E >= 16: draws word 2 + parity of block 0, then blocks 1 + parity, 3 + parity,
+// ...  Rare for the workloads here, so it recomputes block 0 rather than keep it live.
+// Inlined: callers give it a single call site (an out-of-line call would make every live
+// register a spill).
+__device__ __forceinline__ int poisson_ptrs(float E, const PairStream &q, int parity) {
     uint4 buf = q.block(0);
     uint32_t blk = 0;
-    int pos = 2;
+    int pos = 2 + parity;
     auto next = [&]() {
         if (pos == 4) {
-            buf = q.block(++blk);
+            blk = blk == 0 ? 1u + (uint32_t)parity : blk + 2u;
+            buf = q.block(blk);
             pos = 0;
         }
         const uint32_t w = pos == 0 ? buf.x : pos == 1 ? buf.y : pos == 2 ? buf.z : buf.w;
-        ++pos;
+        pos = blk == 0 ? 4 : pos + 1;
         return philox_unit(w);
     };
     float slam = __fsqrt_rn(E);
@@ -142,23 +149,27 @@ __device__ __forceinline__ int poisson_ptrs(float E, PixelStream q) {
     return (int)floorf(E);
 }
 
-// Poisson count of a pixel whose block 0 gave the inversion uniform u (word 2).
+// Poisson count of a pixel of the given parity whose block 0 gave the inversion uniform u
+// (word 2 + parity).
 template <bool TAB>
-__device__ __forceinline__ int poisson_count(float E, float u, float p0, const PixelStream &q,
+__device__ __forceinline__ int poisson_count(float E, float u, float p0, const PairStream &q, int parity,
                                              const float *rk) {
     if (!(E > 0.0f)) return 0;
     if (E < 16.0f) return poisson_inversion<TAB>(E, u, p0, rk);
-    return poisson_ptrs(E, q);
+    return poisson_ptrs(E, q, parity);
 }
 
-// One detector pixel: Poisson photon count plus Gaussian read noise.
+// One detector pixel: Poisson photon count plus Gaussian read noise (forms its pair's block).
 __device__ __forceinline__ float noise_pixel(float E, float read_noise, uint64_t seed,
                                              uint32_t pixel, uint32_t wfs, uint32_t tlo,
                                              uint32_t thi) {
-    const PixelStream q = pixel_stream(seed, pixel, wfs, tlo, thi);
+    const PairStream q = pair_stream(seed, pixel, wfs, tlo, thi);
     const uint4 r = q.block(0);
-    const int k = poisson_count<false>(E, philox_unit(r.z), expf(-E), q, nullptr);
-    return (float)k + read_noise * box_muller(r.x, r.y);
+    const int parity = (int)(pixel & 1u);
+    float ze, zo;
+    box_muller_pair(r.x, r.y, ze, zo);
+    const int k = poisson_count<false>(E, philox_unit(parity ? r.w : r.z), expf(-E), q, parity, nullptr);
+    return (float)k + read_noise * (parity ? zo : ze);
 }
 
 // Fills rk[0 .. kRecipTable) with RN(1/k) (entry 0 = 1); call from every thread of the block.

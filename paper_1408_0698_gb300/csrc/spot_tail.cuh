@@ -118,14 +118,14 @@ __device__ __forceinline__ void ngs_binned(const float *Iw, int lane, float (&Bv
 }
 
 // Photometry, noise and the centroid of subaperture v of WFS W; lane 0 writes the slopes.
-// rk: RN(1/k) table (fill_recip_table) in shared memory.  The generator blocks and
-// read-noise deviates of a lane's nd/2 pixels are formed first, side by side; the
-// inversion searches follow, and the rare pixels with E >= 16 go last through one PTRS
-// call site.
+// rk: RN(1/k) table (fill_recip_table) in shared memory.  One generator block per pixel
+// pair; each exchange between the lane pair is followed by both pixels' inversion searches,
+// and the rare pixels with E >= 16 go last through one PTRS call site.
 template <int nd>
 __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc &W, const InstDyn &D,
                                        uint64_t seed, int v, int lane, const float *rk) {
     constexpr int nd2 = nd * nd, J = nd / 2;
+    static_assert(nd == 16, "pixel pairs are the lane pairs (ix, ix + 1) of a 16-lane row");
     const int ix = lane & 15, half = lane >> 4;
     const float cd = 0.5f * (float)(nd - 1);
     float sb = 0.0f;
@@ -143,28 +143,34 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
     if (ix < nd) {
         float cv[J];
         if (D.noise) {
+            // Pixel pairs (2m, 2m + 1) are the lanes (ix, ix + 1) of one row: the even lane
+            // forms the pair blocks of its first J/2 rows, the odd lane those of its last J/2,
+            // and each hands its partner that pixel's deviate and uniform; rows m and
+            // m + J/2 are then sampled together.
             const uint32_t pix0 = (uint32_t)(v * nd2 + half * J * nd + ix);
-            const PixelStream q0 = pixel_stream(seed, pix0, (uint32_t)W.gs_index, tlo, thi);
-            float z[J], u[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                PixelStream q = q0;
-                q.pixel = pix0 + (uint32_t)(j * nd);
-                const uint4 r = q.block(0);
-                z[j] = box_muller(r.x, r.y);
-                u[j] = philox_unit(r.z);
-            }
-            // inversion for E < 16; pixels at or above it are marked and sampled below
+            const int par = ix & 1;
             uint32_t big = 0;
+            float z[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const float e = scale * Bv[j];
-                int k = 0;
-                if (e >= 16.0f)
-                    big |= 1u << j;
-                else if (e > 0.0f)
-                    k = poisson_inversion<true>(e, u[j], expf(-e), rk);
-                cv[j] = (float)k + W.read_noise * z[j];
+            for (int m = 0; m < J / 2; ++m) {
+                const uint32_t pix = pix0 + (uint32_t)((par * (J / 2) + m) * nd);
+                const uint4 r = pair_stream(seed, pix, (uint32_t)W.gs_index, tlo, thi).block(0);
+                float ze, zd;
+                box_muller_pair(r.x, r.y, ze, zd);
+                const float zr = __shfl_xor_sync(0xffffffffu, par ? ze : zd, 1);
+                const float ur = __shfl_xor_sync(0xffffffffu, philox_unit(par ? r.z : r.w), 1);
+                const float zo = par ? zd : ze, uo = philox_unit(par ? r.w : r.z);
+                z[m] = par ? zr : zo;
+                z[m + J / 2] = par ? zo : zr;
+                const float ua = par ? ur : uo, ub = par ? uo : ur;
+                const float ea = scale * Bv[m], eb = scale * Bv[m + J / 2];
+                int ka = 0, kb = 0;
+                if (ea >= 16.0f) big |= 1u << m;
+                else if (ea > 0.0f) ka = poisson_inversion<true>(ea, ua, expf(-ea), rk);
+                if (eb >= 16.0f) big |= 1u << (m + J / 2);
+                else if (eb > 0.0f) kb = poisson_inversion<true>(eb, ub, expf(-eb), rk);
+                cv[m] = (float)ka + W.read_noise * z[m];
+                cv[m + J / 2] = (float)kb + W.read_noise * z[m + J / 2];
             }
             while (big) {  // PTRS: one call site, rare
                 const int j = __ffs(big) - 1;
@@ -176,9 +182,8 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
                         e = scale * Bv[jj];
                         zj = z[jj];
                     }
-                PixelStream q = q0;
-                q.pixel = pix0 + (uint32_t)(j * nd);
-                const float c = (float)poisson_ptrs(e, q) + W.read_noise * zj;
+                const PairStream q = pair_stream(seed, pix0 + (uint32_t)(j * nd), (uint32_t)W.gs_index, tlo, thi);
+                const float c = (float)poisson_ptrs(e, q, par) + W.read_noise * zj;
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj)
                     if (jj == j) cv[jj] = c;
