@@ -7,7 +7,7 @@
 //   U[k][q]  = sum_p F[k][p] X[p][q]                 (lane k, registers)
 //   Y[k][m]  = sum_q U[k][q] F[m][q],  I = |Y|^2       (lane k, m looped)
 //   Ta[k][dx] = sum_m I[k][m] Ga[dx][m]               (fused: I never stored)
-//   M[dy][dx] = Kt[dy][dx] sum_k Ga[dy][k] Ta[k][dx]  (2x2 register tiles)
+//   M[dy][dx] = Kt[dy][dx] sum_k Ga[dy][k] Ta[k][dx]  (DFT across the lanes)
 //   P[dy][ix] = sum_dx M[dy][dx] G[dx][ix]            (lane = ix, half-warp = dy half)
 //   B[iy][ix] = Re sum_dy G[dy][iy] P[dy][ix]         (half-warp partials + one shuffle)
 // then photometry, noise and the centroid with warp reductions.  All sizes are
@@ -25,27 +25,21 @@ __device__ __forceinline__ void cmac2(float2 &acc, const float2 a, const float2 
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <int n, int nd>
 struct N32Layout {
-    static constexpr int N = 32, D2 = 2 * n - 1, NO = n | 1, GAK = 33;
+    static constexpr int N = 32, D2 = 2 * n - 1;
     // per-CTA tables (float2 units)
     static constexpr int oFk = 0;                 // [p][k]   F[k][p]      (lane-k column)
     static constexpr int oFm = oFk + n * N;        // [m][q]   F[m][q]      (broadcast rows)
     static constexpr int oGam = oFm + N * n;       // [m][dx]  Ga[dx][m]    (broadcast rows)
-    static constexpr int oGak = oGam + N * n;      // [dyi][GAK] Ga(dy, k), conjugated for dy < 0
-    static constexpr int oG = oGak + (2 * n - 1) * GAK;  // [d][nd]  G[d][i]
+    static constexpr int oFft = oGam + N * n;      // lane-DFT twiddles and phases (tail::fill_fft_table)
+    static constexpr int oG = oFft + tail::kFftTable;  // [d][nd]  G[d][i]
     static constexpr int oRk = oG + n * nd;         // RN(1/k) for the Poisson inversion (floats)
     static constexpr int table = oRk + kRecipTable / 2;
     // per-warp scratch (float2 units)
     static constexpr int wX = 0;                   // [p][q]
-    static constexpr int wTa = wX + n * n;         // [k][NO]
-    static constexpr int wM = wTa + N * NO;        // [dyi][n]
+    static constexpr int wTa = wX + n * n;         // Q: [nd][n]
+    static constexpr int wM = wTa + nd * n;        // [dyi][n]
     static constexpr int wI = wM + D2 * n;         // [k][N+1] floats (NGS binning only)
     static constexpr int warp = wI + (N * (N + 1) + 1) / 2;
 };
@@ -55,12 +49,12 @@ struct N32Layout {
 template <int n, int nd>
 __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArgs a) {
     using Lay = N32Layout<n, nd>;
-    constexpr int N = 32, D2 = Lay::D2, NO = Lay::NO, GAK = Lay::GAK, b = N / nd;
+    constexpr int N = 32, D2 = Lay::D2;
     constexpr int nd2 = nd * nd;
     static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
     extern __shared__ __align__(16) float2 sm2[];
     float2 *Fk = sm2 + Lay::oFk, *Fm = sm2 + Lay::oFm, *Gam = sm2 + Lay::oGam;
-    float2 *Gak = sm2 + Lay::oGak, *Gt = sm2 + Lay::oG;
+    float2 *fft = sm2 + Lay::oFft, *Gt = sm2 + Lay::oG;
     // global tables: F[q*N + m] = F[m][q]; Ga[d*N + k]; G[d*nd + i]
     for (int i = threadIdx.x; i < n * N; i += blockDim.x) {
         const int q = i / N, m = i - q * N;
@@ -70,12 +64,11 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         const int d = q, k = m;     // Ga has the same [d][k] shape
         const float2 g = a.Ga[i];
         Gam[k * n + d] = g;
-        Gak[(d + n - 1) * GAK + k] = g;                          // dy = +d
-        if (d > 0) Gak[(n - 1 - d) * GAK + k] = make_float2(g.x, -g.y);  // dy = -d
     }
     for (int i = threadIdx.x; i < n * nd; i += blockDim.x) Gt[i] = a.G[i];
     float *rk = reinterpret_cast<float *>(sm2 + Lay::oRk);
     fill_recip_table(rk, threadIdx.x, blockDim.x);
+    tail::fill_fft_table(fft, threadIdx.x, blockDim.x);
     __syncthreads();
     wait_prior_grid();
 
@@ -85,9 +78,6 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float2 *Mw = sm2 + Lay::table + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
 
-    const float cd = 0.5f * (float)(nd - 1);
-    const int ix = lane & 15, half = lane >> 4;
-
     for (int g = blockIdx.x * nw + wib; g < a.total; g += gridDim.x * nw) {
         const WfsDesc &W = a.wfs[find_wfs(a.wfs, a.n_wfs, g)];
         const InstDyn &D = a.dyn[W.inst];
@@ -95,8 +85,6 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
         const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
         const int v = g - W.subap_begin;
-        float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
-        float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
         __syncwarp();
 
         // field, piston-free
@@ -148,10 +136,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 
         float Bv[nd / 2];  // B[iy][ix] for iy = half*(nd/2) + j
         if (W.is_lgs) {
-#pragma unroll
-            for (int d = 0; d < n; ++d) Ta[lane * NO + d] = T[d];
-            __syncwarp();
-            tail::lgs_binned<n, nd, NO, GAK>(Ta, Mw, Ta, Gak, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
+            tail::lgs_binned<n, nd>(T, Mw, Ta, fft, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
         } else {
             __syncwarp();
             tail::ngs_binned<nd>(Iw, lane, Bv);

@@ -130,15 +130,9 @@ __device__ __forceinline__ void cmacc(float2 &acc, const float2 a, const float2 
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-__device__ __forceinline__ float wsum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <int n, int nd>
 struct TcLayout {
-    static constexpr int N = 32, D2 = 2 * n - 1, NO = n | 1, GAK = 33;
+    static constexpr int N = 32, D2 = 2 * n - 1;
     // byte offsets; tensor-core tiles first (1024-aligned)
     static constexpr int oB1 = 0;                  // 64 rows x 128 B: [F_hi; F_hi; F_lo] blocks
     static constexpr int oB2h = oB1 + 8192;        // 32 rows x 128 B: [Ga_hi; Ga_hi]
@@ -148,13 +142,13 @@ struct TcLayout {
     static constexpr int oA = oB2l + 4096;
     static constexpr int oTab = oA + 16384 * kWG;  // CUDA-core tables (float2)
     static constexpr int tFk = 0;                  // [p][k]  F[k][p]
-    static constexpr int tGak = tFk + n * N;       // [dyi][GAK] Ga(dy, k), conjugated rows for dy < 0
-    static constexpr int tG = tGak + D2 * GAK;     // [d][nd] G[d][i]
+    static constexpr int tFft = tFk + n * N;       // lane-DFT twiddles and phases (tail::fill_fft_table)
+    static constexpr int tG = tFft + tail::kFftTable;  // [d][nd] G[d][i]
     static constexpr int tRk = tG + n * nd;       // RN(1/k) for the Poisson inversion (floats)
     static constexpr int tEnd = tRk + kRecipTable / 2;
     static constexpr int oWarp = oTab + tEnd * 8;  // per-warp scratch (float2)
-    // the NGS image rows (wI) alias the LGS transfer-domain scratch (wTa, wM)
-    static constexpr int wX = 0, wTa = wX + n * n, wM = wTa + N * NO, wI = wTa;
+    // the NGS image rows (wI) alias the LGS scratch (wQ, wM)
+    static constexpr int wX = 0, wQ = wX + n * n, wM = wQ + nd * n, wI = wQ;
     static constexpr int lgs_end = wM + D2 * n, ngs_end = wI + (N * (N + 1) + 1) / 2;
     static constexpr int warp = lgs_end > ngs_end ? lgs_end : ngs_end;
     static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;  // per warpgroup: 2 mbarriers, flag
@@ -166,7 +160,7 @@ struct TcLayout {
 template <int n, int nd>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__ ShArgs a) {
     using Lay = TcLayout<n, nd>;
-    constexpr int N = 32, D2 = Lay::D2, NO = Lay::NO, GAK = Lay::GAK, b = N / nd, nd2 = nd * nd;
+    constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
     static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -175,7 +169,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     const int wg = wib >> 2, wq = wib & 3;  // warpgroup, warp within it (= TMEM lane quarter)
     uint8_t *sA1 = smem + Lay::oA + 16384 * wg, *sA2 = sA1;
     float2 *tab = reinterpret_cast<float2 *>(smem + Lay::oTab);
-    float2 *Fk = tab + Lay::tFk, *Gak = tab + Lay::tGak, *Gt = tab + Lay::tG;
+    float2 *Fk = tab + Lay::tFk, *fft = tab + Lay::tFft, *Gt = tab + Lay::tG;
     float *rk = reinterpret_cast<float *>(tab + Lay::tRk);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + 32 * wg);
     int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 32 * wg + 16);
@@ -196,12 +190,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             const int p = i / N, k = i - p * N;
             Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
         }
-        for (int i = tid; i < D2 * N; i += kTcThreads) {
-            const int dyi = i / N, k = i - dyi * N, dy = dyi - (n - 1);
-            float2 g = a.Ga[(dy >= 0 ? dy : -dy) * N + k];
-            if (dy < 0) g.y = -g.y;
-            Gak[dyi * GAK + k] = g;
-        }
+        tail::fill_fft_table(fft, tid, kTcThreads);
         for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
         fill_recip_table(rk, tid, kTcThreads);
     }
@@ -227,11 +216,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
 
     float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
-    float2 *Ta = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wTa;
+    float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
     float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
-    const float cd = 0.5f * (float)(nd - 1);
-    const int ix = lane & 15, half = lane >> 4;
     const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
     const int groups = (a.total + 3) / 4;
     const bool issuer = wq == 0 && lane == 0;
@@ -361,14 +348,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         }
         if (!mbar_wait(&mbar[1], phase)) *sflag = 1;
         fence_after_sync();
+        float2 T[n];  // row k = lane of the first inverse stage (LGS)
         {
             uint32_t r[32];
             GBWFS_TMEM_LD32(r, t_row + 64);
             tmem_wait_ld();
-            if (active && W.is_lgs) {
 #pragma unroll
-                for (int d = 0; d < n; ++d) Ta[lane * NO + d] = make_float2(__uint_as_float(r[d]), __uint_as_float(r[16 + d]));
-            }
+            for (int d = 0; d < n; ++d) T[d] = make_float2(__uint_as_float(r[d]), __uint_as_float(r[16 + d]));
         }
         phase ^= 1u;
         fence_before_sync();  // TMEM reads of this group precede the next group's MMAs
@@ -378,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         // remaining stages on the CUDA cores (per warp)
         float Bv[nd / 2];
         if (W.is_lgs)
-            tail::lgs_binned<n, nd, NO, GAK>(Ta, Mw, Ta, Gak, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
+            tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
         else
             tail::ngs_binned<nd>(Iw, lane, Bv);
         tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk);

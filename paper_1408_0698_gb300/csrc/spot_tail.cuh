@@ -3,13 +3,16 @@
 // (Sec. 4 LGS SH: elongation by the sodium kernel, binning, noise-added image,
 // centroid).  Shared by the FP32 and tensor-core kernels.
 //
-//   M[dy][dx] = Kt[dy][dx] sum_k Ga(dy, k) Ta[k][dx]      (1 x 2 register tiles)
+//   M[dy][dx] = Kt[dy][dx] sum_k Ga(dy, k) T[k][dx]       (k = lane: a 32-point DFT)
 //   Q[iy][dx] = sum_dy G(dy, iy) M[dy][dx]                 (lane = iy, half-warp = dx half)
 //   B[iy][ix] = Re sum_dx Q[iy][dx] G[dx][ix]              (lane = ix, half-warp = iy half)
-// with Ga(dy, k) = exp(+2 pi i (k - cN) dy / N) and G(dy, i) = sum_{r<b} w^{(b i + r - cN) dy}
-// (conjugated for dy < 0).  Kt carries 1/N^2 and the Hermitian weight c_dx, so B is the
-// binned elongated spot.  Then E = photons fill B / sum B, C = Poisson(E) + ron z (or E),
-// and the centre of gravity.
+// with Ga(dy, k) = exp(+2 pi i (k - cN) dy / N) = ph(dy) w^(k dy), w = exp(2 pi i / N),
+// ph(dy) = exp(-2 pi i cN dy / N), and G(dy, i) = sum_{r<b} w^{(b i + r - cN) dy}
+// (conjugated for dy < 0).  The sum over k is a DFT of each column across the lanes: radix 2,
+// decimation in frequency, one shuffle per stage and component; lane i ends with frequency
+// bitrev5(i).  Kt carries 1/N^2 and the Hermitian weight c_dx, so B is the binned elongated
+// spot.  Then E = photons fill B / sum B, C = Poisson(E) + ron z (or E), and the centre of
+// gravity.
 #pragma once
 #include "internal.h"
 #include "noise.cuh"
@@ -28,31 +31,60 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Ta: [32][NO] (row k), Gak: [2n-1][gak] rows Ga(dy, .) already conjugated for dy < 0,
-// Gt: [n][nd] G[d][i].  M and Q are per-warp scratch ([2n-1][n], [nd][n]).  On return
-// Bv[j] = B[half * nd/2 + j][ix] for lane = half * 16 + ix.
-template <int n, int nd, int NO, int GAK>
-__device__ __forceinline__ void lgs_binned(const float2 *Ta, float2 *M, float2 *Q, const float2 *Gak,
-                                           const float2 *Gt, const float2 *kt, int lane, float (&Bv)[nd / 2]) {
-    constexpr int N = 32, D2 = 2 * n - 1, DXP = (n + 1) / 2, TASKS = D2 * DXP, DXH = (n + 1) / 2;
-    static_assert(nd == 16, "the detector tile maps to 16 lanes x 2 half-warps");
-    // M: tasks (dy, dx pair), three rounds over the warp for n = 10
-    for (int task = lane; task < TASKS; task += 32) {
-        const int dyi = task / DXP, dx0 = 2 * (task - dyi * DXP);
-        const bool has1 = dx0 + 1 < n;
-        const float2 *g = Gak + dyi * GAK;
-        float2 c0 = make_float2(0.f, 0.f), c1 = c0;
-#pragma unroll 8
-        for (int k = 0; k < N; ++k) {
-            const float2 ga = g[k];
-            cmac(c0, ga, Ta[k * NO + dx0]);
-            if (has1) cmac(c1, ga, Ta[k * NO + dx0 + 1]);
+constexpr int kFftTable = 6 * 32;  // float2: five stages of twiddles, then ph(dy), per lane
+
+// Per-lane DFT constants: entry s * 32 + lane (s < 5, span h = 16 >> s) is 1 for the upper
+// lane of a butterfly and w^((lane mod h) 16 / h) for the lower; entry 5 * 32 + lane is
+// ph(dy) of the lane's output frequency.  Call from every thread of the block.
+__device__ __forceinline__ void fill_fft_table(float2 *tab, int tid, int nthreads) {
+    for (int i = tid; i < kFftTable; i += nthreads) {
+        const int st = i >> 5, l = i & 31;
+        float sn = 0.0f, cs = 1.0f;
+        if (st < 5) {
+            const int h = 16 >> st;
+            if (l & h) sincospif((float)((l & (h - 1)) * (16 / h)) / 16.0f, &sn, &cs);
+        } else {
+            const int f = (int)(__brev((unsigned)l) >> 27), dy = f < 16 ? f : f - 32;
+            sincospif((float)(-31 * dy) / 32.0f, &sn, &cs);  // 2 cN / N = 31 / 32
         }
-        const float2 k0 = __ldg(kt + dyi * n + dx0);
-        M[dyi * n + dx0] = make_float2(c0.x * k0.x - c0.y * k0.y, c0.x * k0.y + c0.y * k0.x);
-        if (has1) {
-            const float2 k1 = __ldg(kt + dyi * n + dx0 + 1);
-            M[dyi * n + dx0 + 1] = make_float2(c1.x * k1.x - c1.y * k1.y, c1.x * k1.y + c1.y * k1.x);
+        tab[i] = make_float2(cs, sn);
+    }
+}
+
+// T: this lane's row k = lane of the first stage (T[k][dx], dx < n), consumed.  fft: the
+// table above.  Gt: [n][nd] G[d][i].  M and Q are per-warp scratch ([2n-1][n], [nd][n]).
+// On return Bv[j] = B[half * nd/2 + j][ix] for lane = half * 16 + ix.
+template <int n, int nd>
+__device__ __forceinline__ void lgs_binned(float2 (&T)[n], float2 *M, float2 *Q, const float2 *fft,
+                                           const float2 *Gt, const float2 *kt, int lane, float (&Bv)[nd / 2]) {
+    constexpr int D2 = 2 * n - 1, DXH = (n + 1) / 2;
+    static_assert(nd == 16, "the detector tile maps to 16 lanes x 2 half-warps");
+    static_assert(n <= 16, "frequencies |dy| < n must be distinct modulo 32");
+    // M: DFT over the lanes, five radix-2 stages
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int h = 16 >> st;
+        const float sgn = (lane & h) ? -1.0f : 1.0f;
+        const float2 tw = fft[st * 32 + lane];
+#pragma unroll
+        for (int d = 0; d < n; ++d) {
+            const float tx = __shfl_xor_sync(0xffffffffu, T[d].x, h);
+            const float ty = __shfl_xor_sync(0xffffffffu, T[d].y, h);
+            const float sx = fmaf(sgn, T[d].x, tx), sy = fmaf(sgn, T[d].y, ty);
+            T[d] = make_float2(sx * tw.x - sy * tw.y, sx * tw.y + sy * tw.x);
+        }
+    }
+    {
+        const int f = (int)(__brev((unsigned)lane) >> 27), dy = f < 16 ? f : f - 32;
+        if (dy > -n && dy < n) {
+            const int dyi = dy + n - 1;
+            const float2 ph = fft[5 * 32 + lane];
+#pragma unroll
+            for (int d = 0; d < n; ++d) {
+                const float2 x = make_float2(T[d].x * ph.x - T[d].y * ph.y, T[d].x * ph.y + T[d].y * ph.x);
+                const float2 k0 = __ldg(kt + dyi * n + d);
+                M[dyi * n + d] = make_float2(x.x * k0.x - x.y * k0.y, x.x * k0.y + x.y * k0.x);
+            }
         }
     }
     __syncwarp();
