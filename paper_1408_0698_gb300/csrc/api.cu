@@ -43,6 +43,7 @@ struct SpotGroup {
     int first = 0, count = 0, total = 0;
     int kind = 0;            // SpotKind
     int grid_cap = 0, cta_warps = 0;
+    int proj_base = 0, proj_count = 0;  // this group's projection blocks
 };
 
 int spot_kind(const wfs_geometry &g) {
@@ -401,28 +402,33 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
 
     static thread_local ProjArgs pa;
     pa.inst = h->d_inst;
-    pa.wfs = h->d_wfs;
-    pa.n_wfs = (int)h->wfs_host.size();
     pa.n_inst = 1;
     pa.box_cap = h->proj_box;
     pa.status = h->d_status;
     pa.dyn[0] = dyn;
     cudaError_t e;
-    if (h->proj_blocks > 0) {
-        long slot = timed_begin(h, "project", stream);
-        e = launch_project(pa, h->proj_blocks, stream);
-        timed_end(h, slot, stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "projection launch");
-    }
+    // projection of a contiguous range of the WFS table (a group's WFSs, or all of them)
+    auto project = [&](int first, int count, int base, int blocks, cudaStream_t ls) -> cudaError_t {
+        if (blocks <= 0) return cudaSuccess;
+        pa.wfs = h->d_wfs + first;
+        pa.n_wfs = count;
+        pa.block_base = base;
+        long slot = timed_begin(h, "project", ls);
+        cudaError_t err = launch_project(pa, blocks, ls);
+        timed_end(h, slot, ls);
+        return err;
+    };
 
-    // The largest group runs on the caller's stream, launched last; the others run on side
-    // streams forked after the projection (launched first, so their few CTAs are resident
-    // before the large launch fills the GPU) and joined before the call returns.
+    // The largest group runs on the caller's stream; each other group (a few CTAs: the NGS of
+    // an LGS system) runs its own projection and spot kernel on a side stream forked at the
+    // start of the call, so that its work can overlap the large projection, and is joined
+    // before the call returns.  (A higher priority for the side streams made the frame slower:
+    // their CTAs then displace the large projection's.)
     size_t big = 0;
     for (size_t j = 1; j < h->groups.size(); ++j)
         if (h->groups[j].total > h->groups[big].total) big = j;
     static thread_local ShArgs sa;
-    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls) -> cudaError_t {
+    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project) -> cudaError_t {
         memset(&sa, 0, offsetof(ShArgs, dyn));
         fill_geom_args(sa, h->geoms[G.geom]);
         sa.inst = h->d_inst;
@@ -435,22 +441,32 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.n_inst = 1;
         sa.dyn[0] = dyn;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
-        cudaError_t err = launch_spot(G.kind, sa, ls, ls == stream && h->proj_blocks > 0 && !h->timing);
+        cudaError_t err = launch_spot(G.kind, sa, ls, after_project && !h->timing);
         timed_end(h, sl, ls);
         return err;
     };
     size_t k = 0;
     for (size_t j = 0; j < h->groups.size(); ++j) {
-        if (j == big || h->groups[j].total == 0) continue;
+        const SpotGroup &G = h->groups[j];
+        if (j == big || G.total == 0) continue;
         if (k >= h->side.size()) return fail(h, WFS_EINVAL, "internal: missing side stream");
         if (k == 0 && (e = cudaEventRecord(h->ev_fork, stream)) != cudaSuccess) return cuda_fail(h, e, "fork");
-        if ((e = cudaStreamWaitEvent(h->side[k], h->ev_fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork wait");
-        if ((e = launch_group(h->groups[j], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "spot launch");
-        if ((e = cudaEventRecord(h->ev_join[k], h->side[k])) != cudaSuccess) return cuda_fail(h, e, "join");
+        cudaStream_t ss = h->side[k];
+        if ((e = cudaStreamWaitEvent(ss, h->ev_fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork wait");
+        if ((e = project(G.first, G.count, G.proj_base, G.proj_count, ss)) != cudaSuccess)
+            return cuda_fail(h, e, "projection launch");
+        if ((e = launch_group(G, ss, G.proj_count > 0)) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+        if ((e = cudaEventRecord(h->ev_join[k], ss)) != cudaSuccess) return cuda_fail(h, e, "join");
         ++k;
     }
-    if (!h->groups.empty() && h->groups[big].total > 0)
-        if ((e = launch_group(h->groups[big], stream)) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+    if (!h->groups.empty()) {
+        const SpotGroup &G = h->groups[big];
+        // with a single group this projects every WFS (blocks 0 .. proj_blocks)
+        if ((e = project(G.first, G.count, G.proj_base, G.proj_count, stream)) != cudaSuccess)
+            return cuda_fail(h, e, "projection launch");
+        if (G.total > 0 && (e = launch_group(G, stream, G.proj_count > 0)) != cudaSuccess)
+            return cuda_fail(h, e, "spot launch");
+    }
     for (size_t j = 0; j < k; ++j)
         if ((e = cudaStreamWaitEvent(stream, h->ev_join[j], 0)) != cudaSuccess) return cuda_fail(h, e, "join wait");
     return WFS_OK;
@@ -641,6 +657,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
             SpotGroup G;
             G.geom = gi;
             G.first = (int)h->wfs_host.size();
+            G.proj_base = blocks;
             G.kind = spot_kind(geom[gi]);
             for (int w = 0; w < n_gs; ++w) {
                 const GsDev &s = h->gs[w];
@@ -681,6 +698,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 h->wfs_host.push_back(d);
                 ++G.count;
             }
+            G.proj_count = blocks - G.proj_base;
             if (G.count) h->groups.push_back(G);
         }
         h->proj_blocks = blocks;
@@ -1254,6 +1272,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
     pa.inst = b->d_inst;
     pa.wfs = sl.d;
     pa.n_wfs = count;
+    pa.block_base = 0;
     pa.n_inst = n;
     pa.box_cap = box;
     pa.status = b->hs[0]->d_status;

@@ -67,6 +67,8 @@ struct ProjArgs {
     const WfsDesc *wfs;
     int n_wfs, n_inst;
     int box_cap;                    // floats of shared memory for tables and screen box
+    int block_base;                 // projection block of this launch's first CTA (a launch
+                                    // may cover a contiguous range of the WFS table)
     int *status;                    // device status word (limit errors)
     InstDyn dyn[kMaxInstances];
 };

@@ -37,11 +37,12 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
     __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
 
-    // the WFS owning this CTA: last entry whose first CTA is <= blockIdx.x
+    // the WFS owning this CTA: last entry whose first CTA is <= bid
+    const int bid = (int)blockIdx.x + a.block_base;
     int lo = 0, hi = a.n_wfs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (a.wfs[mid].proj_block_begin <= (int)blockIdx.x) lo = mid;
+        if (a.wfs[mid].proj_block_begin <= bid) lo = mid;
         else hi = mid - 1;
     }
     const WfsDesc &W = a.wfs[lo];
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
         // streams in while this one is interpolated); coordinates come from per-column and
         // per-row tables (a pixel's screen column depends on its pupil column only)
         extern __shared__ float psm[];
-        const int4 sg = W.segs[(int)blockIdx.x - W.proj_block_begin];  // sy, v_first, count, sx0
+        const int4 sg = W.segs[bid - W.proj_block_begin];  // sy, v_first, count, sx0
         const int n = W.n, nn = n * n, ncol = sg.z * n;
         const int box_floats = ((a.box_cap - ((4 * (ncol + n) + 3) & ~3)) / 2) & ~3;
         float2 *tab[2] = {reinterpret_cast<float2 *>(psm), reinterpret_cast<float2 *>(psm) + (ncol + n)};
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
 
     // each thread: one 2x2 block of pupil pixels (rows p, p+1; columns q, q+1) of one subaperture
     const int n = W.n, nn = n * n, nb = (n + 1) >> 1, nbb = nb * nb;
-    const int blk = ((int)blockIdx.x - W.proj_block_begin) * kProjThreads + threadIdx.x;
+    const int blk = (bid - W.proj_block_begin) * kProjThreads + threadIdx.x;
     if (blk >= W.n_valid * nbb) return;
     const int v = blk / nbb, r = blk - v * nbb, bp = r / nb, bq = r - bp * nb;
     const int p0 = 2 * bp, q0 = 2 * bq;
