@@ -89,6 +89,7 @@ struct wfs_ctx {
     size_t opd_total = 0, int_total = 0, det_total = 0;
     int total_valid = 0;
     int *d_status = nullptr;
+    int *d_work = nullptr;  // dynamic work counters, one pair per spot group
     // host-buffer path: two staging buffer sets used alternately, uploads on a copy stream
     float *d_screens_stage[2] = {nullptr, nullptr};
     float *d_slopes_stage[2] = {nullptr, nullptr};
@@ -145,6 +146,9 @@ struct wfs_batch_ctx {
         cudaEvent_t copied = nullptr;
     };
     std::vector<Slot> slots;
+    // dynamic work counters: one pair per class for graph / direct launches, then one pair per
+    // (subset slot, class)
+    int *d_work = nullptr;
 };
 
 namespace {
@@ -282,6 +286,7 @@ void release(wfs_ctx *h) {
     }
     cudaFree(h->d_opd);
     cudaFree(h->d_status);
+    cudaFree(h->d_work);
     cudaFree(h->d_inst);
     cudaFree(h->d_wfs);
     for (int i = 0; i < 2; ++i) {
@@ -439,6 +444,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.grid_cap = G.grid_cap;
         sa.cta_warps = G.cta_warps;
         sa.n_inst = 1;
+        sa.work = h->d_work + 2 * (&G - h->groups.data());
         sa.dyn[0] = dyn;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
         cudaError_t err = launch_spot(G.kind, sa, ls, after_project && !h->timing);
@@ -735,6 +741,8 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
     if ((e = cudaMalloc(&h->d_opd, (opd ? opd : 1) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_work, 2 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
+        (e = cudaMemset(h->d_work, 0, 2 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         release(h);
         delete h;
@@ -926,6 +934,7 @@ void batch_free(wfs_batch b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_inst);
     cudaFree(b->d_wfs);
+    cudaFree(b->d_work);
     delete b->pa;
     for (ShArgs *p : b->sa) delete p;
     delete b;
@@ -1145,7 +1154,9 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     std::vector<InstDesc> inst(n);
     for (int i = 0; i < n; ++i) inst[i] = hs[i]->inst_host;
     cudaError_t e;
-    if ((e = upload(&b->d_inst, inst)) != cudaSuccess || (e = upload(&b->d_wfs, b->wfs_host)) != cudaSuccess) {
+    const size_t work_bytes = 2 * sizeof(int) * b->classes.size() * (1 + kBatchSlots) + 2 * sizeof(int);
+    if ((e = upload(&b->d_inst, inst)) != cudaSuccess || (e = upload(&b->d_wfs, b->wfs_host)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_work, work_bytes)) != cudaSuccess || (e = cudaMemset(b->d_work, 0, work_bytes)) != cudaSuccess) {
         batch_free(b);
         return cuda_fail(nullptr, e, "batch table upload");
     }
@@ -1167,6 +1178,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
         a->total = bc.total;
         a->status = hs[0]->d_status;
         a->n_inst = n;
+        a->work = b->d_work + 2 * b->sa.size();
         b->sa.push_back(a);
     }
     const char *g = getenv("GBWFS_BATCH_GRAPH");
@@ -1291,6 +1303,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
         sa.grid_cap = bc.grid_cap;
         sa.cta_warps = bc.cta_warps;
         sa.n_inst = n;
+        sa.work = b->d_work + 2 * (b->classes.size() * (1 + (size_t)slot) + c);
         memcpy(sa.dyn, pa.dyn, sizeof(InstDyn) * n);
         if ((e = launch_spot(bc.kind, sa, (cudaStream_t)stream)) != cudaSuccess)
             return cuda_fail(nullptr, e, "batch subset spot launch");

@@ -87,6 +87,10 @@ struct ShArgs {
     int grid_cap;        // maximum CTAs (0 = the launcher's default)
     int cta_warps;       // warps per CTA where the kernel allows a choice (0 = default)
     int n_inst;
+    // Dynamic work split of the 32-point kernels: {next ticket, CTAs done}, zero between
+    // launches (the last CTA to finish resets it), used by one launch at a time; null = a
+    // static split.
+    int *work;
     InstDyn dyn[kMaxInstances];
 };
 

@@ -78,7 +78,12 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float2 *Mw = sm2 + Lay::table + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
 
-    for (int g = blockIdx.x * nw + wib; g < a.total; g += gridDim.x * nw) {
+    // Work split: each warp starts with subaperture blockIdx.x * nw + wib; with a.work, lane 0
+    // draws one ticket per iteration (issued at the top, used at the bottom).
+    const int nwarps = gridDim.x * nw;
+    for (int g = blockIdx.x * nw + wib; g < a.total;) {
+        int ticket = 0;
+        if (a.work && lane == 0) ticket = atomicAdd(a.work, 1);
         const WfsDesc &W = a.wfs[find_wfs(a.wfs, a.n_wfs, g)];
         const InstDyn &D = a.dyn[W.inst];
         const uint64_t seed = a.inst[W.inst].seed;
@@ -142,6 +147,19 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             tail::ngs_binned<nd>(Iw, lane, Bv);
         }
         tail::finish<nd>(Bv, W, D, seed, v, lane, rk);
+        g = a.work ? nwarps + __shfl_sync(0xffffffffu, ticket, 0) : g + nwarps;
+    }
+    if (a.work) {
+        // every ticket of this CTA was drawn before the barrier; the last CTA to get here leaves
+        // the counters at zero for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
+                a.work[0] = 0;
+                a.work[1] = 0;
+            }
+        }
     }
 }
 

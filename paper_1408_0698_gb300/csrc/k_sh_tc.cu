@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     float *rk = reinterpret_cast<float *>(tab + Lay::tRk);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + 32 * wg);
     int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 32 * wg + 16);
+    int *snext = reinterpret_cast<int *>(smem + Lay::oMisc + 32 * wg + 20);  // next group (dynamic split)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + 32 * kWG);
     const uint32_t bar_id = 1 + wg;
     auto wg_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(128) : "memory"); };
@@ -224,7 +225,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     const bool issuer = wq == 0 && lane == 0;
     uint32_t phase = 0;
 
-    for (int grp = blockIdx.x * kWG + wg; grp < groups; grp += gridDim.x * kWG) {
+    // Work split: each warpgroup starts with group blockIdx.x * kWG + wg; with a.work the
+    // issuer then draws one ticket per iteration (issued at the top, published before the first
+    // warpgroup barrier, read after it), so CTAs that start late take fewer groups.
+    const int nwg = gridDim.x * kWG;
+    int grp_next = 0;
+    for (int grp = blockIdx.x * kWG + wg; grp < groups; grp = grp_next) {
+        int ticket = 0;
+        if (a.work && issuer) ticket = atomicAdd(a.work, 1);
         const int g = 4 * grp + wq;
         const bool active = g < a.total;
         const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
@@ -278,10 +286,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
                 *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
             }
         }
+        if (a.work && issuer) *snext = nwg + ticket;
         fence_async_smem();
         fence_before_sync();
         wg_sync();
         fence_after_sync();
+        grp_next = a.work ? *snext : grp + nwg;
         if (*sflag) break;  // a previous wait timed out (uniform: read after the barrier)
         if (issuer) {
 #pragma unroll
@@ -372,6 +382,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     fence_before_sync();
     __syncthreads();
     if (*sflag && issuer && a.status) atomicCAS(a.status, 0, 5 /* WFS_ETIMEOUT */);
+    if (a.work && tid == 0) {
+        // every ticket of this CTA was drawn before the barrier above; the last CTA to get here
+        // leaves the counters at zero for the next launch
+        __threadfence();
+        if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
+            a.work[0] = 0;
+            a.work[1] = 0;
+        }
+    }
     fence_after_sync();
     if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_all), "r"(kTmemCols));
 }
