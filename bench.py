@@ -48,12 +48,16 @@ def peaks():
 
 
 def spot_flops(n, N, nd, lgs):
-    """FP32 flops (FMA = 2) of one subaperture in the CUDA-core spot kernel:
-    DFT 8Nn(n+N) + |.|^2 3N^2; LGS elongation+binning through the transfer function
-    4N^2 n + (2n-1) n (8N+6) + 8 (2n-1) nd n + 4 nd^2 (2n-1); NGS binning N^2; the
-    photometry and centroid 6 nd^2."""
+    """FP32 flops (FMA = 2) of one subaperture in the spot kernels: DFT 8Nn(n+N), |.|^2 3N^2,
+    photometry and centroid 6 nd^2; NGS binning N^2.  LGS elongation and binning through the
+    transfer function: Ta 4N^2 n, then
+      32-point kernels: M as a radix-2 DFT across the lanes, 10 log2(N) N n, times the phase
+      and Kt 12 (2n-1) n; Q = G^T M 8 (2n-1) n nd; B = Re Q G 4 nd^2 n;
+      other sizes (direct sums): M (2n-1) n (8N+6); P = M G 8 (2n-1) nd n; B 4 nd^2 (2n-1)."""
     f = 8 * N * n * (n + N) + 3 * N * N + 6 * nd * nd
-    if lgs:
+    if lgs and N == 32:
+        f += 4 * N * N * n + 10 * 5 * N * n + 12 * (2 * n - 1) * n + 8 * (2 * n - 1) * n * nd + 4 * nd * nd * n
+    elif lgs:
         f += 4 * N * N * n + (2 * n - 1) * n * (8 * N + 6) + 8 * (2 * n - 1) * nd * n + 4 * nd * nd * (2 * n - 1)
     else:
         f += N * N

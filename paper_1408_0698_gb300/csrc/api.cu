@@ -89,7 +89,7 @@ struct wfs_ctx {
     size_t opd_total = 0, int_total = 0, det_total = 0;
     int total_valid = 0;
     int *d_status = nullptr;
-    int *d_work = nullptr;  // dynamic work counters, one pair per spot group
+    int *d_work = nullptr;  // ticket counters: a pair per spot group, then a pair per group's projection
     // host-buffer path: two staging buffer sets used alternately, uploads on a copy stream
     float *d_screens_stage[2] = {nullptr, nullptr};
     float *d_slopes_stage[2] = {nullptr, nullptr};
@@ -413,11 +413,13 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     pa.dyn[0] = dyn;
     cudaError_t e;
     // projection of a contiguous range of the WFS table (a group's WFSs, or all of them)
-    auto project = [&](int first, int count, int base, int blocks, cudaStream_t ls) -> cudaError_t {
+    auto project = [&](const SpotGroup &G, cudaStream_t ls) -> cudaError_t {
+        const int blocks = G.proj_count;
         if (blocks <= 0) return cudaSuccess;
-        pa.wfs = h->d_wfs + first;
-        pa.n_wfs = count;
-        pa.block_base = base;
+        pa.wfs = h->d_wfs + G.first;
+        pa.n_wfs = G.count;
+        pa.block_base = G.proj_base;
+        pa.work = h->d_work + 2 * (h->groups.size() + 1) + 2 * (&G - h->groups.data());
         long slot = timed_begin(h, "project", ls);
         cudaError_t err = launch_project(pa, blocks, ls);
         timed_end(h, slot, ls);
@@ -433,7 +435,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     for (size_t j = 1; j < h->groups.size(); ++j)
         if (h->groups[j].total > h->groups[big].total) big = j;
     static thread_local ShArgs sa;
-    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project) -> cudaError_t {
+    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project, bool fused) -> cudaError_t {
         memset(&sa, 0, offsetof(ShArgs, dyn));
         fill_geom_args(sa, h->geoms[G.geom]);
         sa.inst = h->d_inst;
@@ -445,6 +447,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.cta_warps = G.cta_warps;
         sa.n_inst = 1;
         sa.work = h->d_work + 2 * (&G - h->groups.data());
+        sa.project = fused ? 1 : 0;
         sa.dyn[0] = dyn;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
         cudaError_t err = launch_spot(G.kind, sa, ls, after_project && !h->timing);
@@ -459,18 +462,21 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         if (k == 0 && (e = cudaEventRecord(h->ev_fork, stream)) != cudaSuccess) return cuda_fail(h, e, "fork");
         cudaStream_t ss = h->side[k];
         if ((e = cudaStreamWaitEvent(ss, h->ev_fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork wait");
-        if ((e = project(G.first, G.count, G.proj_base, G.proj_count, ss)) != cudaSuccess)
-            return cuda_fail(h, e, "projection launch");
-        if ((e = launch_group(G, ss, G.proj_count > 0)) != cudaSuccess) return cuda_fail(h, e, "spot launch");
+        // a generic-kernel group (a few NGS subapertures) projects inside its spot kernel: one
+        // launch that starts with the call and owns its SMs only while it runs
+        const bool fused = G.kind == kSpotGeneric;
+        if (!fused && (e = project(G, ss)) != cudaSuccess) return cuda_fail(h, e, "projection launch");
+        if ((e = launch_group(G, ss, !fused && G.proj_count > 0, fused)) != cudaSuccess)
+            return cuda_fail(h, e, "spot launch");
         if ((e = cudaEventRecord(h->ev_join[k], ss)) != cudaSuccess) return cuda_fail(h, e, "join");
         ++k;
     }
     if (!h->groups.empty()) {
         const SpotGroup &G = h->groups[big];
         // with a single group this projects every WFS (blocks 0 .. proj_blocks)
-        if ((e = project(G.first, G.count, G.proj_base, G.proj_count, stream)) != cudaSuccess)
+        if ((e = project(G, stream)) != cudaSuccess)
             return cuda_fail(h, e, "projection launch");
-        if (G.total > 0 && (e = launch_group(G, stream, G.proj_count > 0)) != cudaSuccess)
+        if (G.total > 0 && (e = launch_group(G, stream, G.proj_count > 0, false)) != cudaSuccess)
             return cuda_fail(h, e, "spot launch");
     }
     for (size_t j = 0; j < k; ++j)
@@ -741,8 +747,8 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
     if ((e = cudaMalloc(&h->d_opd, (opd ? opd : 1) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_work, 2 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
-        (e = cudaMemset(h->d_work, 0, 2 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_work, 4 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
+        (e = cudaMemset(h->d_work, 0, 4 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         release(h);
         delete h;
@@ -1154,7 +1160,10 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     std::vector<InstDesc> inst(n);
     for (int i = 0; i < n; ++i) inst[i] = hs[i]->inst_host;
     cudaError_t e;
-    const size_t work_bytes = 2 * sizeof(int) * b->classes.size() * (1 + kBatchSlots) + 2 * sizeof(int);
+    // spot counters (a pair per class, then per slot and class), then projection counters (the
+    // graph's pair, then a pair per slot)
+    const size_t proj_off = 2 * b->classes.size() * (1 + kBatchSlots);
+    const size_t work_bytes = sizeof(int) * (proj_off + 2 * (1 + kBatchSlots) + 2);
     if ((e = upload(&b->d_inst, inst)) != cudaSuccess || (e = upload(&b->d_wfs, b->wfs_host)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_work, work_bytes)) != cudaSuccess || (e = cudaMemset(b->d_work, 0, work_bytes)) != cudaSuccess) {
         batch_free(b);
@@ -1167,6 +1176,8 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     b->pa->n_wfs = (int)b->wfs_host.size();
     b->pa->n_inst = n;
     b->pa->box_cap = b->proj_box;
+    b->pa->n_blocks = b->proj_blocks;
+    b->pa->work = b->d_work + 2 * b->classes.size() * (1 + kBatchSlots);
     b->pa->status = hs[0]->d_status;
     for (const BatchClass &bc : b->classes) {
         ShArgs *a = new ShArgs();
@@ -1285,6 +1296,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
     pa.wfs = sl.d;
     pa.n_wfs = count;
     pa.block_base = 0;
+    pa.work = b->d_work + 2 * b->classes.size() * (1 + kBatchSlots) + 2 * (1 + (size_t)slot);
     pa.n_inst = n;
     pa.box_cap = box;
     pa.status = b->hs[0]->d_status;

@@ -67,8 +67,11 @@ struct ProjArgs {
     const WfsDesc *wfs;
     int n_wfs, n_inst;
     int box_cap;                    // floats of shared memory for tables and screen box
-    int block_base;                 // projection block of this launch's first CTA (a launch
+    int block_base;                 // projection block of this launch's first block (a launch
                                     // may cover a contiguous range of the WFS table)
+    int n_blocks;                   // blocks in this launch (set by the launcher)
+    int *work;                      // ticket counter pair {next, CTAs done}, zero between
+                                    // launches, one launch at a time; null = one CTA per block
     int *status;                    // device status word (limit errors)
     InstDyn dyn[kMaxInstances];
 };
@@ -91,6 +94,8 @@ struct ShArgs {
     // launches (the last CTA to finish resets it), used by one launch at a time; null = a
     // static split.
     int *work;
+    int project;         // generic kernel: 1 = project each subaperture's OPD from the screens
+                         // itself (no separate projection launch); written to dyn.opd too
     InstDyn dyn[kMaxInstances];
 };
 

@@ -1,23 +1,14 @@
-// k_project.cu -- layered frozen-flow projection (Sec. 4 "Open Loop
-// generation": the layers' screens are piled up, each shifted for the star's
-// direction and for the temporal evolution; for an LGS the pupil projection
-// shrinks with altitude, c = 1 - h / range).  No Fresnel propagation.
+// k_project.cu -- layered frozen-flow projection (Sec. 4 "Open Loop generation": the layers'
+// screens are piled up, each shifted for the star's direction and for the temporal evolution;
+// for an LGS the pupil projection shrinks with altitude, c = 1 - h / range).  No Fresnel
+// propagation.  The coordinate arithmetic (FP64 per-layer offsets, FP32 per-pixel term with an
+// exact two-float split) is in proj_math.cuh; it keeps long runs (large v t) exact to FP64
+// rounding and the fractional coordinate accurate to ~1e-7 px.
 //
-// For pupil pixel x (metres from the pupil centre) and layer l the sampled
-// screen coordinate, in screen pixels from the screen origin, is
-//     u = S/2 + (c_l x + theta h_l - (x0_l + v_l t)) / ds
-// split as  u = [S/2 + (theta h_l - x0_l - v_l t)/ds]  +  c_l (dx/ds) j'
-// where j' is the pixel's half-integer column offset from the pupil centre.
-// The first (time-dependent, possibly large) term is evaluated once per CTA
-// in FP64 and split into an integer base (mod S) and an FP32 fraction.  The
-// per-pixel term uses FP32 only: the scale c_l dx/ds is held as two floats
-// (hi + lo) and the product with j' is split exactly with an FMA, so the
-// fractional coordinate is accurate to ~1e-7 px even 400 px from the centre.
-// This keeps long runs (large v t) exact to FP64 rounding.
-//
-// Output layout: per WFS, [n_valid][n][n] (subaperture-tiled), so the spot
-// kernel reads each subaperture's n*n OPD as one contiguous block.
+// Output layout: per WFS, [n_valid][n][n] (subaperture-tiled), so the spot kernel reads each
+// subaperture's n*n OPD as one contiguous block.
 #include "internal.h"
+#include "proj_math.cuh"
 
 namespace gbwfs {
 
@@ -32,13 +23,12 @@ __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
     return r < 0 ? r + S : r;
 }
 
-__global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
-    allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
-    __shared__ int s_bu[kMaxLayers], s_bv[kMaxLayers];
-    __shared__ float s_fu[kMaxLayers], s_fv[kMaxLayers], s_c[kMaxLayers], s_cl[kMaxLayers];
+// One projection block (a tiled segment, or kProjThreads 2x2 pixel blocks); every thread of
+// the CTA calls it (its shared memory is free again once all threads have returned).
+__device__ __forceinline__ void project_one(const ProjArgs &a, const int bid) {
+    __shared__ LayerOffs s_off[kMaxLayers];
 
-    // the WFS owning this CTA: last entry whose first CTA is <= bid
-    const int bid = (int)blockIdx.x + a.block_base;
+    // the WFS owning this block: last entry whose first block is <= bid
     int lo = 0, hi = a.n_wfs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -50,41 +40,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     const InstDyn &D = a.dyn[W.inst];
     const int S = I.S;
 
-    if ((int)threadIdx.x < I.n_layers) {
-        const int l = threadIdx.x;
-        const double h = I.alt[l];
-        const double c = W.is_lgs ? 1.0 - h / W.range_m : 1.0;
-        const double inv_ds = 1.0 / I.ds;
-        const double ou = 0.5 * S + (W.theta_x * h - (I.x0[l] + I.vx[l] * D.t)) * inv_ds;
-        const double ov = 0.5 * S + (W.theta_y * h - (I.y0[l] + I.vy[l] * D.t)) * inv_ds;
-        const double bu = floor(ou), bv = floor(ov);
-        s_fu[l] = (float)(ou - bu);
-        s_fv[l] = (float)(ov - bv);
-        // base index mod S (exact: bu, bv are integers well inside 2^53)
-        long long iu = (long long)bu % S, iv = (long long)bv % S;
-        if (iu < 0) iu += S;
-        if (iv < 0) iv += S;
-        s_bu[l] = (int)iu;
-        s_bv[l] = (int)iv;
-        const double cs = c * W.pupil_dx_over_ds;
-        s_c[l] = (float)cs;
-        s_cl[l] = (float)(cs - (double)s_c[l]);
-    }
+    if ((int)threadIdx.x < I.n_layers) s_off[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
     __syncthreads();
 
     const bool pow2 = (S & (S - 1)) == 0;
     if (W.tiled) {
-        // one run of consecutive subapertures of one subaperture row; each layer's screen
-        // footprint is staged in shared memory (cp.async, double-buffered so the next layer
-        // streams in while this one is interpolated); coordinates come from per-column and
-        // per-row tables (a pixel's screen column depends on its pupil column only)
+        // One run of consecutive subapertures of one subaperture row.  Each layer's screen
+        // footprint is staged in shared memory by cp.async; coordinates come from per-column
+        // and per-row tables (a pixel's screen column depends on its pupil column only).
+        // Tables and boxes are triple-buffered: in iteration l the CTA fills buffer
+        // (l + 1) mod 3, last read by layer l - 2, which every thread finished before the
+        // previous barrier; so one barrier per layer suffices (box l landed, tables l visible).
         extern __shared__ float psm[];
+        __shared__ int4 s_geom[kMaxLayers];  // per layer: box origin (bx0, by0) and size (bw, bh)
         const int4 sg = W.segs[bid - W.proj_block_begin];  // sy, v_first, count, sx0
-        const int n = W.n, nn = n * n, ncol = sg.z * n;
-        const int box_floats = ((a.box_cap - ((4 * (ncol + n) + 3) & ~3)) / 2) & ~3;
-        float2 *tab[2] = {reinterpret_cast<float2 *>(psm), reinterpret_cast<float2 *>(psm) + (ncol + n)};
-        const int box_off = (4 * (ncol + n) + 3) & ~3;  // 16-byte aligned boxes
-        float *boxb[2] = {psm + box_off, psm + box_off + (box_floats & ~3)};
+        const int n = W.n, nn = n * n, ncol = sg.z * n, L = I.n_layers;
+        const int tab_floats = (6 * (ncol + n) + 3) & ~3;  // three tables, 16-byte aligned boxes
+        const int box_floats = ((a.box_cap - tab_floats) / 3) & ~3;
+        // buffer i: tables at tab0 + i (ncol + n), box at box0 + i box_floats
+        float2 *const tab0 = reinterpret_cast<float2 *>(psm);
+        float *const box0 = psm + tab_floats;
         const float half = 0.5f * (float)(W.n_sub * n - 1);
         // thread -> (pupil row p, columns ch + k nch, k < kTilePx): lanes of a warp take
         // consecutive columns of one row, so their table and box reads fall in distinct banks
@@ -94,43 +69,45 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
         float acc[kTilePx];
 #pragma unroll
         for (int k = 0; k < kTilePx; ++k) acc[k] = 0.0f;
-        auto tables = [&](int l, float2 *t) {
-            const float ch = s_c[l], cl = s_cl[l];
-            for (int j = threadIdx.x; j < ncol + n; j += kProjThreads) {
-                const bool col = j < ncol;
-                const float xr = col ? (float)(sg.w * n + j) - half : (float)(sg.x * n + (j - ncol)) - half;
-                const float ph = __fmul_rn(ch, xr), pl = fmaf(ch, xr, -ph) + cl * xr;
-                const float ih = floorf(ph);
-                const float ru = ((ph - ih) + pl) + (col ? s_fu[l] : s_fv[l]);
-                const float iu = floorf(ru);
-                t[j] = make_float2(__int_as_float((int)ih + (int)iu), ru - iu);
-            }
+        // table entry j of layer l (column j < ncol, else row j - ncol): integer screen offset
+        // from the layer base (as float bits) and the fraction
+        auto coord = [&](int l, int j) -> float2 {
+            const bool col = j < ncol;
+            const float xr = col ? (float)(sg.w * n + j) - half : (float)(sg.x * n + (j - ncol)) - half;
+            int off;
+            float frac;
+            screen_offset(s_off[l].c, s_off[l].cl, col ? s_off[l].fu : s_off[l].fv, xr, off, frac);
+            return make_float2(__int_as_float(off), frac);
         };
-        // Box origin (relative to the layer base) and width, the origin rounded down so that
-        // the box's first screen column is a multiple of 4 (16-byte copies when S % 4 == 0).
+        auto tables = [&](int l, float2 *t) {
+            for (int j = threadIdx.x; j < ncol + n; j += kProjThreads) t[j] = coord(l, j);
+        };
+        // Box origin (relative to the layer base) and size, the origin rounded down so that the
+        // box's first screen column is a multiple of 4 (16-byte copies when S % 4 == 0).
         const bool vec = (S & 3) == 0;
-        auto box_geom = [&](int l, const float2 *t, int &bx0, int &by0, int &bw, int &bh) {
-            bx0 = __float_as_int(t[0].x);
-            by0 = __float_as_int(t[ncol].x);
-            bw = __float_as_int(t[ncol - 1].x) - bx0 + 2;
-            bh = __float_as_int(t[ncol + n - 1].x) - by0 + 2;
+        if ((int)threadIdx.x < L) {
+            const int l = threadIdx.x;
+            int bx0 = __float_as_int(coord(l, 0).x), by0 = __float_as_int(coord(l, ncol).x);
+            int bw = __float_as_int(coord(l, ncol - 1).x) - bx0 + 2;
+            const int bh = __float_as_int(coord(l, ncol + n - 1).x) - by0 + 2;
             if (vec) {
-                const int off = wrap_index(s_bu[l] + bx0, S, pow2) & 3;
+                const int off = wrap_index(s_off[l].bu + bx0, S, pow2) & 3;
                 bx0 -= off;
                 bw = (bw + off + 3) & ~3;
             }
-        };
+            s_geom[l] = make_int4(bx0, by0, bw, bh);
+        }
         // returns false (for every thread) when the box would not fit
-        auto issue_box = [&](int l, const float2 *t, float *box) -> bool {
-            int bx0, by0, bw, bh;
-            box_geom(l, t, bx0, by0, bw, bh);
+        auto issue_box = [&](int l, float *box) -> bool {
+            const int4 gm = s_geom[l];
+            const int bx0 = gm.x, by0 = gm.y, bw = gm.z, bh = gm.w;
             if (bw * bh > box_floats) return false;
             const float *scr = D.screens + (size_t)l * S * S;
             if (vec) {
                 // one warp per box row, one lane per 16-byte chunk
-                const int cw = bw >> 2, lane = threadIdx.x & 31, cbase = s_bu[l] + bx0;
+                const int cw = bw >> 2, lane = threadIdx.x & 31, cbase = s_off[l].bu + bx0;
                 for (int r = threadIdx.x >> 5; r < bh; r += kProjThreads / 32) {
-                    const float *srow = scr + (size_t)wrap_index(s_bv[l] + by0 + r, S, pow2) * S;
+                    const float *srow = scr + (size_t)wrap_index(s_off[l].bv + by0 + r, S, pow2) * S;
                     float *drow = box + r * bw;
                     for (int c4 = lane; c4 < cw; c4 += 32) {
                         const float *src = srow + wrap_index(cbase + 4 * c4, S, pow2);
@@ -140,9 +117,9 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
                 }
             } else {
                 for (int r = 0; r < bh; ++r) {
-                    const float *grow = scr + (size_t)wrap_index(s_bv[l] + by0 + r, S, pow2) * S;
+                    const float *grow = scr + (size_t)wrap_index(s_off[l].bv + by0 + r, S, pow2) * S;
                     for (int c = threadIdx.x; c < bw; c += kProjThreads) {
-                        const float *src = grow + wrap_index(s_bu[l] + bx0 + c, S, pow2);
+                        const float *src = grow + wrap_index(s_off[l].bu + bx0 + c, S, pow2);
                         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(box + r * bw + c);
                         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
                     }
@@ -151,29 +128,29 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
             asm volatile("cp.async.commit_group;" ::: "memory");
             return true;
         };
-        bool fits = true;
-        tables(0, tab[0]);
-        __syncthreads();
-        fits = issue_box(0, tab[0], boxb[0]);
-        for (int l = 0; l < I.n_layers && fits; ++l) {
-            const int cur = l & 1, nxt = cur ^ 1;
-            const bool more = l + 1 < I.n_layers;
-            if (more) tables(l + 1, tab[nxt]);
-            __syncthreads();
+        tables(0, tab0);
+        __syncthreads();  // geometry of every layer, tables of layer 0
+        bool fits = issue_box(0, box0);
+        for (int l = 0; l < L && fits; ++l) {
+            const int cur = l % 3, nxt = (l + 1) % 3;
+            const bool more = l + 1 < L;
             bool fits_next = true;
-            if (more) fits_next = issue_box(l + 1, tab[nxt], boxb[nxt]);
+            if (more) {
+                tables(l + 1, tab0 + nxt * (ncol + n));
+                fits_next = issue_box(l + 1, box0 + nxt * box_floats);
+            }
             if (more && fits_next)
                 asm volatile("cp.async.wait_group 1;" ::: "memory");
             else
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();
-            const float2 *t = tab[cur];
-            const float *box = boxb[cur];
-            int bx0, by0, bw, bh;
-            box_geom(l, t, bx0, by0, bw, bh);
+            const float2 *t = tab0 + cur * (ncol + n);
+            const float *box = box0 + cur * box_floats;
+            const int4 gm = s_geom[l];
+            const int bw = gm.z;
             if (has_task) {
                 const float2 rp = t[ncol + p];
-                const float *brow = box + (__float_as_int(rp.x) - by0) * bw - bx0;
+                const float *brow = box + (__float_as_int(rp.x) - gm.y) * bw - gm.x;
 #pragma unroll
                 for (int k = 0; k < kTilePx; ++k) {
                     const int j = ch + k * nch;
@@ -187,7 +164,6 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
                     }
                 }
             }
-            __syncthreads();  // this layer's tables and box are free for layer l + 2
             fits = fits_next;
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -228,7 +204,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
     }
     float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     for (int l = 0; l < I.n_layers; ++l) {
-        const float ch = s_c[l], cl = s_cl[l];
+        const LayerOffs lo = s_off[l];
         const float *scr = D.screens + (size_t)l * S * S;
         int ci0[2], ci1[2];
         float fx[2];
@@ -236,36 +212,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
         float gy[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            // c * x = ph + pl exactly (to FP32 rounding of the small part)
-            const float ph = __fmul_rn(ch, xr[j]), pl = fmaf(ch, xr[j], -ph) + cl * xr[j];
-            const float ih = floorf(ph);
-            const float ru = ((ph - ih) + pl) + s_fu[l];  // in [-eps, 2)
-            const float iu = floorf(ru);
-            fx[j] = ru - iu;
-            int i0 = s_bu[l] + (int)ih + (int)iu;
-            const float qh = __fmul_rn(ch, yr[j]), ql = fmaf(ch, yr[j], -qh) + cl * yr[j];
-            const float jh = floorf(qh);
-            const float rv = ((qh - jh) + ql) + s_fv[l];
-            const float jv = floorf(rv);
-            gy[j] = rv - jv;
-            int j0 = s_bv[l] + (int)jh + (int)jv;
-            int i1, j1;
-            if (pow2) {
-                i0 &= S - 1;
-                j0 &= S - 1;
-                i1 = (i0 + 1) & (S - 1);
-                j1 = (j0 + 1) & (S - 1);
-            } else {
-                // |c x / ds| < S is enforced when the handle is created: one wrap suffices
-                i0 += (i0 < 0) ? S : 0;
-                i0 -= (i0 >= S) ? S : 0;
-                j0 += (j0 < 0) ? S : 0;
-                j0 -= (j0 >= S) ? S : 0;
-                i1 = (i0 + 1 == S) ? 0 : i0 + 1;
-                j1 = (j0 + 1 == S) ? 0 : j0 + 1;
-            }
-            ci0[j] = i0;
-            ci1[j] = i1;
+            int ou, ov, j0, j1;
+            screen_offset(lo.c, lo.cl, lo.fu, xr[j], ou, fx[j]);
+            screen_offset(lo.c, lo.cl, lo.fv, yr[j], ov, gy[j]);
+            wrap_pair(lo.bu + ou, S, pow2, ci0[j], ci1[j]);
+            wrap_pair(lo.bv + ov, S, pow2, j0, j1);
             row0[j] = scr + (size_t)j0 * S;
             row1[j] = scr + (size_t)j1 * S;
         }
@@ -288,6 +239,36 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
             if (p0 + a2 < n && q0 + b2 < n) opd[(p0 + a2) * n + q0 + b2] = acc[a2][b2];
 }
 
+// Blocks 0 .. n_blocks of this launch.  Each CTA starts with block blockIdx.x; with a.work the
+// grid holds only as many CTAs as fit at once and each draws its next block from the ticket
+// counter (issued at the top, consumed after the block), so CTAs that start late take fewer
+// blocks and no partial last wave is left; the last CTA to finish resets the counter.
+__global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
+    allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
+    __shared__ int s_next;
+    int blk = blockIdx.x;
+    while (blk < a.n_blocks) {
+        int ticket = 0;
+        if (a.work && threadIdx.x == 0) ticket = atomicAdd(a.work, 1);
+        project_one(a, blk + a.block_base);
+        __syncthreads();  // the block's shared memory is free; orders s_next
+        if (a.work) {
+            if (threadIdx.x == 0) s_next = (int)gridDim.x + ticket;
+            __syncthreads();
+            blk = s_next;
+        } else {
+            blk += gridDim.x;
+        }
+    }
+    if (a.work && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
+            a.work[0] = 0;
+            a.work[1] = 0;
+        }
+    }
+}
+
 int segment_max_count(int n) {
     // a segment of c subaperture columns has n rows x ceil(c n / kTilePx) column sets, one
     // per thread
@@ -304,9 +285,9 @@ int project_blocks(const WfsDesc &d) {
 
 int project_box_floats(const WfsDesc &d) {
     if (!d.tiled) return 0;
-    // two sets of coordinate tables (2 x (ncol + n) float2) and two boxes of at most
-    // (ncol + 2) x (n + 2) screen pixels (one per layer in flight)
-    return 4 * (d.seg_cols + d.n) + 4 + 2 * ((d.seg_cols + 9) * (d.n + 3) + 4);
+    // three sets of coordinate tables (3 x (ncol + n) float2) and three boxes of at most
+    // (ncol + 2) x (n + 2) screen pixels (padded for the 16-byte alignment)
+    return 6 * (d.seg_cols + d.n) + 4 + 3 * ((d.seg_cols + 9) * (d.n + 3) + 4);
 }
 
 void build_segments(const std::vector<int32_t> &ids, int n_sub, int max_count, std::vector<int4> &segs,
@@ -333,7 +314,9 @@ cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) 
     LaunchShape sh;
     cudaError_t e = project_launch_shape(a, total_blocks, &sh);
     if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&a};
+    ProjArgs b = a;
+    b.n_blocks = total_blocks;
+    void *args[] = {(void *)&b};
     return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
 }
 
@@ -341,8 +324,26 @@ cudaError_t project_launch_shape(const ProjArgs &a, int total_blocks, LaunchShap
     const size_t smem = (size_t)a.box_cap * sizeof(float) + (a.box_cap ? 64 : 0);
     cudaError_t e = cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int grid = total_blocks > 0 ? total_blocks : 1;
+    if (a.work) {
+        // resident capacity for this shared-memory size (cached per thread)
+        static thread_local size_t c_smem = (size_t)-1;
+        static thread_local int c_dev = -1, c_cap = 0;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (smem != c_smem || dev != c_dev) {
+            int per_sm = 0, sms = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project, kProjThreads, smem)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return e;
+            c_smem = smem;
+            c_dev = dev;
+            c_cap = per_sm * sms;
+        }
+        if (c_cap > 0 && grid > c_cap) grid = c_cap;
+    }
     out->func = (const void *)k_project;
-    out->grid = dim3(total_blocks > 0 ? total_blocks : 1);
+    out->grid = dim3(grid);
     out->block = dim3(kProjThreads);
     out->smem = smem;
     return cudaSuccess;

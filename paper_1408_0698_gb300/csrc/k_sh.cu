@@ -22,6 +22,7 @@
 
 #include "internal.h"
 #include "noise.cuh"
+#include "proj_math.cuh"
 
 namespace gbwfs {
 
@@ -40,7 +41,7 @@ __host__ __device__ inline int team_floats(int n, int N, int nd, int team) {
     r2 = r2 > nd * nd ? r2 : nd * nd;
     r2 += r2 & 1;
     const int red = 4 * (team / 32) + 4;
-    return ri + r1 + r2 + red;
+    return ri + r1 + r2 + red + 6 * kMaxLayers;  // then the layer offsets of a fused projection
 }
 
 template <int TEAM>
@@ -135,12 +136,50 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
 
         // field
         const float *opd = D.opd + W.opd_off + (size_t)v * nn;
+        float *so = reinterpret_cast<float *>(U);  // a fused projection's OPD (U is written later)
+        if (a.project) {
+            // this subaperture's OPD straight from the screens: the arithmetic of the projection
+            // kernel (layer offsets in FP64, bilinear samples summed over the layers in order)
+            LayerOffs *lo = reinterpret_cast<LayerOffs *>(red + 4 * (TEAM / 32) + 4);
+            const InstDesc &I = a.inst[W.inst];
+            if (tid < I.n_layers) lo[tid] = layer_offsets(I, W, D.t, tid);
+            team_sync<TEAM>(team);
+            const int S = I.S;
+            const bool pow2 = (S & (S - 1)) == 0;
+            const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
+            const float half = 0.5f * (float)(W.n_sub * n - 1);
+            float *out = D.opd + W.opd_off + (size_t)v * nn;
+            for (int i = tid; i < nn; i += TEAM) {
+                const int pp = i / n, qq = i - pp * n;
+                const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                float acc = 0.0f;
+                for (int l = 0; l < I.n_layers; ++l) {
+                    const LayerOffs L0 = lo[l];
+                    int ou, ov, i0, i1, j0, j1;
+                    float fx, gy;
+                    screen_offset(L0.c, L0.cl, L0.fu, xr, ou, fx);
+                    screen_offset(L0.c, L0.cl, L0.fv, yr, ov, gy);
+                    wrap_pair(L0.bu + ou, S, pow2, i0, i1);
+                    wrap_pair(L0.bv + ov, S, pow2, j0, j1);
+                    const float *scr = D.screens + (size_t)l * S * S;
+                    const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
+                    const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+                    const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+                    const float top = fmaf(fx, s01 - s00, s00);
+                    const float bot = fmaf(fx, s11 - s10, s10);
+                    acc += fmaf(gy, bot - top, top);
+                }
+                so[i] = acc;
+                out[i] = acc;
+            }
+            team_sync<TEAM>(team);
+        }
         const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
-        const float ref = __ldg(opd);
+        const float ref = a.project ? so[0] : __ldg(opd);
         for (int i = tid; i < nn; i += TEAM) {
             const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
             float s, c;
-            sincosf(W.k_phase * (__ldg(opd + i) - ref), &s, &c);
+            sincosf(W.k_phase * ((a.project ? so[i] : __ldg(opd + i)) - ref), &s, &c);
             X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
         }
         team_sync<TEAM>(team);
