@@ -7,6 +7,8 @@
 //
 // Output layout: per WFS, [n_valid][n][n] (subaperture-tiled), so the spot kernel reads each
 // subaperture's n*n OPD as one contiguous block.
+#include <algorithm>
+
 #include "internal.h"
 #include "proj_math.cuh"
 
@@ -25,7 +27,9 @@ __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
 
 // One projection block (a tiled segment, or kProjThreads 2x2 pixel blocks); every thread of
 // the CTA calls it (its shared memory is free again once all threads have returned).
-__device__ __forceinline__ void project_one(const ProjArgs &a, const int bid) {
+// last_wfs: the WFS whose layer offsets s_off holds (a persistent CTA skips the FP64 offsets
+// when consecutive blocks belong to the same WFS).
+__device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, int &last_wfs) {
     __shared__ LayerOffs s_off[kMaxLayers];
 
     // the WFS owning this block: last entry whose first block is <= bid
@@ -40,8 +44,11 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid) {
     const InstDyn &D = a.dyn[W.inst];
     const int S = I.S;
 
-    if ((int)threadIdx.x < I.n_layers) s_off[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
-    __syncthreads();
+    if (lo != last_wfs) {  // uniform: last_wfs was written before the caller's barrier
+        if ((int)threadIdx.x < I.n_layers) s_off[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x == 0) last_wfs = lo;  // read again only after the caller's barrier
+    }
 
     const bool pow2 = (S & (S - 1)) == 0;
     if (W.tiled) {
@@ -245,12 +252,14 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid) {
 // blocks and no partial last wave is left; the last CTA to finish resets the counter.
 __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
     allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
-    __shared__ int s_next;
+    __shared__ int s_next, s_last_wfs;
+    if (threadIdx.x == 0) s_last_wfs = -1;
+    __syncthreads();
     int blk = blockIdx.x;
     while (blk < a.n_blocks) {
         int ticket = 0;
         if (a.work && threadIdx.x == 0) ticket = atomicAdd(a.work, 1);
-        project_one(a, blk + a.block_base);
+        project_one(a, blk + a.block_base, s_last_wfs);
         __syncthreads();  // the block's shared memory is free; orders s_next
         if (a.work) {
             if (threadIdx.x == 0) s_next = (int)gridDim.x + ticket;
@@ -307,6 +316,8 @@ void build_segments(const std::vector<int32_t> &ids, int n_sub, int max_count, s
         segs.push_back(make_int4(sy, (int)v, 1, sx));
         if (*max_run < 1) *max_run = 1;
     }
+    // longest runs first: with the projection's ticket order the short ones fill the tail
+    std::stable_sort(segs.begin(), segs.end(), [](const int4 &x, const int4 &y) { return x.z > y.z; });
 }
 
 cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s) {

@@ -309,9 +309,16 @@ size_t sh_fp32_smem_bytes(int n, int N, int nd, int *team_threads, int *teams_pe
 }
 
 namespace {
+constexpr size_t kSelfProjectSmem = 160 * 1024;
+
 cudaError_t generic_shape(const ShArgs &a, LaunchShape *out) {
     int team = 0, teams = 0;
-    const size_t smem = sh_fp32_smem_bytes(a.n, a.N, a.nd, &team, &teams);
+    size_t smem = sh_fp32_smem_bytes(a.n, a.N, a.nd, &team, &teams);
+    // A self-projecting launch (a few NGS subapertures beside a large projection) asks for
+    // enough shared memory that no projection CTA (about 74 KB) fits on its SMs: it then runs
+    // alone there and finishes early instead of being stretched across the projection, which
+    // takes the freed SMs afterwards.
+    if (a.project && smem < kSelfProjectSmem) smem = kSelfProjectSmem;
     int blocks = (a.total + teams - 1) / teams;
     const int cap = a.grid_cap > 0 ? a.grid_cap : 152 * 32;
     if (blocks > cap) blocks = cap;
