@@ -122,6 +122,17 @@ __device__ __forceinline__ int find_wfs(const WfsDesc *w, int n, int g) {
 #endif
 
 // A launch as a graph kernel node: function, grid, block, dynamic shared memory.
+// exp(i phi) of the pupil field: Cody-Waite reduction (Cody and Waite, "Software Manual for
+// the Elementary Functions", 1980) of phi to [-pi, pi] with 2 pi held as two floats (the FP32
+// value of 2 pi and the remainder), then the hardware sine and cosine of the reduced argument.
+// Absolute error about 1e-6 for the phases of a wavefront sensor (|phi| up to ~1e3).
+__device__ __forceinline__ void field_phasor(float phi, float &s, float &c) {
+    const float m = rintf(phi * 0.159154943f);  // round(phi / (2 pi))
+    float r = fmaf(-m, 6.28318548f, phi);
+    r = fmaf(-m, -1.74845553e-7f, r);
+    __sincosf(r, &s, &c);
+}
+
 // Programmatic dependent launch: the projection lets the next grid on its stream start
 // early; a spot kernel blocks here until the preceding grid has completed and its writes are
 // visible (a no-op when the launch had no programmatic dependency).

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
         for (int i = tid; i < nn; i += TEAM) {
             const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
             float s, c;
-            sincosf(W.k_phase * ((a.project ? so[i] : __ldg(opd + i)) - ref), &s, &c);
+            field_phasor(W.k_phase * ((a.project ? so[i] : __ldg(opd + i)) - ref), s, c);
             X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
         }
         team_sync<TEAM>(team);

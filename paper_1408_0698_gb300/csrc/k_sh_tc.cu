@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             for (int i = lane; i < n * n; i += 32) {
                 const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                 float s, c;
-                sincosf(W.k_phase * (__ldg(opd + i) - ref), &s, &c);
+                field_phasor(W.k_phase * (__ldg(opd + i) - ref), s, c);
                 X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
             }
             __syncwarp();
