@@ -90,6 +90,7 @@ struct wfs_ctx {
     int total_valid = 0;
     int *d_status = nullptr;
     int *d_work = nullptr;  // ticket counters: a pair per spot group, then a pair per group's projection
+    float *d_E = nullptr;   // expected images of the split noise pass (det_total floats)
     // host-buffer path: two staging buffer sets used alternately, uploads on a copy stream
     float *d_screens_stage[2] = {nullptr, nullptr};
     float *d_slopes_stage[2] = {nullptr, nullptr};
@@ -138,6 +139,7 @@ struct wfs_batch_ctx {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t proj_node = nullptr;
     std::vector<cudaGraphNode_t> spot_nodes;  // per class (null when the class is empty)
+    std::vector<cudaGraphNode_t> noise_nodes; // per class (null unless the class splits its noise pass)
     int use_graph = 1;
     // subset calls: per slot, a pinned staging table, its device copy and a copy-done event
     struct Slot {
@@ -287,6 +289,7 @@ void release(wfs_ctx *h) {
     cudaFree(h->d_opd);
     cudaFree(h->d_status);
     cudaFree(h->d_work);
+    cudaFree(h->d_E);
     cudaFree(h->d_inst);
     cudaFree(h->d_wfs);
     for (int i = 0; i < 2; ++i) {
@@ -400,7 +403,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     dyn.opd = (st && st->opd) ? st->opd : h->d_opd;
     dyn.slopes = slopes;
     dyn.st_I = st ? st->intensity : nullptr;
-    dyn.st_E = st ? st->expected : nullptr;
+    dyn.st_E = (st && st->expected) ? st->expected : h->d_E;  // the split noise pass reads E back
     dyn.st_C = st ? st->counts : nullptr;
     dyn.t = t;
     dyn.noise = h->noise;
@@ -448,10 +451,16 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.n_inst = 1;
         sa.work = h->d_work + 2 * (&G - h->groups.data());
         sa.project = fused ? 1 : 0;
+        sa.split_noise = splits_noise(G.kind) ? 1 : 0;
         sa.dyn[0] = dyn;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
         cudaError_t err = launch_spot(G.kind, sa, ls, after_project && !h->timing);
         timed_end(h, sl, ls);
+        if (err == cudaSuccess && sa.split_noise) {
+            long sn = timed_begin(h, "noise_cog", ls);
+            err = launch_noise_cog(sa, ls, !h->timing);
+            timed_end(h, sn, ls);
+        }
         return err;
     };
     size_t k = 0;
@@ -745,6 +754,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
     h->int_total = inten;
     h->det_total = det;
     if ((e = cudaMalloc(&h->d_opd, (opd ? opd : 1) * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_E, (det ? det : 1) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_status, sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(h->d_status, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&h->d_work, 4 * sizeof(int) * (h->groups.size() + 1))) != cudaSuccess ||
@@ -953,6 +963,7 @@ void batch_drop_graph(wfs_batch b) {
     b->graph = nullptr;
     b->proj_node = nullptr;
     b->spot_nodes.clear();
+    b->noise_nodes.clear();
 }
 
 // Per-call parameters of every node.
@@ -968,6 +979,7 @@ wfs_status batch_fill(wfs_batch b, const float *const *screens, const double *t,
         d.slopes = slopes[i];
         d.t = t[i];
         d.noise = b->hs[i]->noise;
+        d.st_E = b->hs[i]->d_E;
         b->hs[i]->last_stream = nullptr;
     }
     for (size_t c = 0; c < b->classes.size(); ++c) {
@@ -994,6 +1006,7 @@ cudaError_t batch_build_graph(wfs_batch b) {
     kp.kernelParams = pargs;
     if ((e = cudaGraphAddKernelNode(&b->proj_node, b->graph, nullptr, 0, &kp)) != cudaSuccess) return e;
     b->spot_nodes.assign(b->classes.size(), nullptr);
+    b->noise_nodes.assign(b->classes.size(), nullptr);
     for (size_t c = 0; c < b->classes.size(); ++c) {
         if (b->classes[c].total <= 0) continue;
         LaunchShape sh;
@@ -1006,6 +1019,16 @@ cudaError_t batch_build_graph(wfs_batch b) {
         kp.sharedMemBytes = (unsigned)sh.smem;
         kp.kernelParams = sargs;
         if ((e = cudaGraphAddKernelNode(&b->spot_nodes[c], b->graph, &b->proj_node, 1, &kp)) != cudaSuccess) return e;
+        if (!b->sa[c]->split_noise) continue;
+        if ((e = noise_cog_launch_shape(*b->sa[c], &sh)) != cudaSuccess) return e;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)sh.func;
+        kp.gridDim = sh.grid;
+        kp.blockDim = sh.block;
+        kp.sharedMemBytes = (unsigned)sh.smem;
+        kp.kernelParams = sargs;
+        if ((e = cudaGraphAddKernelNode(&b->noise_nodes[c], b->graph, &b->spot_nodes[c], 1, &kp)) != cudaSuccess)
+            return e;
     }
     return cudaGraphInstantiate(&b->exec, b->graph, 0);
 }
@@ -1035,6 +1058,15 @@ cudaError_t batch_update_graph(wfs_batch b) {
         kp.sharedMemBytes = (unsigned)sh.smem;
         kp.kernelParams = sargs;
         if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->spot_nodes[c], &kp)) != cudaSuccess) return e;
+        if (!b->noise_nodes[c]) continue;
+        if ((e = noise_cog_launch_shape(*b->sa[c], &sh)) != cudaSuccess) return e;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)sh.func;
+        kp.gridDim = sh.grid;
+        kp.blockDim = sh.block;
+        kp.sharedMemBytes = (unsigned)sh.smem;
+        kp.kernelParams = sargs;
+        if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->noise_nodes[c], &kp)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -1042,8 +1074,10 @@ cudaError_t batch_update_graph(wfs_batch b) {
 cudaError_t batch_launch_direct(wfs_batch b, cudaStream_t s) {
     cudaError_t e = launch_project(*b->pa, b->proj_blocks, s);
     if (e != cudaSuccess) return e;
-    for (size_t c = 0; c < b->classes.size(); ++c)
+    for (size_t c = 0; c < b->classes.size(); ++c) {
         if ((e = launch_spot(b->classes[c].kind, *b->sa[c], s)) != cudaSuccess) return e;
+        if (b->sa[c]->split_noise && (e = launch_noise_cog(*b->sa[c], s, false)) != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 
@@ -1190,6 +1224,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
         a->status = hs[0]->d_status;
         a->n_inst = n;
         a->work = b->d_work + 2 * b->sa.size();
+        a->split_noise = splits_noise(bc.kind) ? 1 : 0;
         b->sa.push_back(a);
     }
     const char *g = getenv("GBWFS_BATCH_GRAPH");
@@ -1268,6 +1303,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
             d.slopes = slopes_out[pos[i]];
             d.t = t_s[pos[i]];
             d.noise = b->hs[i]->noise;
+            d.st_E = b->hs[i]->d_E;
         }
     int count = 0, blocks = 0, box = 0;
     std::vector<int> cls_first(b->classes.size()), cls_count(b->classes.size()), cls_total(b->classes.size());
@@ -1316,9 +1352,12 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
         sa.cta_warps = bc.cta_warps;
         sa.n_inst = n;
         sa.work = b->d_work + 2 * (b->classes.size() * (1 + (size_t)slot) + c);
+        sa.split_noise = splits_noise(bc.kind) ? 1 : 0;
         memcpy(sa.dyn, pa.dyn, sizeof(InstDyn) * n);
         if ((e = launch_spot(bc.kind, sa, (cudaStream_t)stream)) != cudaSuccess)
             return cuda_fail(nullptr, e, "batch subset spot launch");
+        if (sa.split_noise && (e = launch_noise_cog(sa, (cudaStream_t)stream, false)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "batch subset noise launch");
     }
     return WFS_OK;
 }

@@ -96,6 +96,8 @@ struct ShArgs {
     int *work;
     int project;         // generic kernel: 1 = project each subaperture's OPD from the screens
                          // itself (no separate projection launch); written to dyn.opd too
+    int split_noise;     // 32-point kernels: 1 = store the expected image (dyn.st_E, required)
+                         // and stop; launch_noise_cog completes the measurement
     InstDyn dyn[kMaxInstances];
 };
 
@@ -171,6 +173,12 @@ cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out);
 // before the projection has finished (programmatic dependent launch); the spot kernels wait
 // for the preceding grid to complete before they read its output.
 cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s, bool after_project = false);
+// Noise and centroid of a 32-point group launched with split_noise (n_det = 16); after_spot:
+// follows that spot kernel on s as a programmatic dependent launch.
+cudaError_t launch_noise_cog(const ShArgs &a, cudaStream_t s, bool after_spot);
+cudaError_t noise_cog_launch_shape(const ShArgs &a, LaunchShape *out);
+// Whether a spot kind stores expected images and leaves noise and centroid to k_noise_cog.
+inline bool splits_noise(int kind) { return kind == kSpotN32 || kind == kSpotTc; }
 // Swizzled BF16 operand tiles of the two constant matrices (F^T blocks, Ga blocks),
 // from FP64 tables laid out [q][m] (F) and [d][k] (Ga).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,

@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     tail::fill_fft_table(fft, threadIdx.x, blockDim.x);
     __syncthreads();
     wait_prior_grid();
+    if (a.split_noise) allow_dependent_grid();  // the noise kernel may take SMs as CTAs retire
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float2 *X = sm2 + Lay::table + wib * Lay::warp + Lay::wX;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             __syncwarp();
             tail::ngs_binned<nd>(Iw, lane, Bv);
         }
-        tail::finish<nd>(Bv, W, D, seed, v, lane, rk);
+        tail::finish<nd>(Bv, W, D, seed, v, lane, rk, a.split_noise != 0);
         g = a.work ? nwarps + __shfl_sync(0xffffffffu, ticket, 0) : g + nwarps;
     }
     if (a.work) {

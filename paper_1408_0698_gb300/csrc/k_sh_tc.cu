@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     fence_after_sync();
     const uint32_t tmem_all = *tslot;
     wait_prior_grid();
+    if (a.split_noise) allow_dependent_grid();  // the noise kernel may take SMs as CTAs retire
     const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
     constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
         else
             tail::ngs_binned<nd>(Iw, lane, Bv);
-        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk);
+        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);
     }
     fence_before_sync();
     __syncthreads();

@@ -149,17 +149,13 @@ __device__ __forceinline__ void ngs_binned(const float *Iw, int lane, float (&Bv
     }
 }
 
-// Photometry, noise and the centroid of subaperture v of WFS W; lane 0 writes the slopes.
-// rk: RN(1/k) table (fill_recip_table) in shared memory.  One generator block per pixel
-// pair; each exchange between the lane pair is followed by both pixels' inversion searches,
-// and the rare pixels with E >= 16 go last through one PTRS call site.
+// Photometry: ev[j] = E of detector row half * nd/2 + j, column ix (lane = half * 16 + ix),
+// E = photons fill B / sum B.
 template <int nd>
-__device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc &W, const InstDyn &D,
-                                       uint64_t seed, int v, int lane, const float *rk) {
-    constexpr int nd2 = nd * nd, J = nd / 2;
-    static_assert(nd == 16, "pixel pairs are the lane pairs (ix, ix + 1) of a 16-lane row");
-    const int ix = lane & 15, half = lane >> 4;
-    const float cd = 0.5f * (float)(nd - 1);
+__device__ __forceinline__ void expected(const float (&Bv)[nd / 2], const WfsDesc &W, int v, int lane,
+                                         float (&ev)[nd / 2]) {
+    constexpr int J = nd / 2;
+    const int ix = lane & 15;
     float sb = 0.0f;
     if (ix < nd) {
 #pragma unroll
@@ -167,9 +163,36 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
     }
     sb = warp_sum(sb);
     const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
+#pragma unroll
+    for (int j = 0; j < J; ++j) ev[j] = scale * Bv[j];
+}
+
+// Stores E of subaperture v to D.st_E (when given).
+template <int nd>
+__device__ __forceinline__ void store_expected(const float (&ev)[nd / 2], const WfsDesc &W, const InstDyn &D,
+                                               int v, int lane) {
+    constexpr int nd2 = nd * nd, J = nd / 2;
+    const int ix = lane & 15, half = lane >> 4;
+    if (!D.st_E || ix >= nd) return;
+    float *st_E = D.st_E + W.det_off + (size_t)v * nd2;
+#pragma unroll
+    for (int j = 0; j < J; ++j) st_E[(half * J + j) * nd + ix] = ev[j];
+}
+
+// Noise and the centroid of subaperture v of WFS W from its expected image ev (the layout of
+// expected()); lane 0 writes the slopes.  rk: RN(1/k) table (fill_recip_table) in shared
+// memory.  One generator block per pixel pair; each exchange between the lane pair is followed
+// by both pixels' inversion searches, and the rare pixels with E >= 16 go last through one PTRS
+// call site.
+template <int nd>
+__device__ __forceinline__ void noise_centroid(const float (&ev)[nd / 2], const WfsDesc &W, const InstDyn &D,
+                                               uint64_t seed, int v, int lane, const float *rk) {
+    constexpr int nd2 = nd * nd, J = nd / 2;
+    static_assert(nd == 16, "pixel pairs are the lane pairs (ix, ix + 1) of a 16-lane row");
+    const int ix = lane & 15, half = lane >> 4;
+    const float cd = 0.5f * (float)(nd - 1);
     const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
     const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
-    float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
     float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
     float sc = 0.0f, sx = 0.0f, sy = 0.0f;
     if (ix < nd) {
@@ -195,7 +218,7 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
                 z[m] = par ? zr : zo;
                 z[m + J / 2] = par ? zo : zr;
                 const float ua = par ? ur : uo, ub = par ? uo : ur;
-                const float ea = scale * Bv[m], eb = scale * Bv[m + J / 2];
+                const float ea = ev[m], eb = ev[m + J / 2];
                 int ka = 0, kb = 0;
                 if (ea >= 16.0f) big |= 1u << m;
                 else if (ea > 0.0f) ka = poisson_inversion<true>(ea, ua, expf(-ea), rk);
@@ -211,7 +234,7 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
 #pragma unroll
                 for (int jj = 0; jj < J; ++jj)
                     if (jj == j) {
-                        e = scale * Bv[jj];
+                        e = ev[jj];
                         zj = z[jj];
                     }
                 const PairStream q = pair_stream(seed, pix0 + (uint32_t)(j * nd), (uint32_t)W.gs_index, tlo, thi);
@@ -222,12 +245,11 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < J; ++j) cv[j] = scale * Bv[j];
+            for (int j = 0; j < J; ++j) cv[j] = ev[j];
         }
 #pragma unroll
         for (int j = 0; j < J; ++j) {
             const int iy = half * J + j, o = iy * nd + ix;
-            if (st_E) st_E[(size_t)v * nd2 + o] = scale * Bv[j];
             if (st_C) st_C[(size_t)v * nd2 + o] = cv[j];
             sc += cv[j];
             sx = fmaf((float)ix - cd, cv[j], sx);
@@ -243,6 +265,17 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
         sl[2 * v] = ok ? sx / sc : 0.0f;
         sl[2 * v + 1] = ok ? sy / sc : 0.0f;
     }
+}
+
+// Photometry, noise and the centroid in one pass (the spot kernel completes the measurement);
+// with split, only the expected image is stored and the noise kernel completes it.
+template <int nd>
+__device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc &W, const InstDyn &D,
+                                       uint64_t seed, int v, int lane, const float *rk, bool split) {
+    float ev[nd / 2];
+    expected<nd>(Bv, W, v, lane, ev);
+    store_expected<nd>(ev, W, D, v, lane);
+    if (!split) noise_centroid<nd>(ev, W, D, seed, v, lane, rk);
 }
 
 }  // namespace tail
