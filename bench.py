@@ -48,19 +48,23 @@ def peaks():
 
 
 def spot_flops(n, N, nd, lgs):
-    """FP32 flops (FMA = 2) of one subaperture in the spot kernels: DFT 8Nn(n+N), |.|^2 3N^2,
-    photometry and centroid 6 nd^2; NGS binning N^2.  LGS elongation and binning through the
-    transfer function: Ta 4N^2 n, then
+    """FP32 flops (FMA = 2) of one subaperture in its spot kernel: DFT 8Nn(n+N), |.|^2 3N^2.
+    LGS elongation and binning through the transfer function: Ta 4N^2 n, then
       32-point kernels: M as a radix-2 DFT across the lanes, 10 log2(N) N n, times the phase
-      and Kt 12 (2n-1) n; Q = G^T M 8 (2n-1) n nd; B = Re Q G 4 nd^2 n;
-      other sizes (direct sums): M (2n-1) n (8N+6); P = M G 8 (2n-1) nd n; B 4 nd^2 (2n-1)."""
-    f = 8 * N * n * (n + N) + 3 * N * N + 6 * nd * nd
+      and Kt 12 (2n-1) n; Q = G^T M 8 (2n-1) n nd; B = Re Q G 4 nd^2 n; photometry 2 nd^2
+      (the centroid, 4 nd^2, runs in the separate noise pass);
+      other sizes (direct sums): M (2n-1) n (8N+6); P = M G 8 (2n-1) nd n; B 4 nd^2 (2n-1);
+      photometry and centroid 6 nd^2.
+    NGS: binning N^2, photometry and centroid 6 nd^2."""
+    f = 8 * N * n * (n + N) + 3 * N * N
     if lgs and N == 32:
         f += 4 * N * N * n + 10 * 5 * N * n + 12 * (2 * n - 1) * n + 8 * (2 * n - 1) * n * nd + 4 * nd * nd * n
+        f += 2 * nd * nd
     elif lgs:
         f += 4 * N * N * n + (2 * n - 1) * n * (8 * N + 6) + 8 * (2 * n - 1) * nd * n + 4 * nd * nd * (2 * n - 1)
+        f += 6 * nd * nd
     else:
-        f += N * N
+        f += N * N + 6 * nd * nd
     return f
 
 
@@ -72,10 +76,11 @@ def source_sha(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "internal.h"],
-                  "spot_n32": ["k_sh_n32.cu", "noise.cuh", "internal.h"],
-                  "spot_tc": ["k_sh_tc.cu", "noise.cuh", "internal.h"],
-                  "project": ["k_project.cu", "internal.h"]}
+KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "proj_math.cuh", "internal.h"],
+                  "spot_n32": ["k_sh_n32.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
+                  "spot_tc": ["k_sh_tc.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
+                  "noise_cog": ["k_noise_cog.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
+                  "project": ["k_project.cu", "proj_math.cuh", "internal.h"]}
 
 
 def ncu_traffic(kernel_key):
@@ -377,6 +382,15 @@ def main():
             tflops = nv * 2 * 32 * (64 * 64 + 32 * 128) / avg_s / 1e12
             roof["tensor_pipe"] = {"achieved": tflops, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                                    "frac": tflops / pk["bf16_tflops"], "peak_source": kind}
+    if "noise_cog" in ktimes:
+        # the noise-and-centroid pass: detector pixels of the 32-point subapertures per second
+        launches, tot_ms = ktimes["noise_cog"]
+        px = sum(w.layouts[k].n_valid * cfg.geometries[s.geometry_index].n_det ** 2
+                 for k, s in enumerate(cfg.stars) if cfg.geometries[s.geometry_index].n_fft == 32)
+        if roof is not None:
+            roof["noise_pass"] = {"avg_launch_ms": tot_ms / launches, "pixels_per_launch": px,
+                                  "gpixels_per_s": px / (tot_ms / launches / 1e3) / 1e9,
+                                  "traffic": ncu_traffic("noise_cog")}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
