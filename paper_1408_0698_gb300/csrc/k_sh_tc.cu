@@ -150,7 +150,11 @@ struct TcLayout {
     // the NGS image rows (wI) alias the LGS scratch (wQ, wM)
     static constexpr int wX = 0, wQ = wX + n * n, wM = wQ + nd * n, wI = wQ;
     static constexpr int lgs_end = wM + D2 * n, ngs_end = wI + (N * (N + 1) + 1) / 2;
-    static constexpr int warp = lgs_end > ngs_end ? lgs_end : ngs_end;
+    // an LGS subaperture's elongation table K~ ([2n-1][n] complex), staged by cp.async at the
+    // top of a group and read by the elongation stage; it may overlap the NGS rows, which an LGS
+    // subaperture never writes (a warp's copies land before its next NGS image)
+    static constexpr int wKt = lgs_end;
+    static constexpr int warp = wKt + D2 * n > ngs_end ? wKt + D2 * n : ngs_end;
     static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;  // per warpgroup: 2 mbarriers, flag
     static constexpr int bytes = oMisc + 32 * kWG + 16;
 };
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     using Lay = TcLayout<n, nd>;
     constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
+    static_assert(n % 2 == 0 && Lay::wKt % 2 == 0 && Lay::warp % 2 == 0 && Lay::oWarp % 16 == 0,
+                  "16-byte aligned K~ staging");
     static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB1 = smem + Lay::oB1, *sB2h = smem + Lay::oB2h, *sB2l = smem + Lay::oB2l;
@@ -219,6 +225,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 
     float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
+    float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
     float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
     const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
@@ -239,6 +246,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
         const InstDyn &D = a.dyn[W.inst];
         const int v = active ? g - W.subap_begin : 0;
+        if (active && W.is_lgs) {
+            // K~ of this subaperture: (2n-1) n complex = 16-byte chunks (n even)
+            const float4 *src = reinterpret_cast<const float4 *>(W.ktil + (size_t)v * (D2 * n));
+            for (int c = lane; c < D2 * n / 2; c += 32) {
+                const uint32_t dst = smem_u32(reinterpret_cast<float4 *>(Kts) + c);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + c) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
 
         // field and U = F X (CUDA cores)
         float2 U[n];
@@ -374,12 +390,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 
         // remaining stages on the CUDA cores (per warp)
         float Bv[nd / 2];
-        if (W.is_lgs)
-            tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
-        else
+        if (W.is_lgs) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, Kts, lane, Bv);
+        } else
             tail::ngs_binned<nd>(Iw, lane, Bv);
         tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the CTA
     fence_before_sync();
     __syncthreads();
     if (*sflag && issuer && a.status) atomicCAS(a.status, 0, 5 /* WFS_ETIMEOUT */);

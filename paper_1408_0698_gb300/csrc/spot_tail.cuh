@@ -52,7 +52,8 @@ __device__ __forceinline__ void fill_fft_table(float2 *tab, int tid, int nthread
 }
 
 // T: this lane's row k = lane of the first stage (T[k][dx], dx < n), consumed.  fft: the
-// table above.  Gt: [n][nd] G[d][i].  M and Q are per-warp scratch ([2n-1][n], [nd][n]).
+// table above.  Gt: [n][nd] G[d][i].  kt: the subaperture's K~ [2n-1][n] (global or shared
+// memory).  M and Q are per-warp scratch ([2n-1][n], [nd][n]).
 // On return Bv[j] = B[half * nd/2 + j][ix] for lane = half * 16 + ix.
 template <int n, int nd>
 __device__ __forceinline__ void lgs_binned(float2 (&T)[n], float2 *M, float2 *Q, const float2 *fft,
@@ -82,7 +83,7 @@ __device__ __forceinline__ void lgs_binned(float2 (&T)[n], float2 *M, float2 *Q,
 #pragma unroll
             for (int d = 0; d < n; ++d) {
                 const float2 x = make_float2(T[d].x * ph.x - T[d].y * ph.y, T[d].x * ph.y + T[d].y * ph.x);
-                const float2 k0 = __ldg(kt + dyi * n + d);
+                const float2 k0 = kt[dyi * n + d];
                 M[dyi * n + d] = make_float2(x.x * k0.x - x.y * k0.y, x.x * k0.y + x.y * k0.x);
             }
         }
