@@ -412,6 +412,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     pa.inst = h->d_inst;
     pa.n_inst = 1;
     pa.box_cap = h->proj_box;
+    pa.max_layers = h->inst_host.n_layers;
     pa.status = h->d_status;
     pa.dyn[0] = dyn;
     cudaError_t e;
@@ -1211,6 +1212,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     b->pa->n_inst = n;
     b->pa->box_cap = b->proj_box;
     b->pa->n_blocks = b->proj_blocks;
+    for (int i = 0; i < n; ++i) b->pa->max_layers = std::max(b->pa->max_layers, hs[i]->inst_host.n_layers);
     b->pa->work = b->d_work + 2 * b->classes.size() * (1 + kBatchSlots);
     b->pa->status = hs[0]->d_status;
     for (const BatchClass &bc : b->classes) {
@@ -1332,6 +1334,8 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
     pa.wfs = sl.d;
     pa.n_wfs = count;
     pa.block_base = 0;
+    pa.max_layers = 0;
+    for (size_t i = 0; i < b->hs.size(); ++i) pa.max_layers = std::max(pa.max_layers, b->hs[i]->inst_host.n_layers);
     pa.work = b->d_work + 2 * b->classes.size() * (1 + kBatchSlots) + 2 * (1 + (size_t)slot);
     pa.n_inst = n;
     pa.box_cap = box;

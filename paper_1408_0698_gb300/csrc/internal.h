@@ -70,6 +70,7 @@ struct ProjArgs {
     int block_base;                 // projection block of this launch's first block (a launch
                                     // may cover a contiguous range of the WFS table)
     int n_blocks;                   // blocks in this launch (set by the launcher)
+    int max_layers;                 // largest n_layers of the launch's instances
     int *work;                      // ticket counter pair {next, CTAs done}, zero between
                                     // launches, one launch at a time; null = one CTA per block
     int *status;                    // device status word (limit errors)

@@ -25,12 +25,15 @@ __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
     return r < 0 ? r + S : r;
 }
 
+constexpr int kOffsTable = 64;  // layer offsets a CTA keeps for every (WFS, layer) of its launch
+
 // One projection block (a tiled segment, or kProjThreads 2x2 pixel blocks); every thread of
-// the CTA calls it (its shared memory is free again once all threads have returned).
-// last_wfs: the WFS whose layer offsets s_off holds (a persistent CTA skips the FP64 offsets
-// when consecutive blocks belong to the same WFS).
-__device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, int &last_wfs) {
-    __shared__ LayerOffs s_off[kMaxLayers];
+// the CTA calls it (its shared memory is free again once all threads have returned).  tab: the
+// CTA's layer offsets; with all_offs, entry w * max_layers + l for every WFS w of the launch
+// (filled once at the start of the kernel), else entries 0 .. L of the WFS last_wfs (refilled
+// when a block belongs to another WFS).
+__device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, int &last_wfs, LayerOffs *tab,
+                                            bool all_offs) {
 
     // the WFS owning this block: last entry whose first block is <= bid
     int lo = 0, hi = a.n_wfs - 1;
@@ -44,8 +47,9 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
     const InstDyn &D = a.dyn[W.inst];
     const int S = I.S;
 
-    if (lo != last_wfs) {  // uniform: last_wfs was written before the caller's barrier
-        if ((int)threadIdx.x < I.n_layers) s_off[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
+    const LayerOffs *s_off = all_offs ? tab + lo * a.max_layers : tab;
+    if (!all_offs && lo != last_wfs) {  // uniform: last_wfs was written before the caller's barrier
+        if ((int)threadIdx.x < I.n_layers) tab[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
         __syncthreads();
         if (threadIdx.x == 0) last_wfs = lo;  // read again only after the caller's barrier
     }
@@ -253,13 +257,24 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
 __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
     allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
     __shared__ int s_next, s_last_wfs;
+    __shared__ LayerOffs s_tab[kOffsTable];
+    // the layer offsets of every (WFS, layer) of this launch, once per CTA, when they fit
+    const bool all_offs = a.n_wfs * a.max_layers <= kOffsTable;
+    if (all_offs) {
+        for (int i = threadIdx.x; i < a.n_wfs * a.max_layers; i += blockDim.x) {
+            const int w = i / a.max_layers, l = i - w * a.max_layers;
+            const WfsDesc &W = a.wfs[w];
+            const InstDesc &I = a.inst[W.inst];
+            if (l < I.n_layers) s_tab[i] = layer_offsets(I, W, a.dyn[W.inst].t, l);
+        }
+    }
     if (threadIdx.x == 0) s_last_wfs = -1;
     __syncthreads();
     int blk = blockIdx.x;
     while (blk < a.n_blocks) {
         int ticket = 0;
         if (a.work && threadIdx.x == 0) ticket = atomicAdd(a.work, 1);
-        project_one(a, blk + a.block_base, s_last_wfs);
+        project_one(a, blk + a.block_base, s_last_wfs, s_tab, all_offs);
         __syncthreads();  // the block's shared memory is free; orders s_next
         if (a.work) {
             if (threadIdx.x == 0) s_next = (int)gridDim.x + ticket;

@@ -283,6 +283,7 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
     h_pa.box_cap = 0;  // direct gathers: no projection tiles in the static scratch
     h_pa.block_base = 0;
     h_pa.work = nullptr;  // one CTA per block
+    h_pa.max_layers = h_inst.n_layers;
     h_pa.status = (int *)(base + o_status);
     h_pa.dyn[0] = dyn;
     if ((e = launch_project(h_pa, project_blocks(h_wfs), s)) != cudaSuccess)
