@@ -170,9 +170,20 @@ def cpu_baseline(cfg, scr, t, target_s=12.0):
         else:
             spots += len(oracle.measure_wfs(cfg, scr, w, t)["slopes"])
     dt = time.perf_counter() - t0
+    # the same oracle on one core, over a sixteenth of that sample (LGS subapertures only)
+    oracle.set_threads(1)
+    try:
+        sel = np.arange(0, 4632, stride * 16, dtype=np.int32)
+        t1 = time.perf_counter()
+        oracle.measure_wfs(cfg, scr, 0, t, sel=sel)
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(nthreads)
     return {"value": spots / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{spots} spots of one ELT frame (every {stride}th LGS subaperture of 6 WFSs "
-                      f"+ all 12 NGS subapertures), FP64, {dt:.1f} s"}
+                      f"+ all 12 NGS subapertures), FP64, {dt:.1f} s",
+            "single_thread": {"value": len(sel) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{len(sel)} LGS subapertures of WFS 0, {dt1:.1f} s"}}
 
 
 def replica_throughput(local_ms, spots_per_step, steps, world, dev):
@@ -187,20 +198,34 @@ def replica_throughput(local_ms, spots_per_step, steps, world, dev):
     return world * spots_per_step * steps / (ms_max / 1e3), world * steps / (ms_max / 1e3), ms_max
 
 
-def served(load=0.8, duration_s=4.0, n_runs=32, budget_gb=150.0, slots=3):
+def served(load=0.8, duration_s=4.0, n_runs=32, budget_gb=150.0, slots=3, other_loads=(0.5, 0.95),
+           small_budget_gb=1.0):
     """Continuous-batching serving of frame requests from n_runs concurrent MC runs drawn from
     configs 1-3, device-resident (admitted by HBM footprint), Poisson arrivals at `load` times
-    the measured batched capacity; p50/p99 latency and served throughput."""
+    the measured batched capacity; p50/p99 latency and served throughput.  Also the other
+    offered loads, and `load` under a small HBM budget at which admission binds (runs wait for
+    earlier runs to retire)."""
     from paper_1408_0698_gb300 import serving
     runs = serving.make_runs(n_runs, 5000)
     budget = int(budget_gb * (1 << 30))
     cap = serving.capacity(runs, budget, slots)
-    arrivals = serving.poisson_arrivals(runs, load * cap / n_runs, duration_s, seed=11)
-    srv = serving.Server(runs, budget, slots)
-    srv.preadmit()
-    st = srv.serve(arrivals).summary()
+
+    def one(ld, bud, preadmit=True):
+        arrivals = serving.poisson_arrivals(runs, ld * cap / n_runs, duration_s, seed=11)
+        srv = serving.Server(runs, bud, slots)
+        if preadmit:
+            srv.preadmit()
+        return srv.serve(arrivals).summary()
+
+    st = one(load, budget)
     st.update({"load": load, "capacity_frames_per_s": cap, "runs": n_runs, "budget_gb": budget_gb,
                "slots": slots, "mix": "configs 1-3 (seeded)"})
+    keys = ("p50_ms", "p99_ms", "frames_per_s", "spots_per_s", "mean_batch", "max_admitted")
+    st["other_loads"] = [dict({"load": ld}, **{k: v for k, v in one(ld, budget).items() if k in keys})
+                         for ld in other_loads]
+    small = one(load, int(small_budget_gb * (1 << 30)), preadmit=False)
+    st["small_budget"] = dict({"load": load, "budget_gb": small_budget_gb},
+                              **{k: v for k, v in small.items() if k in keys + ("requests",)})
     return st
 
 

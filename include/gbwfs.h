@@ -179,8 +179,10 @@ wfs_status wfs_destroy(wfs_handle h);
  *   slopes_out: device, float [sum_w n_valid_w][2], (x, y) in detector pixels,
  *     guide stars concatenated in order.
  * Asynchronous on `stream`; no allocation, no host synchronisation; inputs
- * are not modified.  Two calls on one handle must not overlap in time on
- * different streams (they share the handle's device scratch).
+ * are not modified.  One stream at a time: the handle's device scratch belongs
+ * to the work in flight, so a call on another stream while the previous
+ * measurement is still running returns WFS_EBUSY (nothing is launched); calls
+ * on the same stream are ordered by the stream.
  */
 wfs_status wfs_measure(wfs_handle h, const float *screens, double t_s, float *slopes_out,
                        void *stream);

@@ -95,6 +95,8 @@ def lib():
                                           C.c_double, C.c_uint64, C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
             L.orc_measure_wfs.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = None
         return _lib
 
 
@@ -152,6 +154,11 @@ def _geom(tel, g):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (timing only; results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 def pupil_mask(D, eps, Np):

@@ -45,6 +45,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the following parallel loops (timing only; results do not depend on it). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ---- pupil and subapertures (Sec. 2 pupil sampling; Sec. 4 subaperture split) ---- */
 
 static int lit(double D, double eps, int Np, int i, int j)

@@ -90,6 +90,7 @@ int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
                     double *opd, double *I, double *Ie, double *E, double *C);
 
 int orc_num_threads(void);
+void orc_set_threads(int n);
 
 #ifdef __cplusplus
 }

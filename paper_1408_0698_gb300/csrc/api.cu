@@ -102,6 +102,7 @@ struct wfs_ctx {
     // side streams for the spot launches of the second and later geometries
     std::vector<cudaStream_t> side;
     cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_measured = nullptr;  // recorded at the end of each measurement (one stream at a time)
     std::vector<cudaEvent_t> ev_join;
     // kernel timing
     bool timing = false;
@@ -307,6 +308,8 @@ void release(wfs_ctx *h) {
     h->ev_join.clear();
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     h->ev_fork = nullptr;
+    if (h->ev_measured) cudaEventDestroy(h->ev_measured);
+    h->ev_measured = nullptr;
 }
 
 wfs_status validate(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs, int n_geom,
@@ -396,6 +399,10 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != h->device) return fail(h, WFS_EINVAL, "current device differs from the handle's device");
+    // one stream at a time: the handle's scratch (OPD, expected images) belongs to the work in
+    // flight on the stream of the previous call
+    if (stream != h->last_stream && cudaEventQuery(h->ev_measured) == cudaErrorNotReady)
+        return fail(h, WFS_EBUSY, "handle busy on another stream (its previous measurement is still running)");
     h->last_stream = stream;
     InstDyn dyn;
     memset(&dyn, 0, sizeof dyn);
@@ -491,6 +498,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     }
     for (size_t j = 0; j < k; ++j)
         if ((e = cudaStreamWaitEvent(stream, h->ev_join[j], 0)) != cudaSuccess) return cuda_fail(h, e, "join wait");
+    if ((e = cudaEventRecord(h->ev_measured, stream)) != cudaSuccess) return cuda_fail(h, e, "completion event");
     return WFS_OK;
 }
 
@@ -745,7 +753,8 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
         h->side.push_back(st);
         h->ev_join.push_back(ev);
     }
-    if (n_geom > 1 && (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
+    if ((e = cudaEventCreateWithFlags(&h->ev_measured, cudaEventDisableTiming)) != cudaSuccess ||
+        (n_geom > 1 && (e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess)) {
         release(h);
         delete h;
         return cuda_fail(nullptr, e, "fork event creation");
@@ -804,6 +813,8 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
         if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(h, e, "host-path copy stream");
     }
+    if (s != h->last_stream && cudaEventQuery(h->ev_measured) == cudaErrorNotReady)
+        return fail(h, WFS_EBUSY, "handle busy on another stream (its previous measurement is still running)");
     const int i = (int)(h->host_calls & 1);
     // the staging set is free once the frame that used it two calls ago has finished
     if (h->host_calls >= 2 && (e = cudaStreamWaitEvent(h->copy_stream, h->ev_done[i], 0)) != cudaSuccess)

@@ -359,3 +359,27 @@ def test_host_path_alternating_buffers():
         ref, _ = run_library(cfg, scr, t, seed=5, noise=True, stages=False, handle=w)
         assert np.array_equal(o.numpy(), np.concatenate([d["slopes"] for d in ref]))
     w.close()
+
+
+def test_busy_on_another_stream():
+    """One stream at a time: while a measurement is still queued or running on one stream, a
+    call on another stream is refused with WFS_EBUSY and launches nothing; once it has finished,
+    the other stream may use the handle and gets the same slopes."""
+    cfg = inputs.config1()
+    scr = torch.as_tensor(inputs.make_screens(cfg.layers, cfg.seed)).cuda()
+    w = native.Wfs(cfg, seed=2, noise=False)
+    a = torch.full((w.total, 2), float("nan"), device="cuda")
+    b = torch.full((w.total, 2), float("nan"), device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        torch.cuda._sleep(200_000_000)  # a bounded busy wait queued ahead of the measurement
+        native.wfs_measure(w.h, scr.data_ptr(), 0.004, a.data_ptr(), s1.cuda_stream)
+    with pytest.raises(native.WfsError) as err:
+        native.wfs_measure(w.h, scr.data_ptr(), 0.004, b.data_ptr(), s2.cuda_stream)
+    assert err.value.status == native.STATUS_NAMES.index("WFS_EBUSY")
+    torch.cuda.synchronize()
+    assert torch.isnan(b).all()
+    native.wfs_measure(w.h, scr.data_ptr(), 0.004, b.data_ptr(), s2.cuda_stream)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    w.close()
