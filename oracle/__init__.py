@@ -12,6 +12,7 @@ this module only builds it and marshals numpy arrays through ctypes.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import math
 import os
 import subprocess
@@ -62,6 +63,11 @@ class _Layers(C.Structure):
                 ("y0", C.POINTER(C.c_double))]
 
 
+class _Dm(C.Structure):
+    _fields_ = [("n_act", C.c_int), ("pitch_m", C.c_double), ("alt_m", C.c_double),
+                ("coupling", C.c_double), ("support", C.c_int)]
+
+
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
 _ip = C.POINTER(C.c_int32)
@@ -94,6 +100,9 @@ def lib():
             L.orc_measure_wfs.argtypes = [C.POINTER(_Geom), C.POINTER(_Star), C.c_int, C.POINTER(_Layers), _fp,
                                           C.c_double, C.c_uint64, C.c_int, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp, _dp]
             L.orc_measure_wfs.restype = C.c_int
+            L.orc_dm_value.argtypes = [C.POINTER(_Dm), _dp, C.c_double, C.c_double]
+            L.orc_dm_value.restype = C.c_double
+            L.orc_dm_layer.argtypes = [C.POINTER(_Dm), _dp, C.c_int, C.c_double, _fp]
             L.orc_num_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_set_threads.restype = None
@@ -295,3 +304,68 @@ def measure(cfg, screens, t, seed=0, noise=False):
     """All guide stars of a configuration: slopes concatenated [sum_w n_valid_w, 2]."""
     return np.concatenate([measure_wfs(cfg, screens, w, t, seed, noise)["slopes"]
                            for w in range(len(cfg.stars))], axis=0)
+
+
+# ---------------------------------------------------------------- closed loop
+# Sec. 3 "Influence function and modal base" and "The closed loop": the mirrors are linear
+# combinations of a modal base defined on their actuators; the sensors measure the open-loop
+# wavefront minus the mirrors; the slopes times the control matrix are the differential
+# coefficients added to the mirror's (pure integrator, one gain per mode).
+
+def _dm(d):
+    return _Dm(int(d.n_act), float(d.pitch_m), float(d.alt_m), float(d.coupling), int(d.support))
+
+
+def dm_value(dm, act, x, y):
+    """Correction-layer value (minus the mirror shape) at (x, y) metres in the mirror's plane."""
+    a = _f64(np.asarray(act).ravel())
+    D = _dm(dm)
+    return lib().orc_dm_value(C.byref(D), _ptr(a, _dp), float(x), float(y))
+
+
+def dm_layer(dm, act, S, ds):
+    """[S, S] float32 correction layer of one mirror with actuator commands act [n_act^2]."""
+    a = _f64(np.asarray(act).ravel())
+    if a.size != dm.n_act * dm.n_act:
+        raise ValueError("act must hold n_act^2 commands")
+    out = np.zeros((S, S), dtype=np.float32)
+    D = _dm(dm)
+    lib().orc_dm_layer(C.byref(D), _ptr(a, _dp), int(S), float(ds), _ptr(out, _fp))
+    return out
+
+
+def with_dm_layers(cfg, screens, dms, layers):
+    """The configuration and screens with each mirror's correction layer appended as one more
+    layer at the mirror's altitude, without wind or initial offset."""
+    lay = cfg.layers
+    k = len(dms)
+    z = np.zeros(k)
+    lay2 = dataclasses.replace(
+        lay, alt_m=np.concatenate([_f64(lay.alt_m), [float(d.alt_m) for d in dms]]),
+        wind_vx_mps=np.concatenate([_f64(lay.wind_vx_mps), z]),
+        wind_vy_mps=np.concatenate([_f64(lay.wind_vy_mps), z]),
+        x0_m=np.concatenate([_f64(lay.x0_m), z]), y0_m=np.concatenate([_f64(lay.y0_m), z]))
+    cfg2 = dataclasses.replace(cfg, layers=lay2)
+    scr = np.concatenate([np.asarray(screens, dtype=np.float32),
+                          np.stack([np.asarray(l, dtype=np.float32) for l in layers])], axis=0)
+    return cfg2, scr
+
+
+def actuators(dms, m2a, coeffs):
+    """Per mirror: its actuator commands m2a_d @ c_d, c_d its slice of the coefficient vector."""
+    out, o = [], 0
+    for d, M in zip(dms, m2a):
+        M = _f64(M)
+        out.append(M @ _f64(coeffs)[o:o + M.shape[1]])
+        o += M.shape[1]
+    return out
+
+
+def loop_step(cfg, screens, t, dms, m2a, cm, gain, coeffs, seed=0, noise=False):
+    """One integrator step: the slopes [n, 2] of the residual seen through the mirrors whose
+    modal coefficients are ``coeffs``, and the next coefficients coeffs + gain * (cm @ s)."""
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    layers = [dm_layer(d, a, S, ds) for d, a in zip(dms, actuators(dms, m2a, coeffs))]
+    cfg2, scr2 = with_dm_layers(cfg, screens, dms, layers)
+    s = measure(cfg2, scr2, t, seed, noise)
+    return s, _f64(coeffs) + _f64(gain) * (_f64(cm) @ s.ravel())

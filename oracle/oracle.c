@@ -407,6 +407,47 @@ void orc_cog(int nd, const double *C, double *sx, double *sy)
     }
 }
 
+/* ---- deformable mirrors (Sec. 3 "Influence function and modal base") ---- */
+
+/* Influence along one axis at u pitches: a Gaussian of value k at one pitch, lowered by its
+   value at the support radius and renormalised, so that it reaches 0 continuously there. */
+static double dm_axis(double u, double k, int R)
+{
+    double edge = pow(k, (double)R * R);
+    double g = pow(k, u * u) - edge;
+    return g > 0.0 ? g / (1.0 - edge) : 0.0;
+}
+
+double orc_dm_value(const orc_dm *dm, const double *act, double x, double y)
+{
+    double c = (dm->n_act - 1) / 2.0, sum = 0.0;
+    /* actuators farther than the support contribute zero terms: visit the others only, in
+       the natural (ay, ax) order */
+    int ax0 = (int)floor(x / dm->pitch_m + c) - dm->support - 1, ax1 = ax0 + 2 * dm->support + 3;
+    int ay0 = (int)floor(y / dm->pitch_m + c) - dm->support - 1, ay1 = ay0 + 2 * dm->support + 3;
+    if (ax0 < 0) ax0 = 0;
+    if (ay0 < 0) ay0 = 0;
+    if (ax1 > dm->n_act - 1) ax1 = dm->n_act - 1;
+    if (ay1 > dm->n_act - 1) ay1 = dm->n_act - 1;
+    for (int ay = ay0; ay <= ay1; ++ay) {
+        double wy = dm_axis(y / dm->pitch_m - (ay - c), dm->coupling, dm->support);
+        for (int ax = ax0; ax <= ax1; ++ax) {
+            double wx = dm_axis(x / dm->pitch_m - (ax - c), dm->coupling, dm->support);
+            sum += act[(size_t)ay * dm->n_act + ax] * wx * wy;
+        }
+    }
+    /* the mirror takes its shape out of the beam */
+    return -sum;
+}
+
+void orc_dm_layer(const orc_dm *dm, const double *act, int S, double ds, float *layer)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < S; ++i)
+        for (int j = 0; j < S; ++j)
+            layer[(size_t)i * S + j] = (float)orc_dm_value(dm, act, (j - S / 2.0) * ds, (i - S / 2.0) * ds);
+}
+
 /* ---- one wavefront sensor ---- */
 
 int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,

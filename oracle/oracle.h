@@ -89,6 +89,31 @@ int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
                     int noise, int n_sel, const int32_t *sel, double *slopes,
                     double *opd, double *I, double *Ie, double *E, double *C);
 
+/*
+ * Closed loop (Sec. 3 "Influence function and modal base", "The closed loop").
+ * A deformable mirror is an n_act x n_act grid of actuators at pitch p (metres in
+ * its conjugate plane at altitude alt_m), centred on the axis: actuator (ay, ax)
+ * at ((ax - c) p, (ay - c) p), c = (n_act - 1) / 2.  Its influence function is
+ * separable, w(u_x) w(u_y) with u in pitches and
+ *     w(u) = max(0, k^(u^2) - k^(R^2)) / (1 - k^(R^2)),   k = coupling, R = support,
+ * a Gaussian that is 1 on its actuator, ~k at one pitch and falls continuously to 0
+ * at R pitches.  The mirror's correction layer is a screen on the atmospheric grid
+ * (pixel (i, j) at x = (j - S/2) ds, y = (i - S/2) ds), the NEGATED mirror shape
+ * -sum_a act[a] w w: the residual the sensors see is the open-loop wavefront minus
+ * the mirror, so the layer enters the projection like one more turbulent layer at
+ * alt_m with no wind.
+ */
+typedef struct {
+    int n_act;
+    double pitch_m, alt_m, coupling;
+    int support;
+} orc_dm;
+
+/* Correction-layer value at (x, y) metres in the mirror's plane, act[ay * n_act + ax]. */
+double orc_dm_value(const orc_dm *dm, const double *act, double x, double y);
+/* The whole S x S correction layer (FP64 sums rounded to FP32, as screens are stored). */
+void orc_dm_layer(const orc_dm *dm, const double *act, int S, double ds, float *layer);
+
 int orc_num_threads(void);
 void orc_set_threads(int n);
 

@@ -229,6 +229,45 @@ def config4_instances(n_instances: int = 64, seed: int = 4000,
 
 
 # ---------------------------------------------------------------------------
+# Deformable mirrors and control matrices of the closed loop (Sec. 2: ~5000 modes for
+# the ground-layer mirror, ~1400 and ~1800 for two post-focal mirrors with a 1 m actuator
+# pitch on the primary; Sec. 3: the mirrors are combinations of a modal base over their
+# actuators, the control matrix maps slopes to modal coefficients).  Only descriptions
+# and seeded random matrices here: the modal base and the control matrix are inputs.
+# ---------------------------------------------------------------------------
+@dataclass
+class Dm:
+    n_act: int           # actuators per side of the square grid (centred on the axis)
+    pitch_m: float       # actuator pitch in the mirror's conjugate plane
+    alt_m: float         # conjugation altitude
+    n_modes: int
+    coupling: float = 0.15   # influence at one pitch
+    support: int = 3         # influence radius in pitches
+
+
+def elt_dms() -> List[Dm]:
+    """The three mirrors of the ELT workload: ground (81 x 81 at the subaperture pitch,
+    5000 modes) and post-focal at 4 km (43 x 43, 1 m, 1400 modes) and 12.7 km (50 x 50,
+    1 m, 1800 modes), each wide enough for the 160 arcsec field at its altitude."""
+    return [Dm(81, 39.0 / 80.0, 0.0, 5000), Dm(43, 1.0, 4000.0, 1400), Dm(50, 1.0, 12700.0, 1800)]
+
+
+def modal_base(dm: Dm, seed: int, amplitude_m: float = 1e-8) -> np.ndarray:
+    """[n_act^2, n_modes] float32 synthetic modal base: independent Gaussian actuator
+    patterns of rms ``amplitude_m`` per actuator (any base of the mirror's actuator space
+    is admissible as an input)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((dm.n_act * dm.n_act, dm.n_modes)) * amplitude_m).astype(np.float32)
+
+
+def random_control_matrix(n_modes: int, n_slopes: int, seed: int, scale: float = 1e-3) -> np.ndarray:
+    """[n_modes, n_slopes] float32 synthetic control matrix (uniform in +-scale / sqrt(n_slopes)),
+    a stand-in of the right size where no calibrated one is needed (timing)."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-1.0, 1.0, (n_modes, n_slopes)) * (scale / math.sqrt(n_slopes))).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
 # von Karman phase screens (Sec. 3, atmospheric layers block).
 # ---------------------------------------------------------------------------
 def von_karman_screen(S: int, dx: float, r0: float, L0: float, rng: np.random.Generator):

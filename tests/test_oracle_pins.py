@@ -494,3 +494,124 @@ def test_oracle_regression_fixtures():
     ref = np.loadtxt(f"{GOLDEN}/config2_lgs1_t0.01_slopes.txt")
     s = oracle.measure_wfs(cfg, scr, 1, 0.01, sel=ref[:, 0].astype(np.int32))["slopes"]
     assert np.allclose(s, ref[:, 1:], rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- closed loop: mirrors
+
+def _poke(dm, ay, ax, v=1.0):
+    a = np.zeros(dm.n_act * dm.n_act)
+    a[ay * dm.n_act + ax] = v
+    return a
+
+
+def test_dm_poke_physics():
+    """One actuator: the correction layer is minus a bump of height 1 on the actuator, the
+    coupling at one pitch, symmetric, and zero from the support radius on."""
+    dm = inputs.Dm(n_act=7, pitch_m=0.4, alt_m=0.0, n_modes=1, coupling=0.15, support=3)
+    a = _poke(dm, 3, 3)
+    v = lambda x, y: oracle.dm_value(dm, a, x, y)
+    assert v(0, 0) == pytest.approx(-1.0, abs=1e-14)
+    # coupling: the neighbour's influence relative to the actuator's, to within k^(R^2)
+    for (x, y) in [(0.4, 0), (-0.4, 0), (0, 0.4), (0, -0.4)]:
+        assert v(x, y) / v(0, 0) == pytest.approx(0.15, abs=0.15 ** 9)
+    # separable (rank one) and even in x and y
+    for x, y in [(0.13, 0.27), (0.5, -0.61), (-0.9, 0.05)]:
+        assert v(x, y) * v(0, 0) == pytest.approx(v(x, 0) * v(0, y), rel=1e-12)
+        assert v(-x, y) == pytest.approx(v(x, y), rel=1e-12)
+        assert v(x, -y) == pytest.approx(v(x, y), rel=1e-12)
+    # continuous fall to zero at the support radius, exactly zero beyond
+    assert abs(v(3 * 0.4 - 1e-7, 0)) < 1e-6
+    assert v(3 * 0.4 + 1e-9, 0) == 0.0 and v(0, -5 * 0.4) == 0.0
+    # decreasing away from the actuator
+    xs = np.linspace(0, 1.2, 25)
+    vals = [-v(x, 0) for x in xs]
+    assert all(b <= c for b, c in zip(vals[1:], vals[:-1]))
+
+
+def test_dm_layer_grid_geometry():
+    """Actuator (ay, ax) sits at ((ax - c) p, (ay - c) p) with pixel (i, j) at ((j - S/2) ds,
+    (i - S/2) ds): a poke one actuator over moves the layer by p / ds pixels along that axis
+    only; linear in the commands."""
+    dm = inputs.Dm(n_act=9, pitch_m=0.4, alt_m=0.0, n_modes=1, coupling=0.2, support=2)
+    S, ds = 64, 0.1                                   # pitch = 4 pixels
+    L0 = oracle.dm_layer(dm, _poke(dm, 4, 4), S, ds)  # central actuator on pixel (32, 32)
+    assert L0[32, 32] == np.float32(-1.0)
+    assert np.unravel_index(np.argmin(L0), L0.shape) == (32, 32)
+    Lx = oracle.dm_layer(dm, _poke(dm, 4, 6), S, ds)
+    Ly = oracle.dm_layer(dm, _poke(dm, 1, 4), S, ds)
+    np.testing.assert_array_equal(Lx, np.roll(L0, 8, axis=1))
+    np.testing.assert_array_equal(Ly, np.roll(L0, -12, axis=0))
+    rng = np.random.default_rng(5)
+    a, b = rng.standard_normal(81), rng.standard_normal(81)
+    La, Lb = oracle.dm_layer(dm, a, S, ds), oracle.dm_layer(dm, b, S, ds)
+    Lab = oracle.dm_layer(dm, 2.0 * a - 0.5 * b, S, ds)
+    np.testing.assert_allclose(Lab, 2.0 * La - 0.5 * Lb, atol=1e-6 * np.abs(Lab).max())
+    # even n_act: the grid's centre falls between actuators
+    dm8 = inputs.Dm(n_act=8, pitch_m=0.4, alt_m=0.0, n_modes=1, coupling=0.2, support=2)
+    flat = oracle.dm_layer(dm8, np.ones(64), S, ds)
+    np.testing.assert_allclose(flat[32, 32 - 2], flat[32, 32 + 2], rtol=1e-6)
+    np.testing.assert_allclose(flat[32 - 6, 32], flat[32 + 6, 32], rtol=1e-6)
+
+
+def _small_loop_cfg(is_lgs=False, alt=0.0):
+    """4 m telescope, 10 x 10 subapertures of 8 px, N = 16, 8 x 8 detector pixels; one
+    ground (or alt) layer without wind."""
+    tel = inputs.Telescope(4.0, 0.0)
+    geom = [inputs.Geometry(10, 8, 16, 8, 0.5, inputs.PREC_FP32)]
+    if is_lgs:
+        star = inputs._lgs(10 * inputs.ARCSEC, -5 * inputs.ARCSEC, 0.3, 0)
+    else:
+        star = inputs._ngs(5 * inputs.ARCSEC, 0.0, 700e-9, 0, photons=1000.0)
+    lay = inputs.Layers(alt_m=np.array([alt]), wind_vx_mps=np.zeros(1), wind_vy_mps=np.zeros(1),
+                        x0_m=np.zeros(1), y0_m=np.zeros(1), screen_size=128, screen_dx_m=0.05)
+    return inputs.Config("loop_small", tel, geom, [star], lay, seed=7)
+
+
+@pytest.mark.parametrize("is_lgs,alt", [(False, 0.0), (True, 0.0), (True, 6000.0)])
+def test_dm_layer_equal_to_minus_screen_cancels_exactly(is_lgs, alt):
+    """A mirror layer at the screen's altitude holding minus the screen leaves a flat
+    wavefront: the slopes equal those of zero screens bit for bit (any slip in the mirror
+    layer's cone, shift or sign breaks it)."""
+    cfg = _small_loop_cfg(is_lgs, alt)
+    scr = inputs.make_screens(cfg.layers, 3)
+    dm = inputs.Dm(11, 0.4, alt, 1)
+    cfg2, scr2 = oracle.with_dm_layers(cfg, scr, [dm], [-scr[0]])
+    s = oracle.measure(cfg2, scr2, 0.0)
+    s0 = oracle.measure(cfg, np.zeros_like(scr), 0.0)
+    np.testing.assert_array_equal(s, s0)
+    assert np.abs(oracle.measure(cfg, scr, 0.0)).max() > 0.05   # the screen alone is not flat
+
+
+def test_closed_loop_integrator_corrects_a_static_modal_aberration():
+    """Pure integrator with unit gains and CM = pinv(IM), IM registered by push-pull of each
+    mode in the beam: a static aberration made of the mirror's modes is removed in one step
+    (linear regime), and the next slopes are near zero.  A sign slip doubles the residual."""
+    cfg = _small_loop_cfg()
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    dm = inputs.Dm(11, 0.4, 0.0, 8, coupling=0.15, support=3)
+    M = inputs.modal_base(dm, 11, amplitude_m=1e-8).astype(np.float64)
+    zero = np.zeros((1, S, S), np.float32)
+    ns = 2 * len(oracle.measure(cfg, zero, 0.0))
+    # interaction matrix: slopes per unit coefficient of +mode in the beam (= minus its layer)
+    IM = np.zeros((ns, dm.n_modes))
+    amp = 0.5
+    for m in range(dm.n_modes):
+        beam = -oracle.dm_layer(dm, M[:, m] * amp, S, ds)
+        sp = oracle.measure(cfg, beam[None], 0.0).ravel()
+        sm = oracle.measure(cfg, -beam[None], 0.0).ravel()
+        IM[:, m] = (sp - sm) / (2 * amp)
+    CM = np.linalg.pinv(IM)
+    c_star = np.random.default_rng(2).standard_normal(dm.n_modes)
+    ol = -oracle.dm_layer(dm, M @ c_star, S, ds)[None]
+    gain = np.ones(dm.n_modes)
+    s0, c1 = oracle.loop_step(cfg, ol, 0.0, [dm], [M], CM, gain, np.zeros(dm.n_modes))
+    assert np.linalg.norm(c1 - c_star) < 0.05 * np.linalg.norm(c_star)
+    s1, c2 = oracle.loop_step(cfg, ol, 0.0, [dm], [M], CM, gain, c1)
+    assert np.linalg.norm(s1) < 0.05 * np.linalg.norm(s0)
+    assert np.linalg.norm(c2 - c_star) <= np.linalg.norm(c1 - c_star) + 1e-12
+    # gains of zero leave the coefficients alone; a wrong sign makes the residual worse
+    _, c_same = oracle.loop_step(cfg, ol, 0.0, [dm], [M], CM, 0 * gain, c1)
+    np.testing.assert_array_equal(c_same, c1)
+    sb, cb = oracle.loop_step(cfg, ol, 0.0, [dm], [M], -CM, gain, np.zeros(dm.n_modes))
+    sb1, _ = oracle.loop_step(cfg, ol, 0.0, [dm], [M], CM, gain, cb)
+    assert np.linalg.norm(sb1) > 1.5 * np.linalg.norm(s0)
