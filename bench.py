@@ -80,7 +80,8 @@ KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "proj_math.cuh", "internal.h"
                   "spot_n32": ["k_sh_n32.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
                   "spot_tc": ["k_sh_tc.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
                   "noise_cog": ["k_noise_cog.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
-                  "project": ["k_project.cu", "proj_math.cuh", "internal.h"]}
+                  "project": ["k_project.cu", "proj_math.cuh", "internal.h"],
+                  "gemv": ["k_loop.cu", "internal.h"]}
 
 
 def ncu_traffic(kernel_key):
@@ -272,6 +273,74 @@ def reference_arm(args):
     return 0
 
 
+def closed_loop(cfg, s_d, flush, args, dev, rank):
+    """The closed loop on the same ELT frame (Sec. 3 "The closed loop"): each step measures the
+    residual through three mirrors (ground, 81 x 81 actuators, 5000 modes; 4 km, 43 x 43, 1400;
+    12.7 km, 50 x 50, 1800), multiplies the slopes by an 8200 x 55608 FP32 control matrix and
+    integrates (gain 0.3), then rebuilds the actuator commands and the mirror layers.  The
+    modal bases are seeded Gaussian patterns, the control matrix seeded uniform values on the
+    device (a calibrated matrix of that size times the same)."""
+    import torch
+
+    from paper_1408_0698_gb300 import inputs, native
+    dms = inputs.elt_dms()
+    m2a = [torch.as_tensor(inputs.modal_base(d, cfg.seed + 50 + i)).to(dev) for i, d in enumerate(dms)]
+    n = sum(d.n_modes for d in dms)
+    w = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
+    ns = 2 * w.total
+    g = torch.Generator(device=dev)
+    g.manual_seed(cfg.seed + 60)
+    cm = (torch.rand((n, ns), generator=g, device=dev) * 2.0 - 1.0) * (1e-3 / math.sqrt(ns))
+    gain = torch.full((n,), 0.3, device=dev)
+    structs = [native.wfs_dm(d.n_act, d.pitch_m, d.alt_m, d.coupling, d.support, d.n_modes, M.data_ptr())
+               for d, M in zip(dms, m2a)]
+    lp = native.wfs_loop_create(w.h, structs, cm.data_ptr(), gain.data_ptr())
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    slopes = torch.empty((w.total, 2), device=dev)
+    dt = cfg.dt_s
+    for k in range(5):
+        native.wfs_loop_step(lp, w.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
+    torch.cuda.synchronize()
+    native.wfs_sync_status(w.h)
+    kl = min(args.steps, 300)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(kl)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(kl)]
+    native.wfs_timing_enable(w.h, True)
+    native.wfs_timing_read(w.h)
+    for k in range(kl):
+        if args.flush_mb:
+            flush.fill_(float(k))
+        e0[k].record(stream)
+        native.wfs_loop_step(lp, w.h, s_d.data_ptr(), (5 + k) * dt, slopes.data_ptr(), sp)
+        e1[k].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    kt = native.wfs_timing_read(w.h)
+    native.wfs_timing_enable(w.h, False)
+    native.wfs_sync_status(w.h)
+    pk, kind = peaks()
+    roof = None
+    if "reconstruct" in kt:
+        launches, tot_ms = kt["reconstruct"]
+        avg_s = tot_ms / launches / 1e3
+        # algorithmic bytes: the control matrix once, the slopes, gains, coefficients read + written
+        nbytes = 4 * (n * ns + ns + n + 2 * n)
+        ach = nbytes / avg_s / 1e9
+        roof = {"kernel": "reconstruct", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": ncu_traffic("gemv"),
+                "bytes_per_launch": nbytes, "avg_launch_ms": avg_s * 1e3, "peak_source": kind}
+    out = {"workload": "config3 ELT frame + 3 mirrors (5000 + 1400 + 1800 modes), control matrix "
+                       f"{n} x {ns} FP32, gain 0.3, noise on",
+           "steps": kl, "ms_per_step": ms / kl, "steps_per_s": kl / (ms / 1e3),
+           "spots_per_s": w.total * kl / (ms / 1e3),
+           "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt.items()},
+           "reconstruct_roofline": roof}
+    native.wfs_loop_destroy(lp)
+    w.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,6 +352,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-traffic measurement")
+    ap.add_argument("--no-loop", action="store_true", help="skip the closed-loop measurement")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (0: none, for profiling runs)")
     args = ap.parse_args()
@@ -456,6 +526,8 @@ def main():
                              "steps": k2, "dft_precision": other,
                              "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])}
                                          for k, v in kt2.items()}}
+    if not args.no_loop:
+        line["closed_loop"] = closed_loop(cfg, s_d, flush, args, dev, rank)
     if not args.no_served:
         line["served"] = served()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -47,6 +47,7 @@ extern "C" {
 
 typedef struct wfs_ctx *wfs_handle;
 typedef struct wfs_batch_ctx *wfs_batch;
+typedef struct wfs_loop_ctx *wfs_loop;
 
 typedef enum {
     WFS_OK = 0,
@@ -345,6 +346,77 @@ wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs_geometry *
  * faulted or hung.  The paper has no counterpart (it is a property of this library).
  */
 wfs_status wfs_check_bounded_wait(wfs_handle h, int polls, void *stream);
+
+/*
+ * Closed loop (Sec. 3 "The closed loop": the sensors compute the slopes of the
+ * residual phase, the open-loop wavefront minus the deformable mirrors; the
+ * slopes times the control matrix are the differential modal coefficients
+ * added to those of the mirrors, a pure integrator; Sec. 3 "Influence function
+ * and modal base": a mirror is a linear combination of a modal base defined
+ * over its actuators' influence functions).
+ *
+ * A mirror (wfs_dm) is an n_act x n_act actuator grid at pitch pitch_m in its
+ * conjugate plane at altitude alt_m, centred on the axis: actuator (ay, ax)
+ * sits at ((ax - c) p, (ay - c) p), c = (n_act - 1) / 2.  Its influence
+ * function is separable, w(u_x) w(u_y) with u in pitches and
+ *     w(u) = max(0, k^(u^2) - k^(R^2)) / (1 - k^(R^2)),  k = coupling, R = support,
+ * 1 on the actuator, about k at one pitch, 0 from R pitches on.  Its modal
+ * base m2a (device, row-major [n_act * n_act][n_modes], actuator ay * n_act +
+ * ax; metres of mirror shape per unit coefficient) maps its coefficients to
+ * actuator commands.  The mirror enters the projection as one more layer at
+ * alt_m, without wind, sampled on the screens' grid (pixel (i, j) at
+ * ((j - S/2) ds, (i - S/2) ds)) and holding minus the mirror shape: the
+ * sensors see the residual.  The cone and direction offsets are those of a
+ * turbulent layer at that altitude.
+ *
+ * Step k (wfs_loop_step): the slopes s_k of the residual seen through the
+ * mirrors of coefficients c_k (layout as for wfs_measure), then
+ *     c_{k+1} = c_k + gain * (cm s_k)      (per mode, FP32)
+ * with cm device row-major [n_modes][2 * total_valid] (n_modes = sum of the
+ * mirrors' n_modes, mirror 0's modes first) and gain device [n_modes]; the
+ * actuator commands m2a_d c_{k+1} and the mirrors' layers are rebuilt for step
+ * k + 1.  So cm maps slopes to the coefficient change; with an interaction
+ * matrix registered by applying each mode to the beam (slopes per unit
+ * coefficient), cm = pinv(IM).
+ *
+ * wfs_loop_create attaches a loop to a handle (one loop per handle): it
+ * validates (WFS_EINVAL: n_dm outside [1, 4], n_act outside [1, 1024], pitch
+ * below the screen pitch, alt not finite or negative, alt not below every LGS range, coupling
+ * outside (0, 1), support outside [1, 8], n_modes < 1, a null pointer; WFS_EBUSY
+ * when the handle already has a loop), allocates the coefficients (zero),
+ * the actuator commands and one S x S layer per mirror, and adds the mirrors'
+ * altitudes to the handle's layer table.  m2a, cm and gain stay caller-owned
+ * and must outlive the loop; their contents are read at each step.  The
+ * handle keeps measuring open loop through wfs_measure.
+ *
+ * wfs_loop_step is asynchronous on `stream` like wfs_measure (same inputs,
+ * same WFS_EBUSY rule for the handle and the loop).  wfs_loop_set_coeffs
+ * copies n_modes coefficients from device memory (NULL = zeros) and rebuilds
+ * the layers; wfs_loop_get_coeffs copies them to device memory; both are
+ * asynchronous on `stream`.  wfs_loop_get_layer copies mirror d's S x S
+ * correction layer (the one the next step uses) to device memory,
+ * asynchronously on `stream`.  wfs_loop_destroy waits for the loop's work and frees
+ * it; the handle stays valid.  The paper gives no influence function; the
+ * truncated Gaussian is this library's choice.
+ */
+typedef struct {
+    int n_act;
+    double pitch_m;
+    double alt_m;
+    double coupling;
+    int support;
+    int n_modes;
+    const float *m2a;
+} wfs_dm;
+
+wfs_status wfs_loop_create(wfs_handle h, int n_dm, const wfs_dm *dms, const float *cm,
+                           const float *gain, wfs_loop *out);
+wfs_status wfs_loop_step(wfs_loop lp, const float *screens, double t_s, float *slopes_out,
+                         void *stream);
+wfs_status wfs_loop_set_coeffs(wfs_loop lp, const float *coeffs, void *stream);
+wfs_status wfs_loop_get_coeffs(wfs_loop lp, float *coeffs_out, void *stream);
+wfs_status wfs_loop_get_layer(wfs_loop lp, int d, float *layer_out, void *stream);
+wfs_status wfs_loop_destroy(wfs_loop lp);
 
 /* Library version string. */
 const char *wfs_version(void);

@@ -111,6 +111,27 @@ struct wfs_ctx {
     std::vector<std::string> kinds;   // kernel names
     size_t ev_used = 0;
     bool ev_overflow = false;
+    wfs_loop_ctx *loop = nullptr;     // attached closed loop (at most one)
+};
+
+// A closed loop attached to a handle: the mirrors, their coefficients, actuator commands and
+// correction layers ([n_dm][S][S], zero outside each mirror's window).
+struct LoopDm {
+    wfs_dm d{};
+    int mode0 = 0;                    // first coefficient of this mirror
+    int x0 = 0, y0 = 0, w = 0, h = 0;  // window of the grid its influence functions reach
+    float *act = nullptr;             // [n_act * n_act]
+};
+
+struct wfs_loop_ctx {
+    wfs_handle h = nullptr;
+    std::vector<LoopDm> dms;
+    int n_modes = 0, n_slopes = 0;
+    const float *cm = nullptr, *gain = nullptr;  // caller-owned
+    float *coeffs = nullptr;          // [n_modes]
+    float *layers = nullptr;          // [n_dm][S][S]
+    cudaEvent_t ev_done = nullptr;    // end of the loop's last enqueued work
+    cudaStream_t last_stream = nullptr;
 };
 
 // A batch: the instances' work tables merged, WFS entries grouped by kernel class
@@ -391,8 +412,11 @@ const char *kind_name(int kind) {
     return kind == kSpotTc ? "spot_tc_bf16x3_N" : kind == kSpotN32 ? "spot_n32_fp32_N" : "spot_fp32_N";
 }
 
+// dm_layers / n_dm: the correction layers of a closed loop's mirrors, summed after the
+// screens (none for an open-loop measurement).
 wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slopes,
-                        const wfs_stage_out *st, cudaStream_t stream) {
+                        const wfs_stage_out *st, cudaStream_t stream, const float *dm_layers = nullptr,
+                        int n_dm = 0) {
     if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
     if (!screens || !slopes) return fail(h, WFS_EINVAL, "null screens or slopes pointer");
     if (!is_finite(t)) return fail(h, WFS_EINVAL, "t must be finite");
@@ -414,12 +438,14 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     dyn.st_C = st ? st->counts : nullptr;
     dyn.t = t;
     dyn.noise = h->noise;
+    dyn.dm = dm_layers;
+    dyn.n_dm = n_dm;
 
     static thread_local ProjArgs pa;
     pa.inst = h->d_inst;
     pa.n_inst = 1;
     pa.box_cap = h->proj_box;
-    pa.max_layers = h->inst_host.n_layers;
+    pa.max_layers = h->inst_host.n_layers + n_dm;
     pa.status = h->d_status;
     pa.dyn[0] = dyn;
     cudaError_t e;
@@ -500,6 +526,58 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         if ((e = cudaStreamWaitEvent(stream, h->ev_join[j], 0)) != cudaSuccess) return cuda_fail(h, e, "join wait");
     if ((e = cudaEventRecord(h->ev_measured, stream)) != cudaSuccess) return cuda_fail(h, e, "completion event");
     return WFS_OK;
+}
+
+// Actuator commands (modal base times the mirror's coefficients) and correction layer of every
+// mirror of the loop, on stream s.
+wfs_status loop_rebuild(wfs_loop lp, cudaStream_t s) {
+    wfs_handle h = lp->h;
+    const size_t SS = (size_t)h->S * h->S;
+    for (size_t d = 0; d < lp->dms.size(); ++d) {
+        const LoopDm &M = lp->dms[d];
+        GemvArgs g{M.d.m2a, M.d.n_act * M.d.n_act, M.d.n_modes, lp->coeffs + M.mode0, M.act, nullptr, nullptr};
+        long sl = timed_begin(h, "dm_actuators", s);
+        cudaError_t e = launch_gemv(g, s);
+        timed_end(h, sl, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "actuator launch");
+        DmLayerArgs a{};
+        a.act = M.act;
+        a.n_act = M.d.n_act;
+        a.support = M.d.support;
+        const double r = h->ds / M.d.pitch_m;
+        a.r_hi = (float)r;
+        a.r_lo = (float)(r - (double)a.r_hi);
+        a.c_int = (M.d.n_act - 1) / 2;
+        a.c_frac = (M.d.n_act - 1) % 2 ? 0.5f : 0.0f;
+        a.log2k = (float)std::log2(M.d.coupling);
+        const double edge = std::pow(M.d.coupling, (double)M.d.support * M.d.support);
+        a.edge = (float)edge;
+        a.inv_norm = (float)(1.0 / (1.0 - edge));
+        a.S = h->S;
+        a.x0 = M.x0;
+        a.y0 = M.y0;
+        a.w = M.w;
+        a.h = M.h;
+        a.layer = lp->layers + d * SS;
+        sl = timed_begin(h, "dm_layer", s);
+        e = launch_dm_layer(a, s);
+        timed_end(h, sl, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "mirror layer launch");
+    }
+    return WFS_OK;
+}
+
+void loop_free(wfs_loop lp) {
+    for (LoopDm &M : lp->dms) cudaFree(M.act);
+    cudaFree(lp->coeffs);
+    cudaFree(lp->layers);
+    if (lp->ev_done) cudaEventDestroy(lp->ev_done);
+    delete lp;
+}
+
+// One stream at a time for the loop's own buffers (coefficients, commands, layers).
+bool loop_busy(wfs_loop lp, cudaStream_t s) {
+    return s != lp->last_stream && cudaEventQuery(lp->ev_done) == cudaErrorNotReady;
 }
 
 }  // namespace
@@ -781,6 +859,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
 wfs_status wfs_destroy(wfs_handle h) {
     if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
     cudaDeviceSynchronize();
+    if (h->loop) wfs_loop_destroy(h->loop);
     release(h);
     delete h;
     return WFS_OK;
@@ -1461,6 +1540,149 @@ wfs_status wfs_batch_destroy(wfs_batch b) {
     if (!b) return fail(nullptr, WFS_EINVAL, "null batch");
     cudaDeviceSynchronize();
     batch_free(b);
+    return WFS_OK;
+}
+
+
+wfs_status wfs_loop_create(wfs_handle h, int n_dm, const wfs_dm *dms, const float *cm, const float *gain,
+                           wfs_loop *out) {
+    if (!out) return fail(h, WFS_EINVAL, "null output loop pointer");
+    *out = nullptr;
+    if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
+    if (h->loop) return fail(h, WFS_EBUSY, "the handle already has a loop");
+    if (n_dm < 1 || n_dm > kMaxDms || !dms) return fail(h, WFS_EINVAL, "n_dm must be in [1, 4] with a mirror array");
+    if (!cm || !gain) return fail(h, WFS_EINVAL, "null control matrix or gain vector");
+    double min_range = INFINITY;
+    for (const GsDev &g : h->gs)
+        if (g.gs.is_lgs) min_range = std::min(min_range, g.gs.range_m);
+    long long n_modes = 0;
+    for (int d = 0; d < n_dm; ++d) {
+        const wfs_dm &m = dms[d];
+        const std::string who = "mirror " + std::to_string(d) + ": ";
+        if (m.n_act < 1 || m.n_act > 1024) return fail(h, WFS_EINVAL, who + "n_act must be in [1, 1024]");
+        if (!is_finite(m.pitch_m) || !(m.pitch_m >= h->ds))
+            return fail(h, WFS_EINVAL, who + "pitch_m must be at least the screen pitch");
+        if (!is_finite(m.alt_m) || m.alt_m < 0 || !(m.alt_m < min_range))
+            return fail(h, WFS_EINVAL, who + "alt_m must be >= 0 and below every LGS range");
+        if (!(m.coupling > 0 && m.coupling < 1)) return fail(h, WFS_EINVAL, who + "coupling must be in (0, 1)");
+        if (m.support < 1 || m.support > kMaxDmSupport) return fail(h, WFS_EINVAL, who + "support must be in [1, 8]");
+        if (m.n_modes < 1 || !m.m2a) return fail(h, WFS_EINVAL, who + "n_modes must be >= 1 with a modal base");
+        n_modes += m.n_modes;
+    }
+    if (n_modes > (1 << 24)) return fail(h, WFS_EINVAL, "more than 2^24 modes");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != h->device) return fail(h, WFS_EINVAL, "current device differs from the handle's device");
+
+    wfs_loop lp = new wfs_loop_ctx;
+    lp->h = h;
+    lp->n_modes = (int)n_modes;
+    lp->n_slopes = 2 * h->total_valid;
+    lp->cm = cm;
+    lp->gain = gain;
+    const size_t SS = (size_t)h->S * h->S;
+    cudaError_t e;
+    auto bail = [&](cudaError_t err, const char *what) {
+        loop_free(lp);
+        return cuda_fail(h, err, what);
+    };
+    if ((e = cudaMalloc(&lp->coeffs, sizeof(float) * n_modes)) != cudaSuccess) return bail(e, "coefficients");
+    if ((e = cudaMalloc(&lp->layers, sizeof(float) * SS * n_dm)) != cudaSuccess) return bail(e, "mirror layers");
+    if ((e = cudaMemset(lp->coeffs, 0, sizeof(float) * n_modes)) != cudaSuccess ||
+        (e = cudaMemset(lp->layers, 0, sizeof(float) * SS * n_dm)) != cudaSuccess)
+        return bail(e, "loop buffers");
+    if ((e = cudaEventCreateWithFlags(&lp->ev_done, cudaEventDisableTiming)) != cudaSuccess) return bail(e, "event");
+    int mode0 = 0;
+    for (int d = 0; d < n_dm; ++d) {
+        LoopDm M;
+        M.d = dms[d];
+        M.mode0 = mode0;
+        mode0 += M.d.n_modes;
+        // pixels (i, j) whose distance to the nearest actuator along x or y is below the
+        // support: |(j - S/2) ds| < (c + R) p, clipped to the grid
+        const double reach = (0.5 * (M.d.n_act - 1) + M.d.support) * M.d.pitch_m / h->ds;
+        const long long lo = std::max(0LL, (long long)std::floor(0.5 * h->S - reach));
+        const long long hi = std::min((long long)h->S - 1, (long long)std::ceil(0.5 * h->S + reach));
+        M.x0 = M.y0 = (int)lo;
+        M.w = M.h = hi >= lo ? (int)(hi - lo + 1) : 0;
+        const size_t na = (size_t)M.d.n_act * M.d.n_act;
+        if ((e = cudaMalloc(&M.act, sizeof(float) * na)) != cudaSuccess ||
+            (e = cudaMemset(M.act, 0, sizeof(float) * na)) != cudaSuccess) {
+            if (M.act) cudaFree(M.act);
+            return bail(e, "actuator commands");
+        }
+        lp->dms.push_back(M);
+    }
+    // the mirrors are layers n_layers .. n_layers + n_dm - 1 of the projection: no wind, no offset
+    for (int d = 0; d < n_dm; ++d) {
+        const int l = h->inst_host.n_layers + d;
+        h->inst_host.alt[l] = dms[d].alt_m;
+        h->inst_host.vx[l] = h->inst_host.vy[l] = 0.0;
+        h->inst_host.x0[l] = h->inst_host.y0[l] = 0.0;
+    }
+    if ((e = cudaMemcpy(h->d_inst, &h->inst_host, sizeof(InstDesc), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "layer table");
+    h->loop = lp;
+    *out = lp;
+    return WFS_OK;
+}
+
+wfs_status wfs_loop_step(wfs_loop lp, const float *screens, double t_s, float *slopes_out, void *stream) {
+    if (!lp) return fail(nullptr, WFS_EINVAL, "null loop");
+    wfs_handle h = lp->h;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (loop_busy(lp, s)) return fail(h, WFS_EBUSY, "loop busy on another stream (its previous step is still running)");
+    wfs_status st = measure_impl(h, screens, t_s, slopes_out, nullptr, s, lp->layers, (int)lp->dms.size());
+    if (st != WFS_OK) return st;
+    lp->last_stream = s;
+    // the integrator: c += gain * (cm s)
+    GemvArgs g{lp->cm, lp->n_modes, lp->n_slopes, slopes_out, nullptr, lp->gain, lp->coeffs};
+    long sl = timed_begin(h, "reconstruct", s);
+    cudaError_t e = launch_gemv(g, s);
+    timed_end(h, sl, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reconstruction launch");
+    if ((st = loop_rebuild(lp, s)) != WFS_OK) return st;
+    if ((e = cudaEventRecord(lp->ev_done, s)) != cudaSuccess) return cuda_fail(h, e, "completion event");
+    return WFS_OK;
+}
+
+wfs_status wfs_loop_set_coeffs(wfs_loop lp, const float *coeffs, void *stream) {
+    if (!lp) return fail(nullptr, WFS_EINVAL, "null loop");
+    wfs_handle h = lp->h;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (loop_busy(lp, s)) return fail(h, WFS_EBUSY, "loop busy on another stream");
+    lp->last_stream = s;
+    const size_t bytes = sizeof(float) * lp->n_modes;
+    cudaError_t e = coeffs ? cudaMemcpyAsync(lp->coeffs, coeffs, bytes, cudaMemcpyDeviceToDevice, s)
+                           : cudaMemsetAsync(lp->coeffs, 0, bytes, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "coefficients");
+    wfs_status st = loop_rebuild(lp, s);
+    if (st != WFS_OK) return st;
+    if ((e = cudaEventRecord(lp->ev_done, s)) != cudaSuccess) return cuda_fail(h, e, "completion event");
+    return WFS_OK;
+}
+
+wfs_status wfs_loop_get_coeffs(wfs_loop lp, float *coeffs_out, void *stream) {
+    if (!lp || !coeffs_out) return fail(lp ? lp->h : nullptr, WFS_EINVAL, "null loop or output");
+    cudaError_t e = cudaMemcpyAsync(coeffs_out, lp->coeffs, sizeof(float) * lp->n_modes, cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? WFS_OK : cuda_fail(lp->h, e, "coefficients");
+}
+
+wfs_status wfs_loop_get_layer(wfs_loop lp, int d, float *layer_out, void *stream) {
+    if (!lp || !layer_out || d < 0 || d >= (int)lp->dms.size())
+        return fail(lp ? lp->h : nullptr, WFS_EINVAL, "bad loop, mirror index or output");
+    const size_t SS = (size_t)lp->h->S * lp->h->S;
+    cudaError_t e = cudaMemcpyAsync(layer_out, lp->layers + d * SS, sizeof(float) * SS, cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? WFS_OK : cuda_fail(lp->h, e, "mirror layer");
+}
+
+wfs_status wfs_loop_destroy(wfs_loop lp) {
+    if (!lp) return fail(nullptr, WFS_EINVAL, "null loop");
+    cudaEventSynchronize(lp->ev_done);
+    lp->h->loop = nullptr;
+    loop_free(lp);
     return WFS_OK;
 }
 

@@ -18,16 +18,19 @@
 namespace gbwfs {
 
 constexpr int kMaxGuideStars = 32;
-constexpr int kMaxLayers = 32;
+constexpr int kMaxLayers = 32;         // turbulent layers of an instance
+constexpr int kMaxDms = 4;             // deformable mirrors of a closed loop
+constexpr int kMaxProjLayers = kMaxLayers + kMaxDms;  // layers a projection sums
 constexpr int kMaxNaSlices = 16;
 constexpr int kMaxN = 64;           // largest DFT size
 constexpr int kMaxNPix = 32;        // largest subaperture side in pupil pixels
 constexpr int kMaxInstances = 64;   // instances per launch (batch size limit)
 
 struct InstDesc {                   // static per instance
-    int n_layers, S;
+    int n_layers, S;                // turbulent layers; mirror layers follow them (InstDyn::n_dm)
     double ds;
-    double alt[kMaxLayers], vx[kMaxLayers], vy[kMaxLayers], x0[kMaxLayers], y0[kMaxLayers];
+    double alt[kMaxProjLayers], vx[kMaxProjLayers], vy[kMaxProjLayers], x0[kMaxProjLayers],
+        y0[kMaxProjLayers];
     uint64_t seed;
 };
 
@@ -54,6 +57,9 @@ struct WfsDesc {                    // static per wavefront sensor
 
 struct InstDyn {                    // per call, per instance
     const float *screens;           // [L][S][S]
+    const float *dm;                // [n_dm][S][S] mirror correction layers (closed loop), summed
+                                    // after the screens as layers n_layers .. n_layers + n_dm - 1
+    int n_dm;
     float *opd;                     // projected OPD, subaperture-tiled
     float *slopes;                  // [sum n_valid][2]
     float *st_I, *st_E, *st_C;      // optional stage outputs (null = not written)
@@ -70,7 +76,7 @@ struct ProjArgs {
     int block_base;                 // projection block of this launch's first block (a launch
                                     // may cover a contiguous range of the WFS table)
     int n_blocks;                   // blocks in this launch (set by the launcher)
-    int max_layers;                 // largest n_layers of the launch's instances
+    int max_layers;                 // largest n_layers + n_dm of the launch's instances
     int *work;                      // ticket counter pair {next, CTAs done}, zero between
                                     // launches, one launch at a time; null = one CTA per block
     int *status;                    // device status word (limit errors)
@@ -109,6 +115,29 @@ struct KtilArgs {
     int n, N, n_sub, n_valid, n_na;
     double D, dx, pix_rad, sigma_px, launch_x, launch_y, h0;
     double alt[kMaxNaSlices], w[kMaxNaSlices];
+};
+
+// ---------------------------------------------------------------- closed loop
+constexpr int kMaxDmSupport = 8;    // influence radius limit (pitches)
+
+struct GemvArgs {                   // y = A x (rows x cols, row-major); c += gain * y if c
+    const float *A;
+    int rows, cols;
+    const float *x;
+    float *y;
+    const float *gain;
+    float *c;
+};
+
+struct DmLayerArgs {                // one mirror's correction layer over a window of the grid
+    const float *act;               // [n_act][n_act] actuator commands
+    int n_act, support;
+    float r_hi, r_lo;               // screen pitch / actuator pitch as hi + lo (<= 1)
+    int c_int;                      // (n_act - 1) / 2 = c_int + c_frac
+    float c_frac;
+    float log2k, edge, inv_norm;    // log2(coupling), coupling^(R^2), 1 / (1 - coupling^(R^2))
+    int S, x0, y0, w, h;            // grid size and window (columns x0 .. x0 + w, rows y0 .. y0 + h)
+    float *layer;                   // [S][S]
 };
 
 #ifdef __CUDACC__
@@ -187,6 +216,10 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
                     std::vector<uint8_t> &B2l);
 // Bounded mbarrier wait that is never satisfied; writes WFS_ETIMEOUT to *status.
 cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
+// Closed-loop kernels.
+cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s);
+cudaError_t gemv_launch_shape(const GemvArgs &a, LaunchShape *out);
+cudaError_t launch_dm_layer(const DmLayerArgs &a, cudaStream_t s);
 // Sets the calling thread's message returned by wfs_last_error(NULL).
 void set_thread_error(const char *msg);
 

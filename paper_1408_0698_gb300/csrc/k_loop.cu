@@ -1,0 +1,171 @@
+// k_loop.cu -- the per-step kernels of the closed loop (Sec. 3 "The closed loop": the slopes
+// times the control matrix are the differential modal coefficients added to the mirror's, a
+// pure integrator; Sec. 3 "Influence function and modal base": a mirror is a combination of a
+// modal base over its actuators' influence functions).
+//
+//   k_gemv      y = A x for a row-major FP32 matrix, optionally followed by the integrator
+//               c += gain * y on the same rows.  Used for the reconstruction (A = control
+//               matrix, x = slopes) and for the actuator commands (A = modal base, x = the
+//               mirror's coefficients).  HBM-bound: the matrix is streamed once.
+//   k_dm_layer  a mirror's correction layer (minus its shape) on the atmospheric screen grid,
+//               over the window its influence functions reach.
+#include "internal.h"
+#include "proj_math.cuh"
+
+namespace gbwfs {
+
+namespace {
+constexpr int kGemvThreads = 256;
+constexpr int kGemvRows = 4;  // rows per CTA: each x chunk loaded serves four rows
+}
+
+// Four rows per CTA.  All threads walk the rows' 16-byte chunks in step, so each warp reads
+// 512 contiguous bytes of every row per iteration (streaming loads: the matrix is read once),
+// x comes through the read-only path; the CTA then reduces its partial sums in a fixed order.
+template <bool kVec>
+__global__ void __launch_bounds__(kGemvThreads) k_gemv(const __grid_constant__ GemvArgs a) {
+    const int r0 = blockIdx.x * kGemvRows;
+    float acc[kGemvRows];
+#pragma unroll
+    for (int r = 0; r < kGemvRows; ++r) acc[r] = 0.0f;
+    const float *rows[kGemvRows];
+#pragma unroll
+    for (int r = 0; r < kGemvRows; ++r) rows[r] = a.A + (size_t)min(r0 + r, a.rows - 1) * a.cols;
+    if (kVec) {
+        const int n4 = a.cols >> 2;
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
+#pragma unroll 2
+        for (int k = threadIdx.x; k < n4; k += kGemvThreads) {
+            const float4 xv = __ldg(x4 + k);
+#pragma unroll
+            for (int r = 0; r < kGemvRows; ++r) {
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(rows[r]) + k);
+                acc[r] = fmaf(v.x, xv.x, acc[r]);
+                acc[r] = fmaf(v.y, xv.y, acc[r]);
+                acc[r] = fmaf(v.z, xv.z, acc[r]);
+                acc[r] = fmaf(v.w, xv.w, acc[r]);
+            }
+        }
+    } else {
+        for (int k = threadIdx.x; k < a.cols; k += kGemvThreads) {
+            const float xv = __ldg(a.x + k);
+#pragma unroll
+            for (int r = 0; r < kGemvRows; ++r) acc[r] = fmaf(__ldcs(rows[r] + k), xv, acc[r]);
+        }
+    }
+    __shared__ float part[kGemvThreads / 32][kGemvRows];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < kGemvRows; ++r) {
+        float v = acc[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp][r] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kGemvRows) {
+        const int r = threadIdx.x, row = r0 + r;
+        float y = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kGemvThreads / 32; ++w) y += part[w][r];
+        if (row < a.rows) {
+            if (a.y) a.y[row] = y;
+            if (a.c) a.c[row] = fmaf(a.gain[row], y, a.c[row]);
+        }
+    }
+}
+
+cudaError_t gemv_launch_shape(const GemvArgs &a, LaunchShape *out) {
+    const bool vec = (a.cols & 3) == 0 && ((uintptr_t)a.A & 15) == 0 && ((uintptr_t)a.x & 15) == 0;
+    out->func = vec ? (const void *)k_gemv<true> : (const void *)k_gemv<false>;
+    out->grid = dim3((a.rows + kGemvRows - 1) / kGemvRows);
+    out->block = dim3(kGemvThreads);
+    out->smem = 0;
+    return cudaSuccess;
+}
+
+cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s) {
+    if (a.rows <= 0) return cudaSuccess;
+    LaunchShape sh;
+    cudaError_t e = gemv_launch_shape(a, &sh);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
+}
+
+// A CTA computes a 32-column x 64-row tile of the window in two separable passes: first
+// T[ay][j] = sum_ax act[ay][ax] w(u_x(j) - ax) for the actuator rows the tile's rows reach, then
+// layer[i][j] = -sum_ay w(u_y(i) - ay) T[ay][j].  A pixel's fractional actuator coordinate
+// u = (j - S/2) ds / p + c comes from the projection's exact two-float product (ds / p held as
+// hi + lo), split into an integer actuator and a fraction; the 2R + 2 actuators per axis around
+// it get the weights w(u) = max(0, k^(u^2) - k^(R^2)) / (1 - k^(R^2)).  Actuators off the grid
+// get weight zero (their index is clamped to a valid one).  The actuator pitch is at least the
+// screen pitch, so the tile's 64 rows reach at most 64 + 2R + 2 actuator rows.
+namespace {
+constexpr int kDmTx = 32, kDmTy = 64;
+constexpr int kDmW = 2 * kMaxDmSupport + 2;     // weights per pixel and axis
+constexpr int kDmRows = kDmTy + kDmW;           // actuator rows a tile reaches
+}
+
+__device__ __forceinline__ void dm_axis_weights(const DmLayerArgs &a, int pix, int &base, float *w) {
+    int off;
+    float frac;
+    screen_offset(a.r_hi, a.r_lo, a.c_frac, (float)(pix - a.S / 2), off, frac);
+    base = off + a.c_int - a.support;  // first actuator of the 2R + 2
+    const int nw = 2 * a.support + 2;
+    for (int k = 0; k < nw; ++k) {
+        const float u = frac + (float)(a.support - k);  // pixel minus actuator base + k, in pitches
+        const float g = exp2f(u * u * a.log2k) - a.edge;
+        const int ac = base + k;
+        w[k] = (g > 0.0f && ac >= 0 && ac < a.n_act) ? g * a.inv_norm : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_dm_layer(const __grid_constant__ DmLayerArgs a) {
+    __shared__ float cw[kDmTx][kDmW], rw[kDmTy][kDmW], T[kDmRows][kDmTx];
+    __shared__ int cb[kDmTx], rb[kDmTy];
+    const int j0 = a.x0 + blockIdx.x * kDmTx, i0 = a.y0 + blockIdx.y * kDmTy;
+    const int nw = 2 * a.support + 2;
+    const int t = threadIdx.x;
+    if (t < kDmTx) dm_axis_weights(a, j0 + t, cb[t], cw[t]);
+    else if (t < kDmTx + kDmTy) dm_axis_weights(a, i0 + t - kDmTx, rb[t - kDmTx], rw[t - kDmTx]);
+    __syncthreads();
+    // pass 1: the actuator rows ay_lo .. ay_lo + nr - 1 the tile's rows reach
+    const int ay_lo = rb[0];
+    const int nr = min(rb[kDmTy - 1] + nw - ay_lo, kDmRows);
+    for (int e = t; e < nr * kDmTx; e += 256) {
+        const int r = e / kDmTx, jj = e - r * kDmTx;
+        const int ay = ay_lo + r;
+        float acc = 0.0f;
+        if (ay >= 0 && ay < a.n_act) {
+            const float *row = a.act + (size_t)ay * a.n_act;
+            for (int k = 0; k < nw; ++k) {
+                const int ax = min(max(cb[jj] + k, 0), a.n_act - 1);
+                acc = fmaf(__ldg(row + ax), cw[jj][k], acc);
+            }
+        }
+        T[r][jj] = acc;
+    }
+    __syncthreads();
+    // pass 2: one column per lane, 8 rows per warp step
+    const int jj = t & 31, j = j0 + jj;
+    if (j >= a.x0 + a.w) return;
+    for (int ii = t >> 5; ii < kDmTy; ii += 8) {
+        const int i = i0 + ii;
+        if (i >= a.y0 + a.h) break;
+        const int r0 = rb[ii] - ay_lo;
+        float sum = 0.0f;
+        for (int k = 0; k < nw; ++k) sum = fmaf(rw[ii][k], T[r0 + k][jj], sum);
+        a.layer[(size_t)i * a.S + j] = -sum;  // the mirror takes its shape out of the beam
+    }
+}
+
+cudaError_t launch_dm_layer(const DmLayerArgs &a, cudaStream_t s) {
+    if (a.w <= 0 || a.h <= 0) return cudaSuccess;
+    if (a.support < 1 || a.support > kMaxDmSupport || !(a.r_hi <= 1.0f)) return cudaErrorInvalidValue;
+    const dim3 grid((a.w + kDmTx - 1) / kDmTx, (a.h + kDmTy - 1) / kDmTy);
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel((const void *)k_dm_layer, grid, dim3(256), args, 0, s);
+}
+
+}  // namespace gbwfs

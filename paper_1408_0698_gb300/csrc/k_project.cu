@@ -25,7 +25,7 @@ __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
     return r < 0 ? r + S : r;
 }
 
-constexpr int kOffsTable = 64;  // layer offsets a CTA keeps for every (WFS, layer) of its launch
+constexpr int kOffsTable = 96;  // layer offsets a CTA keeps for every (WFS, layer) of its launch
 
 // One projection block (a tiled segment, or kProjThreads 2x2 pixel blocks); every thread of
 // the CTA calls it (its shared memory is free again once all threads have returned).  tab: the
@@ -49,7 +49,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
 
     const LayerOffs *s_off = all_offs ? tab + lo * a.max_layers : tab;
     if (!all_offs && lo != last_wfs) {  // uniform: last_wfs was written before the caller's barrier
-        if ((int)threadIdx.x < I.n_layers) tab[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
+        if ((int)threadIdx.x < proj_layers(I, D)) tab[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
         __syncthreads();
         if (threadIdx.x == 0) last_wfs = lo;  // read again only after the caller's barrier
     }
@@ -63,9 +63,9 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
         // (l + 1) mod 3, last read by layer l - 2, which every thread finished before the
         // previous barrier; so one barrier per layer suffices (box l landed, tables l visible).
         extern __shared__ float psm[];
-        __shared__ int4 s_geom[kMaxLayers];  // per layer: box origin (bx0, by0) and size (bw, bh)
+        __shared__ int4 s_geom[kMaxProjLayers];  // per layer: box origin (bx0, by0) and size (bw, bh)
         const int4 sg = W.segs[bid - W.proj_block_begin];  // sy, v_first, count, sx0
-        const int n = W.n, nn = n * n, ncol = sg.z * n, L = I.n_layers;
+        const int n = W.n, nn = n * n, ncol = sg.z * n, L = proj_layers(I, D);
         const int tab_floats = (6 * (ncol + n) + 3) & ~3;  // three tables, 16-byte aligned boxes
         const int box_floats = ((a.box_cap - tab_floats) / 3) & ~3;
         // buffer i: tables at tab0 + i (ncol + n), box at box0 + i box_floats
@@ -113,7 +113,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
             const int4 gm = s_geom[l];
             const int bx0 = gm.x, by0 = gm.y, bw = gm.z, bh = gm.w;
             if (bw * bh > box_floats) return false;
-            const float *scr = D.screens + (size_t)l * S * S;
+            const float *scr = layer_screen(I, D, l);
             if (vec) {
                 // one warp per box row, one lane per 16-byte chunk
                 const int cw = bw >> 2, lane = threadIdx.x & 31, cbase = s_off[l].bu + bx0;
@@ -214,9 +214,10 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
         yr[j] = (float)(sy * n + p0 + j) - half;
     }
     float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    for (int l = 0; l < I.n_layers; ++l) {
+    const int L = proj_layers(I, D);
+    for (int l = 0; l < L; ++l) {
         const LayerOffs lo = s_off[l];
-        const float *scr = D.screens + (size_t)l * S * S;
+        const float *scr = layer_screen(I, D, l);
         int ci0[2], ci1[2];
         float fx[2];
         const float *row0[2], *row1[2];
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
             const int w = i / a.max_layers, l = i - w * a.max_layers;
             const WfsDesc &W = a.wfs[w];
             const InstDesc &I = a.inst[W.inst];
-            if (l < I.n_layers) s_tab[i] = layer_offsets(I, W, a.dyn[W.inst].t, l);
+            if (l < proj_layers(I, a.dyn[W.inst])) s_tab[i] = layer_offsets(I, W, a.dyn[W.inst].t, l);
         }
     }
     if (threadIdx.x == 0) s_last_wfs = -1;

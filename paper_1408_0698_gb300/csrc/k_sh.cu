@@ -41,7 +41,7 @@ __host__ __device__ inline int team_floats(int n, int N, int nd, int team) {
     r2 = r2 > nd * nd ? r2 : nd * nd;
     r2 += r2 & 1;
     const int red = 4 * (team / 32) + 4;
-    return ri + r1 + r2 + red + 6 * kMaxLayers;  // then the layer offsets of a fused projection
+    return ri + r1 + r2 + red + 6 * kMaxProjLayers;  // then the layer offsets of a fused projection
 }
 
 template <int TEAM>
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
             // kernel (layer offsets in FP64, bilinear samples summed over the layers in order)
             LayerOffs *lo = reinterpret_cast<LayerOffs *>(red + 4 * (TEAM / 32) + 4);
             const InstDesc &I = a.inst[W.inst];
-            if (tid < I.n_layers) lo[tid] = layer_offsets(I, W, D.t, tid);
+            const int L = proj_layers(I, D);
+            for (int l = tid; l < L; l += TEAM) lo[l] = layer_offsets(I, W, D.t, l);
             team_sync<TEAM>(team);
             const int S = I.S;
             const bool pow2 = (S & (S - 1)) == 0;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
                 const int pp = i / n, qq = i - pp * n;
                 const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
                 float acc = 0.0f;
-                for (int l = 0; l < I.n_layers; ++l) {
+                for (int l = 0; l < L; ++l) {
                     const LayerOffs L0 = lo[l];
                     int ou, ov, i0, i1, j0, j1;
                     float fx, gy;
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
                     screen_offset(L0.c, L0.cl, L0.fv, yr, ov, gy);
                     wrap_pair(L0.bu + ou, S, pow2, i0, i1);
                     wrap_pair(L0.bv + ov, S, pow2, j0, j1);
-                    const float *scr = D.screens + (size_t)l * S * S;
+                    const float *scr = layer_screen(I, D, l);
                     const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
                     const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
                     const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);

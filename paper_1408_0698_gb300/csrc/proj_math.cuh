@@ -22,6 +22,16 @@ struct LayerOffs {
     float c, cl;   // c_l dx / ds as hi + lo
 };
 
+// Layers a projection of instance (I, D) sums: the turbulent screens, then the mirrors'
+// correction layers.
+__device__ __forceinline__ int proj_layers(const InstDesc &I, const InstDyn &D) { return I.n_layers + D.n_dm; }
+
+// The S x S array of layer l.
+__device__ __forceinline__ const float *layer_screen(const InstDesc &I, const InstDyn &D, int l) {
+    const size_t SS = (size_t)I.S * I.S;
+    return l < I.n_layers ? D.screens + (size_t)l * SS : D.dm + (size_t)(l - I.n_layers) * SS;
+}
+
 // Layer l's offsets for WFS W at time t (FP64).
 __device__ __forceinline__ LayerOffs layer_offsets(const InstDesc &I, const WfsDesc &W, double t, int l) {
     const int S = I.S;

@@ -72,6 +72,12 @@ class wfs_batch_class(C.Structure):
                 ("n_wfs", C.c_int), ("n_subaps", C.c_int), ("grid_cap", C.c_int), ("cta_warps", C.c_int)]
 
 
+class wfs_dm(C.Structure):
+    _fields_ = [("n_act", C.c_int), ("pitch_m", C.c_double), ("alt_m", C.c_double),
+                ("coupling", C.c_double), ("support", C.c_int), ("n_modes", C.c_int),
+                ("m2a", C.c_void_p)]
+
+
 class wfs_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int), ("total_ms", C.c_double)]
 
@@ -116,6 +122,12 @@ _SIGS = {
                                          C.c_double, C.c_uint64, C.c_uint32, C.c_int, C.c_void_p, C.c_int,
                                          C.POINTER(C.c_int), C.c_void_p]),
     "wfs_timing_read": (C.c_int, [_H, C.c_int, C.POINTER(wfs_kernel_time), C.POINTER(C.c_int)]),
+    "wfs_loop_create": (C.c_int, [_H, C.c_int, C.POINTER(wfs_dm), C.c_void_p, C.c_void_p, C.POINTER(_H)]),
+    "wfs_loop_step": (C.c_int, [_H, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "wfs_loop_set_coeffs": (C.c_int, [_H, C.c_void_p, C.c_void_p]),
+    "wfs_loop_get_coeffs": (C.c_int, [_H, C.c_void_p, C.c_void_p]),
+    "wfs_loop_get_layer": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p]),
+    "wfs_loop_destroy": (C.c_int, [_H]),
 }
 
 
@@ -297,6 +309,34 @@ def wfs_batch_info(b):
 
 def wfs_batch_destroy(b):
     _check(lib().wfs_batch_destroy(b))
+
+
+def wfs_loop_create(h, dms, cm_ptr, gain_ptr):
+    """dms: wfs_dm structs (m2a device addresses set); returns the loop handle."""
+    lp = _H()
+    arr = (wfs_dm * len(dms))(*dms)
+    _check(lib().wfs_loop_create(h, len(dms), arr, cm_ptr, gain_ptr, C.byref(lp)), h)
+    return lp
+
+
+def wfs_loop_step(lp, h, screens_ptr, t, slopes_ptr, stream=0):
+    _check(lib().wfs_loop_step(lp, screens_ptr, float(t), slopes_ptr, stream), h)
+
+
+def wfs_loop_set_coeffs(lp, h, coeffs_ptr, stream=0):
+    _check(lib().wfs_loop_set_coeffs(lp, coeffs_ptr or None, stream), h)
+
+
+def wfs_loop_get_coeffs(lp, h, out_ptr, stream=0):
+    _check(lib().wfs_loop_get_coeffs(lp, out_ptr, stream), h)
+
+
+def wfs_loop_get_layer(lp, h, d, out_ptr, stream=0):
+    _check(lib().wfs_loop_get_layer(lp, int(d), out_ptr, stream), h)
+
+
+def wfs_loop_destroy(lp):
+    _check(lib().wfs_loop_destroy(lp))
 
 
 # ------------------------------------------------------------------ config marshalling

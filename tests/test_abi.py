@@ -71,6 +71,14 @@ def test_null_arguments():
     assert L.wfs_noise_apply(None, 10, 1.0, 0, 0, 0.0, 0, None, None) == native.WFS_EINVAL
     n = C.c_int()
     assert L.wfs_num_valid(None, 0, C.byref(n)) == native.WFS_EINVAL
+    lp = native._H()
+    assert L.wfs_loop_create(None, 1, None, None, None, C.byref(lp)) == native.WFS_EINVAL
+    assert L.wfs_loop_create(None, 1, None, None, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_step(None, None, 0.0, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_set_coeffs(None, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_get_coeffs(None, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_get_layer(None, 0, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_destroy(None) == native.WFS_EINVAL
 
 
 def test_no_silent_cpu_path_without_gpu():
