@@ -369,3 +369,29 @@ def loop_step(cfg, screens, t, dms, m2a, cm, gain, coeffs, seed=0, noise=False):
     cfg2, scr2 = with_dm_layers(cfg, screens, dms, layers)
     s = measure(cfg2, scr2, t, seed, noise)
     return s, _f64(coeffs) + _f64(gain) * (_f64(cm) @ s.ravel())
+
+
+def interaction_matrix(cfg, star_index, dms, m2a, amplitude, modes=None):
+    """Push-pull registration (Sec. 3 "The calibration of the interaction matrices"; Sec. 5: a
+    modal push-pull scheme): for each mode m, the slopes of guide star ``star_index`` with
+    +amplitude of the mode in the beam (mirror coefficient -amplitude) minus those with
+    -amplitude, over 2 amplitude; no turbulence, no noise, t = 0.  Returns [len(modes), 2 n_valid]
+    (row m: slopes x, y interleaved per subaperture)."""
+    n = sum(M.shape[1] for M in m2a)
+    modes = range(n) if modes is None else modes
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    empty = dataclasses.replace(cfg.layers, alt_m=np.zeros(0), wind_vx_mps=np.zeros(0),
+                                wind_vy_mps=np.zeros(0), x0_m=np.zeros(0), y0_m=np.zeros(0))
+    cfg0 = dataclasses.replace(cfg, layers=empty)
+    no_screens = np.zeros((0, S, S), np.float32)
+    rows = []
+    for m in modes:
+        s = []
+        for sign in (-1.0, 1.0):
+            c = np.zeros(n)
+            c[m] = sign * amplitude
+            layers = [dm_layer(d, a, S, ds) for d, a in zip(dms, actuators(dms, m2a, c))]
+            cfg2, scr2 = with_dm_layers(cfg0, no_screens, dms, layers)
+            s.append(measure_wfs(cfg2, scr2, star_index, 0.0)["slopes"].ravel())
+        rows.append((s[0] - s[1]) / (2.0 * amplitude))
+    return np.array(rows)

@@ -590,16 +590,8 @@ def test_closed_loop_integrator_corrects_a_static_modal_aberration():
     S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
     dm = inputs.Dm(11, 0.4, 0.0, 8, coupling=0.15, support=3)
     M = inputs.modal_base(dm, 11, amplitude_m=1e-8).astype(np.float64)
-    zero = np.zeros((1, S, S), np.float32)
-    ns = 2 * len(oracle.measure(cfg, zero, 0.0))
     # interaction matrix: slopes per unit coefficient of +mode in the beam (= minus its layer)
-    IM = np.zeros((ns, dm.n_modes))
-    amp = 0.5
-    for m in range(dm.n_modes):
-        beam = -oracle.dm_layer(dm, M[:, m] * amp, S, ds)
-        sp = oracle.measure(cfg, beam[None], 0.0).ravel()
-        sm = oracle.measure(cfg, -beam[None], 0.0).ravel()
-        IM[:, m] = (sp - sm) / (2 * amp)
+    IM = oracle.interaction_matrix(cfg, 0, [dm], [M], 0.5).T
     CM = np.linalg.pinv(IM)
     c_star = np.random.default_rng(2).standard_normal(dm.n_modes)
     ol = -oracle.dm_layer(dm, M @ c_star, S, ds)[None]
@@ -615,3 +607,27 @@ def test_closed_loop_integrator_corrects_a_static_modal_aberration():
     sb, cb = oracle.loop_step(cfg, ol, 0.0, [dm], [M], -CM, gain, np.zeros(dm.n_modes))
     sb1, _ = oracle.loop_step(cfg, ol, 0.0, [dm], [M], CM, gain, cb)
     assert np.linalg.norm(sb1) > 1.5 * np.linalg.norm(s0)
+
+
+def test_interaction_matrix_push_pull():
+    """Push-pull rows: the mode put in the beam as a screen (minus its mirror layer) gives the
+    same slopes through the plain measurement; the central difference is odd in the amplitude
+    and converges (halving the amplitude changes it by O(a^2)); a pure actuator-space tilt of
+    the mirror gives x slopes of one sign and no mean y slope."""
+    cfg = _small_loop_cfg()
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    dm = inputs.Dm(11, 0.4, 0.0, 3)
+    M = inputs.modal_base(dm, 4, amplitude_m=1e-8).astype(np.float64)
+    xa = (np.arange(11) - 5) * 0.4
+    M[:, 2] = np.tile(xa, 11) * 2e-8                           # tilt along x: act ~ x_a
+    a = 0.5
+    IM = oracle.interaction_matrix(cfg, 0, [dm], [M], a)
+    beam = -oracle.dm_layer(dm, M[:, 0] * a, S, ds)            # +a of mode 0 in the beam
+    ref = (oracle.measure(cfg, beam[None], 0.0) - oracle.measure(cfg, -beam[None], 0.0)).ravel() / (2 * a)
+    np.testing.assert_allclose(IM[0], ref, rtol=0, atol=1e-12)
+    IMn = oracle.interaction_matrix(cfg, 0, [dm], [M], -a)
+    np.testing.assert_allclose(IMn, IM, rtol=0, atol=1e-12)
+    IMh = oracle.interaction_matrix(cfg, 0, [dm], [M], a / 2)
+    assert np.linalg.norm(IMh - IM) < 0.05 * np.linalg.norm(IM)
+    tilt = IM[2].reshape(-1, 2)
+    assert np.all(tilt[:, 0] > 0) and abs(tilt[:, 1].mean()) < 1e-3 * tilt[:, 0].mean()
