@@ -341,6 +341,48 @@ def closed_loop(cfg, s_d, flush, args, dev, rank):
     return out
 
 
+def calibration(cfg, args, dev, rank):
+    """Push-pull registration of the interaction matrix of the ground mirror (81 x 81 actuators,
+    5000 modes) with one 80 x 80 LGS of the ELT frame -- the calibration the paper times (Sec. 5:
+    5000 modes, 80 x 80 subapertures, one LGS, about 14 hours).  Two measurements per mode, no
+    noise, no turbulence; timed with CUDA events after one untimed registration."""
+    import torch
+
+    from paper_1408_0698_gb300 import inputs, native
+    dm = inputs.elt_dms()[0]
+    M = torch.as_tensor(inputs.modal_base(dm, cfg.seed + 70)).to(dev)
+    w = native.Wfs(cfg, seed=cfg.seed + rank, noise=False)
+    ns = 2 * w.total
+    cm = torch.zeros((dm.n_modes, ns), device=dev)
+    gain = torch.zeros(dm.n_modes, device=dev)
+    lp = native.wfs_loop_create(w.h, [native.wfs_dm(dm.n_act, dm.pitch_m, dm.alt_m, dm.coupling, dm.support,
+                                                    dm.n_modes, M.data_ptr())], cm.data_ptr(), gain.data_ptr())
+    nv = native.wfs_num_valid(w.h, 0)
+    im = torch.empty((dm.n_modes, 2 * nv), device=dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    native.wfs_loop_calibrate(lp, w.h, 0, 1.0, im.data_ptr(), sp)
+    torch.cuda.synchronize()
+    reps = 3
+    native.wfs_timing_enable(w.h, True)
+    native.wfs_timing_read(w.h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        native.wfs_loop_calibrate(lp, w.h, 0, 1.0, im.data_ptr(), sp)
+    e1.record()
+    torch.cuda.synchronize()
+    native.wfs_sync_status(w.h)
+    kt = native.wfs_timing_read(w.h)
+    s = e0.elapsed_time(e1) / 1e3 / reps
+    native.wfs_loop_destroy(lp)
+    w.close()
+    return {"workload": f"ground mirror {dm.n_act}x{dm.n_act} actuators, {dm.n_modes} modes, push-pull with LGS 0 "
+                        f"of the ELT frame ({nv} subapertures, BF16x3 spots), no noise",
+            "seconds": s, "modes_per_s": dm.n_modes / s, "spots_per_s": 2 * dm.n_modes * nv / s,
+            "repetitions": reps, "paper_seconds": 14 * 3600.0,
+            "kernels": {k: {"launches": v[0] // reps, "avg_ms": v[1] / max(1, v[0])} for k, v in kt.items()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,6 +570,7 @@ def main():
                                          for k, v in kt2.items()}}
     if not args.no_loop:
         line["closed_loop"] = closed_loop(cfg, s_d, flush, args, dev, rank)
+        line["calibration"] = calibration(cfg, args, dev, rank)
     if not args.no_served:
         line["served"] = served()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -418,6 +418,27 @@ wfs_status wfs_loop_get_coeffs(wfs_loop lp, float *coeffs_out, void *stream);
 wfs_status wfs_loop_get_layer(wfs_loop lp, int d, float *layer_out, void *stream);
 wfs_status wfs_loop_destroy(wfs_loop lp);
 
+/*
+ * wfs_loop_calibrate -- push-pull registration of the interaction matrix of
+ * guide star gs over all the loop's modes (Sec. 3 "The calibration of the
+ * interaction matrices": the modes of the base register the slopes of the WFS;
+ * Sec. 5: a modal push-pull scheme, 5000 modes of one LGS).  For each mode m
+ * the star is measured with +amplitude of the mode in the beam (mirror
+ * coefficient -amplitude, the other coefficients 0) and with -amplitude,
+ * without turbulence, without noise, at t = 0, through the same projection
+ * and spot kernels as wfs_loop_step; row m of im_out (device, row-major
+ * [n_modes][2 n_valid_gs], x and y interleaved per subaperture as in
+ * wfs_measure) is the difference over 2 amplitude: slopes per unit
+ * coefficient, so that cm = pinv(im^T) restricted to that star's slopes.
+ * Modes go 32 at a time (64 measurements per launch).  The first call for a
+ * star allocates its scratch (64 layers of S x S floats plus the star's OPD,
+ * expected images and slopes, 64 times) and synchronises the device; later
+ * calls for the same star are asynchronous on `stream`.  The loop's
+ * coefficients and layers are left unchanged.  WFS_EINVAL: gs out of range,
+ * amplitude zero or not finite, null im_out.
+ */
+wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_out, void *stream);
+
 /* Library version string. */
 const char *wfs_version(void);
 

@@ -123,7 +123,21 @@ struct LoopDm {
     float *act = nullptr;             // [n_act * n_act]
 };
 
+// Scratch of the push-pull calibration: kMaxInstances copies of one guide star's WFS entry
+// (instance i = mode k of the chunk pushed (i = 2k) or pulled (i = 2k + 1)), each with its own
+// mirror layer, OPD, expected images and slopes.
+struct CalibScratch {
+    int gs = -1, kind = 0, geom = 0, group = 0, nv = 0, blocks_per_wfs = 0;
+    size_t opd_stride = 0, det_stride = 0;
+    WfsDesc *d_wfs = nullptr;        // [kMaxInstances]
+    InstDesc *d_inst = nullptr;      // [n_dm][kMaxInstances]: a mirror as the only layer
+    float *opd = nullptr, *E = nullptr, *slopes = nullptr, *layers = nullptr;
+    int *work = nullptr;             // ticket pairs: projection, spot kernel
+    int cur_dm = -1;                 // mirror whose windows the layer buffers hold
+};
+
 struct wfs_loop_ctx {
+    CalibScratch cal;
     wfs_handle h = nullptr;
     std::vector<LoopDm> dms;
     int n_modes = 0, n_slopes = 0;
@@ -530,9 +544,38 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
 
 // Actuator commands (modal base times the mirror's coefficients) and correction layer of every
 // mirror of the loop, on stream s.
+// Layer arguments of mirror M with commands act_scale * act[i * act_stride].
+DmLayerArgs dm_layer_args(wfs_handle h, const LoopDm &M, const float *act, int act_stride, float act_scale,
+                          float *layer) {
+    DmLayerArgs a{};
+    a.act = act;
+    a.act_stride = act_stride;
+    a.act_scale = act_scale;
+    a.n_act = M.d.n_act;
+    a.support = M.d.support;
+    const double r = h->ds / M.d.pitch_m;
+    a.r_hi = (float)r;
+    a.r_lo = (float)(r - (double)a.r_hi);
+    a.c_int = (M.d.n_act - 1) / 2;
+    a.c_frac = (M.d.n_act - 1) % 2 ? 0.5f : 0.0f;
+    a.log2k = (float)std::log2(M.d.coupling);
+    const double edge = std::pow(M.d.coupling, (double)M.d.support * M.d.support);
+    a.edge = (float)edge;
+    a.inv_norm = (float)(1.0 / (1.0 - edge));
+    a.S = h->S;
+    a.x0 = M.x0;
+    a.y0 = M.y0;
+    a.w = M.w;
+    a.h = M.h;
+    a.layer = layer;
+    return a;
+}
+
 wfs_status loop_rebuild(wfs_loop lp, cudaStream_t s) {
     wfs_handle h = lp->h;
     const size_t SS = (size_t)h->S * h->S;
+    static thread_local DmLayerBatch batch;
+    batch.n = (int)lp->dms.size();
     for (size_t d = 0; d < lp->dms.size(); ++d) {
         const LoopDm &M = lp->dms[d];
         GemvArgs g{M.d.m2a, M.d.n_act * M.d.n_act, M.d.n_modes, lp->coeffs + M.mode0, M.act, nullptr, nullptr};
@@ -540,34 +583,91 @@ wfs_status loop_rebuild(wfs_loop lp, cudaStream_t s) {
         cudaError_t e = launch_gemv(g, s);
         timed_end(h, sl, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "actuator launch");
-        DmLayerArgs a{};
-        a.act = M.act;
-        a.n_act = M.d.n_act;
-        a.support = M.d.support;
-        const double r = h->ds / M.d.pitch_m;
-        a.r_hi = (float)r;
-        a.r_lo = (float)(r - (double)a.r_hi);
-        a.c_int = (M.d.n_act - 1) / 2;
-        a.c_frac = (M.d.n_act - 1) % 2 ? 0.5f : 0.0f;
-        a.log2k = (float)std::log2(M.d.coupling);
-        const double edge = std::pow(M.d.coupling, (double)M.d.support * M.d.support);
-        a.edge = (float)edge;
-        a.inv_norm = (float)(1.0 / (1.0 - edge));
-        a.S = h->S;
-        a.x0 = M.x0;
-        a.y0 = M.y0;
-        a.w = M.w;
-        a.h = M.h;
-        a.layer = lp->layers + d * SS;
-        sl = timed_begin(h, "dm_layer", s);
-        e = launch_dm_layer(a, s);
-        timed_end(h, sl, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "mirror layer launch");
+        batch.l[d] = dm_layer_args(h, M, M.act, 1, 1.0f, lp->layers + d * SS);
     }
+    long sl = timed_begin(h, "dm_layer", s);
+    cudaError_t e = launch_dm_layers(batch, s);
+    timed_end(h, sl, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "mirror layer launch");
+    return WFS_OK;
+}
+
+void calib_free(CalibScratch &c) {
+    cudaFree(c.d_wfs);
+    cudaFree(c.d_inst);
+    cudaFree(c.opd);
+    cudaFree(c.E);
+    cudaFree(c.slopes);
+    cudaFree(c.layers);
+    cudaFree(c.work);
+    c = CalibScratch{};
+}
+
+// Builds the calibration scratch for guide star gs (kept until another star is calibrated).
+wfs_status calib_prepare(wfs_loop lp, int gs) {
+    wfs_handle h = lp->h;
+    CalibScratch &c = lp->cal;
+    if (c.gs == gs) return WFS_OK;
+    cudaDeviceSynchronize();  // the previous star's scratch may still be in use
+    calib_free(c);
+    int k = -1;
+    for (size_t i = 0; i < h->wfs_host.size(); ++i)
+        if (h->wfs_host[i].gs_index == gs) k = (int)i;
+    if (k < 0) return fail(h, WFS_EINVAL, "internal: guide star not in the work table");
+    int grp = -1;
+    for (size_t g = 0; g < h->groups.size(); ++g)
+        if (k >= h->groups[g].first && k < h->groups[g].first + h->groups[g].count) grp = (int)g;
+    if (grp < 0) return fail(h, WFS_EINVAL, "internal: guide star in no spot group");
+    const WfsDesc base = h->wfs_host[k];
+    const GeomDev &G = h->geoms[h->groups[grp].geom];
+    c.kind = h->groups[grp].kind;
+    c.geom = h->groups[grp].geom;
+    c.group = grp;
+    c.nv = base.n_valid;
+    c.blocks_per_wfs = project_blocks(base);
+    c.opd_stride = (size_t)c.nv * base.n * base.n;
+    c.det_stride = (size_t)c.nv * G.g.n_det * G.g.n_det;
+    std::vector<WfsDesc> w(kMaxInstances, base);
+    for (int i = 0; i < kMaxInstances; ++i) {
+        w[i].inst = i;
+        w[i].opd_off = w[i].slope_off = w[i].int_off = w[i].det_off = 0;
+        w[i].proj_block_begin = i * c.blocks_per_wfs;
+        w[i].subap_begin = i * c.nv;
+    }
+    const int n_dm = (int)lp->dms.size();
+    std::vector<InstDesc> in((size_t)n_dm * kMaxInstances);
+    for (int d = 0; d < n_dm; ++d) {
+        InstDesc I = h->inst_host;
+        I.n_layers = 0;  // the mirror is the only layer (InstDyn::n_dm = 1)
+        I.alt[0] = lp->dms[d].d.alt_m;
+        I.vx[0] = I.vy[0] = I.x0[0] = I.y0[0] = 0.0;
+        for (int i = 0; i < kMaxInstances; ++i) in[(size_t)d * kMaxInstances + i] = I;
+    }
+    const size_t SS = (size_t)h->S * h->S;
+    cudaError_t e;
+    auto bail = [&](cudaError_t err, const char *what) {
+        calib_free(c);
+        return cuda_fail(h, err, what);
+    };
+    if ((e = cudaMalloc(&c.d_wfs, sizeof(WfsDesc) * kMaxInstances)) != cudaSuccess) return bail(e, "calibration table");
+    if ((e = cudaMalloc(&c.d_inst, sizeof(InstDesc) * in.size())) != cudaSuccess) return bail(e, "calibration table");
+    if ((e = cudaMalloc(&c.opd, sizeof(float) * c.opd_stride * kMaxInstances)) != cudaSuccess ||
+        (e = cudaMalloc(&c.E, sizeof(float) * c.det_stride * kMaxInstances)) != cudaSuccess ||
+        (e = cudaMalloc(&c.slopes, sizeof(float) * 2 * c.nv * kMaxInstances)) != cudaSuccess ||
+        (e = cudaMalloc(&c.layers, sizeof(float) * SS * kMaxInstances)) != cudaSuccess ||
+        (e = cudaMalloc(&c.work, sizeof(int) * 4)) != cudaSuccess)
+        return bail(e, "calibration scratch");
+    if ((e = cudaMemcpy(c.d_wfs, w.data(), sizeof(WfsDesc) * kMaxInstances, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c.d_inst, in.data(), sizeof(InstDesc) * in.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(c.work, 0, sizeof(int) * 4)) != cudaSuccess)
+        return bail(e, "calibration tables");
+    c.gs = gs;
+    c.cur_dm = -1;
     return WFS_OK;
 }
 
 void loop_free(wfs_loop lp) {
+    calib_free(lp->cal);
     for (LoopDm &M : lp->dms) cudaFree(M.act);
     cudaFree(lp->coeffs);
     cudaFree(lp->layers);
@@ -1683,6 +1783,102 @@ wfs_status wfs_loop_destroy(wfs_loop lp) {
     cudaEventSynchronize(lp->ev_done);
     lp->h->loop = nullptr;
     loop_free(lp);
+    return WFS_OK;
+}
+
+
+wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_out, void *stream) {
+    if (!lp) return fail(nullptr, WFS_EINVAL, "null loop");
+    wfs_handle h = lp->h;
+    if (gs < 0 || gs >= (int)h->gs.size()) return fail(h, WFS_EINVAL, "guide star index out of range");
+    if (!is_finite(amplitude) || amplitude == 0.0) return fail(h, WFS_EINVAL, "amplitude must be finite and non-zero");
+    if (!im_out) return fail(h, WFS_EINVAL, "null output");
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (loop_busy(lp, s)) return fail(h, WFS_EBUSY, "loop busy on another stream");
+    wfs_status st = calib_prepare(lp, gs);
+    if (st != WFS_OK) return st;
+    lp->last_stream = s;
+    CalibScratch &c = lp->cal;
+    const SpotGroup &G = h->groups[c.group];
+    const size_t SS = (size_t)h->S * h->S;
+    const int n_slopes = 2 * c.nv;
+    const int per_chunk = kMaxInstances / 2;
+    static thread_local DmLayerBatch batch;
+    static thread_local ProjArgs pa;
+    static thread_local ShArgs sa;
+    cudaError_t e;
+    for (size_t d = 0; d < lp->dms.size(); ++d) {
+        const LoopDm &M = lp->dms[d];
+        if (c.cur_dm != (int)d) {  // other windows: clear what the previous mirror left
+            if ((e = cudaMemsetAsync(c.layers, 0, sizeof(float) * SS * kMaxInstances, s)) != cudaSuccess)
+                return cuda_fail(h, e, "calibration layers");
+            c.cur_dm = (int)d;
+        }
+        for (int m0 = 0; m0 < M.d.n_modes; m0 += per_chunk) {
+            const int K = std::min(per_chunk, M.d.n_modes - m0), ni = 2 * K;
+            // instance 2k: +amplitude of mode m0 + k in the beam (coefficient -amplitude), 2k + 1: -amplitude
+            batch.n = ni;
+            for (int i = 0; i < ni; ++i)
+                batch.l[i] = dm_layer_args(h, M, M.d.m2a + m0 + i / 2, M.d.n_modes,
+                                           (float)((i & 1) ? amplitude : -amplitude), c.layers + i * SS);
+            long sl = timed_begin(h, "dm_layer", s);
+            e = launch_dm_layers(batch, s);
+            timed_end(h, sl, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "calibration layers");
+            InstDyn dyn;
+            memset(&dyn, 0, sizeof dyn);
+            dyn.n_dm = 1;
+            pa.inst = c.d_inst + d * kMaxInstances;
+            pa.wfs = c.d_wfs;
+            pa.n_wfs = ni;
+            pa.n_inst = ni;
+            pa.box_cap = h->proj_box;
+            pa.block_base = 0;
+            pa.max_layers = 1;
+            pa.work = c.work;
+            pa.status = h->d_status;
+            for (int i = 0; i < ni; ++i) {
+                dyn.dm = c.layers + i * SS;
+                dyn.opd = c.opd + i * c.opd_stride;
+                dyn.slopes = c.slopes + (size_t)i * n_slopes;
+                dyn.st_E = c.E + i * c.det_stride;
+                pa.dyn[i] = dyn;
+            }
+            sl = timed_begin(h, "project", s);
+            e = launch_project(pa, ni * c.blocks_per_wfs, s);
+            timed_end(h, sl, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "calibration projection");
+            memset(&sa, 0, offsetof(ShArgs, dyn));
+            fill_geom_args(sa, h->geoms[c.geom]);
+            sa.inst = pa.inst;
+            sa.wfs = c.d_wfs;
+            sa.n_wfs = ni;
+            sa.total = ni * c.nv;
+            sa.status = h->d_status;
+            sa.grid_cap = G.grid_cap;
+            sa.cta_warps = G.cta_warps;
+            sa.n_inst = ni;
+            sa.work = c.work + 2;
+            sa.project = 0;
+            sa.split_noise = splits_noise(c.kind) ? 1 : 0;
+            memcpy(sa.dyn, pa.dyn, sizeof(InstDyn) * ni);
+            sl = timed_begin(h, kind_name(c.kind) + std::to_string(sa.N), s);
+            e = launch_spot(c.kind, sa, s, !h->timing);
+            timed_end(h, sl, s);
+            if (e == cudaSuccess && sa.split_noise) {
+                sl = timed_begin(h, "noise_cog", s);
+                e = launch_noise_cog(sa, s, !h->timing);
+                timed_end(h, sl, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(h, e, "calibration spot launch");
+            sl = timed_begin(h, "push_pull_rows", s);
+            e = launch_push_pull_rows(c.slopes, K, n_slopes, (float)(0.5 / amplitude),
+                                      im_out + (size_t)(M.mode0 + m0) * n_slopes, s);
+            timed_end(h, sl, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "interaction rows");
+        }
+    }
+    if ((e = cudaEventRecord(lp->ev_done, s)) != cudaSuccess) return cuda_fail(h, e, "completion event");
     return WFS_OK;
 }
 

@@ -130,7 +130,9 @@ struct GemvArgs {                   // y = A x (rows x cols, row-major); c += ga
 };
 
 struct DmLayerArgs {                // one mirror's correction layer over a window of the grid
-    const float *act;               // [n_act][n_act] actuator commands
+    const float *act;               // actuator commands: act_scale * act[(ay n_act + ax) act_stride]
+    int act_stride;                 // 1 for a command vector, n_modes for a modal-base column
+    float act_scale;
     int n_act, support;
     float r_hi, r_lo;               // screen pitch / actuator pitch as hi + lo (<= 1)
     int c_int;                      // (n_act - 1) / 2 = c_int + c_frac
@@ -219,7 +221,16 @@ cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
 // Closed-loop kernels.
 cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s);
 cudaError_t gemv_launch_shape(const GemvArgs &a, LaunchShape *out);
-cudaError_t launch_dm_layer(const DmLayerArgs &a, cudaStream_t s);
+// Correction layers of n mirrors (or push-pull instances) in one launch, n <= kMaxInstances.
+struct DmLayerBatch {
+    int n;
+    DmLayerArgs l[kMaxInstances];
+};
+cudaError_t launch_dm_layers(const DmLayerBatch &b, cudaStream_t s);
+// IM rows of a push-pull chunk: im[k][j] = (s[2k][j] - s[2k+1][j]) / (2 amplitude) for k < n_modes,
+// j < n_slopes, instance i's slopes at s + i * n_slopes.
+cudaError_t launch_push_pull_rows(const float *s, int n_modes, int n_slopes, float inv_2a, float *im,
+                                  cudaStream_t st);
 // Sets the calling thread's message returned by wfs_last_error(NULL).
 void set_thread_error(const char *msg);
 

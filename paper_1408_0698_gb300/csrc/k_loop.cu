@@ -121,9 +121,13 @@ __device__ __forceinline__ void dm_axis_weights(const DmLayerArgs &a, int pix, i
     }
 }
 
-__global__ void __launch_bounds__(256) k_dm_layer(const __grid_constant__ DmLayerArgs a) {
+// blockIdx.z: the layer of the batch; the grid covers the largest window, CTAs past a smaller
+// one leave at once.
+__global__ void __launch_bounds__(256) k_dm_layer(const __grid_constant__ DmLayerBatch b) {
     __shared__ float cw[kDmTx][kDmW], rw[kDmTy][kDmW], T[kDmRows][kDmTx];
     __shared__ int cb[kDmTx], rb[kDmTy];
+    const DmLayerArgs &a = b.l[blockIdx.z];
+    if ((int)blockIdx.x * kDmTx >= a.w || (int)blockIdx.y * kDmTy >= a.h) return;
     const int j0 = a.x0 + blockIdx.x * kDmTx, i0 = a.y0 + blockIdx.y * kDmTy;
     const int nw = 2 * a.support + 2;
     const int t = threadIdx.x;
@@ -138,13 +142,13 @@ __global__ void __launch_bounds__(256) k_dm_layer(const __grid_constant__ DmLaye
         const int ay = ay_lo + r;
         float acc = 0.0f;
         if (ay >= 0 && ay < a.n_act) {
-            const float *row = a.act + (size_t)ay * a.n_act;
+            const float *row = a.act + (size_t)ay * a.n_act * a.act_stride;
             for (int k = 0; k < nw; ++k) {
                 const int ax = min(max(cb[jj] + k, 0), a.n_act - 1);
-                acc = fmaf(__ldg(row + ax), cw[jj][k], acc);
+                acc = fmaf(__ldg(row + (size_t)ax * a.act_stride), cw[jj][k], acc);
             }
         }
-        T[r][jj] = acc;
+        T[r][jj] = acc * a.act_scale;
     }
     __syncthreads();
     // pass 2: one column per lane, 8 rows per warp step
@@ -160,12 +164,37 @@ __global__ void __launch_bounds__(256) k_dm_layer(const __grid_constant__ DmLaye
     }
 }
 
-cudaError_t launch_dm_layer(const DmLayerArgs &a, cudaStream_t s) {
-    if (a.w <= 0 || a.h <= 0) return cudaSuccess;
-    if (a.support < 1 || a.support > kMaxDmSupport || !(a.r_hi <= 1.0f)) return cudaErrorInvalidValue;
-    const dim3 grid((a.w + kDmTx - 1) / kDmTx, (a.h + kDmTy - 1) / kDmTy);
-    void *args[] = {(void *)&a};
-    return cudaLaunchKernel((const void *)k_dm_layer, grid, dim3(256), args, 0, s);
+cudaError_t launch_dm_layers(const DmLayerBatch &b, cudaStream_t s) {
+    if (b.n <= 0) return cudaSuccess;
+    if (b.n > kMaxInstances) return cudaErrorInvalidValue;
+    int gx = 0, gy = 0;
+    for (int i = 0; i < b.n; ++i) {
+        const DmLayerArgs &a = b.l[i];
+        if (a.support < 1 || a.support > kMaxDmSupport || !(a.r_hi <= 1.0f) || a.w < 0 || a.h < 0)
+            return cudaErrorInvalidValue;
+        gx = max(gx, (a.w + kDmTx - 1) / kDmTx);
+        gy = max(gy, (a.h + kDmTy - 1) / kDmTy);
+    }
+    if (gx == 0 || gy == 0) return cudaSuccess;
+    void *args[] = {(void *)&b};
+    return cudaLaunchKernel((const void *)k_dm_layer, dim3(gx, gy, b.n), dim3(256), args, 0, s);
+}
+
+__global__ void k_push_pull_rows(const float *__restrict__ s, int n_modes, int n_slopes, float inv_2a,
+                                 float *__restrict__ im) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n_modes * n_slopes) return;
+    const int k = (int)(e / n_slopes), j = (int)(e - (long long)k * n_slopes);
+    const float *push = s + (size_t)(2 * k) * n_slopes, *pull = push + n_slopes;
+    im[e] = (push[j] - pull[j]) * inv_2a;
+}
+
+cudaError_t launch_push_pull_rows(const float *s, int n_modes, int n_slopes, float inv_2a, float *im,
+                                  cudaStream_t st) {
+    const long long n = (long long)n_modes * n_slopes;
+    if (n <= 0) return cudaSuccess;
+    k_push_pull_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, n_modes, n_slopes, inv_2a, im);
+    return cudaGetLastError();
 }
 
 }  // namespace gbwfs

@@ -128,6 +128,7 @@ _SIGS = {
     "wfs_loop_get_coeffs": (C.c_int, [_H, C.c_void_p, C.c_void_p]),
     "wfs_loop_get_layer": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p]),
     "wfs_loop_destroy": (C.c_int, [_H]),
+    "wfs_loop_calibrate": (C.c_int, [_H, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -333,6 +334,10 @@ def wfs_loop_get_coeffs(lp, h, out_ptr, stream=0):
 
 def wfs_loop_get_layer(lp, h, d, out_ptr, stream=0):
     _check(lib().wfs_loop_get_layer(lp, int(d), out_ptr, stream), h)
+
+
+def wfs_loop_calibrate(lp, h, gs, amplitude, im_ptr, stream=0):
+    _check(lib().wfs_loop_calibrate(lp, int(gs), float(amplitude), im_ptr, stream), h)
 
 
 def wfs_loop_destroy(lp):

@@ -239,3 +239,64 @@ def test_elt_loop_step_full_size():
     tol = _coeff_tol(cm, gain, 1) + 1e-5 * np.abs(c_ref)
     assert np.all(np.abs(c_gpu - c_ref) <= tol)
     L.close()
+
+
+def _calibrate(L, gs, amp, nv):
+    im = torch.full((L.n_modes, 2 * nv), float("nan"), device="cuda")
+    native.wfs_loop_calibrate(L.lp, L.w.h, gs, amp, im.data_ptr(), L.stream)
+    torch.cuda.synchronize()
+    native.wfs_sync_status(L.w.h)
+    return im.cpu().numpy().astype(np.float64)
+
+
+def _check_im(im_gpu, im_ref, amp):
+    """Rows are slope differences over 2a: the slope bars apply to the rows times 2a."""
+    d = (im_gpu - im_ref) * 2 * abs(amp)
+    assert np.all(np.sqrt(np.mean(d ** 2, axis=1)) < SLOPE_RMS)
+    assert np.abs(d).max() < SLOPE_MAX
+
+
+@pytest.mark.parametrize("which", ["ngs_small", "config2"])
+def test_calibration_matches_oracle(which):
+    """Push-pull interaction matrices of every guide star over all modes (two mirrors on
+    config 2, one above the ground; modes not a multiple of the 32-mode chunk) against the
+    oracle's."""
+    if which == "ngs_small":
+        cfg, dms = _small_cfg(), [inputs.Dm(11, 0.4, 0.0, 40)]
+    else:
+        cfg, dms = inputs.config2(), [inputs.Dm(21, 0.4, 0.0, 37), inputs.Dm(15, 0.7, 6000.0, 9)]
+    m2a = [inputs.modal_base(d, 21 + i, amplitude_m=2e-8) for i, d in enumerate(dms)]
+    n = sum(d.n_modes for d in dms)
+    L = _Loop(cfg, dms, m2a, np.zeros((n, 2)), np.zeros(n))
+    c = np.random.default_rng(0).standard_normal(n)
+    L.set_coeffs(c)
+    before = [L.layer(d) for d in range(len(dms))]
+    amp = 0.5
+    for gs in range(len(cfg.stars)):
+        nv = native.wfs_num_valid(L.w.h, gs)
+        im = _calibrate(L, gs, amp, nv)
+        ref = oracle.interaction_matrix(cfg, gs, dms, m2a, amp)
+        _check_im(im, ref, amp)
+    # the loop's own state is untouched
+    np.testing.assert_array_equal(L.coeffs(), c.astype(np.float32))
+    for d in range(len(dms)):
+        np.testing.assert_array_equal(L.layer(d), before[d])
+    L.close()
+
+
+def test_calibration_elt_m4_full_size():
+    """The paper's calibration workload: the 5000 modes of the 81 x 81 ground mirror with one
+    80 x 80 LGS of the ELT frame (BF16x3 spots), all modes on the GPU; sampled modes from
+    every chunk position against the oracle."""
+    cfg = inputs.config3()
+    dm = inputs.elt_dms()[0]
+    M = inputs.modal_base(dm, 40)
+    L = _Loop(cfg, [dm], [M], np.zeros((dm.n_modes, 2)), np.zeros(dm.n_modes))
+    nv = native.wfs_num_valid(L.w.h, 0)
+    amp = 1.0
+    im = _calibrate(L, 0, amp, nv)
+    assert np.all(np.isfinite(im))
+    pick = [0, 31, 32, 2500, 4999]
+    ref = oracle.interaction_matrix(cfg, 0, [dm], [M.astype(np.float64)], amp, modes=pick)
+    _check_im(im[pick], ref, amp)
+    L.close()
