@@ -53,14 +53,15 @@ class _Star(C.Structure):
                 ("range_m", C.c_double), ("wavelength_m", C.c_double), ("launch_x", C.c_double),
                 ("launch_y", C.c_double), ("spot_fwhm_rad", C.c_double), ("photons", C.c_double),
                 ("read_noise", C.c_double), ("n_na", C.c_int),
-                ("na_alt", C.POINTER(C.c_double)), ("na_weight", C.POINTER(C.c_double))]
+                ("na_alt", C.POINTER(C.c_double)), ("na_weight", C.POINTER(C.c_double)),
+                ("up_diameter", C.c_double), ("up_samples", C.c_int)]
 
 
 class _Layers(C.Structure):
     _fields_ = [("n_layers", C.c_int), ("S", C.c_int), ("dx", C.c_double),
                 ("alt", C.POINTER(C.c_double)), ("vx", C.POINTER(C.c_double)),
                 ("vy", C.POINTER(C.c_double)), ("x0", C.POINTER(C.c_double)),
-                ("y0", C.POINTER(C.c_double))]
+                ("y0", C.POINTER(C.c_double)), ("n_atm", C.c_int)]
 
 
 class _Dm(C.Structure):
@@ -103,6 +104,7 @@ def lib():
             L.orc_dm_value.argtypes = [C.POINTER(_Dm), _dp, C.c_double, C.c_double]
             L.orc_dm_value.restype = C.c_double
             L.orc_dm_layer.argtypes = [C.POINTER(_Dm), _dp, C.c_int, C.c_double, _fp]
+            L.orc_uplink_tilt.argtypes = [C.POINTER(_Layers), _fp, C.POINTER(_Star), C.c_double, _dp, _dp]
             L.orc_num_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_set_threads.restype = None
@@ -141,6 +143,8 @@ def _star(gs, keep):
     s.n_na = len(gs.na_alt_m) if gs.is_lgs else 0
     s.na_alt = keep.d(gs.na_alt_m if len(gs.na_alt_m) else [0.0])
     s.na_weight = keep.d(gs.na_weight if len(gs.na_weight) else [0.0])
+    s.up_diameter = float(getattr(gs, "uplink_diameter_m", 0.0)) if gs.is_lgs else 0.0
+    s.up_samples = int(getattr(gs, "uplink_samples", 0))
     return s
 
 
@@ -149,6 +153,7 @@ def _layers(lay, keep):
     L.n_layers, L.S, L.dx = lay.n_layers, lay.screen_size, lay.screen_dx_m
     L.alt, L.vx, L.vy = keep.d(lay.alt_m), keep.d(lay.wind_vx_mps), keep.d(lay.wind_vy_mps)
     L.x0, L.y0 = keep.d(lay.x0_m), keep.d(lay.y0_m)
+    L.n_atm = lay.n_layers - int(getattr(lay, "n_mirrors", 0))
     return L
 
 
@@ -344,7 +349,8 @@ def with_dm_layers(cfg, screens, dms, layers):
         lay, alt_m=np.concatenate([_f64(lay.alt_m), [float(d.alt_m) for d in dms]]),
         wind_vx_mps=np.concatenate([_f64(lay.wind_vx_mps), z]),
         wind_vy_mps=np.concatenate([_f64(lay.wind_vy_mps), z]),
-        x0_m=np.concatenate([_f64(lay.x0_m), z]), y0_m=np.concatenate([_f64(lay.y0_m), z]))
+        x0_m=np.concatenate([_f64(lay.x0_m), z]), y0_m=np.concatenate([_f64(lay.y0_m), z]),
+        n_mirrors=int(getattr(lay, "n_mirrors", 0)) + k)
     cfg2 = dataclasses.replace(cfg, layers=lay2)
     scr = np.concatenate([np.asarray(screens, dtype=np.float32),
                           np.stack([np.asarray(l, dtype=np.float32) for l in layers])], axis=0)
@@ -381,7 +387,7 @@ def interaction_matrix(cfg, star_index, dms, m2a, amplitude, modes=None):
     modes = range(n) if modes is None else modes
     S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
     empty = dataclasses.replace(cfg.layers, alt_m=np.zeros(0), wind_vx_mps=np.zeros(0),
-                                wind_vy_mps=np.zeros(0), x0_m=np.zeros(0), y0_m=np.zeros(0))
+                                wind_vy_mps=np.zeros(0), x0_m=np.zeros(0), y0_m=np.zeros(0), n_mirrors=0)
     cfg0 = dataclasses.replace(cfg, layers=empty)
     no_screens = np.zeros((0, S, S), np.float32)
     rows = []
@@ -395,3 +401,14 @@ def interaction_matrix(cfg, star_index, dms, m2a, amplitude, modes=None):
             s.append(measure_wfs(cfg2, scr2, star_index, 0.0)["slopes"].ravel())
         rows.append((s[0] - s[1]) / (2.0 * amplitude))
     return np.array(rows)
+
+
+def uplink_tilt(cfg, screens, star_index, t):
+    """(dx, dy) radians: the LGS uplink tip-tilt that moves the whole spot."""
+    keep = _Keep()
+    L = _layers(cfg.layers, keep)
+    s = _star(cfg.stars[star_index], keep)
+    sc = np.ascontiguousarray(screens, dtype=np.float32)
+    dx, dy = C.c_double(), C.c_double()
+    lib().orc_uplink_tilt(C.byref(L), _ptr(sc, _fp), C.byref(s), float(t), C.byref(dx), C.byref(dy))
+    return dx.value, dy.value

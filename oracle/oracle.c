@@ -140,6 +140,40 @@ void orc_project_grid(double D, int Np, const orc_layers *L, const float *screen
         }
 }
 
+/* ---- LGS uplink tip-tilt (Sec. 4 Open Loop generation) ---- */
+
+void orc_uplink_tilt(const orc_layers *L, const float *screens, const orc_star *gs, double t,
+                     double *dx, double *dy)
+{
+    *dx = *dy = 0.0;
+    if (!gs->is_lgs || !(gs->up_diameter > 0) || gs->up_samples < 2) return;
+    int n = gs->up_samples;
+    double D = gs->up_diameter, H = gs->range_m;
+    for (int l = 0; l < L->n_atm; ++l) {
+        double h = L->alt[l];
+        if (!(h < H)) continue;
+        /* centre of the beam at the layer: from the launch point towards the spot */
+        double cx = gs->launch_x * (1.0 - h / H) + gs->theta_x * h;
+        double cy = gs->launch_y * (1.0 - h / H) + gs->theta_y * h;
+        double sxv = 0.0, syv = 0.0, sxx = 0.0, syy = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double ox = (j - (n - 1) / 2.0) * D / n, oy = (i - (n - 1) / 2.0) * D / n;
+                if (ox * ox + oy * oy > D * D / 4.0) continue;
+                double u = L->S / 2.0 + (cx + ox - (L->x0[l] + L->vx[l] * t)) / L->dx;
+                double v = L->S / 2.0 + (cy + oy - (L->y0[l] + L->vy[l] * t)) / L->dx;
+                double val = orc_bilinear(screens + (size_t)l * L->S * L->S, L->S, u, v);
+                sxv += ox * val;
+                syv += oy * val;
+                sxx += ox * ox;
+                syy += oy * oy;
+            }
+        /* plane fit: the offsets sum to zero over the symmetric sample set, so the mean drops out */
+        *dx += sxv / sxx * (H - h) / H;
+        *dy += syv / syy * (H - h) / H;
+    }
+}
+
 /* ---- spot by DFT (Sec. 4 LGS SH; Sec. 2 DFT) ---- */
 
 /* F[k][p] = exp(-2 pi i (k - cN)(p - cn) / N), cN = (N-1)/2, cn = (n-1)/2 */
@@ -464,6 +498,8 @@ int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
     if (!sel) n_sel = nv;
     double dx = g->diameter_m / Np;
     double pix_rad = gs->wavelength_m / (N * dx);
+    double upx, upy;
+    orc_uplink_tilt(L, screens, gs, t, &upx, &upy);
 
 #pragma omp parallel for schedule(dynamic)
     for (int s = 0; s < n_sel; ++s) {
@@ -479,7 +515,7 @@ int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
             for (int q = 0; q < n; ++q) {
                 int i = sy * n + p, j = sx * n + q;
                 double x = (j - (Np - 1) / 2.0) * dx, y = (i - (Np - 1) / 2.0) * dx;
-                double o = orc_opd(L, screens, gs, x, y, t);
+                double o = orc_opd(L, screens, gs, x, y, t) + (upx * x + upy * y);
                 if (opd_out) opd_out[(size_t)s * n * n + p * n + q] = o;
                 if (lit(g->diameter_m, g->obstruction, Np, i, j)) {
                     double phi = 2.0 * M_PI * o / gs->wavelength_m;

@@ -36,12 +36,16 @@ typedef struct {
     double launch_x, launch_y, spot_fwhm_rad, photons, read_noise;
     int n_na;
     const double *na_alt, *na_weight;
+    double up_diameter;               /* LGS uplink beam diameter (m); 0 = no uplink tip-tilt */
+    int up_samples;                   /* samples across the uplink beam */
 } orc_star;
 
 typedef struct {
     int n_layers, S;
     double dx;
     const double *alt, *vx, *vy, *x0, *y0;
+    int n_atm;                        /* turbulent layers (the first n_atm); the rest are mirror
+                                         layers, which the uplink beam does not cross */
 } orc_layers;
 
 /* Pupil: binary mask from the pixel-centre test eps*D/2 <= r <= D/2. */
@@ -57,6 +61,16 @@ double orc_opd(const orc_layers *L, const float *screens, const orc_star *gs,
 /* OPD on the whole Np x Np pupil grid of a geometry. */
 void orc_project_grid(double D, int Np, const orc_layers *L, const float *screens,
                       const orc_star *gs, double t, double *opd);
+/* LGS uplink tip-tilt (Sec. 4 Open Loop generation: the laser's projection on the sodium layer
+   is shifted by the tip-tilt integrated over the upward path).  The beam, of diameter
+   up_diameter, runs from the launch point (launch_x, launch_y) on the ground to theta * range on
+   the sodium layer; at each turbulent layer it is deflected by the least-squares plane slope of
+   the layer's OPD over its footprint (up_samples^2 points on a square grid of pitch
+   up_diameter / up_samples, those inside the disc), and the deflection acts over the rest of the
+   way up: (dx, dy) = sum_l slope_l (range - h_l) / range, the angle by which the whole spot moves.
+   The measurement adds dx x + dy y to the pupil OPD.  Zero for an NGS or up_diameter = 0. */
+void orc_uplink_tilt(const orc_layers *L, const float *screens, const orc_star *gs, double t,
+                     double *dx, double *dy);
 /* Centred 2-D DFT of an n x n field into N x N: Y = F X F^T. */
 void orc_dft2(int n, int N, const double *xr, const double *xi, double *yr, double *yi);
 /* Sodium elongation kernel (N x N, sums to one) of the subaperture centred at (rbx, rby). */

@@ -65,6 +65,8 @@ class GuideStar:
     spot_fwhm_rad: float = 0.0
     na_alt_m: np.ndarray = field(default_factory=lambda: np.zeros(0))
     na_weight: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    uplink_diameter_m: float = 0.0   # LGS launch beam diameter; 0 = no uplink tip-tilt
+    uplink_samples: int = 16         # samples across the launch beam
 
 
 @dataclass
@@ -80,6 +82,7 @@ class Layers:
     r0_m: float = 0.15
     L0_m: float = 25.0
     weights: np.ndarray = field(default_factory=lambda: np.ones(1))
+    n_mirrors: int = 0   # trailing layers that are mirror correction layers (closed loop)
 
     @property
     def n_layers(self) -> int:

@@ -6,6 +6,7 @@ invariant (Parseval, energy conservation, mirror symmetry), an exact special cas
 (integer shifts, linear screens) or statistics.  Each is chosen so that a plausible
 slip (dropped term, wrong sign or index, transposed operand) fails at least one.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -631,3 +632,60 @@ def test_interaction_matrix_push_pull():
     assert np.linalg.norm(IMh - IM) < 0.05 * np.linalg.norm(IM)
     tilt = IM[2].reshape(-1, 2)
     assert np.all(tilt[:, 0] > 0) and abs(tilt[:, 1].mean()) < 1e-3 * tilt[:, 0].mean()
+
+
+# ---------------------------------------------------------------- LGS uplink tip-tilt
+
+def _linear_layers_cfg(slopes_xy, alts, S=512, dx=0.05):
+    """Screens that are exact planes a x + b y (metres of OPD per metre) around the pupil."""
+    n = len(alts)
+    lay = inputs.Layers(alt_m=np.array(alts, float), wind_vx_mps=np.full(n, 3.0), wind_vy_mps=np.full(n, -2.0),
+                        x0_m=np.zeros(n), y0_m=np.zeros(n), screen_size=S, screen_dx_m=dx)
+    j = (np.arange(S) - S / 2) * dx
+    X, Y = np.meshgrid(j, j)
+    scr = np.stack([(a * X + b * Y).astype(np.float32) for a, b in slopes_xy])
+    return lay, scr
+
+
+def test_uplink_tilt_of_planar_layers_is_exact():
+    """Planar layers: the footprint plane fit returns each layer's gradient exactly, and the
+    deflections add with the lever arm (H - h) / H; zero for an NGS, without a beam, and for
+    layers at or above the sodium."""
+    ab = [(2e-6, -1e-6), (-5e-7, 3e-6), (1e-6, 1e-6)]
+    alts = [0.0, 8000.0, 15000.0]
+    lay, scr = _linear_layers_cfg(ab, alts)
+    star = inputs._lgs(20 * inputs.ARCSEC, 10 * inputs.ARCSEC, 0.7, 0)
+    star.uplink_diameter_m, star.uplink_samples = 0.5, 16
+    cfg = inputs.Config("up", inputs.Telescope(8.0, 0.0), [inputs.Geometry(10, 8, 16, 8)], [star], lay, seed=1)
+    H = star.range_m
+    dx, dy = oracle.uplink_tilt(cfg, scr, 0, 0.01)
+    ex = sum(a * (H - h) / H for (a, _), h in zip(ab, alts))
+    ey = sum(b * (H - h) / H for (_, b), h in zip(ab, alts))
+    assert dx == pytest.approx(ex, rel=1e-6) and dy == pytest.approx(ey, rel=1e-6)
+    star.uplink_diameter_m = 0.0
+    assert oracle.uplink_tilt(cfg, scr, 0, 0.01) == (0.0, 0.0)
+    ngs = inputs._ngs(0.0, 0.0, 700e-9, 0)
+    ngs.uplink_diameter_m = 0.5
+    cfg.stars = [ngs]
+    assert oracle.uplink_tilt(cfg, scr, 0, 0.01) == (0.0, 0.0)
+
+
+def test_uplink_tilt_equals_a_ground_tilt_layer():
+    """The measurement adds the uplink tilt to the pupil OPD: the slopes equal those without
+    uplink plus a ground layer that is exactly the plane dx x + dy y."""
+    cfg = _small_loop_cfg(is_lgs=True)
+    scr = inputs.make_screens(cfg.layers, 5)
+    cfg.stars[0].uplink_diameter_m = 0.4
+    cfg.stars[0].uplink_samples = 12
+    dx, dy = oracle.uplink_tilt(cfg, scr, 0, 0.0)
+    assert abs(dx) + abs(dy) > 1e-8
+    s_up = oracle.measure(cfg, scr, 0.0)
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    j = (np.arange(S) - S / 2) * ds
+    X, Y = np.meshgrid(j, j)
+    plane = (dx * X + dy * Y).astype(np.float32)
+    cfg_off = dataclasses.replace(cfg, stars=[dataclasses.replace(cfg.stars[0], uplink_diameter_m=0.0)])
+    cfg2, scr2 = oracle.with_dm_layers(cfg_off, scr, [inputs.Dm(3, 1.0, 0.0, 1)], [plane])
+    s_ref = oracle.measure(cfg2, scr2, 0.0)
+    np.testing.assert_allclose(s_up, s_ref, rtol=0, atol=1e-6)
+    assert np.abs(s_up - oracle.measure(cfg_off, scr, 0.0)).max() > 1e-3
