@@ -439,6 +439,29 @@ wfs_status wfs_loop_destroy(wfs_loop lp);
  */
 wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_out, void *stream);
 
+/*
+ * wfs_set_uplink -- the LGS uplink tip-tilt (Sec. 4 "Open Loop generation":
+ * the projection of the laser beam on the sodium layer is computed with the
+ * spot shift induced by the tip-tilt integrated over the upward path).  For
+ * laser guide star gs, a launch beam of diameter diameter_m runs from the
+ * star's launch point on the ground to theta * range; at each turbulent layer
+ * (not the loop's mirror layers) it is deflected by the least-squares plane
+ * slope of the layer's OPD over its footprint (samples x samples points on a
+ * square grid of pitch diameter_m / samples, those inside the disc, sampled
+ * bilinearly like the projection at the frame's time), and the deflection acts
+ * over the rest of the way up, times (range - h) / range.  The sum is the angle
+ * by which the whole spot moves; every later measurement of the handle adds
+ * it to the star's pupil OPD as a tilt (dx x + dy y), computed per frame by one
+ * small kernel before the projection.  diameter_m = 0 turns it off (default).
+ * Waits for the handle's measurement in flight, then updates its work table.
+ * Batches measure without it: wfs_batch_create rejects a handle with it on
+ * (WFS_EUNSUPPORTED).  WFS_EINVAL: gs out of range, an NGS with diameter_m > 0,
+ * diameter_m negative, not finite or not below half the screen width,
+ * samples outside [2, 64].  The paper gives
+ * no beam size or fit; the plane fit over a disc is this library's reading.
+ */
+wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples);
+
 /* Library version string. */
 const char *wfs_version(void);
 

@@ -63,6 +63,8 @@ struct GsDev {
     float2 *d_ktil = nullptr;
     int4 *d_segs = nullptr;
     int n_segs = 0, seg_cols = 0, tiled = 0;
+    double up_diam = 0.0;   // LGS uplink beam diameter (0: off)
+    int up_n = 0;
     size_t slope_off = 0, opd_off = 0, int_off = 0, det_off = 0;
 };
 
@@ -112,6 +114,11 @@ struct wfs_ctx {
     size_t ev_used = 0;
     bool ev_overflow = false;
     wfs_loop_ctx *loop = nullptr;     // attached closed loop (at most one)
+    float2 *d_uplink = nullptr;       // per guide star: uplink tilt per pupil pixel (x, y)
+    float2 *d_uplink_part = nullptr;  // per (WFS, layer) deflection
+    int *d_uplink_count = nullptr;    // per WFS: layers done (zero between launches)
+    int n_uplink = 0;                 // guide stars with the uplink tip-tilt on
+    cudaEvent_t ev_uplink = nullptr;  // after the uplink kernel: side groups with the uplink wait on it
 };
 
 // A closed loop attached to a handle: the mirrors, their coefficients, actuator commands and
@@ -307,6 +314,11 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 }
 
 void release(wfs_ctx *h) {
+    cudaFree(h->d_uplink);
+    cudaFree(h->d_uplink_part);
+    cudaFree(h->d_uplink_count);
+    if (h->ev_uplink) cudaEventDestroy(h->ev_uplink);
+    h->d_uplink = nullptr;
     for (auto &g : h->geoms) {
         cudaFree(g.F);
         cudaFree(g.Ga);
@@ -456,13 +468,13 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     dyn.n_dm = n_dm;
 
     static thread_local ProjArgs pa;
+    cudaError_t e;
     pa.inst = h->d_inst;
     pa.n_inst = 1;
     pa.box_cap = h->proj_box;
     pa.max_layers = h->inst_host.n_layers + n_dm;
     pa.status = h->d_status;
     pa.dyn[0] = dyn;
-    cudaError_t e;
     // projection of a contiguous range of the WFS table (a group's WFSs, or all of them)
     auto project = [&](const SpotGroup &G, cudaStream_t ls) -> cudaError_t {
         const int blocks = G.proj_count;
@@ -472,7 +484,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         pa.block_base = G.proj_base;
         pa.work = h->d_work + 2 * (h->groups.size() + 1) + 2 * (&G - h->groups.data());
         long slot = timed_begin(h, "project", ls);
-        cudaError_t err = launch_project(pa, blocks, ls);
+        cudaError_t err = launch_project(pa, blocks, ls, ls == stream && h->n_uplink > 0 && !h->timing);
         timed_end(h, slot, ls);
         return err;
     };
@@ -511,14 +523,29 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         }
         return err;
     };
+    // the side groups fork before the uplink kernel; a side group holding a WFS with the uplink
+    // on also waits for it (the projections add the uplink tilt)
+    const bool forks = h->groups.size() > 1;
+    if (forks && (e = cudaEventRecord(h->ev_fork, stream)) != cudaSuccess) return cuda_fail(h, e, "fork");
+    if (h->n_uplink > 0) {
+        long slot = timed_begin(h, "uplink", stream);
+        e = launch_uplink(h->d_inst, h->d_wfs, (int)h->wfs_host.size(), h->inst_host.n_layers, h->d_uplink_part,
+                          h->d_uplink_count, &dyn, stream);
+        timed_end(h, slot, stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "uplink launch");
+        if ((e = cudaEventRecord(h->ev_uplink, stream)) != cudaSuccess) return cuda_fail(h, e, "uplink event");
+    }
     size_t k = 0;
     for (size_t j = 0; j < h->groups.size(); ++j) {
         const SpotGroup &G = h->groups[j];
         if (j == big || G.total == 0) continue;
         if (k >= h->side.size()) return fail(h, WFS_EINVAL, "internal: missing side stream");
-        if (k == 0 && (e = cudaEventRecord(h->ev_fork, stream)) != cudaSuccess) return cuda_fail(h, e, "fork");
         cudaStream_t ss = h->side[k];
         if ((e = cudaStreamWaitEvent(ss, h->ev_fork, 0)) != cudaSuccess) return cuda_fail(h, e, "fork wait");
+        bool needs_uplink = false;
+        for (int q = 0; q < G.count; ++q) needs_uplink |= h->wfs_host[G.first + q].uplink != nullptr;
+        if (needs_uplink && (e = cudaStreamWaitEvent(ss, h->ev_uplink, 0)) != cudaSuccess)
+            return cuda_fail(h, e, "uplink wait");
         // a generic-kernel group (a few NGS subapertures) projects inside its spot kernel: one
         // launch that starts with the call and owns its SMs only while it runs
         const bool fused = G.kind == kSpotGeneric;
@@ -631,6 +658,7 @@ wfs_status calib_prepare(wfs_loop lp, int gs) {
     for (int i = 0; i < kMaxInstances; ++i) {
         w[i].inst = i;
         w[i].opd_off = w[i].slope_off = w[i].int_off = w[i].det_off = 0;
+        w[i].uplink = nullptr;  // no turbulence: no uplink tilt
         w[i].proj_block_begin = i * c.blocks_per_wfs;
         w[i].subap_begin = i * c.nv;
     }
@@ -898,6 +926,9 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 d.n_segs = s.n_segs;
                 d.tiled = s.tiled;
                 d.seg_cols = s.seg_cols;
+                d.launch_x = s.gs.launch_x_m;
+                d.launch_y = s.gs.launch_y_m;
+                d.uplink = nullptr;
                 d.proj_block_begin = blocks;
                 blocks += project_blocks(d);
                 if (project_box_floats(d) > h->proj_box) h->proj_box = project_box_floats(d);
@@ -1328,6 +1359,8 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
         if (hs[i]->device != dev) return fail(nullptr, WFS_EINVAL, "batch handles must live on the current device");
         for (int j = 0; j < i; ++j)
             if (hs[j] == hs[i]) return fail(nullptr, WFS_EINVAL, "a handle appears twice in the batch");
+        if (hs[i]->n_uplink > 0)
+            return fail(nullptr, WFS_EUNSUPPORTED, "batch: a handle has the uplink tip-tilt on (not batched)");
     }
     wfs_batch b = new wfs_batch_ctx();
     b->hs.assign(hs, hs + n);
@@ -1359,6 +1392,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
             for (int k = 0; k < G.count; ++k) {
                 WfsDesc d = hs[i]->wfs_host[G.first + k];
                 d.inst = i;
+                d.uplink = nullptr;  // batches measure without the uplink tip-tilt
                 per[c].push_back(d);
             }
         }
@@ -1879,6 +1913,44 @@ wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_o
         }
     }
     if ((e = cudaEventRecord(lp->ev_done, s)) != cudaSuccess) return cuda_fail(h, e, "completion event");
+    return WFS_OK;
+}
+
+
+wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples) {
+    if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
+    if (gs < 0 || gs >= (int)h->gs.size()) return fail(h, WFS_EINVAL, "guide star index out of range");
+    GsDev &g = h->gs[gs];
+    const bool on = diameter_m > 0;
+    if (!is_finite(diameter_m) || diameter_m < 0) return fail(h, WFS_EINVAL, "diameter_m must be finite and >= 0");
+    if (on && !g.gs.is_lgs) return fail(h, WFS_EINVAL, "the uplink tip-tilt applies to laser guide stars only");
+    if (on && (samples < 2 || samples > 64)) return fail(h, WFS_EINVAL, "samples must be in [2, 64]");
+    if (on && diameter_m / samples < 1e-6) return fail(h, WFS_EINVAL, "uplink sample pitch below 1 micron");
+    if (on && !(diameter_m < 0.5 * h->S * h->ds)) return fail(h, WFS_EINVAL, "uplink beam wider than half the screen");
+    cudaError_t e;
+    if (on && !h->d_uplink) {
+        const size_t nw = h->wfs_host.size();
+        if ((e = cudaMalloc(&h->d_uplink, sizeof(float2) * h->gs.size())) != cudaSuccess ||
+            (e = cudaMemset(h->d_uplink, 0, sizeof(float2) * h->gs.size())) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_uplink_part, sizeof(float2) * nw * kMaxLayers)) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_uplink_count, sizeof(int) * nw)) != cudaSuccess ||
+            (e = cudaMemset(h->d_uplink_count, 0, sizeof(int) * nw)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&h->ev_uplink, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(h, e, "uplink buffer");
+    }
+    cudaEventSynchronize(h->ev_measured);  // the work table is read by the measurement in flight
+    for (size_t k = 0; k < h->wfs_host.size(); ++k) {
+        WfsDesc &d = h->wfs_host[k];
+        if (d.gs_index != gs) continue;
+        d.uplink = on ? h->d_uplink + gs : nullptr;
+        d.up_diam = on ? diameter_m : 0.0;
+        d.up_n = on ? samples : 0;
+        if ((e = cudaMemcpy(h->d_wfs + k, &d, sizeof(WfsDesc), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(h, e, "work table");
+    }
+    if (on != (g.up_diam > 0)) h->n_uplink += on ? 1 : -1;
+    g.up_diam = on ? diameter_m : 0.0;
+    g.up_n = on ? samples : 0;
     return WFS_OK;
 }
 

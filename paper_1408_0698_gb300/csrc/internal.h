@@ -53,6 +53,11 @@ struct WfsDesc {                    // static per wavefront sensor
     // valid subapertures of one subaperture row, {sy, first valid index, count, sx of first}
     const int4 *segs;
     int n_segs, tiled, seg_cols;    // seg_cols: largest run width in pupil columns
+    // LGS uplink tip-tilt (null: off): the kernel k_uplink writes the spot's deflection times
+    // the pupil pitch (OPD per pupil pixel, x and y) here before the projection adds it
+    float2 *uplink;
+    double launch_x, launch_y, up_diam;
+    int up_n;
 };
 
 struct InstDyn {                    // per call, per instance
@@ -180,7 +185,9 @@ struct LaunchShape {
 };
 
 // Launchers (return the cudaGetLastError() of the launch).
-cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s);
+// after_uplink: the launch follows the uplink kernel on s as a programmatic dependent launch
+// (the projection waits for it before adding the uplink tilt).
+cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s, bool after_uplink = false);
 cudaError_t project_launch_shape(const ProjArgs &a, int total_blocks, LaunchShape *out);
 // CTAs the projection needs for one WFS.
 int project_blocks(const WfsDesc &d);
@@ -218,6 +225,10 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
                     std::vector<uint8_t> &B2l);
 // Bounded mbarrier wait that is never satisfied; writes WFS_ETIMEOUT to *status.
 cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
+// LGS uplink tip-tilt of every WFS of the table that has it on: one CTA per (WFS, turbulent
+// layer); part [n_wfs][kMaxLayers] scratch, count [n_wfs] zero between launches.
+cudaError_t launch_uplink(const InstDesc *inst, const WfsDesc *wfs, int n_wfs, int max_layers, float2 *part,
+                          int *count, const InstDyn *dyn0, cudaStream_t s);
 // Closed-loop kernels.
 cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s);
 cudaError_t gemv_launch_shape(const GemvArgs &a, LaunchShape *out);

@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
                     const float bot = fmaf(fx, s11 - s10, s10);
                     acc += fmaf(gy, bot - top, top);
                 }
+                if (W.uplink) acc += fmaf(W.uplink->x, xr, W.uplink->y * yr);
                 so[i] = acc;
                 out[i] = acc;
             }

@@ -129,6 +129,7 @@ _SIGS = {
     "wfs_loop_get_layer": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_void_p]),
     "wfs_loop_destroy": (C.c_int, [_H]),
     "wfs_loop_calibrate": (C.c_int, [_H, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
+    "wfs_set_uplink": (C.c_int, [_H, C.c_int, C.c_double, C.c_int]),
 }
 
 
@@ -340,6 +341,10 @@ def wfs_loop_calibrate(lp, h, gs, amplitude, im_ptr, stream=0):
     _check(lib().wfs_loop_calibrate(lp, int(gs), float(amplitude), im_ptr, stream), h)
 
 
+def wfs_set_uplink(h, gs, diameter_m, samples=16):
+    _check(lib().wfs_set_uplink(h, int(gs), float(diameter_m), int(samples)), h)
+
+
 def wfs_loop_destroy(lp):
     _check(lib().wfs_loop_destroy(lp))
 
@@ -384,6 +389,9 @@ class Wfs:
         self.cfg = cfg
         self.h = wfs_create(tel, stars, geoms, lay, seed, noise)
         self.n_gs = len(cfg.stars)
+        for k, st in enumerate(cfg.stars):
+            if st.is_lgs and getattr(st, "uplink_diameter_m", 0.0) > 0:
+                wfs_set_uplink(self.h, k, st.uplink_diameter_m, st.uplink_samples)
         self.total = wfs_total_valid(self.h)
         self.layouts = [wfs_layout(self.h, w) for w in range(self.n_gs)]
 
