@@ -54,7 +54,7 @@ class _Star(C.Structure):
                 ("launch_y", C.c_double), ("spot_fwhm_rad", C.c_double), ("photons", C.c_double),
                 ("read_noise", C.c_double), ("n_na", C.c_int),
                 ("na_alt", C.POINTER(C.c_double)), ("na_weight", C.POINTER(C.c_double)),
-                ("up_diameter", C.c_double), ("up_samples", C.c_int)]
+                ("up_diameter", C.c_double), ("up_samples", C.c_int), ("slices", C.c_int)]
 
 
 class _Layers(C.Structure):
@@ -145,6 +145,7 @@ def _star(gs, keep):
     s.na_weight = keep.d(gs.na_weight if len(gs.na_weight) else [0.0])
     s.up_diameter = float(getattr(gs, "uplink_diameter_m", 0.0)) if gs.is_lgs else 0.0
     s.up_samples = int(getattr(gs, "uplink_samples", 0))
+    s.slices = int(bool(getattr(gs, "per_slice", False))) if gs.is_lgs else 0
     return s
 
 

@@ -510,26 +510,55 @@ int orc_measure_wfs(const orc_wfs_geom *g, const orc_star *gs, int wfs_index,
         double *yr = malloc(sizeof(double) * N * N), *yi = malloc(sizeof(double) * N * N);
         double *I = malloc(sizeof(double) * N * N), *Ie = malloc(sizeof(double) * N * N);
         double *B = malloc(sizeof(double) * nd * nd), *C = malloc(sizeof(double) * nd * nd);
-        /* field of the subaperture: a exp(i 2 pi OPD / lambda) */
-        for (int p = 0; p < n; ++p)
-            for (int q = 0; q < n; ++q) {
-                int i = sy * n + p, j = sx * n + q;
-                double x = (j - (Np - 1) / 2.0) * dx, y = (i - (Np - 1) / 2.0) * dx;
-                double o = orc_opd(L, screens, gs, x, y, t) + (upx * x + upy * y);
-                if (opd_out) opd_out[(size_t)s * n * n + p * n + q] = o;
-                if (lit(g->diameter_m, g->obstruction, Np, i, j)) {
-                    double phi = 2.0 * M_PI * o / gs->wavelength_m;
-                    xr[p * n + q] = cos(phi);
-                    xi[p * n + q] = sin(phi);
-                }
+        const int per_slice = gs->is_lgs && gs->slices;
+        const int ns = per_slice ? gs->n_na : 1;
+        for (int k = 0; k < N * N; ++k) I[k] = 0.0;
+        for (int sl = 0; sl < ns; ++sl) {
+            /* the slice's source: the star's range replaced by the slice altitude (cone), and
+               its geometric term relative to the focus at the star's range */
+            orc_star src = *gs;
+            double kgeo = 0.0, wsl = 1.0;
+            if (per_slice) {
+                src.range_m = gs->na_alt[sl];
+                kgeo = 1.0 / gs->range_m - 1.0 / gs->na_alt[sl];
+                wsl = gs->na_weight[sl];
             }
-        orc_dft2(n, N, xr, xi, yr, yi);
-        for (int k = 0; k < N * N; ++k) I[k] = yr[k] * yr[k] + yi[k] * yi[k];
+            /* field of the subaperture: a exp(i 2 pi OPD / lambda) */
+            for (int p = 0; p < n; ++p)
+                for (int q = 0; q < n; ++q) {
+                    int i = sy * n + p, j = sx * n + q;
+                    double x = (j - (Np - 1) / 2.0) * dx, y = (i - (Np - 1) / 2.0) * dx;
+                    double o = orc_opd(L, screens, &src, x, y, t) + (upx * x + upy * y);
+                    if (opd_out && sl == 0) opd_out[(size_t)s * n * n + p * n + q] = o;
+                    if (per_slice) {
+                        double ex = x - gs->launch_x, ey = y - gs->launch_y;
+                        o += 0.5 * (ex * ex + ey * ey) * kgeo;
+                    }
+                    if (lit(g->diameter_m, g->obstruction, Np, i, j)) {
+                        double phi = 2.0 * M_PI * o / gs->wavelength_m;
+                        xr[p * n + q] = cos(phi);
+                        xi[p * n + q] = sin(phi);
+                    }
+                }
+            orc_dft2(n, N, xr, xi, yr, yi);
+            /* the slice's spot weighted by the sodium profile, piled up */
+            for (int k = 0; k < N * N; ++k) I[k] += wsl * (yr[k] * yr[k] + yi[k] * yi[k]);
+        }
         if (gs->is_lgs) {
             double *K = malloc(sizeof(double) * N * N);
             double rbx = ((sx + 0.5) * n) * dx - g->diameter_m / 2.0;
             double rby = ((sy + 0.5) * n) * dx - g->diameter_m / 2.0;
-            orc_elong_kernel(N, pix_rad, rbx, rby, gs, K);
+            if (per_slice) {
+                /* the slices' offsets are in their wavefronts: the Gaussian extent alone */
+                orc_star one = *gs;
+                double h0 = gs->range_m, w1 = 1.0;
+                one.n_na = 1;
+                one.na_alt = &h0;
+                one.na_weight = &w1;
+                orc_elong_kernel(N, pix_rad, rbx, rby, &one, K);
+            } else {
+                orc_elong_kernel(N, pix_rad, rbx, rby, gs, K);
+            }
             orc_convolve(N, I, K, Ie);
             free(K);
         } else {

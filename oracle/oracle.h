@@ -38,6 +38,8 @@ typedef struct {
     const double *na_alt, *na_weight;
     double up_diameter;               /* LGS uplink beam diameter (m); 0 = no uplink tip-tilt */
     int up_samples;                   /* samples across the uplink beam */
+    int slices;                       /* LGS model: 0 = one projection and the elongation kernel,
+                                         1 = one wavefront and one DFT per sodium slice */
 } orc_star;
 
 typedef struct {
@@ -92,6 +94,17 @@ void orc_noise_image(int n, const float *E, float read_noise, uint64_t seed, uin
 void orc_cog(int nd, const double *C, double *sx, double *sy);
 
 /*
+ * LGS per-slice model (Sec. 4 "Open Loop generation": one projection of the beam per sodium
+ * sub-layer, each with the pupil projection of its altitude; "LGS Shack Hartmann wavefront
+ * sensor": per sub-layer the proper tip-tilt and defocus, the spot weighted by the sodium
+ * profile, a Gaussian for the spot's physical extent, the sub-layer images piled up).  Slice s
+ * at altitude h_s with weight w_s: OPD_s(x) = the layers projected with the cone 1 - h_l / h_s,
+ * plus the uplink tilt, plus the slice's geometric term 1/2 |x - r_L|^2 (1/h0 - 1/h_s) (its
+ * tip-tilt (r_b - r_L)(1/h0 - 1/h_s) at subaperture centre r_b, the elongation, and its
+ * in-subaperture defocus), h0 = the star's range (the WFS focus); I = sum_s w_s |DFT(X_s)|^2,
+ * then the Gaussian alone (the elongation kernel of one slice at h0).  The OPD stage output is
+ * the first slice's OPD without its geometric term.
+ *
  * One wavefront sensor, one time t.  sel lists indices into the valid-subap
  * list (NULL = all); every output is per selected subap and may be NULL
  * except slopes:  slopes[n_sel][2], opd[n_sel][n*n], I[n_sel][N*N],

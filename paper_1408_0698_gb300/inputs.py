@@ -67,6 +67,7 @@ class GuideStar:
     na_weight: np.ndarray = field(default_factory=lambda: np.zeros(0))
     uplink_diameter_m: float = 0.0   # LGS launch beam diameter; 0 = no uplink tip-tilt
     uplink_samples: int = 16         # samples across the launch beam
+    per_slice: bool = False          # LGS: one wavefront and DFT per sodium slice
 
 
 @dataclass

@@ -689,3 +689,73 @@ def test_uplink_tilt_equals_a_ground_tilt_layer():
     s_ref = oracle.measure(cfg2, scr2, 0.0)
     np.testing.assert_allclose(s_up, s_ref, rtol=0, atol=1e-6)
     assert np.abs(s_up - oracle.measure(cfg_off, scr, 0.0)).max() > 1e-3
+
+
+# ---------------------------------------------------------------- LGS per-slice model
+
+def _slice_cfg(alts_layers, S=256, dx=0.05, seed=9):
+    """4 m telescope, 10 x 10 subapertures of 8 px (N = 16), one LGS 5 m launch, 3 slices."""
+    tel = inputs.Telescope(4.0, 0.0)
+    geom = [inputs.Geometry(10, 8, 16, 8, 0.5, inputs.PREC_FP32)]
+    h, w = inputs.sodium_slices(90e3, 10e3, 3)
+    star = inputs._lgs(15 * inputs.ARCSEC, -10 * inputs.ARCSEC, 0.6, 0, fwhm=1.0 * inputs.ARCSEC, na=(h, w))
+    n = len(alts_layers)
+    lay = inputs.Layers(alt_m=np.array(alts_layers, float), wind_vx_mps=np.full(n, 4.0), wind_vy_mps=np.zeros(n),
+                        x0_m=np.zeros(n), y0_m=np.zeros(n), screen_size=S, screen_dx_m=dx,
+                        weights=np.full(n, 1.0 / n))
+    return inputs.Config("slices", tel, geom, [star], lay, seed=seed)
+
+
+def test_per_slice_single_slice_at_focus_is_the_kernel_model():
+    cfg = _slice_cfg([0.0, 7000.0])
+    scr = inputs.make_screens(cfg.layers, 2)
+    st = cfg.stars[0]
+    one = dataclasses.replace(st, na_alt_m=np.array([st.range_m]), na_weight=np.array([1.0]))
+    a = oracle.measure_wfs(dataclasses.replace(cfg, stars=[one]), scr, 0, 0.01, stages=True)
+    b = oracle.measure_wfs(dataclasses.replace(cfg, stars=[dataclasses.replace(one, per_slice=True)]), scr, 0, 0.01,
+                           stages=True)
+    for k in ("slopes", "I", "Ie", "E"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_per_slice_slice_equals_cone_plus_geometric_screen():
+    """One slice at h_s: the layers seen with the cone 1 - h/h_s and the slice's geometric
+    term 1/2 |x - r_L|^2 (1/h0 - 1/h_s).  Built independently: a star at range h_s (cone, no
+    offset) plus a ground screen holding that quadratic (bilinear at pixel centres adds only a
+    constant) gives the same spot to FP32 rounding of the screen."""
+    cfg = _slice_cfg([5000.0])
+    scr = inputs.make_screens(cfg.layers, 4)
+    st = cfg.stars[0]
+    hs, h0 = 84e3, st.range_m
+    sl = dataclasses.replace(st, na_alt_m=np.array([hs]), na_weight=np.array([1.0]), per_slice=True)
+    a = oracle.measure_wfs(dataclasses.replace(cfg, stars=[sl]), scr, 0, 0.0, stages=True)
+    ref_star = dataclasses.replace(st, range_m=hs, na_alt_m=np.array([hs]), na_weight=np.array([1.0]))
+    S, ds = cfg.layers.screen_size, cfg.layers.screen_dx_m
+    j = (np.arange(S) - S / 2) * ds
+    X, Y = np.meshgrid(j, j)
+    quad = 0.5 * ((X - st.launch_x_m) ** 2 + (Y - st.launch_y_m) ** 2) * (1 / h0 - 1 / hs)
+    cfg2, scr2 = oracle.with_dm_layers(dataclasses.replace(cfg, stars=[ref_star]), scr,
+                                       [inputs.Dm(3, 1.0, 0.0, 1)], [quad.astype(np.float32)])
+    # the spot's physical extent is an angle: the Gaussian is the same for both stars
+    b = oracle.measure_wfs(cfg2, scr2, 0, 0.0, stages=True)
+    rel = np.abs(a["Ie"] - b["Ie"]).max() / np.abs(b["Ie"]).max()
+    assert rel < 1e-5, rel
+    np.testing.assert_allclose(a["slopes"], b["slopes"], atol=1e-5)
+    # the quadratic moves the spot: without it the slopes differ
+    c = oracle.measure_wfs(dataclasses.replace(cfg, stars=[ref_star]), scr, 0, 0.0)
+    assert np.abs(c["slopes"] - a["slopes"]).max() > 0.05
+
+
+def test_per_slice_pile_up_is_linear_in_the_profile():
+    cfg = _slice_cfg([0.0, 7000.0])
+    scr = inputs.make_screens(cfg.layers, 6)
+    st = dataclasses.replace(cfg.stars[0], per_slice=True)
+    wa = np.array([0.2, 0.0, 0.5])
+    wb = np.array([0.0, 0.7, 0.1])
+    Ie = lambda w: oracle.measure_wfs(dataclasses.replace(cfg, stars=[dataclasses.replace(st, na_weight=w)]),
+                                      scr, 0, 0.0, stages=True)["Ie"]
+    np.testing.assert_allclose(Ie(wa + wb), Ie(wa) + Ie(wb), rtol=0, atol=1e-12 * np.abs(Ie(wa + wb)).max())
+    # and close to the elongation-kernel model (same slices, one projection)
+    s_slice = oracle.measure_wfs(dataclasses.replace(cfg, stars=[st]), scr, 0, 0.0)["slopes"]
+    s_kern = oracle.measure_wfs(cfg, scr, 0, 0.0)["slopes"]
+    assert np.sqrt(np.mean((s_slice - s_kern) ** 2)) < 0.02
