@@ -613,6 +613,31 @@ def main():
     line["uplink_path"] = {"value": spots * k3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3 / k3, "steps": k3,
                            "uplink": "6 LGS, 0.4 m launch beam, 24 x 24 samples",
                            "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt3.items()}}
+    # the same frame with the paper's per-slice LGS model (8 wavefronts and 8 DFTs per LGS
+    # subaperture, FP32 generic kernel)
+    w4 = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
+    native.wfs_set_lgs_model(w4.h, 1)
+    k4 = min(args.steps, 100)
+    for k in range(3):
+        native.wfs_measure(w4.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
+    native.wfs_timing_enable(w4.h, True)
+    native.wfs_timing_read(w4.h)
+    torch.cuda.synchronize()
+    for k in range(k4):
+        if args.flush_mb:
+            flush.fill_(float(k))
+        ev0[k].record(stream)
+        native.wfs_measure(w4.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    ms4 = sum(a.elapsed_time(b) for a, b in zip(ev0[:k4], ev1[:k4]))
+    kt4 = native.wfs_timing_read(w4.h)
+    native.wfs_sync_status(w4.h)
+    w4.close()
+    n_sl = len(cfg.stars[0].na_alt_m)
+    line["per_slice_path"] = {"value": spots * k4 / (ms4 / 1e3), "unit": UNIT, "ms_per_step": ms4 / k4, "steps": k4,
+                              "model": f"per-slice LGS, {n_sl} slices (one wavefront and DFT each), FP32",
+                              "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt4.items()}}
     if not args.no_loop:
         line["closed_loop"] = closed_loop(cfg, s_d, flush, args, dev, rank)
         line["calibration"] = calibration(cfg, args, dev, rank)

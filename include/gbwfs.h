@@ -462,6 +462,31 @@ wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_o
  */
 wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples);
 
+/*
+ * wfs_set_lgs_model -- how the handle's laser guide stars form their spots.
+ * 0 (default): one projection with the cone to the star's range and the
+ * sodium elongation as a convolution kernel (sum over slices of the profile
+ * weight times the Gaussian extent shifted by the slice's offset), on the
+ * geometry's spot kernel.  1: the paper's per-slice model (Sec. 4 "Open Loop
+ * generation": one projection of the beam per sodium sub-layer, each with the
+ * pupil projection of its altitude; "LGS Shack Hartmann wavefront sensor": for
+ * each sub-layer its tip-tilt and defocus, the spot multiplied by the sodium
+ * profile, a Gaussian for the physical extent, the sub-layer images piled up):
+ * for slice s at altitude h_s, OPD_s = the layers seen with the cone
+ * 1 - h_l / h_s (mirror layers included) plus the uplink tilt plus
+ * 1/2 |x - r_L|^2 (1/h0 - 1/h_s) (h0 = the star's range, the focus; r_L the
+ * launch point), one DFT per slice, I = sum_s w_s |DFT|^2, then the Gaussian
+ * extent alone, binning, photometry, noise and centroid as in model 0.  It
+ * runs on the self-projecting FP32 generic kernel (one DFT per slice: n_na
+ * times the DFT work), whatever the geometry's precision; the OPD stage output
+ * holds the first slice's OPD without its geometric term.  Waits for the
+ * handle's measurement in flight and updates its work tables (the first switch
+ * to 1 also builds the Gaussian tables, synchronously).  Batches and
+ * wfs_loop_calibrate do not support model 1 (WFS_EUNSUPPORTED).  WFS_EINVAL:
+ * model not 0 or 1.
+ */
+wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice);
+
 /* Library version string. */
 const char *wfs_version(void);
 

@@ -44,6 +44,10 @@ struct SpotGroup {
     int kind = 0;            // SpotKind
     int grid_cap = 0, cta_warps = 0;
     int proj_base = 0, proj_count = 0;  // this group's projection blocks
+    // LGS per-slice model: the group runs the self-projecting generic kernel; the kind and
+    // launch shape of the elongation-kernel model are kept to restore it
+    bool per_slice = false;
+    int base_kind = 0, base_grid_cap = 0, base_cta_warps = 0;
 };
 
 int spot_kind(const wfs_geometry &g) {
@@ -61,6 +65,7 @@ struct GsDev {
     uint32_t *d_mask = nullptr;
     float *d_fill = nullptr;
     float2 *d_ktil = nullptr;
+    float2 *d_ktil_g = nullptr;  // per-slice model: the Gaussian extent alone
     int4 *d_segs = nullptr;
     int n_segs = 0, seg_cols = 0, tiled = 0;
     double up_diam = 0.0;   // LGS uplink beam diameter (0: off)
@@ -115,9 +120,11 @@ struct wfs_ctx {
     bool ev_overflow = false;
     wfs_loop_ctx *loop = nullptr;     // attached closed loop (at most one)
     float2 *d_uplink = nullptr;       // per guide star: uplink tilt per pupil pixel (x, y)
-    float2 *d_uplink_part = nullptr;  // per (WFS, layer) deflection
+    double2 *d_uplink_part = nullptr; // per (WFS, layer) deflection
     int *d_uplink_count = nullptr;    // per WFS: layers done (zero between launches)
     int n_uplink = 0;                 // guide stars with the uplink tip-tilt on
+    bool per_slice = false;           // LGS per-slice model on
+    SliceDesc *d_slices = nullptr;    // per guide star (LGS entries used)
     cudaEvent_t ev_uplink = nullptr;  // after the uplink kernel: side groups with the uplink wait on it
 };
 
@@ -315,6 +322,8 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 
 void release(wfs_ctx *h) {
     cudaFree(h->d_uplink);
+    cudaFree(h->d_slices);
+    h->d_slices = nullptr;
     cudaFree(h->d_uplink_part);
     cudaFree(h->d_uplink_count);
     if (h->ev_uplink) cudaEventDestroy(h->ev_uplink);
@@ -332,6 +341,7 @@ void release(wfs_ctx *h) {
         cudaFree(s.d_mask);
         cudaFree(s.d_fill);
         cudaFree(s.d_ktil);
+        cudaFree(s.d_ktil_g);
         cudaFree(s.d_segs);
     }
     cudaFree(h->d_opd);
@@ -498,7 +508,9 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     for (size_t j = 1; j < h->groups.size(); ++j)
         if (h->groups[j].total > h->groups[big].total) big = j;
     static thread_local ShArgs sa;
-    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project, bool fused) -> cudaError_t {
+    // project_mode: 0 = a projection launch precedes, 1 = self-projecting on a side stream,
+    // 2 = self-projecting on the caller's stream
+    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project, int project_mode) -> cudaError_t {
         memset(&sa, 0, offsetof(ShArgs, dyn));
         fill_geom_args(sa, h->geoms[G.geom]);
         sa.inst = h->d_inst;
@@ -510,7 +522,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.cta_warps = G.cta_warps;
         sa.n_inst = 1;
         sa.work = h->d_work + 2 * (&G - h->groups.data());
-        sa.project = fused ? 1 : 0;
+        sa.project = project_mode;
         sa.split_noise = splits_noise(G.kind) ? 1 : 0;
         sa.dyn[0] = dyn;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
@@ -550,23 +562,56 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         // launch that starts with the call and owns its SMs only while it runs
         const bool fused = G.kind == kSpotGeneric;
         if (!fused && (e = project(G, ss)) != cudaSuccess) return cuda_fail(h, e, "projection launch");
-        if ((e = launch_group(G, ss, !fused && G.proj_count > 0, fused)) != cudaSuccess)
+        if ((e = launch_group(G, ss, !fused && G.proj_count > 0, fused ? 1 : 0)) != cudaSuccess)
             return cuda_fail(h, e, "spot launch");
         if ((e = cudaEventRecord(h->ev_join[k], ss)) != cudaSuccess) return cuda_fail(h, e, "join");
         ++k;
     }
     if (!h->groups.empty()) {
         const SpotGroup &G = h->groups[big];
-        // with a single group this projects every WFS (blocks 0 .. proj_blocks)
-        if ((e = project(G, stream)) != cudaSuccess)
-            return cuda_fail(h, e, "projection launch");
-        if (G.total > 0 && (e = launch_group(G, stream, G.proj_count > 0, false)) != cudaSuccess)
-            return cuda_fail(h, e, "spot launch");
+        if (G.per_slice) {
+            // the per-slice model projects one wavefront per sodium slice inside the spot kernel
+            if (G.total > 0 && (e = launch_group(G, stream, false, 2)) != cudaSuccess)
+                return cuda_fail(h, e, "spot launch");
+        } else {
+            // with a single group this projects every WFS (blocks 0 .. proj_blocks)
+            if ((e = project(G, stream)) != cudaSuccess)
+                return cuda_fail(h, e, "projection launch");
+            if (G.total > 0 && (e = launch_group(G, stream, G.proj_count > 0, 0)) != cudaSuccess)
+                return cuda_fail(h, e, "spot launch");
+        }
     }
     for (size_t j = 0; j < k; ++j)
         if ((e = cudaStreamWaitEvent(stream, h->ev_join[j], 0)) != cudaSuccess) return cuda_fail(h, e, "join wait");
     if ((e = cudaEventRecord(h->ev_measured, stream)) != cudaSuccess) return cuda_fail(h, e, "completion event");
     return WFS_OK;
+}
+
+// Slice tables of every LGS (weights, curvatures, per-layer cones including any mirror layers),
+// uploaded to h->d_slices.
+wfs_status refresh_slices(wfs_handle h) {
+    if (!h->per_slice) return WFS_OK;
+    std::vector<SliceDesc> sd(h->gs.size());
+    memset(sd.data(), 0, sizeof(SliceDesc) * sd.size());
+    for (size_t g = 0; g < h->gs.size(); ++g) {
+        const GsDev &G = h->gs[g];
+        if (!G.gs.is_lgs) continue;
+        const wfs_geometry &geo = h->geoms[G.gs.geometry_index].g;
+        const double r = (h->tel.diameter_m / (geo.n_sub * geo.n_pix_sub)) / h->ds;
+        SliceDesc &d = sd[g];
+        d.n = (int)G.na_alt.size();
+        for (int s = 0; s < d.n; ++s) {
+            d.w[s] = (float)G.na_w[s];
+            d.k[s] = (float)(1.0 / G.gs.range_m - 1.0 / G.na_alt[s]);
+            for (int l = 0; l < kMaxProjLayers; ++l) {
+                const double c = (1.0 - h->inst_host.alt[l] / G.na_alt[s]) * r;
+                d.c[s][l].x = (float)c;
+                d.c[s][l].y = (float)(c - (double)d.c[s][l].x);
+            }
+        }
+    }
+    cudaError_t e = cudaMemcpy(h->d_slices, sd.data(), sizeof(SliceDesc) * sd.size(), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? WFS_OK : cuda_fail(h, e, "slice tables");
 }
 
 // Actuator commands (modal base times the mirror's coefficients) and correction layer of every
@@ -1361,6 +1406,8 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
             if (hs[j] == hs[i]) return fail(nullptr, WFS_EINVAL, "a handle appears twice in the batch");
         if (hs[i]->n_uplink > 0)
             return fail(nullptr, WFS_EUNSUPPORTED, "batch: a handle has the uplink tip-tilt on (not batched)");
+        if (hs[i]->per_slice)
+            return fail(nullptr, WFS_EUNSUPPORTED, "batch: a handle has the LGS per-slice model on (not batched)");
     }
     wfs_batch b = new wfs_batch_ctx();
     b->hs.assign(hs, hs + n);
@@ -1756,6 +1803,10 @@ wfs_status wfs_loop_create(wfs_handle h, int n_dm, const wfs_dm *dms, const floa
     }
     if ((e = cudaMemcpy(h->d_inst, &h->inst_host, sizeof(InstDesc), cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e, "layer table");
+    if (refresh_slices(h) != WFS_OK) {
+        loop_free(lp);
+        return WFS_ECUDA;
+    }
     h->loop = lp;
     *out = lp;
     return WFS_OK;
@@ -1829,6 +1880,7 @@ wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_o
     if (!im_out) return fail(h, WFS_EINVAL, "null output");
     const cudaStream_t s = (cudaStream_t)stream;
     if (loop_busy(lp, s)) return fail(h, WFS_EBUSY, "loop busy on another stream");
+    if (h->per_slice) return fail(h, WFS_EUNSUPPORTED, "calibration with the LGS per-slice model is not built");
     wfs_status st = calib_prepare(lp, gs);
     if (st != WFS_OK) return st;
     lp->last_stream = s;
@@ -1932,7 +1984,7 @@ wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples) 
         const size_t nw = h->wfs_host.size();
         if ((e = cudaMalloc(&h->d_uplink, sizeof(float2) * h->gs.size())) != cudaSuccess ||
             (e = cudaMemset(h->d_uplink, 0, sizeof(float2) * h->gs.size())) != cudaSuccess ||
-            (e = cudaMalloc(&h->d_uplink_part, sizeof(float2) * nw * kMaxLayers)) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_uplink_part, sizeof(double2) * nw * kMaxLayers)) != cudaSuccess ||
             (e = cudaMalloc(&h->d_uplink_count, sizeof(int) * nw)) != cudaSuccess ||
             (e = cudaMemset(h->d_uplink_count, 0, sizeof(int) * nw)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&h->ev_uplink, cudaEventDisableTiming)) != cudaSuccess)
@@ -1951,6 +2003,81 @@ wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples) 
     if (on != (g.up_diam > 0)) h->n_uplink += on ? 1 : -1;
     g.up_diam = on ? diameter_m : 0.0;
     g.up_n = on ? samples : 0;
+    return WFS_OK;
+}
+
+
+wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
+    if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
+    if (per_slice != 0 && per_slice != 1) return fail(h, WFS_EINVAL, "model must be 0 (elongation kernel) or 1 (per slice)");
+    if ((per_slice != 0) == h->per_slice) return WFS_OK;
+    cudaEventSynchronize(h->ev_measured);  // the work tables are read by the measurement in flight
+    cudaError_t e;
+    if (per_slice) {
+        if (!h->d_slices && (e = cudaMalloc(&h->d_slices, sizeof(SliceDesc) * h->gs.size())) != cudaSuccess)
+            return cuda_fail(h, e, "slice tables");
+        // the Gaussian extent alone: the elongation table of one slice at the focus
+        for (size_t g = 0; g < h->gs.size(); ++g) {
+            GsDev &G = h->gs[g];
+            if (!G.gs.is_lgs || G.d_ktil_g || G.n_valid == 0) continue;
+            const wfs_geometry &geo = h->geoms[G.gs.geometry_index].g;
+            const int n = geo.n_pix_sub, Np = geo.n_sub * n;
+            const size_t kt = (size_t)G.n_valid * (2 * n - 1) * n;
+            if ((e = cudaMalloc(&G.d_ktil_g, kt * sizeof(float2))) != cudaSuccess) return cuda_fail(h, e, "Gaussian table");
+            KtilArgs ka;
+            memset(&ka, 0, sizeof ka);
+            ka.subap = G.d_ids;
+            ka.ktil = G.d_ktil_g;
+            ka.n = n;
+            ka.N = geo.n_fft;
+            ka.n_sub = geo.n_sub;
+            ka.n_valid = G.n_valid;
+            ka.n_na = 1;
+            ka.D = h->tel.diameter_m;
+            ka.dx = h->tel.diameter_m / Np;
+            ka.pix_rad = G.gs.wavelength_m / (geo.n_fft * ka.dx);
+            ka.sigma_px = G.gs.spot_fwhm_rad / (2.0 * std::sqrt(2.0 * std::log(2.0))) / ka.pix_rad;
+            ka.launch_x = G.gs.launch_x_m;
+            ka.launch_y = G.gs.launch_y_m;
+            ka.h0 = G.gs.range_m;
+            ka.alt[0] = G.gs.range_m;
+            ka.w[0] = 1.0;
+            if ((e = launch_ktil(ka, 0)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess)
+                return cuda_fail(h, e, "Gaussian table");
+        }
+    }
+    h->per_slice = per_slice != 0;
+    if (per_slice && refresh_slices(h) != WFS_OK) {
+        h->per_slice = false;
+        return WFS_ECUDA;
+    }
+    for (SpotGroup &G : h->groups) {
+        bool lgs = false;
+        for (int q = 0; q < G.count; ++q) lgs |= h->wfs_host[G.first + q].is_lgs != 0;
+        if (!lgs) continue;
+        if (per_slice) {
+            G.base_kind = G.kind;
+            G.base_grid_cap = G.grid_cap;
+            G.base_cta_warps = G.cta_warps;
+            G.kind = kSpotGeneric;
+            G.grid_cap = G.cta_warps = 0;
+        } else {
+            G.kind = G.base_kind;
+            G.grid_cap = G.base_grid_cap;
+            G.cta_warps = G.base_cta_warps;
+        }
+        G.per_slice = per_slice != 0;
+        for (int q = 0; q < G.count; ++q) {
+            WfsDesc &d = h->wfs_host[G.first + q];
+            if (!d.is_lgs) continue;
+            const GsDev &gd = h->gs[d.gs_index];
+            d.slices = per_slice ? h->d_slices + d.gs_index : nullptr;
+            d.ktil = per_slice ? gd.d_ktil_g : gd.d_ktil;
+        }
+    }
+    if ((e = cudaMemcpy(h->d_wfs, h->wfs_host.data(), sizeof(WfsDesc) * h->wfs_host.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(h, e, "work table");
     return WFS_OK;
 }
 

@@ -34,6 +34,15 @@ struct InstDesc {                   // static per instance
     uint64_t seed;
 };
 
+// LGS per-slice model of one WFS (Sec. 4: one projection and one spot per sodium sub-layer):
+// per slice s its profile weight, its geometric curvature 1/h0 - 1/h_s, and per layer l the
+// pupil-to-screen scale (1 - h_l / h_s) dx_pupil / ds as hi + lo.
+struct SliceDesc {
+    int n;
+    float w[kMaxNaSlices], k[kMaxNaSlices];
+    float2 c[kMaxNaSlices][kMaxProjLayers];
+};
+
 struct WfsDesc {                    // static per wavefront sensor
     int inst;                       // index into the launch's instance tables
     int gs_index;                   // guide-star index within its handle (noise counter)
@@ -58,6 +67,9 @@ struct WfsDesc {                    // static per wavefront sensor
     float2 *uplink;
     double launch_x, launch_y, up_diam;
     int up_n;
+    // LGS per-slice model (null: one projection and the elongation kernel); read by the
+    // self-projecting generic spot kernel, whose ktil then holds the Gaussian extent alone
+    const SliceDesc *slices;
 };
 
 struct InstDyn {                    // per call, per instance
@@ -107,7 +119,9 @@ struct ShArgs {
     // static split.
     int *work;
     int project;         // generic kernel: 1 = project each subaperture's OPD from the screens
-                         // itself (no separate projection launch); written to dyn.opd too
+                         // itself (no separate projection launch; written to dyn.opd too) on a
+                         // side stream, with the shared-memory reservation that keeps projection
+                         // CTAs off its SMs; 2 = the same without the reservation
     int split_noise;     // 32-point kernels: 1 = store the expected image (dyn.st_E, required)
                          // and stop; launch_noise_cog completes the measurement
     InstDyn dyn[kMaxInstances];
@@ -227,7 +241,7 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
 cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
 // LGS uplink tip-tilt of every WFS of the table that has it on: one CTA per (WFS, turbulent
 // layer); part [n_wfs][kMaxLayers] scratch, count [n_wfs] zero between launches.
-cudaError_t launch_uplink(const InstDesc *inst, const WfsDesc *wfs, int n_wfs, int max_layers, float2 *part,
+cudaError_t launch_uplink(const InstDesc *inst, const WfsDesc *wfs, int n_wfs, int max_layers, double2 *part,
                           int *count, const InstDyn *dyn0, cudaStream_t s);
 // Closed-loop kernels.
 cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s);

@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant_
 // sum(o v) / sum(o^2).  The last CTA of a WFS to finish adds the layers' parts in layer order
 // (fixed-order sums throughout) and resets the WFS's counter.
 __global__ void __launch_bounds__(256) k_uplink(const InstDesc *__restrict__ inst, const WfsDesc *__restrict__ wfs,
-                                                float2 *part, int *count, const __grid_constant__ InstDyn d0) {
+                                                double2 *part, int *count, const __grid_constant__ InstDyn d0) {
     allow_dependent_grid();  // the projection may start; it waits for this grid before adding the tilt
     const int wi = blockIdx.x, l = blockIdx.y;
     const WfsDesc &W = wfs[wi];
@@ -391,27 +391,26 @@ __global__ void __launch_bounds__(256) k_uplink(const InstDesc *__restrict__ ins
             a3 += red[3][w];
         }
         const double arm = (H - h) / H;
-        part[wi * kMaxLayers + l] =
-            h < H ? make_float2((float)(a0 / a2 * arm), (float)(a1 / a3 * arm)) : make_float2(0.0f, 0.0f);
+        part[wi * kMaxLayers + l] = h < H ? make_double2(a0 / a2 * arm, a1 / a3 * arm) : make_double2(0.0, 0.0);
         __threadfence();
         s_last = atomicAdd(count + wi, 1) == I.n_layers - 1;
     }
     __syncthreads();
     if (s_last && t == 0) {
         __threadfence();
-        float dx = 0.0f, dy = 0.0f;
+        double dx = 0.0, dy = 0.0;
         for (int k = 0; k < I.n_layers; ++k) {
-            const float2 p = __ldcg(part + wi * kMaxLayers + k);
+            const double2 p = __ldcg(part + wi * kMaxLayers + k);
             dx += p.x;
             dy += p.y;
         }
-        const float px = (float)(W.pupil_dx_over_ds * I.ds);  // pupil pitch (m)
-        *W.uplink = make_float2(dx * px, dy * px);
+        const double px = W.pupil_dx_over_ds * I.ds;  // pupil pitch (m)
+        *W.uplink = make_float2((float)(dx * px), (float)(dy * px));
         count[wi] = 0;
     }
 }
 
-cudaError_t launch_uplink(const InstDesc *inst, const WfsDesc *wfs, int n_wfs, int max_layers, float2 *part,
+cudaError_t launch_uplink(const InstDesc *inst, const WfsDesc *wfs, int n_wfs, int max_layers, double2 *part,
                           int *count, const InstDyn *dyn0, cudaStream_t s) {
     if (n_wfs <= 0 || max_layers <= 0) return cudaSuccess;
     k_uplink<<<dim3(n_wfs, max_layers), 256, 0, s>>>(inst, wfs, part, count, *dyn0);

@@ -137,73 +137,102 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
         // field
         const float *opd = D.opd + W.opd_off + (size_t)v * nn;
         float *so = reinterpret_cast<float *>(U);  // a fused projection's OPD (U is written later)
+        // LGS per-slice model (self-projecting launches only): one wavefront and one DFT per
+        // sodium slice, the spots weighted by the profile and summed into I
+        const SliceDesc *SD = (a.project && W.slices) ? W.slices : nullptr;
+        const int n_sl = SD ? SD->n : 1;
+        LayerOffs *lo = reinterpret_cast<LayerOffs *>(red + 4 * (TEAM / 32) + 4);
         if (a.project) {
-            // this subaperture's OPD straight from the screens: the arithmetic of the projection
-            // kernel (layer offsets in FP64, bilinear samples summed over the layers in order)
-            LayerOffs *lo = reinterpret_cast<LayerOffs *>(red + 4 * (TEAM / 32) + 4);
             const InstDesc &I = a.inst[W.inst];
             const int L = proj_layers(I, D);
             for (int l = tid; l < L; l += TEAM) lo[l] = layer_offsets(I, W, D.t, l);
             team_sync<TEAM>(team);
-            const int S = I.S;
-            const bool pow2 = (S & (S - 1)) == 0;
-            const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
-            const float half = 0.5f * (float)(W.n_sub * n - 1);
-            float *out = D.opd + W.opd_off + (size_t)v * nn;
-            for (int i = tid; i < nn; i += TEAM) {
-                const int pp = i / n, qq = i - pp * n;
-                const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
-                float acc = 0.0f;
-                for (int l = 0; l < L; ++l) {
-                    const LayerOffs L0 = lo[l];
-                    int ou, ov, i0, i1, j0, j1;
-                    float fx, gy;
-                    screen_offset(L0.c, L0.cl, L0.fu, xr, ou, fx);
-                    screen_offset(L0.c, L0.cl, L0.fv, yr, ov, gy);
-                    wrap_pair(L0.bu + ou, S, pow2, i0, i1);
-                    wrap_pair(L0.bv + ov, S, pow2, j0, j1);
-                    const float *scr = layer_screen(I, D, l);
-                    const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
-                    const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
-                    const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
-                    const float top = fmaf(fx, s01 - s00, s00);
-                    const float bot = fmaf(fx, s11 - s10, s10);
-                    acc += fmaf(gy, bot - top, top);
+        }
+        for (int sl = 0; sl < n_sl; ++sl) {
+            if (a.project) {
+                // this subaperture's OPD straight from the screens: the arithmetic of the projection
+                // kernel (layer offsets in FP64, bilinear samples summed over the layers in order);
+                // a slice sees the layers through its own cone (the scale), the offsets are shared
+                const InstDesc &I = a.inst[W.inst];
+                const int L = proj_layers(I, D);
+                const int S = I.S;
+                const bool pow2 = (S & (S - 1)) == 0;
+                const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
+                const float half = 0.5f * (float)(W.n_sub * n - 1);
+                float *out = D.opd + W.opd_off + (size_t)v * nn;
+                // the slice's geometric term 1/2 |x - r_L|^2 k_s relative to the subaperture centre r_b:
+                // k_s ((x - r_b).(r_b - r_L) + 1/2 |x - r_b|^2)
+                float ebx = 0.0f, eby = 0.0f, dxp = 0.0f, ks = 0.0f;
+                if (SD) {
+                    dxp = (float)(W.pupil_dx_over_ds * I.ds);
+                    const float c0 = 0.5f * (float)(n - 1);
+                    ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
+                    eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
+                    ks = SD->k[sl];
                 }
-                if (W.uplink) acc += fmaf(W.uplink->x, xr, W.uplink->y * yr);
-                so[i] = acc;
-                out[i] = acc;
+                for (int i = tid; i < nn; i += TEAM) {
+                    const int pp = i / n, qq = i - pp * n;
+                    const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                    float acc = 0.0f;
+                    for (int l = 0; l < L; ++l) {
+                        const LayerOffs L0 = lo[l];
+                        const float ch = SD ? SD->c[sl][l].x : L0.c, cl = SD ? SD->c[sl][l].y : L0.cl;
+                        int ou, ov, i0, i1, j0, j1;
+                        float fx, gy;
+                        screen_offset(ch, cl, L0.fu, xr, ou, fx);
+                        screen_offset(ch, cl, L0.fv, yr, ov, gy);
+                        wrap_pair(L0.bu + ou, S, pow2, i0, i1);
+                        wrap_pair(L0.bv + ov, S, pow2, j0, j1);
+                        const float *scr = layer_screen(I, D, l);
+                        const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
+                        const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+                        const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+                        const float top = fmaf(fx, s01 - s00, s00);
+                        const float bot = fmaf(fx, s11 - s10, s10);
+                        acc += fmaf(gy, bot - top, top);
+                    }
+                    if (W.uplink) acc += fmaf(W.uplink->x, xr, W.uplink->y * yr);
+                    if (sl == 0) out[i] = acc;
+                    if (SD) {
+                        const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
+                        const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
+                        acc += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+                    }
+                    so[i] = acc;
+                }
+                team_sync<TEAM>(team);
+            }
+            const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
+            const float ref = a.project ? so[0] : __ldg(opd);
+            for (int i = tid; i < nn; i += TEAM) {
+                const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
+                float s, c;
+                field_phasor(W.k_phase * ((a.project ? so[i] : __ldg(opd + i)) - ref), s, c);
+                X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+            }
+            team_sync<TEAM>(team);
+            // U = F X : U[k][q] = sum_p F[k][p] X[p][q]
+            for (int o = tid; o < N * n; o += TEAM) {
+                const int k = o / n, q = o - k * n;
+                float2 acc = make_float2(0.0f, 0.0f);
+                for (int p = 0; p < n; ++p) acc = cmac(acc, sF[p * N + k], X[p * n + q]);
+                U[o] = acc;
+            }
+            team_sync<TEAM>(team);
+            // I = |U F^T|^2, or the slices' sum of w_s |U F^T|^2
+            const float wsl = SD ? SD->w[sl] : 1.0f;
+            const bool last = sl == n_sl - 1;
+            for (int o = tid; o < N * N; o += TEAM) {
+                const int k = o / N, m = o - k * N;
+                float2 acc = make_float2(0.0f, 0.0f);
+                for (int q = 0; q < n; ++q) acc = cmac(acc, U[k * n + q], sF[q * N + m]);
+                const float in = fmaf(acc.x, acc.x, acc.y * acc.y);
+                const float tot = SD ? (sl == 0 ? wsl * in : fmaf(wsl, in, I[k * (N + 1) + m])) : in;
+                I[k * (N + 1) + m] = tot;
+                if (st_I && last) st_I[(size_t)v * N * N + o] = tot;
             }
             team_sync<TEAM>(team);
         }
-        const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
-        const float ref = a.project ? so[0] : __ldg(opd);
-        for (int i = tid; i < nn; i += TEAM) {
-            const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
-            float s, c;
-            field_phasor(W.k_phase * ((a.project ? so[i] : __ldg(opd + i)) - ref), s, c);
-            X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
-        }
-        team_sync<TEAM>(team);
-        // U = F X : U[k][q] = sum_p F[k][p] X[p][q]
-        for (int o = tid; o < N * n; o += TEAM) {
-            const int k = o / n, q = o - k * n;
-            float2 acc = make_float2(0.0f, 0.0f);
-            for (int p = 0; p < n; ++p) acc = cmac(acc, sF[p * N + k], X[p * n + q]);
-            U[o] = acc;
-        }
-        team_sync<TEAM>(team);
-        // I = |U F^T|^2
-        for (int o = tid; o < N * N; o += TEAM) {
-            const int k = o / N, m = o - k * N;
-            float2 acc = make_float2(0.0f, 0.0f);
-            for (int q = 0; q < n; ++q) acc = cmac(acc, U[k * n + q], sF[q * N + m]);
-            const float in = fmaf(acc.x, acc.x, acc.y * acc.y);
-            I[k * (N + 1) + m] = in;
-            if (st_I) st_I[(size_t)v * N * N + o] = in;
-        }
-        team_sync<TEAM>(team);
-
         if (W.is_lgs) {
             // Ta[k][dx] = sum_m I[k][m] Ga[dx][m]
             for (int o = tid; o < N * n; o += TEAM) {
@@ -320,7 +349,7 @@ cudaError_t generic_shape(const ShArgs &a, LaunchShape *out) {
     // enough shared memory that no projection CTA (about 74 KB) fits on its SMs: it then runs
     // alone there and finishes early instead of being stretched across the projection, which
     // takes the freed SMs afterwards.
-    if (a.project && smem < kSelfProjectSmem) smem = kSelfProjectSmem;
+    if (a.project == 1 && smem < kSelfProjectSmem) smem = kSelfProjectSmem;
     int blocks = (a.total + teams - 1) / teams;
     const int cap = a.grid_cap > 0 ? a.grid_cap : 152 * 32;
     if (blocks > cap) blocks = cap;

@@ -130,6 +130,7 @@ _SIGS = {
     "wfs_loop_destroy": (C.c_int, [_H]),
     "wfs_loop_calibrate": (C.c_int, [_H, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "wfs_set_uplink": (C.c_int, [_H, C.c_int, C.c_double, C.c_int]),
+    "wfs_set_lgs_model": (C.c_int, [_H, C.c_int]),
 }
 
 
@@ -345,6 +346,10 @@ def wfs_set_uplink(h, gs, diameter_m, samples=16):
     _check(lib().wfs_set_uplink(h, int(gs), float(diameter_m), int(samples)), h)
 
 
+def wfs_set_lgs_model(h, per_slice):
+    _check(lib().wfs_set_lgs_model(h, int(bool(per_slice))), h)
+
+
 def wfs_loop_destroy(lp):
     _check(lib().wfs_loop_destroy(lp))
 
@@ -392,6 +397,11 @@ class Wfs:
         for k, st in enumerate(cfg.stars):
             if st.is_lgs and getattr(st, "uplink_diameter_m", 0.0) > 0:
                 wfs_set_uplink(self.h, k, st.uplink_diameter_m, st.uplink_samples)
+        per_slice = {bool(getattr(st, "per_slice", False)) for st in cfg.stars if st.is_lgs}
+        if len(per_slice) > 1:
+            raise ValueError("the LGS model is per handle: set per_slice on all laser guide stars or none")
+        if per_slice == {True}:
+            wfs_set_lgs_model(self.h, True)
         self.total = wfs_total_valid(self.h)
         self.layouts = [wfs_layout(self.h, w) for w in range(self.n_gs)]
 
