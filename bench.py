@@ -395,6 +395,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-traffic measurement")
     ap.add_argument("--no-loop", action="store_true", help="skip the closed-loop measurement")
+    ap.add_argument("--no-calib", action="store_true", help="skip the push-pull calibration measurement")
+    ap.add_argument("--paths", default="fp32,uplink,slices",
+                    help="comparison paths timed after the headline (comma list of fp32, uplink, slices; 'none')")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (0: none, for profiling runs)")
     args = ap.parse_args()
@@ -563,8 +566,35 @@ def main():
             # the timed steps launch what the timing pass counted, per step
             "gpu_launches": int(round(sum(v[0] for v in ktimes.values()) / kk * args.steps)),
             "roofline": roof, "e2e": e2e, "clocks": clk, "wall_s_timed": wall}
+    paths = set(args.paths.split(","))
     # the other DFT precision, timed the same way on the same inputs (comparison path)
     other = "fp32" if args.precision == "bf16x3" else "bf16x3"
+    if "fp32" in paths:
+        time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
+    if "uplink" in paths:
+        time_uplink(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
+    if "slices" in paths:
+        time_per_slice(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
+    if not args.no_loop:
+        line["closed_loop"] = closed_loop(cfg, s_d, flush, args, dev, rank)
+    if not args.no_calib:
+        line["calibration"] = calibration(cfg, args, dev, rank)
+    if not args.no_served:
+        line["served"] = served()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, scr, 0.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    w.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
+    import torch
+
+    from paper_1408_0698_gb300 import inputs, native
     w2 = native.Wfs(inputs.config3(inputs.PREC_FP32 if other == "fp32" else inputs.PREC_BF16X3),
                     seed=cfg.seed + rank, noise=True)
     k2 = min(args.steps, 300)
@@ -588,7 +618,13 @@ def main():
                              "steps": k2, "dft_precision": other,
                              "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])}
                                          for k, v in kt2.items()}}
-    # the same frame with the LGS uplink tip-tilt on (0.4 m launch beam, 24 x 24 samples)
+
+
+def time_uplink(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
+    """The same frame with the LGS uplink tip-tilt on (0.4 m launch beam, 24 x 24 samples)."""
+    import torch
+
+    from paper_1408_0698_gb300 import native
     w3 = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
     for k, st in enumerate(cfg.stars):
         if st.is_lgs:
@@ -613,8 +649,14 @@ def main():
     line["uplink_path"] = {"value": spots * k3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3 / k3, "steps": k3,
                            "uplink": "6 LGS, 0.4 m launch beam, 24 x 24 samples",
                            "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt3.items()}}
-    # the same frame with the paper's per-slice LGS model (8 wavefronts and 8 DFTs per LGS
-    # subaperture, FP32 generic kernel)
+
+
+def time_per_slice(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
+    """The same frame with the paper's per-slice LGS model (8 wavefronts and 8 DFTs per LGS
+    subaperture, FP32 generic kernel)."""
+    import torch
+
+    from paper_1408_0698_gb300 import native
     w4 = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
     native.wfs_set_lgs_model(w4.h, 1)
     k4 = min(args.steps, 100)
@@ -638,19 +680,6 @@ def main():
     line["per_slice_path"] = {"value": spots * k4 / (ms4 / 1e3), "unit": UNIT, "ms_per_step": ms4 / k4, "steps": k4,
                               "model": f"per-slice LGS, {n_sl} slices (one wavefront and DFT each), FP32",
                               "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt4.items()}}
-    if not args.no_loop:
-        line["closed_loop"] = closed_loop(cfg, s_d, flush, args, dev, rank)
-        line["calibration"] = calibration(cfg, args, dev, rank)
-    if not args.no_served:
-        line["served"] = served()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, scr, 0.0)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    w.close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
 
 
 if __name__ == "__main__":
