@@ -81,7 +81,9 @@ KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "proj_math.cuh", "internal.h"
                   "spot_tc": ["k_sh_tc.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
                   "noise_cog": ["k_noise_cog.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
                   "project": ["k_project.cu", "proj_math.cuh", "internal.h"],
-                  "gemv": ["k_loop.cu", "internal.h"]}
+                  "gemv": ["k_loop.cu", "proj_math.cuh", "internal.h"],
+                  "dm_layer": ["k_loop.cu", "proj_math.cuh", "internal.h"],
+                  "uplink": ["k_uplink.cu", "proj_math.cuh", "internal.h"]}
 
 
 def ncu_traffic(kernel_key):
@@ -306,8 +308,7 @@ def closed_loop(cfg, s_d, flush, args, dev, rank):
     kl = min(args.steps, 300)
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(kl)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(kl)]
-    native.wfs_timing_enable(w.h, True)
-    native.wfs_timing_read(w.h)
+    # steps with no event between kernels, then per-kernel durations from 30 more with events
     for k in range(kl):
         if args.flush_mb:
             flush.fill_(float(k))
@@ -316,6 +317,13 @@ def closed_loop(cfg, s_d, flush, args, dev, rank):
         e1[k].record(stream)
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    native.wfs_timing_enable(w.h, True)
+    native.wfs_timing_read(w.h)
+    for k in range(min(kl, 30)):
+        if args.flush_mb:
+            flush.fill_(float(k))
+        native.wfs_loop_step(lp, w.h, s_d.data_ptr(), (5 + kl + k) * dt, slopes.data_ptr(), sp)
+    torch.cuda.synchronize()
     kt = native.wfs_timing_read(w.h)
     native.wfs_timing_enable(w.h, False)
     native.wfs_sync_status(w.h)
@@ -363,24 +371,28 @@ def calibration(cfg, args, dev, rank):
     native.wfs_loop_calibrate(lp, w.h, 0, 1.0, im.data_ptr(), sp)
     torch.cuda.synchronize()
     reps = 3
-    native.wfs_timing_enable(w.h, True)
-    native.wfs_timing_read(w.h)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
         native.wfs_loop_calibrate(lp, w.h, 0, 1.0, im.data_ptr(), sp)
     e1.record()
     torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3 / reps
+    # per-kernel durations from one more registration with the library's events
+    native.wfs_timing_enable(w.h, True)
+    native.wfs_timing_read(w.h)
+    native.wfs_loop_calibrate(lp, w.h, 0, 1.0, im.data_ptr(), sp)
+    torch.cuda.synchronize()
     native.wfs_sync_status(w.h)
     kt = native.wfs_timing_read(w.h)
-    s = e0.elapsed_time(e1) / 1e3 / reps
+    native.wfs_timing_enable(w.h, False)
     native.wfs_loop_destroy(lp)
     w.close()
     return {"workload": f"ground mirror {dm.n_act}x{dm.n_act} actuators, {dm.n_modes} modes, push-pull with LGS 0 "
                         f"of the ELT frame ({nv} subapertures, BF16x3 spots), no noise",
             "seconds": s, "modes_per_s": dm.n_modes / s, "spots_per_s": 2 * dm.n_modes * nv / s,
             "repetitions": reps, "paper_seconds": 14 * 3600.0,
-            "kernels": {k: {"launches": v[0] // reps, "avg_ms": v[1] / max(1, v[0])} for k, v in kt.items()}}
+            "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt.items()}}
 
 
 def main():
@@ -591,95 +603,75 @@ def main():
     return 0
 
 
-def time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
+def time_frames(w, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, steps, kernel_steps=30):
+    """ms per frame of handle w: `steps` frames with no event between the kernels of a frame
+    (events there stop the programmatic dependent launches from overlapping), then per-kernel
+    durations from `kernel_steps` more frames with the library's events around every launch."""
     import torch
 
+    from paper_1408_0698_gb300 import native
+    for k in range(3):
+        native.wfs_measure(w.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        if args.flush_mb:
+            flush.fill_(float(k))
+        ev0[k].record(stream)
+        native.wfs_measure(w.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0[:steps], ev1[:steps])) / steps
+    native.wfs_timing_enable(w.h, True)
+    native.wfs_timing_read(w.h)
+    for k in range(min(kernel_steps, steps)):
+        if args.flush_mb:
+            flush.fill_(float(k))
+        native.wfs_measure(w.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
+    torch.cuda.synchronize()
+    native.wfs_timing_enable(w.h, False)
+    kt = native.wfs_timing_read(w.h)
+    native.wfs_sync_status(w.h)
+    return ms, {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt.items()}
+
+
+def time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
     from paper_1408_0698_gb300 import inputs, native
     w2 = native.Wfs(inputs.config3(inputs.PREC_FP32 if other == "fp32" else inputs.PREC_BF16X3),
                     seed=cfg.seed + rank, noise=True)
     k2 = min(args.steps, 300)
-    for k in range(3):
-        native.wfs_measure(w2.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
-    native.wfs_timing_enable(w2.h, True)
-    native.wfs_timing_read(w2.h)
-    torch.cuda.synchronize()
-    ms2 = 0.0
-    for k in range(k2):
-        if args.flush_mb:
-            flush.fill_(float(k))
-        ev0[k].record(stream)
-        native.wfs_measure(w2.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
-        ev1[k].record(stream)
-    torch.cuda.synchronize()
-    ms2 = sum(a.elapsed_time(b) for a, b in zip(ev0[:k2], ev1[:k2]))
-    kt2 = native.wfs_timing_read(w2.h)
+    ms, kt = time_frames(w2, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, k2)
     w2.close()
-    line[f"{other}_path"] = {"value": spots * k2 / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2 / k2,
-                             "steps": k2, "dft_precision": other,
-                             "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])}
-                                         for k, v in kt2.items()}}
+    line[f"{other}_path"] = {"value": spots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k2,
+                             "dft_precision": other, "kernels": kt}
 
 
 def time_uplink(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
     """The same frame with the LGS uplink tip-tilt on (0.4 m launch beam, 24 x 24 samples)."""
-    import torch
-
     from paper_1408_0698_gb300 import native
     w3 = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
     for k, st in enumerate(cfg.stars):
         if st.is_lgs:
             native.wfs_set_uplink(w3.h, k, 0.4, 24)
     k3 = min(args.steps, 300)
-    for k in range(3):
-        native.wfs_measure(w3.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
-    native.wfs_timing_enable(w3.h, True)
-    native.wfs_timing_read(w3.h)
-    torch.cuda.synchronize()
-    for k in range(k3):
-        if args.flush_mb:
-            flush.fill_(float(k))
-        ev0[k].record(stream)
-        native.wfs_measure(w3.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
-        ev1[k].record(stream)
-    torch.cuda.synchronize()
-    ms3 = sum(a.elapsed_time(b) for a, b in zip(ev0[:k3], ev1[:k3]))
-    kt3 = native.wfs_timing_read(w3.h)
-    native.wfs_sync_status(w3.h)
+    ms, kt = time_frames(w3, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, k3)
     w3.close()
-    line["uplink_path"] = {"value": spots * k3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3 / k3, "steps": k3,
-                           "uplink": "6 LGS, 0.4 m launch beam, 24 x 24 samples",
-                           "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt3.items()}}
+    line["uplink_path"] = {"value": spots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k3,
+                           "uplink": "6 LGS, 0.4 m launch beam, 24 x 24 samples", "kernels": kt}
 
 
 def time_per_slice(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
     """The same frame with the paper's per-slice LGS model (8 wavefronts and 8 DFTs per LGS
     subaperture, FP32 generic kernel)."""
-    import torch
-
     from paper_1408_0698_gb300 import native
     w4 = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
     native.wfs_set_lgs_model(w4.h, 1)
     k4 = min(args.steps, 100)
-    for k in range(3):
-        native.wfs_measure(w4.h, s_d.data_ptr(), k * dt, slopes.data_ptr(), sp)
-    native.wfs_timing_enable(w4.h, True)
-    native.wfs_timing_read(w4.h)
-    torch.cuda.synchronize()
-    for k in range(k4):
-        if args.flush_mb:
-            flush.fill_(float(k))
-        ev0[k].record(stream)
-        native.wfs_measure(w4.h, s_d.data_ptr(), (args.warmup + k) * dt, slopes.data_ptr(), sp)
-        ev1[k].record(stream)
-    torch.cuda.synchronize()
-    ms4 = sum(a.elapsed_time(b) for a, b in zip(ev0[:k4], ev1[:k4]))
-    kt4 = native.wfs_timing_read(w4.h)
-    native.wfs_sync_status(w4.h)
+    ms, kt = time_frames(w4, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, k4, kernel_steps=10)
     w4.close()
     n_sl = len(cfg.stars[0].na_alt_m)
-    line["per_slice_path"] = {"value": spots * k4 / (ms4 / 1e3), "unit": UNIT, "ms_per_step": ms4 / k4, "steps": k4,
+    line["per_slice_path"] = {"value": spots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k4,
                               "model": f"per-slice LGS, {n_sl} slices (one wavefront and DFT each), FP32",
-                              "kernels": {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt4.items()}}
+                              "kernels": kt}
 
 
 if __name__ == "__main__":
