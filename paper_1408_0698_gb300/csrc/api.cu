@@ -560,7 +560,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
             return cuda_fail(h, e, "uplink wait");
         // a generic-kernel group (a few NGS subapertures) projects inside its spot kernel: one
         // launch that starts with the call and owns its SMs only while it runs
-        const bool fused = G.kind == kSpotGeneric;
+        const bool fused = G.kind == kSpotGeneric || G.per_slice;
         if (!fused && (e = project(G, ss)) != cudaSuccess) return cuda_fail(h, e, "projection launch");
         if ((e = launch_group(G, ss, !fused && G.proj_count > 0, fused ? 1 : 0)) != cudaSuccess)
             return cuda_fail(h, e, "spot launch");
@@ -2059,7 +2059,9 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             G.base_kind = G.kind;
             G.base_grid_cap = G.grid_cap;
             G.base_cta_warps = G.cta_warps;
-            G.kind = kSpotGeneric;
+            // the self-projecting 32-point kernel where the geometry has it, else the generic one
+            const wfs_geometry &geo = h->geoms[G.geom].g;
+            G.kind = sh_n32_supported(geo.n_pix_sub, geo.n_fft, geo.n_det) ? kSpotN32 : kSpotGeneric;
             G.grid_cap = G.cta_warps = 0;
         } else {
             G.kind = G.base_kind;

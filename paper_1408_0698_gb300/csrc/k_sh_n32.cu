@@ -12,8 +12,16 @@
 //   B[iy][ix] = Re sum_dy G[dy][iy] P[dy][ix]         (half-warp partials + one shuffle)
 // then photometry, noise and the centroid with warp reductions.  All sizes are
 // compile-time constants.
+//
+// The self-projecting variant (kFused, launched with ShArgs::project) projects each
+// subaperture's OPD itself and runs the LGS per-slice model (Sec. 4: one wavefront and one
+// spot per sodium sub-layer, piled up with the profile weights): per slice the layers are
+// sampled through the slice's cone, the uplink tilt and the slice's geometric term are added,
+// and w_s |Y|^2 enters the first inverse-transform stage T directly (T is linear in I), so the
+// slices' spots are never stored.
 #include "internal.h"
 #include "noise.cuh"
+#include "proj_math.cuh"
 #include "spot_tail.cuh"
 
 namespace gbwfs {
@@ -25,7 +33,7 @@ __device__ __forceinline__ void cmac2(float2 &acc, const float2 a, const float2 
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-template <int n, int nd>
+template <int n, int nd, bool kFused = false>
 struct N32Layout {
     static constexpr int N = 32, D2 = 2 * n - 1;
     // per-CTA tables (float2 units)
@@ -41,14 +49,16 @@ struct N32Layout {
     static constexpr int wTa = wX + n * n;         // Q: [nd][n]
     static constexpr int wM = wTa + nd * n;        // [dyi][n]
     static constexpr int wI = wM + D2 * n;         // [k][N+1] floats (NGS binning only)
-    static constexpr int warp = wI + (N * (N + 1) + 1) / 2;
+    static constexpr int wOpd = wI + (N * (N + 1) + 1) / 2;  // self-projecting: [p][q] floats
+    static constexpr int wLo = wOpd + (kFused ? (n * n + 1) / 2 : 0);  // layer offsets (LayerOffs)
+    static constexpr int warp = wLo + (kFused ? (kMaxProjLayers * (int)sizeof(LayerOffs) + 7) / 8 : 0);
 };
 
 }  // namespace
 
-template <int n, int nd>
+template <int n, int nd, bool kFused>
 __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArgs a) {
-    using Lay = N32Layout<n, nd>;
+    using Lay = N32Layout<n, nd, kFused>;
     constexpr int N = 32, D2 = Lay::D2;
     constexpr int nd2 = nd * nd;
     static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
@@ -78,6 +88,8 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float2 *Ta = sm2 + Lay::table + wib * Lay::warp + Lay::wTa;
     float2 *Mw = sm2 + Lay::table + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
+    float *opdw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wOpd);
+    LayerOffs *low = reinterpret_cast<LayerOffs *>(sm2 + Lay::table + wib * Lay::warp + Lay::wLo);
 
     // Work split: each warp starts with subaperture blockIdx.x * nw + wib; with a.work, lane 0
     // draws one ticket per iteration (issued at the top, used at the bottom).
@@ -93,50 +105,130 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         const int v = g - W.subap_begin;
         __syncwarp();
 
-        // field, piston-free
+        const SliceDesc *SD = kFused ? W.slices : nullptr;
+        const int n_sl = SD ? SD->n : 1;
         const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
         const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
-        const float ref = __ldg(opd);
-        for (int i = lane; i < n * n; i += 32) {
-            const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
-            float s, c;
-            field_phasor(W.k_phase * (__ldg(opd + i) - ref), s, c);
-            X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+        int L = 0;
+        if (kFused) {
+            // the layer offsets of this subaperture's WFS (FP64; shared by the slices)
+            const InstDesc &I = a.inst[W.inst];
+            L = proj_layers(I, D);
+            for (int l = lane; l < L; l += 32) low[l] = layer_offsets(I, W, D.t, l);
+            __syncwarp();
         }
-        __syncwarp();
-
-        // U[k][q], k = lane
-        float2 U[n];
-#pragma unroll
-        for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
-#pragma unroll
-        for (int p = 0; p < n; ++p) {
-            const float2 f = Fk[p * N + lane];
-#pragma unroll
-            for (int q = 0; q < n; ++q) cmac2(U[q], f, X[p * n + q]);
-        }
-
-        // Y, I and the first inverse-transform stage, row by row
         float2 T[n];
 #pragma unroll
         for (int d = 0; d < n; ++d) T[d] = make_float2(0.0f, 0.0f);
         float *stI = D.st_I ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
-#pragma unroll 2
-        for (int m = 0; m < N; ++m) {
-            float2 y = make_float2(0.0f, 0.0f);
+        for (int sl = 0; sl < n_sl; ++sl) {
+            if (kFused) {
+                // this subaperture's OPD for slice sl: the projection's arithmetic with the slice's
+                // cone (scale), the uplink tilt, and the slice's geometric term about the centre
+                const InstDesc &I = a.inst[W.inst];
+                const int S = I.S;
+                const bool pow2 = (S & (S - 1)) == 0;
+                const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
+                const float half = 0.5f * (float)(W.n_sub * n - 1);
+                float ebx = 0.0f, eby = 0.0f, dxp = 0.0f, ks = 0.0f;
+                if (SD) {
+                    dxp = (float)(W.pupil_dx_over_ds * I.ds);
+                    const float c0 = 0.5f * (float)(n - 1);
+                    ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
+                    eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
+                    ks = SD->k[sl];
+                }
+                float *out = D.opd + W.opd_off + (size_t)v * (n * n);
+                for (int i = lane; i < n * n; i += 32) {
+                    const int pp = i / n, qq = i - pp * n;
+                    const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                    float acc = 0.0f;
+                    for (int l = 0; l < L; ++l) {
+                        const LayerOffs L0 = low[l];
+                        const float ch = SD ? SD->c[sl][l].x : L0.c, cl = SD ? SD->c[sl][l].y : L0.cl;
+                        int ou, ov, i0, i1, j0, j1;
+                        float fx, gy;
+                        screen_offset(ch, cl, L0.fu, xr, ou, fx);
+                        screen_offset(ch, cl, L0.fv, yr, ov, gy);
+                        wrap_pair(L0.bu + ou, S, pow2, i0, i1);
+                        wrap_pair(L0.bv + ov, S, pow2, j0, j1);
+                        const float *scr = layer_screen(I, D, l);
+                        const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
+                        const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+                        const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+                        const float top = fmaf(fx, s01 - s00, s00);
+                        const float bot = fmaf(fx, s11 - s10, s10);
+                        acc += fmaf(gy, bot - top, top);
+                    }
+                    if (W.uplink) acc += fmaf(W.uplink->x, xr, W.uplink->y * yr);
+                    if (sl == 0) out[i] = acc;
+                    if (SD) {
+                        const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
+                        const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
+                        acc += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+                    }
+                    opdw[i] = acc;
+                }
+                __syncwarp();
+            }
+
+            // field, piston-free
+            const float ref = kFused ? opdw[0] : __ldg(opd);
+            for (int i = lane; i < n * n; i += 32) {
+                const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
+                float s, c;
+                field_phasor(W.k_phase * ((kFused ? opdw[i] : __ldg(opd + i)) - ref), s, c);
+                X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+            }
+            __syncwarp();
+
+            // U[k][q], k = lane
+            float2 U[n];
 #pragma unroll
-            for (int q = 0; q < n; ++q) cmac2(y, U[q], Fm[m * n + q]);
-            const float in = fmaf(y.x, y.x, y.y * y.y);
-            if (stI) stI[m] = in;
-            if (W.is_lgs) {
+            for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                const float2 f = Fk[p * N + lane];
+#pragma unroll
+                for (int q = 0; q < n; ++q) cmac2(U[q], f, X[p * n + q]);
+            }
+
+            // Y, I (times the slice's weight) and the first inverse-transform stage, row by row
+            const float wsl = SD ? SD->w[sl] : 1.0f;
+#pragma unroll 2
+            for (int m = 0; m < N; ++m) {
+                float2 y = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int q = 0; q < n; ++q) cmac2(y, U[q], Fm[m * n + q]);
+                const float in = SD ? wsl * fmaf(y.x, y.x, y.y * y.y) : fmaf(y.x, y.x, y.y * y.y);
+                if (stI) stI[m] = sl == 0 ? in : stI[m] + in;
+                if (kFused) {
+                    // the slices' spots summed in the warp's rows; T once after the last slice
+                    float *ir = Iw + lane * (N + 1) + m;
+                    *ir = sl == 0 ? in : *ir + in;
+                } else if (W.is_lgs) {
+#pragma unroll
+                    for (int d = 0; d < n; ++d) {
+                        const float2 ga = Gam[m * n + d];
+                        T[d].x = fmaf(in, ga.x, T[d].x);
+                        T[d].y = fmaf(in, ga.y, T[d].y);
+                    }
+                } else {
+                    Iw[lane * (N + 1) + m] = in;
+                }
+            }
+            __syncwarp();  // X and the slice's OPD are rewritten by the next slice
+        }
+        if (kFused && W.is_lgs) {
+#pragma unroll 2
+            for (int m = 0; m < N; ++m) {
+                const float in = Iw[lane * (N + 1) + m];
 #pragma unroll
                 for (int d = 0; d < n; ++d) {
                     const float2 ga = Gam[m * n + d];
                     T[d].x = fmaf(in, ga.x, T[d].x);
                     T[d].y = fmaf(in, ga.y, T[d].y);
                 }
-            } else {
-                Iw[lane * (N + 1) + m] = in;
             }
         }
 
@@ -165,22 +257,28 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 }
 
 namespace {
-template <int n, int nd>
-cudaError_t shape_n32(const ShArgs &a, LaunchShape *out) {
-    using Lay = N32Layout<n, nd>;
+template <int n, int nd, bool kFused>
+cudaError_t shape_n32_k(const ShArgs &a, LaunchShape *out) {
+    using Lay = N32Layout<n, nd, kFused>;
     const int warps = (a.cta_warps == 4 || a.cta_warps == 8) ? a.cta_warps : 8;
     const size_t smem = (size_t)(Lay::table + warps * Lay::warp) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_sh_n32<n, nd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sh_n32<n, nd, kFused>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (a.total + warps - 1) / warps;
     const int cap = a.grid_cap > 0 ? a.grid_cap : 152 * 2 * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    out->func = (const void *)k_sh_n32<n, nd>;
+    out->func = (const void *)k_sh_n32<n, nd, kFused>;
     out->grid = dim3(blocks);
     out->block = dim3(warps * 32);
     out->smem = smem;
     return cudaSuccess;
+}
+
+// ShArgs::project selects the self-projecting variant (its own layer sampling, per-slice model).
+template <int n, int nd>
+cudaError_t shape_n32(const ShArgs &a, LaunchShape *out) {
+    return a.project ? shape_n32_k<n, nd, true>(a, out) : shape_n32_k<n, nd, false>(a, out);
 }
 }  // namespace
 
