@@ -51,7 +51,8 @@ struct N32Layout {
     static constexpr int wI = wM + D2 * n;         // [k][N+1] floats (NGS binning only)
     static constexpr int wOpd = wI + (N * (N + 1) + 1) / 2;  // self-projecting: [p][q] floats
     static constexpr int wLo = wOpd + (kFused ? (n * n + 1) / 2 : 0);  // layer offsets (LayerOffs)
-    static constexpr int warp = wLo + (kFused ? (kMaxProjLayers * (int)sizeof(LayerOffs) + 7) / 8 : 0);
+    static constexpr int wCt = wLo + (kFused ? (kMaxProjLayers * (int)sizeof(LayerOffs) + 15) / 16 * 2 : 0);
+    static constexpr int warp = wCt + (kFused ? 2 * (2 * n) : 0);  // coordinate table: 2n float4
 };
 
 }  // namespace
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
     float *opdw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wOpd);
     LayerOffs *low = reinterpret_cast<LayerOffs *>(sm2 + Lay::table + wib * Lay::warp + Lay::wLo);
+    float4 *ctab = reinterpret_cast<float4 *>(sm2 + Lay::table + wib * Lay::warp + Lay::wCt);
 
     // Work split: each warp starts with subaperture blockIdx.x * nw + wib; with a.work, lane 0
     // draws one ticket per iteration (issued at the top, used at the bottom).
@@ -139,35 +141,61 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
                     ks = SD->k[sl];
                 }
                 float *out = D.opd + W.opd_off + (size_t)v * (n * n);
-                for (int i = lane; i < n * n; i += 32) {
-                    const int pp = i / n, qq = i - pp * n;
-                    const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
-                    float acc = 0.0f;
-                    for (int l = 0; l < L; ++l) {
-                        const LayerOffs L0 = low[l];
+                // per layer: lanes 0 .. n-1 make the column coordinates (wrapped indices and
+                // fraction), lanes n .. 2n-1 the row coordinates; then every pixel reads its
+                // column's and row's entries
+                constexpr int NPX = (n * n + 31) / 32;
+                float acc[NPX];
+#pragma unroll
+                for (int k = 0; k < NPX; ++k) acc[k] = 0.0f;
+                for (int l = 0; l < L; ++l) {
+                    const LayerOffs L0 = low[l];
+                    if (lane < 2 * n) {
+                        const bool col = lane < n;
                         const float ch = SD ? SD->c[sl][l].x : L0.c, cl = SD ? SD->c[sl][l].y : L0.cl;
-                        int ou, ov, i0, i1, j0, j1;
-                        float fx, gy;
-                        screen_offset(ch, cl, L0.fu, xr, ou, fx);
-                        screen_offset(ch, cl, L0.fv, yr, ov, gy);
-                        wrap_pair(L0.bu + ou, S, pow2, i0, i1);
-                        wrap_pair(L0.bv + ov, S, pow2, j0, j1);
-                        const float *scr = layer_screen(I, D, l);
-                        const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
-                        const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
-                        const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
-                        const float top = fmaf(fx, s01 - s00, s00);
-                        const float bot = fmaf(fx, s11 - s10, s10);
-                        acc += fmaf(gy, bot - top, top);
+                        const float xr = col ? (float)(sx * n + lane) - half : (float)(sy * n + lane - n) - half;
+                        int o, i0, i1;
+                        float f;
+                        screen_offset(ch, cl, col ? L0.fu : L0.fv, xr, o, f);
+                        wrap_pair((col ? L0.bu : L0.bv) + o, S, pow2, i0, i1);
+                        ctab[lane] = make_float4(__int_as_float(i0), __int_as_float(i1), f, 0.0f);
                     }
-                    if (W.uplink) acc += fmaf(W.uplink->x, xr, W.uplink->y * yr);
-                    if (sl == 0) out[i] = acc;
-                    if (SD) {
-                        const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
-                        const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
-                        acc += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+                    __syncwarp();
+                    const float *scr = layer_screen(I, D, l);
+#pragma unroll
+                    for (int k = 0; k < NPX; ++k) {
+                        const int i = lane + 32 * k;
+                        if (i < n * n) {
+                            const int pp = i / n, qq = i - pp * n;
+                            const float4 c = ctab[qq], r = ctab[n + pp];
+                            const float *r0 = scr + (size_t)__float_as_int(r.x) * S;
+                            const float *r1 = scr + (size_t)__float_as_int(r.y) * S;
+                            const int i0 = __float_as_int(c.x), i1 = __float_as_int(c.y);
+                            const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+                            const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+                            const float top = fmaf(c.z, s01 - s00, s00);
+                            const float bot = fmaf(c.z, s11 - s10, s10);
+                            acc[k] += fmaf(r.z, bot - top, top);
+                        }
                     }
-                    opdw[i] = acc;
+                    __syncwarp();  // the coordinates are rewritten for the next layer
+                }
+#pragma unroll
+                for (int k = 0; k < NPX; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i < n * n) {
+                        const int pp = i / n, qq = i - pp * n;
+                        const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                        float o = acc[k];
+                        if (W.uplink) o += fmaf(W.uplink->x, xr, W.uplink->y * yr);
+                        if (sl == 0) out[i] = o;
+                        if (SD) {
+                            const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
+                            const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
+                            o += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+                        }
+                        opdw[i] = o;
+                    }
                 }
                 __syncwarp();
             }
