@@ -2059,9 +2059,11 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             G.base_kind = G.kind;
             G.base_grid_cap = G.grid_cap;
             G.base_cta_warps = G.cta_warps;
-            // the self-projecting 32-point kernel where the geometry has it, else the generic one
+            // the self-projecting variant of the geometry's 32-point kernel (tensor-core or FP32)
+            // where it has one, else the generic kernel
             const wfs_geometry &geo = h->geoms[G.geom].g;
-            G.kind = sh_n32_supported(geo.n_pix_sub, geo.n_fft, geo.n_det) ? kSpotN32 : kSpotGeneric;
+            if (G.kind != kSpotTc)
+                G.kind = sh_n32_supported(geo.n_pix_sub, geo.n_fft, geo.n_det) ? kSpotN32 : kSpotGeneric;
             G.grid_cap = G.cta_warps = 0;
         } else {
             G.kind = G.base_kind;

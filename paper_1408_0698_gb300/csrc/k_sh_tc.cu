@@ -22,6 +22,13 @@
 //
 // CTA = one warpgroup (4 warps); warp w owns subaperture 4g + w of group g and its
 // lane k owns DFT row k, which is also TMEM lane 32 w + k of both accumulators.
+//
+// The self-projecting variant (kFused, launched with ShArgs::project) projects each
+// subaperture's OPD itself and runs the LGS per-slice model (Sec. 4: one wavefront and one
+// spot per sodium sub-layer, piled up with the profile weights): per slice the warp samples the
+// layers through the slice's cone (per-layer coordinate tables), adds the uplink tilt and the
+// slice's geometric term, forms U, and the warpgroup's Y = U F^T runs on the tensor cores; the
+// weighted |Y|^2 of the slices are summed in the warp's shared rows, which then feed Ta = I Ga^T.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -29,6 +36,7 @@
 
 #include "internal.h"
 #include "noise.cuh"
+#include "proj_math.cuh"
 #include "spot_tail.cuh"
 
 namespace gbwfs {
@@ -130,7 +138,7 @@ __device__ __forceinline__ void cmacc(float2 &acc, const float2 a, const float2 
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-template <int n, int nd>
+template <int n, int nd, bool kFused = false>
 struct TcLayout {
     static constexpr int N = 32, D2 = 2 * n - 1;
     // byte offsets; tensor-core tiles first (1024-aligned)
@@ -154,9 +162,18 @@ struct TcLayout {
     // top of a group and read by the elongation stage; it may overlap the NGS rows, which an LGS
     // subaperture never writes (a warp's copies land before its next NGS image)
     static constexpr int wKt = lgs_end;
-    static constexpr int warp = wKt + D2 * n > ngs_end ? wKt + D2 * n : ngs_end;
-    static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;  // per warpgroup: 2 mbarriers, flag
-    static constexpr int bytes = oMisc + 32 * kWG + 16;
+    static constexpr int base_warp = wKt + D2 * n > ngs_end ? wKt + D2 * n : ngs_end;
+    // self-projecting variant: the summed spot rows use the NGS rows (wI; K~ is staged after
+    // them), then the slice's OPD, the layer offsets and the per-layer coordinate table
+    static constexpr int wOpd = base_warp;
+    static constexpr int wLo = wOpd + (kFused ? (n * n + 1) / 2 + ((n * n + 1) / 2) % 2 : 0);
+    static constexpr int wCt = wLo + (kFused ? (kMaxProjLayers * (int)sizeof(LayerOffs) + 15) / 16 * 2 : 0);
+    static constexpr int warp = wCt + (kFused ? 4 * n : 0);
+    // per warpgroup: 2 mbarriers (0), flag (16), next group (20); self-projecting variant: the
+    // slice counts of its 4 warps (32)
+    static constexpr int misc = kFused ? 48 : 32;
+    static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;
+    static constexpr int bytes = oMisc + misc * kWG + 16;
 };
 
 }  // namespace
@@ -415,6 +432,401 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_all), "r"(kTmemCols));
 }
 
+// The self-projecting per-slice variant (see the file comment).
+template <int n, int nd>
+__global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constant__ ShArgs a) {
+    constexpr bool kFused = true;
+    using Lay = TcLayout<n, nd, kFused>;
+    constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
+    static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
+    static_assert(n % 2 == 0 && Lay::wKt % 2 == 0 && Lay::warp % 2 == 0 && Lay::oWarp % 16 == 0,
+                  "16-byte aligned K~ staging");
+    static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sB1 = smem + Lay::oB1, *sB2h = smem + Lay::oB2h, *sB2l = smem + Lay::oB2l;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const int wg = wib >> 2, wq = wib & 3;  // warpgroup, warp within it (= TMEM lane quarter)
+    uint8_t *sA1 = smem + Lay::oA + 16384 * wg, *sA2 = sA1;
+    float2 *tab = reinterpret_cast<float2 *>(smem + Lay::oTab);
+    float2 *Fk = tab + Lay::tFk, *fft = tab + Lay::tFft, *Gt = tab + Lay::tG;
+    float *rk = reinterpret_cast<float *>(tab + Lay::tRk);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + Lay::misc * wg);
+    int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 16);
+    int *snext = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 20);  // next group (dynamic split)
+    int *snsl = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 32);   // slices per warp (kFused)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + Lay::misc * kWG);
+    const uint32_t bar_id = 1 + wg;
+    auto wg_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(128) : "memory"); };
+    // constant operand tiles (pre-swizzled on the host) and CUDA-core tables
+    {
+        const uint4 *src1 = reinterpret_cast<const uint4 *>(a.tc_B1);
+        const uint4 *src2 = reinterpret_cast<const uint4 *>(a.tc_B2h);
+        const uint4 *src3 = reinterpret_cast<const uint4 *>(a.tc_B2l);
+        for (int i = tid; i < 8192 / 16; i += kTcThreads) reinterpret_cast<uint4 *>(sB1)[i] = src1[i];
+        for (int i = tid; i < 4096 / 16; i += kTcThreads) {
+            reinterpret_cast<uint4 *>(sB2h)[i] = src2[i];
+            reinterpret_cast<uint4 *>(sB2l)[i] = src3[i];
+        }
+        for (int i = tid; i < n * N; i += kTcThreads) {
+            const int p = i / N, k = i - p * N;
+            Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
+        }
+        tail::fill_fft_table(fft, tid, kTcThreads);
+        for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
+        fill_recip_table(rk, tid, kTcThreads);
+    }
+    if (wib == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (wq == 0 && lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        *sflag = 0;
+    }
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem_all = *tslot;
+    wait_prior_grid();
+    if (a.split_noise) allow_dependent_grid();  // the noise kernel may take SMs as CTAs retire
+    const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
+    const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
+    constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
+
+    float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
+    float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
+    float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
+    float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
+    float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
+    float *opdw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wOpd);
+    LayerOffs *low = reinterpret_cast<LayerOffs *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wLo);
+    float4 *ctab = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wCt);
+    const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
+    const int groups = (a.total + 3) / 4;
+    const bool issuer = wq == 0 && lane == 0;
+    uint32_t phase = 0, phase0 = 0;  // mbarrier parities: [1] once per group, [0] once per slice
+
+    // Work split: each warpgroup starts with group blockIdx.x * kWG + wg; with a.work the
+    // issuer then draws one ticket per iteration (issued at the top, published before the first
+    // warpgroup barrier, read after it), so CTAs that start late take fewer groups.
+    const int nwg = gridDim.x * kWG;
+    int grp_next = 0;
+    for (int grp = blockIdx.x * kWG + wg; grp < groups; grp = grp_next) {
+        int ticket = 0;
+        if (a.work && issuer) ticket = atomicAdd(a.work, 1);
+        const int g = 4 * grp + wq;
+        const bool active = g < a.total;
+        const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
+        const InstDyn &D = a.dyn[W.inst];
+        const int v = active ? g - W.subap_begin : 0;
+        // K~ of this subaperture: (2n-1) n complex = 16-byte chunks (n even); the self-projecting
+        // variant stages it after its slices, whose summed rows share the space
+        auto stage_ktil = [&]() {
+            const float4 *src = reinterpret_cast<const float4 *>(W.ktil + (size_t)v * (D2 * n));
+            for (int c = lane; c < D2 * n / 2; c += 32) {
+                const uint32_t dst = smem_u32(reinterpret_cast<float4 *>(Kts) + c);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + c) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (!kFused && active && W.is_lgs) stage_ktil();
+
+        // slices: one for the elongation-kernel model; the warpgroup runs the largest count of
+        // its four subapertures (a subaperture with fewer adds nothing in the extra ones)
+        const SliceDesc *SD = (kFused && active) ? W.slices : nullptr;
+        const int my_n = SD ? SD->n : 1;
+        int n_sl = 1, L = 0;
+        if (kFused) {
+            if (lane == 0) snsl[wq] = my_n;
+            if (active) {
+                const InstDesc &I = a.inst[W.inst];
+                L = proj_layers(I, D);
+                for (int l = lane; l < L; l += 32) low[l] = layer_offsets(I, W, D.t, l);
+            }
+            wg_sync();
+            n_sl = max(max(snsl[0], snsl[1]), max(snsl[2], snsl[3]));
+        }
+        bool quit = false;
+        for (int sl = 0; sl < n_sl; ++sl) {
+            // field and U = F X (CUDA cores)
+            float2 U[n];
+#pragma unroll
+            for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
+            if (active && sl < my_n) {
+                if (kFused) {
+                    // the slice's OPD: the projection's arithmetic with the slice's cone, through
+                    // per-layer coordinate tables (lanes 0 .. n-1 columns, n .. 2n-1 rows), plus the
+                    // uplink tilt and the slice's geometric term about the subaperture centre
+                    const InstDesc &I = a.inst[W.inst];
+                    const int S = I.S;
+                    const bool pow2 = (S & (S - 1)) == 0;
+                    const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
+                    const float half = 0.5f * (float)(W.n_sub * n - 1);
+                    constexpr int NPX = (n * n + 31) / 32;
+                    float acc[NPX];
+#pragma unroll
+                    for (int k = 0; k < NPX; ++k) acc[k] = 0.0f;
+                    for (int l = 0; l < L; ++l) {
+                        const LayerOffs L0 = low[l];
+                        if (lane < 2 * n) {
+                            const bool col = lane < n;
+                            const float ch = SD ? SD->c[sl][l].x : L0.c, cl = SD ? SD->c[sl][l].y : L0.cl;
+                            const float xr = col ? (float)(sx * n + lane) - half : (float)(sy * n + lane - n) - half;
+                            int o, i0, i1;
+                            float f;
+                            screen_offset(ch, cl, col ? L0.fu : L0.fv, xr, o, f);
+                            wrap_pair((col ? L0.bu : L0.bv) + o, S, pow2, i0, i1);
+                            ctab[lane] = make_float4(__int_as_float(i0), __int_as_float(i1), f, 0.0f);
+                        }
+                        __syncwarp();
+                        const float *scr = layer_screen(I, D, l);
+#pragma unroll
+                        for (int k = 0; k < NPX; ++k) {
+                            const int i = lane + 32 * k;
+                            if (i < n * n) {
+                                const int pp = i / n, qq = i - pp * n;
+                                const float4 c = ctab[qq], r = ctab[n + pp];
+                                const float *r0 = scr + (size_t)__float_as_int(r.x) * S;
+                                const float *r1 = scr + (size_t)__float_as_int(r.y) * S;
+                                const int i0 = __float_as_int(c.x), i1 = __float_as_int(c.y);
+                                const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+                                const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+                                const float top = fmaf(c.z, s01 - s00, s00);
+                                const float bot = fmaf(c.z, s11 - s10, s10);
+                                acc[k] += fmaf(r.z, bot - top, top);
+                            }
+                        }
+                        __syncwarp();  // the coordinates are rewritten for the next layer
+                    }
+                    float ebx = 0.0f, eby = 0.0f, dxp = 0.0f, ks = 0.0f;
+                    if (SD) {
+                        dxp = (float)(W.pupil_dx_over_ds * I.ds);
+                        const float c0 = 0.5f * (float)(n - 1);
+                        ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
+                        eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
+                        ks = SD->k[sl];
+                    }
+                    float *out = D.opd + W.opd_off + (size_t)v * (n * n);
+#pragma unroll
+                    for (int k = 0; k < NPX; ++k) {
+                        const int i = lane + 32 * k;
+                        if (i < n * n) {
+                            const int pp = i / n, qq = i - pp * n;
+                            const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                            float o = acc[k];
+                            if (W.uplink) o += fmaf(W.uplink->x, xr, W.uplink->y * yr);
+                            if (sl == 0) out[i] = o;
+                            if (SD) {
+                                const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
+                                const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
+                                o += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+                            }
+                            opdw[i] = o;
+                        }
+                    }
+                    __syncwarp();
+                }
+                const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
+                const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
+                const float ref = kFused ? opdw[0] : __ldg(opd);
+                for (int i = lane; i < n * n; i += 32) {
+                    const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
+                    float s, c;
+                    field_phasor(W.k_phase * ((kFused ? opdw[i] : __ldg(opd + i)) - ref), s, c);
+                    X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int p = 0; p < n; ++p) {
+                    const float2 f = Fk[p * N + lane];
+#pragma unroll
+                    for (int q = 0; q < n; ++q) cmacc(U[q], f, X[p * n + q]);
+                }
+            }
+            // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
+            {
+                float hv[2 * n], lv[2 * n];
+#pragma unroll
+                for (int q = 0; q < n; ++q) {
+                    split_bf16(U[q].x, hv[q], lv[q]);
+                    split_bf16(U[q].y, hv[n + q], lv[n + q]);
+                }
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    uint32_t wds[4];
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        float vv[2];
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int e = ch * 8 + e2 * 2 + h2;
+                            const int t = e / (2 * n), j = e % (2 * n);
+                            vv[h2] = e >= 6 * n ? 0.0f : (t == 1 ? lv[j] : hv[j]);
+                        }
+                        wds[e2] = pack_bf16(vv[0], vv[1]);
+                    }
+                    *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                }
+            }
+            if (sl == 0 && a.work && issuer) *snext = nwg + ticket;
+            fence_async_smem();
+            fence_before_sync();
+            wg_sync();
+            fence_after_sync();
+            if (sl == 0) grp_next = a.work ? *snext : grp + nwg;
+            if (*sflag) {  // a previous wait timed out (uniform: read after the barrier)
+                quit = true;
+                break;
+            }
+            if (issuer) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    mma_bf16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
+                mma_commit(&mbar[0]);
+            }
+            // the elongation-kernel model completes mbar[0] once per group like mbar[1]
+            if (!mbar_wait(&mbar[0], kFused ? phase0 : phase)) *sflag = 1;
+            if (kFused) phase0 ^= 1u;
+            fence_after_sync();
+            // Y row from TMEM -> I = |Y|^2; the elongation-kernel model writes the second operand
+            // row [I_hi | I_lo] at once, the per-slice model adds w_s I into the warp's rows
+            {
+                float *dstI = (active && D.st_I && (!kFused || sl == n_sl - 1))
+                                  ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N
+                                  : nullptr;
+                const float wsl = (SD && sl < my_n) ? SD->w[sl] : (kFused && sl > 0 ? 0.0f : 1.0f);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t r[16], r2[16];
+                    GBWFS_TMEM_LD16(r, t_row + 16 * hh);
+                    GBWFS_TMEM_LD16(r2, t_row + 32 + 16 * hh);
+                    tmem_wait_ld();
+                    float I[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
+                        I[m] = fmaf(yr, yr, yi * yi);
+                    }
+                    if (kFused) {
+                        float *ir = Iw + lane * (N + 1) + 16 * hh;
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) {
+                            const float tot = sl == 0 ? wsl * I[m] : fmaf(wsl, I[m], ir[m]);
+                            ir[m] = tot;
+                            if (dstI) dstI[16 * hh + m] = tot;
+                        }
+                        continue;
+                    }
+                    if (dstI) {
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) dstI[16 * hh + m] = I[m];
+                    }
+                    if (active && !W.is_lgs) {
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) Iw[lane * (N + 1) + 16 * hh + m] = I[m];
+                    }
+#pragma unroll
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int e2 = 0; e2 < 4; ++e2) {
+                            float h0, l0, h1, l1;
+                            split_bf16(I[c2 * 8 + 2 * e2], h0, l0);
+                            split_bf16(I[c2 * 8 + 2 * e2 + 1], h1, l1);
+                            hw[e2] = pack_bf16(h0, h1);
+                            lw[e2] = pack_bf16(l0, l1);
+                        }
+                        *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (2 * hh + c2) * 8)) =
+                            make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (4 + 2 * hh + c2) * 8)) =
+                            make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+            }
+            fence_before_sync();  // these TMEM reads precede the next slice's MMA
+            __syncwarp();         // the warp's rows are complete before the next slice adds to them
+        }
+        if (quit) break;
+        if (kFused) {
+            // the summed rows -> second operand row [I_hi | I_lo] (after the last slice's MMA), then
+            // the K~ staging, which reuses their space
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    float h0, l0, h1, l1;
+                    split_bf16(Iw[lane * (N + 1) + c4 * 8 + 2 * e2], h0, l0);
+                    split_bf16(Iw[lane * (N + 1) + c4 * 8 + 2 * e2 + 1], h1, l1);
+                    hw[e2] = pack_bf16(h0, h1);
+                    lw[e2] = pack_bf16(l0, l1);
+                }
+                *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, c4 * 8)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (4 + c4) * 8)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            __syncwarp();
+            if (active && W.is_lgs) stage_ktil();
+        }
+        fence_async_smem();
+        fence_before_sync();
+        wg_sync();
+        fence_after_sync();
+        if (*sflag) break;
+        if (issuer) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2l) + 32 * s), idesc2, 1);
+            mma_commit(&mbar[1]);
+        }
+        if (!mbar_wait(&mbar[1], phase)) *sflag = 1;
+        fence_after_sync();
+        float2 T[n];  // row k = lane of the first inverse stage (LGS)
+        {
+            uint32_t r[32];
+            GBWFS_TMEM_LD32(r, t_row + 64);
+            tmem_wait_ld();
+#pragma unroll
+            for (int d = 0; d < n; ++d) T[d] = make_float2(__uint_as_float(r[d]), __uint_as_float(r[16 + d]));
+        }
+        phase ^= 1u;
+        fence_before_sync();  // TMEM reads of this group precede the next group's MMAs
+        if (!active) continue;
+        __syncwarp();
+
+        // remaining stages on the CUDA cores (per warp)
+        float Bv[nd / 2];
+        if (W.is_lgs) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, Kts, lane, Bv);
+        } else
+            tail::ngs_binned<nd>(Iw, lane, Bv);
+        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the CTA
+    fence_before_sync();
+    __syncthreads();
+    if (*sflag && issuer && a.status) atomicCAS(a.status, 0, 5 /* WFS_ETIMEOUT */);
+    if (a.work && tid == 0) {
+        // every ticket of this CTA was drawn before the barrier above; the last CTA to get here
+        // leaves the counters at zero for the next launch
+        __threadfence();
+        if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
+            a.work[0] = 0;
+            a.work[1] = 0;
+        }
+    }
+    fence_after_sync();
+    if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_all), "r"(kTmemCols));
+}
+
 // ---------------------------------------------------------------- wait check
 // One CTA waits on an mbarrier that nothing will ever arrive on, with a short bound, then
 // reports WFS_ETIMEOUT in *status: the same bounded wait the spot kernel uses, exercised
@@ -460,11 +872,12 @@ float bf16_float(uint16_t h) {
     return f;
 }
 
-template <int n, int nd>
-cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
-    using Lay = TcLayout<n, nd>;
+template <int n, int nd, bool kFused>
+cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
+    using Lay = TcLayout<n, nd, kFused>;
+    const void *f = kFused ? (const void *)k_sh_tc_sl<n, nd> : (const void *)k_sh_tc<n, nd>;
     const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
-    cudaError_t e = cudaFuncSetAttribute(k_sh_tc<n, nd>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int groups = (a.total + 3) / 4;
     const int cta_groups = (groups + kWG - 1) / kWG;
@@ -472,11 +885,17 @@ cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
     const int cap = a.grid_cap > 0 && a.grid_cap < 152 * 2 ? a.grid_cap : 152 * 2;
     int blocks = cta_groups < cap ? cta_groups : cap;
     if (blocks < 1) blocks = 1;
-    out->func = (const void *)k_sh_tc<n, nd>;
+    out->func = f;
     out->grid = dim3(blocks);
     out->block = dim3(kTcThreads);
     out->smem = smem;
     return cudaSuccess;
+}
+
+// ShArgs::project selects the self-projecting variant (its own layer sampling, per-slice model).
+template <int n, int nd>
+cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
+    return a.project ? shape_tc_k<n, nd, true>(a, out) : shape_tc_k<n, nd, false>(a, out);
 }
 
 }  // namespace

@@ -41,10 +41,12 @@ def test_per_slice_with_uplink_config2():
     w.close()
 
 
-def test_per_slice_elt_sampled_full_launch():
-    """The ELT frame with the per-slice model on the six LGS (8 slices each) at full size:
-    sampled subapertures of every star against the oracle."""
-    cfg = _per_slice(inputs.config3())
+@pytest.mark.parametrize("precision", [inputs.PREC_BF16X3, inputs.PREC_FP32])
+def test_per_slice_elt_sampled_full_launch(precision):
+    """The ELT frame with the per-slice model on the six LGS (8 slices each) at full size, on
+    the self-projecting tensor-core kernel (BF16x3) and on the FP32 32-point kernel: sampled
+    subapertures of every star against the oracle."""
+    cfg = _per_slice(inputs.config3(precision))
     scr = inputs.make_screens(cfg.layers, cfg.seed)
     t = 0.05
     gpu, w = run_library(cfg, scr, t)
