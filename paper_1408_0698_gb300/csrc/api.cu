@@ -48,6 +48,10 @@ struct SpotGroup {
     // launch shape of the elongation-kernel model are kept to restore it
     bool per_slice = false;
     int base_kind = 0, base_grid_cap = 0, base_cta_warps = 0;
+    // 32-point kernels: the per-slice OPDs come from one projection of every (WFS, slice) pair
+    bool sl_projected = false;
+    WfsDesc *d_sl_wfs = nullptr;
+    int sl_count = 0, sl_blocks = 0;
 };
 
 int spot_kind(const wfs_geometry &g) {
@@ -125,6 +129,7 @@ struct wfs_ctx {
     int n_uplink = 0;                 // guide stars with the uplink tip-tilt on
     bool per_slice = false;           // LGS per-slice model on
     SliceDesc *d_slices = nullptr;    // per guide star (LGS entries used)
+    float *d_opd_sl = nullptr;        // per-slice OPDs: slice s at s * opd_total
     cudaEvent_t ev_uplink = nullptr;  // after the uplink kernel: side groups with the uplink wait on it
 };
 
@@ -324,6 +329,12 @@ void release(wfs_ctx *h) {
     cudaFree(h->d_uplink);
     cudaFree(h->d_slices);
     h->d_slices = nullptr;
+    cudaFree(h->d_opd_sl);
+    h->d_opd_sl = nullptr;
+    for (SpotGroup &G : h->groups) {
+        cudaFree(G.d_sl_wfs);
+        G.d_sl_wfs = nullptr;
+    }
     cudaFree(h->d_uplink_part);
     cudaFree(h->d_uplink_count);
     if (h->ev_uplink) cudaEventDestroy(h->ev_uplink);
@@ -510,7 +521,9 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     static thread_local ShArgs sa;
     // project_mode: 0 = a projection launch precedes, 1 = self-projecting on a side stream,
     // 2 = self-projecting on the caller's stream
-    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project, int project_mode) -> cudaError_t {
+    // slice_stride > 0: the per-slice 32-point kernels read slice s of the OPDs from d_opd_sl
+    auto launch_group = [&](const SpotGroup &G, cudaStream_t ls, bool after_project, int project_mode,
+                            long long slice_stride = 0) -> cudaError_t {
         memset(&sa, 0, offsetof(ShArgs, dyn));
         fill_geom_args(sa, h->geoms[G.geom]);
         sa.inst = h->d_inst;
@@ -524,7 +537,9 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.work = h->d_work + 2 * (&G - h->groups.data());
         sa.project = project_mode;
         sa.split_noise = splits_noise(G.kind) ? 1 : 0;
+        sa.slice_opd_stride = slice_stride;
         sa.dyn[0] = dyn;
+        if (slice_stride > 0) sa.dyn[0].opd = h->d_opd_sl;
         long sl = timed_begin(h, kind_name(G.kind) + std::to_string(sa.N), ls);
         cudaError_t err = launch_spot(G.kind, sa, ls, after_project && !h->timing);
         timed_end(h, sl, ls);
@@ -569,7 +584,30 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     }
     if (!h->groups.empty()) {
         const SpotGroup &G = h->groups[big];
-        if (G.per_slice) {
+        if (G.per_slice && G.sl_projected) {
+            // the per-slice model: one projection of every (WFS, slice) pair into the slice OPDs,
+            // then the 32-point kernel's per-slice variant
+            pa.wfs = G.d_sl_wfs;
+            pa.n_wfs = G.sl_count;
+            pa.block_base = 0;
+            pa.work = h->d_work + 2 * (h->groups.size() + 1) + 2 * big;
+            pa.dyn[0].opd = h->d_opd_sl;
+            long slot = timed_begin(h, "project", stream);
+            e = launch_project(pa, G.sl_blocks, stream, h->n_uplink > 0 && !h->timing);
+            timed_end(h, slot, stream);
+            pa.dyn[0].opd = dyn.opd;
+            if (e != cudaSuccess) return cuda_fail(h, e, "projection launch");
+            const bool copies = st && st->opd;  // the OPD stage: the first slice's OPDs
+            for (int q = 0; copies && q < G.count; ++q) {
+                const WfsDesc &d = h->wfs_host[G.first + q];
+                if ((e = cudaMemcpyAsync(st->opd + d.opd_off, h->d_opd_sl + d.opd_off,
+                                         sizeof(float) * (size_t)d.n_valid * d.n * d.n, cudaMemcpyDeviceToDevice,
+                                         stream)) != cudaSuccess)
+                    return cuda_fail(h, e, "OPD stage copy");
+            }
+            if (G.total > 0 && (e = launch_group(G, stream, !copies, 0, (long long)h->opd_total)) != cudaSuccess)
+                return cuda_fail(h, e, "spot launch");
+        } else if (G.per_slice) {
             // the per-slice model projects one wavefront per sodium slice inside the spot kernel
             if (G.total > 0 && (e = launch_group(G, stream, false, 2)) != cudaSuccess)
                 return cuda_fail(h, e, "spot launch");
@@ -2077,6 +2115,38 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             const GsDev &gd = h->gs[d.gs_index];
             d.slices = per_slice ? h->d_slices + d.gs_index : nullptr;
             d.ktil = per_slice ? gd.d_ktil_g : gd.d_ktil;
+        }
+        // 32-point kernels read per-slice OPDs made by one projection launch over copies of the
+        // WFS entries whose range is the slice altitude (the cone) and whose OPD goes to slice s
+        cudaFree(G.d_sl_wfs);
+        G.d_sl_wfs = nullptr;
+        G.sl_projected = per_slice && (G.kind == kSpotTc || G.kind == kSpotN32);
+        if (G.sl_projected) {
+            std::vector<WfsDesc> t;
+            int blocks = 0;
+            for (int q = 0; q < G.count; ++q) {
+                const WfsDesc &d0 = h->wfs_host[G.first + q];
+                const GsDev &gd = h->gs[d0.gs_index];
+                const size_t ns = d0.is_lgs ? gd.na_alt.size() : 1;
+                for (size_t sl = 0; sl < ns; ++sl) {
+                    WfsDesc d = d0;
+                    if (d0.is_lgs) d.range_m = gd.na_alt[sl];
+                    d.opd_off = d0.opd_off + (long long)(sl * h->opd_total);
+                    d.proj_block_begin = blocks;
+                    blocks += project_blocks(d);
+                    t.push_back(d);
+                }
+            }
+            G.sl_count = (int)t.size();
+            G.sl_blocks = blocks;
+            if ((e = upload(&G.d_sl_wfs, t)) != cudaSuccess) return cuda_fail(h, e, "slice projection table");
+            if (!h->d_opd_sl) {
+                size_t n_max = 1;
+                for (const GsDev &gd : h->gs)
+                    if (gd.gs.is_lgs) n_max = std::max(n_max, gd.na_alt.size());
+                if ((e = cudaMalloc(&h->d_opd_sl, sizeof(float) * h->opd_total * n_max)) != cudaSuccess)
+                    return cuda_fail(h, e, "slice OPDs");
+            }
         }
     }
     if ((e = cudaMemcpy(h->d_wfs, h->wfs_host.data(), sizeof(WfsDesc) * h->wfs_host.size(), cudaMemcpyHostToDevice)) !=

@@ -122,6 +122,9 @@ struct ShArgs {
                          // itself (no separate projection launch; written to dyn.opd too) on a
                          // side stream, with the shared-memory reservation that keeps projection
                          // CTAs off its SMs; 2 = the same without the reservation
+    // 32-point kernels, LGS per-slice model: slice s of a subaperture's OPD sits
+    // s * slice_opd_stride floats after slice 0 (projected by k_project); 0 = one OPD
+    long long slice_opd_stride;
     int split_noise;     // 32-point kernels: 1 = store the expected image (dyn.st_E, required)
                          // and stop; launch_noise_cog completes the measurement
     InstDyn dyn[kMaxInstances];

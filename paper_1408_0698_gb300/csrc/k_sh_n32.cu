@@ -13,15 +13,13 @@
 // then photometry, noise and the centroid with warp reductions.  All sizes are
 // compile-time constants.
 //
-// The self-projecting variant (kFused, launched with ShArgs::project) projects each
-// subaperture's OPD itself and runs the LGS per-slice model (Sec. 4: one wavefront and one
-// spot per sodium sub-layer, piled up with the profile weights): per slice the layers are
-// sampled through the slice's cone, the uplink tilt and the slice's geometric term are added,
-// and w_s |Y|^2 enters the first inverse-transform stage T directly (T is linear in I), so the
-// slices' spots are never stored.
+// The per-slice variant (kFused, launched with ShArgs::slice_opd_stride) runs the LGS per-slice
+// model (Sec. 4: one wavefront and one spot per sodium sub-layer, piled up with the profile
+// weights): the projection has made one OPD per slice (the layers through the slice's cone);
+// per slice the warp adds the slice's geometric term, and the weighted spots are summed in the
+// warp's shared rows before the first inverse-transform stage T.
 #include "internal.h"
 #include "noise.cuh"
-#include "proj_math.cuh"
 #include "spot_tail.cuh"
 
 namespace gbwfs {
@@ -49,10 +47,7 @@ struct N32Layout {
     static constexpr int wTa = wX + n * n;         // Q: [nd][n]
     static constexpr int wM = wTa + nd * n;        // [dyi][n]
     static constexpr int wI = wM + D2 * n;         // [k][N+1] floats (NGS binning only)
-    static constexpr int wOpd = wI + (N * (N + 1) + 1) / 2;  // self-projecting: [p][q] floats
-    static constexpr int wLo = wOpd + (kFused ? (n * n + 1) / 2 : 0);  // layer offsets (LayerOffs)
-    static constexpr int wCt = wLo + (kFused ? (kMaxProjLayers * (int)sizeof(LayerOffs) + 15) / 16 * 2 : 0);
-    static constexpr int warp = wCt + (kFused ? 2 * (2 * n) : 0);  // coordinate table: 2n float4
+    static constexpr int warp = wI + (N * (N + 1) + 1) / 2;
 };
 
 }  // namespace
@@ -89,9 +84,6 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     float2 *Ta = sm2 + Lay::table + wib * Lay::warp + Lay::wTa;
     float2 *Mw = sm2 + Lay::table + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
-    float *opdw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wOpd);
-    LayerOffs *low = reinterpret_cast<LayerOffs *>(sm2 + Lay::table + wib * Lay::warp + Lay::wLo);
-    float4 *ctab = reinterpret_cast<float4 *>(sm2 + Lay::table + wib * Lay::warp + Lay::wCt);
 
     // Work split: each warp starts with subaperture blockIdx.x * nw + wib; with a.work, lane 0
     // draws one ticket per iteration (issued at the top, used at the bottom).
@@ -109,103 +101,37 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 
         const SliceDesc *SD = kFused ? W.slices : nullptr;
         const int n_sl = SD ? SD->n : 1;
-        const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
         const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
-        int L = 0;
-        if (kFused) {
-            // the layer offsets of this subaperture's WFS (FP64; shared by the slices)
-            const InstDesc &I = a.inst[W.inst];
-            L = proj_layers(I, D);
-            for (int l = lane; l < L; l += 32) low[l] = layer_offsets(I, W, D.t, l);
-            __syncwarp();
-        }
         float2 T[n];
 #pragma unroll
         for (int d = 0; d < n; ++d) T[d] = make_float2(0.0f, 0.0f);
         float *stI = D.st_I ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
+        // per-slice model: the slice's geometric term k_s ((x - r_b).(r_b - r_L) + 1/2 |x - r_b|^2)
+        // about the subaperture centre r_b, added to the slice's projected OPD
+        float ebx = 0.0f, eby = 0.0f, dxp = 0.0f;
+        if (SD) {
+            const InstDesc &I = a.inst[W.inst];
+            const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
+            const float half = 0.5f * (float)(W.n_sub * n - 1), c0 = 0.5f * (float)(n - 1);
+            dxp = (float)(W.pupil_dx_over_ds * I.ds);
+            ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
+            eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
+        }
         for (int sl = 0; sl < n_sl; ++sl) {
-            if (kFused) {
-                // this subaperture's OPD for slice sl: the projection's arithmetic with the slice's
-                // cone (scale), the uplink tilt, and the slice's geometric term about the centre
-                const InstDesc &I = a.inst[W.inst];
-                const int S = I.S;
-                const bool pow2 = (S & (S - 1)) == 0;
-                const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
-                const float half = 0.5f * (float)(W.n_sub * n - 1);
-                float ebx = 0.0f, eby = 0.0f, dxp = 0.0f, ks = 0.0f;
-                if (SD) {
-                    dxp = (float)(W.pupil_dx_over_ds * I.ds);
-                    const float c0 = 0.5f * (float)(n - 1);
-                    ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
-                    eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
-                    ks = SD->k[sl];
-                }
-                float *out = D.opd + W.opd_off + (size_t)v * (n * n);
-                // per layer: lanes 0 .. n-1 make the column coordinates (wrapped indices and
-                // fraction), lanes n .. 2n-1 the row coordinates; then every pixel reads its
-                // column's and row's entries
-                constexpr int NPX = (n * n + 31) / 32;
-                float acc[NPX];
-#pragma unroll
-                for (int k = 0; k < NPX; ++k) acc[k] = 0.0f;
-                for (int l = 0; l < L; ++l) {
-                    const LayerOffs L0 = low[l];
-                    if (lane < 2 * n) {
-                        const bool col = lane < n;
-                        const float ch = SD ? SD->c[sl][l].x : L0.c, cl = SD ? SD->c[sl][l].y : L0.cl;
-                        const float xr = col ? (float)(sx * n + lane) - half : (float)(sy * n + lane - n) - half;
-                        int o, i0, i1;
-                        float f;
-                        screen_offset(ch, cl, col ? L0.fu : L0.fv, xr, o, f);
-                        wrap_pair((col ? L0.bu : L0.bv) + o, S, pow2, i0, i1);
-                        ctab[lane] = make_float4(__int_as_float(i0), __int_as_float(i1), f, 0.0f);
-                    }
-                    __syncwarp();
-                    const float *scr = layer_screen(I, D, l);
-#pragma unroll
-                    for (int k = 0; k < NPX; ++k) {
-                        const int i = lane + 32 * k;
-                        if (i < n * n) {
-                            const int pp = i / n, qq = i - pp * n;
-                            const float4 c = ctab[qq], r = ctab[n + pp];
-                            const float *r0 = scr + (size_t)__float_as_int(r.x) * S;
-                            const float *r1 = scr + (size_t)__float_as_int(r.y) * S;
-                            const int i0 = __float_as_int(c.x), i1 = __float_as_int(c.y);
-                            const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
-                            const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
-                            const float top = fmaf(c.z, s01 - s00, s00);
-                            const float bot = fmaf(c.z, s11 - s10, s10);
-                            acc[k] += fmaf(r.z, bot - top, top);
-                        }
-                    }
-                    __syncwarp();  // the coordinates are rewritten for the next layer
-                }
-#pragma unroll
-                for (int k = 0; k < NPX; ++k) {
-                    const int i = lane + 32 * k;
-                    if (i < n * n) {
-                        const int pp = i / n, qq = i - pp * n;
-                        const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
-                        float o = acc[k];
-                        if (W.uplink) o += fmaf(W.uplink->x, xr, W.uplink->y * yr);
-                        if (sl == 0) out[i] = o;
-                        if (SD) {
-                            const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
-                            const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
-                            o += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
-                        }
-                        opdw[i] = o;
-                    }
-                }
-                __syncwarp();
-            }
-
+            const float *opd = D.opd + W.opd_off + (size_t)sl * a.slice_opd_stride + (size_t)v * (n * n);
+            const float ks = SD ? SD->k[sl] : 0.0f;
+            auto geo = [&](int i) -> float {
+                const int pp = i / n, qq = i - pp * n;
+                const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
+                const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
+                return ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+            };
             // field, piston-free
-            const float ref = kFused ? opdw[0] : __ldg(opd);
+            const float ref = __ldg(opd) + (kFused ? geo(0) : 0.0f);
             for (int i = lane; i < n * n; i += 32) {
                 const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                 float s, c;
-                field_phasor(W.k_phase * ((kFused ? opdw[i] : __ldg(opd + i)) - ref), s, c);
+                field_phasor(W.k_phase * ((__ldg(opd + i) + (kFused ? geo(i) : 0.0f)) - ref), s, c);
                 X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
             }
             __syncwarp();
@@ -303,10 +229,10 @@ cudaError_t shape_n32_k(const ShArgs &a, LaunchShape *out) {
     return cudaSuccess;
 }
 
-// ShArgs::project selects the self-projecting variant (its own layer sampling, per-slice model).
+// ShArgs::slice_opd_stride selects the per-slice variant.
 template <int n, int nd>
 cudaError_t shape_n32(const ShArgs &a, LaunchShape *out) {
-    return a.project ? shape_n32_k<n, nd, true>(a, out) : shape_n32_k<n, nd, false>(a, out);
+    return a.slice_opd_stride > 0 ? shape_n32_k<n, nd, true>(a, out) : shape_n32_k<n, nd, false>(a, out);
 }
 }  // namespace
 

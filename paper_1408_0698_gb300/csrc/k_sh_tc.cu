@@ -23,12 +23,12 @@
 // CTA = one warpgroup (4 warps); warp w owns subaperture 4g + w of group g and its
 // lane k owns DFT row k, which is also TMEM lane 32 w + k of both accumulators.
 //
-// The self-projecting variant (kFused, launched with ShArgs::project) projects each
-// subaperture's OPD itself and runs the LGS per-slice model (Sec. 4: one wavefront and one
-// spot per sodium sub-layer, piled up with the profile weights): per slice the warp samples the
-// layers through the slice's cone (per-layer coordinate tables), adds the uplink tilt and the
-// slice's geometric term, forms U, and the warpgroup's Y = U F^T runs on the tensor cores; the
-// weighted |Y|^2 of the slices are summed in the warp's shared rows, which then feed Ta = I Ga^T.
+// The per-slice variant (k_sh_tc_sl, launched with ShArgs::slice_opd_stride) runs the LGS
+// per-slice model (Sec. 4: one wavefront and one spot per sodium sub-layer, piled up with the
+// profile weights): the projection has made one OPD per slice (the layers through the slice's
+// cone); per slice the warp adds the slice's geometric term, forms U, and the warpgroup's
+// Y = U F^T runs on the tensor cores; the weighted |Y|^2 of the slices are summed in the warp's
+// shared rows, which then feed Ta = I Ga^T.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -36,7 +36,6 @@
 
 #include "internal.h"
 #include "noise.cuh"
-#include "proj_math.cuh"
 #include "spot_tail.cuh"
 
 namespace gbwfs {
@@ -163,14 +162,10 @@ struct TcLayout {
     // subaperture never writes (a warp's copies land before its next NGS image)
     static constexpr int wKt = lgs_end;
     static constexpr int base_warp = wKt + D2 * n > ngs_end ? wKt + D2 * n : ngs_end;
-    // self-projecting variant: the summed spot rows use the NGS rows (wI; K~ is staged after
-    // them), then the slice's OPD, the layer offsets and the per-layer coordinate table
-    static constexpr int wOpd = base_warp;
-    static constexpr int wLo = wOpd + (kFused ? (n * n + 1) / 2 + ((n * n + 1) / 2) % 2 : 0);
-    static constexpr int wCt = wLo + (kFused ? (kMaxProjLayers * (int)sizeof(LayerOffs) + 15) / 16 * 2 : 0);
-    static constexpr int warp = wCt + (kFused ? 4 * n : 0);
-    // per warpgroup: 2 mbarriers (0), flag (16), next group (20); self-projecting variant: the
-    // slice counts of its 4 warps (32)
+    // per-slice variant: the summed spot rows use the NGS rows (wI; K~ is staged after them)
+    static constexpr int warp = base_warp;
+    // per warpgroup: 2 mbarriers (0), flag (16), next group (20); per-slice variant: the slice
+    // counts of its 4 warps (32)
     static constexpr int misc = kFused ? 48 : 32;
     static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;
     static constexpr int bytes = oMisc + misc * kWG + 16;
@@ -502,9 +497,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
     float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
     float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
-    float *opdw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wOpd);
-    LayerOffs *low = reinterpret_cast<LayerOffs *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wLo);
-    float4 *ctab = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wCt);
     const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
     const int groups = (a.total + 3) / 4;
     const bool issuer = wq == 0 && lane == 0;
@@ -539,14 +531,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
         // its four subapertures (a subaperture with fewer adds nothing in the extra ones)
         const SliceDesc *SD = (kFused && active) ? W.slices : nullptr;
         const int my_n = SD ? SD->n : 1;
-        int n_sl = 1, L = 0;
+        int n_sl = 1;
         if (kFused) {
             if (lane == 0) snsl[wq] = my_n;
-            if (active) {
-                const InstDesc &I = a.inst[W.inst];
-                L = proj_layers(I, D);
-                for (int l = lane; l < L; l += 32) low[l] = layer_offsets(I, W, D.t, l);
-            }
             wg_sync();
             n_sl = max(max(snsl[0], snsl[1]), max(snsl[2], snsl[3]));
         }
@@ -557,86 +544,31 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
 #pragma unroll
             for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
             if (active && sl < my_n) {
-                if (kFused) {
-                    // the slice's OPD: the projection's arithmetic with the slice's cone, through
-                    // per-layer coordinate tables (lanes 0 .. n-1 columns, n .. 2n-1 rows), plus the
-                    // uplink tilt and the slice's geometric term about the subaperture centre
+                // the slice's OPD (projected through its cone) plus its geometric term
+                // k_s ((x - r_b).(r_b - r_L) + 1/2 |x - r_b|^2) about the subaperture centre r_b
+                const float *opd = D.opd + W.opd_off + (size_t)sl * a.slice_opd_stride + (size_t)v * (n * n);
+                float ebx = 0.0f, eby = 0.0f, dxp = 0.0f, ks = 0.0f;
+                if (SD) {
                     const InstDesc &I = a.inst[W.inst];
-                    const int S = I.S;
-                    const bool pow2 = (S & (S - 1)) == 0;
                     const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
-                    const float half = 0.5f * (float)(W.n_sub * n - 1);
-                    constexpr int NPX = (n * n + 31) / 32;
-                    float acc[NPX];
-#pragma unroll
-                    for (int k = 0; k < NPX; ++k) acc[k] = 0.0f;
-                    for (int l = 0; l < L; ++l) {
-                        const LayerOffs L0 = low[l];
-                        if (lane < 2 * n) {
-                            const bool col = lane < n;
-                            const float ch = SD ? SD->c[sl][l].x : L0.c, cl = SD ? SD->c[sl][l].y : L0.cl;
-                            const float xr = col ? (float)(sx * n + lane) - half : (float)(sy * n + lane - n) - half;
-                            int o, i0, i1;
-                            float f;
-                            screen_offset(ch, cl, col ? L0.fu : L0.fv, xr, o, f);
-                            wrap_pair((col ? L0.bu : L0.bv) + o, S, pow2, i0, i1);
-                            ctab[lane] = make_float4(__int_as_float(i0), __int_as_float(i1), f, 0.0f);
-                        }
-                        __syncwarp();
-                        const float *scr = layer_screen(I, D, l);
-#pragma unroll
-                        for (int k = 0; k < NPX; ++k) {
-                            const int i = lane + 32 * k;
-                            if (i < n * n) {
-                                const int pp = i / n, qq = i - pp * n;
-                                const float4 c = ctab[qq], r = ctab[n + pp];
-                                const float *r0 = scr + (size_t)__float_as_int(r.x) * S;
-                                const float *r1 = scr + (size_t)__float_as_int(r.y) * S;
-                                const int i0 = __float_as_int(c.x), i1 = __float_as_int(c.y);
-                                const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
-                                const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
-                                const float top = fmaf(c.z, s01 - s00, s00);
-                                const float bot = fmaf(c.z, s11 - s10, s10);
-                                acc[k] += fmaf(r.z, bot - top, top);
-                            }
-                        }
-                        __syncwarp();  // the coordinates are rewritten for the next layer
-                    }
-                    float ebx = 0.0f, eby = 0.0f, dxp = 0.0f, ks = 0.0f;
-                    if (SD) {
-                        dxp = (float)(W.pupil_dx_over_ds * I.ds);
-                        const float c0 = 0.5f * (float)(n - 1);
-                        ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
-                        eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
-                        ks = SD->k[sl];
-                    }
-                    float *out = D.opd + W.opd_off + (size_t)v * (n * n);
-#pragma unroll
-                    for (int k = 0; k < NPX; ++k) {
-                        const int i = lane + 32 * k;
-                        if (i < n * n) {
-                            const int pp = i / n, qq = i - pp * n;
-                            const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
-                            float o = acc[k];
-                            if (W.uplink) o += fmaf(W.uplink->x, xr, W.uplink->y * yr);
-                            if (sl == 0) out[i] = o;
-                            if (SD) {
-                                const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
-                                const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
-                                o += ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
-                            }
-                            opdw[i] = o;
-                        }
-                    }
-                    __syncwarp();
+                    const float half = 0.5f * (float)(W.n_sub * n - 1), c0 = 0.5f * (float)(n - 1);
+                    dxp = (float)(W.pupil_dx_over_ds * I.ds);
+                    ebx = ((float)(sx * n) + c0 - half) * dxp - (float)W.launch_x;
+                    eby = ((float)(sy * n) + c0 - half) * dxp - (float)W.launch_y;
+                    ks = SD->k[sl];
                 }
-                const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
+                auto geo = [&](int i) -> float {
+                    const int pp = i / n, qq = i - pp * n;
+                    const float ux = ((float)qq - 0.5f * (float)(n - 1)) * dxp;
+                    const float uy = ((float)pp - 0.5f * (float)(n - 1)) * dxp;
+                    return ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
+                };
                 const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
-                const float ref = kFused ? opdw[0] : __ldg(opd);
+                const float ref = __ldg(opd) + geo(0);
                 for (int i = lane; i < n * n; i += 32) {
                     const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                     float s, c;
-                    field_phasor(W.k_phase * ((kFused ? opdw[i] : __ldg(opd + i)) - ref), s, c);
+                    field_phasor(W.k_phase * ((__ldg(opd + i) + geo(i)) - ref), s, c);
                     X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
                 }
                 __syncwarp();
@@ -892,10 +824,10 @@ cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
     return cudaSuccess;
 }
 
-// ShArgs::project selects the self-projecting variant (its own layer sampling, per-slice model).
+// ShArgs::slice_opd_stride selects the per-slice variant.
 template <int n, int nd>
 cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
-    return a.project ? shape_tc_k<n, nd, true>(a, out) : shape_tc_k<n, nd, false>(a, out);
+    return a.slice_opd_stride > 0 ? shape_tc_k<n, nd, true>(a, out) : shape_tc_k<n, nd, false>(a, out);
 }
 
 }  // namespace
