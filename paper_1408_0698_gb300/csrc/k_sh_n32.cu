@@ -13,7 +13,7 @@
 // then photometry, noise and the centroid with warp reductions.  All sizes are
 // compile-time constants.
 //
-// The per-slice variant (kFused, launched with ShArgs::slice_opd_stride) runs the LGS per-slice
+// The per-slice variant (kSlices, launched with ShArgs::slice_opd_stride) runs the LGS per-slice
 // model (Sec. 4: one wavefront and one spot per sodium sub-layer, piled up with the profile
 // weights): the projection has made one OPD per slice (the layers through the slice's cone);
 // per slice the warp adds the slice's geometric term, and the weighted spots are summed in the
@@ -31,7 +31,7 @@ __device__ __forceinline__ void cmac2(float2 &acc, const float2 a, const float2 
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-template <int n, int nd, bool kFused = false>
+template <int n, int nd, bool kSlices = false>
 struct N32Layout {
     static constexpr int N = 32, D2 = 2 * n - 1;
     // per-CTA tables (float2 units)
@@ -52,9 +52,9 @@ struct N32Layout {
 
 }  // namespace
 
-template <int n, int nd, bool kFused>
+template <int n, int nd, bool kSlices>
 __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArgs a) {
-    using Lay = N32Layout<n, nd, kFused>;
+    using Lay = N32Layout<n, nd, kSlices>;
     constexpr int N = 32, D2 = Lay::D2;
     constexpr int nd2 = nd * nd;
     static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         const int v = g - W.subap_begin;
         __syncwarp();
 
-        const SliceDesc *SD = kFused ? W.slices : nullptr;
+        const SliceDesc *SD = kSlices ? W.slices : nullptr;
         const int n_sl = SD ? SD->n : 1;
         const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
         float2 T[n];
@@ -127,11 +127,11 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
                 return ks * fmaf(ux, ebx, fmaf(uy, eby, 0.5f * fmaf(ux, ux, uy * uy)));
             };
             // field, piston-free
-            const float ref = __ldg(opd) + (kFused ? geo(0) : 0.0f);
+            const float ref = __ldg(opd) + (kSlices ? geo(0) : 0.0f);
             for (int i = lane; i < n * n; i += 32) {
                 const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                 float s, c;
-                field_phasor(W.k_phase * ((__ldg(opd + i) + (kFused ? geo(i) : 0.0f)) - ref), s, c);
+                field_phasor(W.k_phase * ((__ldg(opd + i) + (kSlices ? geo(i) : 0.0f)) - ref), s, c);
                 X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
             }
             __syncwarp();
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
                 for (int q = 0; q < n; ++q) cmac2(y, U[q], Fm[m * n + q]);
                 const float in = SD ? wsl * fmaf(y.x, y.x, y.y * y.y) : fmaf(y.x, y.x, y.y * y.y);
                 if (stI) stI[m] = sl == 0 ? in : stI[m] + in;
-                if (kFused) {
+                if (kSlices) {
                     // the slices' spots summed in the warp's rows; T once after the last slice
                     float *ir = Iw + lane * (N + 1) + m;
                     *ir = sl == 0 ? in : *ir + in;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             }
             __syncwarp();  // X and the slice's OPD are rewritten by the next slice
         }
-        if (kFused && W.is_lgs) {
+        if (kSlices && W.is_lgs) {
 #pragma unroll 2
             for (int m = 0; m < N; ++m) {
                 const float in = Iw[lane * (N + 1) + m];
@@ -211,18 +211,18 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 }
 
 namespace {
-template <int n, int nd, bool kFused>
+template <int n, int nd, bool kSlices>
 cudaError_t shape_n32_k(const ShArgs &a, LaunchShape *out) {
-    using Lay = N32Layout<n, nd, kFused>;
+    using Lay = N32Layout<n, nd, kSlices>;
     const int warps = (a.cta_warps == 4 || a.cta_warps == 8) ? a.cta_warps : 8;
     const size_t smem = (size_t)(Lay::table + warps * Lay::warp) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_sh_n32<n, nd, kFused>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sh_n32<n, nd, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (a.total + warps - 1) / warps;
     const int cap = a.grid_cap > 0 ? a.grid_cap : 152 * 2 * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    out->func = (const void *)k_sh_n32<n, nd, kFused>;
+    out->func = (const void *)k_sh_n32<n, nd, kSlices>;
     out->grid = dim3(blocks);
     out->block = dim3(warps * 32);
     out->smem = smem;

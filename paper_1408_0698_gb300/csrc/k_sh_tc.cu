@@ -137,7 +137,7 @@ __device__ __forceinline__ void cmacc(float2 &acc, const float2 a, const float2 
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
 }
 
-template <int n, int nd, bool kFused = false>
+template <int n, int nd, bool kSlices = false>
 struct TcLayout {
     static constexpr int N = 32, D2 = 2 * n - 1;
     // byte offsets; tensor-core tiles first (1024-aligned)
@@ -166,7 +166,7 @@ struct TcLayout {
     static constexpr int warp = base_warp;
     // per warpgroup: 2 mbarriers (0), flag (16), next group (20); per-slice variant: the slice
     // counts of its 4 warps (32)
-    static constexpr int misc = kFused ? 48 : 32;
+    static constexpr int misc = kSlices ? 48 : 32;
     static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;
     static constexpr int bytes = oMisc + misc * kWG + 16;
 };
@@ -430,8 +430,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 // The self-projecting per-slice variant (see the file comment).
 template <int n, int nd>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constant__ ShArgs a) {
-    constexpr bool kFused = true;
-    using Lay = TcLayout<n, nd, kFused>;
+    constexpr bool kSlices = true;
+    using Lay = TcLayout<n, nd, kSlices>;
     constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
     static_assert(n % 2 == 0 && Lay::wKt % 2 == 0 && Lay::warp % 2 == 0 && Lay::oWarp % 16 == 0,
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + Lay::misc * wg);
     int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 16);
     int *snext = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 20);  // next group (dynamic split)
-    int *snsl = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 32);   // slices per warp (kFused)
+    int *snsl = reinterpret_cast<int *>(smem + Lay::oMisc + Lay::misc * wg + 32);   // slices per warp (kSlices)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + Lay::misc * kWG);
     const uint32_t bar_id = 1 + wg;
     auto wg_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(128) : "memory"); };
@@ -525,14 +525,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
-        if (!kFused && active && W.is_lgs) stage_ktil();
+        if (!kSlices && active && W.is_lgs) stage_ktil();
 
         // slices: one for the elongation-kernel model; the warpgroup runs the largest count of
         // its four subapertures (a subaperture with fewer adds nothing in the extra ones)
-        const SliceDesc *SD = (kFused && active) ? W.slices : nullptr;
+        const SliceDesc *SD = (kSlices && active) ? W.slices : nullptr;
         const int my_n = SD ? SD->n : 1;
         int n_sl = 1;
-        if (kFused) {
+        if (kSlices) {
             if (lane == 0) snsl[wq] = my_n;
             wg_sync();
             n_sl = max(max(snsl[0], snsl[1]), max(snsl[2], snsl[3]));
@@ -621,16 +621,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                 mma_commit(&mbar[0]);
             }
             // the elongation-kernel model completes mbar[0] once per group like mbar[1]
-            if (!mbar_wait(&mbar[0], kFused ? phase0 : phase)) *sflag = 1;
-            if (kFused) phase0 ^= 1u;
+            if (!mbar_wait(&mbar[0], kSlices ? phase0 : phase)) *sflag = 1;
+            if (kSlices) phase0 ^= 1u;
             fence_after_sync();
             // Y row from TMEM -> I = |Y|^2; the elongation-kernel model writes the second operand
             // row [I_hi | I_lo] at once, the per-slice model adds w_s I into the warp's rows
             {
-                float *dstI = (active && D.st_I && (!kFused || sl == n_sl - 1))
+                float *dstI = (active && D.st_I && (!kSlices || sl == n_sl - 1))
                                   ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N
                                   : nullptr;
-                const float wsl = (SD && sl < my_n) ? SD->w[sl] : (kFused && sl > 0 ? 0.0f : 1.0f);
+                const float wsl = (SD && sl < my_n) ? SD->w[sl] : (kSlices && sl > 0 ? 0.0f : 1.0f);
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     uint32_t r[16], r2[16];
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                         const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
                         I[m] = fmaf(yr, yr, yi * yi);
                     }
-                    if (kFused) {
+                    if (kSlices) {
                         float *ir = Iw + lane * (N + 1) + 16 * hh;
 #pragma unroll
                         for (int m = 0; m < 16; ++m) {
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
             __syncwarp();         // the warp's rows are complete before the next slice adds to them
         }
         if (quit) break;
-        if (kFused) {
+        if (kSlices) {
             // the summed rows -> second operand row [I_hi | I_lo] (after the last slice's MMA), then
             // the K~ staging, which reuses their space
 #pragma unroll
@@ -804,10 +804,10 @@ float bf16_float(uint16_t h) {
     return f;
 }
 
-template <int n, int nd, bool kFused>
+template <int n, int nd, bool kSlices>
 cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
-    using Lay = TcLayout<n, nd, kFused>;
-    const void *f = kFused ? (const void *)k_sh_tc_sl<n, nd> : (const void *)k_sh_tc<n, nd>;
+    using Lay = TcLayout<n, nd, kSlices>;
+    const void *f = kSlices ? (const void *)k_sh_tc_sl<n, nd> : (const void *)k_sh_tc<n, nd>;
     const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
