@@ -48,6 +48,7 @@ extern "C" {
 typedef struct wfs_ctx *wfs_handle;
 typedef struct wfs_batch_ctx *wfs_batch;
 typedef struct wfs_loop_ctx *wfs_loop;
+typedef struct wfs_loop_batch_ctx *wfs_loop_batch;
 
 typedef enum {
     WFS_OK = 0,
@@ -417,6 +418,26 @@ wfs_status wfs_loop_set_coeffs(wfs_loop lp, const float *coeffs, void *stream);
 wfs_status wfs_loop_get_coeffs(wfs_loop lp, float *coeffs_out, void *stream);
 wfs_status wfs_loop_get_layer(wfs_loop lp, int d, float *layer_out, void *stream);
 wfs_status wfs_loop_destroy(wfs_loop lp);
+
+/*
+ * Batches of closed loops (Monte-Carlo runs of one system).  wfs_loop_batch_create
+ * groups n <= 64 loops (each on its own handle) that share the control matrix
+ * pointer, the slope count and the mirrors (same descriptions and modal-base
+ * pointers); WFS_EINVAL otherwise.  It keeps the loop pointers (they must
+ * outlive the batch).  wfs_loop_batch_step(b, screens[n], t_s[n],
+ * slopes_out[n], stream) is equivalent, result for result, to wfs_loop_step of
+ * each loop in order on `stream`: the measurements run one after the other,
+ * then the control matrix and each modal base are read once per 4 loops (the
+ * reconstruction and the actuator commands of up to 4 loops share one launch;
+ * each loop's sums keep the single-loop order, so the results are bit for bit
+ * those of separate steps), and all the loops' mirror layers are rebuilt in
+ * launches of up to 64 layers.  Same WFS_EBUSY rule as wfs_loop_step for
+ * every loop.  wfs_loop_batch_destroy frees the batch, not the loops.
+ */
+wfs_status wfs_loop_batch_create(int n, const wfs_loop *loops, wfs_loop_batch *out);
+wfs_status wfs_loop_batch_step(wfs_loop_batch b, const float *const *screens, const double *t_s,
+                               float *const *slopes_out, void *stream);
+wfs_status wfs_loop_batch_destroy(wfs_loop_batch b);
 
 /*
  * wfs_loop_calibrate -- push-pull registration of the interaction matrix of

@@ -167,6 +167,12 @@ struct wfs_loop_ctx {
     cudaStream_t last_stream = nullptr;
 };
 
+// Loops stepped together: they share the control matrix and the mirrors' modal bases, which
+// the reconstruction and the actuator commands then read once for up to kMaxGemvVec loops.
+struct wfs_loop_batch_ctx {
+    std::vector<wfs_loop> loops;
+};
+
 // A batch: the instances' work tables merged, WFS entries grouped by kernel class
 // (kind, n, N, nd) across instances, replayed as one CUDA graph (projection node, then one
 // spot node per class in parallel) whose kernel parameters are rewritten per call.
@@ -2152,6 +2158,124 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
     if ((e = cudaMemcpy(h->d_wfs, h->wfs_host.data(), sizeof(WfsDesc) * h->wfs_host.size(), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(h, e, "work table");
+    return WFS_OK;
+}
+
+
+wfs_status wfs_loop_batch_create(int n, const wfs_loop *loops, wfs_loop_batch *out) {
+    if (!out) return fail(nullptr, WFS_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (n < 1 || n > kMaxInstances || !loops) return fail(nullptr, WFS_EINVAL, "n must be in [1, 64] with a loop array");
+    for (int i = 0; i < n; ++i) {
+        const wfs_loop a = loops[i], b = loops[0];
+        if (!a) return fail(nullptr, WFS_EINVAL, "null loop in batch");
+        for (int j = 0; j < i; ++j)
+            if (loops[j] == a) return fail(nullptr, WFS_EINVAL, "a loop appears twice in the batch");
+        bool same = a->cm == b->cm && a->n_modes == b->n_modes && a->n_slopes == b->n_slopes &&
+                    a->dms.size() == b->dms.size() && a->h->S == b->h->S && a->h->device == b->h->device;
+        for (size_t d = 0; same && d < a->dms.size(); ++d) {
+            const wfs_dm &x = a->dms[d].d, &y = b->dms[d].d;
+            same = x.n_act == y.n_act && x.pitch_m == y.pitch_m && x.alt_m == y.alt_m && x.coupling == y.coupling &&
+                   x.support == y.support && x.n_modes == y.n_modes && x.m2a == y.m2a;
+        }
+        if (!same)
+            return fail(nullptr, WFS_EINVAL, "loops of a batch share the control matrix, the slope count and the mirrors");
+    }
+    wfs_loop_batch b = new wfs_loop_batch_ctx;
+    b->loops.assign(loops, loops + n);
+    *out = b;
+    return WFS_OK;
+}
+
+wfs_status wfs_loop_batch_step(wfs_loop_batch b, const float *const *screens, const double *t_s,
+                               float *const *slopes_out, void *stream) {
+    if (!b || !screens || !t_s || !slopes_out) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)b->loops.size();
+    for (int i = 0; i < n; ++i) {
+        if (!screens[i] || !slopes_out[i] || !is_finite(t_s[i]))
+            return fail(nullptr, WFS_EINVAL, "batch: null buffer or non-finite time for loop " + std::to_string(i));
+        if (loop_busy(b->loops[i], s)) return fail(b->loops[i]->h, WFS_EBUSY, "a loop of the batch is busy on another stream");
+    }
+    // the measurements, one loop after the other
+    for (int i = 0; i < n; ++i) {
+        wfs_loop lp = b->loops[i];
+        wfs_status st = measure_impl(lp->h, screens[i], t_s[i], slopes_out[i], nullptr, s, lp->layers, (int)lp->dms.size());
+        if (st != WFS_OK) return st;
+        lp->last_stream = s;
+    }
+    const wfs_loop l0 = b->loops[0];
+    wfs_handle h0 = l0->h;
+    cudaError_t e;
+    // the integrator, up to kMaxGemvVec loops per read of the control matrix
+    for (int i0 = 0; i0 < n; i0 += kMaxGemvVec) {
+        GemvMultiArgs g{};
+        g.A = l0->cm;
+        g.rows = l0->n_modes;
+        g.cols = l0->n_slopes;
+        g.nb = std::min(kMaxGemvVec, n - i0);
+        for (int k = 0; k < g.nb; ++k) {
+            const wfs_loop lp = b->loops[i0 + k];
+            g.x[k] = slopes_out[i0 + k];
+            g.y[k] = nullptr;
+            g.gain[k] = lp->gain;
+            g.c[k] = lp->coeffs;
+        }
+        long sl = timed_begin(h0, "reconstruct", s);
+        e = launch_gemv_multi(g, s);
+        timed_end(h0, sl, s);
+        if (e != cudaSuccess) return cuda_fail(h0, e, "reconstruction launch");
+    }
+    // actuator commands per mirror (one read of its modal base per kMaxGemvVec loops), then every
+    // loop's layers in launches of up to kMaxInstances
+    for (size_t d = 0; d < l0->dms.size(); ++d) {
+        const LoopDm &M = l0->dms[d];
+        for (int i0 = 0; i0 < n; i0 += kMaxGemvVec) {
+            GemvMultiArgs g{};
+            g.A = M.d.m2a;
+            g.rows = M.d.n_act * M.d.n_act;
+            g.cols = M.d.n_modes;
+            g.nb = std::min(kMaxGemvVec, n - i0);
+            for (int k = 0; k < g.nb; ++k) {
+                const wfs_loop lp = b->loops[i0 + k];
+                g.x[k] = lp->coeffs + lp->dms[d].mode0;
+                g.y[k] = lp->dms[d].act;
+                g.gain[k] = nullptr;
+                g.c[k] = nullptr;
+            }
+            long sl = timed_begin(h0, "dm_actuators", s);
+            e = launch_gemv_multi(g, s);
+            timed_end(h0, sl, s);
+            if (e != cudaSuccess) return cuda_fail(h0, e, "actuator launch");
+        }
+    }
+    static thread_local DmLayerBatch lb;
+    lb.n = 0;
+    auto flush_layers = [&]() -> cudaError_t {
+        if (lb.n == 0) return cudaSuccess;
+        long sl = timed_begin(h0, "dm_layer", s);
+        cudaError_t err = launch_dm_layers(lb, s);
+        timed_end(h0, sl, s);
+        lb.n = 0;
+        return err;
+    };
+    for (int i = 0; i < n; ++i) {
+        const wfs_loop lp = b->loops[i];
+        const size_t SS = (size_t)lp->h->S * lp->h->S;
+        for (size_t d = 0; d < lp->dms.size(); ++d) {
+            if (lb.n == kMaxInstances && (e = flush_layers()) != cudaSuccess) return cuda_fail(h0, e, "mirror layer launch");
+            lb.l[lb.n++] = dm_layer_args(lp->h, lp->dms[d], lp->dms[d].act, 1, 1.0f, lp->layers + d * SS);
+        }
+    }
+    if ((e = flush_layers()) != cudaSuccess) return cuda_fail(h0, e, "mirror layer launch");
+    for (int i = 0; i < n; ++i)
+        if ((e = cudaEventRecord(b->loops[i]->ev_done, s)) != cudaSuccess) return cuda_fail(b->loops[i]->h, e, "completion event");
+    return WFS_OK;
+}
+
+wfs_status wfs_loop_batch_destroy(wfs_loop_batch b) {
+    if (!b) return fail(nullptr, WFS_EINVAL, "null loop batch");
+    delete b;
     return WFS_OK;
 }
 

@@ -151,6 +151,18 @@ struct GemvArgs {                   // y = A x (rows x cols, row-major); c += ga
     float *c;
 };
 
+// The same for nb <= kMaxGemvVec vectors sharing the matrix (read once): column b is computed
+// in exactly the order of a single-vector launch.
+constexpr int kMaxGemvVec = 4;  // 4 vectors: 80 registers, 3 CTAs per SM
+struct GemvMultiArgs {
+    const float *A;
+    int rows, cols, nb;
+    const float *x[kMaxGemvVec];
+    float *y[kMaxGemvVec];
+    const float *gain[kMaxGemvVec];
+    float *c[kMaxGemvVec];
+};
+
 struct DmLayerArgs {                // one mirror's correction layer over a window of the grid
     const float *act;               // actuator commands: act_scale * act[(ay n_act + ax) act_stride]
     int act_stride;                 // 1 for a command vector, n_modes for a modal-base column
@@ -248,6 +260,7 @@ cudaError_t launch_uplink(const InstDesc *inst, const WfsDesc *wfs, int n_wfs, i
                           int *count, const InstDyn *dyn0, cudaStream_t s);
 // Closed-loop kernels.
 cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s);
+cudaError_t launch_gemv_multi(const GemvMultiArgs &a, cudaStream_t s);
 cudaError_t gemv_launch_shape(const GemvArgs &a, LaunchShape *out);
 // Correction layers of n mirrors (or push-pull instances) in one launch, n <= kMaxInstances.
 struct DmLayerBatch {

@@ -21,77 +21,140 @@ constexpr int kGemvRows = 4;  // rows per CTA: each x chunk loaded serves four r
 
 // Four rows per CTA.  All threads walk the rows' 16-byte chunks in step, so each warp reads
 // 512 contiguous bytes of every row per iteration (streaming loads: the matrix is read once),
-// x comes through the read-only path; the CTA then reduces its partial sums in a fixed order.
-template <bool kVec>
-__global__ void __launch_bounds__(kGemvThreads) k_gemv(const __grid_constant__ GemvArgs a) {
+// the NB vectors come through the read-only path; the CTA then reduces its partial sums in a
+// fixed order.  Each (row, vector) pair accumulates in the same order whatever NB is, so a
+// vector's result does not depend on the others it shares the launch with.
+template <int NB, bool kVec>
+__global__ void __launch_bounds__(kGemvThreads) k_gemv(const __grid_constant__ GemvMultiArgs a) {
     const int r0 = blockIdx.x * kGemvRows;
-    float acc[kGemvRows];
+    float acc[kGemvRows][NB];
 #pragma unroll
-    for (int r = 0; r < kGemvRows; ++r) acc[r] = 0.0f;
+    for (int r = 0; r < kGemvRows; ++r)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[r][b] = 0.0f;
     const float *rows[kGemvRows];
 #pragma unroll
     for (int r = 0; r < kGemvRows; ++r) rows[r] = a.A + (size_t)min(r0 + r, a.rows - 1) * a.cols;
     if (kVec) {
         const int n4 = a.cols >> 2;
-        const float4 *x4 = reinterpret_cast<const float4 *>(a.x);
 #pragma unroll 2
         for (int k = threadIdx.x; k < n4; k += kGemvThreads) {
-            const float4 xv = __ldg(x4 + k);
+            float4 xv[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) xv[b] = __ldg(reinterpret_cast<const float4 *>(a.x[b]) + k);
 #pragma unroll
             for (int r = 0; r < kGemvRows; ++r) {
                 const float4 v = __ldcs(reinterpret_cast<const float4 *>(rows[r]) + k);
-                acc[r] = fmaf(v.x, xv.x, acc[r]);
-                acc[r] = fmaf(v.y, xv.y, acc[r]);
-                acc[r] = fmaf(v.z, xv.z, acc[r]);
-                acc[r] = fmaf(v.w, xv.w, acc[r]);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    acc[r][b] = fmaf(v.x, xv[b].x, acc[r][b]);
+                    acc[r][b] = fmaf(v.y, xv[b].y, acc[r][b]);
+                    acc[r][b] = fmaf(v.z, xv[b].z, acc[r][b]);
+                    acc[r][b] = fmaf(v.w, xv[b].w, acc[r][b]);
+                }
             }
         }
     } else {
         for (int k = threadIdx.x; k < a.cols; k += kGemvThreads) {
-            const float xv = __ldg(a.x + k);
+            float xv[NB];
 #pragma unroll
-            for (int r = 0; r < kGemvRows; ++r) acc[r] = fmaf(__ldcs(rows[r] + k), xv, acc[r]);
+            for (int b = 0; b < NB; ++b) xv[b] = __ldg(a.x[b] + k);
+#pragma unroll
+            for (int r = 0; r < kGemvRows; ++r) {
+                const float v = __ldcs(rows[r] + k);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) acc[r][b] = fmaf(v, xv[b], acc[r][b]);
+            }
         }
     }
-    __shared__ float part[kGemvThreads / 32][kGemvRows];
+    __shared__ float part[kGemvThreads / 32][kGemvRows][NB];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int r = 0; r < kGemvRows; ++r) {
-        float v = acc[r];
+    for (int r = 0; r < kGemvRows; ++r)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) part[warp][r] = v;
-    }
+        for (int b = 0; b < NB; ++b) {
+            float v = acc[r][b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) part[warp][r][b] = v;
+        }
     __syncthreads();
-    if (threadIdx.x < kGemvRows) {
-        const int r = threadIdx.x, row = r0 + r;
+    if (threadIdx.x < kGemvRows * NB) {
+        const int r = threadIdx.x % kGemvRows, b = threadIdx.x / kGemvRows, row = r0 + r;
         float y = 0.0f;
 #pragma unroll
-        for (int w = 0; w < kGemvThreads / 32; ++w) y += part[w][r];
+        for (int w = 0; w < kGemvThreads / 32; ++w) y += part[w][r][b];
         if (row < a.rows) {
-            if (a.y) a.y[row] = y;
-            if (a.c) a.c[row] = fmaf(a.gain[row], y, a.c[row]);
+            if (a.y[b]) a.y[b][row] = y;
+            if (a.c[b]) a.c[b][row] = fmaf(a.gain[b][row], y, a.c[b][row]);
         }
     }
 }
 
+namespace {
+template <int NB>
+const void *gemv_func(bool vec) {
+    return vec ? (const void *)k_gemv<NB, true> : (const void *)k_gemv<NB, false>;
+}
+}  // namespace
+
+cudaError_t launch_gemv_multi(const GemvMultiArgs &a, cudaStream_t s) {
+    if (a.rows <= 0 || a.nb <= 0) return cudaSuccess;
+    if (a.nb > kMaxGemvVec) return cudaErrorInvalidValue;
+    const bool vec = (a.cols & 3) == 0 && ((uintptr_t)a.A & 15) == 0;
+    bool aligned = true;
+    for (int b = 0; b < a.nb; ++b) aligned = aligned && ((uintptr_t)a.x[b] & 15) == 0;
+    if (vec && !aligned && a.nb > 1) {
+        // a vector off the 16-byte grid: each vector alone, so that each keeps the summation
+        // order a single-vector launch would give it
+        for (int b = 0; b < a.nb; ++b) {
+            GemvMultiArgs one = a;
+            one.nb = 1;
+            one.x[0] = a.x[b];
+            one.y[0] = a.y[b];
+            one.gain[0] = a.gain[b];
+            one.c[0] = a.c[b];
+            const cudaError_t e = launch_gemv_multi(one, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const void *f = nullptr;
+    switch (a.nb) {
+        case 1: f = gemv_func<1>(vec && aligned); break;
+        case 2: f = gemv_func<2>(vec && aligned); break;
+        case 3: f = gemv_func<3>(vec && aligned); break;
+        default: f = gemv_func<4>(vec && aligned); break;
+    }
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(f, dim3((a.rows + kGemvRows - 1) / kGemvRows), dim3(kGemvThreads), args, 0, s);
+}
+
+namespace {
+GemvMultiArgs one_vector(const GemvArgs &a) {
+    GemvMultiArgs m{};
+    m.A = a.A;
+    m.rows = a.rows;
+    m.cols = a.cols;
+    m.nb = 1;
+    m.x[0] = a.x;
+    m.y[0] = a.y;
+    m.gain[0] = a.gain;
+    m.c[0] = a.c;
+    return m;
+}
+}  // namespace
+
 cudaError_t gemv_launch_shape(const GemvArgs &a, LaunchShape *out) {
     const bool vec = (a.cols & 3) == 0 && ((uintptr_t)a.A & 15) == 0 && ((uintptr_t)a.x & 15) == 0;
-    out->func = vec ? (const void *)k_gemv<true> : (const void *)k_gemv<false>;
+    out->func = gemv_func<1>(vec);
     out->grid = dim3((a.rows + kGemvRows - 1) / kGemvRows);
     out->block = dim3(kGemvThreads);
     out->smem = 0;
     return cudaSuccess;
 }
 
-cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s) {
-    if (a.rows <= 0) return cudaSuccess;
-    LaunchShape sh;
-    cudaError_t e = gemv_launch_shape(a, &sh);
-    if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&a};
-    return cudaLaunchKernel(sh.func, sh.grid, sh.block, args, sh.smem, s);
-}
+cudaError_t launch_gemv(const GemvArgs &a, cudaStream_t s) { return launch_gemv_multi(one_vector(a), s); }
 
 // A CTA computes a 32-column x 64-row tile of the window in two separable passes: first
 // T[ay][j] = sum_ax act[ay][ax] w(u_x(j) - ax) for the actuator rows the tile's rows reach, then

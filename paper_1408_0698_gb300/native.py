@@ -131,6 +131,10 @@ _SIGS = {
     "wfs_loop_calibrate": (C.c_int, [_H, C.c_int, C.c_double, C.c_void_p, C.c_void_p]),
     "wfs_set_uplink": (C.c_int, [_H, C.c_int, C.c_double, C.c_int]),
     "wfs_set_lgs_model": (C.c_int, [_H, C.c_int]),
+    "wfs_loop_batch_create": (C.c_int, [C.c_int, C.POINTER(_H), C.POINTER(_H)]),
+    "wfs_loop_batch_step": (C.c_int, [_H, C.POINTER(C.c_void_p), C.POINTER(C.c_double), C.POINTER(C.c_void_p),
+                                      C.c_void_p]),
+    "wfs_loop_batch_destroy": (C.c_int, [_H]),
 }
 
 
@@ -348,6 +352,25 @@ def wfs_set_uplink(h, gs, diameter_m, samples=16):
 
 def wfs_set_lgs_model(h, per_slice):
     _check(lib().wfs_set_lgs_model(h, int(bool(per_slice))), h)
+
+
+def wfs_loop_batch_create(loops):
+    b = _H()
+    arr = (_H * len(loops))(*loops)
+    _check(lib().wfs_loop_batch_create(len(loops), arr, C.byref(b)))
+    return b
+
+
+def wfs_loop_batch_step(b, screens_ptrs, ts, slopes_ptrs, stream=0):
+    n = len(ts)
+    sp = (C.c_void_p * n)(*screens_ptrs)
+    tt = (C.c_double * n)(*[float(t) for t in ts])
+    op = (C.c_void_p * n)(*slopes_ptrs)
+    _check(lib().wfs_loop_batch_step(b, sp, tt, op, stream))
+
+
+def wfs_loop_batch_destroy(b):
+    _check(lib().wfs_loop_batch_destroy(b))
 
 
 def wfs_loop_destroy(lp):

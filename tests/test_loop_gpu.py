@@ -300,3 +300,68 @@ def test_calibration_elt_m4_full_size():
     ref = oracle.interaction_matrix(cfg, 0, [dm], [M.astype(np.float64)], amp, modes=pick)
     _check_im(im[pick], ref, amp)
     L.close()
+
+
+def test_loop_batch_equals_separate_steps():
+    """Five loops of one system (own handles, screens, seeds and coefficients) stepped as a
+    batch give, bit for bit, the slopes, coefficients and mirror layers of separate steps (the
+    shared reconstruction launch keeps each loop's summation order; four plus one loops)."""
+    cfg = inputs.config2()
+    dms = [inputs.Dm(21, 0.4, 0.0, 14), inputs.Dm(15, 0.7, 6000.0, 6)]
+    m2a = [_dev(inputs.modal_base(d, 60 + i, amplitude_m=2e-8)) for i, d in enumerate(dms)]
+    n = sum(d.n_modes for d in dms)
+    w = native.Wfs(cfg)
+    ns = 2 * w.total
+    w.close()
+    cm = _dev(inputs.random_control_matrix(n, ns, seed=61, scale=0.5))
+    gains = [_dev(np.random.default_rng(70 + i).uniform(0.2, 0.6, n)) for i in range(5)]
+    structs = [native.wfs_dm(d.n_act, d.pitch_m, d.alt_m, d.coupling, d.support, d.n_modes, M.data_ptr())
+               for d, M in zip(dms, m2a)]
+    st = torch.cuda.current_stream().cuda_stream
+    scr = [_dev(inputs.make_screens(cfg.layers, 100 + i)) for i in range(5)]
+    c0 = [_dev(np.random.default_rng(80 + i).standard_normal(n)) for i in range(5)]
+
+    def make():
+        hs, lps = [], []
+        for i in range(5):
+            h = native.Wfs(cfg, seed=90 + i, noise=True)
+            lp = native.wfs_loop_create(h.h, structs, cm.data_ptr(), gains[i].data_ptr())
+            native.wfs_loop_set_coeffs(lp, h.h, c0[i].data_ptr(), st)
+            hs.append(h)
+            lps.append(lp)
+        return hs, lps
+
+    ha, la = make()
+    hb, lb = make()
+    b = native.wfs_loop_batch_create(lb)
+    sa = [torch.zeros((ns // 2, 2), device="cuda") for _ in range(5)]
+    sb = [torch.zeros((ns // 2, 2), device="cuda") for _ in range(5)]
+    for k in range(3):
+        ts = [0.003 * k + 0.001 * i for i in range(5)]
+        for i in range(5):
+            native.wfs_loop_step(la[i], ha[i].h, scr[i].data_ptr(), ts[i], sa[i].data_ptr(), st)
+        native.wfs_loop_batch_step(b, [x.data_ptr() for x in scr], ts, [x.data_ptr() for x in sb], st)
+        torch.cuda.synchronize()
+        for i in range(5):
+            assert torch.equal(sa[i], sb[i]), f"step {k} loop {i} slopes"
+    ca, cb = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    la_, lb_ = torch.zeros((512, 512), device="cuda"), torch.zeros((512, 512), device="cuda")
+    for i in range(5):
+        native.wfs_loop_get_coeffs(la[i], ha[i].h, ca.data_ptr(), st)
+        native.wfs_loop_get_coeffs(lb[i], hb[i].h, cb.data_ptr(), st)
+        torch.cuda.synchronize()
+        assert torch.equal(ca, cb), f"loop {i} coefficients"
+        for d in range(2):
+            native.wfs_loop_get_layer(la[i], ha[i].h, d, la_.data_ptr(), st)
+            native.wfs_loop_get_layer(lb[i], hb[i].h, d, lb_.data_ptr(), st)
+            torch.cuda.synchronize()
+            assert torch.equal(la_, lb_), f"loop {i} mirror {d}"
+    # a loop with another control matrix does not join the batch
+    other = torch.zeros_like(cm)
+    h = native.Wfs(cfg)
+    lo = native.wfs_loop_create(h.h, structs, other.data_ptr(), gains[0].data_ptr())
+    with pytest.raises(native.WfsError, match="WFS_EINVAL"):
+        native.wfs_loop_batch_create([lb[0], lo])
+    native.wfs_loop_batch_destroy(b)
+    for x in ha + hb + [h]:
+        x.close()
