@@ -365,3 +365,30 @@ def test_loop_batch_equals_separate_steps():
     native.wfs_loop_batch_destroy(b)
     for x in ha + hb + [h]:
         x.close()
+
+
+def test_loop_step_with_uplink():
+    """A loop step of LGS with the uplink tip-tilt on: the launch beam crosses the turbulent
+    layers only, not the mirrors' correction layers (the oracle marks them as mirror layers)."""
+    import dataclasses
+    cfg = inputs.config2()
+    cfg = dataclasses.replace(cfg, stars=[dataclasses.replace(s, uplink_diameter_m=0.5, uplink_samples=16)
+                                          if s.is_lgs else s for s in cfg.stars])
+    scr = inputs.make_screens(cfg.layers, cfg.seed + 3)
+    dms = [inputs.Dm(21, 0.4, 0.0, 10), inputs.Dm(15, 0.7, 6000.0, 5)]
+    m2a = [inputs.modal_base(d, 40 + i, amplitude_m=3e-8) for i, d in enumerate(dms)]
+    n = sum(d.n_modes for d in dms)
+    w = native.Wfs(cfg)
+    ns = 2 * w.total
+    w.close()
+    cm = inputs.random_control_matrix(n, ns, seed=41, scale=0.5)
+    gain = np.full(n, 0.5)
+    c = np.random.default_rng(42).standard_normal(n)
+    L = _Loop(cfg, dms, m2a, cm, gain)
+    L.set_coeffs(c)
+    s_gpu = L.step(_dev(scr), 0.004)
+    s_ref, c_ref = oracle.loop_step(cfg, scr, 0.004, dms, m2a, cm, gain, c.astype(np.float32).astype(np.float64))
+    assert slope_rms(s_gpu, s_ref) < SLOPE_RMS
+    assert np.abs(s_gpu - s_ref).max() < SLOPE_MAX
+    assert np.all(np.abs(L.coeffs() - c_ref) <= _coeff_tol(cm, gain, 1) + 1e-5 * np.abs(c_ref))
+    L.close()
