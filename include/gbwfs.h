@@ -498,10 +498,11 @@ wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples);
  * 1/2 |x - r_L|^2 (1/h0 - 1/h_s) (h0 = the star's range, the focus; r_L the
  * launch point), one DFT per slice, I = sum_s w_s |DFT|^2, then the Gaussian
  * extent alone, binning, photometry, noise and centroid as in model 0.  It
- * runs on a self-projecting variant of the geometry's spot kernel (the
- * tensor-core BF16x3 or FP32 32-point kernel where the geometry has one, else
- * the generic FP32 kernel; one DFT per slice: n_na times the DFT work); the
- * OPD stage output
+ * runs on per-slice variants of the spot kernels (on the 32-point geometries
+ * one projection launch makes every slice's OPD and the tensor-core BF16x3 or
+ * FP32 kernel's variant reads them; other geometries use the generic FP32
+ * kernel, which projects each slice itself; one DFT per slice: n_na times the
+ * DFT work); the OPD stage output
  * holds the first slice's OPD without its geometric term.  Waits for the
  * handle's measurement in flight and updates its work tables (the first switch
  * to 1 also builds the Gaussian tables, synchronously).  Batches and

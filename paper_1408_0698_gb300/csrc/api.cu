@@ -44,8 +44,9 @@ struct SpotGroup {
     int kind = 0;            // SpotKind
     int grid_cap = 0, cta_warps = 0;
     int proj_base = 0, proj_count = 0;  // this group's projection blocks
-    // LGS per-slice model: the group runs the self-projecting generic kernel; the kind and
-    // launch shape of the elongation-kernel model are kept to restore it
+    // LGS per-slice model: the group runs a per-slice spot kernel (the 32-point kernels' variants
+    // after a projection of every (WFS, slice) pair, else the self-projecting generic kernel); the
+    // kind and launch shape of the elongation-kernel model are kept to restore it
     bool per_slice = false;
     int base_kind = 0, base_grid_cap = 0, base_cta_warps = 0;
     // 32-point kernels: the per-slice OPDs come from one projection of every (WFS, slice) pair
@@ -2103,8 +2104,8 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             G.base_kind = G.kind;
             G.base_grid_cap = G.grid_cap;
             G.base_cta_warps = G.cta_warps;
-            // the self-projecting variant of the geometry's 32-point kernel (tensor-core or FP32)
-            // where it has one, else the generic kernel
+            // the per-slice variant of the geometry's 32-point kernel (tensor-core or FP32) where
+            // it has one, else the self-projecting generic kernel
             const wfs_geometry &geo = h->geoms[G.geom].g;
             if (G.kind != kSpotTc)
                 G.kind = sh_n32_supported(geo.n_pix_sub, geo.n_fft, geo.n_det) ? kSpotN32 : kSpotGeneric;

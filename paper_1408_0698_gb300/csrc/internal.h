@@ -67,8 +67,8 @@ struct WfsDesc {                    // static per wavefront sensor
     float2 *uplink;
     double launch_x, launch_y, up_diam;
     int up_n;
-    // LGS per-slice model (null: one projection and the elongation kernel); read by the
-    // self-projecting generic spot kernel, whose ktil then holds the Gaussian extent alone
+    // LGS per-slice model (null: one projection and the elongation kernel); read by the per-slice
+    // spot kernels, for which ktil holds the Gaussian extent alone
     const SliceDesc *slices;
 };
 

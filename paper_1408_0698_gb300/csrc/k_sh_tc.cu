@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     if (wib == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_all), "r"(kTmemCols));
 }
 
-// The self-projecting per-slice variant (see the file comment).
+// The per-slice variant (see the file comment).
 template <int n, int nd>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constant__ ShArgs a) {
     constexpr bool kSlices = true;
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
         const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
         const InstDyn &D = a.dyn[W.inst];
         const int v = active ? g - W.subap_begin : 0;
-        // K~ of this subaperture: (2n-1) n complex = 16-byte chunks (n even); the self-projecting
+        // K~ of this subaperture: (2n-1) n complex = 16-byte chunks (n even); the per-slice
         // variant stages it after its slices, whose summed rows share the space
         auto stage_ktil = [&]() {
             const float4 *src = reinterpret_cast<const float4 *>(W.ktil + (size_t)v * (D2 * n));
