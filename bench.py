@@ -702,7 +702,7 @@ def time_per_slice(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, sp
     w4.close()
     n_sl = len(cfg.stars[0].na_alt_m)
     line["per_slice_path"] = {"value": spots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k4,
-                              "model": f"per-slice LGS, {n_sl} slices (one wavefront and DFT each), FP32",
+                              "model": f"per-slice LGS, {n_sl} slices (one wavefront and DFT each): one projection of every (LGS, slice) pair, tensor-core per-slice spot kernel",
                               "kernels": kt}
 
 
