@@ -495,6 +495,22 @@ def test_oracle_regression_fixtures():
     ref = np.loadtxt(f"{GOLDEN}/config2_lgs1_t0.01_slopes.txt")
     s = oracle.measure_wfs(cfg, scr, 1, 0.01, sel=ref[:, 0].astype(np.int32))["slopes"]
     assert np.allclose(s, ref[:, 1:], rtol=0, atol=1e-12)
+    st = dataclasses.replace(cfg.stars[0], per_slice=True, uplink_diameter_m=0.5, uplink_samples=16)
+    ref = np.loadtxt(f"{GOLDEN}/config2_lgs0_slices_uplink_t0.01_slopes.txt")
+    s = oracle.measure_wfs(dataclasses.replace(cfg, stars=[st] + cfg.stars[1:]), scr, 0, 0.01,
+                           sel=ref[:, 0].astype(np.int32))["slopes"]
+    assert np.allclose(s, ref[:, 1:], rtol=0, atol=1e-12)
+    cfg = inputs.config1()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    dm = inputs.Dm(21, 0.4, 0.0, 12)
+    M = inputs.modal_base(dm, 5, amplitude_m=2e-8).astype(np.float64)
+    cm = inputs.random_control_matrix(12, 2 * 316, seed=6, scale=0.5).astype(np.float64)
+    ref = np.loadtxt(f"{GOLDEN}/config1_loop_step_coeffs.txt")
+    _, c1 = oracle.loop_step(cfg, scr, 0.002, [dm], [M], cm, np.full(12, 0.4), ref[:, 0])
+    assert np.allclose(c1, ref[:, 1], rtol=0, atol=1e-12)
+    ref = np.loadtxt(f"{GOLDEN}/config1_interaction_rows.txt")
+    im = oracle.interaction_matrix(cfg, 0, [dm], [M], 0.5, modes=[0, 5, 11])
+    assert np.allclose(im.T, ref, rtol=0, atol=1e-12)
 
 
 # ---------------------------------------------------------------- closed loop: mirrors
