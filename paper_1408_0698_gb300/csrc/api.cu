@@ -659,6 +659,44 @@ wfs_status refresh_slices(wfs_handle h) {
     return e == cudaSuccess ? WFS_OK : cuda_fail(h, e, "slice tables");
 }
 
+// 32-point kernels read per-slice OPDs made by one projection launch over copies of the WFS
+// entries whose range is the slice altitude (the cone) and whose OPD goes to slice s; the copies
+// follow the work table (rebuilt when it changes, e.g. the uplink switch).
+wfs_status build_slice_projection(wfs_handle h) {
+    cudaError_t e;
+    for (SpotGroup &G : h->groups) {
+        cudaFree(G.d_sl_wfs);
+        G.d_sl_wfs = nullptr;
+        if (!G.sl_projected) continue;
+        std::vector<WfsDesc> t;
+        int blocks = 0;
+        for (int q = 0; q < G.count; ++q) {
+            const WfsDesc &d0 = h->wfs_host[G.first + q];
+            const GsDev &gd = h->gs[d0.gs_index];
+            const size_t ns = d0.is_lgs ? gd.na_alt.size() : 1;
+            for (size_t sl = 0; sl < ns; ++sl) {
+                WfsDesc d = d0;
+                if (d0.is_lgs) d.range_m = gd.na_alt[sl];
+                d.opd_off = d0.opd_off + (long long)(sl * h->opd_total);
+                d.proj_block_begin = blocks;
+                blocks += project_blocks(d);
+                t.push_back(d);
+            }
+        }
+        G.sl_count = (int)t.size();
+        G.sl_blocks = blocks;
+        if ((e = upload(&G.d_sl_wfs, t)) != cudaSuccess) return cuda_fail(h, e, "slice projection table");
+        if (!h->d_opd_sl) {
+            size_t n_max = 1;
+            for (const GsDev &gd : h->gs)
+                if (gd.gs.is_lgs) n_max = std::max(n_max, gd.na_alt.size());
+            if ((e = cudaMalloc(&h->d_opd_sl, sizeof(float) * h->opd_total * n_max)) != cudaSuccess)
+                return cuda_fail(h, e, "slice OPDs");
+        }
+    }
+    return WFS_OK;
+}
+
 // Actuator commands (modal base times the mirror's coefficients) and correction layer of every
 // mirror of the loop, on stream s.
 // Layer arguments of mirror M with commands act_scale * act[i * act_stride].
@@ -2048,6 +2086,7 @@ wfs_status wfs_set_uplink(wfs_handle h, int gs, double diameter_m, int samples) 
     if (on != (g.up_diam > 0)) h->n_uplink += on ? 1 : -1;
     g.up_diam = on ? diameter_m : 0.0;
     g.up_n = on ? samples : 0;
+    if (h->per_slice) return build_slice_projection(h);  // the slice copies carry the uplink too
     return WFS_OK;
 }
 
@@ -2123,39 +2162,9 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             d.slices = per_slice ? h->d_slices + d.gs_index : nullptr;
             d.ktil = per_slice ? gd.d_ktil_g : gd.d_ktil;
         }
-        // 32-point kernels read per-slice OPDs made by one projection launch over copies of the
-        // WFS entries whose range is the slice altitude (the cone) and whose OPD goes to slice s
-        cudaFree(G.d_sl_wfs);
-        G.d_sl_wfs = nullptr;
         G.sl_projected = per_slice && (G.kind == kSpotTc || G.kind == kSpotN32);
-        if (G.sl_projected) {
-            std::vector<WfsDesc> t;
-            int blocks = 0;
-            for (int q = 0; q < G.count; ++q) {
-                const WfsDesc &d0 = h->wfs_host[G.first + q];
-                const GsDev &gd = h->gs[d0.gs_index];
-                const size_t ns = d0.is_lgs ? gd.na_alt.size() : 1;
-                for (size_t sl = 0; sl < ns; ++sl) {
-                    WfsDesc d = d0;
-                    if (d0.is_lgs) d.range_m = gd.na_alt[sl];
-                    d.opd_off = d0.opd_off + (long long)(sl * h->opd_total);
-                    d.proj_block_begin = blocks;
-                    blocks += project_blocks(d);
-                    t.push_back(d);
-                }
-            }
-            G.sl_count = (int)t.size();
-            G.sl_blocks = blocks;
-            if ((e = upload(&G.d_sl_wfs, t)) != cudaSuccess) return cuda_fail(h, e, "slice projection table");
-            if (!h->d_opd_sl) {
-                size_t n_max = 1;
-                for (const GsDev &gd : h->gs)
-                    if (gd.gs.is_lgs) n_max = std::max(n_max, gd.na_alt.size());
-                if ((e = cudaMalloc(&h->d_opd_sl, sizeof(float) * h->opd_total * n_max)) != cudaSuccess)
-                    return cuda_fail(h, e, "slice OPDs");
-            }
-        }
     }
+    if (build_slice_projection(h) != WFS_OK) return WFS_ECUDA;
     if ((e = cudaMemcpy(h->d_wfs, h->wfs_host.data(), sizeof(WfsDesc) * h->wfs_host.size(), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(h, e, "work table");

@@ -107,3 +107,21 @@ def test_per_slice_closed_loop_step():
     with pytest.raises(native.WfsError, match="WFS_EUNSUPPORTED"):
         native.wfs_loop_calibrate(lp, w.h, 0, 1.0, out.data_ptr(), st)
     w.close()
+
+
+def test_per_slice_then_uplink_elt():
+    """The uplink switched on after the per-slice model (the slice projection copies follow the
+    work table): sampled ELT subapertures against the oracle with both."""
+    base = _per_slice(inputs.config3())
+    both = _per_slice(inputs.config3(), uplink_diameter_m=0.4, uplink_samples=16)
+    scr = inputs.make_screens(base.layers, base.seed + 2)
+    w = native.Wfs(base)
+    for k, s in enumerate(base.stars):
+        if s.is_lgs:
+            native.wfs_set_uplink(w.h, k, 0.4, 16)
+    t = 0.02
+    gpu, _ = run_library(both, scr, t, handle=w)
+    sel = [np.arange(3 * k, len(d["slopes"]), 211, dtype=np.int32) if both.stars[k].is_lgs
+           else np.arange(len(d["slopes"]), dtype=np.int32) for k, d in enumerate(gpu)]
+    _check_wfs(both, scr, t, gpu, sel=sel)
+    w.close()
