@@ -79,6 +79,14 @@ def test_null_arguments():
     assert L.wfs_loop_get_coeffs(None, None, None) == native.WFS_EINVAL
     assert L.wfs_loop_get_layer(None, 0, None, None) == native.WFS_EINVAL
     assert L.wfs_loop_destroy(None) == native.WFS_EINVAL
+    assert L.wfs_loop_calibrate(None, 0, 1.0, None, None) == native.WFS_EINVAL
+    b = native._H()
+    assert L.wfs_loop_batch_create(0, None, C.byref(b)) == native.WFS_EINVAL
+    assert L.wfs_loop_batch_create(1, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_batch_step(None, None, None, None, None) == native.WFS_EINVAL
+    assert L.wfs_loop_batch_destroy(None) == native.WFS_EINVAL
+    assert L.wfs_set_uplink(None, 0, 0.5, 16) == native.WFS_EINVAL
+    assert L.wfs_set_lgs_model(None, 1) == native.WFS_EINVAL
 
 
 def test_no_silent_cpu_path_without_gpu():
