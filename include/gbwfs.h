@@ -57,7 +57,9 @@ typedef enum {
     WFS_ECUDA = 3,        /* a CUDA runtime call failed */
     WFS_EBUSY = 4,        /* handle in use */
     WFS_ETIMEOUT = 5,     /* a bounded device wait gave up */
-    WFS_EUNSUPPORTED = 6  /* valid request this build does not implement */
+    WFS_EUNSUPPORTED = 6, /* valid request this build does not implement */
+    WFS_EBOUNDS = 7       /* the bounds-checked build (GBWFS_CHECK) met an out-of-range index
+                             in a kernel and skipped that access (never in the normal build) */
 } wfs_status;
 
 /* DFT arithmetic of a geometry (the rest of the path is FP32 throughout). */

@@ -11,6 +11,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libgbwfs.so")
+# The bounds-checked build (-DGBWFS_CHECK): kernels test their global indices, record WFS_EBOUNDS
+# and skip an out-of-range access; a debugging stand-in for a memory checker.
+CHECK_BUILD = os.path.join(BUILD, "check")
+CHECK_SO = os.path.join(CHECK_BUILD, "libgbwfs_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,25 +34,27 @@ def _deps():
     return out
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(SO):
+def up_to_date(so: str = SO) -> bool:
+    if not os.path.exists(so):
         return False
-    t = os.path.getmtime(SO)
+    t = os.path.getmtime(so)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    if not force and up_to_date():
-        return SO
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list | None = None, check: bool = False) -> str:
+    """Compiles the library (check=True: the bounds-checked build, in its own folder)."""
+    out_dir, so = (CHECK_BUILD, CHECK_SO) if check else (BUILD, SO)
+    if not force and up_to_date(so):
+        return so
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                     "-I", os.path.join(ROOT, "include")] + (extra or [])
+                     "-I", os.path.join(ROOT, "include")] + (["-DGBWFS_CHECK"] if check else []) + (extra or [])
     if verbose:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [cc, "-c", src, "-o", obj] + common
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -60,14 +66,14 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     if verbose:
         for _, log in results:
             print(log)
-    tmp = SO + f".{os.getpid()}.tmp"
+    tmp = so + f".{os.getpid()}.tmp"
     cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + [
         "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, SO)
-    return SO
+    os.replace(tmp, so)
+    return so
 
 
 if __name__ == "__main__":

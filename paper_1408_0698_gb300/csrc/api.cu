@@ -12,6 +12,7 @@
 // Per frame: one projection launch for all guide stars, then one spot launch
 // per geometry.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstddef>
@@ -23,6 +24,29 @@
 
 #include "../../include/gbwfs.h"
 #include "internal.h"
+
+namespace {
+// One NVTX range per public compute call, in the domain "gbwfs", so that a profiler groups each
+// call's kernels under its name (e.g. ncu --nvtx --nvtx-include "gbwfs@wfs_measure/").  NVTX is
+// header-only; without a tool attached each push and pop is a test of a null function pointer.
+nvtxDomainHandle_t nvtx_domain() {
+    static const nvtxDomainHandle_t d = nvtxDomainCreateA("gbwfs");
+    return d;
+}
+struct NvtxRange {
+    explicit NvtxRange(const char *name) {
+        nvtxEventAttributes_t a{};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        nvtxDomainRangePushEx(nvtx_domain(), &a);
+    }
+    ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 using namespace gbwfs;
 
@@ -842,7 +866,11 @@ void gbwfs::set_thread_error(const char *msg) { tl_error = msg ? msg : ""; }
 
 extern "C" {
 
+#ifdef GBWFS_CHECK
+const char *wfs_version(void) { return "gbwfs 0.1 (sm_103a, bounds-checked)"; }
+#else
 const char *wfs_version(void) { return "gbwfs 0.1 (sm_103a)"; }
+#endif
 
 const char *wfs_last_error(wfs_handle h) { return h ? h->err.c_str() : tl_error.c_str(); }
 
@@ -1125,16 +1153,19 @@ wfs_status wfs_destroy(wfs_handle h) {
 }
 
 wfs_status wfs_measure(wfs_handle h, const float *screens, double t_s, float *slopes_out, void *stream) {
+    const NvtxRange nvtx_range("wfs_measure");
     return measure_impl(h, screens, t_s, slopes_out, nullptr, (cudaStream_t)stream);
 }
 
 wfs_status wfs_measure_stages(wfs_handle h, const float *screens, double t_s, float *slopes_out,
                               const wfs_stage_out *stages, void *stream) {
+    const NvtxRange nvtx_range("wfs_measure_stages");
     return measure_impl(h, screens, t_s, slopes_out, stages, (cudaStream_t)stream);
 }
 
 wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s, float *slopes_host,
                             void *stream) {
+    const NvtxRange nvtx_range("wfs_measure_host");
     if (!h) return fail(nullptr, WFS_EINVAL, "null handle");
     if (!screens_host || !slopes_host) return fail(h, WFS_EINVAL, "null host buffer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1279,6 +1310,7 @@ wfs_status wfs_check_bounded_wait(wfs_handle h, int polls, void *stream) {
 
 wfs_status wfs_noise_apply(const float *expected, int n, float read_noise_e, uint64_t seed,
                            uint32_t wfs_index, double t_s, uint32_t pixel0, float *counts, void *stream) {
+    const NvtxRange nvtx_range("wfs_noise_apply");
     if (!expected || !counts || n < 0) return fail(nullptr, WFS_EINVAL, "bad noise arguments");
     if (wfs_index >= (1u << 16)) return fail(nullptr, WFS_EINVAL, "wfs_index must be < 65536");
     if (!(read_noise_e >= 0) || !is_finite(t_s)) return fail(nullptr, WFS_EINVAL, "bad read noise or time");
@@ -1591,6 +1623,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
 
 wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const double *t_s,
                              float *const *slopes_out, void *stream) {
+    const NvtxRange nvtx_range("wfs_batch_measure");
     if (!b || !screens || !t_s || !slopes_out) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
     int dev = -1;
     cudaGetDevice(&dev);
@@ -1618,6 +1651,7 @@ wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const dou
 wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const int *active,
                                     const float *const *screens, const double *t_s, float *const *slopes_out,
                                     void *stream) {
+    const NvtxRange nvtx_range("wfs_batch_measure_subset");
     if (!b || (n_active > 0 && (!active || !screens || !t_s || !slopes_out)) || n_active < 0)
         return fail(nullptr, WFS_EINVAL, "bad batch subset arguments");
     if (slot < 0 || slot >= kBatchSlots) return fail(nullptr, WFS_EINVAL, "batch subset slot out of range");
@@ -1722,6 +1756,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
 
 wfs_status wfs_batch_tune(wfs_batch b, const float *const *screens, const double *t_s, float *const *slopes_out,
                           void *stream) {
+    const NvtxRange nvtx_range("wfs_batch_tune");
     if (!b || !screens || !t_s || !slopes_out) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
     wfs_status st = batch_fill(b, screens, t_s, slopes_out);
     if (st != WFS_OK) return st;
@@ -1896,6 +1931,7 @@ wfs_status wfs_loop_create(wfs_handle h, int n_dm, const wfs_dm *dms, const floa
 }
 
 wfs_status wfs_loop_step(wfs_loop lp, const float *screens, double t_s, float *slopes_out, void *stream) {
+    const NvtxRange nvtx_range("wfs_loop_step");
     if (!lp) return fail(nullptr, WFS_EINVAL, "null loop");
     wfs_handle h = lp->h;
     const cudaStream_t s = (cudaStream_t)stream;
@@ -1956,6 +1992,7 @@ wfs_status wfs_loop_destroy(wfs_loop lp) {
 
 
 wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_out, void *stream) {
+    const NvtxRange nvtx_range("wfs_loop_calibrate");
     if (!lp) return fail(nullptr, WFS_EINVAL, "null loop");
     wfs_handle h = lp->h;
     if (gs < 0 || gs >= (int)h->gs.size()) return fail(h, WFS_EINVAL, "guide star index out of range");
@@ -2199,6 +2236,7 @@ wfs_status wfs_loop_batch_create(int n, const wfs_loop *loops, wfs_loop_batch *o
 
 wfs_status wfs_loop_batch_step(wfs_loop_batch b, const float *const *screens, const double *t_s,
                                float *const *slopes_out, void *stream) {
+    const NvtxRange nvtx_range("wfs_loop_batch_step");
     if (!b || !screens || !t_s || !slopes_out) return fail(nullptr, WFS_EINVAL, "bad batch arguments");
     const cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)b->loops.size();

@@ -177,6 +177,20 @@ struct DmLayerArgs {                // one mirror's correction layer over a wind
 };
 
 #ifdef __CUDACC__
+// Bounds checks of the checked build (-DGBWFS_CHECK, a stand-in for a memory checker): guard
+// records WFS_EBOUNDS (7) in the status word and returns false when ok is false, and the caller
+// then skips the access; in the normal build it is the constant true and costs nothing.
+__device__ __forceinline__ bool guard(bool ok, int *status) {
+#ifdef GBWFS_CHECK
+    if (!ok && status) atomicCAS(status, 0, 7);
+    return ok;
+#else
+    (void)ok;
+    (void)status;
+    return true;
+#endif
+}
+
 // The WFS of a launch that owns global subaperture g (binary search on subap_begin).
 __device__ __forceinline__ int find_wfs(const WfsDesc *w, int n, int g) {
     int lo = 0, hi = n - 1;

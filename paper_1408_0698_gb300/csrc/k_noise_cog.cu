@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(32 * kNcWarps, 4) k_noise_cog(const __grid_con
     const WfsDesc &W = a.wfs[find_wfs(a.wfs, a.n_wfs, g)];
     const InstDyn &D = a.dyn[W.inst];
     const int v = g - W.subap_begin;
+    if (!guard(v >= 0 && v < W.n_valid, a.status)) return;
     constexpr int J = nd / 2;
     const int ix = lane & 15, half = lane >> 4;
     const float *E = D.st_E + W.det_off + (size_t)v * (nd * nd);

@@ -121,6 +121,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
                     const float *srow = scr + (size_t)wrap_index(s_off[l].bv + by0 + r, S, pow2) * S;
                     float *drow = box + r * bw;
                     for (int c4 = lane; c4 < cw; c4 += 32) {
+                        if (!guard(r * bw + 4 * c4 + 3 < box_floats, a.status)) continue;
                         const float *src = srow + wrap_index(cbase + 4 * c4, S, pow2);
                         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(drow + 4 * c4);
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -130,6 +131,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
                 for (int r = 0; r < bh; ++r) {
                     const float *grow = scr + (size_t)wrap_index(s_off[l].bv + by0 + r, S, pow2) * S;
                     for (int c = threadIdx.x; c < bw; c += kProjThreads) {
+                        if (!guard(r * bw + c < box_floats, a.status)) continue;
                         const float *src = grow + wrap_index(s_off[l].bu + bx0 + c, S, pow2);
                         const uint32_t dst = (uint32_t)__cvta_generic_to_shared(box + r * bw + c);
                         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
@@ -168,6 +170,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
                     if (j < ncol) {
                         const float2 cj = t[j];
                         const float *b0 = brow + __float_as_int(cj.x);
+                        if (!guard(b0 >= box && b0 + bw + 1 < box + box_floats, a.status)) continue;
                         const float s00 = b0[0], s01 = b0[1], s10 = b0[bw], s11 = b0[bw + 1];
                         const float top = fmaf(cj.y, s01 - s00, s00);
                         const float bot = fmaf(cj.y, s11 - s10, s10);
@@ -212,6 +215,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
     const int blk = (bid - W.proj_block_begin) * kProjThreads + threadIdx.x;
     if (blk >= W.n_valid * nbb) return;
     const int v = blk / nbb, r = blk - v * nbb, bp = r / nb, bq = r - bp * nb;
+    if (!guard(v < W.n_valid, a.status)) return;
     const int p0 = 2 * bp, q0 = 2 * bq;
     const int id = __ldg(W.subap + v);
     const int sy = id / W.n_sub, sx = id - sy * W.n_sub;
@@ -238,6 +242,10 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
             screen_offset(lo.c, lo.cl, lo.fv, yr[j], ov, gy[j]);
             wrap_pair(lo.bu + ou, S, pow2, ci0[j], ci1[j]);
             wrap_pair(lo.bv + ov, S, pow2, j0, j1);
+            if (!guard(ci0[j] >= 0 && ci0[j] < S && ci1[j] >= 0 && ci1[j] < S && j0 >= 0 && j0 < S && j1 >= 0 && j1 < S,
+                       a.status)) {
+                ci0[j] = ci1[j] = j0 = j1 = 0;  // a checked build reads a valid sample instead
+            }
             row0[j] = scr + (size_t)j0 * S;
             row1[j] = scr + (size_t)j1 * S;
         }

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
         const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
         const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
         const int v = g - W.subap_begin;
+        if (!guard(v >= 0 && v < W.n_valid, a.status)) continue;  // uniform over the team
         float *st_I = D.st_I ? D.st_I + W.int_off : nullptr;
         float *st_E = D.st_E ? D.st_E + W.det_off : nullptr;
         float *st_C = D.st_C ? D.st_C + W.det_off : nullptr;
@@ -183,6 +184,9 @@ __global__ void __launch_bounds__(TEAM > 256 ? TEAM : 256) k_sh_fp32(const __gri
                         screen_offset(ch, cl, L0.fv, yr, ov, gy);
                         wrap_pair(L0.bu + ou, S, pow2, i0, i1);
                         wrap_pair(L0.bv + ov, S, pow2, j0, j1);
+                        if (!guard(i0 >= 0 && i1 < S && i1 >= 0 && j0 >= 0 && j1 < S && j1 >= 0 && i0 < S && j0 < S,
+                                   a.status))
+                            continue;
                         const float *scr = layer_screen(I, D, l);
                         const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
                         const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);

@@ -98,6 +98,10 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
         const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
         const int v = g - W.subap_begin;
         __syncwarp();
+        if (!guard(v >= 0 && v < W.n_valid, a.status)) {  // uniform over the warp
+            g = a.work ? nwarps + __shfl_sync(0xffffffffu, ticket, 0) : g + nwarps;
+            continue;
+        }
 
         const SliceDesc *SD = kSlices ? W.slices : nullptr;
         const int n_sl = SD ? SD->n : 1;

@@ -254,10 +254,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         int ticket = 0;
         if (a.work && issuer) ticket = atomicAdd(a.work, 1);
         const int g = 4 * grp + wq;
-        const bool active = g < a.total;
+        bool active = g < a.total;
         const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
         const InstDyn &D = a.dyn[W.inst];
         const int v = active ? g - W.subap_begin : 0;
+        active = active && guard(v >= 0 && v < W.n_valid, a.status);
         if (active && W.is_lgs) {
             // K~ of this subaperture: (2n-1) n complex = 16-byte chunks (n even)
             const float4 *src = reinterpret_cast<const float4 *>(W.ktil + (size_t)v * (D2 * n));
@@ -511,10 +512,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
         int ticket = 0;
         if (a.work && issuer) ticket = atomicAdd(a.work, 1);
         const int g = 4 * grp + wq;
-        const bool active = g < a.total;
+        bool active = g < a.total;
         const WfsDesc &W = a.wfs[active ? find_wfs(a.wfs, a.n_wfs, g) : 0];
         const InstDyn &D = a.dyn[W.inst];
         const int v = active ? g - W.subap_begin : 0;
+        active = active && guard(v >= 0 && v < W.n_valid, a.status);
         // K~ of this subaperture: (2n-1) n complex = 16-byte chunks (n even); the per-slice
         // variant stages it after its slices, whose summed rows share the space
         auto stage_ktil = [&]() {

@@ -18,9 +18,9 @@ import numpy as np
 
 from . import build as _build
 
-WFS_OK, WFS_EINVAL, WFS_ENOMEM, WFS_ECUDA, WFS_EBUSY, WFS_ETIMEOUT, WFS_EUNSUPPORTED = range(7)
+WFS_OK, WFS_EINVAL, WFS_ENOMEM, WFS_ECUDA, WFS_EBUSY, WFS_ETIMEOUT, WFS_EUNSUPPORTED, WFS_EBOUNDS = range(8)
 STATUS_NAMES = ["WFS_OK", "WFS_EINVAL", "WFS_ENOMEM", "WFS_ECUDA", "WFS_EBUSY", "WFS_ETIMEOUT",
-                "WFS_EUNSUPPORTED"]
+                "WFS_EUNSUPPORTED", "WFS_EBOUNDS"]
 WFS_PREC_FP32, WFS_PREC_BF16X3, WFS_PREC_FP16S = 0, 1, 2
 
 
@@ -147,11 +147,16 @@ def header_symbols(path=None):
 
 
 def lib(build_if_missing: bool = True):
-    """Load libgbwfs.so (building it first if stale and allowed)."""
+    """Load libgbwfs.so (building it first if stale and allowed); with the environment variable
+    GBWFS_CHECKED=1, the bounds-checked build instead."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build_if_missing else _build.SO
+            checked = os.environ.get("GBWFS_CHECKED") == "1"
+            if build_if_missing:
+                path = _build.build(check=checked)
+            else:
+                path = _build.CHECK_SO if checked else _build.SO
             if not os.path.exists(path):
                 raise RuntimeError(f"libgbwfs.so not built ({path}); run __graft_entry__.build()")
             L = C.CDLL(path)

@@ -2,6 +2,9 @@
 rejects bad descriptions synchronously, before any device work."""
 import ctypes as C
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -17,6 +20,20 @@ def test_library_exports_every_header_symbol():
     assert not missing, missing
     assert set(names) == set(native._SIGS), "binding and header disagree"
     assert "sm_103a" in native.wfs_version()
+
+
+def test_checked_library_exports_the_same_symbols():
+    """The bounds-checked build (-DGBWFS_CHECK) compiles from the same sources and exports the
+    same entry points; it names itself in the version string."""
+    code = ("from paper_1408_0698_gb300 import native; L = native.lib(); "
+            "names = native.header_symbols(); "
+            "assert all(hasattr(L, n) for n in names); "
+            "assert L._name.endswith('libgbwfs_check.so'); print(native.wfs_version())")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900,
+                       env=dict(os.environ, GBWFS_CHECKED="1"),
+                       cwd=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "bounds-checked" in r.stdout
 
 
 def _create(cfg, **kw):
