@@ -77,9 +77,12 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
         const int nch = (ncol + kTilePx - 1) / kTilePx, ntask = n * nch;  // ntask <= kProjThreads
         const bool has_task = (int)threadIdx.x < ntask;
         const int p = has_task ? (int)threadIdx.x / nch : 0, ch = (int)threadIdx.x - p * nch;
-        float acc[kTilePx];
+        // acc[k / 2] holds the pixels k (x) and k + 1 (y), summed with packed FP32x2 operations
+        // (each half rounded as the scalar operation)
+        static_assert(kTilePx % 2 == 0, "pixels travel in pairs");
+        float2 acc[kTilePx / 2];
 #pragma unroll
-        for (int k = 0; k < kTilePx; ++k) acc[k] = 0.0f;
+        for (int k = 0; k < kTilePx / 2; ++k) acc[k] = make_float2(0.0f, 0.0f);
         // table entry j of layer l (column j < ncol, else row j - ncol): integer screen offset
         // from the layer base (as float bits) and the fraction
         auto coord = [&](int l, int j) -> float2 {
@@ -164,17 +167,32 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
             if (has_task) {
                 const float2 rp = t[ncol + p];
                 const float *brow = box + (__float_as_int(rp.x) - gm.y) * bw - gm.x;
+                const float2 gy = make_float2(rp.y, rp.y), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-                for (int k = 0; k < kTilePx; ++k) {
-                    const int j = ch + k * nch;
-                    if (j < ncol) {
+                for (int k = 0; k < kTilePx; k += 2) {
+                    const int j = ch + k * nch, j2 = j + nch;
+                    if (j2 < ncol) {
+                        // two pixels: x - y as fma(y, -1, x) is the rounded difference
+                        const float2 ca = t[j], cb = t[j2];
+                        const float *b0 = brow + __float_as_int(ca.x), *b1 = brow + __float_as_int(cb.x);
+                        if (!guard(b0 >= box && b0 + bw + 1 < box + box_floats && b1 >= box &&
+                                       b1 + bw + 1 < box + box_floats,
+                                   a.status))
+                            continue;
+                        const float2 fx = make_float2(ca.y, cb.y);
+                        const float2 s00 = make_float2(b0[0], b1[0]), s01 = make_float2(b0[1], b1[1]);
+                        const float2 s10 = make_float2(b0[bw], b1[bw]), s11 = make_float2(b0[bw + 1], b1[bw + 1]);
+                        const float2 top = __ffma2_rn(fx, __ffma2_rn(s00, m1, s01), s00);
+                        const float2 bot = __ffma2_rn(fx, __ffma2_rn(s10, m1, s11), s10);
+                        acc[k / 2] = __fadd2_rn(acc[k / 2], __ffma2_rn(gy, __ffma2_rn(top, m1, bot), top));
+                    } else if (j < ncol) {
                         const float2 cj = t[j];
                         const float *b0 = brow + __float_as_int(cj.x);
                         if (!guard(b0 >= box && b0 + bw + 1 < box + box_floats, a.status)) continue;
                         const float s00 = b0[0], s01 = b0[1], s10 = b0[bw], s11 = b0[bw + 1];
                         const float top = fmaf(cj.y, s01 - s00, s00);
                         const float bot = fmaf(cj.y, s11 - s10, s10);
-                        acc[k] += fmaf(rp.y, bot - top, top);
+                        acc[k / 2].x += fmaf(rp.y, bot - top, top);
                     }
                 }
             }
@@ -198,7 +216,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
 #pragma unroll
             for (int k = 0; k < kTilePx; ++k) {
                 const float xr = (float)(sg.w * n + ch + k * nch) - half;
-                if (ch + k * nch < ncol) opd[v * nn + q] = acc[k] + fmaf(up.x, xr, row_tilt);
+                if (ch + k * nch < ncol) opd[v * nn + q] = (k & 1 ? acc[k / 2].y : acc[k / 2].x) + fmaf(up.x, xr, row_tilt);
                 q += dq;
                 v += dv;
                 if (q >= n) {
@@ -278,7 +296,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
 // grid holds only as many CTAs as fit at once and each draws its next block from the ticket
 // counter (issued at the top, consumed after the block), so CTAs that start late take fewer
 // blocks and no partial last wave is left; the last CTA to finish resets the counter.
-__global__ void __launch_bounds__(kProjThreads) k_project(const __grid_constant__ ProjArgs a) {
+__global__ void __launch_bounds__(kProjThreads, 3) k_project(const __grid_constant__ ProjArgs a) {
     allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
     __shared__ int s_next, s_last_wfs;
     __shared__ LayerOffs s_tab[kOffsTable];

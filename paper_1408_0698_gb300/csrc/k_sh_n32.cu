@@ -48,6 +48,8 @@ struct N32Layout {
     static constexpr int wM = wTa + nd * n;        // [dyi][n]
     static constexpr int wI = wM + D2 * n;         // [k][N+1] floats (NGS binning only)
     static constexpr int warp = wI + (N * (N + 1) + 1) / 2;
+    static_assert(table % 2 == 0 && warp % 2 == 0 && wTa % 2 == 0 && wM % 2 == 0,
+                  "16-byte aligned column-pair scratch");
 };
 
 }  // namespace
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 
         float Bv[nd / 2];  // B[iy][ix] for iy = half*(nd/2) + j
         if (W.is_lgs) {
-            tail::lgs_binned<n, nd>(T, Mw, Ta, fft, Gt, W.ktil + (size_t)v * (D2 * n), lane, Bv);
+            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Ta), fft, Gt,
+                                       W.ktil + (size_t)v * (D2 * n), lane, Bv);
         } else {
             __syncwarp();
             tail::ngs_binned<nd>(Iw, lane, Bv);

@@ -132,9 +132,41 @@ __device__ __forceinline__ void split_bf16(float x, float &hi, float &lo) {
     lo = x - hi;
 }
 
-__device__ __forceinline__ void cmacc(float2 &acc, const float2 a, const float2 b) {
-    acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
-    acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+// The field X of one subaperture in the warp's scratch as column pairs: entry [p][q/2] holds
+// (re q, re q+1, im q, im q+1) of row p (q even).
+template <int n>
+__device__ __forceinline__ void store_field(float4 *X4, int i, float c, float s) {
+    const int p = i / n, q = i - p * n;
+    float *e = reinterpret_cast<float *>(X4 + p * (n / 2) + (q >> 1)) + (q & 1);
+    e[0] = c;
+    e[2] = s;
+}
+
+// U[q] = sum_p F[k][p] X[p][q] for this lane's DFT row k: two columns per packed FP32x2 FMA
+// (each half rounded as fmaf); per p, re += -f.im x.im then f.re x.re, im += f.im x.re then
+// f.re x.im.
+template <int n, int N>
+__device__ __forceinline__ void field_rows(const float2 *Fk, const float4 *X4, int lane, float2 (&U)[n]) {
+    float2 ur[n / 2], ui[n / 2];
+#pragma unroll
+    for (int c = 0; c < n / 2; ++c) ur[c] = ui[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        const float2 f = Fk[p * N + lane];
+        const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y), nfy = make_float2(-f.y, -f.y);
+#pragma unroll
+        for (int c = 0; c < n / 2; ++c) {
+            const float4 x = X4[p * (n / 2) + c];
+            const float2 xr = make_float2(x.x, x.y), xi = make_float2(x.z, x.w);
+            ur[c] = __ffma2_rn(fx, xr, __ffma2_rn(nfy, xi, ur[c]));
+            ui[c] = __ffma2_rn(fx, xi, __ffma2_rn(fy, xr, ui[c]));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < n / 2; ++c) {
+        U[2 * c] = make_float2(ur[c].x, ui[c].x);
+        U[2 * c + 1] = make_float2(ur[c].y, ui[c].y);
+    }
 }
 
 template <int n, int nd, bool kSlices = false>
@@ -155,7 +187,9 @@ struct TcLayout {
     static constexpr int tEnd = tRk + kRecipTable / 2;
     static constexpr int oWarp = oTab + tEnd * 8;  // per-warp scratch (float2)
     // the NGS image rows (wI) alias the LGS scratch (wQ, wM)
+    // (X, Q and M hold column pairs, 16-byte aligned)
     static constexpr int wX = 0, wQ = wX + n * n, wM = wQ + nd * n, wI = wQ;
+    static_assert(wQ % 2 == 0 && wM % 2 == 0, "16-byte aligned column-pair scratch");
     static constexpr int lgs_end = wM + D2 * n, ngs_end = wI + (N * (N + 1) + 1) / 2;
     // an LGS subaperture's elongation table K~ ([2n-1][n] complex), staged by cp.async at the
     // top of a group and read by the elongation stage; it may overlap the NGS rows, which an LGS
@@ -235,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
     constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
 
-    float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
+    float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
     float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
     float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
@@ -281,15 +315,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
                 const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                 float s, c;
                 field_phasor(W.k_phase * (__ldg(opd + i) - ref), s, c);
-                X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+                store_field<n>(X4, i, lit ? c : 0.0f, lit ? s : 0.0f);
             }
             __syncwarp();
-#pragma unroll
-            for (int p = 0; p < n; ++p) {
-                const float2 f = Fk[p * N + lane];
-#pragma unroll
-                for (int q = 0; q < n; ++q) cmacc(U[q], f, X[p * n + q]);
-            }
+            field_rows<n, N>(Fk, X4, lane, U);
         }
         // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
         {
@@ -406,7 +435,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         if (W.is_lgs) {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncwarp();
-            tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, Kts, lane, Bv);
+            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Qw), fft, Gt, Kts,
+                                    lane, Bv);
         } else
             tail::ngs_binned<nd>(Iw, lane, Bv);
         tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);
@@ -493,7 +523,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
     constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
 
-    float2 *X = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX;
+    float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
     float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
     float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
@@ -571,15 +601,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                     const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                     float s, c;
                     field_phasor(W.k_phase * ((__ldg(opd + i) + geo(i)) - ref), s, c);
-                    X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+                    store_field<n>(X4, i, lit ? c : 0.0f, lit ? s : 0.0f);
                 }
                 __syncwarp();
-#pragma unroll
-                for (int p = 0; p < n; ++p) {
-                    const float2 f = Fk[p * N + lane];
-#pragma unroll
-                    for (int q = 0; q < n; ++q) cmacc(U[q], f, X[p * n + q]);
-                }
+                field_rows<n, N>(Fk, X4, lane, U);
             }
             // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
             {
@@ -739,7 +764,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
         if (W.is_lgs) {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncwarp();
-            tail::lgs_binned<n, nd>(T, Mw, Qw, fft, Gt, Kts, lane, Bv);
+            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Qw), fft, Gt, Kts,
+                                    lane, Bv);
         } else
             tail::ngs_binned<nd>(Iw, lane, Bv);
         tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);

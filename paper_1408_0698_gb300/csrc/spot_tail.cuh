@@ -51,28 +51,47 @@ __device__ __forceinline__ void fill_fft_table(float2 *tab, int tid, int nthread
     }
 }
 
+// Packed FP32x2 arithmetic (one instruction for two lanes of values, each rounded as the scalar
+// operation): the column pairs (dx, dx + 1) of the tail travel together.
+__device__ __forceinline__ float2 dup2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
 // T: this lane's row k = lane of the first stage (T[k][dx], dx < n), consumed.  fft: the
 // table above.  Gt: [n][nd] G[d][i].  kt: the subaperture's K~ [2n-1][n] (global or shared
-// memory).  M and Q are per-warp scratch ([2n-1][n], [nd][n]).
+// memory).  M and Q are per-warp scratch ([2n-1][n/2] and [nd][n/2], 16-byte aligned), each
+// entry a column pair (re dx, re dx+1, im dx, im dx+1).
 // On return Bv[j] = B[half * nd/2 + j][ix] for lane = half * 16 + ix.
 template <int n, int nd>
-__device__ __forceinline__ void lgs_binned(float2 (&T)[n], float2 *M, float2 *Q, const float2 *fft,
+__device__ __forceinline__ void lgs_binned(float2 (&T)[n], float4 *M, float4 *Q, const float2 *fft,
                                            const float2 *Gt, const float2 *kt, int lane, float (&Bv)[nd / 2]) {
-    constexpr int D2 = 2 * n - 1, DXH = (n + 1) / 2;
+    constexpr int D2 = 2 * n - 1, P = n / 2, PH = (P + 1) / 2;
     static_assert(nd == 16, "the detector tile maps to 16 lanes x 2 half-warps");
     static_assert(n <= 16, "frequencies |dy| < n must be distinct modulo 32");
+    static_assert(n % 2 == 0, "columns travel in pairs");
+    // columns as pairs: Tr[c] = (re 2c, re 2c+1), Ti[c] = (im 2c, im 2c+1)
+    float2 Tr[P], Ti[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+        Tr[c] = make_float2(T[2 * c].x, T[2 * c + 1].x);
+        Ti[c] = make_float2(T[2 * c].y, T[2 * c + 1].y);
+    }
     // M: DFT over the lanes, five radix-2 stages
 #pragma unroll
     for (int st = 0; st < 5; ++st) {
         const int h = 16 >> st;
-        const float sgn = (lane & h) ? -1.0f : 1.0f;
+        const float2 sg = dup2((lane & h) ? -1.0f : 1.0f);
         const float2 tw = fft[st * 32 + lane];
+        const float2 twx = dup2(tw.x), twy = dup2(tw.y), ntwy = dup2(-tw.y);
 #pragma unroll
-        for (int d = 0; d < n; ++d) {
-            const float tx = __shfl_xor_sync(0xffffffffu, T[d].x, h);
-            const float ty = __shfl_xor_sync(0xffffffffu, T[d].y, h);
-            const float sx = fmaf(sgn, T[d].x, tx), sy = fmaf(sgn, T[d].y, ty);
-            T[d] = make_float2(sx * tw.x - sy * tw.y, sx * tw.y + sy * tw.x);
+        for (int c = 0; c < P; ++c) {
+            const float2 tr = make_float2(__shfl_xor_sync(0xffffffffu, Tr[c].x, h),
+                                          __shfl_xor_sync(0xffffffffu, Tr[c].y, h));
+            const float2 ti = make_float2(__shfl_xor_sync(0xffffffffu, Ti[c].x, h),
+                                          __shfl_xor_sync(0xffffffffu, Ti[c].y, h));
+            const float2 sr = fma2(sg, Tr[c], tr), si = fma2(sg, Ti[c], ti);
+            Tr[c] = fma2(si, ntwy, mul2(sr, twx));
+            Ti[c] = fma2(si, twx, mul2(sr, twy));
         }
     }
     {
@@ -80,54 +99,69 @@ __device__ __forceinline__ void lgs_binned(float2 (&T)[n], float2 *M, float2 *Q,
         if (dy > -n && dy < n) {
             const int dyi = dy + n - 1;
             const float2 ph = fft[5 * 32 + lane];
+            const float2 phx = dup2(ph.x), phy = dup2(ph.y), nphy = dup2(-ph.y);
 #pragma unroll
-            for (int d = 0; d < n; ++d) {
-                const float2 x = make_float2(T[d].x * ph.x - T[d].y * ph.y, T[d].x * ph.y + T[d].y * ph.x);
-                const float2 k0 = kt[dyi * n + d];
-                M[dyi * n + d] = make_float2(x.x * k0.x - x.y * k0.y, x.x * k0.y + x.y * k0.x);
+            for (int c = 0; c < P; ++c) {
+                const float2 xr = fma2(Ti[c], nphy, mul2(Tr[c], phx));
+                const float2 xi = fma2(Ti[c], phx, mul2(Tr[c], phy));
+                const float2 k0 = kt[dyi * n + 2 * c], k1 = kt[dyi * n + 2 * c + 1];
+                M[dyi * P + c] = make_float4(xr.x * k0.x - xi.x * k0.y, xr.y * k1.x - xi.y * k1.y,
+                                             xr.x * k0.y + xi.x * k0.x, xr.y * k1.y + xi.y * k1.x);
             }
         }
     }
     __syncwarp();
-    // Q[iy][dx] for iy = lane & 15, dx in this half
+    // Q[iy][dx] for iy = lane & 15; half 0 takes the column pairs [0, PH), half 1 the rest
     const int ix = lane & 15, half = lane >> 4;
     {
         const int iy = ix;
-        float2 q[DXH];
+        float2 qr[PH], qi[PH];
 #pragma unroll
-        for (int j = 0; j < DXH; ++j) q[j] = make_float2(0.f, 0.f);
+        for (int j = 0; j < PH; ++j) qr[j] = qi[j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int dyi = 0; dyi < D2; ++dyi) {
             const int dy = dyi - (n - 1);
-            float2 gv = Gt[(dy >= 0 ? dy : -dy) * nd + iy];
-            if (dy < 0) gv.y = -gv.y;
+            const float2 gv = Gt[(dy >= 0 ? dy : -dy) * nd + iy];
+            const float gy = dy < 0 ? -gv.y : gv.y;
+            const float2 gx2 = dup2(gv.x), gy2 = dup2(gy), ngy2 = dup2(-gy);
 #pragma unroll
-            for (int j = 0; j < DXH; ++j) {
-                const int dx = half * DXH + j;
-                if (dx < n) cmac(q[j], gv, M[dyi * n + dx]);
+            for (int j = 0; j < PH; ++j) {
+                const int c = half * PH + j;
+                if (c < P) {
+                    const float4 m = M[dyi * P + c];
+                    const float2 mr = make_float2(m.x, m.y), mi = make_float2(m.z, m.w);
+                    // per column: re += g.x m.re - g.y m.im, im += g.x m.im + g.y m.re
+                    qr[j] = fma2(gx2, mr, fma2(ngy2, mi, qr[j]));
+                    qi[j] = fma2(gx2, mi, fma2(gy2, mr, qi[j]));
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < DXH; ++j) {
-            const int dx = half * DXH + j;
-            if (dx < n) Q[iy * n + dx] = q[j];
+        for (int j = 0; j < PH; ++j) {
+            const int c = half * PH + j;
+            if (c < P) Q[iy * P + c] = make_float4(qr[j].x, qr[j].y, qi[j].x, qi[j].y);
         }
     }
     __syncwarp();
-    // B[iy][ix] for iy in this half
-    float2 gc[n];
+    // B[iy][ix] for iy in this half: Re sum_dx Q[iy][dx] G[dx][ix], even and odd columns summed
+    // apart
+    float2 gcx[P], ngcy[P];
 #pragma unroll
-    for (int d = 0; d < n; ++d) gc[d] = Gt[d * nd + ix];
+    for (int c = 0; c < P; ++c) {
+        const float2 g0 = Gt[(2 * c) * nd + ix], g1 = Gt[(2 * c + 1) * nd + ix];
+        gcx[c] = make_float2(g0.x, g1.x);
+        ngcy[c] = make_float2(-g0.y, -g1.y);
+    }
 #pragma unroll
     for (int j = 0; j < nd / 2; ++j) {
         const int iy = half * (nd / 2) + j;
-        float s = 0.0f;
+        float2 s = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int d = 0; d < n; ++d) {
-            const float2 qv = Q[iy * n + d];
-            s = fmaf(qv.x, gc[d].x, fmaf(-qv.y, gc[d].y, s));
+        for (int c = 0; c < P; ++c) {
+            const float4 qv = Q[iy * P + c];
+            s = fma2(make_float2(qv.x, qv.y), gcx[c], fma2(make_float2(qv.z, qv.w), ngcy[c], s));
         }
-        Bv[j] = s;
+        Bv[j] = s.x + s.y;
     }
 }
 
