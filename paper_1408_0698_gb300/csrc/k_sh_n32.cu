@@ -134,11 +134,24 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             };
             // field, piston-free
             const float ref = __ldg(opd) + (kSlices ? geo(0) : 0.0f);
-            for (int i = lane; i < n * n; i += 32) {
-                const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
-                float s, c;
-                field_phasor(W.k_phase * ((__ldg(opd + i) + (kSlices ? geo(i) : 0.0f)) - ref), s, c);
-                X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+            // all of the lane's loads first (element i = lane + 32 m, mask word m)
+            constexpr int kFw = (n * n + 31) / 32;
+            float o[kFw];
+            uint32_t mw[kFw];
+#pragma unroll
+            for (int m = 0; m < kFw; ++m) {
+                o[m] = lane + 32 * m < n * n ? __ldg(opd + lane + 32 * m) : 0.0f;
+                mw[m] = __ldg(mk + m);
+            }
+#pragma unroll
+            for (int m = 0; m < kFw; ++m) {
+                const int i = lane + 32 * m;
+                if (i < n * n) {
+                    const bool lit = (mw[m] >> lane) & 1u;
+                    float s, c;
+                    field_phasor(W.k_phase * ((o[m] + (kSlices ? geo(i) : 0.0f)) - ref), s, c);
+                    X[i] = lit ? make_float2(c, s) : make_float2(0.0f, 0.0f);
+                }
             }
             __syncwarp();
 

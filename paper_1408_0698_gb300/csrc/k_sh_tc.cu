@@ -311,11 +311,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
             const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
             const float ref = __ldg(opd);
-            for (int i = lane; i < n * n; i += 32) {
-                const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
-                float s, c;
-                field_phasor(W.k_phase * (__ldg(opd + i) - ref), s, c);
-                store_field<n>(X4, i, lit ? c : 0.0f, lit ? s : 0.0f);
+            // all of the lane's loads first (element i = lane + 32 m, mask word m)
+            constexpr int kFw = (n * n + 31) / 32;
+            float o[kFw];
+            uint32_t mw[kFw];
+#pragma unroll
+            for (int m = 0; m < kFw; ++m) {
+                o[m] = lane + 32 * m < n * n ? __ldg(opd + lane + 32 * m) : 0.0f;
+                mw[m] = __ldg(mk + m);
+            }
+#pragma unroll
+            for (int m = 0; m < kFw; ++m) {
+                const int i = lane + 32 * m;
+                if (i < n * n) {
+                    const bool lit = (mw[m] >> lane) & 1u;
+                    float s, c;
+                    field_phasor(W.k_phase * (o[m] - ref), s, c);
+                    store_field<n>(X4, i, lit ? c : 0.0f, lit ? s : 0.0f);
+                }
             }
             __syncwarp();
             field_rows<n, N>(Fk, X4, lane, U);
@@ -597,11 +610,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                 };
                 const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
                 const float ref = __ldg(opd) + geo(0);
-                for (int i = lane; i < n * n; i += 32) {
-                    const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
-                    float s, c;
-                    field_phasor(W.k_phase * ((__ldg(opd + i) + geo(i)) - ref), s, c);
-                    store_field<n>(X4, i, lit ? c : 0.0f, lit ? s : 0.0f);
+                // all of the lane's loads first (element i = lane + 32 m, mask word m)
+                constexpr int kFw = (n * n + 31) / 32;
+                float o[kFw];
+                uint32_t mw[kFw];
+#pragma unroll
+                for (int m = 0; m < kFw; ++m) {
+                    o[m] = lane + 32 * m < n * n ? __ldg(opd + lane + 32 * m) : 0.0f;
+                    mw[m] = __ldg(mk + m);
+                }
+#pragma unroll
+                for (int m = 0; m < kFw; ++m) {
+                    const int i = lane + 32 * m;
+                    if (i < n * n) {
+                        const bool lit = (mw[m] >> lane) & 1u;
+                        float s, c;
+                        field_phasor(W.k_phase * ((o[m] + geo(i)) - ref), s, c);
+                        store_field<n>(X4, i, lit ? c : 0.0f, lit ? s : 0.0f);
+                    }
                 }
                 __syncwarp();
                 field_rows<n, N>(Fk, X4, lane, U);
