@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SH-WFS spots/s & ELT 6-LGS frames/s at ≤1e-3 px slope err; served p50/p99"
 UNIT = "spots/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16s": 2}      # WFS_PREC_FP32, _BF16X3, _FP16S
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -433,15 +434,16 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3"],
-                    help="DFT arithmetic of the LGS geometry for the headline (the other is timed beside it)")
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "fp16s"],
+                    help="DFT arithmetic of the LGS geometry for the headline (the others are timed beside it)")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served-traffic measurement")
     ap.add_argument("--no-loop", action="store_true", help="skip the closed-loop measurement")
     ap.add_argument("--no-calib", action="store_true", help="skip the push-pull calibration measurement")
-    ap.add_argument("--paths", default="fp32,uplink,slices",
-                    help="comparison paths timed after the headline (comma list of fp32, uplink, slices; 'none')")
+    ap.add_argument("--paths", default="fp32,fp16s,uplink,slices",
+                    help="comparison paths timed after the headline (comma list of fp32, fp16s, uplink, "
+                         "slices; 'none'); fp32 and fp16s time the other DFT precisions")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (0: none, for profiling runs)")
     args = ap.parse_args()
@@ -463,7 +465,7 @@ def main():
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    prec = inputs.PREC_FP32 if args.precision == "fp32" else inputs.PREC_BF16X3
+    prec = PRECISIONS[args.precision]
     cfg = inputs.config3(prec)
     scr = inputs.make_screens(cfg.layers, cfg.seed + 17 * rank)   # one MC run per rank
     w = native.Wfs(cfg, seed=cfg.seed + rank, noise=True)
@@ -611,10 +613,12 @@ def main():
             "gpu_launches": int(round(sum(v[0] for v in ktimes.values()) / kk * args.steps)),
             "roofline": roof, "e2e": e2e, "clocks": clk, "wall_s_timed": wall}
     paths = set(args.paths.split(","))
-    # the other DFT precision, timed the same way on the same inputs (comparison path)
-    other = "fp32" if args.precision == "bf16x3" else "bf16x3"
-    if "fp32" in paths:
-        time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
+    # the other DFT precisions, timed the same way on the same inputs (comparison paths; the
+    # "fp32" path times BF16 x3 when the headline is FP32)
+    for key in ("fp32", "fp16s"):
+        other = key if args.precision != key else "bf16x3"
+        if key in paths and other != args.precision:
+            time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
     if "uplink" in paths:
         time_uplink(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
     if "slices" in paths:
@@ -668,8 +672,7 @@ def time_frames(w, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, steps, ke
 
 def time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):
     from paper_1408_0698_gb300 import inputs, native
-    w2 = native.Wfs(inputs.config3(inputs.PREC_FP32 if other == "fp32" else inputs.PREC_BF16X3),
-                    seed=cfg.seed + rank, noise=True)
+    w2 = native.Wfs(inputs.config3(PRECISIONS[other]), seed=cfg.seed + rank, noise=True)
     k2 = min(args.steps, 300)
     ms, kt = time_frames(w2, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, k2)
     w2.close()

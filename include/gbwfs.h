@@ -62,11 +62,17 @@ typedef enum {
                              in a kernel and skipped that access (never in the normal build) */
 } wfs_status;
 
-/* DFT arithmetic of a geometry (the rest of the path is FP32 throughout). */
+/*
+ * DFT arithmetic of a geometry (the rest of the path is FP32 throughout).  The two
+ * tensor-core forms are built for n_fft = 32 with (n_pix_sub, n_det) = (10, 16) or
+ * (8, 16); other geometries with them get WFS_EUNSUPPORTED from wfs_create.
+ */
 enum {
     WFS_PREC_FP32 = 0,    /* plain FP32 on the CUDA cores */
     WFS_PREC_BF16X3 = 1,  /* tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
-    WFS_PREC_FP16S = 2    /* reserved: FP16 with scaling */
+    WFS_PREC_FP16S = 2    /* tensor cores, FP16 hi/lo split, 3 products, FP32 accumulate;
+                             each subaperture's operands are scaled by powers of two into
+                             FP16's normal range (exact, undone after the products) */
 };
 
 /* Telescope pupil: circular, diameter D, central obstruction eps (fraction of D). */

@@ -81,6 +81,7 @@ struct SpotGroup {
 
 int spot_kind(const wfs_geometry &g) {
     if (g.precision == WFS_PREC_BF16X3) return kSpotTc;
+    if (g.precision == WFS_PREC_FP16S) return kSpotTcF16;
     return sh_n32_supported(g.n_pix_sub, g.n_fft, g.n_det) ? kSpotN32 : kSpotGeneric;
 }
 
@@ -487,7 +488,10 @@ void fill_geom_args(ShArgs &sa, const GeomDev &G) {
 }
 
 const char *kind_name(int kind) {
-    return kind == kSpotTc ? "spot_tc_bf16x3_N" : kind == kSpotN32 ? "spot_n32_fp32_N" : "spot_fp32_N";
+    return kind == kSpotTc      ? "spot_tc_bf16x3_N"
+           : kind == kSpotTcF16 ? "spot_tc_fp16s_N"
+           : kind == kSpotN32   ? "spot_n32_fp32_N"
+                                : "spot_fp32_N";
 }
 
 // dm_layers / n_dm: the correction layers of a closed loop's mirrors, summed after the
@@ -883,12 +887,11 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
     if (st != WFS_OK) return st;
     for (int i = 0; i < n_geom; ++i) {
         const wfs_geometry &g = geom[i];
-        if (g.precision == WFS_PREC_FP16S)
-            return fail(nullptr, WFS_EUNSUPPORTED, "geometry " + std::to_string(i) + ": WFS_PREC_FP16S is not built");
-        if (g.precision == WFS_PREC_BF16X3 && !sh_tc_supported(g.n_pix_sub, g.n_fft, g.n_det))
+        if ((g.precision == WFS_PREC_BF16X3 || g.precision == WFS_PREC_FP16S) &&
+            !sh_tc_supported(g.n_pix_sub, g.n_fft, g.n_det))
             return fail(nullptr, WFS_EUNSUPPORTED,
-                        "geometry " + std::to_string(i) +
-                            ": WFS_PREC_BF16X3 is built for n_fft = 32 with (n_pix_sub, n_det) = (10, 16) or (8, 16)");
+                        "geometry " + std::to_string(i) + (g.precision == WFS_PREC_FP16S ? ": WFS_PREC_FP16S" : ": WFS_PREC_BF16X3") +
+                            " is built for n_fft = 32 with (n_pix_sub, n_det) = (10, 16) or (8, 16)");
     }
 
     wfs_ctx *h = new wfs_ctx();
@@ -920,11 +923,11 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
             delete h;
             return cuda_fail(nullptr, e, "table upload");
         }
-        if (geom[i].precision == WFS_PREC_BF16X3) {
+        if (geom[i].precision == WFS_PREC_BF16X3 || geom[i].precision == WFS_PREC_FP16S) {
             const int n = geom[i].n_pix_sub, N = geom[i].n_fft;
             std::vector<uint8_t> b1, b2h, b2l;
             build_tc_tiles(n, N, F64.data(), F64.data() + (size_t)n * N, Ga64.data(), Ga64.data() + (size_t)n * N,
-                           b1, b2h, b2l);
+                           geom[i].precision == WFS_PREC_FP16S, b1, b2h, b2l);
             if ((e = upload(&G.tcB1, b1)) != cudaSuccess || (e = upload(&G.tcB2h, b2h)) != cudaSuccess ||
                 (e = upload(&G.tcB2l, b2l)) != cudaSuccess) {
                 release(h);
@@ -1773,7 +1776,7 @@ wfs_status wfs_batch_tune(wfs_batch b, const float *const *screens, const double
         if (bc.kind == kSpotN32) {
             for (int w : {4, 8})
                 for (int m : {2, 4, 8, 16}) cand.push_back({152 * m * (8 / w), w});
-        } else if (bc.kind == kSpotTc) {
+        } else if (is_tc(bc.kind)) {
             for (int m : {1, 2}) cand.push_back({152 * m, 0});
         } else {
             for (int m : {2, 4, 8, 32}) cand.push_back({152 * m, 0});
@@ -2183,7 +2186,7 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             // the per-slice variant of the geometry's 32-point kernel (tensor-core or FP32) where
             // it has one, else the self-projecting generic kernel
             const wfs_geometry &geo = h->geoms[G.geom].g;
-            if (G.kind != kSpotTc)
+            if (!is_tc(G.kind))
                 G.kind = sh_n32_supported(geo.n_pix_sub, geo.n_fft, geo.n_det) ? kSpotN32 : kSpotGeneric;
             G.grid_cap = G.cta_warps = 0;
         } else {
@@ -2199,7 +2202,7 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             d.slices = per_slice ? h->d_slices + d.gs_index : nullptr;
             d.ktil = per_slice ? gd.d_ktil_g : gd.d_ktil;
         }
-        G.sl_projected = per_slice && (G.kind == kSpotTc || G.kind == kSpotN32);
+        G.sl_projected = per_slice && (is_tc(G.kind) || G.kind == kSpotN32);
     }
     if (build_slice_projection(h) != WFS_OK) return WFS_ECUDA;
     if ((e = cudaMemcpy(h->d_wfs, h->wfs_host.data(), sizeof(WfsDesc) * h->wfs_host.size(), cudaMemcpyHostToDevice)) !=

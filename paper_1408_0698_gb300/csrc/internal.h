@@ -245,8 +245,9 @@ cudaError_t launch_ktil(const KtilArgs &a, cudaStream_t s);
 cudaError_t launch_noise(const float *E, int n, float ron, uint64_t seed, uint32_t wfs, double t,
                          uint32_t pixel0, float *C, cudaStream_t s);
 // Spot kernels: kind 0 = generic FP32 (any geometry), 1 = FP32 specialised for N = 32,
-// 2 = tensor core (BF16 x3) for N = 32.
-enum SpotKind { kSpotGeneric = 0, kSpotN32 = 1, kSpotTc = 2 };
+// 2 = tensor core (BF16 x3) for N = 32, 3 = tensor core (scaled FP16 x3) for N = 32.
+enum SpotKind { kSpotGeneric = 0, kSpotN32 = 1, kSpotTc = 2, kSpotTcF16 = 3 };
+inline bool is_tc(int kind) { return kind == kSpotTc || kind == kSpotTcF16; }
 bool sh_n32_supported(int n, int N, int nd);
 bool sh_tc_supported(int n, int N, int nd);
 // Shape of the launch (sets the kernel's dynamic shared-memory attribute).
@@ -260,11 +261,11 @@ cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s, bool after_pr
 cudaError_t launch_noise_cog(const ShArgs &a, cudaStream_t s, bool after_spot);
 cudaError_t noise_cog_launch_shape(const ShArgs &a, LaunchShape *out);
 // Whether a spot kind stores expected images and leaves noise and centroid to k_noise_cog.
-inline bool splits_noise(int kind) { return kind == kSpotN32 || kind == kSpotTc; }
-// Swizzled BF16 operand tiles of the two constant matrices (F^T blocks, Ga blocks),
+inline bool splits_noise(int kind) { return kind == kSpotN32 || is_tc(kind); }
+// Swizzled BF16 (f16: FP16) operand tiles of the two constant matrices (F^T blocks, Ga blocks),
 // from FP64 tables laid out [q][m] (F) and [d][k] (Ga).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
-                    const double *Ga_im64, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
+                    const double *Ga_im64, bool f16, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
                     std::vector<uint8_t> &B2l);
 // Bounded mbarrier wait that is never satisfied; writes WFS_ETIMEOUT to *status.
 cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);

@@ -30,6 +30,7 @@
 // Y = U F^T runs on the tensor cores; the weighted |Y|^2 of the slices are summed in the warp's
 // shared rows, which then feed Ta = I Ga^T.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <string.h>
 
 #include <vector>
@@ -61,12 +62,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor of kind::f16: BF16 x BF16 -> F32, both K-major.
-__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: A and B of format fmt (0 = FP16, 1 = BF16; both operands
+// always the same type) -> F32, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -122,15 +124,50 @@ __host__ __device__ inline uint32_t sw128_off(int r, int k) {
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&v);
+// The operand element of the tensor-core products: BF16 (8-bit significand), or FP16 (11-bit)
+// with a power-of-two scale per subaperture and operand that puts its largest magnitude in
+// [2^13, 2^14), inside FP16's normal range.  x = hi + lo exactly in FP32; the MMAs take
+// hi*hi + lo*hi + hi*lo.
+template <bool kF16>
+struct TcElt {
+    static constexpr uint32_t fmt = 1;  // BF16
+    static __device__ __forceinline__ void split(float x, float &hi, float &lo) {
+        hi = __bfloat162float(__float2bfloat16_rn(x));
+        lo = x - hi;
+    }
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&v);
+    }
+};
+template <>
+struct TcElt<true> {
+    static constexpr uint32_t fmt = 0;  // FP16
+    static __device__ __forceinline__ void split(float x, float &hi, float &lo) {
+        hi = __half2float(__float2half_rn(x));
+        lo = x - hi;
+    }
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        const __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&v);
+    }
+};
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-__device__ __forceinline__ void split_bf16(float x, float &hi, float &lo) {
-    hi = __bfloat162float(__float2bfloat16_rn(x));
-    lo = x - hi;
+// The FP16 operand scale 2^e: x 2^e in [2^13, 2^14) for the largest magnitude x (e = 0 for
+// x = 0; |e| <= 60).
+__device__ __forceinline__ int f16_scale_exp(float mx) {
+    if (!(mx > 0.0f)) return 0;
+    const int ex = (int)((__float_as_uint(mx) >> 23) & 0xFFu) - 127;
+    return max(-60, min(60, 13 - ex));
 }
+
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }  // |e| <= 126
 
 // The field X of one subaperture in the warp's scratch as column pairs: entry [p][q/2] holds
 // (re q, re q+1, im q, im q+1) of row p (q even).
@@ -207,9 +244,10 @@ struct TcLayout {
 
 }  // namespace
 
-template <int n, int nd>
+template <int n, int nd, bool kF16>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__ ShArgs a) {
     using Lay = TcLayout<n, nd>;
+    using E = TcElt<kF16>;
     constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
     static_assert(n % 2 == 0 && Lay::wKt % 2 == 0 && Lay::warp % 2 == 0 && Lay::oWarp % 16 == 0,
@@ -267,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     if (a.split_noise) allow_dependent_grid();  // the noise kernel may take SMs as CTAs retire
     const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
-    constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
+    constexpr uint32_t idesc1 = tc_idesc(128, 64, E::fmt), idesc2 = tc_idesc(128, 32, E::fmt);
 
     float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
@@ -333,13 +371,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             __syncwarp();
             field_rows<n, N>(Fk, X4, lane, U);
         }
+        // FP16: U times 2^eu (exact), eu from the subaperture's largest component
+        int eu = 0;
+        if constexpr (kF16) {
+            float mx = 0.0f;
+#pragma unroll
+            for (int q = 0; q < n; ++q) mx = fmaxf(mx, fmaxf(fabsf(U[q].x), fabsf(U[q].y)));
+            eu = f16_scale_exp(warp_max(mx));
+            const float su = pow2f(eu);
+#pragma unroll
+            for (int q = 0; q < n; ++q) U[q] = make_float2(U[q].x * su, U[q].y * su);
+        }
         // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
         {
             float hv[2 * n], lv[2 * n];
 #pragma unroll
             for (int q = 0; q < n; ++q) {
-                split_bf16(U[q].x, hv[q], lv[q]);
-                split_bf16(U[q].y, hv[n + q], lv[n + q]);
+                E::split(U[q].x, hv[q], lv[q]);
+                E::split(U[q].y, hv[n + q], lv[n + q]);
             }
 #pragma unroll
             for (int ch = 0; ch < 8; ++ch) {
@@ -353,7 +402,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
                         const int t = e / (2 * n), j = e % (2 * n);
                         vv[h2] = e >= 6 * n ? 0.0f : (t == 1 ? lv[j] : hv[j]);
                     }
-                    wds[e2] = pack_bf16(vv[0], vv[1]);
+                    wds[e2] = E::pack(vv[0], vv[1]);
                 }
                 *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
             }
@@ -368,25 +417,47 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         if (issuer) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
+                mma_f16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
             mma_commit(&mbar[0]);
         }
         if (!mbar_wait(&mbar[0], phase)) *sflag = 1;
         fence_after_sync();
-        // Y row from TMEM -> I = |Y|^2 -> second operand row [I_hi | I_lo], 16 columns at a time
-        {
-            float *dstI = (active && D.st_I) ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
+        // Y row from TMEM -> I = |Y|^2 -> second operand row [I_hi | I_lo], 16 columns at a time.
+        // FP16: Y carries 2^eu, so the intensity is |Y|^2 2^-2eu (exact); the operand takes
+        // |Y|^2 2^ei, ei from a first pass over the warp's rows.
+        int ei = 0;
+        if constexpr (kF16) {
+            float mx = 0.0f;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 uint32_t r[16], r2[16];
                 GBWFS_TMEM_LD16(r, t_row + 16 * hh);
                 GBWFS_TMEM_LD16(r2, t_row + 32 + 16 * hh);
                 tmem_wait_ld();
-                float I[16];
 #pragma unroll
                 for (int m = 0; m < 16; ++m) {
                     const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
-                    I[m] = fmaf(yr, yr, yi * yi);
+                    mx = fmaxf(mx, fmaf(yr, yr, yi * yi));
+                }
+            }
+            ei = f16_scale_exp(warp_max(mx));
+        }
+        {
+            float *dstI = (active && D.st_I) ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
+            const float uy = kF16 ? pow2f(-eu) : 1.0f, si = kF16 ? pow2f(ei) : 1.0f;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                uint32_t r[16], r2[16];
+                GBWFS_TMEM_LD16(r, t_row + 16 * hh);
+                GBWFS_TMEM_LD16(r2, t_row + 32 + 16 * hh);
+                tmem_wait_ld();
+                float I[16], Iop[16];  // the intensity, and the operand value
+#pragma unroll
+                for (int m = 0; m < 16; ++m) {
+                    const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
+                    const float y2 = fmaf(yr, yr, yi * yi);
+                    I[m] = kF16 ? y2 * uy * uy : y2;
+                    Iop[m] = kF16 ? y2 * si : y2;
                 }
                 if (dstI) {
 #pragma unroll
@@ -402,10 +473,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 #pragma unroll
                     for (int e2 = 0; e2 < 4; ++e2) {
                         float h0, l0, h1, l1;
-                        split_bf16(I[c2 * 8 + 2 * e2], h0, l0);
-                        split_bf16(I[c2 * 8 + 2 * e2 + 1], h1, l1);
-                        hw[e2] = pack_bf16(h0, h1);
-                        lw[e2] = pack_bf16(l0, l1);
+                        E::split(Iop[c2 * 8 + 2 * e2], h0, l0);
+                        E::split(Iop[c2 * 8 + 2 * e2 + 1], h1, l1);
+                        hw[e2] = E::pack(h0, h1);
+                        lw[e2] = E::pack(l0, l1);
                     }
                     *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (2 * hh + c2) * 8)) =
                         make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -422,10 +493,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         if (issuer) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
+                mma_f16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2l) + 32 * s), idesc2, 1);
+                mma_f16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2l) + 32 * s), idesc2, 1);
             mma_commit(&mbar[1]);
         }
         if (!mbar_wait(&mbar[1], phase)) *sflag = 1;
@@ -437,6 +508,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             tmem_wait_ld();
 #pragma unroll
             for (int d = 0; d < n; ++d) T[d] = make_float2(__uint_as_float(r[d]), __uint_as_float(r[16 + d]));
+            if constexpr (kF16) {
+                // T carries 2^(ei + 2 eu): three exact power-of-two factors
+                const float ti = pow2f(-ei), tu = pow2f(-eu);
+#pragma unroll
+                for (int d = 0; d < n; ++d) T[d] = make_float2(T[d].x * ti * tu * tu, T[d].y * ti * tu * tu);
+            }
         }
         phase ^= 1u;
         fence_before_sync();  // TMEM reads of this group precede the next group's MMAs
@@ -472,10 +549,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 }
 
 // The per-slice variant (see the file comment).
-template <int n, int nd>
+template <int n, int nd, bool kF16>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constant__ ShArgs a) {
     constexpr bool kSlices = true;
     using Lay = TcLayout<n, nd, kSlices>;
+    using E = TcElt<kF16>;
     constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
     static_assert(n % 2 == 0 && Lay::wKt % 2 == 0 && Lay::warp % 2 == 0 && Lay::oWarp % 16 == 0,
@@ -534,7 +612,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
     if (a.split_noise) allow_dependent_grid();  // the noise kernel may take SMs as CTAs retire
     const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
-    constexpr uint32_t idesc1 = bf16_idesc(128, 64), idesc2 = bf16_idesc(128, 32);
+    constexpr uint32_t idesc1 = tc_idesc(128, 64, E::fmt), idesc2 = tc_idesc(128, 32, E::fmt);
 
     float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
@@ -632,13 +710,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                 __syncwarp();
                 field_rows<n, N>(Fk, X4, lane, U);
             }
+            // FP16: U times 2^eu (exact), eu from the slice's largest component
+            int eu = 0;
+            if constexpr (kF16) {
+                float mx = 0.0f;
+#pragma unroll
+                for (int q = 0; q < n; ++q) mx = fmaxf(mx, fmaxf(fabsf(U[q].x), fabsf(U[q].y)));
+                eu = f16_scale_exp(warp_max(mx));
+                const float su = pow2f(eu);
+#pragma unroll
+                for (int q = 0; q < n; ++q) U[q] = make_float2(U[q].x * su, U[q].y * su);
+            }
             // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
             {
                 float hv[2 * n], lv[2 * n];
 #pragma unroll
                 for (int q = 0; q < n; ++q) {
-                    split_bf16(U[q].x, hv[q], lv[q]);
-                    split_bf16(U[q].y, hv[n + q], lv[n + q]);
+                    E::split(U[q].x, hv[q], lv[q]);
+                    E::split(U[q].y, hv[n + q], lv[n + q]);
                 }
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {
@@ -652,7 +741,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                             const int t = e / (2 * n), j = e % (2 * n);
                             vv[h2] = e >= 6 * n ? 0.0f : (t == 1 ? lv[j] : hv[j]);
                         }
-                        wds[e2] = pack_bf16(vv[0], vv[1]);
+                        wds[e2] = E::pack(vv[0], vv[1]);
                     }
                     *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
                 }
@@ -670,7 +759,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
             if (issuer) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
-                    mma_bf16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
+                    mma_f16(tmem, sw128_desc(smem_u32(sA1) + 32 * s), sw128_desc(smem_u32(sB1) + 32 * s), idesc1, s > 0);
                 mma_commit(&mbar[0]);
             }
             // the elongation-kernel model completes mbar[0] once per group like mbar[1]
@@ -684,6 +773,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                                   ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N
                                   : nullptr;
                 const float wsl = (SD && sl < my_n) ? SD->w[sl] : (kSlices && sl > 0 ? 0.0f : 1.0f);
+                const float uy = kF16 ? pow2f(-eu) : 1.0f;  // FP16: Y carries 2^eu
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     uint32_t r[16], r2[16];
@@ -694,7 +784,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
 #pragma unroll
                     for (int m = 0; m < 16; ++m) {
                         const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
-                        I[m] = fmaf(yr, yr, yi * yi);
+                        const float y2 = fmaf(yr, yr, yi * yi);
+                        I[m] = kF16 ? y2 * uy * uy : y2;
                     }
                     if (kSlices) {
                         float *ir = Iw + lane * (N + 1) + 16 * hh;
@@ -720,10 +811,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
 #pragma unroll
                         for (int e2 = 0; e2 < 4; ++e2) {
                             float h0, l0, h1, l1;
-                            split_bf16(I[c2 * 8 + 2 * e2], h0, l0);
-                            split_bf16(I[c2 * 8 + 2 * e2 + 1], h1, l1);
-                            hw[e2] = pack_bf16(h0, h1);
-                            lw[e2] = pack_bf16(l0, l1);
+                            E::split(I[c2 * 8 + 2 * e2], h0, l0);
+                            E::split(I[c2 * 8 + 2 * e2 + 1], h1, l1);
+                            hw[e2] = E::pack(h0, h1);
+                            lw[e2] = E::pack(l0, l1);
                         }
                         *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (2 * hh + c2) * 8)) =
                             make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -736,19 +827,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
             __syncwarp();         // the warp's rows are complete before the next slice adds to them
         }
         if (quit) break;
+        int ei = 0;  // FP16: the second operand carries 2^ei
         if (kSlices) {
             // the summed rows -> second operand row [I_hi | I_lo] (after the last slice's MMA), then
             // the K~ staging, which reuses their space
+            if constexpr (kF16) {
+                float mx = 0.0f;
+#pragma unroll
+                for (int c = 0; c < N; ++c) mx = fmaxf(mx, Iw[lane * (N + 1) + c]);
+                ei = f16_scale_exp(warp_max(mx));
+            }
+            const float si = kF16 ? pow2f(ei) : 1.0f;
 #pragma unroll
             for (int c4 = 0; c4 < 4; ++c4) {
                 uint32_t hw[4], lw[4];
 #pragma unroll
                 for (int e2 = 0; e2 < 4; ++e2) {
                     float h0, l0, h1, l1;
-                    split_bf16(Iw[lane * (N + 1) + c4 * 8 + 2 * e2], h0, l0);
-                    split_bf16(Iw[lane * (N + 1) + c4 * 8 + 2 * e2 + 1], h1, l1);
-                    hw[e2] = pack_bf16(h0, h1);
-                    lw[e2] = pack_bf16(l0, l1);
+                    const float i0 = Iw[lane * (N + 1) + c4 * 8 + 2 * e2], i1 = Iw[lane * (N + 1) + c4 * 8 + 2 * e2 + 1];
+                    E::split(kF16 ? i0 * si : i0, h0, l0);
+                    E::split(kF16 ? i1 * si : i1, h1, l1);
+                    hw[e2] = E::pack(h0, h1);
+                    lw[e2] = E::pack(l0, l1);
                 }
                 *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, c4 * 8)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (4 + c4) * 8)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -764,10 +864,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
         if (issuer) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
+                mma_f16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2h) + 32 * s), idesc2, s > 0);
 #pragma unroll
             for (int s = 0; s < 4; ++s)
-                mma_bf16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2l) + 32 * s), idesc2, 1);
+                mma_f16(tmem + 64, sw128_desc(smem_u32(sA2) + 32 * s), sw128_desc(smem_u32(sB2l) + 32 * s), idesc2, 1);
             mma_commit(&mbar[1]);
         }
         if (!mbar_wait(&mbar[1], phase)) *sflag = 1;
@@ -779,6 +879,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
             tmem_wait_ld();
 #pragma unroll
             for (int d = 0; d < n; ++d) T[d] = make_float2(__uint_as_float(r[d]), __uint_as_float(r[16 + d]));
+            if constexpr (kF16) {
+                const float ti = pow2f(-ei);
+#pragma unroll
+                for (int d = 0; d < n; ++d) T[d] = make_float2(T[d].x * ti, T[d].y * ti);
+            }
         }
         phase ^= 1u;
         fence_before_sync();  // TMEM reads of this group precede the next group's MMAs
@@ -858,10 +963,10 @@ float bf16_float(uint16_t h) {
     return f;
 }
 
-template <int n, int nd, bool kSlices>
+template <int n, int nd, bool kSlices, bool kF16>
 cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
     using Lay = TcLayout<n, nd, kSlices>;
-    const void *f = kSlices ? (const void *)k_sh_tc_sl<n, nd> : (const void *)k_sh_tc<n, nd>;
+    const void *f = kSlices ? (const void *)k_sh_tc_sl<n, nd, kF16> : (const void *)k_sh_tc<n, nd, kF16>;
     const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -880,23 +985,35 @@ cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
 
 // ShArgs::slice_opd_stride selects the per-slice variant.
 template <int n, int nd>
-cudaError_t shape_tc(const ShArgs &a, LaunchShape *out) {
-    return a.slice_opd_stride > 0 ? shape_tc_k<n, nd, true>(a, out) : shape_tc_k<n, nd, false>(a, out);
+cudaError_t shape_tc(const ShArgs &a, LaunchShape *out, bool f16) {
+    if (f16) return a.slice_opd_stride > 0 ? shape_tc_k<n, nd, true, true>(a, out) : shape_tc_k<n, nd, false, true>(a, out);
+    return a.slice_opd_stride > 0 ? shape_tc_k<n, nd, true, false>(a, out) : shape_tc_k<n, nd, false, false>(a, out);
 }
 
 }  // namespace
 
 bool sh_tc_supported(int n, int N, int nd) { return N == 32 && ((n == 10 && nd == 16) || (n == 8 && nd == 16)); }
 
-// Operand tiles of the two constant matrices, already in the swizzled shared layout.
+// Operand tiles of the two constant matrices, already in the swizzled shared layout, in BF16 or
+// FP16 (hi = the element's rounding of the value, lo = that of the remainder).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
-                    const double *Ga_im64, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
+                    const double *Ga_im64, bool f16, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
                     std::vector<uint8_t> &B2l) {
     B1.assign(8192, 0);
     B2h.assign(4096, 0);
     B2l.assign(4096, 0);
-    auto put = [](std::vector<uint8_t> &t, int r, int k, float v) {
-        const uint16_t h = bf16_bits(v);
+    auto bits = [f16](float v) -> uint16_t {
+        if (!f16) return bf16_bits(v);
+        const __half h = __float2half_rn(v);
+        uint16_t u;
+        memcpy(&u, &h, 2);
+        return u;
+    };
+    auto rounded = [f16](float v) -> float {
+        return f16 ? __half2float(__float2half_rn(v)) : bf16_float(bf16_bits(v));
+    };
+    auto put = [&](std::vector<uint8_t> &t, int r, int k, float v) {
+        const uint16_t h = bits(v);
         memcpy(t.data() + sw128_off(r, k), &h, 2);
     };
     // B1[row = c' * 32 + m][K = t * 2n + c * n + q]
@@ -911,7 +1028,7 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
                         else if (c == 1 && cp == 0) val = -fi;
                         else if (c == 0 && cp == 1) val = fi;
                         else val = fr;
-                        const float hi = bf16_float(bf16_bits((float)val));
+                        const float hi = rounded((float)val);
                         const float lo = (float)(val - (double)hi);
                         put(B1, cp * 32 + m, t * 2 * n + c * n + q, t == 2 ? lo : hi);
                     }
@@ -920,7 +1037,7 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
         for (int dx = 0; dx < n; ++dx)
             for (int m = 0; m < N; ++m) {
                 const double val = cpp == 0 ? Ga_re64[dx * N + m] : Ga_im64[dx * N + m];
-                const float hi = bf16_float(bf16_bits((float)val));
+                const float hi = rounded((float)val);
                 const float lo = (float)(val - (double)hi);
                 put(B2h, cpp * 16 + dx, m, hi);
                 put(B2h, cpp * 16 + dx, 32 + m, hi);
@@ -928,9 +1045,9 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
             }
 }
 
-cudaError_t tc_launch_shape(const ShArgs &a, LaunchShape *out) {
-    if (a.n == 10 && a.nd == 16) return shape_tc<10, 16>(a, out);
-    if (a.n == 8 && a.nd == 16) return shape_tc<8, 16>(a, out);
+cudaError_t tc_launch_shape(const ShArgs &a, LaunchShape *out, bool f16) {
+    if (a.n == 10 && a.nd == 16) return shape_tc<10, 16>(a, out, f16);
+    if (a.n == 8 && a.nd == 16) return shape_tc<8, 16>(a, out, f16);
     return cudaErrorInvalidValue;
 }
 

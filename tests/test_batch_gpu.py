@@ -12,12 +12,18 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+MIXED = "mixed"  # tensor-core geometries alternate between BF16 x3 and scaled FP16 x3
+
+
 def _instances(k, seed=4000, prec=inputs.PREC_FP32):
-    insts = inputs.config4_instances(k, seed, precision=prec)
+    insts = inputs.config4_instances(k, seed, precision=inputs.PREC_BF16X3 if prec == MIXED else prec)
     out = []
-    for c in insts:
+    for i, c in enumerate(insts):
         g = c.geometries[0]
-        if prec == inputs.PREC_BF16X3 and not (g.n_fft == 32 and g.n_pix_sub in (8, 10) and g.n_det == 16):
+        tc_ok = g.n_fft == 32 and g.n_pix_sub in (8, 10) and g.n_det == 16
+        if prec == MIXED:
+            g.precision = (inputs.PREC_BF16X3 if i % 2 else inputs.PREC_FP16S) if tc_ok else inputs.PREC_FP32
+        elif prec in (inputs.PREC_BF16X3, inputs.PREC_FP16S) and not tc_ok:
             g.precision = inputs.PREC_FP32
         out.append(c)
     return out
@@ -44,7 +50,7 @@ def _alone(hs, scr, ts):
     return [r.cpu().numpy() for r in res]
 
 
-@pytest.mark.parametrize("prec,noise", [(inputs.PREC_FP32, True), (inputs.PREC_BF16X3, False)])
+@pytest.mark.parametrize("prec,noise", [(inputs.PREC_FP32, True), (inputs.PREC_BF16X3, False), (MIXED, True)])
 def test_uneven_batch_equals_alone(prec, noise):
     insts = _instances(24, 4000, prec)
     hs, scr, outs = _setup(insts, noise)

@@ -280,12 +280,17 @@ def test_host_buffer_path_and_batch_match_device_path():
     w1.close()
 
 
-# ---------------------------------------------------------------- split-BF16 tensor-core DFT
+# ---------------------------------------------------------------- tensor-core DFT (split BF16, scaled FP16)
 
-def test_config3_bf16x3_sampled_parity_full_launch():
-    """The ELT frame with the LGS DFT on the tensor cores (BF16 x3, FP32 accumulation), full
-    launch, sampled subapertures against the FP64 oracle at the same bars as the FP32 path."""
-    cfg = inputs.config3(inputs.PREC_BF16X3)
+TC_PRECISIONS = [inputs.PREC_BF16X3, inputs.PREC_FP16S]
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_config3_bf16x3_sampled_parity_full_launch(precision):
+    """The ELT frame with the LGS DFT on the tensor cores (BF16 x3, or FP16 x3 with power-of-two
+    scaling; FP32 accumulation), full launch, sampled subapertures against the FP64 oracle at
+    the same bars as the FP32 path."""
+    cfg = inputs.config3(precision)
     scr = inputs.make_screens(cfg.layers, cfg.seed)
     t = 0.071
     gpu, w = run_library(cfg, scr, t)
@@ -299,11 +304,12 @@ def test_config3_bf16x3_sampled_parity_full_launch():
     w.close()
 
 
-def test_bf16x3_matches_fp32_path_everywhere():
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_bf16x3_matches_fp32_path_everywhere(precision):
     """Full ELT frame: every subaperture of the tensor-core path against the FP32 path."""
     scr = inputs.make_screens(inputs.config3().layers, 3000)
     a, wa = run_library(inputs.config3(inputs.PREC_FP32), scr, 0.2, stages=True)
-    b, wb = run_library(inputs.config3(inputs.PREC_BF16X3), scr, 0.2, stages=True)
+    b, wb = run_library(inputs.config3(precision), scr, 0.2, stages=True)
     for x, y in zip(a, b):
         assert slope_rms(y["slopes"], x["slopes"]) < SLOPE_RMS
         assert rel_per_subap(y["E"], x["E"]) < INT_REL
@@ -312,13 +318,14 @@ def test_bf16x3_matches_fp32_path_everywhere():
     wb.close()
 
 
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
 @pytest.mark.parametrize("n_sub,n,lgs,noise", [(13, 10, True, False), (11, 8, True, True),
                                                (9, 10, False, False), (7, 8, False, True)])
-def test_bf16x3_edge_geometries(n_sub, n, lgs, noise):
+def test_bf16x3_edge_geometries(n_sub, n, lgs, noise, precision):
     """Ragged groups (valid count not a multiple of 4), NGS spots through the tensor-core
     kernel's binning branch, n = 8 and 10, noise on and off."""
     cfg = _small_cfg(n_sub, n, 32, 16, lgs)
-    cfg.geometries[0].precision = inputs.PREC_BF16X3
+    cfg.geometries[0].precision = precision
     scr = inputs.make_screens(cfg.layers, 8)
     gpu, w = run_library(cfg, scr, 0.003, seed=4, noise=noise)
     assert w.total % 4 != 0 or n_sub == 9
@@ -330,11 +337,31 @@ def test_bf16x3_edge_geometries(n_sub, n, lgs, noise):
     w.close()
 
 
-def test_bf16x3_unsupported_geometry_is_refused():
-    cfg = inputs.config2(inputs.PREC_BF16X3)
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_bf16x3_unsupported_geometry_is_refused(precision):
+    cfg = inputs.config2(precision)
     with pytest.raises(native.WfsError) as ei:
         native.Wfs(cfg)
     assert ei.value.status == native.WFS_EUNSUPPORTED
+
+
+def test_fp16s_error_no_larger_than_bf16x3():
+    """FP16 carries 11 significand bits to BF16's 8, so with its operands scaled into the normal
+    range its split products are the more accurate: on sampled ELT subapertures its largest
+    relative intensity error against the oracle stays within that of BF16 x3 (plus a margin for
+    the FP32 rounding both share).  Prints both errors."""
+    scr = inputs.make_screens(inputs.config3().layers, 77)
+    errs = {}
+    for prec in TC_PRECISIONS:
+        cfg = inputs.config3(prec)
+        gpu, w = run_library(cfg, scr, 0.013)
+        w.close()
+        sel = np.arange(5, len(gpu[0]["slopes"]), 41, dtype=np.int32)
+        ref = oracle.measure_wfs(cfg, scr, 0, 0.013, sel=sel, stages=True)
+        errs[prec] = (rel_per_subap(gpu[0]["I"][sel], ref["I"]), slope_rms(gpu[0]["slopes"][sel], ref["slopes"]))
+    print("intensity rel / slope RMS vs oracle: BF16x3 %.3g / %.3g, FP16S %.3g / %.3g"
+          % (errs[inputs.PREC_BF16X3] + errs[inputs.PREC_FP16S]))
+    assert errs[inputs.PREC_FP16S][0] <= errs[inputs.PREC_BF16X3][0] * 1.05 + 1e-7
 
 
 def test_bounded_wait_reports_timeout_without_fault():

@@ -41,7 +41,7 @@ def test_per_slice_with_uplink_config2():
     w.close()
 
 
-@pytest.mark.parametrize("precision", [inputs.PREC_BF16X3, inputs.PREC_FP32])
+@pytest.mark.parametrize("precision", [inputs.PREC_BF16X3, inputs.PREC_FP16S, inputs.PREC_FP32])
 def test_per_slice_elt_sampled_full_launch(precision):
     """The ELT frame with the per-slice model on the six LGS (8 slices each) at full size, on
     the self-projecting tensor-core kernel (BF16x3) and on the FP32 32-point kernel: sampled
