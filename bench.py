@@ -537,16 +537,20 @@ def main():
     if world > 1:
         dist.barrier()
     e0.record(stream)
+    h2d = d2h = 0
     for k in range(ke):
         native.wfs_measure_host(w.h, host_scr.data_ptr(), k * dt, host_sl.data_ptr(), sp)
+        b_in, b_out = native.wfs_host_transfer_bytes(w.h)  # the library copies only what the frame reads
+        h2d += b_in
+        d2h += b_out
     e1.record(stream)
     torch.cuda.synchronize()
     e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
     e2e = {"value": world * spots * ke / (float(e_ms.item()) / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": int(host_scr.numel() * 4), "d2h_bytes_per_step": int(host_sl.numel() * 4),
-           "steps": ke}
+           "h2d_bytes_per_step": int(round(h2d / ke)), "d2h_bytes_per_step": int(round(d2h / ke)),
+           "host_input_bytes_per_step": int(host_scr.numel() * 4), "steps": ke}
 
     # roofline of the dominant kernel (the spot launch with the most work; launches of other
     # geometries run concurrently on side streams, so event windows overlap), from the live

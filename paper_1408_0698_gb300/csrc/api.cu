@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -134,6 +135,7 @@ struct wfs_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
     unsigned long long host_calls = 0;
+    unsigned long long host_h2d = 0, host_d2h = 0;  // bytes the last host-buffer call copied
     cudaStream_t last_stream = nullptr;
     std::string err;
     // side streams for the spot launches of the second and later geometries
@@ -1166,6 +1168,91 @@ wfs_status wfs_measure_stages(wfs_handle h, const float *screens, double t_s, fl
     return measure_impl(h, screens, t_s, slopes_out, stages, (cudaStream_t)stream);
 }
 
+namespace {
+
+// A run of whole rows of one layer copied host -> device: offset of its first element, rows.
+struct ScreenRows {
+    size_t off;
+    int rows;
+};
+
+// The rows of the turbulent screens that a frame at time t reads (the host-buffer path copies
+// only those).  Per layer, the union over the guide stars of the rows of the projected pupil
+// square at every cone scale the star's model uses (1 for an NGS; 1 - h/range for an LGS, and
+// 1 - h/h_s for each sodium slice of the per-slice model) and of the LGS uplink beam's disc,
+// each widened by the bilinear tap and four rows of margin for rounding; as runs of rows (mod S,
+// runs closer than 64 rows merged).  Whole rows are contiguous, so each run is one linear copy
+// (rectangles of part rows went through the copy engines at a quarter of the linear rate).  The
+// coordinates are the projection's and the uplink's (layer offsets in FP64).
+void screen_rows(const wfs_ctx *h, double t, std::vector<ScreenRows> &out) {
+    const int S = h->S;
+    out.clear();
+    std::vector<uint8_t> mr(S);
+    std::vector<std::pair<int, int>> rr;
+    auto mark = [S](std::vector<uint8_t> &m, double lo, double hi) {
+        const long long a = (long long)std::floor(lo) - 4, b = (long long)std::floor(hi) + 5;
+        if (b - a + 1 >= S) {
+            std::fill(m.begin(), m.end(), (uint8_t)1);
+            return;
+        }
+        for (long long i = a; i <= b; ++i) m[(size_t)(((i % S) + S) % S)] = 1;
+    };
+    auto runs = [S](const std::vector<uint8_t> &m, std::vector<std::pair<int, int>> &r) {
+        r.clear();
+        for (int i = 0; i < S;) {
+            if (!m[i]) {
+                ++i;
+                continue;
+            }
+            int j = i;
+            while (j < S && m[j]) ++j;
+            if (!r.empty() && i - (r.back().first + r.back().second) <= 64)
+                r.back().second = j - r.back().first;
+            else
+                r.push_back({i, j - i});
+            i = j;
+        }
+    };
+    for (int l = 0; l < h->n_layers; ++l) {
+        std::fill(mr.begin(), mr.end(), (uint8_t)0);
+        const double hl = h->alt[l], sy = h->y0[l] + h->vy[l] * t;
+        for (const GsDev &G : h->gs) {
+            const wfs_guide_star &g = G.gs;
+            const wfs_geometry &geo = h->geoms[g.geometry_index].g;
+            const int Np = geo.n_sub * geo.n_pix_sub;
+            const double pdx = (h->tel.diameter_m / Np) / h->ds;  // pupil pitch in screen pixels
+            const double ov = 0.5 * S + (g.theta_y_rad * hl - sy) / h->ds;
+            auto pupil = [&](double c) {
+                const double half = std::fabs(c) * pdx * 0.5 * (Np - 1);
+                mark(mr, ov - half, ov + half);
+            };
+            if (!g.is_lgs) {
+                pupil(1.0);
+                continue;
+            }
+            pupil(1.0 - hl / g.range_m);
+            if (h->per_slice)
+                for (double hs : G.na_alt) pupil(1.0 - hl / hs);
+            if (G.up_diam > 0.0 && hl < g.range_m) {
+                const double cy = g.launch_y_m * (1.0 - hl / g.range_m) + g.theta_y_rad * hl;
+                const double vv = 0.5 * S + (cy - sy) / h->ds, r = 0.5 * G.up_diam / h->ds;
+                mark(mr, vv - r, vv + r);
+            }
+        }
+        runs(mr, rr);
+        for (const auto &a : rr) out.push_back({(size_t)l * S * S + (size_t)a.first * S, a.second});
+    }
+}
+
+}  // namespace
+
+wfs_status wfs_host_transfer_bytes(wfs_handle h, uint64_t *h2d_bytes, uint64_t *d2h_bytes) {
+    if (!h || !h2d_bytes || !d2h_bytes) return fail(h, WFS_EINVAL, "null argument");
+    *h2d_bytes = h->host_h2d;
+    *d2h_bytes = h->host_d2h;
+    return WFS_OK;
+}
+
 wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s, float *slopes_host,
                             void *stream) {
     const NvtxRange nvtx_range("wfs_measure_host");
@@ -1176,8 +1263,11 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
     const size_t nsl = 2 * (size_t)h->total_valid;
     cudaError_t e;
     if (!h->d_screens_stage[0]) {
+        // staging screens start as NaN (all bits set), so a read outside the uploaded parts
+        // shows in the results
         for (int i = 0; i < 2; ++i)
             if ((e = cudaMalloc(&h->d_screens_stage[i], nscr * sizeof(float))) != cudaSuccess ||
+                (e = cudaMemset(h->d_screens_stage[i], 0xFF, nscr * sizeof(float))) != cudaSuccess ||
                 (e = cudaMalloc(&h->d_slopes_stage[i], (nsl + 1) * sizeof(float))) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
@@ -1191,9 +1281,22 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
     // the staging set is free once the frame that used it two calls ago has finished
     if (h->host_calls >= 2 && (e = cudaStreamWaitEvent(h->copy_stream, h->ev_done[i], 0)) != cudaSuccess)
         return cuda_fail(h, e, "host-path wait");
-    if ((e = cudaMemcpyAsync(h->d_screens_stage[i], screens_host, nscr * sizeof(float), cudaMemcpyHostToDevice,
-                             h->copy_stream)) != cudaSuccess ||
-        (e = cudaEventRecord(h->ev_copied[i], h->copy_stream)) != cudaSuccess ||
+    // the rows of the screens this frame reads; the whole set when they cover most of it
+    std::vector<ScreenRows> runs;
+    screen_rows(h, t_s, runs);
+    size_t part = 0;
+    for (const ScreenRows &r : runs) part += (size_t)r.rows * h->S;
+    if (part * 10 >= nscr * 9) {
+        part = nscr;
+        e = cudaMemcpyAsync(h->d_screens_stage[i], screens_host, nscr * sizeof(float), cudaMemcpyHostToDevice,
+                            h->copy_stream);
+    } else {
+        e = cudaSuccess;
+        for (size_t k = 0; k < runs.size() && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(h->d_screens_stage[i] + runs[k].off, screens_host + runs[k].off,
+                                (size_t)runs[k].rows * h->S * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream);
+    }
+    if (e != cudaSuccess || (e = cudaEventRecord(h->ev_copied[i], h->copy_stream)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s, h->ev_copied[i], 0)) != cudaSuccess)
         return cuda_fail(h, e, "screen upload");
     wfs_status st = measure_impl(h, h->d_screens_stage[i], t_s, h->d_slopes_stage[i], nullptr, s);
@@ -1203,6 +1306,8 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
         (e = cudaEventRecord(h->ev_done[i], s)) != cudaSuccess)
         return cuda_fail(h, e, "slope download");
     ++h->host_calls;
+    h->host_h2d = part * sizeof(float);
+    h->host_d2h = nsl * sizeof(float);
     return WFS_OK;
 }
 

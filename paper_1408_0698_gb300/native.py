@@ -96,6 +96,7 @@ _SIGS = {
     "wfs_measure_stages": (C.c_int, [_H, C.c_void_p, C.c_double, C.c_void_p,
                                      C.POINTER(wfs_stage_out), C.c_void_p]),
     "wfs_measure_host": (C.c_int, [_H, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    "wfs_host_transfer_bytes": (C.c_int, [_H, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "wfs_set_noise": (C.c_int, [_H, C.c_int]),
     "wfs_num_valid": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int)]),
     "wfs_total_valid": (C.c_int, [_H, C.POINTER(C.c_int)]),
@@ -213,6 +214,13 @@ def wfs_measure_stages(h, screens_ptr, t, slopes_ptr, opd=0, intensity=0, expect
 
 def wfs_measure_host(h, screens_host_ptr, t, slopes_host_ptr, stream=0):
     _check(lib().wfs_measure_host(h, screens_host_ptr, float(t), slopes_host_ptr, stream), h)
+
+
+def wfs_host_transfer_bytes(h):
+    """(host -> device, device -> host) bytes of the handle's last wfs_measure_host call."""
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(lib().wfs_host_transfer_bytes(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
 
 
 def wfs_set_noise(h, enable):

@@ -104,6 +104,8 @@ def test_null_arguments():
     assert L.wfs_loop_batch_destroy(None) == native.WFS_EINVAL
     assert L.wfs_set_uplink(None, 0, 0.5, 16) == native.WFS_EINVAL
     assert L.wfs_set_lgs_model(None, 1) == native.WFS_EINVAL
+    u = C.c_uint64()
+    assert L.wfs_host_transfer_bytes(None, C.byref(u), C.byref(u)) == native.WFS_EINVAL
 
 
 def test_no_silent_cpu_path_without_gpu():

@@ -398,6 +398,35 @@ def test_host_path_alternating_buffers():
     w.close()
 
 
+def test_host_path_uploads_only_the_read_parts():
+    """The host-buffer path copies only the parts of the screens a frame reads.  Its staging
+    screens start as NaN and every call brings a different screen set, so a read outside the
+    copied parts would show as NaN or as another frame's data: on the ELT frame (uplink on, then
+    the per-slice model, wind shifts of many pixels) every call equals the device path bit for
+    bit, and less than the whole set was copied."""
+    import dataclasses
+    cfg = inputs.config3()
+    cfg = dataclasses.replace(cfg, stars=[dataclasses.replace(st, uplink_diameter_m=0.4, uplink_samples=16)
+                                          if st.is_lgs else st for st in cfg.stars])
+    w = native.Wfs(cfg, seed=9, noise=True)
+    full = 4 * cfg.layers.screen_size ** 2 * len(cfg.layers.alt_m)
+    out = torch.empty((w.total, 2)).pin_memory()
+    for k, (t, per_slice) in enumerate([(0.0, False), (0.37, False), (1.5, False), (2.2, True), (2.9, True)]):
+        if per_slice:
+            native.wfs_set_lgs_model(w.h, True)
+        scr = inputs.make_screens(cfg.layers, 900 + k)
+        host_scr = torch.as_tensor(scr).pin_memory()
+        native.wfs_measure_host(w.h, host_scr.data_ptr(), t, out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        h2d, d2h = native.wfs_host_transfer_bytes(w.h)
+        assert 0 < h2d < 0.9 * full and d2h == 8 * w.total
+        got = out.numpy().copy()
+        ref, _ = run_library(cfg, scr, t, seed=9, noise=True, stages=False, handle=w)
+        assert np.all(np.isfinite(got)), f"call {k}"
+        assert np.array_equal(got, np.concatenate([d["slopes"] for d in ref])), f"call {k}"
+    w.close()
+
+
 def test_busy_on_another_stream():
     """One stream at a time: while a measurement is still queued or running on one stream, a
     call on another stream is refused with WFS_EBUSY and launches nothing; once it has finished,
