@@ -1,6 +1,7 @@
 // k_sh_tc.cu -- the spot kernel with the DFT contraction on the 5th-generation
 // tensor cores (tcgen05, BF16 hi/lo split with three products, FP32
-// accumulation in tensor memory), for 32-point DFT geometries with n <= 10.
+// accumulation in tensor memory; or the same with FP16 hi/lo and per-subaperture
+// power-of-two operand scaling), for 32-point DFT geometries with n <= 10.
 //
 // Arithmetic (Sec. 4 LGS SH: spot by DFT, sodium elongation, binning, noise,
 // centroid) is that of k_sh.cu; only the two contractions whose second operand
@@ -13,15 +14,16 @@
 //               x [Ga_hi; Ga_hi] (64) then [I_hi | I_lo] x [Ga_lo; 0] (64)
 //
 // Each BF16 pair (x_hi, x_lo = bf16(x - x_hi)) carries ~16 significant bits; the
-// dropped lo*lo products are ~2^-16 of each term.  Operands live in shared memory
+// dropped lo*lo products are ~2^-16 of each term.  An FP16 pair carries ~22 bits once the
+// operand is scaled into FP16's normal range (TcElt).  Operands live in shared memory
 // in the 128-byte-swizzled K-major layout (8-row x 128-byte atoms); one elected
 // thread issues the MMAs and commits them to an mbarrier; every wait is bounded
 // and a timeout is reported in the status word (the kernel then frees its tensor
 // memory and returns).  U = F X, the column transform, binning, photometry,
 // noise and the centroid run on the CUDA cores exactly as in the FP32 kernels.
 //
-// CTA = one warpgroup (4 warps); warp w owns subaperture 4g + w of group g and its
-// lane k owns DFT row k, which is also TMEM lane 32 w + k of both accumulators.
+// CTA = two warpgroups (4 warps each); warp w of a warpgroup owns subaperture 4g + w of its
+// group g and its lane k owns DFT row k, which is also TMEM lane 32 w + k of both accumulators.
 //
 // The per-slice variant (k_sh_tc_sl, launched with ShArgs::slice_opd_stride) runs the LGS
 // per-slice model (Sec. 4: one wavefront and one spot per sodium sub-layer, piled up with the
