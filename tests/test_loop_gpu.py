@@ -284,11 +284,12 @@ def test_calibration_matches_oracle(which):
     L.close()
 
 
-def test_calibration_elt_m4_full_size():
+@pytest.mark.parametrize("precision", [inputs.PREC_BF16X3, inputs.PREC_FP16S])
+def test_calibration_elt_m4_full_size(precision):
     """The paper's calibration workload: the 5000 modes of the 81 x 81 ground mirror with one
-    80 x 80 LGS of the ELT frame (BF16x3 spots), all modes on the GPU; sampled modes from
-    every chunk position against the oracle."""
-    cfg = inputs.config3()
+    80 x 80 LGS of the ELT frame (tensor-core spots, BF16x3 or scaled FP16x3), all modes on the
+    GPU; sampled modes from every chunk position against the oracle."""
+    cfg = inputs.config3(precision)
     dm = inputs.elt_dms()[0]
     M = inputs.modal_base(dm, 40)
     L = _Loop(cfg, [dm], [M], np.zeros((dm.n_modes, 2)), np.zeros(dm.n_modes))
