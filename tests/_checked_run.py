@@ -2,9 +2,10 @@
 
 Run as a child process, once with the normal library and once with the bounds-checked one
 (environment variable GBWFS_CHECKED=1): the parent test compares the two files.  Covered:
-the generic, 32-point and tensor-core spot kernels, the projection (direct and tiled), the
-noise and centroid pass, the uplink tip-tilt, the per-slice LGS model, a loop step with
-mirror layers, a push-pull calibration and a batch of two handles.  Every result is
+the generic, 32-point and tensor-core spot kernels (BF16 x3 and scaled FP16 x3), the projection
+(direct and tiled), the noise and centroid pass, the uplink tip-tilt, the per-slice LGS model,
+the host-buffer path, a loop step with mirror layers, a push-pull calibration and a batch of two
+handles.  Every result is
 followed by wfs_sync_status, which raises on a device status such as WFS_EBOUNDS.
 """
 import dataclasses
@@ -46,12 +47,24 @@ def main(out):
     res["config2"] = _measure(c2, s2, 0.013, noise=True)
     res["config2_uplink"] = _measure(_lgs(c2, uplink_diameter_m=0.5, uplink_samples=16), s2, 0.0)
     res["config2_slices"] = _measure(_lgs(c2, per_slice=True), s2, 0.0)
-    for name, prec in (("elt_bf16x3", inputs.PREC_BF16X3), ("elt_fp32", inputs.PREC_FP32)):
+    for name, prec in (("elt_bf16x3", inputs.PREC_BF16X3), ("elt_fp16s", inputs.PREC_FP16S),
+                       ("elt_fp32", inputs.PREC_FP32)):
         c3 = inputs.config3(prec)
         s3 = _dev(inputs.make_screens(c3.layers, c3.seed))
         res[name] = _measure(c3, s3, 0.05, noise=True)
         res[name + "_slices"] = _measure(_lgs(c3, per_slice=True), s3, 0.05)
         del s3
+
+    # the host-buffer path (only the rows a frame reads are uploaded), two frames
+    w = native.Wfs(c2, seed=4, noise=True)
+    host_scr = torch.as_tensor(inputs.make_screens(c2.layers, c2.seed + 5)).pin_memory()
+    for k, t in enumerate((0.0, 0.8)):
+        hbuf = torch.empty((w.total, 2)).pin_memory()
+        native.wfs_measure_host(w.h, host_scr.data_ptr(), t, hbuf.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        native.wfs_sync_status(w.h)
+        res[f"host{k}"] = hbuf.numpy().copy()
+    w.close()
 
     # a loop step and a calibration on config 2 with two mirrors
     dms = [inputs.Dm(21, 0.4, 0.0, 37), inputs.Dm(15, 0.7, 6000.0, 9)]
