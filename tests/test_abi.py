@@ -117,3 +117,19 @@ def test_no_silent_cpu_path_without_gpu():
     st, h = _create(inputs.config1())
     assert st in (native.WFS_ECUDA, native.WFS_ENOMEM)
     assert not h.value
+
+
+def test_c_example_builds_and_reports_errors(tmp_path):
+    """The plain-C99 example compiles with gcc -Wall -Werror against the header and the library;
+    without a GPU it stops at wfs_create with the library's CUDA error status and message."""
+    torch = pytest.importorskip("torch")
+    from _c_example import compile_example
+    exe = compile_example(str(tmp_path / "measure_frame"))
+    if torch.cuda.is_available():
+        pytest.skip("GPU present: tests/test_c_example_gpu.py runs it")
+    np.zeros(256 * 256, np.float32).tofile(tmp_path / "s.f32")
+    r = subprocess.run([exe, str(tmp_path / "s.f32"), "0.0", str(tmp_path / "o.f32")], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 1
+    assert "wfs_create: status %d" % native.WFS_ECUDA in r.stderr
+
