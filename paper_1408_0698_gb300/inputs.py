@@ -252,7 +252,8 @@ class Dm:
 def elt_dms() -> List[Dm]:
     """The three mirrors of the ELT workload: ground (81 x 81 at the subaperture pitch,
     5000 modes) and post-focal at 4 km (43 x 43, 1 m, 1400 modes) and 12.7 km (50 x 50,
-    1 m, 1800 modes), each wide enough for the 160 arcsec field at its altitude."""
+    1 m, 1800 modes), each with n_act pitches covering the meta-pupil of the 160 arcsec field
+    at its altitude."""
     return [Dm(81, 39.0 / 80.0, 0.0, 5000), Dm(43, 1.0, 4000.0, 1400), Dm(50, 1.0, 12700.0, 1800)]
 
 

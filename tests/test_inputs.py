@@ -68,3 +68,28 @@ def test_config_parameters():
     assert len(insts) == 64
     assert not any(i.stars[0].is_lgs and i.geometries[0].n_sub == 2 for i in insts)
     assert {i.geometries[0].n_fft for i in insts} == {16, 24, 32, 64}
+
+
+def test_mirror_inputs_of_the_elt_workload():
+    """The ELT mirrors: 5000 + 1400 + 1800 = 8200 modes (the paper's M4 count on the ground
+    mirror), the ground grid at the 80 x 80 subaperture pitch over 39 m, and each post-focal
+    grid wide enough for the 160 arcsec field at its altitude; the modal bases and control
+    matrices are seeded, of the stated shapes and amplitudes.  "Wide enough": n_act pitches (the
+    actuator span plus half a pitch at each edge) cover the meta-pupil, D + field x altitude."""
+    dms = inputs.elt_dms()
+    assert [d.n_modes for d in dms] == [5000, 1400, 1800]
+    assert sum(d.n_modes for d in dms) == 8200
+    g = dms[0]
+    assert g.n_act == 81 and g.alt_m == 0.0 and abs(g.pitch_m - 39.0 / 80) < 1e-12
+    field = 160.0 / 3600.0 * math.pi / 180.0
+    for d in dms[1:]:
+        assert d.n_act * d.pitch_m >= 39.0 + field * d.alt_m
+        assert d.n_modes <= d.n_act * d.n_act
+    M = inputs.modal_base(g, 40, amplitude_m=2e-8)
+    assert M.shape == (81 * 81, 5000) and M.dtype == np.float32
+    assert abs(float(M.std()) / 2e-8 - 1) < 0.01
+    np.testing.assert_array_equal(M, inputs.modal_base(g, 40, amplitude_m=2e-8))
+    cm = inputs.random_control_matrix(300, 2000, seed=3, scale=0.5)
+    assert cm.shape == (300, 2000) and cm.dtype == np.float32
+    assert np.abs(cm).max() <= 0.5 / math.sqrt(2000) * (1 + 1e-6)
+    np.testing.assert_array_equal(cm, inputs.random_control_matrix(300, 2000, seed=3, scale=0.5))
