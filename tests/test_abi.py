@@ -22,6 +22,25 @@ def test_library_exports_every_header_symbol():
     assert "sm_103a" in native.wfs_version()
 
 
+def test_binding_argument_counts_match_the_header():
+    """Every prototype in include/gbwfs.h has as many parameters as its ctypes signature, and
+    pointer parameters sit where the binding passes pointers."""
+    import re
+    text = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                             "gbwfs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = dict(re.findall(r"\b(wfs_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text))
+    assert set(protos) == set(native._SIGS)
+    for name, params in protos.items():
+        params = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        argtypes = native._SIGS[name][1]
+        assert len(params) == len(argtypes), (name, params, argtypes)
+        for p, a in zip(params, argtypes):
+            is_ptr = "*" in p or p.startswith("wfs_handle") or p.startswith("wfs_loop") or p.startswith("wfs_batch")
+            a_ptr = issubclass(a, (C._Pointer, C.Array, C.c_void_p, C.c_char_p))
+            assert is_ptr == a_ptr, (name, p, a)
+
+
 def test_checked_library_exports_the_same_symbols():
     """The bounds-checked build (-DGBWFS_CHECK) compiles from the same sources and exports the
     same entry points; it names itself in the version string."""
