@@ -1487,8 +1487,7 @@ cudaError_t batch_build_graph(wfs_batch b) {
     LaunchShape ps;
     project_launch_shape(*b->pa, b->proj_blocks, &ps);
     void *pargs[] = {(void *)b->pa};
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof kp);
+    cudaKernelNodeParams kp = {};
     kp.func = (void *)ps.func;
     kp.gridDim = ps.grid;
     kp.blockDim = ps.block;
@@ -1502,7 +1501,7 @@ cudaError_t batch_build_graph(wfs_batch b) {
         LaunchShape sh;
         if ((e = spot_launch_shape(b->classes[c].kind, *b->sa[c], &sh)) != cudaSuccess) return e;
         void *sargs[] = {(void *)b->sa[c]};
-        memset(&kp, 0, sizeof kp);
+        kp = cudaKernelNodeParams{};
         kp.func = (void *)sh.func;
         kp.gridDim = sh.grid;
         kp.blockDim = sh.block;
@@ -1511,7 +1510,7 @@ cudaError_t batch_build_graph(wfs_batch b) {
         if ((e = cudaGraphAddKernelNode(&b->spot_nodes[c], b->graph, &b->proj_node, 1, &kp)) != cudaSuccess) return e;
         if (!b->sa[c]->split_noise) continue;
         if ((e = noise_cog_launch_shape(*b->sa[c], &sh)) != cudaSuccess) return e;
-        memset(&kp, 0, sizeof kp);
+        kp = cudaKernelNodeParams{};
         kp.func = (void *)sh.func;
         kp.gridDim = sh.grid;
         kp.blockDim = sh.block;
@@ -1528,8 +1527,7 @@ cudaError_t batch_update_graph(wfs_batch b) {
     LaunchShape ps;
     project_launch_shape(*b->pa, b->proj_blocks, &ps);
     void *pargs[] = {(void *)b->pa};
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof kp);
+    cudaKernelNodeParams kp = {};
     kp.func = (void *)ps.func;
     kp.gridDim = ps.grid;
     kp.blockDim = ps.block;
@@ -1541,7 +1539,7 @@ cudaError_t batch_update_graph(wfs_batch b) {
         LaunchShape sh;
         if ((e = spot_launch_shape(b->classes[c].kind, *b->sa[c], &sh)) != cudaSuccess) return e;
         void *sargs[] = {(void *)b->sa[c]};
-        memset(&kp, 0, sizeof kp);
+        kp = cudaKernelNodeParams{};
         kp.func = (void *)sh.func;
         kp.gridDim = sh.grid;
         kp.blockDim = sh.block;
@@ -1550,7 +1548,7 @@ cudaError_t batch_update_graph(wfs_batch b) {
         if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->spot_nodes[c], &kp)) != cudaSuccess) return e;
         if (!b->noise_nodes[c]) continue;
         if ((e = noise_cog_launch_shape(*b->sa[c], &sh)) != cudaSuccess) return e;
-        memset(&kp, 0, sizeof kp);
+        kp = cudaKernelNodeParams{};
         kp.func = (void *)sh.func;
         kp.gridDim = sh.grid;
         kp.blockDim = sh.block;
