@@ -152,3 +152,24 @@ def test_c_example_builds_and_reports_errors(tmp_path):
     assert r.returncode == 1
     assert "wfs_create: status %d" % native.WFS_ECUDA in r.stderr
 
+
+
+def test_product_and_oracle_share_no_code():
+    """The library's sources include nothing from oracle/ and the oracle nothing from the
+    package; the package's Python modules do not import the oracle (only tests/, the smoke entry
+    point and bench.py's CPU legs may)."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1408_0698_gb300")
+    csrc = os.path.join(pkg, "csrc")
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in " ".join(re.findall(r'#include\s*[<"]([^>"]+)[>"]', text)), f
+    for f in os.listdir(os.path.join(root, "oracle")):
+        if f.endswith((".c", ".h")):
+            incs = re.findall(r'#include\s*[<"]([^>"]+)[>"]', open(os.path.join(root, "oracle", f)).read())
+            assert not any("gbwfs" in i or "csrc" in i or "paper_1408" in i for i in incs), (f, incs)
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            text = open(os.path.join(pkg, f)).read()
+            assert not re.search(r"^\s*(import oracle|from oracle)", text, flags=re.M), f
