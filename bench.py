@@ -36,6 +36,8 @@ METRIC = "SH-WFS spots/s & ELT 6-LGS frames/s at ≤1e-3 px slope err; served p5
 UNIT = "spots/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 PRECISIONS = {"fp32": 0, "bf16x3": 1, "fp16s": 2}      # WFS_PREC_FP32, _BF16X3, _FP16S
+WORKLOAD = ("config3 ELT frame: 800x800 px pupil (4.875e-2 m), 6 LGS 80x80 (n=10, N=32, 16x16 det px, "
+            "8 Na slices) + 3 NGS 2x2 (n=32, N=64), 10 layers, noise on")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -160,7 +162,7 @@ def cpu_baseline(cfg, scr, t, target_s=12.0):
     import oracle
     nthreads = oracle.num_threads()
     t0 = time.perf_counter()
-    oracle.measure_wfs(cfg, scr, 0, t, sel=np.arange(0, 4632, 97, dtype=np.int32))
+    oracle.measure_wfs(cfg, scr, 0, t, seed=cfg.seed, noise=True, sel=np.arange(0, 4632, 97, dtype=np.int32))
     per = (time.perf_counter() - t0) / len(range(0, 4632, 97))
     n_lgs_per_wfs = max(1, int(target_s / per / 6))
     stride = max(1, 4632 // n_lgs_per_wfs)
@@ -169,23 +171,23 @@ def cpu_baseline(cfg, scr, t, target_s=12.0):
     for w, s in enumerate(cfg.stars):
         if s.is_lgs:
             sel = np.arange(w % stride, 4632, stride, dtype=np.int32)
-            oracle.measure_wfs(cfg, scr, w, t, sel=sel)
+            oracle.measure_wfs(cfg, scr, w, t, seed=cfg.seed, noise=True, sel=sel)
             spots += len(sel)
         else:
-            spots += len(oracle.measure_wfs(cfg, scr, w, t)["slopes"])
+            spots += len(oracle.measure_wfs(cfg, scr, w, t, seed=cfg.seed, noise=True)["slopes"])
     dt = time.perf_counter() - t0
     # the same oracle on one core, over a sixteenth of that sample (LGS subapertures only)
     oracle.set_threads(1)
     try:
         sel = np.arange(0, 4632, stride * 16, dtype=np.int32)
         t1 = time.perf_counter()
-        oracle.measure_wfs(cfg, scr, 0, t, sel=sel)
+        oracle.measure_wfs(cfg, scr, 0, t, seed=cfg.seed, noise=True, sel=sel)
         dt1 = time.perf_counter() - t1
     finally:
         oracle.set_threads(nthreads)
     return {"value": spots / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{spots} spots of one ELT frame (every {stride}th LGS subaperture of 6 WFSs "
-                      f"+ all 12 NGS subapertures), FP64, {dt:.1f} s",
+                      f"+ all 12 NGS subapertures), FP64, noise on, {dt:.1f} s",
             "single_thread": {"value": len(sel) / dt1, "unit": UNIT, "cores": 1,
                               "sample": f"{len(sel)} LGS subapertures of WFS 0, {dt1:.1f} s"}}
 
@@ -244,15 +246,15 @@ def reference_arm(args):
     scr = inputs.make_screens(cfg.layers, cfg.seed)
     budget = 150.0 / max(1, args.steps + args.warmup)
     t0 = time.perf_counter()
-    oracle.measure_wfs(cfg, scr, 0, 0.0, sel=np.arange(0, 4632, 193, dtype=np.int32))
+    oracle.measure_wfs(cfg, scr, 0, 0.0, seed=cfg.seed, noise=True, sel=np.arange(0, 4632, 193, dtype=np.int32))
     per = (time.perf_counter() - t0) / len(range(0, 4632, 193))
-    per_step = max(1, min(4632 * 6, int(budget / per)))
+    per_step = max(1, min(4632, int(budget / per)))  # subapertures of one LGS WFS per step
     rng = np.random.default_rng(0)
 
     def step(k):
         w = k % 6
-        sel = np.sort(rng.choice(4632, size=min(per_step, 4632), replace=False)).astype(np.int32)
-        oracle.measure_wfs(cfg, scr, w, k * cfg.dt_s, sel=sel)
+        sel = np.sort(rng.choice(4632, size=per_step, replace=False)).astype(np.int32)
+        oracle.measure_wfs(cfg, scr, w, k * cfg.dt_s, seed=cfg.seed, noise=True, sel=sel)
         return len(sel)
 
     for k in range(args.warmup):
@@ -267,10 +269,10 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "ELT frame sample (config3: 6 LGS 80x80 + 3 NGS 2x2, 10 layers)",
-                       "spots_per_step": per_step},
+            "config": {"workload": WORKLOAD, "sample_spots_per_step": per_step},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{per_step} LGS subapertures per step, FP64 oracle"},
+                             "sample": f"{per_step} subapertures of one LGS WFS per step (the six in "
+                                       f"turn), FP64 oracle"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -601,9 +603,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "config3 ELT frame: 800x800 px pupil (4.875e-2 m), 6 LGS 80x80 "
-                                   "(n=10, N=32, 16x16 det px, 8 Na slices) + 3 NGS 2x2 (n=32, N=64), "
-                                   "10 layers, noise on",
+            "config": {"workload": WORKLOAD,
                        "spots_per_frame": spots, "dft_precision": args.precision,
                        "l2": (f"flushed between timed steps ({args.flush_mb} MB write, outside the step events)"
                               if args.flush_mb else "not flushed (profiling run)"),
