@@ -94,6 +94,8 @@ def lib():
             L.orc_convolve.argtypes = [C.c_int, _dp, _dp, _dp]
             L.orc_bin.argtypes = [C.c_int, C.c_int, _dp, _dp]
             L.orc_philox.argtypes = [_up, _up, _up]
+            L.orc_poisson_inversion_n.argtypes = [C.c_float, C.c_int, _fp, _ip]
+            L.orc_poisson_inversion_n.restype = None
             L.orc_noise_pixel.argtypes = [C.c_float, C.c_float, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double, _ip]
             L.orc_noise_pixel.restype = C.c_double
             L.orc_noise_image.argtypes = [C.c_int, _fp, C.c_float, C.c_uint64, C.c_uint32, C.c_double, C.c_uint32, _dp, _ip]
@@ -254,6 +256,14 @@ def philox(ctr, key):
     o = np.zeros(4, dtype=np.uint32)
     lib().orc_philox(_ptr(c, _up), _ptr(k, _up), _ptr(o, _up))
     return o
+
+
+def poisson_inversion(E, u):
+    """The sampler's inversion branch (E < 16) on given FP32 uniforms: the counts it returns."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    k = np.empty(u.size, np.int32)
+    lib().orc_poisson_inversion_n(float(E), u.size, _ptr(u, _fp), _ptr(k, _ip))
+    return k
 
 
 def noise_image(E, read_noise, seed, wfs, t, pixel0=0):

@@ -21,7 +21,11 @@
  * Box-Muller noise, CoG in detector pixels).
  *
  * Build with -ffp-contract=off: the Poisson decisions are taken in FP32 with
- * the same operation order as the GPU kernel, so no fused multiply-adds.
+ * a fixed operation order, so no fused multiply-adds.  A count decided by a
+ * floating-point comparison can only be compared draw by draw if both sides
+ * decide in the same precision with the same roundings; the paper gives no
+ * precision, so the decision is FP32.  The sampler's exact distribution over
+ * every uniform is pinned against the exact Poisson CDF in the tests.
  */
 #include "oracle.h"
 
@@ -344,28 +348,38 @@ static float log_factorial(float k)
     return (x - 0.5f) * logf(x) - x + 0.918938533f + corr;
 }
 
+/* Inversion by sequential search (E < 16): the smallest k with u <= F_k, where
+   F_k = sum_{j<=k} p_j, p_0 = exp(-E) and p_k = p_{k-1} E / k.  FP32, the recurrence
+   evaluated as (p_{k-1} E) (1/k) with 1/k rounded to nearest: three IEEE roundings in
+   a fixed order; the search also stops once F no longer grows.  For E < 16 it stops
+   before k = 43 even at the largest uniform the stream yields. */
+static int32_t poisson_inversion(float E, float u)
+{
+    float p = expf(-E);
+    float F = p;
+    int32_t k = 0;
+    while (u > F) {
+        k = k + 1;
+        p = (p * E) * (1.0f / (float)k);
+        float Fn = F + p;
+        if (Fn == F) break;
+        F = Fn;
+    }
+    return k;
+}
+
+void orc_poisson_inversion_n(float E, int n, const float *u, int32_t *k)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) k[i] = poisson_inversion(E, u[i]);
+}
+
 /* Poisson(E) in FP32: sequential-search inversion for E < 16, Hormann's
-   transformed rejection (PTRS, 1993) for E >= 16.  The inversion recurrence
-   p_k = p_{k-1} E / k is evaluated as (p_{k-1} E) (1/k), 1/k rounded to nearest:
-   three IEEE roundings in a fixed order.  For E < 16 the search stops before
-   k = 43 even at the largest uniform the stream yields. */
+   transformed rejection (PTRS, 1993) for E >= 16. */
 static int32_t poisson_f32(float E, ustream *s)
 {
     if (!(E > 0.0f)) return 0;
-    if (E < 16.0f) {
-        float u = us_next(s);
-        float p = expf(-E);
-        float F = p;
-        int32_t k = 0;
-        while (u > F) {
-            k = k + 1;
-            p = (p * E) * (1.0f / (float)k);
-            float Fn = F + p;
-            if (Fn == F) break;
-            F = Fn;
-        }
-        return k;
-    }
+    if (E < 16.0f) return poisson_inversion(E, us_next(s));
     float slam = sqrtf(E);
     float logE = logf(E);
     float b = 0.931f + 2.53f * slam;

@@ -84,6 +84,10 @@ void orc_convolve(int N, const double *I, const double *K, double *out);
 void orc_bin(int N, int nd, const double *I, double *B);
 /* Philox4x32-10 block function. */
 void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The inversion branch of the Poisson sampler (E < 16) on given uniforms u[0..n): k[i] is
+   the count that the sampler returns for uniform u[i].  Exposed so that the sampler's exact
+   distribution can be tabulated over every uniform the generator can yield. */
+void orc_poisson_inversion_n(float E, int n, const float *u, int32_t *k);
 /* One detector pixel's noisy count; *k_out receives the Poisson draw.  Pixels 2m and 2m + 1
    share Philox block 0 of counter m (read noise from its words 0-1, Poisson from word 2 or 3). */
 double orc_noise_pixel(float E, float read_noise, uint64_t seed, uint32_t pixel,

@@ -320,6 +320,26 @@ def test_frozen_flow_long_run_exact():
 
 # ---------------------------------------------------------------- P10: noise
 
+# Known-answer vectors of Philox4x32-10: Salmon, Moraes, Dror and Shaw, "Parallel random
+# numbers: as easy as 1, 2, 3", SC'11; the vectors are the ones distributed with the authors'
+# Random123 library (counter, key -> output; all-zero, all-ones, and the digits of pi).
+PHILOX_KAT = [
+    ([0x00000000, 0x00000000, 0x00000000, 0x00000000], [0x00000000, 0x00000000],
+     [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+    ([0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF], [0xFFFFFFFF, 0xFFFFFFFF],
+     [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+]
+
+
+@pytest.mark.parametrize("ctr,key,expect", PHILOX_KAT)
+def test_philox_known_answers(ctr, key, expect):
+    """The generator is Philox4x32-10 exactly: a wrong multiplier, Weyl constant, round count
+    or word permutation changes every output word of these published vectors."""
+    assert [int(v) for v in oracle.philox(ctr, key)] == expect
+
+
 def test_philox_uniformity_and_independence():
     n = 1 << 16
     vals = np.zeros((n, 4), np.uint32)
@@ -356,6 +376,64 @@ def test_poisson_moments(E):
     keep = expct > 20
     chi2 = np.sum((obs[keep] - expct[keep]) ** 2 / expct[keep])
     assert chi2 < keep.sum() + 6 * math.sqrt(2 * keep.sum()) + 10
+
+
+ALL_UNIFORMS = None
+
+
+def _all_uniforms():
+    """Every uniform the generator can yield: ((x >> 9) + 1/2) 2^-23 for the 2^23 values of
+    x >> 9, each taken with the same probability (exact in FP32)."""
+    global ALL_UNIFORMS
+    if ALL_UNIFORMS is None:
+        m = np.arange(1 << 23, dtype=np.float64)
+        ALL_UNIFORMS = ((m + 0.5) / 2.0 ** 23).astype(np.float32)
+    return ALL_UNIFORMS
+
+
+@pytest.mark.parametrize("E", [1e-3, 0.05, 0.5, 1.0, 2.5, 5.0, 7.77, 10.0, 12.5, 15.0, 15.999])
+def test_inversion_exact_distribution_is_poisson(E):
+    """The sampler's inversion branch (E < 16, FP32 decisions) tabulated over every uniform
+    the generator yields: its exact CDF P(K <= k) is the Poisson CDF of its mean within the
+    FP32 rounding of the running sum, |P32 - F| <= (4k + 2) 2^-24 + 2^-23 (the recurrence
+    p_k = p_{k-1} E / k costs three roundings a step, the running sum one more, the uniform
+    grid 2^-23).  Tabulating every uniform resolves the rounding itself: any slip in the
+    recurrence (an index, exp(-E), the stopping test) is off by orders of magnitude more.
+    The same table bounds how often an exact-arithmetic decision on the same uniform would
+    differ: at most the summed CDF gaps, under 1e-4 of the draws."""
+    from scipy.stats import poisson
+
+    E = np.float32(E)
+    k = oracle.poisson_inversion(E, _all_uniforms())
+    cnt = np.bincount(k)
+    ks = np.arange(len(cnt))
+    P32 = np.cumsum(cnt) / 2.0 ** 23
+    F = poisson.cdf(ks, float(E))
+    assert np.all(np.abs(P32 - F) <= (4 * ks + 2) * 2.0 ** -24 + 2.0 ** -23)
+    # uniforms whose FP32 decision differs from the exact one lie between the two CDFs
+    assert np.sum(np.abs(P32 - F)) < 1e-4
+    # pmf mean equals E within the same rounding
+    assert abs(np.sum(ks * cnt) / 2.0 ** 23 - float(E)) < 1e-4 * max(1.0, float(E))
+
+
+@pytest.mark.parametrize("E", [16.0, 23.5, 80.0, 1000.0])
+def test_ptrs_pmf_large_sample(E):
+    """PTRS regime (E >= 16): 2^22 draws against the exact Poisson pmf, chi-square over the
+    bins with more than 50 expected counts, and the mean and variance within 5 standard
+    errors (Hormann 1993's transformed rejection is exact in exact arithmetic)."""
+    n = 1 << 22
+    _, K = oracle.noise_image(np.full(n, E, np.float32), 0.0, 2024, 6, 0.375)
+    ks = np.arange(max(0, int(E - 6 * math.sqrt(E))), int(E + 6 * math.sqrt(E)) + 2)
+    logp = np.array([-E + k * math.log(E) - math.lgamma(k + 1) for k in ks])
+    expct = n * np.exp(logp)
+    inside = (K >= ks[0]) & (K <= ks[-1])
+    obs = np.bincount(K[inside] - ks[0], minlength=len(ks))
+    keep = expct > 50
+    chi2 = np.sum((obs[keep] - expct[keep]) ** 2 / expct[keep])
+    dof = keep.sum()
+    assert chi2 < dof + 6 * math.sqrt(2 * dof) + 10, (chi2, dof)
+    assert abs(K.mean() - E) < 5 * math.sqrt(E / n)
+    assert abs(K.var() / E - 1) < 5 * math.sqrt(2.0 / n)
 
 
 def test_inversion_search_length_bound():
