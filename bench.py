@@ -71,6 +71,34 @@ def spot_flops(n, N, nd, lgs):
     return f
 
 
+def dft_useful_flops(n, N):
+    """Useful flops of the spot DFT Y = F X F^T with F in C^{N x n} (FMA = 2): 8 N n (n + N)."""
+    return 8 * N * n * (n + N)
+
+
+# Stages of the 32-point LGS spot kernels that run as tcgen05 MMAs, with their useful FP32 flops
+# (FMA = 2) and the BF16 flops the MMAs issue per subaperture (tile shapes of k_sh_tc: M = 128
+# rows = 4 subapertures x 32 DFT rows, so per subaperture 32 rows of each MMA).
+TC_STAGES = {
+    # Y = U F^T: 8 N^2 n useful; issued N = 64, K = 64 (three split products in one K atom)
+    "Y": (lambda n, N, nd: 8 * N * N * n, lambda n, N, nd: 2 * 32 * 64 * 64),
+    # Ta = I Ga^T: 4 N^2 n useful; issued two chains of N = 32, K = 64
+    "Ta": (lambda n, N, nd: 4 * N * N * n, lambda n, N, nd: 2 * 2 * 32 * 32 * 64),
+    # U = F X: 8 N n^2 useful; issued four MMAs of M = 128 per 4 subapertures (one per
+    # subaperture's field tile), N = 32, K = 64
+    "U": (lambda n, N, nd: 8 * N * n * n, lambda n, N, nd: 2 * 128 * 32 * 64),
+}
+
+
+def tc_stages(kernel_name):
+    """The MMA stages of a spot kernel (by its timing name)."""
+    if kernel_name.startswith("spot_tcu"):
+        return ("U", "Y", "Ta")
+    if kernel_name.startswith("spot_tc"):
+        return ("Y", "Ta")
+    return ()
+
+
 def source_sha(names):
     h = hashlib.sha256()
     for nm in names:
@@ -157,9 +185,18 @@ class ClockSampler:
 
 
 def cpu_baseline(cfg, scr, t, target_s=12.0):
-    """The FP64 oracle, as it stands, on this host's cores, over a bounded sample of the
-    ELT frame: every k-th subaperture of each LGS WFS plus all NGS subapertures."""
+    """The FP64 oracle on this host's cores, over a bounded sample of the ELT frame: every k-th
+    subaperture of each LGS WFS plus all NGS subapertures.  The elongation runs in the oracle's
+    separable form (pinned equal to its direct periodic convolution), as the timing plan asks."""
     import oracle
+    oracle.set_separable(True)
+    try:
+        return _cpu_baseline(oracle, cfg, scr, t, target_s)
+    finally:
+        oracle.set_separable(False)
+
+
+def _cpu_baseline(oracle, cfg, scr, t, target_s):
     nthreads = oracle.num_threads()
     t0 = time.perf_counter()
     oracle.measure_wfs(cfg, scr, 0, t, seed=cfg.seed, noise=True, sel=np.arange(0, 4632, 97, dtype=np.int32))
@@ -187,7 +224,7 @@ def cpu_baseline(cfg, scr, t, target_s=12.0):
         oracle.set_threads(nthreads)
     return {"value": spots / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"{spots} spots of one ELT frame (every {stride}th LGS subaperture of 6 WFSs "
-                      f"+ all 12 NGS subapertures), FP64, noise on, {dt:.1f} s",
+                      f"+ all 12 NGS subapertures), FP64, separable elongation, noise on, {dt:.1f} s",
             "single_thread": {"value": len(sel) / dt1, "unit": UNIT, "cores": 1,
                               "sample": f"{len(sel)} LGS subapertures of WFS 0, {dt1:.1f} s"}}
 
@@ -204,27 +241,27 @@ def replica_throughput(local_ms, spots_per_step, steps, world, dev):
     return world * spots_per_step * steps / (ms_max / 1e3), world * steps / (ms_max / 1e3), ms_max
 
 
-def served(load=0.8, duration_s=4.0, n_runs=32, budget_gb=150.0, slots=3, other_loads=(0.5, 0.95),
-           small_budget_gb=1.0):
+def served(load=0.8, duration_s=20.0, n_runs=32, budget_gb=150.0, slots=3, other_loads=(0.5, 0.95),
+           small_budget_gb=1.0, other_duration_s=4.0):
     """Continuous-batching serving of frame requests from n_runs concurrent MC runs drawn from
     configs 1-3, device-resident (admitted by HBM footprint), Poisson arrivals at `load` times
-    the measured batched capacity; p50/p99 latency and served throughput.  Also the other
-    offered loads, and `load` under a small HBM budget at which admission binds (runs wait for
-    earlier runs to retire)."""
+    the measured batched capacity over duration_s of traffic; p50/p99 latency and served
+    throughput.  Also the other offered loads, and `load` under a small HBM budget at which
+    admission binds (runs wait for earlier runs to retire), over other_duration_s each."""
     from paper_1408_0698_gb300 import serving
     runs = serving.make_runs(n_runs, 5000)
     budget = int(budget_gb * (1 << 30))
     cap = serving.capacity(runs, budget, slots)
 
-    def one(ld, bud, preadmit=True):
-        arrivals = serving.poisson_arrivals(runs, ld * cap / n_runs, duration_s, seed=11)
+    def one(ld, bud, preadmit=True, dur=other_duration_s):
+        arrivals = serving.poisson_arrivals(runs, ld * cap / n_runs, dur, seed=11)
         srv = serving.Server(runs, bud, slots)
         if preadmit:
             srv.preadmit()
         return srv.serve(arrivals).summary()
 
-    st = one(load, budget)
-    st.update({"load": load, "capacity_frames_per_s": cap, "runs": n_runs, "budget_gb": budget_gb,
+    st = one(load, budget, dur=duration_s)
+    st.update({"traffic_s": duration_s, "other_traffic_s": other_duration_s, "load": load, "capacity_frames_per_s": cap, "runs": n_runs, "budget_gb": budget_gb,
                "slots": slots, "mix": "configs 1-3 (seeded)"})
     keys = ("p50_ms", "p99_ms", "frames_per_s", "spots_per_s", "mean_batch", "max_admitted")
     st["other_loads"] = [dict({"load": ld}, **{k: v for k, v in one(ld, budget).items() if k in keys})
@@ -244,6 +281,7 @@ def reference_arm(args):
     from paper_1408_0698_gb300 import inputs
     cfg = inputs.config3(inputs.PREC_FP32)
     scr = inputs.make_screens(cfg.layers, cfg.seed)
+    oracle.set_separable(True)  # the timing form of the elongation (pinned equal to the direct one)
     budget = 150.0 / max(1, args.steps + args.warmup)
     t0 = time.perf_counter()
     oracle.measure_wfs(cfg, scr, 0, 0.0, seed=cfg.seed, noise=True, sel=np.arange(0, 4632, 193, dtype=np.int32))
@@ -272,7 +310,7 @@ def reference_arm(args):
             "config": {"workload": WORKLOAD, "sample_spots_per_step": per_step},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"{per_step} subapertures of one LGS WFS per step (the six in "
-                                       f"turn), FP64 oracle"},
+                                       f"turn), FP64 oracle, separable elongation"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -572,24 +610,10 @@ def main():
     roof = None
     if spots_k:
         name = max(spots_k, key=spot_work)
-        launches, tot_ms = ktimes[name]
-        avg_s = tot_ms / launches / 1e3
-        flops = spot_work(name)
-        ach = flops / avg_s / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
-                "traffic": ncu_traffic("spot_n32" if name.startswith("spot_n32") else
-                                       "spot_tc" if name.startswith("spot_tc") else "spot"),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3}
-        if name.startswith("spot_tc"):
-            # the two tensor-core contractions: M = 32 rows per subaperture, N x K = 64 x 64 and
-            # 32 x 128 BF16 issued per row (three split products included)
-            nv = sum(w.layouts[k].n_valid for k, s in enumerate(cfg.stars)
-                     if cfg.geometries[s.geometry_index].n_fft == 32)
-            tflops = nv * 2 * 32 * (64 * 64 + 32 * 128) / avg_s / 1e12
-            roof["tensor_pipe"] = {"achieved": tflops, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                                   "frac": tflops / pk["bf16_tflops"], "peak_source": kind}
+        roof = spot_roofline(name, ktimes[name], cfg, w, pk, kind)
+    if "project" in ktimes:
+        if roof is not None:
+            roof["projection"] = projection_roofline(ktimes["project"], cfg, w, pk, kind, args.warmup * dt)
     if "noise_cog" in ktimes:
         # the noise-and-centroid pass: detector pixels of the 32-point subapertures per second
         launches, tot_ms = ktimes["noise_cog"]
@@ -641,6 +665,102 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def spot_roofline(name, timing, cfg, w, pk, kind):
+    """Roofline of a spot launch from its live per-launch time: the CUDA-core flops (the
+    algorithmic flops minus those of the stages that run as MMAs) against the FP32 peak (the
+    bound), and beside it the DFT's useful flops 8 N n (n + N) against the measured BF16
+    tensor peak, with the BF16 flops the MMAs issue."""
+    launches, tot_ms = timing
+    avg_s = tot_ms / launches / 1e3
+    N = int(name.split("N")[-1])
+    stages = tc_stages(name)
+    total = cuda = useful = issued = 0
+    for k, s in enumerate(cfg.stars):
+        g = cfg.geometries[s.geometry_index]
+        if g.n_fft != N:
+            continue
+        nv = w.layouts[k].n_valid
+        n, nd = g.n_pix_sub, g.n_det
+        f = spot_flops(n, N, nd, s.is_lgs)
+        on_tc = sum(TC_STAGES[st][0](n, N, nd) for st in stages) if s.is_lgs else 0
+        total += nv * f
+        cuda += nv * (f - on_tc)
+        useful += nv * dft_useful_flops(n, N)
+        issued += nv * sum(TC_STAGES[st][1](n, N, nd) for st in stages) if s.is_lgs else 0
+    ach = cuda / avg_s / 1e12
+    roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_PEAK_TFLOPS,
+            "traffic": ncu_traffic("spot_n32" if name.startswith("spot_n32") else
+                                   "spot_tc" if name.startswith("spot_tc") else "spot"),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+            "flops_per_launch": cuda, "flops_note": "CUDA-core flops only (the MMA stages excluded)",
+            "algorithmic_flops_per_launch": total, "avg_launch_ms": avg_s * 1e3}
+    if stages:
+        t_use = useful / avg_s / 1e12
+        t_iss = issued / avg_s / 1e12
+        roof["tensor_pipe"] = {"useful_dft_flops_per_launch": useful, "achieved": t_use,
+                               "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": t_use / pk["bf16_tflops"],
+                               "issued_bf16_flops_per_launch": issued, "issued_achieved": t_iss,
+                               "issued_frac": t_iss / pk["bf16_tflops"], "mma_stages": list(stages),
+                               "peak_source": f"{kind} (burst)"}
+    return roof
+
+
+def projection_footprint_bytes(cfg, valid_maps, t):
+    """Algorithmic bytes of one projection launch of the 32-point group: every screen pixel
+    that the bilinear taps of the valid pupil pixels touch, counted once per layer (4 B), plus
+    the projected OPD written (4 B per valid pupil pixel).  valid_maps[k]: star k's valid
+    subaperture indices (row-major)."""
+    L = cfg.layers
+    S, ds = L.screen_size, L.screen_dx_m
+    tel = cfg.telescope
+    touched = 0
+    opd_bytes = 0
+    members = [k for k, s in enumerate(cfg.stars) if cfg.geometries[s.geometry_index].n_fft == 32]
+    for l in range(L.n_layers):
+        mask = np.zeros((S, S), bool)
+        h = L.alt_m[l]
+        for k in members:
+            s = cfg.stars[k]
+            g = cfg.geometries[s.geometry_index]
+            n, ns = g.n_pix_sub, g.n_sub
+            Np = ns * n
+            dx = tel.diameter_m / Np
+            idx = np.asarray(valid_maps[k])
+            sy, sx = np.divmod(idx, ns)
+            p, q = np.mgrid[0:n, 0:n]
+            i = (sy[:, None, None] * n + p[None]).ravel()
+            j = (sx[:, None, None] * n + q[None]).ravel()
+            if l == 0:
+                opd_bytes += 4 * i.size
+            x = (j - (Np - 1) / 2.0) * dx
+            y = (i - (Np - 1) / 2.0) * dx
+            c = 1.0 - h / s.range_m if s.is_lgs else 1.0
+            u = S / 2.0 + (c * x + s.theta_x_rad * h - (L.x0_m[l] + L.wind_vx_mps[l] * t)) / ds
+            v = S / 2.0 + (c * y + s.theta_y_rad * h - (L.y0_m[l] + L.wind_vy_mps[l] * t)) / ds
+            iu = np.floor(u).astype(np.int64)
+            iv = np.floor(v).astype(np.int64)
+            for a in (0, 1):
+                for b in (0, 1):
+                    mask[(iv + b) % S, (iu + a) % S] = True
+        touched += int(mask.sum())
+    return 4 * touched + opd_bytes, 4 * touched, opd_bytes
+
+
+def projection_roofline(timing, cfg, w, pk, kind, t):
+    """HBM roofline of the projection: algorithmic bytes (unique screen footprint + OPD) over
+    its live per-launch time, against the measured copy bandwidth."""
+    launches, tot_ms = timing
+    avg_s = tot_ms / launches / 1e3
+    from paper_1408_0698_gb300 import native
+    maps = [native.wfs_valid_map(w.h, k) for k in range(len(cfg.stars))]
+    tot, scr_b, opd_b = projection_footprint_bytes(cfg, maps, t)
+    gbs = tot / avg_s / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "bytes_per_launch": tot, "screen_footprint_bytes": scr_b, "opd_bytes": opd_b,
+            "avg_launch_ms": avg_s * 1e3, "traffic": ncu_traffic("project"), "peak_source": kind}
 
 
 def time_frames(w, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, steps, kernel_steps=30):

@@ -28,7 +28,8 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (OpenMP, no FP contraction)."""
+    """Compile oracle.c with gcc (-O3, OpenMP, no FP contraction; no machine-specific flags, so
+    the x86 and Arm builds give the same results)."""
     src = os.path.join(_HERE, "oracle.c")
     hdr = os.path.join(_HERE, "oracle.h")
     if (not force and os.path.exists(_SO)
@@ -36,7 +37,7 @@ def build(force: bool = False) -> str:
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+    cmd = ["gcc", "-O3", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
            src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
@@ -92,6 +93,11 @@ def lib():
             L.orc_dft2.argtypes = [C.c_int, C.c_int, _dp, _dp, _dp, _dp]
             L.orc_elong_kernel.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(_Star), _dp]
             L.orc_convolve.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.orc_elong_convolve_separable.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                                       C.POINTER(_Star), _dp, _dp]
+            L.orc_elong_convolve_separable.restype = None
+            L.orc_set_separable.argtypes = [C.c_int]
+            L.orc_set_separable.restype = None
             L.orc_bin.argtypes = [C.c_int, C.c_int, _dp, _dp]
             L.orc_philox.argtypes = [_up, _up, _up]
             L.orc_poisson_inversion_n.argtypes = [C.c_float, C.c_int, _fp, _ip]
@@ -234,6 +240,22 @@ def elong_kernel(N, pix_rad, rbx, rby, star):
     K = np.zeros((N, N))
     lib().orc_elong_kernel(N, pix_rad, rbx, rby, C.byref(s), _ptr(K, _dp))
     return K
+
+
+def elong_convolve_separable(I, pix_rad, rbx, rby, star):
+    """The elongation (kernel of elong_kernel, convolution of convolve) in separable form."""
+    keep = _Keep()
+    s = _star(star, keep)
+    I = _f64(I)
+    out = np.zeros_like(I)
+    lib().orc_elong_convolve_separable(I.shape[0], pix_rad, rbx, rby, C.byref(s), _ptr(I, _dp), _ptr(out, _dp))
+    return out
+
+
+def set_separable(on: bool) -> None:
+    """measure_wfs's elongation form: the direct periodic convolution (default, parity) or the
+    separable form (timing)."""
+    lib().orc_set_separable(int(bool(on)))
 
 
 def convolve(I, K):

@@ -80,6 +80,12 @@ void orc_elong_kernel(int N, double pix_rad, double rbx, double rby, const orc_s
                       double *K);
 /* Periodic convolution out = I (*) K on an N x N grid. */
 void orc_convolve(int N, const double *I, const double *K, double *out);
+/* The elongation kernel's convolution in separable form (per slice along rows then columns),
+   equal to orc_elong_kernel + orc_convolve up to summation order. */
+void orc_elong_convolve_separable(int N, double pix_rad, double rbx, double rby,
+                                  const orc_star *gs, const double *I, double *out);
+/* orc_measure_wfs's elongation: 0 = direct periodic convolution (default), 1 = separable. */
+void orc_set_separable(int on);
 /* b x b binning, b = N / nd. */
 void orc_bin(int N, int nd, const double *I, double *B);
 /* Philox4x32-10 block function. */

@@ -1,6 +1,7 @@
 """Uneven batches (config-4 style): one projection launch plus one persistent spot launch per
 kernel class, replayed as a CUDA graph, must give the same slopes as measuring every handle
-alone -- bit for bit, with and without the graph, before and after autotuning."""
+alone -- bit for bit, with and without the graph, before and after autotuning -- and sampled
+subapertures of every instance must match the FP64 oracle."""
 import os
 
 import numpy as np
@@ -10,6 +11,7 @@ from paper_1408_0698_gb300 import inputs, native
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+from _gpu import check_against_oracle  # noqa: E402
 
 
 MIXED = "mixed"  # tensor-core geometries alternate between BF16 x3 and scaled FP16 x3
@@ -65,6 +67,12 @@ def test_uneven_batch_equals_alone(prec, noise):
         ref = _alone(hs, scr, ts)
         for i, (o, r) in enumerate(zip(outs, ref)):
             assert np.array_equal(o.cpu().numpy(), r), f"instance {i} step {step}"
+        if step == 1:
+            # every instance (each geometry, precision and layer count config 4 draws) against
+            # the oracle on sampled subapertures of each of its WFSs
+            for i, (c, w, o) in enumerate(zip(insts, hs, outs)):
+                check_against_oracle(c, scr[i].cpu().numpy(), ts[i], o.cpu().numpy(), w.layouts,
+                                     seed=c.seed, noise=noise, per_wfs=12)
     # tuning changes launch shapes only, never results
     ts = [0.05 + 1e-4 * i for i in range(len(hs))]
     native.wfs_batch_tune(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)

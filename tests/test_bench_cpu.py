@@ -36,3 +36,48 @@ def test_traffic_table_entries():
         lgs = 6 * 4632
         alg = lgs * (19 * 10 * 8 + 100 * 4)
         assert 0.95 < (v - 2.3e6) / alg < 1.05
+
+
+def test_cuda_core_and_tensor_split():
+    """The roofline's split of a 32-point LGS subaperture: with Y = U F^T and Ta = I Ga^T as MMAs
+    the CUDA cores keep 204,904 - 81,920 - 40,960 = 82,024 flops; with U = F X as an MMA too,
+    56,424.  The tensor figure divides the useful DFT flops, 8 N n (n + N) = 107,520."""
+    n, N, nd = 10, 32, 16
+    tot = bench.spot_flops(n, N, nd, True)
+    on_tc = lambda name: sum(bench.TC_STAGES[s][0](n, N, nd) for s in bench.tc_stages(name))
+    assert tot - on_tc("spot_tc_bf16x3_N32") == 82024
+    assert tot - on_tc("spot_tcu_bf16x3_N32") == 82024 - 25600
+    assert on_tc("spot_n32_fp32_N32") == 0
+    assert bench.dft_useful_flops(n, N) == 107520
+    # issued BF16 flops per subaperture of the two original MMA chains: 32 rows x (64 x 64 + 2 x 32 x 64)
+    iss = sum(bench.TC_STAGES[s][1](n, N, nd) for s in bench.tc_stages("spot_tc_bf16x3_N32"))
+    assert iss == 2 * 32 * (64 * 64 + 2 * 32 * 64)
+
+
+def test_projection_footprint_bytes():
+    """Algorithmic bytes of the projection: one on-axis NGS through one ground layer at integer
+    offsets touches the pupil's pixels plus one more row and column (the bilinear taps), once;
+    two stars through the same ground layer at the same position count the screen once."""
+    import dataclasses
+
+    import numpy as np
+
+    import oracle
+    from paper_1408_0698_gb300 import inputs
+
+    cfg = inputs.config1()
+    g = cfg.geometries[0]
+    idx, _ = oracle.valid_subaps(cfg.telescope.diameter_m, cfg.telescope.obstruction, g.n_sub, g.n_pix_sub)
+    # 16-point geometry: make it the 32-point group the function measures
+    cfg.geometries[0] = dataclasses.replace(g, n_fft=32, n_det=16)
+    cfg.layers = dataclasses.replace(cfg.layers, wind_vx_mps=np.zeros(1), wind_vy_mps=np.zeros(1),
+                                     x0_m=np.zeros(1), y0_m=np.zeros(1))
+    tot, scr, opd = bench.projection_footprint_bytes(cfg, [idx], 0.0)
+    n_pix = len(idx) * g.n_pix_sub ** 2
+    assert opd == 4 * n_pix
+    # pupil pixel centres sit at half-pixel screen coordinates: each touches a 2 x 2 block, and the
+    # union over a subaperture of n x n pixels is (n + 1)^2 screen pixels less the shared edges
+    assert n_pix < scr / 4 < 1.5 * n_pix
+    cfg.stars = [cfg.stars[0], dataclasses.replace(cfg.stars[0])]
+    tot2, scr2, opd2 = bench.projection_footprint_bytes(cfg, [idx, idx], 0.0)
+    assert scr2 == scr and opd2 == 2 * opd

@@ -205,6 +205,40 @@ def test_convolution_matches_fft_and_conserves_energy():
     assert abs(out.sum() - I.sum()) < 1e-11 * I.sum()
 
 
+@pytest.mark.parametrize("N,shift", [(16, (0.3, -2.7)), (24, (5.5, 1.25)), (32, (-11.0, 7.4))])
+def test_separable_elongation_equals_direct(N, shift):
+    """The separable form (rows then columns, per slice) equals the elongation kernel's direct
+    periodic convolution to rounding, for an elongation longer than the field (wrap)."""
+    rng = np.random.default_rng(N)
+    I = rng.random((N, N)) ** 3
+    star = _one_slice_star(90e3, 90e3, 1.0 * 4.848e-6)
+    star.na_alt_m = np.array([84e3, 88e3, 90e3, 93e3, 97e3])
+    star.na_weight = np.array([0.1, 0.25, 0.3, 0.2, 0.15])
+    star.launch_x_m, star.launch_y_m = 5.0, -2.0
+    pix = 589e-9 / (N * 0.05)
+    rbx, rby = 5.0 + shift[0], -2.0 + shift[1]
+    K = oracle.elong_kernel(N, pix, rbx, rby, star)
+    direct = oracle.convolve(I, K)
+    sep = oracle.elong_convolve_separable(I, pix, rbx, rby, star)
+    assert np.max(np.abs(sep - direct)) <= 1e-13 * np.abs(direct).max()
+
+
+def test_measure_wfs_separable_equals_direct():
+    """measure_wfs with the separable elongation (the timed CPU baseline) gives the stages and
+    slopes of the direct form to rounding."""
+    cfg = inputs.config2()
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    sel = np.arange(0, 1264, 37, dtype=np.int32)
+    a = oracle.measure_wfs(cfg, scr, 1, 0.01, sel=sel, stages=True)
+    oracle.set_separable(True)
+    try:
+        b = oracle.measure_wfs(cfg, scr, 1, 0.01, sel=sel, stages=True)
+    finally:
+        oracle.set_separable(False)
+    assert np.max(np.abs(a["Ie"] - b["Ie"])) <= 1e-12 * np.abs(a["Ie"]).max()
+    assert np.max(np.abs(a["slopes"] - b["slopes"])) <= 1e-10
+
+
 def test_elongation_centroid_and_antisymmetry():
     """Narrow slices, small shifts: the kernel's first moment is sum_s w_s Delta_s, and
     mirroring the subap about the launch point mirrors the kernel."""

@@ -8,6 +8,7 @@ from paper_1408_0698_gb300 import inputs, native, serving
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+from _gpu import check_against_oracle  # noqa: E402
 
 
 def _small_runs(n=6, seed=77):
@@ -37,6 +38,13 @@ def test_served_results_equal_alone():
         native.wfs_measure(w.h, scr.data_ptr(), step * r.cfg.dt_s, out.data_ptr(), 0)
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy(), srv.results[(rid, step)]), (rid, step)
+        w.close()
+    # a few served results against the FP64 oracle (sampled subapertures of every WFS)
+    for rid, step in pick[:4]:
+        r = runs[rid]
+        w = native.Wfs(r.cfg, seed=r.seed)
+        check_against_oracle(r.cfg, r.screens_host, step * r.cfg.dt_s, srv.results[(rid, step)],
+                             w.layouts, seed=r.seed, noise=True, per_wfs=10)
         w.close()
 
 
