@@ -333,22 +333,27 @@ wfs_status wfs_timing_read(wfs_handle h, int max, wfs_kernel_time *out, int *n_o
  * file-scope device array of WFS_STATIC_SCRATCH_BYTES that every GPU loading
  * the library holds until the process exits.  No cudaMalloc, cudaFree or
  * other allocating routine is called; host staging uses fixed static arrays.
- * A guide star whose tables would not fit, or with more than 8192 valid
- * subapertures, is rejected with WFS_EINVAL and a message from
- * wfs_last_error(NULL).  Only WFS_PREC_FP32 geometries are accepted.
+ * The description is checked as wfs_create checks it.  A guide star whose
+ * tables would not fit, or with more than 8192 valid subapertures, is
+ * rejected with WFS_EINVAL and a message from wfs_last_error(NULL).  Only
+ * WFS_PREC_FP32 geometries are accepted (WFS_EUNSUPPORTED otherwise).
  *
  * Inputs and outputs as for wfs_measure with one guide star: screens (device
  * [n_layers][S][S]), slopes_out (device, room for slopes_capacity (x, y)
  * pairs); *n_valid_out receives the number of valid subapertures written.
- * wfs_index is the guide-star index used in the noise counter, so the result
- * equals that of a handle whose guide star wfs_index is *gs.
+ * wfs_index is the guide-star index used in the noise counter, so the slopes
+ * equal, bit for bit, those of a handle whose guide star wfs_index is *gs.
  *
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress while that device is current: make it before any
- * stream capture.  All calls share the array and the host staging, which keep
- * the last call's contents: calls from several host threads, or calls whose
- * GPU work overlaps on different streams, race.  Calls on one stream are
- * ordered.  Asynchronous on `stream`.
+ * Every call looks up the array's device address with cudaGetSymbolAddress on
+ * the current device.  The first call on a device may load the library's
+ * device code: make it before any stream capture.  The tables are copied from
+ * static pageable host arrays with cudaMemcpyAsync; the copy reads them when
+ * it runs and the next call overwrites them, and the call may wait for the
+ * stream's earlier work before it returns.  All calls share the device array
+ * and the host staging, which keep the last call's contents: calls from
+ * several host threads, or calls whose GPU work overlaps on different
+ * streams, race.  Calls on one stream are ordered.  Otherwise asynchronous on
+ * `stream`.
  */
 #define WFS_STATIC_SCRATCH_BYTES (16u << 20)
 

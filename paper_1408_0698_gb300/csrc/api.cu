@@ -870,6 +870,11 @@ bool loop_busy(wfs_loop lp, cudaStream_t s) {
 
 void gbwfs::set_thread_error(const char *msg) { tl_error = msg ? msg : ""; }
 
+wfs_status gbwfs::validate_description(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs, int n_geom,
+                                       const wfs_geometry *geom, const wfs_layers *L) {
+    return validate(tel, n_gs, gs, n_geom, geom, L);
+}
+
 extern "C" {
 
 #ifdef GBWFS_CHECK

@@ -15,6 +15,8 @@
 
 #include <vector>
 
+#include "../../include/gbwfs.h"
+
 namespace gbwfs {
 
 constexpr int kMaxGuideStars = 32;
@@ -289,5 +291,9 @@ cudaError_t launch_push_pull_rows(const float *s, int n_modes, int n_slopes, flo
                                   cudaStream_t st);
 // Sets the calling thread's message returned by wfs_last_error(NULL).
 void set_thread_error(const char *msg);
+// The argument checks of wfs_create (telescope, guide stars, geometries, layers); on failure
+// the thread's error message says what is wrong.
+wfs_status validate_description(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs, int n_geom,
+                                const wfs_geometry *geom, const wfs_layers *L);
 
 }  // namespace gbwfs

@@ -8,6 +8,7 @@
 // Output layout: per WFS, [n_valid][n][n] (subaperture-tiled), so the spot kernel reads each
 // subaperture's n*n OPD as one contiguous block.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 #include "proj_math.cuh"
@@ -401,8 +402,22 @@ cudaError_t launch_project(const ProjArgs &a, int total_blocks, cudaStream_t s, 
 
 cudaError_t project_launch_shape(const ProjArgs &a, int total_blocks, LaunchShape *out) {
     const size_t smem = (size_t)a.box_cap * sizeof(float) + (a.box_cap ? 64 : 0);
-    cudaError_t e = cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // the kernel's dynamic shared-memory limit is process-wide: only ever raise it, so that a
+    // smaller request (the direct-gather launches ask for none) cannot lower it between another
+    // thread's setting and its launch
+    cudaError_t e = cudaSuccess;
+    {
+        static std::mutex m;
+        static size_t raised[64] = {};  // per device ordinal
+        int d = 0;
+        if ((e = cudaGetDevice(&d)) != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lk(m);
+        if (d < 0 || d >= 64 || smem > raised[d]) {
+            if ((e = cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return e;
+            if (d >= 0 && d < 64) raised[d] = smem;
+        }
+    }
     int grid = total_blocks > 0 ? total_blocks : 1;
     if (a.work) {
         // resident capacity for this shared-memory size (cached per thread)

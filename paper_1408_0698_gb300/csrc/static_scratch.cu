@@ -14,18 +14,24 @@
 // cudaFree or other allocating routine; host-side staging uses fixed static
 // arrays.
 //
-// It launches the same kernels as wfs_measure (projection, elongation table,
-// spot), so its slopes equal those of a handle holding the same guide star at
-// index wfs_index.
+// It launches the kernels a handle holding the same guide star at index
+// wfs_index launches -- the projection (here with direct gathers, which do
+// the same per-tap arithmetic in the same order as the tiled form), the
+// elongation table and the FP32 spot kernel -- so its slopes equal that
+// handle's bit for bit.
 //
-// The device address of the array is looked up once per device with
-// cudaGetSymbolAddress, on the first call made while that device is current;
-// make that first call before any stream capture.  All calls share the array
-// and the static host staging: calls from several host threads, or calls
-// whose GPU work overlaps (different streams without ordering), race.  Calls
-// on one stream are ordered and safe.  Nothing in the array needs to start
-// at zero (every part is written before it is read) except the status word,
-// which each call clears.
+// The device address of the array is looked up with cudaGetSymbolAddress on
+// every call, with the caller's device current (no allocation; the address
+// stays right if the device's context is torn down and made again).  The
+// first call on a device may load the library's device code: make it before
+// any stream capture.  The tables go up with cudaMemcpyAsync from static
+// pageable host arrays: the copy reads them when it runs, the next call
+// overwrites them, and the call may wait for the stream's earlier work before
+// it returns.  All calls share the device array and the host staging: calls
+// from several host threads, or calls whose GPU work overlaps (different
+// streams without ordering), race.  Calls on one stream are ordered and safe.
+// Nothing in the array needs to start at zero (every part is written before
+// it is read) except the status word, which each call clears.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -42,11 +48,8 @@ namespace {
 
 constexpr int kStaticMaxValid = 8192;
 constexpr int kStaticMaskWords = (kMaxNPix * kMaxNPix + 31) / 32;
-constexpr int kStaticMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[WFS_STATIC_SCRATCH_BYTES];
-
-void *g_scratch_addr[kStaticMaxDevices] = {};
 
 // host staging (fixed size, reused by every call)
 int32_t h_ids[kStaticMaxValid];
@@ -90,45 +93,23 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
     if (!tel || !geom || !gs || !L || !screens || !slopes_out || !n_valid_out)
         return st_fail(WFS_EINVAL, "wfs_measure_one_static: null argument");
     *n_valid_out = 0;
+    // the checks of wfs_create on this one star and geometry, then the limits of this path
+    wfs_guide_star gs1 = *gs;
+    gs1.geometry_index = 0;
+    if (wfs_status vs = validate_description(tel, 1, &gs1, 1, geom, L); vs != WFS_OK) return vs;
     const wfs_geometry &g = *geom;
     const int n = g.n_pix_sub, N = g.n_fft, nd = g.n_det;
-    if (!(tel->diameter_m > 0) || !std::isfinite(tel->diameter_m) || !(tel->obstruction >= 0 && tel->obstruction < 1))
-        return st_fail(WFS_EINVAL, "wfs_measure_one_static: bad telescope");
-    if (g.n_sub < 1 || n < 1 || n > kMaxNPix || N < n || N > kMaxN || nd < 1 || N % nd ||
-        !(g.valid_fill > 0 && g.valid_fill <= 1))
-        return st_fail(WFS_EINVAL, "wfs_measure_one_static: bad geometry");
     if (g.precision != WFS_PREC_FP32)
         return st_fail(WFS_EUNSUPPORTED, "wfs_measure_one_static: only WFS_PREC_FP32");
-    if (L->n_layers < 1 || L->n_layers > kMaxLayers || L->screen_size < 2 || !(L->screen_dx_m > 0) ||
-        !L->alt_m || !L->wind_vx_mps || !L->wind_vy_mps || !L->x0_m || !L->y0_m)
-        return st_fail(WFS_EINVAL, "wfs_measure_one_static: bad layers");
-    if (!(gs->wavelength_m > 0) || !(gs->photons_per_subap >= 0) || !(gs->read_noise_e >= 0) ||
-        !std::isfinite(t_s) || wfs_index >= (1u << 16))
-        return st_fail(WFS_EINVAL, "wfs_measure_one_static: bad guide star or time");
-    if (gs->is_lgs) {
-        if (!(gs->range_m > 0) || !std::isfinite(gs->range_m) || !(gs->spot_fwhm_rad > 0) || gs->n_na < 1 ||
-            gs->n_na > kMaxNaSlices || !gs->na_alt_m || !gs->na_weight)
-            return st_fail(WFS_EINVAL, "wfs_measure_one_static: bad LGS description");
-        if (N < 2 * n - 1) return st_fail(WFS_EUNSUPPORTED, "wfs_measure_one_static: LGS needs n_fft >= 2n-1");
-        for (int l = 0; l < L->n_layers; ++l)
-            if (!(L->alt_m[l] < gs->range_m)) return st_fail(WFS_EINVAL, "wfs_measure_one_static: layer above LGS");
-    }
+    if (!std::isfinite(t_s) || wfs_index >= (1u << 16))
+        return st_fail(WFS_EINVAL, "wfs_measure_one_static: bad time or wfs_index");
     const int Np = g.n_sub * n;
-    if (0.5 * Np * (tel->diameter_m / Np) / L->screen_dx_m + 2.0 >= L->screen_size)
-        return st_fail(WFS_EINVAL, "wfs_measure_one_static: pupil footprint larger than the screen");
 
-    // one-time lookup of the scratch array's device address on this device
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
-        return st_fail(WFS_ECUDA, "wfs_measure_one_static: no current device");
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) return st_fail(WFS_ECUDA, "wfs_measure_one_static: cudaGetSymbolAddress failed");
-        g_scratch_addr[dev] = p;
-    }
-    unsigned char *base = (unsigned char *)g_scratch_addr[dev];
+    // the scratch array's device address on the current device
+    void *addr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_static_scratch);
+    if (e != cudaSuccess || !addr) return st_fail(WFS_ECUDA, "wfs_measure_one_static: cudaGetSymbolAddress failed");
+    unsigned char *base = (unsigned char *)addr;
 
     // valid subapertures and lit-pixel bits (FP64 pixel-centre test)
     const int mw = (n * n + 31) / 32;

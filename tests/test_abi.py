@@ -173,3 +173,28 @@ def test_product_and_oracle_share_no_code():
         if f.endswith(".py"):
             text = open(os.path.join(pkg, f)).read()
             assert not re.search(r"^\s*(import oracle|from oracle)", text, flags=re.M), f
+
+
+@pytest.mark.parametrize("edit", ["alt_nan", "weights_zero", "n_sub_huge", "launch_inf", "theta_nan"])
+def test_static_entry_checks_descriptions_like_create(edit):
+    """wfs_measure_one_static applies wfs_create's checks before any device work: descriptions
+    that wfs_create rejects are rejected here too (no GPU is needed to see it)."""
+    cfg = inputs.config2()
+    tel, stars, geoms, lay, keep = native.marshal(cfg)
+    s0, g0 = stars[0], geoms[stars[0].geometry_index]
+    if edit == "alt_nan":
+        lay.alt_m[1] = float("nan")
+    elif edit == "weights_zero":
+        for k in range(s0.n_na):
+            s0.na_weight[k] = 0.0
+    elif edit == "n_sub_huge":
+        g0.n_sub = 5000
+    elif edit == "launch_inf":
+        s0.launch_x_m = float("inf")
+    else:
+        s0.theta_x_rad = float("nan")
+    nv = C.c_int(-1)
+    st = native.lib().wfs_measure_one_static(C.byref(tel), C.byref(g0), C.byref(s0), C.byref(lay), C.c_void_p(16),
+                                             0.0, 1, 0, 0, C.c_void_p(16), 10, C.byref(nv), None)
+    assert st == native.WFS_EINVAL
+    assert nv.value == 0

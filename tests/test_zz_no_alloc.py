@@ -1,8 +1,8 @@
 """wfs_measure_one_static: the measurement for callers that cannot allocate device memory
 (a real-time loop that must not block on the allocator, a host program with a fixed
 device budget, a plugin that only receives buffers).  It keeps its working data in the
-library's static device array instead of a handle's allocations; its slopes must match
-those of wfs_measure on a handle holding the same guide star, call after call.
+library's static device array instead of a handle's allocations; its slopes must equal
+those of wfs_measure on a handle holding the same guide star, bit for bit, call after call.
 
 Collected last on purpose (file name), so a run that stops at the first failure has
 already run every other test."""
@@ -15,8 +15,6 @@ from paper_1408_0698_gb300 import inputs, native
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-SLOPE_RMS = 1e-3   # the slope bar the parity tests use
 
 
 def _one_star(cfg, k):
@@ -49,14 +47,17 @@ def test_static_scratch_entry_matches_wfs_measure(cfg_fn, k, noise):
         assert nv == w.total
         a, b = out[:nv].cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a))
-        assert float(np.sqrt(np.mean((a - b) ** 2))) <= SLOPE_RMS
-        assert np.max(np.abs(a - b)) <= 5 * SLOPE_RMS
+        # the same kernels on the same inputs: bit for bit (the projection's direct gathers do
+        # the tiled form's per-tap arithmetic in the same order)
+        assert np.array_equal(a, b)
         assert np.all(np.isnan(out[nv:].cpu().numpy()))   # nothing written past n_valid
         free = torch.cuda.mem_get_info()[0]
         if call == 0:
             free_after_first = free
         else:
-            assert free == free_after_first               # the second call allocated nothing
+            # the second call allocated nothing (a coarse check: the driver's free-memory figure
+            # moves by whole pages when anything is allocated on the device)
+            assert free == free_after_first
     w.close()
 
 
