@@ -481,9 +481,10 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served-traffic measurement")
     ap.add_argument("--no-loop", action="store_true", help="skip the closed-loop measurement")
     ap.add_argument("--no-calib", action="store_true", help="skip the push-pull calibration measurement")
-    ap.add_argument("--paths", default="fp32,fp16s,uplink,slices",
+    ap.add_argument("--paths", default="fp32,fp16s,uplink,slices,configs,batch",
                     help="comparison paths timed after the headline (comma list of fp32, fp16s, uplink, "
-                         "slices; 'none'); fp32 and fp16s time the other DFT precisions")
+                         "slices, configs, batch; 'none'); fp32 and fp16s time the other DFT precisions, "
+                         "configs the single-instance configs 1 and 2, batch the uneven config-4 batch")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="L2 flush buffer written between timed steps (0: none, for profiling runs)")
     args = ap.parse_args()
@@ -651,6 +652,10 @@ def main():
         time_uplink(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
     if "slices" in paths:
         time_per_slice(line, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt)
+    if "configs" in paths and world == 1:
+        line.update(single_configs(args, dev, flush, ev0, ev1))
+    if "batch" in paths and world == 1:
+        line["batch"] = batch_leg(args, dev, flush)
     if not args.no_loop:
         line["closed_loop"] = closed_loop(cfg, s_d, flush, args, dev, rank)
     if not args.no_calib:
@@ -792,6 +797,89 @@ def time_frames(w, s_d, slopes, sp, stream, flush, ev0, ev1, args, dt, steps, ke
     kt = native.wfs_timing_read(w.h)
     native.wfs_sync_status(w.h)
     return ms, {k: {"launches": v[0], "avg_ms": v[1] / max(1, v[0])} for k, v in kt.items()}
+
+
+def batch_leg(args, dev, flush, n_inst=64, steps=200):
+    """Config 4: n_inst uneven instances (2x2 / 10x10 / 40x40 / 80x80 subapertures, DFT sizes
+    16-64, 1-10 layers, LGS and NGS) measured together by wfs_batch_measure (one projection
+    launch and one spot launch per kernel class, replayed as a CUDA graph), after
+    wfs_batch_tune has picked the launch shapes; BF16 x3 (geometries without a tensor-core
+    kernel stay FP32) against all FP32.  L2 flushed between steps."""
+    import torch
+
+    from paper_1408_0698_gb300 import inputs, native
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    for name, prec in (("bf16x3", inputs.PREC_BF16X3), ("fp32", inputs.PREC_FP32)):
+        insts = inputs.config4_instances(n_inst, 4000, precision=prec)
+        hs, scr, outs, ts = [], [], [], []
+        n_tc = 0
+        for i, c in enumerate(insts):
+            try:
+                w = native.Wfs(c, seed=c.seed, noise=True)
+                n_tc += prec != inputs.PREC_FP32
+            except native.WfsError as e:
+                if e.status != native.WFS_EUNSUPPORTED:
+                    raise
+                c.geometries[0].precision = inputs.PREC_FP32
+                w = native.Wfs(c, seed=c.seed, noise=True)
+            hs.append(w)
+            scr.append(torch.as_tensor(inputs.make_screens(c.layers, c.seed)).to(dev))
+            outs.append(torch.zeros((max(w.total, 1), 2), device=dev))
+        spots = sum(w.total for w in hs)
+        b = native.wfs_batch_create([w.h for w in hs])
+        sps, ops = [x.data_ptr() for x in scr], [o.data_ptr() for o in outs]
+        native.wfs_batch_tune(b, sps, [0.0] * len(hs), ops, sp)
+        for k in range(5):
+            native.wfs_batch_measure(b, sps, [k * 1e-3] * len(hs), ops, sp)
+        torch.cuda.synchronize()
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0[k].record(stream)
+            native.wfs_batch_measure(b, sps, [(5 + k) * 1e-3] * len(hs), ops, sp)
+            e1[k].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(x.elapsed_time(y) for x, y in zip(e0, e1)) / steps
+        info = native.wfs_batch_info(b)
+        native.wfs_batch_destroy(b)
+        for w in hs:
+            w.close()
+        out[name] = {"value": spots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                     "spots_per_step": spots, "instances": len(hs), "instances_on_tensor_cores": n_tc,
+                     "classes": [{k: c[k] for k in ("kind", "n_pix_sub", "n_fft", "n_det", "n_wfs", "n_subaps", "grid_cap", "cta_warps")
+                                  if k in c} for c in info]}
+    out["workload"] = (f"config4: {n_inst} uneven instances (seed 4000) of one WFS each, 2x2/10x10/40x40/80x80 "
+                       "subapertures, DFT 16/24/32/64, 1-10 layers, LGS and NGS, noise on; one batch launch set "
+                       "per step (CUDA graph), autotuned launch shapes")
+    return out
+
+
+def single_configs(args, dev, flush, ev0, ev1):
+    """Configs 1 and 2 as single instances (the plain FP32 path and BF16 x3 on the tensor cores),
+    noise on, frames timed as the headline's."""
+    import torch
+
+    from paper_1408_0698_gb300 import inputs, native
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    out = {}
+    for cname, fn in (("config1", inputs.config1), ("config2", inputs.config2)):
+        res = {}
+        for pname, prec in (("fp32", inputs.PREC_FP32), ("bf16x3", inputs.PREC_BF16X3)):
+            cfg = fn(prec)
+            w = native.Wfs(cfg, seed=cfg.seed, noise=True)
+            s_d = torch.as_tensor(inputs.make_screens(cfg.layers, cfg.seed)).to(dev)
+            sl = torch.empty((w.total, 2), device=dev)
+            k = min(args.steps, 300)
+            ms, kt = time_frames(w, s_d, sl, sp, stream, flush, ev0, ev1, args, cfg.dt_s, k)
+            res[pname] = {"value": w.total / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": k,
+                          "spots_per_frame": w.total, "kernels": kt}
+            w.close()
+        out[cname] = res
+    return out
 
 
 def time_other_precision(line, other, cfg, rank, s_d, slopes, sp, stream, flush, ev0, ev1, spots, args, dt):

@@ -60,6 +60,7 @@ struct GeomDev {
     int mask_words = 0;
     float2 *F = nullptr, *Ga = nullptr, *G = nullptr;
     uint8_t *tcB1 = nullptr, *tcB2h = nullptr, *tcB2l = nullptr;  // BF16X3 operand tiles
+    uint8_t *tcA0 = nullptr;                                        // first-stage operand tile
 };
 
 // One spot launch: consecutive entries of a WFS table sharing a kernel class.
@@ -378,6 +379,7 @@ void release(wfs_ctx *h) {
         cudaFree(g.Ga);
         cudaFree(g.G);
         cudaFree(g.tcB1);
+        cudaFree(g.tcA0);
         cudaFree(g.tcB2h);
         cudaFree(g.tcB2l);
     }
@@ -485,6 +487,11 @@ void fill_geom_args(ShArgs &sa, const GeomDev &G) {
     sa.Ga = G.Ga;
     sa.G = G.G;
     sa.tc_B1 = G.tcB1;
+    sa.tc_A0 = G.tcA0;
+    // the first DFT stage (U = F X) of the tensor-core kernels on the CUDA cores (default, the
+    // faster form) or as a third MMA (GBWFS_TC_MMA_U=1); both meet the same parity bars
+    const char *mu = getenv("GBWFS_TC_MMA_U");
+    sa.mma_u = (mu && mu[0] == '1') ? 1 : 0;
     sa.tc_B2h = G.tcB2h;
     sa.tc_B2l = G.tcB2l;
 }
@@ -573,7 +580,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
         sa.n_inst = 1;
         sa.work = h->d_work + 2 * (&G - h->groups.data());
         sa.project = project_mode;
-        sa.split_noise = splits_noise(G.kind) ? 1 : 0;
+        sa.split_noise = splits_noise(G.kind, sa.N, sa.nd) ? 1 : 0;
         sa.slice_opd_stride = slice_stride;
         sa.dyn[0] = dyn;
         if (slice_stride > 0) sa.dyn[0].opd = h->d_opd_sl;
@@ -898,7 +905,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
             !sh_tc_supported(g.n_pix_sub, g.n_fft, g.n_det))
             return fail(nullptr, WFS_EUNSUPPORTED,
                         "geometry " + std::to_string(i) + (g.precision == WFS_PREC_FP16S ? ": WFS_PREC_FP16S" : ": WFS_PREC_BF16X3") +
-                            " is built for n_fft = 32 with (n_pix_sub, n_det) = (10, 16) or (8, 16)");
+                            " is built for (n_pix_sub, n_fft, n_det) = (10, 32, 16), (8, 32, 16), (8, 16, 8) and (6, 24, 12)");
     }
 
     wfs_ctx *h = new wfs_ctx();
@@ -932,10 +939,11 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
         }
         if (geom[i].precision == WFS_PREC_BF16X3 || geom[i].precision == WFS_PREC_FP16S) {
             const int n = geom[i].n_pix_sub, N = geom[i].n_fft;
-            std::vector<uint8_t> b1, b2h, b2l;
+            std::vector<uint8_t> b1, b2h, b2l, a0;
             build_tc_tiles(n, N, F64.data(), F64.data() + (size_t)n * N, Ga64.data(), Ga64.data() + (size_t)n * N,
-                           geom[i].precision == WFS_PREC_FP16S, b1, b2h, b2l);
+                           geom[i].precision == WFS_PREC_FP16S, b1, b2h, b2l, a0);
             if ((e = upload(&G.tcB1, b1)) != cudaSuccess || (e = upload(&G.tcB2h, b2h)) != cudaSuccess ||
+                (e = upload(&G.tcA0, a0)) != cudaSuccess ||
                 (e = upload(&G.tcB2l, b2l)) != cudaSuccess) {
                 release(h);
                 delete h;
@@ -1723,7 +1731,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
         a->status = hs[0]->d_status;
         a->n_inst = n;
         a->work = b->d_work + 2 * b->sa.size();
-        a->split_noise = splits_noise(bc.kind) ? 1 : 0;
+        a->split_noise = splits_noise(bc.kind, a->N, a->nd) ? 1 : 0;
         b->sa.push_back(a);
     }
     const char *g = getenv("GBWFS_BATCH_GRAPH");
@@ -1855,7 +1863,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
         sa.cta_warps = bc.cta_warps;
         sa.n_inst = n;
         sa.work = b->d_work + 2 * (b->classes.size() * (1 + (size_t)slot) + c);
-        sa.split_noise = splits_noise(bc.kind) ? 1 : 0;
+        sa.split_noise = splits_noise(bc.kind, sa.N, sa.nd) ? 1 : 0;
         memcpy(sa.dyn, pa.dyn, sizeof(InstDyn) * n);
         if ((e = launch_spot(bc.kind, sa, (cudaStream_t)stream)) != cudaSuccess)
             return cuda_fail(nullptr, e, "batch subset spot launch");
@@ -2177,7 +2185,7 @@ wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_o
             sa.n_inst = ni;
             sa.work = c.work + 2;
             sa.project = 0;
-            sa.split_noise = splits_noise(c.kind) ? 1 : 0;
+            sa.split_noise = splits_noise(c.kind, sa.N, sa.nd) ? 1 : 0;
             memcpy(sa.dyn, pa.dyn, sizeof(InstDyn) * ni);
             sl = timed_begin(h, kind_name(c.kind) + std::to_string(sa.N), s);
             e = launch_spot(c.kind, sa, s, !h->timing);
@@ -2294,7 +2302,7 @@ wfs_status wfs_set_lgs_model(wfs_handle h, int per_slice) {
             // the per-slice variant of the geometry's 32-point kernel (tensor-core or FP32) where
             // it has one, else the self-projecting generic kernel
             const wfs_geometry &geo = h->geoms[G.geom].g;
-            if (!is_tc(G.kind))
+            if (!is_tc(G.kind) || !sh_tc_slices_supported(geo.n_pix_sub, geo.n_fft, geo.n_det))
                 G.kind = sh_n32_supported(geo.n_pix_sub, geo.n_fft, geo.n_det) ? kSpotN32 : kSpotGeneric;
             G.grid_cap = G.cta_warps = 0;
         } else {

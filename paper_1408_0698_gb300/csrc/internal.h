@@ -109,6 +109,8 @@ struct ShArgs {
     const float2 *Ga;   // [n][N]  Ga[d*N + k] = exp(+2 pi i (k-cN) d / N), d = 0..n-1
     const float2 *G;    // [n][nd] G[d*nd + i] = sum_{r<b} exp(-2 pi i (b i + r - cN) d / N)
     const void *tc_B1, *tc_B2h, *tc_B2l;  // BF16X3 operand tiles (pre-swizzled)
+    const void *tc_A0;                    // F's rows, four times over: the first DFT stage's operand
+    int mma_u;                            // tensor-core kernels: U = F X as an MMA too (GBWFS_TC_MMA_U=1)
     const InstDesc *inst;
     const WfsDesc *wfs;  // this launch's WFS entries (subap_begin relative to them)
     int n_wfs, total;
@@ -252,6 +254,7 @@ enum SpotKind { kSpotGeneric = 0, kSpotN32 = 1, kSpotTc = 2, kSpotTcF16 = 3 };
 inline bool is_tc(int kind) { return kind == kSpotTc || kind == kSpotTcF16; }
 bool sh_n32_supported(int n, int N, int nd);
 bool sh_tc_supported(int n, int N, int nd);
+bool sh_tc_slices_supported(int n, int N, int nd);
 // Shape of the launch (sets the kernel's dynamic shared-memory attribute).
 cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out);
 // after_project: the launch follows the projection on stream s and may start (prologue only)
@@ -263,12 +266,13 @@ cudaError_t launch_spot(int kind, const ShArgs &a, cudaStream_t s, bool after_pr
 cudaError_t launch_noise_cog(const ShArgs &a, cudaStream_t s, bool after_spot);
 cudaError_t noise_cog_launch_shape(const ShArgs &a, LaunchShape *out);
 // Whether a spot kind stores expected images and leaves noise and centroid to k_noise_cog.
-inline bool splits_noise(int kind) { return kind == kSpotN32 || is_tc(kind); }
+// The 32-point kernels with a 16 x 16 detector leave the noise and the centroid to k_noise_cog.
+inline bool splits_noise(int kind, int N, int nd) { return (kind == kSpotN32 || is_tc(kind)) && N == 32 && nd == 16; }
 // Swizzled BF16 (f16: FP16) operand tiles of the two constant matrices (F^T blocks, Ga blocks),
 // from FP64 tables laid out [q][m] (F) and [d][k] (Ga).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
                     const double *Ga_im64, bool f16, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
-                    std::vector<uint8_t> &B2l);
+                    std::vector<uint8_t> &B2l, std::vector<uint8_t> &A0);
 // Bounded mbarrier wait that is never satisfied; writes WFS_ETIMEOUT to *status.
 cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
 // LGS uplink tip-tilt of every WFS of the table that has it on: one CTA per (WFS, turbulent

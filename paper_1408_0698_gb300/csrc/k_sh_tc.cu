@@ -50,6 +50,7 @@ constexpr int kTcThreads = 128 * kWG;
 constexpr uint32_t kTmemCols = 128 * kWG;  // per warpgroup: D1 columns [0, 64), D2 [64, 96)
 constexpr int kWaitLimit = 1 << 24;      // mbarrier polls before giving up
 
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -141,6 +142,7 @@ struct TcElt {
         const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
         return *reinterpret_cast<const uint32_t *>(&v);
     }
+    static __device__ __forceinline__ uint16_t bits(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
 };
 template <>
 struct TcElt<true> {
@@ -153,6 +155,7 @@ struct TcElt<true> {
         const __half2 v = __floats2half2_rn(a, b);
         return *reinterpret_cast<const uint32_t *>(&v);
     }
+    static __device__ __forceinline__ uint16_t bits(float a) { return __half_as_ushort(__float2half_rn(a)); }
 };
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -208,37 +211,52 @@ __device__ __forceinline__ void field_rows(const float2 *Fk, const float4 *X4, i
     }
 }
 
-template <int n, int nd, bool kSlices = false>
+template <int n, int N_, int nd, bool kSlices = false, bool kMmaU = false>
 struct TcLayout {
-    static constexpr int N = 32, D2 = 2 * n - 1;
+    static constexpr int N = N_, D2 = 2 * n - 1, no = n | 1;
+    // N = 32 with a 16 x 16 detector: the elongation stage as a DFT across the 32 lanes and
+    // the noise in its own pass; other sizes: the stages as direct sums over the warp's rows
+    static constexpr bool kLane = N == 32 && nd == 16;
     // byte offsets; tensor-core tiles first (1024-aligned)
     static constexpr int oB1 = 0;                  // 64 rows x 128 B: [F_hi; F_hi; F_lo] blocks
     static constexpr int oB2h = oB1 + 8192;        // 32 rows x 128 B: [Ga_hi; Ga_hi]
     static constexpr int oB2l = oB2h + 4096;       // 32 rows x 128 B: [Ga_lo; 0]
-    // per warpgroup, 128 rows x 128 B: [U_hi | U_lo | U_hi] for the first MMA, then (after
-    // it has completed) [I_hi | I_lo] for the second
-    static constexpr int oA = oB2l + 4096;
+    // with U = F X as an MMA: 128 rows x 128 B, F's rows [F_hi | F_lo | F_hi] for each of the
+    // four subapertures of a group
+    static constexpr int oA0 = oB2l + 4096;
+    // per warpgroup, 128 rows x 128 B: the fields [X_hi | X_hi | X_lo] of the group's four
+    // subapertures (U = F X as an MMA), then [U_hi | U_lo | U_hi] for the DFT's second MMA,
+    // then (after it has completed) [I_hi | I_lo] for the transfer-function MMA
+    static constexpr int oA = oA0 + (kMmaU ? 16384 : 0);
     static constexpr int oTab = oA + 16384 * kWG;  // CUDA-core tables (float2)
-    static constexpr int tFk = 0;                  // [p][k]  F[k][p]
-    static constexpr int tFft = tFk + n * N;       // lane-DFT twiddles and phases (tail::fill_fft_table)
-    static constexpr int tG = tFft + tail::kFftTable;  // [d][nd] G[d][i]
-    static constexpr int tRk = tG + n * nd;       // RN(1/k) for the Poisson inversion (floats)
+    static constexpr int tFk = 0;                  // [p][k]  F[k][p] (U = F X on the CUDA cores)
+    static constexpr int tFft = tFk + (kMmaU ? 0 : n * N);  // lane-DFT twiddles and phases (tail::fill_fft_table)
+    static constexpr int tG = tFft + (kLane ? tail::kFftTable : 0);  // [d][nd] G[d][i]
+    static constexpr int tGa = tG + n * nd;        // [d][k] Ga (direct-sum stages only)
+    static constexpr int tRk = tGa + (kLane ? 0 : n * N);  // RN(1/k) for the Poisson inversion (floats)
     static constexpr int tEnd = tRk + kRecipTable / 2;
-    static constexpr int oWarp = oTab + tEnd * 8;  // per-warp scratch (float2)
-    // the NGS image rows (wI) alias the LGS scratch (wQ, wM)
-    // (X, Q and M hold column pairs, 16-byte aligned)
-    static constexpr int wX = 0, wQ = wX + n * n, wM = wQ + nd * n, wI = wQ;
+    static constexpr int oWarp = (oTab + tEnd * 8 + 15) / 16 * 16;  // per-warp scratch (float2)
+    static constexpr int even(int x) { return (x + 1) & ~1; }
+    // 32-lane path: the NGS image rows (wI) alias the LGS scratch (wQ, wM); X, Q and M hold
+    // column pairs, 16-byte aligned
+    static constexpr int wX = 0, wQ = wX + n * n, wM = wQ + nd * n;
+    // direct-sum path: Ta [N][no] over the consumed field X, then M [D2][n], P [D2][nd], B
+    // [nd][nd] floats; an NGS's image rows [N][N + 1] floats over X, then B
+    static constexpr int wTa = 0, wMg = even(n * n > N * no ? n * n : N * no), wP = wMg + D2 * n,
+                         wB = kLane ? 0 : wP + D2 * nd;
+    static constexpr int wI = kLane ? wQ : 0, wBn = even((N * (N + 1) + 1) / 2);
     static_assert(wQ % 2 == 0 && wM % 2 == 0, "16-byte aligned column-pair scratch");
-    static constexpr int lgs_end = wM + D2 * n, ngs_end = wI + (N * (N + 1) + 1) / 2;
+    static constexpr int lgs_end = kLane ? wM + D2 * n : even(wB + (nd * nd + 1) / 2);
+    static constexpr int ngs_end = kLane ? wI + (N * (N + 1) + 1) / 2 : wBn + (nd * nd + 1) / 2;
     // an LGS subaperture's elongation table K~ ([2n-1][n] complex), staged by cp.async at the
     // top of a group and read by the elongation stage; it may overlap the NGS rows, which an LGS
     // subaperture never writes (a warp's copies land before its next NGS image)
     static constexpr int wKt = lgs_end;
-    static constexpr int base_warp = wKt + D2 * n > ngs_end ? wKt + D2 * n : ngs_end;
+    static constexpr int base_warp = even(wKt + D2 * n > ngs_end ? wKt + D2 * n : ngs_end);
     // per-slice variant: the summed spot rows use the NGS rows (wI; K~ is staged after them)
     static constexpr int warp = base_warp;
-    // per warpgroup: 2 mbarriers (0), flag (16), next group (20); per-slice variant: the slice
-    // counts of its 4 warps (32)
+    // per warpgroup: 2 mbarriers (0), flag (16), next group (20), the first-stage mbarrier (24);
+    // per-slice variant: the slice counts of its 4 warps (32)
     static constexpr int misc = kSlices ? 48 : 32;
     static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;
     static constexpr int bytes = oMisc + misc * kWG + 16;
@@ -246,22 +264,26 @@ struct TcLayout {
 
 }  // namespace
 
-template <int n, int nd, bool kF16>
+template <int n, int N, int nd, bool kF16, bool kMmaU>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__ ShArgs a) {
-    using Lay = TcLayout<n, nd>;
+    using Lay = TcLayout<n, N, nd, false, kMmaU>;
     using E = TcElt<kF16>;
-    constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
+    constexpr bool kLane = Lay::kLane;
+    constexpr int D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
+    static_assert(N <= 32 && N >= 2 * n - 1, "one DFT row per lane; the autocorrelation fits the grid");
     static_assert(n % 2 == 0 && Lay::wKt % 2 == 0 && Lay::warp % 2 == 0 && Lay::oWarp % 16 == 0,
                   "16-byte aligned K~ staging");
-    static_assert(nd <= 32 && nd2 % 32 == 0, "detector tile must split evenly over a warp");
+    static_assert(!kLane || nd2 % 32 == 0, "detector tile must split evenly over a warp");
+    static_assert(N % nd == 0 && nd % 2 == 0, "whole binning blocks; even detector rows");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB1 = smem + Lay::oB1, *sB2h = smem + Lay::oB2h, *sB2l = smem + Lay::oB2l;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int wg = wib >> 2, wq = wib & 3;  // warpgroup, warp within it (= TMEM lane quarter)
-    uint8_t *sA1 = smem + Lay::oA + 16384 * wg, *sA2 = sA1;
+    uint8_t *sA1 = smem + Lay::oA + 16384 * wg, *sA2 = sA1, *sB0 = sA1, *sA0 = smem + Lay::oA0;
     float2 *tab = reinterpret_cast<float2 *>(smem + Lay::oTab);
     float2 *Fk = tab + Lay::tFk, *fft = tab + Lay::tFft, *Gt = tab + Lay::tG;
+    float2 *Gat = tab + Lay::tGa;
     float *rk = reinterpret_cast<float *>(tab + Lay::tRk);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc + 32 * wg);
     int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 32 * wg + 16);
@@ -279,11 +301,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             reinterpret_cast<uint4 *>(sB2h)[i] = src2[i];
             reinterpret_cast<uint4 *>(sB2l)[i] = src3[i];
         }
-        for (int i = tid; i < n * N; i += kTcThreads) {
-            const int p = i / N, k = i - p * N;
-            Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
+        if constexpr (kMmaU) {
+            // F's rows for the first MMA, and the field tiles cleared once: their K columns past
+            // 6n meet zeros of F's tile, so they must never hold a NaN pattern
+            const uint4 *src0 = reinterpret_cast<const uint4 *>(a.tc_A0);
+            for (int i = tid; i < 16384 / 16; i += kTcThreads) reinterpret_cast<uint4 *>(sA0)[i] = src0[i];
+            for (int i = tid; i < 16384 * kWG / 16; i += kTcThreads)
+                reinterpret_cast<uint4 *>(smem + Lay::oA)[i] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            for (int i = tid; i < n * N; i += kTcThreads) {
+                const int p = i / N, k = i - p * N;
+                Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
+            }
         }
-        tail::fill_fft_table(fft, tid, kTcThreads);
+        if constexpr (kLane) tail::fill_fft_table(fft, tid, kTcThreads);
+        else
+            for (int i = tid; i < n * N; i += kTcThreads) Gat[i] = a.Ga[i];
         for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
         fill_recip_table(rk, tid, kTcThreads);
     }
@@ -295,6 +328,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     if (wq == 0 && lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        if constexpr (kMmaU) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[3])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
         *sflag = 0;
     }
@@ -308,6 +342,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
     const uint32_t tmem = tmem_all + 128u * wg;  // this warpgroup's columns
     const uint32_t t_row = tmem + ((uint32_t)(wq * 32) << 16);
     constexpr uint32_t idesc1 = tc_idesc(128, 64, E::fmt), idesc2 = tc_idesc(128, 32, E::fmt);
+    constexpr uint32_t idesc0 = tc_idesc(128, 128, E::fmt);
 
     float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
@@ -343,11 +378,86 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
 
-        // field and U = F X (CUDA cores)
         float2 U[n];
 #pragma unroll
         for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
-        if (active) {
+        if constexpr (kMmaU) {
+            // the field straight into this subaperture's rows of the first MMA's B tile:
+            // pixel (p, q) -> row q: [X_hi | X_hi | X_lo] of (re p, -im p); row n + q: of (im p,
+            // re p); U = F X lands in TMEM columns 32 wq + (q, n + q) of the warp's lanes
+            if (active) {
+                const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
+                const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
+                const float ref = __ldg(opd);
+                constexpr int kFw = (n * n + 31) / 32;
+                float o[kFw];
+                uint32_t mw[kFw];
+#pragma unroll
+                for (int m = 0; m < kFw; ++m) {
+                    o[m] = lane + 32 * m < n * n ? __ldg(opd + lane + 32 * m) : 0.0f;
+                    mw[m] = __ldg(mk + m);
+                }
+#pragma unroll
+                for (int m = 0; m < kFw; ++m) {
+                    const int i = lane + 32 * m;
+                    if (i < n * n) {
+                        const bool lit = (mw[m] >> lane) & 1u;
+                        float sn, cs;
+                        field_phasor(W.k_phase * (o[m] - ref), sn, cs);
+                        const int p = i / n, q = i - p * n;
+                        float rh, rl, ih, il;
+                        E::split(lit ? cs : 0.0f, rh, rl);
+                        E::split(lit ? sn : 0.0f, ih, il);
+                        const uint16_t brh = E::bits(rh), brl = E::bits(rl), bih = E::bits(ih), bil = E::bits(il);
+                        const int r0 = wq * 32 + q, r1 = r0 + n;
+                        uint8_t *b0 = sB0, *b1 = sB0;
+                        auto st = [](uint8_t *base, int r, int k, uint16_t v16) {
+                            *reinterpret_cast<uint16_t *>(base + sw128_off(r, k)) = v16;
+                        };
+                        // K = t 2n + c n + p; t = 0, 1 take the hi part, t = 2 the lo part
+                        st(b0, r0, p, brh);
+                        st(b0, r0, 2 * n + p, brh);
+                        st(b0, r0, 4 * n + p, brl);
+                        st(b0, r0, n + p, bih ^ 0x8000u);
+                        st(b0, r0, 3 * n + p, bih ^ 0x8000u);
+                        st(b0, r0, 5 * n + p, bil ^ 0x8000u);
+                        st(b1, r1, p, bih);
+                        st(b1, r1, 2 * n + p, bih);
+                        st(b1, r1, 4 * n + p, bil);
+                        st(b1, r1, n + p, brh);
+                        st(b1, r1, 3 * n + p, brh);
+                        st(b1, r1, 5 * n + p, brl);
+                    }
+                }
+            }
+            if (a.work && issuer) *snext = nwg + ticket;
+            fence_async_smem();
+            fence_before_sync();
+            wg_sync();
+            fence_after_sync();
+            grp_next = a.work ? *snext : grp + nwg;
+            if (*sflag) break;
+            if (issuer) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    mma_f16(tmem, sw128_desc(smem_u32(sA0) + 32 * s), sw128_desc(smem_u32(sB0) + 32 * s), idesc0, s > 0);
+                mma_commit(&mbar[3]);
+            }
+            if (!mbar_wait(&mbar[3], phase)) *sflag = 1;
+            fence_after_sync();
+            {
+                uint32_t r[16], r2[16];
+                GBWFS_TMEM_LD16(r, t_row + 32 * wq);
+                GBWFS_TMEM_LD16(r2, t_row + 32 * wq + 16);
+                tmem_wait_ld();
+                auto col = [&](int j) { return __uint_as_float(j < 16 ? r[j] : r2[j - 16]); };
+                if (active && (N == 32 || lane < N)) {
+#pragma unroll
+                    for (int q = 0; q < n; ++q) U[q] = make_float2(col(q), col(n + q));
+                }
+            }
+        } else if (active) {
+            // field and U = F X (CUDA cores)
             const float *opd = D.opd + W.opd_off + (size_t)v * (n * n);
             const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
             const float ref = __ldg(opd);
@@ -371,7 +481,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
                 }
             }
             __syncwarp();
-            field_rows<n, N>(Fk, X4, lane, U);
+            if (N == 32 || lane < N) field_rows<n, N>(Fk, X4, lane, U);  // DFT rows k >= N stay zero
         }
         // FP16: U times 2^eu (exact), eu from the subaperture's largest component
         int eu = 0;
@@ -409,12 +519,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
                 *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
             }
         }
-        if (a.work && issuer) *snext = nwg + ticket;
+        if (!kMmaU && a.work && issuer) *snext = nwg + ticket;
         fence_async_smem();
         fence_before_sync();
         wg_sync();
         fence_after_sync();
-        grp_next = a.work ? *snext : grp + nwg;
+        if (!kMmaU) grp_next = a.work ? *snext : grp + nwg;
         if (*sflag) break;  // a previous wait timed out (uniform: read after the barrier)
         if (issuer) {
 #pragma unroll
@@ -445,7 +555,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
             ei = f16_scale_exp(warp_max(mx));
         }
         {
-            float *dstI = (active && D.st_I) ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
+            float *dstI = (active && D.st_I && lane < N) ? D.st_I + W.int_off + (size_t)v * (N * N) + lane * N : nullptr;
             const float uy = kF16 ? pow2f(-eu) : 1.0f, si = kF16 ? pow2f(ei) : 1.0f;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
@@ -463,11 +573,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
                 }
                 if (dstI) {
 #pragma unroll
-                    for (int m = 0; m < 16; ++m) dstI[16 * hh + m] = I[m];
+                    for (int m = 0; m < 16; ++m)
+                        if (16 * hh + m < N) dstI[16 * hh + m] = I[m];
                 }
-                if (active && !W.is_lgs) {
+                if (active && !W.is_lgs && lane < N) {
 #pragma unroll
-                    for (int m = 0; m < 16; ++m) Iw[lane * (N + 1) + 16 * hh + m] = I[m];
+                    for (int m = 0; m < 16; ++m)
+                        if (16 * hh + m < N) Iw[lane * (N + 1) + 16 * hh + m] = I[m];
                 }
 #pragma unroll
                 for (int c2 = 0; c2 < 2; ++c2) {
@@ -523,15 +635,36 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
         __syncwarp();
 
         // remaining stages on the CUDA cores (per warp)
-        float Bv[nd / 2];
-        if (W.is_lgs) {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            __syncwarp();
-            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Qw), fft, Gt, Kts,
-                                    lane, Bv);
-        } else
-            tail::ngs_binned<nd>(Iw, lane, Bv);
-        tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);
+        if constexpr (kLane) {
+            float Bv[nd / 2];
+            if (W.is_lgs) {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                __syncwarp();
+                tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Qw), fft, Gt,
+                                        Kts, lane, Bv);
+            } else
+                tail::ngs_binned<nd>(Iw, lane, Bv);
+            tail::finish<nd>(Bv, W, D, a.inst[W.inst].seed, v, lane, rk, a.split_noise != 0);
+        } else {
+            float2 *wbase = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp;
+            float *Bw;
+            if (W.is_lgs) {
+                float2 *Ta = wbase + Lay::wTa;
+                if (lane < N) {
+#pragma unroll
+                    for (int d = 0; d < n; ++d) Ta[lane * Lay::no + d] = T[d];
+                }
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                __syncwarp();
+                Bw = reinterpret_cast<float *>(wbase + Lay::wB);
+                tail::lgs_direct<n, N, nd>(Ta, wbase + Lay::wMg, wbase + Lay::wP, Bw, Kts, Gat, Gt, lane);
+            } else {
+                __syncwarp();
+                Bw = reinterpret_cast<float *>(wbase + Lay::wBn);
+                tail::ngs_direct<N, nd>(Iw, Bw, lane);
+            }
+            tail::finish_direct<nd>(Bw, W, D, a.inst[W.inst].seed, v, lane);
+        }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the CTA
     fence_before_sync();
@@ -554,7 +687,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 template <int n, int nd, bool kF16>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constant__ ShArgs a) {
     constexpr bool kSlices = true;
-    using Lay = TcLayout<n, nd, kSlices>;
+    using Lay = TcLayout<n, 32, nd, kSlices>;
     using E = TcElt<kF16>;
     constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
@@ -965,10 +1098,12 @@ float bf16_float(uint16_t h) {
     return f;
 }
 
-template <int n, int nd, bool kSlices, bool kF16>
+template <int n, int N, int nd, bool kSlices, bool kF16, bool kMmaU>
 cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
-    using Lay = TcLayout<n, nd, kSlices>;
-    const void *f = kSlices ? (const void *)k_sh_tc_sl<n, nd, kF16> : (const void *)k_sh_tc<n, nd, kF16>;
+    using Lay = TcLayout<n, N, nd, kSlices, kSlices ? false : kMmaU>;
+    const void *f;
+    if constexpr (kSlices) f = (const void *)k_sh_tc_sl<n, nd, kF16>;
+    else f = (const void *)k_sh_tc<n, N, nd, kF16, kMmaU>;
     const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -985,22 +1120,40 @@ cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
     return cudaSuccess;
 }
 
-// ShArgs::slice_opd_stride selects the per-slice variant.
-template <int n, int nd>
+// ShArgs::slice_opd_stride selects the per-slice variant (32-point geometries only);
+// ShArgs::mma_u the variant with U = F X as an MMA.
+template <int n, int N, int nd>
 cudaError_t shape_tc(const ShArgs &a, LaunchShape *out, bool f16) {
-    if (f16) return a.slice_opd_stride > 0 ? shape_tc_k<n, nd, true, true>(a, out) : shape_tc_k<n, nd, false, true>(a, out);
-    return a.slice_opd_stride > 0 ? shape_tc_k<n, nd, true, false>(a, out) : shape_tc_k<n, nd, false, false>(a, out);
+    if constexpr (N == 32 && nd == 16) {
+        if (a.slice_opd_stride > 0)
+            return f16 ? shape_tc_k<n, N, nd, true, true, false>(a, out) : shape_tc_k<n, N, nd, true, false, false>(a, out);
+    } else {
+        if (a.slice_opd_stride > 0) return cudaErrorInvalidValue;
+    }
+    if (a.mma_u)
+        return f16 ? shape_tc_k<n, N, nd, false, true, true>(a, out) : shape_tc_k<n, N, nd, false, false, true>(a, out);
+    return f16 ? shape_tc_k<n, N, nd, false, true, false>(a, out) : shape_tc_k<n, N, nd, false, false, false>(a, out);
 }
 
 }  // namespace
 
-bool sh_tc_supported(int n, int N, int nd) { return N == 32 && ((n == 10 && nd == 16) || (n == 8 && nd == 16)); }
+// The geometries with a tensor-core spot kernel: 32-point DFTs with a 16 x 16 detector (n = 8
+// or 10), and the other DFT sizes of the configured sensors -- 16-point (n = 8, 8 x 8
+// detector) and 24-point (n = 6, 12 x 12 detector).
+bool sh_tc_supported(int n, int N, int nd) {
+    return (N == 32 && nd == 16 && (n == 10 || n == 8)) || (N == 16 && n == 8 && nd == 8) ||
+           (N == 24 && n == 6 && nd == 12);
+}
+
+// The per-slice LGS variant exists for the 32-point tensor-core geometries.
+bool sh_tc_slices_supported(int n, int N, int nd) { return N == 32 && nd == 16 && (n == 10 || n == 8); }
 
 // Operand tiles of the two constant matrices, already in the swizzled shared layout, in BF16 or
 // FP16 (hi = the element's rounding of the value, lo = that of the remainder).
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
                     const double *Ga_im64, bool f16, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
-                    std::vector<uint8_t> &B2l) {
+                    std::vector<uint8_t> &B2l, std::vector<uint8_t> &A0) {
+    A0.assign(16384, 0);
     B1.assign(8192, 0);
     B2h.assign(4096, 0);
     B2l.assign(4096, 0);
@@ -1034,6 +1187,18 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
                         const float lo = (float)(val - (double)hi);
                         put(B1, cp * 32 + m, t * 2 * n + c * n + q, t == 2 ? lo : hi);
                     }
+    // A0[row = b * 32 + k][K = t * 2n + c * n + p]: F[k][p] (c = 0 real, 1 imaginary) as
+    // [F_hi | F_lo | F_hi], the same for the four subapertures b of a group; rows k >= N zero
+    for (int b = 0; b < 4; ++b)
+        for (int k = 0; k < N; ++k)
+            for (int t = 0; t < 3; ++t)
+                for (int c = 0; c < 2; ++c)
+                    for (int p = 0; p < n; ++p) {
+                        const double val = c == 0 ? F_re64[p * N + k] : F_im64[p * N + k];
+                        const float hi = rounded((float)val);
+                        const float lo = (float)(val - (double)hi);
+                        put(A0, b * 32 + k, t * 2 * n + c * n + p, t == 1 ? lo : hi);
+                    }
     // B2h[row = c'' * 16 + dx][K = h * 32 + m] = Ga_hi, B2l = [Ga_lo; 0]
     for (int cpp = 0; cpp < 2; ++cpp)
         for (int dx = 0; dx < n; ++dx)
@@ -1048,8 +1213,10 @@ void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, co
 }
 
 cudaError_t tc_launch_shape(const ShArgs &a, LaunchShape *out, bool f16) {
-    if (a.n == 10 && a.nd == 16) return shape_tc<10, 16>(a, out, f16);
-    if (a.n == 8 && a.nd == 16) return shape_tc<8, 16>(a, out, f16);
+    if (a.N == 32 && a.n == 10 && a.nd == 16) return shape_tc<10, 32, 16>(a, out, f16);
+    if (a.N == 32 && a.n == 8 && a.nd == 16) return shape_tc<8, 32, 16>(a, out, f16);
+    if (a.N == 16 && a.n == 8 && a.nd == 8) return shape_tc<8, 16, 8>(a, out, f16);
+    if (a.N == 24 && a.n == 6 && a.nd == 12) return shape_tc<6, 24, 12>(a, out, f16);
     return cudaErrorInvalidValue;
 }
 

@@ -313,5 +313,113 @@ __device__ __forceinline__ void finish(const float (&Bv)[nd / 2], const WfsDesc 
     if (!split) noise_centroid<nd>(ev, W, D, seed, v, lane, rk);
 }
 
+// ---- any DFT size (N <= 32) and detector tile: the same stages as direct sums over the warp's
+// rows in shared memory, in the order of the FP32 generic kernel; the noise pixel by pixel.
+
+// Ta: [N][n|1] the first stage (row k, column dx).  kt: the subaperture's K~ [2n-1][n].  Ga:
+// [n][N] Ga[d][k] = exp(+2 pi i (k - cN) d / N) (conjugated for d < 0).  G: [n][nd] G[d][i].
+// M [2n-1][n], P [2n-1][nd] complex and B [nd][nd] real are the warp's scratch; B holds the
+// binned elongated spot on return.
+template <int n, int N, int nd>
+__device__ __forceinline__ void lgs_direct(const float2 *Ta, float2 *M, float2 *P, float *B, const float2 *kt,
+                                           const float2 *Ga, const float2 *G, int lane) {
+    constexpr int D2 = 2 * n - 1, no = n | 1;
+    // M[dy][dx] = Kt[dy][dx] sum_k Ga[dy][k] Ta[k][dx]
+    for (int o = lane; o < D2 * n; o += 32) {
+        const int dyi = o / n, dx = o - dyi * n, dy = dyi - (n - 1);
+        const float2 *ga = Ga + (dy >= 0 ? dy : -dy) * N;
+        const float sg = dy >= 0 ? 1.0f : -1.0f;
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll 8
+        for (int k = 0; k < N; ++k) {
+            float2 gg = ga[k];
+            gg.y *= sg;
+            cmac(acc, gg, Ta[k * no + dx]);
+        }
+        const float2 kv = kt[o];
+        M[o] = make_float2(acc.x * kv.x - acc.y * kv.y, acc.x * kv.y + acc.y * kv.x);
+    }
+    __syncwarp();
+    // P[dy][ix] = sum_dx M[dy][dx] G[dx][ix]
+    for (int o = lane; o < D2 * nd; o += 32) {
+        const int dyi = o / nd, ix = o - dyi * nd;
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int dx = 0; dx < n; ++dx) cmac(acc, M[dyi * n + dx], G[dx * nd + ix]);
+        P[o] = acc;
+    }
+    __syncwarp();
+    // B[iy][ix] = Re sum_dy G[iy][dy] P[dy][ix]
+    for (int o = lane; o < nd * nd; o += 32) {
+        const int iy = o / nd, ix = o - iy * nd;
+        float sum = 0.0f;
+#pragma unroll
+        for (int dyi = 0; dyi < D2; ++dyi) {
+            const int dy = dyi - (n - 1);
+            float2 gg = G[(dy >= 0 ? dy : -dy) * nd + iy];
+            if (dy < 0) gg.y = -gg.y;
+            const float2 pv = P[dyi * nd + ix];
+            sum = fmaf(gg.x, pv.x, fmaf(-gg.y, pv.y, sum));
+        }
+        B[o] = sum;
+    }
+    __syncwarp();
+}
+
+// NGS: b x b binning of the spot image rows I ([N][N + 1] floats) into B [nd][nd].
+template <int N, int nd>
+__device__ __forceinline__ void ngs_direct(const float *I, float *B, int lane) {
+    constexpr int b = N / nd;
+    for (int o = lane; o < nd * nd; o += 32) {
+        const int iy = o / nd, ix = o - iy * nd;
+        float sum = 0.0f;
+#pragma unroll
+        for (int r = 0; r < b; ++r)
+#pragma unroll
+            for (int c = 0; c < b; ++c) sum += I[(b * iy + r) * (N + 1) + b * ix + c];
+        B[o] = sum;
+    }
+    __syncwarp();
+}
+
+// Photometry, noise (pixel by pixel) and the centroid of subaperture v from its binned image B
+// [nd][nd] in the warp's shared memory; lane 0 writes the slopes.
+template <int nd>
+__device__ __forceinline__ void finish_direct(const float *B, const WfsDesc &W, const InstDyn &D, uint64_t seed,
+                                              int v, int lane) {
+    constexpr int nd2 = nd * nd;
+    float sb = 0.0f;
+    for (int o = lane; o < nd2; o += 32) sb += B[o];
+    sb = warp_sum(sb);
+    const float scale = sb > 0.0f ? W.photons * __ldg(W.fill + v) / sb : 0.0f;
+    const float cd = 0.5f * (float)(nd - 1);
+    const uint32_t tlo = (uint32_t)__double_as_longlong(D.t);
+    const uint32_t thi = (uint32_t)((unsigned long long)__double_as_longlong(D.t) >> 32);
+    float *st_E = D.st_E ? D.st_E + W.det_off + (size_t)v * nd2 : nullptr;
+    float *st_C = D.st_C ? D.st_C + W.det_off + (size_t)v * nd2 : nullptr;
+    float sc = 0.0f, sx = 0.0f, sy = 0.0f;
+    for (int o = lane; o < nd2; o += 32) {
+        const int iy = o / nd, ix = o - iy * nd;
+        const float e = scale * B[o];
+        const float c = D.noise ? noise_pixel(e, W.read_noise, seed, (uint32_t)(v * nd2 + o), (uint32_t)W.gs_index,
+                                              tlo, thi)
+                                : e;
+        if (st_E) st_E[o] = e;
+        if (st_C) st_C[o] = c;
+        sc += c;
+        sx = fmaf((float)ix - cd, c, sx);
+        sy = fmaf((float)iy - cd, c, sy);
+    }
+    sc = warp_sum(sc);
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) {
+        const bool ok = sc > 0.0f;
+        float *sl = D.slopes + W.slope_off;
+        sl[2 * v] = ok ? sx / sc : 0.0f;
+        sl[2 * v + 1] = ok ? sy / sc : 0.0f;
+    }
+}
+
 }  // namespace tail
 }  // namespace gbwfs

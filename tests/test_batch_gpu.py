@@ -15,6 +15,8 @@ from _gpu import check_against_oracle  # noqa: E402
 
 
 MIXED = "mixed"  # tensor-core geometries alternate between BF16 x3 and scaled FP16 x3
+# (n_pix_sub, n_fft, n_det) with a tensor-core spot kernel
+TC_GEOMETRIES = {(10, 32, 16), (8, 32, 16), (8, 16, 8), (6, 24, 12)}
 
 
 def _instances(k, seed=4000, prec=inputs.PREC_FP32):
@@ -22,7 +24,7 @@ def _instances(k, seed=4000, prec=inputs.PREC_FP32):
     out = []
     for i, c in enumerate(insts):
         g = c.geometries[0]
-        tc_ok = g.n_fft == 32 and g.n_pix_sub in (8, 10) and g.n_det == 16
+        tc_ok = (g.n_pix_sub, g.n_fft, g.n_det) in TC_GEOMETRIES
         if prec == MIXED:
             g.precision = (inputs.PREC_BF16X3 if i % 2 else inputs.PREC_FP16S) if tc_ok else inputs.PREC_FP32
         elif prec in (inputs.PREC_BF16X3, inputs.PREC_FP16S) and not tc_ok:

@@ -338,8 +338,58 @@ def test_bf16x3_edge_geometries(n_sub, n, lgs, noise, precision):
 
 
 @pytest.mark.parametrize("precision", TC_PRECISIONS)
-def test_bf16x3_unsupported_geometry_is_refused(precision):
+@pytest.mark.parametrize("cfg_fn", [inputs.config1, inputs.config2])
+def test_tensor_core_configs_1_2_full_parity(cfg_fn, precision):
+    """Configs 1 (16-point DFT, 8 x 8 detector) and 2 (24-point DFT, 12 x 12 detector, LGS with
+    elongation and an NGS) with the DFT on the tensor cores: every subaperture of every WFS
+    against the FP64 oracle at the bars of the FP32 path, at two times."""
+    cfg = cfg_fn(precision)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    for t in (0.0, 0.013):
+        gpu, w = run_library(cfg, scr, t)
+        _check_wfs(cfg, scr, t, gpu)
+        w.close()
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_tensor_core_config2_noisy_frame(precision):
+    """Config 2 on the tensor cores with noise: counts equal the oracle's on >= 99.9 % of the
+    pixels, slopes of the subapertures whose counts all agree within the slope bar."""
     cfg = inputs.config2(precision)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    gpu, w = run_library(cfg, scr, 0.02, seed=42, noise=True)
+    for k in (1, 3):
+        ref = oracle.measure_wfs(cfg, scr, k, 0.02, seed=42, noise=True, stages=True)
+        same = np.abs(gpu[k]["C"] - ref["C"]) < 1e-3
+        assert same.mean() >= 0.999, same.mean()
+        ok = np.all(same.reshape(len(same), -1), axis=1)
+        assert slope_rms(gpu[k]["slopes"][ok], ref["slopes"][ok]) < SLOPE_RMS
+    w.close()
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+@pytest.mark.parametrize("n_sub,n,N,nd,lgs,noise", [(9, 8, 16, 8, True, False), (7, 8, 16, 8, False, True),
+                                                    (15, 6, 24, 12, True, True), (5, 6, 24, 12, False, False)])
+def test_tensor_core_16_24_point_edge_geometries(n_sub, n, N, nd, lgs, noise, precision):
+    """16- and 24-point geometries on the tensor cores: ragged groups (valid count not a multiple
+    of 4), LGS and NGS, noise on and off, against the oracle."""
+    cfg = _small_cfg(n_sub, n, N, nd, lgs)
+    cfg.geometries[0].precision = precision
+    scr = inputs.make_screens(cfg.layers, 8)
+    gpu, w = run_library(cfg, scr, 0.003, seed=4, noise=noise)
+    _check_wfs(cfg, scr, 0.003, gpu, noise=noise, seed=4)
+    if noise:
+        ref = oracle.measure_wfs(cfg, scr, 0, 0.003, seed=4, noise=True, stages=True)
+        same = np.abs(gpu[0]["C"] - ref["C"]) < 1e-3
+        assert same.mean() >= 0.999
+    w.close()
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_tensor_core_unsupported_geometry_is_refused(precision):
+    """A geometry without a tensor-core kernel (odd subaperture size) is refused at creation."""
+    cfg = _small_cfg(9, 7, 16, 8, False)
+    cfg.geometries[0].precision = precision
     with pytest.raises(native.WfsError) as ei:
         native.Wfs(cfg)
     assert ei.value.status == native.WFS_EUNSUPPORTED
@@ -448,4 +498,23 @@ def test_busy_on_another_stream():
     native.wfs_measure(w.h, scr.data_ptr(), 0.004, b.data_ptr(), s2.cuda_stream)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+    w.close()
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_first_dft_stage_as_mma_parity(monkeypatch, precision):
+    """The tensor-core kernels' variant with U = F X as a third MMA (GBWFS_TC_MMA_U=1): config 2
+    in full and the ELT frame sampled against the oracle at the same bars."""
+    monkeypatch.setenv("GBWFS_TC_MMA_U", "1")
+    cfg = inputs.config2(precision)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    gpu, w = run_library(cfg, scr, 0.031)
+    _check_wfs(cfg, scr, 0.031, gpu)
+    w.close()
+    cfg = inputs.config3(precision)
+    scr = inputs.make_screens(cfg.layers, cfg.seed)
+    gpu, w = run_library(cfg, scr, 0.05)
+    sel = [np.arange(k, len(d["slopes"]), 37, dtype=np.int32) if cfg.stars[k].is_lgs
+           else np.arange(len(d["slopes"]), dtype=np.int32) for k, d in enumerate(gpu)]
+    _check_wfs(cfg, scr, 0.05, gpu, sel=sel)
     w.close()
