@@ -901,11 +901,17 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
     if (st != WFS_OK) return st;
     for (int i = 0; i < n_geom; ++i) {
         const wfs_geometry &g = geom[i];
-        if ((g.precision == WFS_PREC_BF16X3 || g.precision == WFS_PREC_FP16S) &&
-            !sh_tc_supported(g.n_pix_sub, g.n_fft, g.n_det))
+        if (g.precision != WFS_PREC_BF16X3 && g.precision != WFS_PREC_FP16S) continue;
+        const std::string who = "geometry " + std::to_string(i) + (g.precision == WFS_PREC_FP16S ? ": WFS_PREC_FP16S" : ": WFS_PREC_BF16X3");
+        bool lgs = false;
+        for (int w = 0; w < n_gs; ++w) lgs |= gs[w].geometry_index == i && gs[w].is_lgs;
+        if (sh_tc64_supported(g.n_pix_sub, g.n_fft, g.n_det)) {
+            if (lgs) return fail(nullptr, WFS_EUNSUPPORTED, who + " with n_fft = 64 is built for NGS sensors only");
+        } else if (!sh_tc_supported(g.n_pix_sub, g.n_fft, g.n_det)) {
             return fail(nullptr, WFS_EUNSUPPORTED,
-                        "geometry " + std::to_string(i) + (g.precision == WFS_PREC_FP16S ? ": WFS_PREC_FP16S" : ": WFS_PREC_BF16X3") +
-                            " is built for (n_pix_sub, n_fft, n_det) = (10, 32, 16), (8, 32, 16), (8, 16, 8) and (6, 24, 12)");
+                        who + " is built for (n_pix_sub, n_fft, n_det) = (10, 32, 16), (8, 32, 16), (8, 16, 8), "
+                              "(6, 24, 12) and (32, 64, 32) (NGS)");
+        }
     }
 
     wfs_ctx *h = new wfs_ctx();
@@ -940,8 +946,11 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
         if (geom[i].precision == WFS_PREC_BF16X3 || geom[i].precision == WFS_PREC_FP16S) {
             const int n = geom[i].n_pix_sub, N = geom[i].n_fft;
             std::vector<uint8_t> b1, b2h, b2l, a0;
-            build_tc_tiles(n, N, F64.data(), F64.data() + (size_t)n * N, Ga64.data(), Ga64.data() + (size_t)n * N,
-                           geom[i].precision == WFS_PREC_FP16S, b1, b2h, b2l, a0);
+            if (N == 64)
+                build_tc64_tiles(F64.data(), F64.data() + (size_t)n * N, geom[i].precision == WFS_PREC_FP16S, a0, b1);
+            else
+                build_tc_tiles(n, N, F64.data(), F64.data() + (size_t)n * N, Ga64.data(), Ga64.data() + (size_t)n * N,
+                               geom[i].precision == WFS_PREC_FP16S, b1, b2h, b2l, a0);
             if ((e = upload(&G.tcB1, b1)) != cudaSuccess || (e = upload(&G.tcB2h, b2h)) != cudaSuccess ||
                 (e = upload(&G.tcA0, a0)) != cudaSuccess ||
                 (e = upload(&G.tcB2l, b2l)) != cudaSuccess) {

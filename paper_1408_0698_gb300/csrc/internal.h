@@ -255,6 +255,8 @@ inline bool is_tc(int kind) { return kind == kSpotTc || kind == kSpotTcF16; }
 bool sh_n32_supported(int n, int N, int nd);
 bool sh_tc_supported(int n, int N, int nd);
 bool sh_tc_slices_supported(int n, int N, int nd);
+// The 64-point tensor-core kernel (32 x 32 pupil pixels, 32 x 32 detector; NGS only).
+bool sh_tc64_supported(int n, int N, int nd);
 // Shape of the launch (sets the kernel's dynamic shared-memory attribute).
 cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out);
 // after_project: the launch follows the projection on stream s and may start (prologue only)
@@ -273,6 +275,8 @@ inline bool splits_noise(int kind, int N, int nd) { return (kind == kSpotN32 || 
 void build_tc_tiles(int n, int N, const double *F_re64, const double *F_im64, const double *Ga_re64,
                     const double *Ga_im64, bool f16, std::vector<uint8_t> &B1, std::vector<uint8_t> &B2h,
                     std::vector<uint8_t> &B2l, std::vector<uint8_t> &A0);
+void build_tc64_tiles(const double *F_re64, const double *F_im64, bool f16, std::vector<uint8_t> &A0,
+                      std::vector<uint8_t> &B1);
 // Bounded mbarrier wait that is never satisfied; writes WFS_ETIMEOUT to *status.
 cudaError_t launch_wait_check(int *status, int limit, cudaStream_t s);
 // LGS uplink tip-tilt of every WFS of the table that has it on: one CTA per (WFS, turbulent

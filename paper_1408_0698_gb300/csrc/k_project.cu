@@ -17,9 +17,8 @@ namespace gbwfs {
 
 constexpr int kProjThreads = 256;
 
-constexpr int kProjWarps = kProjThreads / 32;
-constexpr int kRowChunk = 16;   // pupil rows a warp accumulates at once (n <= 16: all of them)
-constexpr int kUnitCols = 32;   // pupil columns of a dense unit: one per lane
+constexpr int kTilePixels = 4096;                         // pupil pixels per tiled CTA
+constexpr int kTilePx = kTilePixels / kProjThreads;       // per thread
 
 __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
     if (pow2) return i & (S - 1);
@@ -29,150 +28,210 @@ __device__ __forceinline__ int wrap_index(int i, int S, bool pow2) {
 
 constexpr int kOffsTable = 96;  // layer offsets a CTA keeps for every (WFS, layer) of its launch
 
-// Work units.  Launch block b of a WFS holds up to kProjWarps warp units: for a WFS sampled
-// densely (pupil pitch <= screen pitch) block b is a run of consecutive valid subapertures of
-// one subaperture row (a segment of at most kProjWarps * 32 pupil columns), and unit (b, w) is
-// its columns [32 w, 32 w + 32) over the segment's n pupil rows; otherwise unit (b, w) is 32
-// threads of 2 x 2 pupil pixels each.  Every warp takes units from the ticket counter.
+// One projection block (a tiled segment, or kProjThreads 2x2 pixel blocks); every thread of
+// the CTA calls it (its shared memory is free again once all threads have returned).  tab: the
+// CTA's layer offsets; with all_offs, entry w * max_layers + l for every WFS w of the launch
+// (filled once at the start of the kernel), else entries 0 .. L of the WFS last_wfs (refilled
+// when a block belongs to another WFS).
+__device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, int &last_wfs, LayerOffs *tab,
+                                            bool all_offs) {
 
-// Dense unit: lane = pupil column j of the segment.  Per layer, each lane finds its column's
-// screen coordinate (integer offset and fraction; the arithmetic of proj_math.cuh); the pupil
-// rows' coordinates are warp-uniform and go through a small per-warp table.  A screen row is
-// read once per layer as two coalesced loads per lane, (s[cb + lane], s[cb + lane + 1]) from
-// lane 0's column cb, and each lane takes its two taps from lane i0 = its column - cb by
-// shuffles.  With a scale c dx/ds <= 1 consecutive pupil rows advance by at most one screen row,
-// so the pair (top row, bottom row) carries over and only the new bottom row is read; the next
-// row is fetched one step ahead.  The per-pixel arithmetic and the order of the layer sum are
-// those of the direct gathers below, so both forms give the same OPD bit for bit.
-__device__ __forceinline__ void project_dense(const ProjArgs &a, const WfsDesc &W, const InstDesc &I,
-                                              const InstDyn &D, const LayerOffs *offs, const int4 sg, int chunk,
-                                              int4 *rows) {
-    const int lane = threadIdx.x & 31;
-    const int n = W.n, nn = n * n, S = I.S, ncol = sg.z * n;
-    const int j = chunk * kUnitCols + lane;
-    const bool live = j < ncol;
+    // the WFS owning this block: last entry whose first block is <= bid
+    int lo = 0, hi = a.n_wfs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.wfs[mid].proj_block_begin <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    const WfsDesc &W = a.wfs[lo];
+    const InstDesc &I = a.inst[W.inst];
+    const InstDyn &D = a.dyn[W.inst];
+    const int S = I.S;
+
+    const LayerOffs *s_off = all_offs ? tab + lo * a.max_layers : tab;
+    if (!all_offs && lo != last_wfs) {  // uniform: last_wfs was written before the caller's barrier
+        if ((int)threadIdx.x < proj_layers(I, D)) tab[threadIdx.x] = layer_offsets(I, W, D.t, threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x == 0) last_wfs = lo;  // read again only after the caller's barrier
+    }
+
     const bool pow2 = (S & (S - 1)) == 0;
-    const float half = 0.5f * (float)(W.n_sub * n - 1);
-    const float xr = (float)(sg.w * n + j) - half;
-    const int L = proj_layers(I, D);
-    float2 up = make_float2(0.0f, 0.0f);
-    bool up_read = false;
-    for (int p0 = 0; p0 < n; p0 += kRowChunk) {
-        const int nr = min(kRowChunk, n - p0);
-        float acc[kRowChunk];
+    if (W.tiled) {
+        // One run of consecutive subapertures of one subaperture row.  Each layer's screen
+        // footprint is staged in shared memory by cp.async; coordinates come from per-column
+        // and per-row tables (a pixel's screen column depends on its pupil column only).
+        // Tables and boxes are triple-buffered: in iteration l the CTA fills buffer
+        // (l + 1) mod 3, last read by layer l - 2, which every thread finished before the
+        // previous barrier; so one barrier per layer suffices (box l landed, tables l visible).
+        extern __shared__ float psm[];
+        __shared__ int4 s_geom[kMaxProjLayers];  // per layer: box origin (bx0, by0) and size (bw, bh)
+        const int4 sg = W.segs[bid - W.proj_block_begin];  // sy, v_first, count, sx0
+        const int n = W.n, nn = n * n, ncol = sg.z * n, L = proj_layers(I, D);
+        const int tab_floats = (6 * (ncol + n) + 3) & ~3;  // three tables, 16-byte aligned boxes
+        const int box_floats = ((a.box_cap - tab_floats) / 3) & ~3;
+        // buffer i: tables at tab0 + i (ncol + n), box at box0 + i box_floats
+        float2 *const tab0 = reinterpret_cast<float2 *>(psm);
+        float *const box0 = psm + tab_floats;
+        const float half = 0.5f * (float)(W.n_sub * n - 1);
+        // thread -> (pupil row p, columns ch + k nch, k < kTilePx): lanes of a warp take
+        // consecutive columns of one row, so their table and box reads fall in distinct banks
+        const int nch = (ncol + kTilePx - 1) / kTilePx, ntask = n * nch;  // ntask <= kProjThreads
+        const bool has_task = (int)threadIdx.x < ntask;
+        const int p = has_task ? (int)threadIdx.x / nch : 0, ch = (int)threadIdx.x - p * nch;
+        // acc[k / 2] holds the pixels k (x) and k + 1 (y), summed with packed FP32x2 operations
+        // (each half rounded as the scalar operation)
+        static_assert(kTilePx % 2 == 0, "pixels travel in pairs");
+        float2 acc[kTilePx / 2];
 #pragma unroll
-        for (int p = 0; p < kRowChunk; ++p) acc[p] = 0.0f;
-        for (int l = 0; l < L; ++l) {
-            const LayerOffs lo = offs[l];
-            const float *scr = layer_screen(I, D, l);
-            // this lane's column
-            int offc;
-            float fx;
-            screen_offset(lo.c, lo.cl, lo.fu, xr, offc, fx);
-            const int colabs = lo.bu + offc;
-            const int cb = __shfl_sync(0xffffffffu, colabs, 0);
-            const int i0 = colabs - cb;
-            const int c0 = wrap_index(cb + lane, S, pow2), c1 = wrap_index(cb + lane + 1, S, pow2);
-            // the rows' coordinates: lane p < nr takes pupil row p0 + p
-            if (lane < nr) {
-                const float yr = (float)(sg.x * n + p0 + lane) - half;
-                int offr;
-                float gy;
-                screen_offset(lo.c, lo.cl, lo.fv, yr, offr, gy);
-                rows[lane] = make_int4(wrap_index(lo.bv + offr, S, pow2), offr, __float_as_int(gy), 0);
+        for (int k = 0; k < kTilePx / 2; ++k) acc[k] = make_float2(0.0f, 0.0f);
+        // table entry j of layer l (column j < ncol, else row j - ncol): integer screen offset
+        // from the layer base (as float bits) and the fraction
+        auto coord = [&](int l, int j) -> float2 {
+            const bool col = j < ncol;
+            const float xr = col ? (float)(sg.w * n + j) - half : (float)(sg.x * n + (j - ncol)) - half;
+            int off;
+            float frac;
+            screen_offset(s_off[l].c, s_off[l].cl, col ? s_off[l].fu : s_off[l].fv, xr, off, frac);
+            return make_float2(__int_as_float(off), frac);
+        };
+        auto tables = [&](int l, float2 *t) {
+            for (int j = threadIdx.x; j < ncol + n; j += kProjThreads) t[j] = coord(l, j);
+        };
+        // Box origin (relative to the layer base) and size, the origin rounded down so that the
+        // box's first screen column is a multiple of 4 (16-byte copies when S % 4 == 0).
+        const bool vec = (S & 3) == 0;
+        if ((int)threadIdx.x < L) {
+            const int l = threadIdx.x;
+            int bx0 = __float_as_int(coord(l, 0).x), by0 = __float_as_int(coord(l, ncol).x);
+            int bw = __float_as_int(coord(l, ncol - 1).x) - bx0 + 2;
+            const int bh = __float_as_int(coord(l, ncol + n - 1).x) - by0 + 2;
+            if (vec) {
+                const int off = wrap_index(s_off[l].bu + bx0, S, pow2) & 3;
+                bx0 -= off;
+                bw = (bw + off + 3) & ~3;
             }
-            __syncwarp();
-            // every live lane's two taps lie within the warp's 32-column window (scale <= 1);
-            // otherwise (not met by the dense geometries) this layer gathers directly
-            const bool window = __all_sync(0xffffffffu, !live || (i0 >= 0 && i0 < 32));
-            const int src = i0 & 31;
-            auto taps = [&](int row) -> float2 {
-                const float *r = scr + (size_t)row * S;
-                const float x0 = __ldg(r + c0), x1 = __ldg(r + c1);
-                return make_float2(__shfl_sync(0xffffffffu, x0, src), __shfl_sync(0xffffffffu, x1, src));
-            };
-            auto taps_direct = [&](int row) -> float2 {
-                const float *r = scr + (size_t)row * S;
-                const int d0 = wrap_index(colabs, S, pow2), d1 = wrap_index(colabs + 1, S, pow2);
-                return make_float2(__ldg(r + d0), __ldg(r + d1));
-            };
-            if (window) {
-                int4 rw = rows[0];
-                int cur = rw.y;  // the top row's offset
-                float2 top = taps(rw.x), bot = taps(wrap_index(rw.x + 1, S, pow2));
-                int nxt = wrap_index(rw.x + 2, S, pow2);
-                float pf0 = __ldg(scr + (size_t)nxt * S + c0), pf1 = __ldg(scr + (size_t)nxt * S + c1);
-#pragma unroll
-                for (int p = 0; p < kRowChunk; ++p) {
-                    if (p < nr) {
-                        if (p > 0) {
-                            rw = rows[p];
-                            const int d = rw.y - cur;
-                            if (d == 1) {
-                                top = bot;
-                                bot = make_float2(__shfl_sync(0xffffffffu, pf0, src), __shfl_sync(0xffffffffu, pf1, src));
-                                nxt = wrap_index(rw.x + 2, S, pow2);
-                                pf0 = __ldg(scr + (size_t)nxt * S + c0);
-                                pf1 = __ldg(scr + (size_t)nxt * S + c1);
-                            } else if (d != 0) {
-                                top = taps(rw.x);
-                                bot = taps(wrap_index(rw.x + 1, S, pow2));
-                                nxt = wrap_index(rw.x + 2, S, pow2);
-                                pf0 = __ldg(scr + (size_t)nxt * S + c0);
-                                pf1 = __ldg(scr + (size_t)nxt * S + c1);
-                            }
-                            cur = rw.y;
-                        }
-                        const float gy = __int_as_float(rw.z);
-                        const float t = fmaf(fx, top.y - top.x, top.x);
-                        const float b = fmaf(fx, bot.y - bot.x, bot.x);
-                        acc[p] += fmaf(gy, b - t, t);
+            s_geom[l] = make_int4(bx0, by0, bw, bh);
+        }
+        // returns false (for every thread) when the box would not fit
+        auto issue_box = [&](int l, float *box) -> bool {
+            const int4 gm = s_geom[l];
+            const int bx0 = gm.x, by0 = gm.y, bw = gm.z, bh = gm.w;
+            if (bw * bh > box_floats) return false;
+            const float *scr = layer_screen(I, D, l);
+            if (vec) {
+                // one warp per box row, one lane per 16-byte chunk
+                const int cw = bw >> 2, lane = threadIdx.x & 31, cbase = s_off[l].bu + bx0;
+                for (int r = threadIdx.x >> 5; r < bh; r += kProjThreads / 32) {
+                    const float *srow = scr + (size_t)wrap_index(s_off[l].bv + by0 + r, S, pow2) * S;
+                    float *drow = box + r * bw;
+                    for (int c4 = lane; c4 < cw; c4 += 32) {
+                        if (!guard(r * bw + 4 * c4 + 3 < box_floats, a.status)) continue;
+                        const float *src = srow + wrap_index(cbase + 4 * c4, S, pow2);
+                        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(drow + 4 * c4);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
                     }
                 }
             } else {
-#pragma unroll
-                for (int p = 0; p < kRowChunk; ++p) {
-                    if (p < nr) {
-                        const int4 rw = rows[p];
-                        const float2 top = taps_direct(rw.x), bot = taps_direct(wrap_index(rw.x + 1, S, pow2));
-                        const float gy = __int_as_float(rw.z);
-                        const float t = fmaf(fx, top.y - top.x, top.x);
-                        const float b = fmaf(fx, bot.y - bot.x, bot.x);
-                        acc[p] += fmaf(gy, b - t, t);
+                for (int r = 0; r < bh; ++r) {
+                    const float *grow = scr + (size_t)wrap_index(s_off[l].bv + by0 + r, S, pow2) * S;
+                    for (int c = threadIdx.x; c < bw; c += kProjThreads) {
+                        if (!guard(r * bw + c < box_floats, a.status)) continue;
+                        const float *src = grow + wrap_index(s_off[l].bu + bx0 + c, S, pow2);
+                        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(box + r * bw + c);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
                     }
                 }
             }
-            __syncwarp();  // the row table is rewritten by the next layer
-        }
-        // the uplink tip-tilt as a plane over the pupil (zero when off); the uplink kernel may
-        // still be running (programmatic dependent launch): wait for it first
-        if (W.uplink && !up_read) {
-            wait_prior_grid();
-            up = *W.uplink;
-            up_read = true;
-        }
-        if (live) {
-            const int v = sg.y + j / n, q = j - (j / n) * n;
-            if (guard(v < W.n_valid, a.status)) {
-                float *opd = D.opd + W.opd_off + (size_t)v * nn + q;
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            return true;
+        };
+        tables(0, tab0);
+        __syncthreads();  // geometry of every layer, tables of layer 0
+        bool fits = issue_box(0, box0);
+        for (int l = 0; l < L && fits; ++l) {
+            const int cur = l % 3, nxt = (l + 1) % 3;
+            const bool more = l + 1 < L;
+            bool fits_next = true;
+            if (more) {
+                tables(l + 1, tab0 + nxt * (ncol + n));
+                fits_next = issue_box(l + 1, box0 + nxt * box_floats);
+            }
+            if (more && fits_next)
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            const float2 *t = tab0 + cur * (ncol + n);
+            const float *box = box0 + cur * box_floats;
+            const int4 gm = s_geom[l];
+            const int bw = gm.z;
+            if (has_task) {
+                const float2 rp = t[ncol + p];
+                const float *brow = box + (__float_as_int(rp.x) - gm.y) * bw - gm.x;
+                const float2 gy = make_float2(rp.y, rp.y), m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-                for (int p = 0; p < kRowChunk; ++p)
-                    if (p < nr) {
-                        const float row_tilt = up.y * ((float)(sg.x * n + p0 + p) - half);
-                        opd[(p0 + p) * n] = acc[p] + fmaf(up.x, xr, row_tilt);
+                for (int k = 0; k < kTilePx; k += 2) {
+                    const int j = ch + k * nch, j2 = j + nch;
+                    if (j2 < ncol) {
+                        // two pixels: x - y as fma(y, -1, x) is the rounded difference
+                        const float2 ca = t[j], cb = t[j2];
+                        const float *b0 = brow + __float_as_int(ca.x), *b1 = brow + __float_as_int(cb.x);
+                        if (!guard(b0 >= box && b0 + bw + 1 < box + box_floats && b1 >= box &&
+                                       b1 + bw + 1 < box + box_floats,
+                                   a.status))
+                            continue;
+                        const float2 fx = make_float2(ca.y, cb.y);
+                        const float2 s00 = make_float2(b0[0], b1[0]), s01 = make_float2(b0[1], b1[1]);
+                        const float2 s10 = make_float2(b0[bw], b1[bw]), s11 = make_float2(b0[bw + 1], b1[bw + 1]);
+                        const float2 top = __ffma2_rn(fx, __ffma2_rn(s00, m1, s01), s00);
+                        const float2 bot = __ffma2_rn(fx, __ffma2_rn(s10, m1, s11), s10);
+                        acc[k / 2] = __fadd2_rn(acc[k / 2], __ffma2_rn(gy, __ffma2_rn(top, m1, bot), top));
+                    } else if (j < ncol) {
+                        const float2 cj = t[j];
+                        const float *b0 = brow + __float_as_int(cj.x);
+                        if (!guard(b0 >= box && b0 + bw + 1 < box + box_floats, a.status)) continue;
+                        const float s00 = b0[0], s01 = b0[1], s10 = b0[bw], s11 = b0[bw + 1];
+                        const float top = fmaf(cj.y, s01 - s00, s00);
+                        const float bot = fmaf(cj.y, s11 - s10, s10);
+                        acc[k / 2].x += fmaf(rp.y, bot - top, top);
                     }
+                }
+            }
+            fits = fits_next;
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (!fits && threadIdx.x == 0 && a.status) atomicCAS(a.status, 0, 6 /* WFS_EUNSUPPORTED */);
+        if (has_task) {
+            // column j = v n + q of the segment -> subaperture v, column q; j advances by nch
+            float *opd = D.opd + W.opd_off + (size_t)sg.y * nn + p * n;
+            const int dv = nch / n, dq = nch - dv * n;
+            int v = ch / n, q = ch - v * n;
+            // the uplink tip-tilt as a plane over the pupil (zero when off); the uplink kernel may
+            // still be running (programmatic dependent launch): wait for it first
+            float2 up = make_float2(0.0f, 0.0f);
+            if (W.uplink) {
+                wait_prior_grid();
+                up = *W.uplink;
+            }
+            const float row_tilt = up.y * ((float)(sg.x * n + p) - half);
+#pragma unroll
+            for (int k = 0; k < kTilePx; ++k) {
+                const float xr = (float)(sg.w * n + ch + k * nch) - half;
+                if (ch + k * nch < ncol) opd[v * nn + q] = (k & 1 ? acc[k / 2].y : acc[k / 2].x) + fmaf(up.x, xr, row_tilt);
+                q += dq;
+                v += dv;
+                if (q >= n) {
+                    q -= n;
+                    ++v;
+                }
             }
         }
+        return;
     }
-}
 
-// Sparse unit: each thread one 2 x 2 block of pupil pixels (rows p, p+1; columns q, q+1) of one
-// subaperture, gathered directly from the screens.
-__device__ __forceinline__ void project_sparse(const ProjArgs &a, const WfsDesc &W, const InstDesc &I,
-                                               const InstDyn &D, const LayerOffs *s_off, int blk) {
-    const int S = I.S;
-    const bool pow2 = (S & (S - 1)) == 0;
+    // each thread: one 2x2 block of pupil pixels (rows p, p+1; columns q, q+1) of one subaperture
     const int n = W.n, nn = n * n, nb = (n + 1) >> 1, nbb = nb * nb;
+    const int blk = (bid - W.proj_block_begin) * kProjThreads + threadIdx.x;
     if (blk >= W.n_valid * nbb) return;
     const int v = blk / nbb, r = blk - v * nbb, bp = r / nb, bq = r - bp * nb;
     if (!guard(v < W.n_valid, a.status)) return;
@@ -234,16 +293,14 @@ __device__ __forceinline__ void project_sparse(const ProjArgs &a, const WfsDesc 
                 opd[(p0 + a2) * n + q0 + b2] = acc[a2][b2] + fmaf(up.x, xr[b2], up.y * yr[a2]);
 }
 
-// Units 0 .. n_blocks * kProjWarps of this launch (unit u = (block u / kProjWarps, warp unit
-// u % kProjWarps)).  Each warp starts with unit blockIdx.x * kProjWarps + its warp; with a.work
-// it then draws its next unit from the ticket counter (so warps that start late take fewer
-// units and no partial last wave is left), and the last warp to finish resets the counter.
+// Blocks 0 .. n_blocks of this launch.  Each CTA starts with block blockIdx.x; with a.work the
+// grid holds only as many CTAs as fit at once and each draws its next block from the ticket
+// counter (issued at the top, consumed after the block), so CTAs that start late take fewer
+// blocks and no partial last wave is left; the last CTA to finish resets the counter.
 __global__ void __launch_bounds__(kProjThreads, 3) k_project(const __grid_constant__ ProjArgs a) {
     allow_dependent_grid();  // every CTA of this grid is resident or done: the spot kernel may start
+    __shared__ int s_next, s_last_wfs;
     __shared__ LayerOffs s_tab[kOffsTable];
-    __shared__ LayerOffs s_wtab[kProjWarps][kMaxProjLayers];
-    __shared__ int4 s_rows[kProjWarps][kRowChunk];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     // the layer offsets of every (WFS, layer) of this launch, once per CTA, when they fit
     const bool all_offs = a.n_wfs * a.max_layers <= kOffsTable;
     if (all_offs) {
@@ -254,46 +311,25 @@ __global__ void __launch_bounds__(kProjThreads, 3) k_project(const __grid_consta
             if (l < proj_layers(I, a.dyn[W.inst])) s_tab[i] = layer_offsets(I, W, a.dyn[W.inst].t, l);
         }
     }
+    if (threadIdx.x == 0) s_last_wfs = -1;
     __syncthreads();
-    const int n_units = a.n_blocks * kProjWarps;
-    int last_wfs = -1;
-    int u = blockIdx.x * kProjWarps + wib;
-    while (u < n_units) {
+    int blk = blockIdx.x;
+    while (blk < a.n_blocks) {
         int ticket = 0;
-        if (a.work && lane == 0) ticket = atomicAdd(a.work, 1);
-        const int bid = u / kProjWarps + a.block_base, unit = u - (u / kProjWarps) * kProjWarps;
-        // the WFS owning this block: last entry whose first block is <= bid
-        int lo = 0, hi = a.n_wfs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.wfs[mid].proj_block_begin <= bid) lo = mid;
-            else hi = mid - 1;
-        }
-        const WfsDesc &W = a.wfs[lo];
-        const InstDesc &I = a.inst[W.inst];
-        const InstDyn &D = a.dyn[W.inst];
-        const LayerOffs *offs = all_offs ? s_tab + lo * a.max_layers : s_wtab[wib];
-        if (!all_offs && lo != last_wfs) {
-            for (int l = lane; l < proj_layers(I, D); l += 32) s_wtab[wib][l] = layer_offsets(I, W, D.t, l);
-            __syncwarp();
-            last_wfs = lo;
-        }
-        if (W.tiled) {
-            const int4 sg = W.segs[bid - W.proj_block_begin];
-            if (unit * kUnitCols < sg.z * W.n) project_dense(a, W, I, D, offs, sg, unit, s_rows[wib]);
-        } else {
-            project_sparse(a, W, I, D, offs, (bid - W.proj_block_begin) * kProjThreads + unit * 32 + lane);
-        }
+        if (a.work && threadIdx.x == 0) ticket = atomicAdd(a.work, 1);
+        project_one(a, blk + a.block_base, s_last_wfs, s_tab, all_offs);
+        __syncthreads();  // the block's shared memory is free; orders s_next
         if (a.work) {
-            ticket = __shfl_sync(0xffffffffu, ticket, 0);
-            u = (int)gridDim.x * kProjWarps + ticket;
+            if (threadIdx.x == 0) s_next = (int)gridDim.x + ticket;
+            __syncthreads();
+            blk = s_next;
         } else {
-            u += (int)gridDim.x * kProjWarps;
+            blk += gridDim.x;
         }
     }
-    if (a.work && lane == 0) {
+    if (a.work && threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(a.work + 1, 1) == (int)gridDim.x * kProjWarps - 1) {
+        if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
             a.work[0] = 0;
             a.work[1] = 0;
         }
@@ -301,8 +337,11 @@ __global__ void __launch_bounds__(kProjThreads, 3) k_project(const __grid_consta
 }
 
 int segment_max_count(int n) {
-    // a segment of c subaperture columns is c n pupil columns: at most one 32-column unit per warp
-    return std::max(1, kProjWarps * kUnitCols / n);
+    // a segment of c subaperture columns has n rows x ceil(c n / kTilePx) column sets, one
+    // per thread
+    int c = 1;
+    while (n * (((c + 1) * n + kTilePx - 1) / kTilePx) <= kProjThreads) ++c;
+    return c;
 }
 
 int project_blocks(const WfsDesc &d) {
@@ -311,8 +350,11 @@ int project_blocks(const WfsDesc &d) {
     return (d.n_valid * nb * nb + kProjThreads - 1) / kProjThreads;
 }
 
-int project_box_floats(const WfsDesc &) {
-    return 0;  // the projection stages nothing in dynamic shared memory
+int project_box_floats(const WfsDesc &d) {
+    if (!d.tiled) return 0;
+    // three sets of coordinate tables (3 x (ncol + n) float2) and three boxes of at most
+    // (ncol + 2) x (n + 2) screen pixels (padded for the 16-byte alignment)
+    return 6 * (d.seg_cols + d.n) + 4 + 3 * ((d.seg_cols + 9) * (d.n + 3) + 4);
 }
 
 void build_segments(const std::vector<int32_t> &ids, int n_sub, int max_count, std::vector<int4> &segs,

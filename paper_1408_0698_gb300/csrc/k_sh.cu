@@ -371,13 +371,14 @@ cudaError_t generic_shape(const ShArgs &a, LaunchShape *out) {
 
 cudaError_t n32_launch_shape(const ShArgs &a, LaunchShape *out);
 cudaError_t tc_launch_shape(const ShArgs &a, LaunchShape *out, bool f16);
+cudaError_t tc64_launch_shape(const ShArgs &a, LaunchShape *out, bool f16);
 
 cudaError_t spot_launch_shape(int kind, const ShArgs &a, LaunchShape *out) {
     switch (kind) {
         case kSpotGeneric: return generic_shape(a, out);
         case kSpotN32: return n32_launch_shape(a, out);
-        case kSpotTc: return tc_launch_shape(a, out, false);
-        case kSpotTcF16: return tc_launch_shape(a, out, true);
+        case kSpotTc: return a.N == 64 ? tc64_launch_shape(a, out, false) : tc_launch_shape(a, out, false);
+        case kSpotTcF16: return a.N == 64 ? tc64_launch_shape(a, out, true) : tc_launch_shape(a, out, true);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -180,15 +180,15 @@ def config2(precision: int = PREC_FP32) -> Config:
     return Config("config2_mcao_8m", tel, geom, stars, lay, seed=2000, dt_s=1e-3, steps=100)
 
 
-def config3(precision: int = PREC_BF16X3) -> Config:
+def config3(precision: int = PREC_BF16X3, ngs_precision: int = None) -> Config:
     """ELT: 800x800 px pupil at 4.875e-2 m, obstruction 0.28; 6 LGS (80x80, n=10, N=32,
     16x16 det px) on a 45" ring; 3 H-band NGS 2x2 (n=32, N=64, 32x32 det px) on a 60" ring;
-    10 layers 0-20 km.  `precision` applies to the LGS geometry; the 12 NGS spots per frame
-    use the FP32 DFT."""
+    10 layers 0-20 km.  `precision` is the DFT arithmetic of both geometries unless
+    `ngs_precision` sets the NGS geometry's."""
     dx = 4.875e-2
     tel = Telescope(800 * dx, 0.28)
     geom = [Geometry(80, 10, 32, 16, 0.5, precision),
-            Geometry(2, 32, 64, 32, 0.5, PREC_FP32)]
+            Geometry(2, 32, 64, 32, 0.5, precision if ngs_precision is None else ngs_precision)]
     stars = [_lgs(tx, ty, az, 0) for (tx, ty, az) in _ring(6, 45.0 * ARCSEC)]
     stars += [_ngs(tx, ty, 1650e-9, 1, photons=5000.0) for (tx, ty, _) in _ring(3, 60.0 * ARCSEC)]
     alts = np.linspace(0.0, 20e3, 10)

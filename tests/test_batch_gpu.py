@@ -16,7 +16,7 @@ from _gpu import check_against_oracle  # noqa: E402
 
 MIXED = "mixed"  # tensor-core geometries alternate between BF16 x3 and scaled FP16 x3
 # (n_pix_sub, n_fft, n_det) with a tensor-core spot kernel
-TC_GEOMETRIES = {(10, 32, 16), (8, 32, 16), (8, 16, 8), (6, 24, 12)}
+TC_GEOMETRIES = {(10, 32, 16), (8, 32, 16), (8, 16, 8), (6, 24, 12), (32, 64, 32)}
 
 
 def _instances(k, seed=4000, prec=inputs.PREC_FP32):

@@ -386,6 +386,34 @@ def test_tensor_core_16_24_point_edge_geometries(n_sub, n, N, nd, lgs, noise, pr
 
 
 @pytest.mark.parametrize("precision", TC_PRECISIONS)
+@pytest.mark.parametrize("n_sub,noise", [(2, False), (3, True), (4, False)])
+def test_tensor_core_64_point_ngs(n_sub, noise, precision):
+    """The 64-point NGS geometry (32 x 32 pupil pixels, 32 x 32 detector) on the tensor cores:
+    2 x 2 to 4 x 4 subapertures (odd valid counts leave half a step idle), noise on and off,
+    every subaperture against the oracle."""
+    cfg = _small_cfg(n_sub, 32, 64, 32, False)
+    cfg.geometries[0].precision = precision
+    scr = inputs.make_screens(cfg.layers, 6)
+    gpu, w = run_library(cfg, scr, 0.002, seed=5, noise=noise)
+    _check_wfs(cfg, scr, 0.002, gpu, noise=noise, seed=5)
+    if noise:
+        ref = oracle.measure_wfs(cfg, scr, 0, 0.002, seed=5, noise=True, stages=True)
+        same = np.abs(gpu[0]["C"] - ref["C"]) < 1e-3
+        assert same.mean() >= 0.999
+    w.close()
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_tensor_core_64_point_lgs_is_refused(precision):
+    """The 64-point tensor-core kernel has no elongation stage: an LGS on it is refused."""
+    cfg = _small_cfg(2, 32, 64, 32, True)
+    cfg.geometries[0].precision = precision
+    with pytest.raises(native.WfsError) as ei:
+        native.Wfs(cfg)
+    assert ei.value.status == native.WFS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
 def test_tensor_core_unsupported_geometry_is_refused(precision):
     """A geometry without a tensor-core kernel (odd subaperture size) is refused at creation."""
     cfg = _small_cfg(9, 7, 16, 8, False)
