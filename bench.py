@@ -109,7 +109,8 @@ def source_sha(names):
 
 KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "proj_math.cuh", "internal.h"],
                   "spot_n32": ["k_sh_n32.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
-                  "spot_tc": ["k_sh_tc.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
+                  "spot_tc": ["k_sh_tc.cu", "spot_tail.cuh", "noise.cuh", "internal.h", "tcgen05.cuh"],
+                  "spot_tc64": ["k_sh_tc64.cu", "noise.cuh", "proj_math.cuh", "internal.h", "tcgen05.cuh"],
                   "noise_cog": ["k_noise_cog.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
                   "project": ["k_project.cu", "proj_math.cuh", "internal.h"],
                   "gemv": ["k_loop.cu", "proj_math.cuh", "internal.h"],
@@ -845,12 +846,41 @@ def batch_leg(args, dev, flush, n_inst=64, steps=200):
         ms = sum(x.elapsed_time(y) for x, y in zip(e0, e1)) / steps
         info = native.wfs_batch_info(b)
         native.wfs_batch_destroy(b)
+        # each kernel class alone (its instances as a batch of their own, one projection and one
+        # spot launch): how much the classes overlap in the graph, i.e. what one persistent launch
+        # over all classes could still gain
+        per_class = []
+        groups = {}
+        for i, c in enumerate(insts):
+            g = c.geometries[0]
+            groups.setdefault((g.precision, g.n_pix_sub, g.n_fft, g.n_det), []).append(i)
+        for key, idx in sorted(groups.items()):
+            bc = native.wfs_batch_create([hs[i].h for i in idx])
+            sp_c, op_c = [sps[i] for i in idx], [ops[i] for i in idx]
+            native.wfs_batch_tune(bc, sp_c, [0.0] * len(idx), op_c, sp)
+            for k in range(3):
+                native.wfs_batch_measure(bc, sp_c, [k * 1e-3] * len(idx), op_c, sp)
+            torch.cuda.synchronize()
+            kc = min(steps, 100)
+            for k in range(kc):
+                flush.fill_(float(k))
+                e0[k].record(stream)
+                native.wfs_batch_measure(bc, sp_c, [(5 + k) * 1e-3] * len(idx), op_c, sp)
+                e1[k].record(stream)
+            torch.cuda.synchronize()
+            per_class.append({"precision": key[0], "n_pix_sub": key[1], "n_fft": key[2], "n_det": key[3],
+                              "instances": len(idx), "spots": sum(hs[i].total for i in idx),
+                              "ms_per_step": sum(x.elapsed_time(y) for x, y in zip(e0[:kc], e1[:kc])) / kc})
+            native.wfs_batch_destroy(bc)
         for w in hs:
             w.close()
         out[name] = {"value": spots / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
                      "spots_per_step": spots, "instances": len(hs), "instances_on_tensor_cores": n_tc,
                      "classes": [{k: c[k] for k in ("kind", "n_pix_sub", "n_fft", "n_det", "n_wfs", "n_subaps", "grid_cap", "cta_warps")
-                                  if k in c} for c in info]}
+                                  if k in c} for c in info],
+                     "classes_alone": per_class,
+                     "sum_of_classes_alone_ms": sum(c["ms_per_step"] for c in per_class),
+                     "largest_class_alone_ms": max(c["ms_per_step"] for c in per_class)}
     out["workload"] = (f"config4: {n_inst} uneven instances (seed 4000) of one WFS each, 2x2/10x10/40x40/80x80 "
                        "subapertures, DFT 16/24/32/64, 1-10 layers, LGS and NGS, noise on; one batch launch set "
                        "per step (CUDA graph), autotuned launch shapes")

@@ -619,7 +619,7 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
             return cuda_fail(h, e, "uplink wait");
         // a generic-kernel group (a few NGS subapertures) projects inside its spot kernel: one
         // launch that starts with the call and owns its SMs only while it runs
-        const bool fused = G.kind == kSpotGeneric || G.per_slice;
+        const bool fused = G.kind == kSpotGeneric || G.per_slice || (is_tc(G.kind) && h->geoms[G.geom].g.n_fft == 64);
         if (!fused && (e = project(G, ss)) != cudaSuccess) return cuda_fail(h, e, "projection launch");
         if ((e = launch_group(G, ss, !fused && G.proj_count > 0, fused ? 1 : 0)) != cudaSuccess)
             return cuda_fail(h, e, "spot launch");
@@ -1901,8 +1901,13 @@ wfs_status wfs_batch_tune(wfs_batch b, const float *const *screens, const double
         if (bc.kind == kSpotN32) {
             for (int w : {4, 8})
                 for (int m : {2, 4, 8, 16}) cand.push_back({152 * m * (8 / w), w});
+        } else if (is_tc(bc.kind) && bc.geom->g.n_fft == 64) {
+            for (int m : {1, 2}) cand.push_back({76 * m, 0});
         } else if (is_tc(bc.kind)) {
-            for (int m : {1, 2}) cand.push_back({152 * m, 0});
+            // tile shape: two warpgroups (8 subapertures) per CTA, at most 2 CTAs per SM, or one
+            // (4 subapertures) with up to 3 CTAs per SM; and the persistent grid size
+            for (int m : {1, 2}) cand.push_back({152 * m, 8});
+            for (int m : {1, 2, 3}) cand.push_back({152 * m, 4});
         } else {
             for (int m : {2, 4, 8, 32}) cand.push_back({152 * m, 0});
         }

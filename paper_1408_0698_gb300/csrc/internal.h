@@ -122,7 +122,7 @@ struct ShArgs {
     // launches (the last CTA to finish resets it), used by one launch at a time; null = a
     // static split.
     int *work;
-    int project;         // generic kernel: 1 = project each subaperture's OPD from the screens
+    int project;         // generic and 64-point tensor-core kernels: 1 = project each subaperture's OPD from the screens
                          // itself (no separate projection launch; written to dyn.opd too) on a
                          // side stream, with the shared-memory reservation that keeps projection
                          // CTAs off its SMs; 2 = the same without the reservation

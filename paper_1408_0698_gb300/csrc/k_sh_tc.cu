@@ -88,7 +88,7 @@ __device__ __forceinline__ void field_rows(const float2 *Fk, const float4 *X4, i
     }
 }
 
-template <int n, int N_, int nd, bool kSlices = false, bool kMmaU = false>
+template <int n, int N_, int nd, bool kSlices = false, bool kMmaU = false, int WG = kWG>
 struct TcLayout {
     static constexpr int N = N_, D2 = 2 * n - 1, no = n | 1;
     // N = 32 with a 16 x 16 detector: the elongation stage as a DFT across the 32 lanes and
@@ -105,7 +105,7 @@ struct TcLayout {
     // subapertures (U = F X as an MMA), then [U_hi | U_lo | U_hi] for the DFT's second MMA,
     // then (after it has completed) [I_hi | I_lo] for the transfer-function MMA
     static constexpr int oA = oA0 + (kMmaU ? 16384 : 0);
-    static constexpr int oTab = oA + 16384 * kWG;  // CUDA-core tables (float2)
+    static constexpr int oTab = oA + 16384 * WG;  // CUDA-core tables (float2)
     static constexpr int tFk = 0;                  // [p][k]  F[k][p] (U = F X on the CUDA cores)
     static constexpr int tFft = tFk + (kMmaU ? 0 : n * N);  // lane-DFT twiddles and phases (tail::fill_fft_table)
     static constexpr int tG = tFft + (kLane ? tail::kFftTable : 0);  // [d][nd] G[d][i]
@@ -135,15 +135,18 @@ struct TcLayout {
     // per warpgroup: 2 mbarriers (0), flag (16), next group (20), the first-stage mbarrier (24);
     // per-slice variant: the slice counts of its 4 warps (32)
     static constexpr int misc = kSlices ? 48 : 32;
-    static constexpr int oMisc = oWarp + 4 * kWG * warp * 8;
-    static constexpr int bytes = oMisc + misc * kWG + 16;
+    static constexpr int oMisc = oWarp + 4 * WG * warp * 8;
+    static constexpr int bytes = oMisc + misc * WG + 16;
 };
 
 }  // namespace
 
-template <int n, int N, int nd, bool kF16, bool kMmaU>
-__global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__ ShArgs a) {
-    using Lay = TcLayout<n, N, nd, false, kMmaU>;
+template <int n, int N, int nd, bool kF16, bool kMmaU, int WG>
+__global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __grid_constant__ ShArgs a) {
+    using Lay = TcLayout<n, N, nd, false, kMmaU, WG>;
+    // warpgroups per CTA (the tile shape the tuner picks): their threads and tensor-memory columns
+    constexpr int kWG = WG, kTcThreads = 128 * WG;
+    constexpr uint32_t kTmemCols = 128 * WG;
     using E = TcElt<kF16>;
     constexpr bool kLane = Lay::kLane;
     constexpr int D2 = Lay::D2, nd2 = nd * nd;
@@ -564,7 +567,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc(const __grid_constant__
 template <int n, int nd, bool kF16>
 __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constant__ ShArgs a) {
     constexpr bool kSlices = true;
-    using Lay = TcLayout<n, 32, nd, kSlices>;
+    using Lay = TcLayout<n, 32, nd, kSlices, false, kWG>;
     using E = TcElt<kF16>;
     constexpr int N = 32, D2 = Lay::D2, nd2 = nd * nd;
     static_assert(6 * n <= 64 && n <= 16, "the split DFT operand must fit one 64-element K atom");
@@ -975,24 +978,26 @@ float bf16_float(uint16_t h) {
     return f;
 }
 
-template <int n, int N, int nd, bool kSlices, bool kF16, bool kMmaU>
+template <int n, int N, int nd, bool kSlices, bool kF16, bool kMmaU, int WG = kWG>
 cudaError_t shape_tc_k(const ShArgs &a, LaunchShape *out) {
-    using Lay = TcLayout<n, N, nd, kSlices, kSlices ? false : kMmaU>;
+    using Lay = TcLayout<n, N, nd, kSlices, kSlices ? false : kMmaU, WG>;
     const void *f;
     if constexpr (kSlices) f = (const void *)k_sh_tc_sl<n, nd, kF16>;
-    else f = (const void *)k_sh_tc<n, N, nd, kF16, kMmaU>;
+    else f = (const void *)k_sh_tc<n, N, nd, kF16, kMmaU, WG>;
     const int smem = Lay::bytes;  // no static shared memory: the dynamic base is 1024-aligned
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int groups = (a.total + 3) / 4;
-    const int cta_groups = (groups + kWG - 1) / kWG;
-    // at most 2 CTAs per SM (shared memory): their tensor memory (2 x 256 columns) always fits
-    const int cap = a.grid_cap > 0 && a.grid_cap < 152 * 2 ? a.grid_cap : 152 * 2;
+    const int cta_groups = (groups + WG - 1) / WG;
+    // resident CTAs per SM: two of two warpgroups or three of one (shared memory); their tensor
+    // memory (4 x 128 or 3 x 128 columns) always fits
+    const int per_sm = WG == 1 ? 3 : 2;
+    const int cap = a.grid_cap > 0 && a.grid_cap < 152 * per_sm ? a.grid_cap : 152 * per_sm;
     int blocks = cta_groups < cap ? cta_groups : cap;
     if (blocks < 1) blocks = 1;
     out->func = f;
     out->grid = dim3(blocks);
-    out->block = dim3(kTcThreads);
+    out->block = dim3(128 * WG);
     out->smem = smem;
     return cudaSuccess;
 }
@@ -1009,6 +1014,9 @@ cudaError_t shape_tc(const ShArgs &a, LaunchShape *out, bool f16) {
     }
     if (a.mma_u)
         return f16 ? shape_tc_k<n, N, nd, false, true, true>(a, out) : shape_tc_k<n, N, nd, false, false, true>(a, out);
+    // ShArgs::cta_warps = 4: one warpgroup per CTA (else two)
+    if (a.cta_warps == 4)
+        return f16 ? shape_tc_k<n, N, nd, false, true, false, 1>(a, out) : shape_tc_k<n, N, nd, false, false, false, 1>(a, out);
     return f16 ? shape_tc_k<n, N, nd, false, true, false>(a, out) : shape_tc_k<n, N, nd, false, false, false>(a, out);
 }
 

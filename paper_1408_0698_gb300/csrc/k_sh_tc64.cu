@@ -16,12 +16,19 @@
 // of the FP32 generic kernel.  One warpgroup per CTA, two subapertures per step; thread t owns
 // DFT row t mod 64 of subaperture t / 64, which is also TMEM lane t.  Every mbarrier wait is
 // bounded; a timeout is recorded in the status word and the CTA frees its tensor memory.
+//
+// With ShArgs::project the kernel projects its subapertures' OPD from the screens itself (the
+// arithmetic of the projection kernel: FP64 layer offsets, bilinear samples summed over the
+// layers in order, the uplink tilt; the OPD also goes to dyn.opd): a few NGS subapertures on a
+// side stream then take their SMs with one launch at the start of a frame instead of queueing a
+// projection behind the large one.
 #include <string.h>
 
 #include <vector>
 
 #include "internal.h"
 #include "noise.cuh"
+#include "proj_math.cuh"
 #include "tcgen05.cuh"
 
 namespace gbwfs {
@@ -41,7 +48,8 @@ struct T64Layout {
     static constexpr int oI = oT + 3 * kAtom;    // the two spots' rows [64][65] floats
     static constexpr int oRed = oI + 2 * kT64N * (kT64N + 1) * 4;  // per-warp partial sums (4 x 4 floats)
     static constexpr int oMisc = oRed + 4 * 4 * 4;                  // 2 mbarriers, flag, TMEM slot
-    static constexpr int bytes = oMisc + 32;
+    static constexpr int oLo = oMisc + 32;                          // layer offsets of the two subapertures
+    static constexpr int bytes = oLo + 2 * kMaxProjLayers * (int)sizeof(LayerOffs) + 16;
 };
 
 }  // namespace
@@ -58,6 +66,8 @@ __global__ void __launch_bounds__(kT64Threads, 1) k_sh_tc64(const __grid_constan
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lay::oMisc);
     int *sflag = reinterpret_cast<int *>(smem + Lay::oMisc + 16);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + Lay::oMisc + 20);
+    float *sref = reinterpret_cast<float *>(smem + Lay::oMisc + 24);  // a self-projected subaperture's piston (x2)
+    LayerOffs *slo = reinterpret_cast<LayerOffs *>(smem + Lay::oLo);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const int b = tid >> 6, k = tid & 63;  // subaperture of the step, DFT row (= TMEM lane tid)
     {
@@ -106,18 +116,76 @@ __global__ void __launch_bounds__(kT64Threads, 1) k_sh_tc64(const __grid_constan
         const InstDyn &D = a.dyn[W.inst];
         const int v = active ? g - W.subap_begin : 0;
         active = active && guard(v >= 0 && v < W.n_valid, a.status);
+        // the subaperture's OPD: from the projection, or projected here (16 pixels per thread)
+        float o[nn / 64];
+        float ref = 0.0f;
+        if (a.project) {
+            const InstDesc &I = a.inst[W.inst];
+            const int L = proj_layers(I, D);
+            if (active)
+                for (int l = k; l < L; l += 64) slo[b * kMaxProjLayers + l] = layer_offsets(I, W, D.t, l);
+            __syncthreads();
+            if (active) {
+                const int S = I.S;
+                const bool pow2 = (S & (S - 1)) == 0;
+                const int id = __ldg(W.subap + v), sy = id / W.n_sub, sx = id - sy * W.n_sub;
+                const float half = 0.5f * (float)(W.n_sub * n - 1);
+                const LayerOffs *lo = slo + b * kMaxProjLayers;
+                float *out = D.opd + W.opd_off + (size_t)v * nn;
+                // layers outside, the thread's 16 pixels inside: every tap of a layer in flight at once
+#pragma unroll
+                for (int m = 0; m < nn / 64; ++m) o[m] = 0.0f;
+                for (int l = 0; l < L; ++l) {
+                    const LayerOffs L0 = lo[l];
+                    const float *scr = layer_screen(I, D, l);
+#pragma unroll
+                    for (int m = 0; m < nn / 64; ++m) {
+                        const int i = k + 64 * m, pp = i >> 5, qq = i & 31;
+                        const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                        int ou, ov, i0, i1, j0, j1;
+                        float fx, gy;
+                        screen_offset(L0.c, L0.cl, L0.fu, xr, ou, fx);
+                        screen_offset(L0.c, L0.cl, L0.fv, yr, ov, gy);
+                        wrap_pair(L0.bu + ou, S, pow2, i0, i1);
+                        wrap_pair(L0.bv + ov, S, pow2, j0, j1);
+                        if (!guard(i0 >= 0 && i1 < S && i1 >= 0 && j0 >= 0 && j1 < S && j1 >= 0 && i0 < S && j0 < S,
+                                   a.status))
+                            continue;
+                        const float *r0 = scr + (size_t)j0 * S, *r1 = scr + (size_t)j1 * S;
+                        const float s00 = __ldg(r0 + i0), s01 = __ldg(r0 + i1);
+                        const float s10 = __ldg(r1 + i0), s11 = __ldg(r1 + i1);
+                        const float top = fmaf(fx, s01 - s00, s00);
+                        const float bot = fmaf(fx, s11 - s10, s10);
+                        o[m] += fmaf(gy, bot - top, top);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < nn / 64; ++m) {
+                    const int i = k + 64 * m, pp = i >> 5, qq = i & 31;
+                    const float xr = (float)(sx * n + qq) - half, yr = (float)(sy * n + pp) - half;
+                    if (W.uplink) o[m] += fmaf(W.uplink->x, xr, W.uplink->y * yr);
+                    out[i] = o[m];
+                }
+                if (k == 0) sref[b] = o[0];
+            }
+            __syncthreads();
+            ref = sref[b];
+        } else if (active) {
+            const float *opd = D.opd + W.opd_off + (size_t)v * nn;
+            ref = __ldg(opd);
+#pragma unroll
+            for (int m = 0; m < nn / 64; ++m) o[m] = __ldg(opd + k + 64 * m);
+        }
         // the field of subaperture b into its rows of the first MMA's B tile: pixel (p, q) ->
         // row 64 b + q: [X_hi | X_hi | X_lo] of (re p, -im p); row 64 b + 32 + q: of (im p, re p)
         if (active) {
-            const float *opd = D.opd + W.opd_off + (size_t)v * nn;
             const uint32_t *mk = W.mask + (size_t)v * a.mask_words;
-            const float ref = __ldg(opd);
-#pragma unroll 4
+#pragma unroll
             for (int m = 0; m < nn / 64; ++m) {
                 const int i = k + 64 * m, p = i >> 5, q = i & 31;
                 const bool lit = (__ldg(mk + (i >> 5)) >> (i & 31)) & 1u;
                 float sn, cs;
-                field_phasor(W.k_phase * (__ldg(opd + i) - ref), sn, cs);
+                field_phasor(W.k_phase * (o[m] - ref), sn, cs);
                 float rh, rl, ih, il;
                 E::split(lit ? cs : 0.0f, rh, rl);
                 E::split(lit ? sn : 0.0f, ih, il);

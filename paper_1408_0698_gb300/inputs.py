@@ -180,11 +180,13 @@ def config2(precision: int = PREC_FP32) -> Config:
     return Config("config2_mcao_8m", tel, geom, stars, lay, seed=2000, dt_s=1e-3, steps=100)
 
 
-def config3(precision: int = PREC_BF16X3, ngs_precision: int = None) -> Config:
+def config3(precision: int = PREC_BF16X3, ngs_precision: int = PREC_FP32) -> Config:
     """ELT: 800x800 px pupil at 4.875e-2 m, obstruction 0.28; 6 LGS (80x80, n=10, N=32,
     16x16 det px) on a 45" ring; 3 H-band NGS 2x2 (n=32, N=64, 32x32 det px) on a 60" ring;
-    10 layers 0-20 km.  `precision` is the DFT arithmetic of both geometries unless
-    `ngs_precision` sets the NGS geometry's."""
+    10 layers 0-20 km.  `precision` is the LGS geometry's DFT arithmetic, `ngs_precision` the
+    NGS geometry's (None: the same as the LGS).  The 12 NGS spots default to FP32: on their side
+    stream the FP32 kernel's 512-thread teams finish them sooner than the 64-point tensor-core
+    kernel's single warpgroup per two subapertures."""
     dx = 4.875e-2
     tel = Telescope(800 * dx, 0.28)
     geom = [Geometry(80, 10, 32, 16, 0.5, precision),

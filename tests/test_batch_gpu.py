@@ -136,3 +136,37 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(native.WfsError):
         native.wfs_batch_create([w.h, w.h])
     w.close()
+
+
+def test_tensor_core_tile_shapes_give_the_same_results(tmp_path, monkeypatch):
+    """Both tile shapes of the tensor-core kernels (two warpgroups per CTA, or one, which the tuner
+    chooses between) measure every class bit for bit as the handles alone: the shape is forced
+    through the tuning cache."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("GBWFS_TUNE_CACHE", str(path))
+    insts = _instances(16, 4300, inputs.PREC_BF16X3)
+    hs, scr, outs = _setup(insts, True)
+    ts = [0.004 + 1e-4 * i for i in range(len(hs))]
+    b = native.wfs_batch_create([w.h for w in hs])
+    native.wfs_batch_tune(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+    native.wfs_batch_destroy(b)
+    lines = path.read_text().split("\n")
+    for shape in (4, 8):
+        forced = []
+        for ln in lines:
+            if not ln.strip():
+                continue
+            k, cap, w = ln.split()
+            forced.append(f"{k} {cap} {shape if k.startswith('kind2_') or k.startswith('kind3_') else w}")
+        path.write_text("\n".join(forced) + "\n")
+        b = native.wfs_batch_create([w.h for w in hs])
+        info = native.wfs_batch_info(b)
+        assert any(c["kind"] in (2, 3) and c["n_fft"] <= 32 and c["cta_warps"] == shape for c in info)
+        native.wfs_batch_measure(b, [s.data_ptr() for s in scr], ts, [o.data_ptr() for o in outs], 0)
+        torch.cuda.synchronize()
+        ref = _alone(hs, scr, ts)
+        for i, (o, r) in enumerate(zip(outs, ref)):
+            assert np.array_equal(o.cpu().numpy(), r), (shape, i)
+        native.wfs_batch_destroy(b)
+    for w in hs:
+        w.close()

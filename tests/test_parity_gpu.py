@@ -286,11 +286,13 @@ TC_PRECISIONS = [inputs.PREC_BF16X3, inputs.PREC_FP16S]
 
 
 @pytest.mark.parametrize("precision", TC_PRECISIONS)
-def test_config3_bf16x3_sampled_parity_full_launch(precision):
+@pytest.mark.parametrize("ngs_on_tc", [False, True])
+def test_config3_bf16x3_sampled_parity_full_launch(precision, ngs_on_tc):
     """The ELT frame with the LGS DFT on the tensor cores (BF16 x3, or FP16 x3 with power-of-two
-    scaling; FP32 accumulation), full launch, sampled subapertures against the FP64 oracle at
-    the same bars as the FP32 path."""
-    cfg = inputs.config3(precision)
+    scaling; FP32 accumulation), and the NGS on the FP32 kernel or on the 64-point tensor-core
+    kernel (self-projecting on its side stream), full launch, sampled subapertures against the
+    FP64 oracle at the same bars as the FP32 path."""
+    cfg = inputs.config3(precision, ngs_precision=precision if ngs_on_tc else inputs.PREC_FP32)
     scr = inputs.make_screens(cfg.layers, cfg.seed)
     t = 0.071
     gpu, w = run_library(cfg, scr, t)
