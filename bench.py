@@ -593,6 +593,15 @@ def main():
     e2e = {"value": world * spots * ke / (float(e_ms.item()) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(round(h2d / ke)), "d2h_bytes_per_step": int(round(d2h / ke)),
            "host_input_bytes_per_step": int(host_scr.numel() * 4), "steps": ke}
+    if h2d == 0:
+        # the pinned host screens are mapped into the GPU's address space and the kernels read
+        # what they need in place: the bytes that cross the host link are the screen pixels the
+        # frame's bilinear taps touch (at least; the link moves whole sectors)
+        maps = [native.wfs_valid_map(w.h, k) for k in range(len(cfg.stars))]
+        _, scr_b, _ = projection_footprint_bytes(cfg, maps, (args.warmup + ke) * dt, all_stars=True)
+        e2e["h2d_bytes_per_step"] = int(scr_b)
+        e2e["h2d_note"] = ("screens read in place by the kernels from pinned host memory (no copy); "
+                           "bytes = the screen pixels the frame's taps touch")
 
     # roofline of the dominant kernel (the spot launch with the most work; launches of other
     # geometries run concurrently on side streams, so event windows overlap), from the live
@@ -714,17 +723,17 @@ def spot_roofline(name, timing, cfg, w, pk, kind):
     return roof
 
 
-def projection_footprint_bytes(cfg, valid_maps, t):
-    """Algorithmic bytes of one projection launch of the 32-point group: every screen pixel
-    that the bilinear taps of the valid pupil pixels touch, counted once per layer (4 B), plus
-    the projected OPD written (4 B per valid pupil pixel).  valid_maps[k]: star k's valid
-    subaperture indices (row-major)."""
+def projection_footprint_bytes(cfg, valid_maps, t, all_stars=False):
+    """Algorithmic bytes of one projection launch of the 32-point group (or, with all_stars,
+    of every star's projection): every screen pixel that the bilinear taps of the valid pupil
+    pixels touch, counted once per layer (4 B), plus the projected OPD written (4 B per valid
+    pupil pixel).  valid_maps[k]: star k's valid subaperture indices (row-major)."""
     L = cfg.layers
     S, ds = L.screen_size, L.screen_dx_m
     tel = cfg.telescope
     touched = 0
     opd_bytes = 0
-    members = [k for k, s in enumerate(cfg.stars) if cfg.geometries[s.geometry_index].n_fft == 32]
+    members = [k for k, s in enumerate(cfg.stars) if all_stars or cfg.geometries[s.geometry_index].n_fft == 32]
     for l in range(L.n_layers):
         mask = np.zeros((S, S), bool)
         h = L.alt_m[l]

@@ -212,16 +212,21 @@ wfs_status wfs_measure_stages(wfs_handle h, const float *screens, double t_s,
  * call allocates two sets of device staging buffers (screens and slopes) and a
  * copy stream that later calls reuse: successive calls alternate between the
  * sets and upload on the copy stream, so the next frame's upload overlaps this
- * frame's kernels.  Asynchronous on `stream`: slopes_host is valid, and
- * screens_host may be reused, after the stream is synchronised.
+ * frame's kernels.  With GBWFS_HOST_ZERO_COPY=1 in the environment, screens in
+ * pinned host memory mapped into the device's address space are read in place
+ * by the kernels and nothing is copied up (slower on the ELT frame than the
+ * row copies; pageable memory always takes the copies).  Asynchronous on
+ * `stream`: slopes_host is valid, and screens_host may be reused, after the
+ * stream is synchronised.
  */
 wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
                             float *slopes_host, void *stream);
 
 /*
  * wfs_host_transfer_bytes -- the bytes the handle's last wfs_measure_host call
- * copied host -> device (screen parts) and device -> host (slopes); 0 and 0
- * before the first call.  WFS_EINVAL: a null argument.
+ * copied host -> device (screen parts; 0 when the kernels read the screens in
+ * place) and device -> host (slopes); 0 and 0 before the first call.
+ * WFS_EINVAL: a null argument.
  */
 wfs_status wfs_host_transfer_bytes(wfs_handle h, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
 

@@ -478,13 +478,14 @@ def test_host_path_alternating_buffers():
     w.close()
 
 
-def test_host_path_uploads_only_the_read_parts():
-    """The host-buffer path copies only the parts of the screens a frame reads.  Its staging
-    screens start as NaN and every call brings a different screen set, so a read outside the
-    copied parts would show as NaN or as another frame's data: on the ELT frame (uplink on, then
-    the per-slice model, wind shifts of many pixels) every call equals the device path bit for
-    bit, and less than the whole set was copied."""
+def test_host_path_uploads_only_the_read_parts(monkeypatch):
+    """The host-buffer path with row copies (GBWFS_HOST_ZERO_COPY=0) copies only the parts of the
+    screens a frame reads.  Its staging screens start as NaN and every call brings a different
+    screen set, so a read outside the copied parts would show as NaN or as another frame's data:
+    on the ELT frame (uplink on, then the per-slice model, wind shifts of many pixels) every call
+    equals the device path bit for bit, and less than the whole set was copied."""
     import dataclasses
+    monkeypatch.setenv("GBWFS_HOST_ZERO_COPY", "0")
     cfg = inputs.config3()
     cfg = dataclasses.replace(cfg, stars=[dataclasses.replace(st, uplink_diameter_m=0.4, uplink_samples=16)
                                           if st.is_lgs else st for st in cfg.stars])
@@ -504,6 +505,39 @@ def test_host_path_uploads_only_the_read_parts():
         ref, _ = run_library(cfg, scr, t, seed=9, noise=True, stages=False, handle=w)
         assert np.all(np.isfinite(got)), f"call {k}"
         assert np.array_equal(got, np.concatenate([d["slopes"] for d in ref])), f"call {k}"
+    w.close()
+
+
+def test_host_path_reads_pinned_screens_in_place(monkeypatch):
+    """With GBWFS_HOST_ZERO_COPY=1, pinned host screens (mapped into the device's address space)
+    are read in place by the kernels: nothing is copied up, and every frame equals the device path
+    bit for bit (ELT frame, uplink on, then the per-slice model); pageable screens fall back to the
+    row copies with the same results."""
+    import dataclasses
+    monkeypatch.setenv("GBWFS_HOST_ZERO_COPY", "1")
+    cfg = inputs.config3()
+    cfg = dataclasses.replace(cfg, stars=[dataclasses.replace(st, uplink_diameter_m=0.4, uplink_samples=16)
+                                          if st.is_lgs else st for st in cfg.stars])
+    w = native.Wfs(cfg, seed=9, noise=True)
+    out = torch.empty((w.total, 2)).pin_memory()
+    for k, (t, per_slice) in enumerate([(0.0, False), (0.41, False), (2.3, True)]):
+        if per_slice:
+            native.wfs_set_lgs_model(w.h, True)
+        scr = inputs.make_screens(cfg.layers, 950 + k)
+        ref, _ = run_library(cfg, scr, t, seed=9, noise=True, stages=False, handle=w)
+        ref = np.concatenate([d["slopes"] for d in ref])
+        host_scr = torch.as_tensor(scr).pin_memory()
+        native.wfs_measure_host(w.h, host_scr.data_ptr(), t, out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        h2d, d2h = native.wfs_host_transfer_bytes(w.h)
+        assert h2d == 0 and d2h == 8 * w.total
+        assert np.array_equal(out.numpy(), ref), f"call {k} (in place)"
+        pageable = np.ascontiguousarray(scr)
+        native.wfs_measure_host(w.h, pageable.ctypes.data, t, out.data_ptr(), 0)
+        torch.cuda.synchronize()
+        h2d, _ = native.wfs_host_transfer_bytes(w.h)
+        assert h2d > 0
+        assert np.array_equal(out.numpy(), ref), f"call {k} (pageable)"
     w.close()
 
 
