@@ -205,10 +205,13 @@ wfs_status wfs_measure_stages(wfs_handle h, const float *screens, double t_s,
  * wfs_measure_host -- the same frame with HOST buffers: copies screens_host
  * (host, same layout as `screens`; pinned memory for asynchronous copies) to
  * the device, measures, and copies the slopes back to slopes_host.  Only the
- * rows of the screens the frame reads are copied: per layer, the rows covered
+ * parts of the screens the frame reads are copied: per layer, the areas covered
  * by the guide stars' projected pupils (every cone scale of the LGS model in
- * use) and LGS uplink beams at time t_s, plus a margin of a few rows (the
- * whole set when those cover nine tenths of it).  The first
+ * use) and LGS uplink beams at time t_s, plus a margin of a few pixels.  Pinned
+ * memory mapped into the device's address space (pinned allocations under
+ * unified addressing) is gathered rectangle by rectangle by a copy kernel
+ * (GBWFS_HOST_RECTS=0 in the environment turns this off); otherwise whole
+ * rows are copied (the whole set when those cover nine tenths of it).  The first
  * call allocates two sets of device staging buffers (screens and slopes) and a
  * copy stream that later calls reuse: successive calls alternate between the
  * sets and upload on the copy stream, so the next frame's upload overlaps this
@@ -224,8 +227,8 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
 
 /*
  * wfs_host_transfer_bytes -- the bytes the handle's last wfs_measure_host call
- * copied host -> device (screen parts; 0 when the kernels read the screens in
- * place) and device -> host (slopes); 0 and 0 before the first call.
+ * copied host -> device (screen rows or rectangles; 0 when the kernels read the
+ * screens in place) and device -> host (slopes); 0 and 0 before the first call.
  * WFS_EINVAL: a null argument.
  */
 wfs_status wfs_host_transfer_bytes(wfs_handle h, uint64_t *h2d_bytes, uint64_t *d2h_bytes);

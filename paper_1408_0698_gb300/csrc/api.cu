@@ -137,6 +137,10 @@ struct wfs_ctx {
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
     unsigned long long host_calls = 0;
     unsigned long long host_h2d = 0, host_d2h = 0;  // bytes the last host-buffer call copied
+    // rectangle copies of mapped pinned host screens: task tables (pinned host, device) per set
+    HostRowTask *h_tasks[2] = {nullptr, nullptr};
+    HostRowTask *d_tasks[2] = {nullptr, nullptr};
+    int task_cap = 0;
     cudaStream_t last_stream = nullptr;
     std::string err;
     // side streams for the spot launches of the second and later geometries
@@ -400,6 +404,8 @@ void release(wfs_ctx *h) {
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->d_screens_stage[i]);
         cudaFree(h->d_slopes_stage[i]);
+        if (h->h_tasks[i]) cudaFreeHost(h->h_tasks[i]);
+        cudaFree(h->d_tasks[i]);
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     }
@@ -1266,6 +1272,112 @@ void screen_rows(const wfs_ctx *h, double t, std::vector<ScreenRows> &out) {
     }
 }
 
+// The rectangles of the turbulent screens a frame at time t reads, as row bands for the gather
+// kernel: per layer, each guide star's projected pupil square at every cone scale its model uses
+// and its LGS uplink beam's disc (the coordinates of screen_rows), widened by the bilinear tap and
+// four pixels of margin; the rows cut at the rectangles' row boundaries, and each band copies one
+// column interval, the union of the rectangles covering it, split at the periodic edges.  Columns
+// in 16-byte units.  Returns false where a rectangle spans the whole screen (the caller then
+// copies rows).
+bool screen_rects(const wfs_ctx *h, double t, std::vector<HostRowTask> &out) {
+    const int S = h->S;
+    out.clear();
+    if (S % 4) return false;
+    struct Rect {
+        long long r0, r1, c0, c1;  // inclusive, unwrapped
+    };
+    std::vector<Rect> rects;
+    std::vector<long long> cuts;
+    for (int l = 0; l < h->n_layers; ++l) {
+        rects.clear();
+        const double hl = h->alt[l];
+        const double sx = h->x0[l] + h->vx[l] * t, sy = h->y0[l] + h->vy[l] * t;
+        auto add = [&](double cu, double cv, double hu, double hv) {
+            rects.push_back({(long long)std::floor(cv - hv) - 4, (long long)std::floor(cv + hv) + 5,
+                             (long long)std::floor(cu - hu) - 4, (long long)std::floor(cu + hu) + 5});
+        };
+        for (const GsDev &G : h->gs) {
+            const wfs_guide_star &g = G.gs;
+            const wfs_geometry &geo = h->geoms[g.geometry_index].g;
+            const int Np = geo.n_sub * geo.n_pix_sub;
+            const double pdx = (h->tel.diameter_m / Np) / h->ds;
+            const double ou = 0.5 * S + (g.theta_x_rad * hl - sx) / h->ds;
+            const double ov = 0.5 * S + (g.theta_y_rad * hl - sy) / h->ds;
+            auto pupil = [&](double c) {
+                const double half = std::fabs(c) * pdx * 0.5 * (Np - 1);
+                add(ou, ov, half, half);
+            };
+            if (!g.is_lgs) {
+                pupil(1.0);
+                continue;
+            }
+            pupil(1.0 - hl / g.range_m);
+            if (h->per_slice)
+                for (double hs : G.na_alt) pupil(1.0 - hl / hs);
+            if (G.up_diam > 0.0 && hl < g.range_m) {
+                const double cx = g.launch_x_m * (1.0 - hl / g.range_m) + g.theta_x_rad * hl;
+                const double cy = g.launch_y_m * (1.0 - hl / g.range_m) + g.theta_y_rad * hl;
+                const double r = 0.5 * G.up_diam / h->ds;
+                add(0.5 * S + (cx - sx) / h->ds, 0.5 * S + (cy - sy) / h->ds, r, r);
+            }
+        }
+        // rows wrapped into [0, S): a rectangle crossing the edge splits in two
+        std::vector<Rect> w;
+        for (const Rect &r : rects) {
+            if (r.r1 - r.r0 + 1 >= S || r.c1 - r.c0 + 1 >= S) return false;
+            const long long sh = ((r.r0 % S) + S) % S - r.r0;
+            const Rect q{r.r0 + sh, r.r1 + sh, r.c0, r.c1};
+            if (q.r1 < S) {
+                w.push_back(q);
+            } else {
+                w.push_back({q.r0, S - 1, q.c0, q.c1});
+                w.push_back({0, q.r1 - S, q.c0, q.c1});
+            }
+        }
+        cuts.clear();
+        for (const Rect &r : w) {
+            cuts.push_back(r.r0);
+            cuts.push_back(r.r1 + 1);
+        }
+        std::sort(cuts.begin(), cuts.end());
+        cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+        for (size_t k = 0; k + 1 < cuts.size(); ++k) {
+            const long long a = cuts[k], b = cuts[k + 1];  // rows [a, b)
+            long long c0 = 0, c1 = -1;
+            for (const Rect &r : w)
+                if (r.r0 <= a && r.r1 >= b - 1) {
+                    if (c1 < c0) {
+                        c0 = r.c0;
+                        c1 = r.c1;
+                    } else {
+                        c0 = std::min(c0, r.c0);
+                        c1 = std::max(c1, r.c1);
+                    }
+                }
+            if (c1 < c0) continue;
+            if (c1 - c0 + 1 >= S) {
+                c0 = 0;
+                c1 = S - 1;
+            }
+            // columns wrapped into [0, S), in 16-byte units
+            const long long sh = ((c0 % S) + S) % S - c0;
+            const long long u0 = c0 + sh, u1 = c1 + sh;
+            auto emit = [&](long long x0, long long x1) {
+                const int q0 = (int)(x0 / 4), q1 = (int)(x1 / 4);
+                const int begin = out.empty() ? 0 : out.back().row_begin + out.back().rows;
+                out.push_back({(long long)l * S + a, (int)(b - a), q0, q1 - q0 + 1, begin});
+            };
+            if (u1 < S) {
+                emit(u0, u1);
+            } else {
+                emit(u0, S - 1);
+                emit(0, u1 - S);
+            }
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
 wfs_status wfs_host_transfer_bytes(wfs_handle h, uint64_t *h2d_bytes, uint64_t *d2h_bytes) {
@@ -1328,6 +1440,65 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
             return WFS_OK;
         }
         cudaGetLastError();  // a failed attribute query of a pageable pointer leaves no error behind
+    }
+    // Screens in pinned host memory mapped into the device's address space: a gather kernel on
+    // the copy stream copies the rectangles the frame reads (GBWFS_HOST_RECTS=0 turns this off;
+    // pageable memory takes the row copies below).
+    {
+        const char *hr = getenv("GBWFS_HOST_RECTS");
+        cudaPointerAttributes pa;
+        std::vector<HostRowTask> tasks;
+        if (!(hr && hr[0] == '0') && cudaPointerGetAttributes(&pa, screens_host) == cudaSuccess &&
+            pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr &&
+            (reinterpret_cast<uintptr_t>(pa.devicePointer) & 15) == 0 && screen_rects(h, t_s, tasks) &&
+            !tasks.empty()) {
+            if ((int)tasks.size() > h->task_cap) {
+                const int cap = (int)tasks.size() * 2;
+                for (int k = 0; k < 2; ++k) {
+                    // the tables of both sets are free: their copies completed with the frames
+                    // that used them
+                    if (h->host_calls > 0 && (e = cudaEventSynchronize(h->ev_copied[k])) != cudaSuccess)
+                        return cuda_fail(h, e, "host-path task table");
+                    if (h->h_tasks[k]) cudaFreeHost(h->h_tasks[k]);
+                    cudaFree(h->d_tasks[k]);
+                    h->h_tasks[k] = nullptr;
+                    h->d_tasks[k] = nullptr;
+                    if ((e = cudaMallocHost(&h->h_tasks[k], cap * sizeof(HostRowTask))) != cudaSuccess ||
+                        (e = cudaMalloc(&h->d_tasks[k], cap * sizeof(HostRowTask))) != cudaSuccess)
+                        return cuda_fail(h, e, "host-path task table");
+                }
+                h->task_cap = cap;
+            }
+            // this set's host table was last read by the copy two calls ago
+            if (h->host_calls >= 2 && (e = cudaEventSynchronize(h->ev_copied[i])) != cudaSuccess)
+                return cuda_fail(h, e, "host-path task table");
+            long long rows = 0, f4 = 0;
+            for (const HostRowTask &k : tasks) {
+                rows += k.rows;
+                f4 += (long long)k.rows * k.c4_count;
+            }
+            memcpy(h->h_tasks[i], tasks.data(), tasks.size() * sizeof(HostRowTask));
+            if ((e = cudaMemcpyAsync(h->d_tasks[i], h->h_tasks[i], tasks.size() * sizeof(HostRowTask),
+                                     cudaMemcpyHostToDevice, h->copy_stream)) != cudaSuccess ||
+                (e = launch_host_gather(static_cast<const float *>(pa.devicePointer), h->d_screens_stage[i],
+                                        h->S, h->d_tasks[i], (int)tasks.size(), (int)rows, (long long)nscr,
+                                        h->copy_stream)) !=
+                    cudaSuccess ||
+                (e = cudaEventRecord(h->ev_copied[i], h->copy_stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(s, h->ev_copied[i], 0)) != cudaSuccess)
+                return cuda_fail(h, e, "screen gather");
+            wfs_status st = measure_impl(h, h->d_screens_stage[i], t_s, h->d_slopes_stage[i], nullptr, s);
+            if (st != WFS_OK) return st;
+            if ((e = cudaMemcpyAsync(slopes_host, h->d_slopes_stage[i], nsl * sizeof(float), cudaMemcpyDeviceToHost,
+                                     s)) != cudaSuccess ||
+                (e = cudaEventRecord(h->ev_done[i], s)) != cudaSuccess)
+                return cuda_fail(h, e, "slope download");
+            ++h->host_calls;
+            h->host_h2d = (unsigned long long)f4 * 16;
+            h->host_d2h = nsl * sizeof(float);
+            return WFS_OK;
+        }
+        cudaGetLastError();
     }
     // the rows of the screens this frame reads; the whole set when they cover most of it
     std::vector<ScreenRows> runs;

@@ -299,6 +299,19 @@ cudaError_t launch_push_pull_rows(const float *s, int n_modes, int n_slopes, flo
                                   cudaStream_t st);
 // Sets the calling thread's message returned by wfs_last_error(NULL).
 void set_thread_error(const char *msg);
+// One band of screen rows the host-buffer path copies: rows [row, row + rows) of the [L * S]
+// rows of the screens (one layer, no periodic wrap), 16-byte columns [c4_first, c4_first + c4_count).
+struct HostRowTask {
+    long long row;
+    int rows;
+    int c4_first;
+    int c4_count;
+    int row_begin;  // the band's first row in the flattened list of all bands' rows
+};
+// Copies the bands from mapped host screens (src, device-accessible) into the device screens dst.
+cudaError_t launch_host_gather(const float *src, float *dst, int S, const HostRowTask *tasks, int n_tasks,
+                               int total_rows, long long n_floats, cudaStream_t s);
+
 // The argument checks of wfs_create (telescope, guide stars, geometries, layers); on failure
 // the thread's error message says what is wrong.
 wfs_status validate_description(const wfs_telescope *tel, int n_gs, const wfs_guide_star *gs, int n_geom,

@@ -479,11 +479,13 @@ def test_host_path_alternating_buffers():
 
 
 def test_host_path_uploads_only_the_read_parts(monkeypatch):
-    """The host-buffer path with row copies (GBWFS_HOST_ZERO_COPY=0) copies only the parts of the
-    screens a frame reads.  Its staging screens start as NaN and every call brings a different
-    screen set, so a read outside the copied parts would show as NaN or as another frame's data:
-    on the ELT frame (uplink on, then the per-slice model, wind shifts of many pixels) every call
-    equals the device path bit for bit, and less than the whole set was copied."""
+    """The host-buffer path copies only the parts of the screens a frame reads: rectangles through
+    the gather kernel (pinned mapped screens, the default) or whole rows (GBWFS_HOST_RECTS=0).
+    Its staging screens start as NaN and every frame brings a different screen set, so a read
+    outside the copied parts would show as NaN or as another frame's data: on the ELT frame
+    (uplink on, then the per-slice model, wind shifts of many pixels) every call equals the device
+    path bit for bit in both forms, less than the whole set was copied, and the rectangles move
+    fewer bytes than the rows.  The two forms alternate, so each keeps to one staging set."""
     import dataclasses
     monkeypatch.setenv("GBWFS_HOST_ZERO_COPY", "0")
     cfg = inputs.config3()
@@ -497,14 +499,21 @@ def test_host_path_uploads_only_the_read_parts(monkeypatch):
             native.wfs_set_lgs_model(w.h, True)
         scr = inputs.make_screens(cfg.layers, 900 + k)
         host_scr = torch.as_tensor(scr).pin_memory()
-        native.wfs_measure_host(w.h, host_scr.data_ptr(), t, out.data_ptr(), 0)
-        torch.cuda.synchronize()
-        h2d, d2h = native.wfs_host_transfer_bytes(w.h)
-        assert 0 < h2d < 0.9 * full and d2h == 8 * w.total
-        got = out.numpy().copy()
         ref, _ = run_library(cfg, scr, t, seed=9, noise=True, stages=False, handle=w)
-        assert np.all(np.isfinite(got)), f"call {k}"
-        assert np.array_equal(got, np.concatenate([d["slopes"] for d in ref])), f"call {k}"
+        ref = np.concatenate([d["slopes"] for d in ref])
+        moved = {}
+        for rects in ("1", "0"):
+            monkeypatch.setenv("GBWFS_HOST_RECTS", rects)
+            out.fill_(float("nan"))
+            native.wfs_measure_host(w.h, host_scr.data_ptr(), t, out.data_ptr(), 0)
+            torch.cuda.synchronize()
+            h2d, d2h = native.wfs_host_transfer_bytes(w.h)
+            assert 0 < h2d < 0.9 * full and d2h == 8 * w.total
+            moved[rects] = h2d
+            got = out.numpy().copy()
+            assert np.all(np.isfinite(got)), f"call {k}, rectangles {rects}"
+            assert np.array_equal(got, ref), f"call {k}, rectangles {rects}"
+        assert moved["1"] < moved["0"], f"call {k}: {moved}"
     w.close()
 
 
