@@ -115,6 +115,8 @@ struct wfs_ctx {
     WfsDesc *d_wfs = nullptr;
     std::vector<SpotGroup> groups;
     int proj_blocks = 0, proj_box = 0;
+    int proj_stage = 0;                 // bulk-copy projection box floats (-1: that form is off)
+    bool screens_host_mapped = false;   // the screens of the current call are mapped host memory
     wfs_telescope tel{};
     std::vector<GeomDev> geoms;
     std::vector<GsDev> gs;
@@ -227,6 +229,8 @@ struct wfs_batch_ctx {
     std::vector<WfsDesc> wfs_host;
     std::vector<BatchClass> classes;
     int proj_blocks = 0, proj_box = 0;
+    int proj_stage = 0;                 // bulk-copy projection box floats (-1: that form is off)
+    int graph_stage = 0;                // the projection form the graph was built with
     ProjArgs *pa = nullptr;          // parameter blocks the graph nodes point to
     std::vector<ShArgs *> sa;
     cudaGraph_t graph = nullptr;
@@ -261,6 +265,23 @@ wfs_status cuda_fail(wfs_handle h, cudaError_t e, const char *what) {
 }
 
 bool is_finite(double x) { return std::isfinite(x); }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// The bulk-copy projection's box floats for WFS d on screens of side S: 0 for a WFS without
+// tiles, -1 where its boxes cannot move by bulk copies (rows not a whole number of 16-byte units,
+// or a box wider than the screen).
+int bulk_stage_floats(const WfsDesc &d, int S) {
+    if (!d.tiled) return 0;
+    if (S % 4 || d.seg_cols + 8 > S || d.n + 3 > S) return -1;
+    return project_stage_floats(d);
+}
+
+// Folds one WFS's value into a launch's: the largest box, or -1 once any WFS cannot use the form.
+void merge_stage(int &acc, int v) {
+    if (acc < 0 || v < 0) acc = -1;
+    else if (v > acc) acc = v;
+}
 
 constexpr size_t kMaxTimedLaunches = 65536;
 
@@ -543,6 +564,11 @@ wfs_status measure_impl(wfs_handle h, const float *screens, double t, float *slo
     pa.inst = h->d_inst;
     pa.n_inst = 1;
     pa.box_cap = h->proj_box;
+    // the bulk-copy form reads 16-byte rows of device memory
+    pa.stage_cap = (h->proj_stage > 0 && !h->screens_host_mapped && aligned16(screens) &&
+                    (n_dm == 0 || aligned16(dm_layers)))
+                       ? h->proj_stage
+                       : 0;
     pa.max_layers = h->inst_host.n_layers + n_dm;
     pa.status = h->d_status;
     pa.dyn[0] = dyn;
@@ -1121,6 +1147,7 @@ wfs_status wfs_create(const wfs_telescope *tel, int n_gs, const wfs_guide_star *
                 d.proj_block_begin = blocks;
                 blocks += project_blocks(d);
                 if (project_box_floats(d) > h->proj_box) h->proj_box = project_box_floats(d);
+                merge_stage(h->proj_stage, bulk_stage_floats(d, h->S));
                 d.subap_begin = G.total;
                 G.total += s.n_valid;
                 h->wfs_host.push_back(d);
@@ -1427,8 +1454,10 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
             pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr) {
             if (h->host_calls >= 2 && (e = cudaStreamWaitEvent(s, h->ev_done[i], 0)) != cudaSuccess)
                 return cuda_fail(h, e, "host-path wait");
+            h->screens_host_mapped = true;
             wfs_status st = measure_impl(h, static_cast<const float *>(pa.devicePointer), t_s, h->d_slopes_stage[i],
                                          nullptr, s);
+            h->screens_host_mapped = false;
             if (st != WFS_OK) return st;
             if ((e = cudaMemcpyAsync(slopes_host, h->d_slopes_stage[i], nsl * sizeof(float), cudaMemcpyDeviceToHost,
                                      s)) != cudaSuccess ||
@@ -1691,6 +1720,9 @@ wfs_status batch_fill(wfs_batch b, const float *const *screens, const double *t,
         d.st_E = b->hs[i]->d_E;
         b->hs[i]->last_stream = nullptr;
     }
+    bool aligned = true;
+    for (int i = 0; i < n; ++i) aligned = aligned && aligned16(screens[i]);
+    b->pa->stage_cap = (b->proj_stage > 0 && aligned) ? b->proj_stage : 0;
     for (size_t c = 0; c < b->classes.size(); ++c) {
         ShArgs &a = *b->sa[c];
         memcpy(a.dyn, b->pa->dyn, sizeof(InstDyn) * n);
@@ -1703,6 +1735,7 @@ wfs_status batch_fill(wfs_batch b, const float *const *screens, const double *t,
 cudaError_t batch_build_graph(wfs_batch b) {
     cudaError_t e;
     if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess) return e;
+    b->graph_stage = b->pa->stage_cap;
     LaunchShape ps;
     project_launch_shape(*b->pa, b->proj_blocks, &ps);
     void *pargs[] = {(void *)b->pa};
@@ -1893,6 +1926,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
             d.proj_block_begin = blocks;
             blocks += project_blocks(d);
             if (project_box_floats(d) > b->proj_box) b->proj_box = project_box_floats(d);
+            merge_stage(b->proj_stage, bulk_stage_floats(d, hs[d.inst]->S));
             b->wfs_host.push_back(d);
             ++bc.count;
         }
@@ -1922,6 +1956,7 @@ wfs_status wfs_batch_create(int n, const wfs_handle *hs, wfs_batch *out) {
     b->pa->n_wfs = (int)b->wfs_host.size();
     b->pa->n_inst = n;
     b->pa->box_cap = b->proj_box;
+    b->pa->stage_cap = b->proj_stage > 0 ? b->proj_stage : 0;
     b->pa->n_blocks = b->proj_blocks;
     for (int i = 0; i < n; ++i) b->pa->max_layers = std::max(b->pa->max_layers, hs[i]->inst_host.n_layers);
     b->pa->work = b->d_work + 2 * b->classes.size() * (1 + kBatchSlots);
@@ -1961,6 +1996,8 @@ wfs_status wfs_batch_measure(wfs_batch b, const float *const *screens, const dou
         if ((e = batch_launch_direct(b, s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch launch");
         return WFS_OK;
     }
+    // the projection node's kernel follows the screens' alignment: a change rebuilds the graph
+    if (b->exec && b->graph_stage != b->pa->stage_cap) batch_drop_graph(b);
     if (!b->exec) {
         if ((e = batch_build_graph(b)) != cudaSuccess) {
             batch_drop_graph(b);
@@ -2020,7 +2057,9 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
             d.noise = b->hs[i]->noise;
             d.st_E = b->hs[i]->d_E;
         }
-    int count = 0, blocks = 0, box = 0;
+    int count = 0, blocks = 0, box = 0, stage = 0;
+    bool aligned = true;
+    for (int j = 0; j < n_active; ++j) aligned = aligned && aligned16(screens[j]);
     std::vector<int> cls_first(b->classes.size()), cls_count(b->classes.size()), cls_total(b->classes.size());
     for (size_t c = 0; c < b->classes.size(); ++c) {
         const BatchClass &bc = b->classes[c];
@@ -2035,6 +2074,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
             d.proj_block_begin = blocks;
             blocks += project_blocks(d);
             if (project_box_floats(d) > box) box = project_box_floats(d);
+            merge_stage(stage, bulk_stage_floats(d, b->hs[src.inst]->S));
             sl.h[count++] = d;
         }
         cls_count[c] = count - cls_first[c];
@@ -2052,6 +2092,7 @@ wfs_status wfs_batch_measure_subset(wfs_batch b, int slot, int n_active, const i
     pa.work = b->d_work + 2 * b->classes.size() * (1 + kBatchSlots) + 2 * (1 + (size_t)slot);
     pa.n_inst = n;
     pa.box_cap = box;
+    pa.stage_cap = (stage > 0 && aligned) ? stage : 0;
     pa.status = b->hs[0]->d_status;
     if (blocks > 0 && (e = launch_project(pa, blocks, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(nullptr, e, "batch subset projection");
@@ -2369,6 +2410,7 @@ wfs_status wfs_loop_calibrate(wfs_loop lp, int gs, double amplitude, float *im_o
             pa.n_wfs = ni;
             pa.n_inst = ni;
             pa.box_cap = h->proj_box;
+            pa.stage_cap = h->proj_stage > 0 ? h->proj_stage : 0;
             pa.block_base = 0;
             pa.max_layers = 1;
             pa.work = c.work;

@@ -92,6 +92,8 @@ struct ProjArgs {
     const WfsDesc *wfs;
     int n_wfs, n_inst;
     int box_cap;                    // floats of shared memory for tables and screen box
+    int stage_cap;                  // floats of one screen box of the bulk-copy form (> 0: that
+                                    // form runs; 0: the cp.async form or direct gathers)
     int block_base;                 // projection block of this launch's first block (a launch
                                     // may cover a contiguous range of the WFS table)
     int n_blocks;                   // blocks in this launch (set by the launcher)
@@ -240,6 +242,11 @@ cudaError_t project_launch_shape(const ProjArgs &a, int total_blocks, LaunchShap
 int project_blocks(const WfsDesc &d);
 // Shared-memory floats the WFS's screen box needs (0 when it is projected by direct gathers).
 int project_box_floats(const WfsDesc &d);
+// Floats of one screen box of the bulk-copy projection for WFS d (0: not tiled).
+int project_stage_floats(const WfsDesc &d);
+// The bulk-copy projection's launch (tiled blocks through screen boxes moved by the bulk-copy
+// unit, direct-gather blocks as in k_project).
+cudaError_t project_bulk_launch_shape(const ProjArgs &a, int total_blocks, LaunchShape *out);
 // Runs of consecutive valid subapertures per subaperture row, at most max_count each.
 void build_segments(const std::vector<int32_t> &ids, int n_sub, int max_count, std::vector<int4> &segs,
                     int *max_run);

@@ -262,6 +262,7 @@ extern "C" wfs_status wfs_measure_one_static(const wfs_telescope *tel, const wfs
     h_pa.n_wfs = 1;
     h_pa.n_inst = 1;
     h_pa.box_cap = 0;  // direct gathers: no projection tiles in the static scratch
+    h_pa.stage_cap = 0;
     h_pa.block_base = 0;
     h_pa.work = nullptr;  // one CTA per block
     h_pa.max_layers = h_inst.n_layers;

@@ -59,6 +59,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
     return done != 0;
 }
 
+// The same wait with the thread suspended while the phase is incomplete (a time hint of 1 ms per
+// try), so that a waiting warp takes no issue slots from the warps that have work; gives up after
+// 4096 tries (about 4 s).
+__device__ __forceinline__ bool mbar_wait_suspend(uint64_t *mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < 4096 && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity), "r"(1000000u)
+            : "memory");
+    return done != 0;
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
