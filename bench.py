@@ -112,7 +112,8 @@ KERNEL_SOURCES = {"spot": ["k_sh.cu", "noise.cuh", "proj_math.cuh", "internal.h"
                   "spot_tc": ["k_sh_tc.cu", "spot_tail.cuh", "noise.cuh", "internal.h", "tcgen05.cuh"],
                   "spot_tc64": ["k_sh_tc64.cu", "noise.cuh", "proj_math.cuh", "internal.h", "tcgen05.cuh"],
                   "noise_cog": ["k_noise_cog.cu", "spot_tail.cuh", "noise.cuh", "internal.h"],
-                  "project": ["k_project.cu", "proj_math.cuh", "internal.h"],
+                  "project": ["k_project_bulk.cu", "k_project.cu", "proj_direct.cuh", "proj_math.cuh", "internal.h",
+                              "tcgen05.cuh"],
                   "gemv": ["k_loop.cu", "proj_math.cuh", "internal.h"],
                   "dm_layer": ["k_loop.cu", "proj_math.cuh", "internal.h"],
                   "uplink": ["k_uplink.cu", "proj_math.cuh", "internal.h"]}

@@ -6,10 +6,11 @@
 // A CTA is two producer warps and eight consumer warps.  The producers walk the CTA's blocks
 // (tickets as in k_project) layer by layer, taking alternate stages: per (block, layer) the
 // producer computes the box of screen pixels the block's taps touch and the box rows of its
-// pupil rows, writes them into one of kStages stage slots, and issues one cp.async.bulk per box row (two where the row crosses the
-// periodic screen's edge) that completes on the slot's mbarrier.  The consumers wait for the slot,
-// interpolate, and hand the slot back through a second mbarrier.  No CTA-wide barrier runs between
-// layers, and no consumer spends instructions on the copies.
+// pupil rows, writes them into one of kStages stage slots, and issues one cp.async.bulk per box
+// row (two where the row crosses the periodic screen's edge) that completes on the slot's
+// mbarrier.  The consumers wait for the slot, interpolate, and hand the slot back through a
+// second mbarrier.  No CTA-wide barrier runs between layers, and no consumer spends instructions
+// on the copies.
 //
 // Consumer thread = two pupil columns of a run of consecutive subapertures, half a run apart (so
 // the lanes of a warp read consecutive box columns), and a group of the run's rows.  Going down a
@@ -35,7 +36,7 @@ constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = 32 * kConsumerWarps;  // = the direct-gather block size
 constexpr int kProducers = 2;                    // producer warps, taking alternate stages
 constexpr int kBulkThreads = kConsumers + 32 * kProducers;
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kRowsPerThread = 16;    // pupil rows a consumer thread keeps in registers
 constexpr int kBulkOffsTable = 512;   // (WFS, layer) offsets a CTA keeps for its whole launch
 constexpr int kBeginCache = 1024;     // WFS first-block indices a CTA keeps in shared memory
