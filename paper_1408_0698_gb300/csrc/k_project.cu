@@ -99,10 +99,14 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
             for (int j = threadIdx.x; j < ncol + n; j += kProjThreads) t[j] = coord(l, j);
         };
         // Box origin (relative to the layer base) and size, the origin rounded down so that the
-        // box's first screen column is a multiple of 4 (16-byte copies when S % 4 == 0).
-        const bool vec = (S & 3) == 0;
+        // box's first screen column is a multiple of 4: 16-byte copies when the layer's rows start
+        // on 16-byte boundaries (S % 4 == 0 and a 16-byte-aligned layer base), else 4-byte copies.
+        auto layer_vec = [&](int l) {
+            return (S & 3) == 0 && (reinterpret_cast<uintptr_t>(layer_screen(I, D, l)) & 15) == 0;
+        };
         if ((int)threadIdx.x < L) {
             const int l = threadIdx.x;
+            const bool vec = layer_vec(l);
             int bx0 = __float_as_int(coord(l, 0).x), by0 = __float_as_int(coord(l, ncol).x);
             int bw = __float_as_int(coord(l, ncol - 1).x) - bx0 + 2;
             const int bh = __float_as_int(coord(l, ncol + n - 1).x) - by0 + 2;
@@ -119,7 +123,7 @@ __device__ __forceinline__ void project_one(const ProjArgs &a, const int bid, in
             const int bx0 = gm.x, by0 = gm.y, bw = gm.z, bh = gm.w;
             if (bw * bh > box_floats) return false;
             const float *scr = layer_screen(I, D, l);
-            if (vec) {
+            if (layer_vec(l)) {
                 // one warp per box row, one lane per 16-byte chunk
                 const int cw = bw >> 2, lane = threadIdx.x & 31, cbase = s_off[l].bu + bx0;
                 for (int r = threadIdx.x >> 5; r < bh; r += kProjThreads / 32) {

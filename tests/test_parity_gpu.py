@@ -228,6 +228,60 @@ def test_edge_geometries(n_sub, n, N, nd, lgs):
     w.close()
 
 
+def _coarse_cfg():
+    """An LGS 8x8 of 10x10-pixel subapertures (the 32-point FP32 kernel, fed by the projection
+    launch) on screens of half its pupil pitch: no shared-memory tiles, direct gathers."""
+    n_sub, n, D = 8, 10, 4.0
+    dx = D / (n_sub * n)
+    S = 1 << int(math.ceil(math.log2(3.0 * n_sub * n + 16)))
+    lay = inputs._layers([0.0, 3e3], [0.7, 0.3], 0.1, 20.0, S, dx / 2)
+    star = inputs._lgs(10 * inputs.ARCSEC, -5 * inputs.ARCSEC, 0.7, 0, photons=500.0)
+    star.spot_fwhm_rad = 1.5 * 589e-9 / (32 * dx)
+    return inputs.Config("coarse", inputs.Telescope(D, 0.0), [inputs.Geometry(n_sub, n, 32, 16, 0.5)], [star],
+                         lay, seed=9)
+
+
+@pytest.mark.parametrize("case", ["elt", "elt_per_slice", "coarse"])
+def test_projection_forms_agree_bit_for_bit(case):
+    """The bulk-copy projection (16-byte-aligned device screens) and the cp.async form (the same
+    screens one float off that alignment) give the same OPD, expected images and slopes bit for
+    bit: the ELT frame with the uplink on at times whose LGS boxes cross the periodic screen's
+    edges (and the per-slice model), and a coarsely sampled WFS whose blocks are direct gathers
+    inside the bulk kernel's pipeline."""
+    import dataclasses
+    if case == "coarse":
+        cfg = _coarse_cfg()
+    else:
+        cfg = inputs.config3()
+        cfg = dataclasses.replace(cfg, stars=[dataclasses.replace(st, uplink_diameter_m=0.4, uplink_samples=16)
+                                              if st.is_lgs else st for st in cfg.stars])
+    w = native.Wfs(cfg, seed=4, noise=True)
+    if case == "elt_per_slice":
+        native.wfs_set_lgs_model(w.h, True)
+    dev = torch.device("cuda:0")
+    scr = torch.as_tensor(inputs.make_screens(cfg.layers, 77)).to(dev).reshape(-1)
+    shifted = torch.empty(scr.numel() + 4, device=dev)
+    shifted[1:1 + scr.numel()].copy_(scr)
+    ptrs = {"bulk": scr.data_ptr(), "cp.async": shifted.data_ptr() + 4}
+    assert ptrs["bulk"] % 16 == 0 and ptrs["cp.async"] % 16 != 0
+    n_opd = max(sum(L.n_valid * L.n * L.n for L in w.layouts), 1)
+    n_int = max(sum(L.n_valid * L.n_fft * L.n_fft for L in w.layouts), 1)
+    n_det = max(sum(L.n_valid * L.n_det * L.n_det for L in w.layouts), 1)
+    stream = torch.cuda.current_stream().cuda_stream
+    for t in (0.0, 2.7, 6.1, 1.0e4 + 0.37):
+        res = {}
+        for form, ptr in ptrs.items():
+            out = [torch.full(sz, float("nan"), device=dev) for sz in ((w.total, 2), (n_opd,), (n_int,), (n_det,), (n_det,))]
+            native.wfs_measure_stages(w.h, ptr, t, *[x.data_ptr() for x in out], stream)
+            torch.cuda.synchronize()
+            native.wfs_sync_status(w.h)
+            res[form] = [out[0].cpu().numpy(), out[1].cpu().numpy(), out[3].cpu().numpy()]
+        for name, a, b in zip(("slopes", "OPD", "E"), res["bulk"], res["cp.async"]):
+            assert np.all(np.isfinite(a)), f"{case} t={t}: {name}"
+            assert np.array_equal(a, b), f"{case} t={t}: {name}"
+    w.close()
+
+
 def test_zero_photons_and_no_valid_subaps():
     cfg = _small_cfg(6, 6, 12, 6, False, photons=0.0)
     scr = inputs.make_screens(cfg.layers, 1)
