@@ -8,8 +8,8 @@
 //   Y[k][m]  = sum_q U[k][q] F[m][q],  I = |Y|^2       (lane k, m looped)
 //   Ta[k][dx] = sum_m I[k][m] Ga[dx][m]               (fused: I never stored)
 //   M[dy][dx] = Kt[dy][dx] sum_k Ga[dy][k] Ta[k][dx]  (DFT across the lanes)
-//   P[dy][ix] = sum_dx M[dy][dx] G[dx][ix]            (lane = ix, half-warp = dy half)
-//   B[iy][ix] = Re sum_dy G[dy][iy] P[dy][ix]         (half-warp partials + one shuffle)
+//   Q[iy][dx] = sum_dy G[dy][iy] M[dy][dx]            (16-point DFT across the lane pairs)
+//   B[iy][ix] = Re sum_dx Q[iy][dx] G[dx][ix]         (lane = ix, half-warp = iy half)
 // then photometry, noise and the centroid with warp reductions.  All sizes are
 // compile-time constants.
 //
@@ -45,10 +45,9 @@ struct N32Layout {
     // per-warp scratch (float2 units)
     static constexpr int wX = 0;                   // [p][q]
     static constexpr int wTa = wX + n * n;         // Q: [nd][n]
-    static constexpr int wM = wTa + nd * n;        // [dyi][n]
-    static constexpr int wI = wM + D2 * n;         // [k][N+1] floats (NGS binning only)
+    static constexpr int wI = wTa + nd * n;        // [k][N+1] floats (NGS binning only)
     static constexpr int warp = wI + (N * (N + 1) + 1) / 2;
-    static_assert(table % 2 == 0 && warp % 2 == 0 && wTa % 2 == 0 && wM % 2 == 0,
+    static_assert(table % 2 == 0 && warp % 2 == 0 && wTa % 2 == 0,
                   "16-byte aligned column-pair scratch");
 };
 
@@ -76,7 +75,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     for (int i = threadIdx.x; i < n * nd; i += blockDim.x) Gt[i] = a.G[i];
     float *rk = reinterpret_cast<float *>(sm2 + Lay::oRk);
     fill_recip_table(rk, threadIdx.x, blockDim.x);
-    tail::fill_fft_table(fft, threadIdx.x, blockDim.x);
+    tail::fill_fft_table<n>(fft, threadIdx.x, blockDim.x);
     __syncthreads();
     wait_prior_grid();
     if (a.split_noise) allow_dependent_grid();  // the noise kernel may take SMs as CTAs retire
@@ -84,7 +83,6 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float2 *X = sm2 + Lay::table + wib * Lay::warp + Lay::wX;
     float2 *Ta = sm2 + Lay::table + wib * Lay::warp + Lay::wTa;
-    float2 *Mw = sm2 + Lay::table + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(sm2 + Lay::table + wib * Lay::warp + Lay::wI);
 
     // Work split: each warp starts with subaperture blockIdx.x * nw + wib; with a.work, lane 0
@@ -207,7 +205,7 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
 
         float Bv[nd / 2];  // B[iy][ix] for iy = half*(nd/2) + j
         if (W.is_lgs) {
-            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Ta), fft, Gt,
+            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Ta), fft, Gt,
                                        W.ktil + (size_t)v * (D2 * n), lane, Bv);
         } else {
             __syncwarp();

@@ -114,16 +114,16 @@ struct TcLayout {
     static constexpr int tEnd = tRk + kRecipTable / 2;
     static constexpr int oWarp = (oTab + tEnd * 8 + 15) / 16 * 16;  // per-warp scratch (float2)
     static constexpr int even(int x) { return (x + 1) & ~1; }
-    // 32-lane path: the NGS image rows (wI) alias the LGS scratch (wQ, wM); X, Q and M hold
-    // column pairs, 16-byte aligned
-    static constexpr int wX = 0, wQ = wX + n * n, wM = wQ + nd * n;
+    // 32-lane path: the NGS image rows (wI) alias the LGS scratch (wQ); X and Q hold column
+    // pairs, 16-byte aligned
+    static constexpr int wX = 0, wQ = wX + n * n;
     // direct-sum path: Ta [N][no] over the consumed field X, then M [D2][n], P [D2][nd], B
     // [nd][nd] floats; an NGS's image rows [N][N + 1] floats over X, then B
     static constexpr int wTa = 0, wMg = even(n * n > N * no ? n * n : N * no), wP = wMg + D2 * n,
                          wB = kLane ? 0 : wP + D2 * nd;
     static constexpr int wI = kLane ? wQ : 0, wBn = even((N * (N + 1) + 1) / 2);
-    static_assert(wQ % 2 == 0 && wM % 2 == 0, "16-byte aligned column-pair scratch");
-    static constexpr int lgs_end = kLane ? wM + D2 * n : even(wB + (nd * nd + 1) / 2);
+    static_assert(wQ % 2 == 0, "16-byte aligned column-pair scratch");
+    static constexpr int lgs_end = kLane ? wQ + nd * n : even(wB + (nd * nd + 1) / 2);
     static constexpr int ngs_end = kLane ? wI + (N * (N + 1) + 1) / 2 : wBn + (nd * nd + 1) / 2;
     // an LGS subaperture's elongation table K~ ([2n-1][n] complex), staged by cp.async at the
     // top of a group and read by the elongation stage; it may overlap the NGS rows, which an LGS
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
                 Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
             }
         }
-        if constexpr (kLane) tail::fill_fft_table(fft, tid, kTcThreads);
+        if constexpr (kLane) tail::fill_fft_table<n>(fft, tid, kTcThreads);
         else
             for (int i = tid; i < n * N; i += kTcThreads) Gat[i] = a.Ga[i];
         for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
     float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
     float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
-    float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
     const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
     const int groups = (a.total + 3) / 4;
@@ -520,7 +519,7 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
             if (W.is_lgs) {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
                 __syncwarp();
-                tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Qw), fft, Gt,
+                tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Qw), fft, Gt,
                                         Kts, lane, Bv);
             } else
                 tail::ngs_binned<nd>(Iw, lane, Bv);
@@ -603,7 +602,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
             const int p = i / N, k = i - p * N;
             Fk[p * N + k] = a.F[i];  // F[q*N + m] = F[m][q]: row index = p, column = k
         }
-        tail::fill_fft_table(fft, tid, kTcThreads);
+        tail::fill_fft_table<n>(fft, tid, kTcThreads);
         for (int i = tid; i < n * nd; i += kTcThreads) Gt[i] = a.G[i];
         fill_recip_table(rk, tid, kTcThreads);
     }
@@ -632,7 +631,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
     float4 *X4 = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wX);
     float2 *Qw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wQ;
     float2 *Kts = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wKt;
-    float2 *Mw = reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wM;
     float *Iw = reinterpret_cast<float *>(reinterpret_cast<float2 *>(smem + Lay::oWarp) + wib * Lay::warp + Lay::wI);
     const int row = wq * 32 + lane;  // this thread's row of the MMA tiles and TMEM lane
     const int groups = (a.total + 3) / 4;
@@ -910,7 +908,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
         if (W.is_lgs) {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncwarp();
-            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Mw), reinterpret_cast<float4 *>(Qw), fft, Gt, Kts,
+            tail::lgs_binned<n, nd>(T, reinterpret_cast<float4 *>(Qw), fft, Gt, Kts,
                                     lane, Bv);
         } else
             tail::ngs_binned<nd>(Iw, lane, Bv);

@@ -4,15 +4,20 @@
 // centroid).  Shared by the FP32 and tensor-core kernels.
 //
 //   M[dy][dx] = Kt[dy][dx] sum_k Ga(dy, k) T[k][dx]       (k = lane: a 32-point DFT)
-//   Q[iy][dx] = sum_dy G(dy, iy) M[dy][dx]                 (lane = iy, half-warp = dx half)
+//   Q[iy][dx] = sum_dy G(dy, iy) M[dy][dx]                 (an nd-point DFT over dy)
 //   B[iy][ix] = Re sum_dx Q[iy][dx] G[dx][ix]              (lane = ix, half-warp = iy half)
 // with Ga(dy, k) = exp(+2 pi i (k - cN) dy / N) = ph(dy) w^(k dy), w = exp(2 pi i / N),
-// ph(dy) = exp(-2 pi i cN dy / N), and G(dy, i) = sum_{r<b} w^{(b i + r - cN) dy}
+// ph(dy) = exp(-2 pi i cN dy / N), and G(dy, i) = sum_{r<b} exp(-2 pi i (b i + r - cN) dy / N)
 // (conjugated for dy < 0).  The sum over k is a DFT of each column across the lanes: radix 2,
 // decimation in frequency, one shuffle per stage and component; lane i ends with frequency
 // bitrev5(i).  Kt carries 1/N^2 and the Hermitian weight c_dx, so B is the binned elongated
-// spot.  Then E = photons fill B / sum B, C = Poisson(E) + ron z (or E), and the centre of
-// gravity.
+// spot.  Since N = b nd, G(dy, i) = h(dy) v^(i dy) with h(dy) = sum_{r<b} exp(-2 pi i (r - cN)
+// dy / N) and v = exp(-2 pi i / nd): Q is the nd-point DFT of m[j] = sum_{dy = j mod nd} h(dy)
+// M[dy][dx].  The lanes i and i ^ 1 hold the frequencies f and f + 16 (the same j, since
+// nd = 16), so one shuffle folds them, and the positions p = i >> 1 hold j = bitrev4(p): a
+// decimation-in-time DFT across the positions ends with Q[p] in natural order, the even lane
+// of each pair working the first column pairs and the odd lane the rest.  Then
+// E = photons fill B / sum B, C = Poisson(E) + ron z (or E), and the centre of gravity.
 #pragma once
 #include "internal.h"
 #include "noise.cuh"
@@ -31,11 +36,15 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-constexpr int kFftTable = 6 * 32;  // float2: five stages of twiddles, then ph(dy), per lane
+constexpr int kFftTable = 10 * 32;  // float2: five stages of twiddles, ph h(dy), four more stages
 
 // Per-lane DFT constants: entry s * 32 + lane (s < 5, span h = 16 >> s) is 1 for the upper
 // lane of a butterfly and w^((lane mod h) 16 / h) for the lower; entry 5 * 32 + lane is
-// ph(dy) of the lane's output frequency.  Call from every thread of the block.
+// ph(dy) h(dy) = sum_{r<2} exp(-2 pi i r dy / 32) of the lane's output frequency dy when
+// |dy| < n, else 0; entry (6 + s) * 32 + lane (s < 4, span q = 2^s in positions p = lane >> 1)
+// is 1 for the upper position of a butterfly and exp(-2 pi i (p mod q) / 2q) for the lower.
+// Call from every thread of the block.
+template <int n>
 __device__ __forceinline__ void fill_fft_table(float2 *tab, int tid, int nthreads) {
     for (int i = tid; i < kFftTable; i += nthreads) {
         const int st = i >> 5, l = i & 31;
@@ -43,9 +52,17 @@ __device__ __forceinline__ void fill_fft_table(float2 *tab, int tid, int nthread
         if (st < 5) {
             const int h = 16 >> st;
             if (l & h) sincospif((float)((l & (h - 1)) * (16 / h)) / 16.0f, &sn, &cs);
-        } else {
+        } else if (st == 5) {
             const int f = (int)(__brev((unsigned)l) >> 27), dy = f < 16 ? f : f - 32;
-            sincospif((float)(-31 * dy) / 32.0f, &sn, &cs);  // 2 cN / N = 31 / 32
+            if (dy > -n && dy < n) {
+                sincospif((float)(-dy) / 16.0f, &sn, &cs);  // exp(-2 pi i dy / 32)
+                cs += 1.0f;
+            } else {
+                cs = 0.0f;
+            }
+        } else {
+            const int q = 1 << (st - 6), p = l >> 1;
+            if (p & q) sincospif((float)(-(p & (q - 1))) / (float)q, &sn, &cs);
         }
         tab[i] = make_float2(cs, sn);
     }
@@ -59,13 +76,13 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 
 // T: this lane's row k = lane of the first stage (T[k][dx], dx < n), consumed.  fft: the
 // table above.  Gt: [n][nd] G[d][i].  kt: the subaperture's K~ [2n-1][n] (global or shared
-// memory).  M and Q are per-warp scratch ([2n-1][n/2] and [nd][n/2], 16-byte aligned), each
-// entry a column pair (re dx, re dx+1, im dx, im dx+1).
+// memory).  Q is per-warp scratch ([nd][n/2], 16-byte aligned), each entry a column pair
+// (re dx, re dx+1, im dx, im dx+1).
 // On return Bv[j] = B[half * nd/2 + j][ix] for lane = half * 16 + ix.
 template <int n, int nd>
-__device__ __forceinline__ void lgs_binned(float2 (&T)[n], float4 *M, float4 *Q, const float2 *fft,
-                                           const float2 *Gt, const float2 *kt, int lane, float (&Bv)[nd / 2]) {
-    constexpr int D2 = 2 * n - 1, P = n / 2, PH = (P + 1) / 2;
+__device__ __forceinline__ void lgs_binned(float2 (&T)[n], float4 *Q, const float2 *fft, const float2 *Gt,
+                                           const float2 *kt, int lane, float (&Bv)[nd / 2]) {
+    constexpr int P = n / 2, PH = (P + 1) / 2;
     static_assert(nd == 16, "the detector tile maps to 16 lanes x 2 half-warps");
     static_assert(n <= 16, "frequencies |dy| < n must be distinct modulo 32");
     static_assert(n % 2 == 0, "columns travel in pairs");
@@ -94,52 +111,71 @@ __device__ __forceinline__ void lgs_binned(float2 (&T)[n], float4 *M, float4 *Q,
             Ti[c] = fma2(si, twx, mul2(sr, twy));
         }
     }
+    // h(dy) M[dy] for the lane's frequency (zero outside the band |dy| < n, through the table),
+    // then folded with the lane holding dy -/+ 16
     {
         const int f = (int)(__brev((unsigned)lane) >> 27), dy = f < 16 ? f : f - 32;
-        if (dy > -n && dy < n) {
-            const int dyi = dy + n - 1;
-            const float2 ph = fft[5 * 32 + lane];
-            const float2 phx = dup2(ph.x), phy = dup2(ph.y), nphy = dup2(-ph.y);
+        const int dyi = min(max(dy + n - 1, 0), 2 * n - 2);
+        const float2 ph = fft[5 * 32 + lane];
+        const float2 phx = dup2(ph.x), phy = dup2(ph.y), nphy = dup2(-ph.y);
 #pragma unroll
-            for (int c = 0; c < P; ++c) {
-                const float2 xr = fma2(Ti[c], nphy, mul2(Tr[c], phx));
-                const float2 xi = fma2(Ti[c], phx, mul2(Tr[c], phy));
-                const float2 k0 = kt[dyi * n + 2 * c], k1 = kt[dyi * n + 2 * c + 1];
-                M[dyi * P + c] = make_float4(xr.x * k0.x - xi.x * k0.y, xr.y * k1.x - xi.y * k1.y,
-                                             xr.x * k0.y + xi.x * k0.x, xr.y * k1.y + xi.y * k1.x);
-            }
+        for (int c = 0; c < P; ++c) {
+            const float2 xr = fma2(Ti[c], nphy, mul2(Tr[c], phx));
+            const float2 xi = fma2(Ti[c], phx, mul2(Tr[c], phy));
+            const float2 k0 = kt[dyi * n + 2 * c], k1 = kt[dyi * n + 2 * c + 1];
+            const float2 kr = make_float2(k0.x, k1.x), ki = make_float2(k0.y, k1.y);
+            const float2 mr = fma2(xi, make_float2(-ki.x, -ki.y), mul2(xr, kr));
+            const float2 mi = fma2(xi, kr, mul2(xr, ki));
+            Tr[c] = __fadd2_rn(mr, make_float2(__shfl_xor_sync(0xffffffffu, mr.x, 1),
+                                               __shfl_xor_sync(0xffffffffu, mr.y, 1)));
+            Ti[c] = __fadd2_rn(mi, make_float2(__shfl_xor_sync(0xffffffffu, mi.x, 1),
+                                               __shfl_xor_sync(0xffffffffu, mi.y, 1)));
         }
     }
-    __syncwarp();
-    // Q[iy][dx] for iy = lane & 15; half 0 takes the column pairs [0, PH), half 1 the rest
-    const int ix = lane & 15, half = lane >> 4;
-    {
-        const int iy = ix;
-        float2 qr[PH], qi[PH];
+    // Q: a 16-point DFT across the positions p = lane >> 1 (input bit-reversed, output in
+    // natural order), four radix-2 decimation-in-time stages; the even lane of a position
+    // takes the column pairs [0, PH), the odd lane the rest
+    const int par = lane & 1;
+    float2 Wr[PH], Wi[PH];
 #pragma unroll
-        for (int j = 0; j < PH; ++j) qr[j] = qi[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < PH; ++j) {
+        const int c1 = PH + j;
+        const float2 zr = c1 < P ? Tr[c1 < P ? c1 : 0] : make_float2(0.0f, 0.0f);
+        const float2 zi = c1 < P ? Ti[c1 < P ? c1 : 0] : make_float2(0.0f, 0.0f);
+        Wr[j] = par ? zr : Tr[j];
+        Wi[j] = par ? zi : Ti[j];
+    }
 #pragma unroll
-        for (int dyi = 0; dyi < D2; ++dyi) {
-            const int dy = dyi - (n - 1);
-            const float2 gv = Gt[(dy >= 0 ? dy : -dy) * nd + iy];
-            const float gy = dy < 0 ? -gv.y : gv.y;
-            const float2 gx2 = dup2(gv.x), gy2 = dup2(gy), ngy2 = dup2(-gy);
-#pragma unroll
-            for (int j = 0; j < PH; ++j) {
-                const int c = half * PH + j;
-                if (c < P) {
-                    const float4 m = M[dyi * P + c];
-                    const float2 mr = make_float2(m.x, m.y), mi = make_float2(m.z, m.w);
-                    // per column: re += g.x m.re - g.y m.im, im += g.x m.im + g.y m.re
-                    qr[j] = fma2(gx2, mr, fma2(ngy2, mi, qr[j]));
-                    qi[j] = fma2(gx2, mi, fma2(gy2, mr, qi[j]));
-                }
-            }
-        }
+    for (int st = 0; st < 4; ++st) {
+        const int q = 1 << st;
+        const float2 sg = dup2(((lane >> 1) & q) ? -1.0f : 1.0f);
+        const float2 tw = fft[(6 + st) * 32 + lane];
+        const float2 twx = dup2(tw.x), twy = dup2(tw.y), ntwy = dup2(-tw.y);
 #pragma unroll
         for (int j = 0; j < PH; ++j) {
-            const int c = half * PH + j;
-            if (c < P) Q[iy * P + c] = make_float4(qr[j].x, qr[j].y, qi[j].x, qi[j].y);
+            // the lower position's value times its twiddle; then upper = own + partner's,
+            // lower = partner's - own
+            float2 vr = Wr[j], vi = Wi[j];
+            if (st > 0) {  // the first stage's twiddles are all 1
+                vr = fma2(Wi[j], ntwy, mul2(Wr[j], twx));
+                vi = fma2(Wi[j], twx, mul2(Wr[j], twy));
+            }
+            const float2 pr = make_float2(__shfl_xor_sync(0xffffffffu, vr.x, 2 * q),
+                                          __shfl_xor_sync(0xffffffffu, vr.y, 2 * q));
+            const float2 pi = make_float2(__shfl_xor_sync(0xffffffffu, vi.x, 2 * q),
+                                          __shfl_xor_sync(0xffffffffu, vi.y, 2 * q));
+            Wr[j] = fma2(sg, vr, pr);
+            Wi[j] = fma2(sg, vi, pi);
+        }
+    }
+    const int ix = lane & 15, half = lane >> 4;
+    __syncwarp();  // earlier reads of the scratch by other lanes are done
+    {
+        const int iy = lane >> 1;
+#pragma unroll
+        for (int j = 0; j < PH; ++j) {
+            const int c = par ? PH + j : j;
+            if (c < P) Q[iy * P + c] = make_float4(Wr[j].x, Wr[j].y, Wi[j].x, Wi[j].y);
         }
     }
     __syncwarp();
