@@ -50,18 +50,28 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def q_dft_flops(n, nd):
+    """Flops of Q = G^T M in the 32-point kernels, per subaperture: the rows |dy| < n folded
+    modulo nd (2 flops per complex add), then an nd-point radix-2 DFT per column dx (nd/2
+    butterflies per stage; 4 flops in the first stage, whose twiddles are 1, 10 in the others:
+    a complex multiply and two complex adds)."""
+    fold = 2 * max(0, (2 * n - 1) - nd) * n
+    stages = int(math.log2(nd))
+    return fold + n * (nd // 2) * (4 + 10 * (stages - 1))
+
+
 def spot_flops(n, N, nd, lgs):
     """FP32 flops (FMA = 2) of one subaperture in its spot kernel: DFT 8Nn(n+N), |.|^2 3N^2.
     LGS elongation and binning through the transfer function: Ta 4N^2 n, then
       32-point kernels: M as a radix-2 DFT across the lanes, 10 log2(N) N n, times the phase
-      and Kt 12 (2n-1) n; Q = G^T M 8 (2n-1) n nd; B = Re Q G 4 nd^2 n; photometry 2 nd^2
-      (the centroid, 4 nd^2, runs in the separate noise pass);
+      and Kt 12 (2n-1) n; Q = G^T M as a folded nd-point DFT (q_dft_flops); B = Re Q G
+      4 nd^2 n; photometry 2 nd^2 (the centroid, 4 nd^2, runs in the separate noise pass);
       other sizes (direct sums): M (2n-1) n (8N+6); P = M G 8 (2n-1) nd n; B 4 nd^2 (2n-1);
       photometry and centroid 6 nd^2.
     NGS: binning N^2, photometry and centroid 6 nd^2."""
     f = 8 * N * n * (n + N) + 3 * N * N
     if lgs and N == 32:
-        f += 4 * N * N * n + 10 * 5 * N * n + 12 * (2 * n - 1) * n + 8 * (2 * n - 1) * n * nd + 4 * nd * nd * n
+        f += 4 * N * N * n + 10 * 5 * N * n + 12 * (2 * n - 1) * n + q_dft_flops(n, nd) + 4 * nd * nd * n
         f += 2 * nd * nd
     elif lgs:
         f += 4 * N * N * n + (2 * n - 1) * n * (8 * N + 6) + 8 * (2 * n - 1) * nd * n + 4 * nd * nd * (2 * n - 1)

@@ -373,27 +373,22 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
 #pragma unroll
             for (int q = 0; q < n; ++q) U[q] = make_float2(U[q].x * su, U[q].y * su);
         }
-        // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
+        // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1); word w of
+        // a block holds its elements (2w, 2w + 1)
         {
-            float hv[2 * n], lv[2 * n];
+            uint32_t hw[n], lw[n];
 #pragma unroll
-            for (int q = 0; q < n; ++q) {
-                E::split(U[q].x, hv[q], lv[q]);
-                E::split(U[q].y, hv[n + q], lv[n + q]);
+            for (int i = 0; i < n / 2; ++i) {
+                E::split2(U[2 * i].x, U[2 * i + 1].x, hw[i], lw[i]);
+                E::split2(U[2 * i].y, U[2 * i + 1].y, hw[n / 2 + i], lw[n / 2 + i]);
             }
 #pragma unroll
             for (int ch = 0; ch < 8; ++ch) {
                 uint32_t wds[4];
 #pragma unroll
                 for (int e2 = 0; e2 < 4; ++e2) {
-                    float vv[2];
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int e = ch * 8 + e2 * 2 + h2;
-                        const int t = e / (2 * n), j = e % (2 * n);
-                        vv[h2] = e >= 6 * n ? 0.0f : (t == 1 ? lv[j] : hv[j]);
-                    }
-                    wds[e2] = E::pack(vv[0], vv[1]);
+                    const int w = ch * 4 + e2, t = w / n, j = w % n;
+                    wds[e2] = w >= 3 * n ? 0u : (t == 1 ? lw[j] : hw[j]);
                 }
                 *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
             }
@@ -444,11 +439,16 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
                 tmem_wait_ld();
                 float I[16], Iop[16];  // the intensity, and the operand value
 #pragma unroll
-                for (int m = 0; m < 16; ++m) {
-                    const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
-                    const float y2 = fmaf(yr, yr, yi * yi);
-                    I[m] = kF16 ? y2 * uy * uy : y2;
-                    Iop[m] = kF16 ? y2 * si : y2;
+                for (int m = 0; m < 16; m += 2) {  // column pairs: each half as fmaf(yr, yr, yi * yi)
+                    const float2 yr = make_float2(__uint_as_float(r[m]), __uint_as_float(r[m + 1]));
+                    const float2 yi = make_float2(__uint_as_float(r2[m]), __uint_as_float(r2[m + 1]));
+                    const float2 y2 = __ffma2_rn(yr, yr, __fmul2_rn(yi, yi));
+                    const float2 iv = kF16 ? __fmul2_rn(__fmul2_rn(y2, make_float2(uy, uy)), make_float2(uy, uy)) : y2;
+                    const float2 ov = kF16 ? __fmul2_rn(y2, make_float2(si, si)) : y2;
+                    I[m] = iv.x;
+                    I[m + 1] = iv.y;
+                    Iop[m] = ov.x;
+                    Iop[m + 1] = ov.y;
                 }
                 if (dstI) {
 #pragma unroll
@@ -465,11 +465,7 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int e2 = 0; e2 < 4; ++e2) {
-                        float h0, l0, h1, l1;
-                        E::split(Iop[c2 * 8 + 2 * e2], h0, l0);
-                        E::split(Iop[c2 * 8 + 2 * e2 + 1], h1, l1);
-                        hw[e2] = E::pack(h0, h1);
-                        lw[e2] = E::pack(l0, l1);
+                        E::split2(Iop[c2 * 8 + 2 * e2], Iop[c2 * 8 + 2 * e2 + 1], hw[e2], lw[e2]);
                     }
                     *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (2 * hh + c2) * 8)) =
                         make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -734,27 +730,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
 #pragma unroll
                 for (int q = 0; q < n; ++q) U[q] = make_float2(U[q].x * su, U[q].y * su);
             }
-            // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1)
+            // A1 row: [U_hi | U_lo | U_hi | 0], each block (re q = 0..n-1, im q = 0..n-1); word w of
+            // a block holds its elements (2w, 2w + 1)
             {
-                float hv[2 * n], lv[2 * n];
+                uint32_t hw[n], lw[n];
 #pragma unroll
-                for (int q = 0; q < n; ++q) {
-                    E::split(U[q].x, hv[q], lv[q]);
-                    E::split(U[q].y, hv[n + q], lv[n + q]);
+                for (int i = 0; i < n / 2; ++i) {
+                    E::split2(U[2 * i].x, U[2 * i + 1].x, hw[i], lw[i]);
+                    E::split2(U[2 * i].y, U[2 * i + 1].y, hw[n / 2 + i], lw[n / 2 + i]);
                 }
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {
                     uint32_t wds[4];
 #pragma unroll
                     for (int e2 = 0; e2 < 4; ++e2) {
-                        float vv[2];
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            const int e = ch * 8 + e2 * 2 + h2;
-                            const int t = e / (2 * n), j = e % (2 * n);
-                            vv[h2] = e >= 6 * n ? 0.0f : (t == 1 ? lv[j] : hv[j]);
-                        }
-                        wds[e2] = E::pack(vv[0], vv[1]);
+                        const int w = ch * 4 + e2, t = w / n, j = w % n;
+                        wds[e2] = w >= 3 * n ? 0u : (t == 1 ? lw[j] : hw[j]);
                     }
                     *reinterpret_cast<uint4 *>(sA1 + sw128_off(row, ch * 8)) = make_uint4(wds[0], wds[1], wds[2], wds[3]);
                 }
@@ -795,10 +786,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                     tmem_wait_ld();
                     float I[16];
 #pragma unroll
-                    for (int m = 0; m < 16; ++m) {
-                        const float yr = __uint_as_float(r[m]), yi = __uint_as_float(r2[m]);
-                        const float y2 = fmaf(yr, yr, yi * yi);
-                        I[m] = kF16 ? y2 * uy * uy : y2;
+                    for (int m = 0; m < 16; m += 2) {  // column pairs: each half as fmaf(yr, yr, yi * yi)
+                        const float2 yr = make_float2(__uint_as_float(r[m]), __uint_as_float(r[m + 1]));
+                        const float2 yi = make_float2(__uint_as_float(r2[m]), __uint_as_float(r2[m + 1]));
+                        const float2 y2 = __ffma2_rn(yr, yr, __fmul2_rn(yi, yi));
+                        const float2 iv = kF16 ? __fmul2_rn(__fmul2_rn(y2, make_float2(uy, uy)), make_float2(uy, uy)) : y2;
+                        I[m] = iv.x;
+                        I[m + 1] = iv.y;
                     }
                     if (kSlices) {
                         float *ir = Iw + lane * (N + 1) + 16 * hh;
@@ -823,11 +817,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int e2 = 0; e2 < 4; ++e2) {
-                            float h0, l0, h1, l1;
-                            E::split(I[c2 * 8 + 2 * e2], h0, l0);
-                            E::split(I[c2 * 8 + 2 * e2 + 1], h1, l1);
-                            hw[e2] = E::pack(h0, h1);
-                            lw[e2] = E::pack(l0, l1);
+                            E::split2(I[c2 * 8 + 2 * e2], I[c2 * 8 + 2 * e2 + 1], hw[e2], lw[e2]);
                         }
                         *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (2 * hh + c2) * 8)) =
                             make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -856,12 +846,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_sh_tc_sl(const __grid_constan
                 uint32_t hw[4], lw[4];
 #pragma unroll
                 for (int e2 = 0; e2 < 4; ++e2) {
-                    float h0, l0, h1, l1;
                     const float i0 = Iw[lane * (N + 1) + c4 * 8 + 2 * e2], i1 = Iw[lane * (N + 1) + c4 * 8 + 2 * e2 + 1];
-                    E::split(kF16 ? i0 * si : i0, h0, l0);
-                    E::split(kF16 ? i1 * si : i1, h1, l1);
-                    hw[e2] = E::pack(h0, h1);
-                    lw[e2] = E::pack(l0, l1);
+                    E::split2(kF16 ? i0 * si : i0, kF16 ? i1 * si : i1, hw[e2], lw[e2]);
                 }
                 *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, c4 * 8)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4 *>(sA2 + sw128_off(row, (4 + c4) * 8)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);

@@ -258,12 +258,8 @@ __global__ void __launch_bounds__(kT64Threads, 1) k_sh_tc64(const __grid_constan
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
-                float h0, l0, h1, l1;
                 const int c0 = ch * 8 + 2 * e2, c1 = c0 + 1;
-                E::split(c0 < 32 ? ur[c0] : ui[c0 - 32], h0, l0);
-                E::split(c1 < 32 ? ur[c1] : ui[c1 - 32], h1, l1);
-                hw[e2] = E::pack(h0, h1);
-                lw[e2] = E::pack(l0, l1);
+                E::split2(c0 < 32 ? ur[c0] : ui[c0 - 32], c1 < 32 ? ur[c1] : ui[c1 - 32], hw[e2], lw[e2]);
             }
             *reinterpret_cast<uint4 *>(at(sT, 0, tid, ch * 8)) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
             *reinterpret_cast<uint4 *>(at(sT, 1, tid, ch * 8)) = make_uint4(lw[0], lw[1], lw[2], lw[3]);

@@ -120,6 +120,13 @@ struct TcElt {
         return *reinterpret_cast<const uint32_t *>(&v);
     }
     static __device__ __forceinline__ uint16_t bits(float a) { return __bfloat16_as_ushort(__float2bfloat16_rn(a)); }
+    // The split of a pair as packed words: hw = pack(hi a, hi b), lw = pack(lo a, lo b) -- the
+    // words pack() gives on split()'s parts (rounding is idempotent, so pack(a, b) holds the hi
+    // parts, which unpack exactly; x - hi is exact).
+    static __device__ __forceinline__ void split2(float a, float b, uint32_t &hw, uint32_t &lw) {
+        hw = pack(a, b);
+        lw = pack(a - __uint_as_float(hw << 16), b - __uint_as_float(hw & 0xFFFF0000u));
+    }
 };
 template <>
 struct TcElt<true> {
@@ -133,6 +140,11 @@ struct TcElt<true> {
         return *reinterpret_cast<const uint32_t *>(&v);
     }
     static __device__ __forceinline__ uint16_t bits(float a) { return __half_as_ushort(__float2half_rn(a)); }
+    static __device__ __forceinline__ void split2(float a, float b, uint32_t &hw, uint32_t &lw) {
+        hw = pack(a, b);
+        const float2 h = __half22float2(*reinterpret_cast<const __half2 *>(&hw));
+        lw = pack(a - h.x, b - h.y);
+    }
 };
 
 __device__ __forceinline__ float warp_sum_tc(float v) {

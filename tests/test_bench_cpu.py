@@ -9,9 +9,17 @@ import bench
 def test_spot_flop_model():
     # 32-point LGS subaperture (n = 10, N = 32, 16 x 16 detector pixels), term by term
     n, N, nd = 10, 32, 16
+    # Q = G^T M as a folded 16-point DFT: 3 folded rows x 10 columns (2 flops each), then per
+    # column 8 butterflies of 4 flops (first stage) and 3 x 8 of 10 flops
+    q = 2 * 3 * n + n * (8 * 4 + 3 * 8 * 10)
+    assert q == bench.q_dft_flops(n, nd) == 2780
     terms = (8 * N * n * (n + N), 3 * N * N, 4 * N * N * n, 10 * int(math.log2(N)) * N * n,
-             12 * (2 * n - 1) * n, 8 * (2 * n - 1) * n * nd, 4 * nd * nd * n, 2 * nd * nd)
-    assert sum(terms) == 204904 == bench.spot_flops(n, N, nd, True)
+             12 * (2 * n - 1) * n, q, 4 * nd * nd * n, 2 * nd * nd)
+    assert sum(terms) == 183364 == bench.spot_flops(n, N, nd, True)
+    # the dense form of Q (8 (2n-1) n nd flops) is 8.7 times the DFT's count
+    assert 8 * (2 * n - 1) * n * nd == 24320
+    # n = 8 on the 32-point grid: 15 rows, none folded
+    assert bench.q_dft_flops(8, 16) == 8 * (8 * 4 + 3 * 8 * 10)
     # the DFT term alone is the useful DFT work of a subaperture, 8 N n (n + N)
     assert terms[0] == 107520
     # NGS (no elongation): DFT, |.|^2, binning, photometry and centroid
@@ -40,13 +48,13 @@ def test_traffic_table_entries():
 
 def test_cuda_core_and_tensor_split():
     """The roofline's split of a 32-point LGS subaperture: with Y = U F^T and Ta = I Ga^T as MMAs
-    the CUDA cores keep 204,904 - 81,920 - 40,960 = 82,024 flops; with U = F X as an MMA too,
-    56,424.  The tensor figure divides the useful DFT flops, 8 N n (n + N) = 107,520."""
+    the CUDA cores keep 183,364 - 81,920 - 40,960 = 60,484 flops; with U = F X as an MMA too,
+    34,884.  The tensor figure divides the useful DFT flops, 8 N n (n + N) = 107,520."""
     n, N, nd = 10, 32, 16
     tot = bench.spot_flops(n, N, nd, True)
     on_tc = lambda name: sum(bench.TC_STAGES[s][0](n, N, nd) for s in bench.tc_stages(name))
-    assert tot - on_tc("spot_tc_bf16x3_N32") == 82024
-    assert tot - on_tc("spot_tcu_bf16x3_N32") == 82024 - 25600
+    assert tot - on_tc("spot_tc_bf16x3_N32") == 60484
+    assert tot - on_tc("spot_tcu_bf16x3_N32") == 60484 - 25600
     assert on_tc("spot_n32_fp32_N32") == 0
     assert bench.dft_useful_flops(n, N) == 107520
     # issued BF16 flops per subaperture of the two original MMA chains: 32 rows x (64 x 64 + 2 x 32 x 64)
