@@ -61,30 +61,57 @@ __device__ __forceinline__ void store_field(float4 *X4, int i, float c, float s)
     e[2] = s;
 }
 
-// U[q] = sum_p F[k][p] X[p][q] for this lane's DFT row k: two columns per packed FP32x2 FMA
-// (each half rounded as fmaf); per p, re += -f.im x.im then f.re x.re, im += f.im x.re then
-// f.re x.im.
+// U[q] = sum_p F[k][p] X[p][q] for this lane's DFT row k (lanes k >= N get zeros).  The rows k
+// and k + N/2 share F up to a sign and a quarter turn: F[k + N/2][p] = F[k][p] (-1)^p i^(n-1)
+// (n even), so of each such pair the lane k sums the even p, E = sum F[k][p] X[p][q], and the
+// lane k + N/2 the odd p, O, both with row k of F; after one exchange U[k] = E + O and
+// U[k + N/2] = i^(n-1) (E - O).  Two columns per packed FP32x2 FMA (each half rounded as fmaf);
+// per p, re += -f.im x.im then f.re x.re, im += f.im x.re then f.re x.im.  Call from the whole
+// warp.
 template <int n, int N>
 __device__ __forceinline__ void field_rows(const float2 *Fk, const float4 *X4, int lane, float2 (&U)[n]) {
-    float2 ur[n / 2], ui[n / 2];
+    constexpr int H = N / 2, P = n / 2;
+    static_assert(n % 2 == 0 && N % 2 == 0, "even/odd halves of the rows and of the columns");
+    const bool upper = lane >= H && lane < N;
+    const int k = lane < N ? (upper ? lane - H : lane) : 0;
+    float2 ur[P], ui[P];
 #pragma unroll
-    for (int c = 0; c < n / 2; ++c) ur[c] = ui[c] = make_float2(0.0f, 0.0f);
+    for (int c = 0; c < P; ++c) ur[c] = ui[c] = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int p = 0; p < n; ++p) {
-        const float2 f = Fk[p * N + lane];
+    for (int j = 0; j < P; ++j) {
+        const int p = 2 * j + (upper ? 1 : 0);
+        const float2 f = Fk[p * N + k];
         const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y), nfy = make_float2(-f.y, -f.y);
 #pragma unroll
-        for (int c = 0; c < n / 2; ++c) {
-            const float4 x = X4[p * (n / 2) + c];
+        for (int c = 0; c < P; ++c) {
+            const float4 x = X4[p * P + c];
             const float2 xr = make_float2(x.x, x.y), xi = make_float2(x.z, x.w);
             ur[c] = __ffma2_rn(fx, xr, __ffma2_rn(nfy, xi, ur[c]));
             ui[c] = __ffma2_rn(fx, xi, __ffma2_rn(fy, xr, ui[c]));
         }
     }
+    // lower lane: own + partner's = E + O; upper: partner's - own = E - O, then times
+    // i^(n-1) = s i (s = +1 for n = 2 mod 4, -1 for n = 0 mod 4): (re, im) -> (-s im, s re)
+    const int src = lane < N ? (upper ? lane - H : lane + H) : lane;
+    const float sg = upper ? -1.0f : 1.0f;
+    constexpr float s = ((n - 1) % 4 == 1) ? 1.0f : -1.0f;
+    const float2 sg2 = make_float2(sg, sg);
+    const float2 A = upper ? make_float2(0.0f, 0.0f) : make_float2(1.0f, 1.0f);
+    const float2 B = upper ? make_float2(-s, -s) : make_float2(0.0f, 0.0f);
+    const float2 Cc = upper ? make_float2(s, s) : make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int c = 0; c < n / 2; ++c) {
-        U[2 * c] = make_float2(ur[c].x, ui[c].x);
-        U[2 * c + 1] = make_float2(ur[c].y, ui[c].y);
+    for (int c = 0; c < P; ++c) {
+        const float2 pr = make_float2(__shfl_sync(0xffffffffu, ur[c].x, src), __shfl_sync(0xffffffffu, ur[c].y, src));
+        const float2 pi = make_float2(__shfl_sync(0xffffffffu, ui[c].x, src), __shfl_sync(0xffffffffu, ui[c].y, src));
+        const float2 vr = __ffma2_rn(sg2, ur[c], pr), vi = __ffma2_rn(sg2, ui[c], pi);
+        ur[c] = __ffma2_rn(vr, A, __fmul2_rn(vi, B));
+        ui[c] = __ffma2_rn(vi, A, __fmul2_rn(vr, Cc));
+    }
+    const bool row = lane < N;
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+        U[2 * c] = row ? make_float2(ur[c].x, ui[c].x) : make_float2(0.0f, 0.0f);
+        U[2 * c + 1] = row ? make_float2(ur[c].y, ui[c].y) : make_float2(0.0f, 0.0f);
     }
 }
 
@@ -360,7 +387,7 @@ __global__ void __launch_bounds__(128 * WG, WG == 1 ? 3 : 2) k_sh_tc(const __gri
                 }
             }
             __syncwarp();
-            if (N == 32 || lane < N) field_rows<n, N>(Fk, X4, lane, U);  // DFT rows k >= N stay zero
+            field_rows<n, N>(Fk, X4, lane, U);  // DFT rows k >= N are zero
         }
         // FP16: U times 2^eu (exact), eu from the subaperture's largest component
         int eu = 0;
