@@ -57,7 +57,10 @@ struct __align__(16) StageMeta {
     float *opd;       // OPD of the run's first subaperture
     const float2 *uplink;
     float4 off;       // layer l's column offset terms: c, cl, fu, -
-    float2 rows[kMaxNPix];  // pupil row p: box row (int bits) and interpolation fraction
+    // pupil row p: byte offset of its lower box row (row + 1) in the box (int bits) and the
+    // interpolation fraction; and its box row
+    float2 rows[kMaxNPix];
+    int row_idx[kMaxNPix];
     LayerOffs offs_all[kMaxProjLayers];
 };
 
@@ -239,7 +242,10 @@ __device__ __forceinline__ void bulk_producer(const ProjArgs &a, float *boxes, S
                 const float *scr = l < n_lay ? scr0 + (size_t)l * SS : dm0 + (size_t)(l - n_lay) * SS;
                 const bool fits = c1 >= c0 && bw * bh <= a.stage_cap && bw <= S && bh <= S && (S & 3) == 0 &&
                                   (reinterpret_cast<uintptr_t>(scr) & 15) == 0;
-                if (row_lane) m->rows[lane] = make_float2(__int_as_float(off - by0), fr);
+                if (row_lane) {
+                    m->rows[lane] = make_float2(__int_as_float((off - by0 + 1) * bw * 4), fr);
+                    m->row_idx[lane] = off - by0;
+                }
                 if (lane == 0) {
                     m->h0 = make_int4(bid, lo, l, L);
                     m->h1 = make_int4(unit ? 2 : 0, fits ? 1 : 0, bx0, bw);
@@ -300,26 +306,33 @@ namespace {
 // R consecutive pupil rows of two columns whose box rows step by 0 or 1: straight-line code (no
 // branch between rows), so the taps of later rows load while earlier rows are interpolated.  A
 // step of 0 keeps the row pair (its lower pair is recomputed from the same taps: the same value);
-// a step of 1 makes the lower pair the upper one.
+// a step of 1 makes the lower pair the upper one.  pa, pb: the box bytes at the two columns;
+// bw4: a box row in bytes.
+__device__ __forceinline__ float2 lerp_at(const char *pa, const char *pb, int off, float2 fx) {
+    const float *ra = reinterpret_cast<const float *>(pa + off), *rb = reinterpret_cast<const float *>(pb + off);
+    const float2 s0 = make_float2(ra[0], rb[0]), s1 = make_float2(ra[1], rb[1]);
+    return __ffma2_rn(fx, __ffma2_rn(s0, make_float2(-1.0f, -1.0f), s1), s0);
+}
+
 template <int R>
-__device__ __forceinline__ void rows_unit(float2 (&acc)[kRowsPerThread], const float2 *rows, const float *box,
-                                          int bw, int ca, int cb, float2 fx) {
+__device__ __forceinline__ void rows_unit(float2 (&acc)[kRowsPerThread], const float2 *rows, const char *pa,
+                                          const char *pb, int bw4, float2 fx) {
     const float2 m1 = make_float2(-1.0f, -1.0f);
     float2 rp[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) rp[i] = rows[i];
     int prev = __float_as_int(rp[0].x);
-    float2 top = lerp_row(box + prev * bw, ca, cb, fx);
-    float2 bot = lerp_row(box + (prev + 1) * bw, ca, cb, fx);
+    float2 top = lerp_at(pa, pb, prev - bw4, fx);
+    float2 bot = lerp_at(pa, pb, prev, fx);
     acc[0] = __fadd2_rn(acc[0], __ffma2_rn(make_float2(rp[0].y, rp[0].y), __ffma2_rn(top, m1, bot), top));
 #pragma unroll
     for (int i = 1; i < R; ++i) {
-        const int ry = __float_as_int(rp[i].x);
-        const float2 nb = lerp_row(box + (ry + 1) * bw, ca, cb, fx);
-        const bool same = ry == prev;
+        const int off = __float_as_int(rp[i].x);
+        const float2 nb = lerp_at(pa, pb, off, fx);
+        const bool same = off == prev;
         top = make_float2(same ? top.x : bot.x, same ? top.y : bot.y);
         bot = nb;
-        prev = ry;
+        prev = off;
         acc[i] = __fadd2_rn(acc[i], __ffma2_rn(make_float2(rp[i].y, rp[i].y), __ffma2_rn(top, m1, bot), top));
     }
 }
@@ -384,9 +397,10 @@ __device__ __forceinline__ void bulk_consumers(const ProjArgs &a, const float *b
                 const float2 fx = make_float2(fa, fb);
                 const float *box = boxes + (size_t)b * a.stage_cap;
                 if (h1.x == 2) {
+                    const char *pa = reinterpret_cast<const char *>(box + ca), *pb = reinterpret_cast<const char *>(box + cb);
                     switch (np) {
 #define GBWFS_ROWS_CASE(R) \
-    case R: rows_unit<R>(acc, m.rows + p0, box, bw, ca, cb, fx); break;
+    case R: rows_unit<R>(acc, m.rows + p0, pa, pb, bw * 4, fx); break;
                         GBWFS_ROWS_CASE(1) GBWFS_ROWS_CASE(2) GBWFS_ROWS_CASE(3) GBWFS_ROWS_CASE(4)
                         GBWFS_ROWS_CASE(5) GBWFS_ROWS_CASE(6) GBWFS_ROWS_CASE(7) GBWFS_ROWS_CASE(8)
                         GBWFS_ROWS_CASE(9) GBWFS_ROWS_CASE(10) GBWFS_ROWS_CASE(11) GBWFS_ROWS_CASE(12)
@@ -396,7 +410,7 @@ __device__ __forceinline__ void bulk_consumers(const ProjArgs &a, const float *b
                     }
                 } else {
                 float2 rp = m.rows[p0];
-                int prev = __float_as_int(rp.x);
+                int prev = m.row_idx[p0];
                 guard(prev >= 0 && prev + 1 < bh, a.status);
                 float2 top = lerp_row(box + prev * bw, ca, cb, fx);
                 float2 bot = lerp_row(box + (prev + 1) * bw, ca, cb, fx);
@@ -405,7 +419,7 @@ __device__ __forceinline__ void bulk_consumers(const ProjArgs &a, const float *b
                 for (int i = 1; i < kRowsPerThread; ++i) {
                     if (i < np) {
                         rp = m.rows[p0 + i];
-                        const int ry = __float_as_int(rp.x);
+                        const int ry = m.row_idx[p0 + i];
                         guard(ry >= 0 && ry + 1 < bh, a.status);
                         const int d = ry - prev;  // the same for the whole warp (its rows are its group's)
                         if (d == 1) {

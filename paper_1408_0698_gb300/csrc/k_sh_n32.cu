@@ -4,8 +4,8 @@
 // Same arithmetic as k_sh.cu (Sec. 4 LGS SH: spot by DFT, sodium elongation,
 // binning, noise, centroid), mapped so that one warp owns one subaperture and
 // lane k owns DFT row k:
-//   U[k][q]  = sum_p F[k][p] X[p][q]                 (lane k, registers)
-//   Y[k][m]  = sum_q U[k][q] F[m][q],  I = |Y|^2       (lane k, m looped)
+//   U[k][q]  = sum_p F[k][p] X[p][q]                 (lanes k, k + 16: even and odd p)
+//   Y[k][m]  = sum_q U[k][q] F[m][q],  I = |Y|^2       (lane k, column pairs m, m + 16)
 //   Ta[k][dx] = sum_m I[k][m] Ga[dx][m]               (fused: I never stored)
 //   M[dy][dx] = Kt[dy][dx] sum_k Ga[dy][k] Ta[k][dx]  (DFT across the lanes)
 //   Q[iy][dx] = sum_dy G[dy][iy] M[dy][dx]            (16-point DFT across the lane pairs)
@@ -153,50 +153,89 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             }
             __syncwarp();
 
-            // U[k][q], k = lane
+            // U[k][q], k = lane.  F[k + 16][p] = F[k][p] (-1)^p i^(n-1): the lane k < 16 sums the
+            // even p and the lane k + 16 the odd p, both with row k of F; after one exchange
+            // U[k] = E + O and U[k + 16] = i^(n-1) (E - O)
             float2 U[n];
 #pragma unroll
             for (int q = 0; q < n; ++q) U[q] = make_float2(0.0f, 0.0f);
+            const bool upper = lane >= N / 2;
+            const int k16 = lane & (N / 2 - 1);
 #pragma unroll
-            for (int p = 0; p < n; ++p) {
-                const float2 f = Fk[p * N + lane];
+            for (int j = 0; j < n / 2; ++j) {
+                const int p = 2 * j + (upper ? 1 : 0);
+                const float2 f = Fk[p * N + k16];
 #pragma unroll
                 for (int q = 0; q < n; ++q) cmac2(U[q], f, X[p * n + q]);
             }
+            {
+                constexpr float sr = ((n - 1) % 4 == 1) ? 1.0f : -1.0f;  // i^(n-1) = sr i
+#pragma unroll
+                for (int q = 0; q < n; ++q) {
+                    const float ox = __shfl_xor_sync(0xffffffffu, U[q].x, N / 2);
+                    const float oy = __shfl_xor_sync(0xffffffffu, U[q].y, N / 2);
+                    if (upper) {
+                        const float dx = ox - U[q].x, dy = oy - U[q].y;
+                        U[q] = make_float2(-sr * dy, sr * dx);
+                    } else {
+                        U[q] = make_float2(U[q].x + ox, U[q].y + oy);
+                    }
+                }
+            }
 
-            // Y, I (times the slice's weight) and the first inverse-transform stage, row by row
+            // Y, I (times the slice's weight) and the first inverse-transform stage, by column
+            // pairs (m, m + 16): F[m + 16][q] = F[m][q] (-1)^q i^(n-1), so Y[m] = E + O and
+            // |Y[m + 16]| = |E - O| with E, O the sums over the even and the odd q; and
+            // Ga[d][m + 16] = (-1)^d Ga[d][m], so the pair adds (I[m] +/- I[m + 16]) Ga[d][m]
             const float wsl = SD ? SD->w[sl] : 1.0f;
 #pragma unroll 2
-            for (int m = 0; m < N; ++m) {
-                float2 y = make_float2(0.0f, 0.0f);
+            for (int m = 0; m < N / 2; ++m) {
+                float2 e = make_float2(0.0f, 0.0f), o = make_float2(0.0f, 0.0f);
 #pragma unroll
-                for (int q = 0; q < n; ++q) cmac2(y, U[q], Fm[m * n + q]);
-                const float in = SD ? wsl * fmaf(y.x, y.x, y.y * y.y) : fmaf(y.x, y.x, y.y * y.y);
-                if (stI) stI[m] = sl == 0 ? in : stI[m] + in;
+                for (int q = 0; q < n; q += 2) {
+                    cmac2(e, U[q], Fm[m * n + q]);
+                    cmac2(o, U[q + 1], Fm[m * n + q + 1]);
+                }
+                const float2 yl = make_float2(e.x + o.x, e.y + o.y), yh = make_float2(e.x - o.x, e.y - o.y);
+                float il = fmaf(yl.x, yl.x, yl.y * yl.y), ih = fmaf(yh.x, yh.x, yh.y * yh.y);
+                if (SD) {
+                    il *= wsl;
+                    ih *= wsl;
+                }
+                if (stI) {
+                    stI[m] = sl == 0 ? il : stI[m] + il;
+                    stI[m + N / 2] = sl == 0 ? ih : stI[m + N / 2] + ih;
+                }
                 if (kSlices) {
                     // the slices' spots summed in the warp's rows; T once after the last slice
                     float *ir = Iw + lane * (N + 1) + m;
-                    *ir = sl == 0 ? in : *ir + in;
+                    ir[0] = sl == 0 ? il : ir[0] + il;
+                    ir[N / 2] = sl == 0 ? ih : ir[N / 2] + ih;
                 } else if (W.is_lgs) {
+                    const float sp = il + ih, sm = il - ih;
 #pragma unroll
                     for (int d = 0; d < n; ++d) {
                         const float2 ga = Gam[m * n + d];
+                        const float in = (d & 1) ? sm : sp;
                         T[d].x = fmaf(in, ga.x, T[d].x);
                         T[d].y = fmaf(in, ga.y, T[d].y);
                     }
                 } else {
-                    Iw[lane * (N + 1) + m] = in;
+                    Iw[lane * (N + 1) + m] = il;
+                    Iw[lane * (N + 1) + m + N / 2] = ih;
                 }
             }
             __syncwarp();  // X and the slice's OPD are rewritten by the next slice
         }
         if (kSlices && W.is_lgs) {
 #pragma unroll 2
-            for (int m = 0; m < N; ++m) {
-                const float in = Iw[lane * (N + 1) + m];
+            for (int m = 0; m < N / 2; ++m) {
+                const float il = Iw[lane * (N + 1) + m], ih = Iw[lane * (N + 1) + m + N / 2];
+                const float sp = il + ih, sm = il - ih;
 #pragma unroll
                 for (int d = 0; d < n; ++d) {
                     const float2 ga = Gam[m * n + d];
+                    const float in = (d & 1) ? sm : sp;
                     T[d].x = fmaf(in, ga.x, T[d].x);
                     T[d].y = fmaf(in, ga.y, T[d].y);
                 }
