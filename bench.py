@@ -60,21 +60,37 @@ def q_dft_flops(n, nd):
     return fold + n * (nd // 2) * (4 + 10 * (stages - 1))
 
 
-def spot_flops(n, N, nd, lgs):
-    """FP32 flops (FMA = 2) of one subaperture in its spot kernel: DFT 8Nn(n+N), |.|^2 3N^2.
+def radix2_stages(kernel, N):
+    """The dense DFT stages a spot kernel computes with the radix-2 pairing of rows (or columns)
+    k and k + N/2 (F[k + N/2][p] = F[k][p] (-1)^p i^(n-1)): U = F X in the tensor-core kernels
+    up to N = 32 and in the FP32 32-point kernel, which also pairs Y = U F^T and Ta = I Ga^T."""
+    if kernel.startswith("spot_n32"):
+        return ("U", "Y", "Ta")
+    if kernel.startswith("spot_tc") and not kernel.startswith("spot_tcu") and N <= 32:
+        return ("U",)
+    return ()
+
+
+def spot_flops(n, N, nd, lgs, kernel=""):
+    """FP32 flops (FMA = 2) of one subaperture in its spot kernel: the DFT U = F X, 8Nn^2, and
+    Y = U F^T, 8N^2n (together 8Nn(n+N)), |.|^2 3N^2; with the radix-2 pairing (radix2_stages)
+    U takes 4Nn^2 + 2Nn (half sums, one complex add each way), Y 4N^2n + 2N^2 and Ta 2N^2n + N^2.
     LGS elongation and binning through the transfer function: Ta 4N^2 n, then
       32-point kernels: M as a radix-2 DFT across the lanes, 10 log2(N) N n, times the phase
       and Kt 12 (2n-1) n; Q = G^T M as a folded nd-point DFT (q_dft_flops); B = Re Q G
       4 nd^2 n; photometry 2 nd^2 (the centroid, 4 nd^2, runs in the separate noise pass);
       other sizes (direct sums): M (2n-1) n (8N+6); P = M G 8 (2n-1) nd n; B 4 nd^2 (2n-1);
       photometry and centroid 6 nd^2.
-    NGS: binning N^2, photometry and centroid 6 nd^2."""
-    f = 8 * N * n * (n + N) + 3 * N * N
+    NGS: binning N^2, photometry and centroid 6 nd^2.  Without a kernel name, every stage dense."""
+    r2 = radix2_stages(kernel, N)
+    f = (4 * N * n * n + 2 * N * n if "U" in r2 else 8 * N * n * n)
+    f += (4 * N * N * n + 2 * N * N if "Y" in r2 else 8 * N * N * n) + 3 * N * N
+    ta = 2 * N * N * n + N * N if "Ta" in r2 else 4 * N * N * n
     if lgs and N == 32:
-        f += 4 * N * N * n + 10 * 5 * N * n + 12 * (2 * n - 1) * n + q_dft_flops(n, nd) + 4 * nd * nd * n
+        f += ta + 10 * 5 * N * n + 12 * (2 * n - 1) * n + q_dft_flops(n, nd) + 4 * nd * nd * n
         f += 2 * nd * nd
     elif lgs:
-        f += 4 * N * N * n + (2 * n - 1) * n * (8 * N + 6) + 8 * (2 * n - 1) * nd * n + 4 * nd * nd * (2 * n - 1)
+        f += ta + (2 * n - 1) * n * (8 * N + 6) + 8 * (2 * n - 1) * nd * n + 4 * nd * nd * (2 * n - 1)
         f += 6 * nd * nd
     else:
         f += N * N + 6 * nd * nd
@@ -625,7 +641,7 @@ def main():
         for k, s in enumerate(cfg.stars):
             g = cfg.geometries[s.geometry_index]
             if g.n_fft == N:
-                f += w.layouts[k].n_valid * spot_flops(g.n_pix_sub, g.n_fft, g.n_det, s.is_lgs)
+                f += w.layouts[k].n_valid * spot_flops(g.n_pix_sub, g.n_fft, g.n_det, s.is_lgs, name)
         return f
 
     spots_k = {k: v for k, v in ktimes.items() if k.startswith("spot_")}
@@ -709,7 +725,7 @@ def spot_roofline(name, timing, cfg, w, pk, kind):
             continue
         nv = w.layouts[k].n_valid
         n, nd = g.n_pix_sub, g.n_det
-        f = spot_flops(n, N, nd, s.is_lgs)
+        f = spot_flops(n, N, nd, s.is_lgs, name)
         on_tc = sum(TC_STAGES[st][0](n, N, nd) for st in stages) if s.is_lgs else 0
         total += nv * f
         cuda += nv * (f - on_tc)

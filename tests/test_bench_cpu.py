@@ -47,14 +47,27 @@ def test_traffic_table_entries():
 
 
 def test_cuda_core_and_tensor_split():
-    """The roofline's split of a 32-point LGS subaperture: with Y = U F^T and Ta = I Ga^T as MMAs
-    the CUDA cores keep 183,364 - 81,920 - 40,960 = 60,484 flops; with U = F X as an MMA too,
-    34,884.  The tensor figure divides the useful DFT flops, 8 N n (n + N) = 107,520."""
+    """The roofline's split of a 32-point LGS subaperture.  The tensor-core kernel computes U = F X
+    with the rows k and k + 16 paired (4 N n^2 + 2 N n = 13,440 flops for the dense 25,600) and
+    Y = U F^T and Ta = I Ga^T as MMAs, so the CUDA cores keep 171,204 - 81,920 - 40,960 = 48,324
+    flops; with U = F X as an MMA too (dense), 34,884.  The FP32 kernel pairs U, Y and Ta:
+    112,836 flops on the CUDA cores.  The tensor figure divides the useful DFT flops,
+    8 N n (n + N) = 107,520, the dense definition."""
     n, N, nd = 10, 32, 16
-    tot = bench.spot_flops(n, N, nd, True)
+    assert bench.radix2_stages("spot_tc_bf16x3_N32", N) == ("U",)
+    assert bench.radix2_stages("spot_tc_bf16x3_N64", 64) == ()
+    assert bench.radix2_stages("spot_n32_fp32_N32", N) == ("U", "Y", "Ta")
+    dense = bench.spot_flops(n, N, nd, True)
+    u2 = 4 * N * n * n + 2 * N * n
+    assert u2 == 13440
     on_tc = lambda name: sum(bench.TC_STAGES[s][0](n, N, nd) for s in bench.tc_stages(name))
-    assert tot - on_tc("spot_tc_bf16x3_N32") == 60484
-    assert tot - on_tc("spot_tcu_bf16x3_N32") == 60484 - 25600
+    tc = bench.spot_flops(n, N, nd, True, "spot_tc_bf16x3_N32")
+    assert tc == dense - 8 * N * n * n + u2 == 171204
+    assert tc - on_tc("spot_tc_bf16x3_N32") == 48324
+    assert bench.spot_flops(n, N, nd, True, "spot_tcu_bf16x3_N32") - on_tc("spot_tcu_bf16x3_N32") == 34884
+    fp = bench.spot_flops(n, N, nd, True, "spot_n32_fp32_N32")
+    y2, ta2 = 4 * N * N * n + 2 * N * N, 2 * N * N * n + N * N
+    assert fp == dense - (8 * N * n * n - u2) - (8 * N * N * n - y2) - (4 * N * N * n - ta2) == 112836
     assert on_tc("spot_n32_fp32_N32") == 0
     assert bench.dft_useful_flops(n, N) == 107520
     # issued BF16 flops per subaperture of the two original MMA chains: 32 rows x (64 x 64 + 2 x 32 x 64)
