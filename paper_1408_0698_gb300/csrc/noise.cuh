@@ -96,24 +96,29 @@ __device__ __forceinline__ float log_factorial_f32(float k) {
 
 // Inversion for 0 < E < 16 with the first Poisson uniform u and p0 = exp(-E): the smallest k
 // with u <= F_k, F_k = F_{k-1} + p_k, stopping early where F stops growing.  With TAB, rk[k]
-// holds RN(1/k) for k < kRecipTable; the search ends before k = 43 for every E < 16 (and only
-// finite 0 < E < 16 reach it), so the table is never overrun.  Otherwise 1/k is rounded on the
-// spot.  Both forms take the same operations in the same order.
+// holds RN(1/k) for k < kRecipTable, and the loop takes two steps a trip (both steps' table
+// entries loaded together, the second step's result dropped when the first stops): the search
+// ends before k = 43 for every E < 16 (and only finite 0 < E < 16 reach it), so no read passes
+// entry 43.  Otherwise 1/k is rounded on the spot.  Both forms take the same operations in the
+// same order.
 template <bool TAB>
 __device__ __forceinline__ int poisson_inversion(float E, float u, float p0, const float *rk) {
     float p = p0, F = p0;
     if (TAB) {
         if (!(u > F)) return 0;
-        const float *r = rk;
-        while (true) {
-            ++r;
-            p = __fmul_rn(__fmul_rn(p, E), *r);
-            const float Fn = __fadd_rn(F, p);
-            const bool stop = Fn == F || !(u > Fn);
-            F = Fn;
-            if (stop) break;
+        for (int k = 1;; k += 2) {
+            const float r1 = rk[k], r2 = rk[k + 1];
+            const float p1 = __fmul_rn(__fmul_rn(p, E), r1);
+            const float F1 = __fadd_rn(F, p1);
+            const bool s1 = F1 == F || !(u > F1);
+            const float p2 = __fmul_rn(__fmul_rn(p1, E), r2);
+            const float F2 = __fadd_rn(F1, p2);
+            const bool s2 = F2 == F1 || !(u > F2);
+            if (s1) return k;
+            if (s2) return k + 1;
+            p = p2;
+            F = F2;
         }
-        return (int)(r - rk);
     }
     int k = 0;
     while (u > F) {

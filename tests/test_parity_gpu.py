@@ -441,6 +441,25 @@ def test_tensor_core_16_24_point_edge_geometries(n_sub, n, N, nd, lgs, noise, pr
     w.close()
 
 
+@pytest.mark.parametrize("precision", [inputs.PREC_FP32] + TC_PRECISIONS)
+@pytest.mark.parametrize("lgs,noise", [(True, False), (True, True), (False, False)])
+def test_32_point_n8_geometry(lgs, noise, precision):
+    """The 32-point kernels with 8-pixel subapertures (the lane-DFT tail with 15 autocorrelation
+    rows, none folded modulo 16; the paired DFT rows k and k + 16 with the quarter turn
+    i^(n-1) = -i): a ragged LGS or NGS sensor in full against the oracle, in FP32 and on the
+    tensor cores, noise on and off."""
+    cfg = _small_cfg(9, 8, 32, 16, lgs)
+    cfg.geometries[0].precision = precision
+    scr = inputs.make_screens(cfg.layers, 12)
+    gpu, w = run_library(cfg, scr, 0.003, seed=6, noise=noise)
+    _check_wfs(cfg, scr, 0.003, gpu, noise=noise, seed=6)
+    if noise:
+        ref = oracle.measure_wfs(cfg, scr, 0, 0.003, seed=6, noise=True, stages=True)
+        same = np.abs(gpu[0]["C"] - ref["C"]) < 1e-3
+        assert same.mean() >= 0.999
+    w.close()
+
+
 @pytest.mark.parametrize("precision", TC_PRECISIONS)
 @pytest.mark.parametrize("n_sub,noise", [(2, False), (3, True), (4, False)])
 def test_tensor_core_64_point_ngs(n_sub, noise, precision):
