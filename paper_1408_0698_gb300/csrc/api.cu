@@ -1433,7 +1433,12 @@ wfs_status wfs_measure_host(wfs_handle h, const float *screens_host, double t_s,
                 (e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
                 (e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_fail(h, e, "host-path staging allocation");
-        if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        // the uploads (and the gather kernel that reads the mapped host screens) run beside the
+        // previous frame's kernels; at the device's highest stream priority their thread blocks
+        // take SM room first whenever a frame kernel's blocks retire
+        int prio_low = 0, prio_high = 0;
+        if ((e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high)) != cudaSuccess ||
+            (e = cudaStreamCreateWithPriority(&h->copy_stream, cudaStreamNonBlocking, prio_high)) != cudaSuccess)
             return cuda_fail(h, e, "host-path copy stream");
     }
     if (s != h->last_stream && cudaEventQuery(h->ev_measured) == cudaErrorNotReady)
