@@ -60,21 +60,24 @@ def q_dft_flops(n, nd):
     return fold + n * (nd // 2) * (4 + 10 * (stages - 1))
 
 
-def radix2_stages(kernel, N):
-    """The dense DFT stages a spot kernel computes with the radix-2 pairing of rows (or columns)
-    k and k + N/2 (F[k + N/2][p] = F[k][p] (-1)^p i^(n-1)): U = F X in the tensor-core kernels
-    up to N = 32 and in the FP32 32-point kernel, which also pairs Y = U F^T and Ta = I Ga^T."""
+def dft_forms(kernel, N):
+    """How a spot kernel computes the dense DFT stages: U = F X with the rows k and k + N/2 paired
+    ("r2": F[k + N/2][p] = F[k][p] (-1)^p i^(n-1)) in the tensor-core kernels up to N = 32 and in
+    the FP32 32-point kernel, which also takes Y = U F^T and Ta = I Ga^T by column quadruples
+    (m + 8j: "r4"); otherwise dense."""
     if kernel.startswith("spot_n32"):
-        return ("U", "Y", "Ta")
+        return {"U": "r2", "Y": "r4", "Ta": "r4"}
     if kernel.startswith("spot_tc") and not kernel.startswith("spot_tcu") and N <= 32:
-        return ("U",)
-    return ()
+        return {"U": "r2", "Y": "dense", "Ta": "dense"}
+    return {"U": "dense", "Y": "dense", "Ta": "dense"}
 
 
 def spot_flops(n, N, nd, lgs, kernel=""):
     """FP32 flops (FMA = 2) of one subaperture in its spot kernel: the DFT U = F X, 8Nn^2, and
-    Y = U F^T, 8N^2n (together 8Nn(n+N)), |.|^2 3N^2; with the radix-2 pairing (radix2_stages)
-    U takes 4Nn^2 + 2Nn (half sums, one complex add each way), Y 4N^2n + 2N^2 and Ta 2N^2n + N^2.
+    Y = U F^T, 8N^2n (together 8Nn(n+N)), |.|^2 3N^2, as each kernel computes them (dft_forms):
+    U paired 4Nn^2 + 2Nn (half sums, one complex add each way); Y by quadruples 2N^2n + 4N^2
+    (quarter sums, a 4-point DFT of them); Ta by quadruples N (N/4) (6 + 4 ceil(n/2) + 8 floor(n/2))
+    (six adds combine the four intensities, a real coefficient for even d, a complex one for odd).
     LGS elongation and binning through the transfer function: Ta 4N^2 n, then
       32-point kernels: M as a radix-2 DFT across the lanes, 10 log2(N) N n, times the phase
       and Kt 12 (2n-1) n; Q = G^T M as a folded nd-point DFT (q_dft_flops); B = Re Q G
@@ -82,10 +85,10 @@ def spot_flops(n, N, nd, lgs, kernel=""):
       other sizes (direct sums): M (2n-1) n (8N+6); P = M G 8 (2n-1) nd n; B 4 nd^2 (2n-1);
       photometry and centroid 6 nd^2.
     NGS: binning N^2, photometry and centroid 6 nd^2.  Without a kernel name, every stage dense."""
-    r2 = radix2_stages(kernel, N)
-    f = (4 * N * n * n + 2 * N * n if "U" in r2 else 8 * N * n * n)
-    f += (4 * N * N * n + 2 * N * N if "Y" in r2 else 8 * N * N * n) + 3 * N * N
-    ta = 2 * N * N * n + N * N if "Ta" in r2 else 4 * N * N * n
+    fm = dft_forms(kernel, N)
+    f = (4 * N * n * n + 2 * N * n if fm["U"] == "r2" else 8 * N * n * n)
+    f += (2 * N * N * n + 4 * N * N if fm["Y"] == "r4" else 8 * N * N * n) + 3 * N * N
+    ta = (N * (N // 4) * (6 + 4 * ((n + 1) // 2) + 8 * (n // 2)) if fm["Ta"] == "r4" else 4 * N * N * n)
     if lgs and N == 32:
         f += ta + 10 * 5 * N * n + 12 * (2 * n - 1) * n + q_dft_flops(n, nd) + 4 * nd * nd * n
         f += 2 * nd * nd

@@ -5,7 +5,7 @@
 // binning, noise, centroid), mapped so that one warp owns one subaperture and
 // lane k owns DFT row k:
 //   U[k][q]  = sum_p F[k][p] X[p][q]                 (lanes k, k + 16: even and odd p)
-//   Y[k][m]  = sum_q U[k][q] F[m][q],  I = |Y|^2       (lane k, column pairs m, m + 16)
+//   Y[k][m]  = sum_q U[k][q] F[m][q],  I = |Y|^2       (lane k, columns m + 8j together)
 //   Ta[k][dx] = sum_m I[k][m] Ga[dx][m]               (fused: I never stored)
 //   M[dy][dx] = Kt[dy][dx] sum_k Ga[dy][k] Ta[k][dx]  (DFT across the lanes)
 //   Q[iy][dx] = sum_dy G[dy][iy] M[dy][dx]            (16-point DFT across the lane pairs)
@@ -29,6 +29,29 @@ namespace {
 __device__ __forceinline__ void cmac2(float2 &acc, const float2 a, const float2 b) {
     acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
     acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+}
+
+// The first transfer-domain stage for the columns (m, m + 8, m + 16, m + 24) of a 32-point
+// row: Ga[d][m + 8j] = i^(jd) Ga[d][m], so T[d] += (sum_j i^(jd) I[m + 8j]) Ga[d][m], whose
+// coefficient is real for even d (I0 + I1 + I2 + I3 or I0 - I1 + I2 - I3) and complex for odd d
+// ((I0 - I2) +/- i (I1 - I3)).  ga: Ga[.][m] for d < n.
+template <int n>
+__device__ __forceinline__ void ta_quad(float2 (&T)[n], const float (&iv)[4], const float2 *ga) {
+    const float P = iv[0] + iv[2], M = iv[0] - iv[2], Q = iv[1] + iv[3], R = iv[1] - iv[3];
+    const float V0 = P + Q, V2 = P - Q;
+#pragma unroll
+    for (int d = 0; d < n; ++d) {
+        const float2 g = ga[d];
+        if ((d & 3) == 0 || (d & 3) == 2) {
+            const float V = (d & 3) == 0 ? V0 : V2;
+            T[d].x = fmaf(V, g.x, T[d].x);
+            T[d].y = fmaf(V, g.y, T[d].y);
+        } else {
+            const float Ri = (d & 3) == 1 ? R : -R;  // V = M + i Ri
+            T[d].x = fmaf(M, g.x, fmaf(-Ri, g.y, T[d].x));
+            T[d].y = fmaf(M, g.y, fmaf(Ri, g.x, T[d].y));
+        }
+    }
 }
 
 template <int n, int nd, bool kSlices = false>
@@ -184,61 +207,55 @@ __global__ void __launch_bounds__(256, 2) k_sh_n32(const __grid_constant__ ShArg
             }
 
             // Y, I (times the slice's weight) and the first inverse-transform stage, by column
-            // pairs (m, m + 16): F[m + 16][q] = F[m][q] (-1)^q i^(n-1), so Y[m] = E + O and
-            // |Y[m + 16]| = |E - O| with E, O the sums over the even and the odd q; and
-            // Ga[d][m + 16] = (-1)^d Ga[d][m], so the pair adds (I[m] +/- I[m + 16]) Ga[d][m]
+            // quadruples (m, m + 8, m + 16, m + 24): F[m + 8j][q] = F[m][q] (-i)^(jq) exp(i pi j cn / 2),
+            // so |Y[m + 8j]| = |T_j| with T_j = sum_r (-i)^(jr) S_r, S_r the sum over q = r mod 4
+            // (a 4-point DFT of the S_r); Ta adds the quadruple through ta_quad
             const float wsl = SD ? SD->w[sl] : 1.0f;
 #pragma unroll 2
-            for (int m = 0; m < N / 2; ++m) {
-                float2 e = make_float2(0.0f, 0.0f), o = make_float2(0.0f, 0.0f);
+            for (int m = 0; m < N / 4; ++m) {
+                float2 S[4];
 #pragma unroll
-                for (int q = 0; q < n; q += 2) {
-                    cmac2(e, U[q], Fm[m * n + q]);
-                    cmac2(o, U[q + 1], Fm[m * n + q + 1]);
-                }
-                const float2 yl = make_float2(e.x + o.x, e.y + o.y), yh = make_float2(e.x - o.x, e.y - o.y);
-                float il = fmaf(yl.x, yl.x, yl.y * yl.y), ih = fmaf(yh.x, yh.x, yh.y * yh.y);
-                if (SD) {
-                    il *= wsl;
-                    ih *= wsl;
+                for (int r = 0; r < 4; ++r) S[r] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int q = 0; q < n; ++q) cmac2(S[q & 3], U[q], Fm[m * n + q]);
+                const float2 A = make_float2(S[0].x + S[2].x, S[0].y + S[2].y);
+                const float2 B = make_float2(S[0].x - S[2].x, S[0].y - S[2].y);
+                const float2 C = make_float2(S[1].x + S[3].x, S[1].y + S[3].y);
+                const float2 Dd = make_float2(S[1].x - S[3].x, S[1].y - S[3].y);
+                // T0 = A + C, T1 = B - i D, T2 = A - C, T3 = B + i D
+                const float2 Tq[4] = {make_float2(A.x + C.x, A.y + C.y), make_float2(B.x + Dd.y, B.y - Dd.x),
+                                      make_float2(A.x - C.x, A.y - C.y), make_float2(B.x - Dd.y, B.y + Dd.x)};
+                float iv[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    iv[j] = fmaf(Tq[j].x, Tq[j].x, Tq[j].y * Tq[j].y);
+                    if (SD) iv[j] *= wsl;
                 }
                 if (stI) {
-                    stI[m] = sl == 0 ? il : stI[m] + il;
-                    stI[m + N / 2] = sl == 0 ? ih : stI[m + N / 2] + ih;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) stI[m + 8 * j] = sl == 0 ? iv[j] : stI[m + 8 * j] + iv[j];
                 }
                 if (kSlices) {
                     // the slices' spots summed in the warp's rows; T once after the last slice
                     float *ir = Iw + lane * (N + 1) + m;
-                    ir[0] = sl == 0 ? il : ir[0] + il;
-                    ir[N / 2] = sl == 0 ? ih : ir[N / 2] + ih;
-                } else if (W.is_lgs) {
-                    const float sp = il + ih, sm = il - ih;
 #pragma unroll
-                    for (int d = 0; d < n; ++d) {
-                        const float2 ga = Gam[m * n + d];
-                        const float in = (d & 1) ? sm : sp;
-                        T[d].x = fmaf(in, ga.x, T[d].x);
-                        T[d].y = fmaf(in, ga.y, T[d].y);
-                    }
+                    for (int j = 0; j < 4; ++j) ir[8 * j] = sl == 0 ? iv[j] : ir[8 * j] + iv[j];
+                } else if (W.is_lgs) {
+                    ta_quad<n>(T, iv, Gam + m * n);
                 } else {
-                    Iw[lane * (N + 1) + m] = il;
-                    Iw[lane * (N + 1) + m + N / 2] = ih;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) Iw[lane * (N + 1) + m + 8 * j] = iv[j];
                 }
             }
             __syncwarp();  // X and the slice's OPD are rewritten by the next slice
         }
         if (kSlices && W.is_lgs) {
 #pragma unroll 2
-            for (int m = 0; m < N / 2; ++m) {
-                const float il = Iw[lane * (N + 1) + m], ih = Iw[lane * (N + 1) + m + N / 2];
-                const float sp = il + ih, sm = il - ih;
+            for (int m = 0; m < N / 4; ++m) {
+                float iv[4];
 #pragma unroll
-                for (int d = 0; d < n; ++d) {
-                    const float2 ga = Gam[m * n + d];
-                    const float in = (d & 1) ? sm : sp;
-                    T[d].x = fmaf(in, ga.x, T[d].x);
-                    T[d].y = fmaf(in, ga.y, T[d].y);
-                }
+                for (int j = 0; j < 4; ++j) iv[j] = Iw[lane * (N + 1) + m + 8 * j];
+                ta_quad<n>(T, iv, Gam + m * n);
             }
         }
 

@@ -50,13 +50,13 @@ def test_cuda_core_and_tensor_split():
     """The roofline's split of a 32-point LGS subaperture.  The tensor-core kernel computes U = F X
     with the rows k and k + 16 paired (4 N n^2 + 2 N n = 13,440 flops for the dense 25,600) and
     Y = U F^T and Ta = I Ga^T as MMAs, so the CUDA cores keep 171,204 - 81,920 - 40,960 = 48,324
-    flops; with U = F X as an MMA too (dense), 34,884.  The FP32 kernel pairs U, Y and Ta:
-    112,836 flops on the CUDA cores.  The tensor figure divides the useful DFT flops,
-    8 N n (n + N) = 107,520, the dense definition."""
+    flops; with U = F X as an MMA too (dense), 34,884.  The FP32 kernel pairs U and takes Y and Ta
+    by column quadruples: 89,796 flops on the CUDA cores.  The tensor figure divides the useful DFT
+    flops, 8 N n (n + N) = 107,520, the dense definition."""
     n, N, nd = 10, 32, 16
-    assert bench.radix2_stages("spot_tc_bf16x3_N32", N) == ("U",)
-    assert bench.radix2_stages("spot_tc_bf16x3_N64", 64) == ()
-    assert bench.radix2_stages("spot_n32_fp32_N32", N) == ("U", "Y", "Ta")
+    assert bench.dft_forms("spot_tc_bf16x3_N32", N) == {"U": "r2", "Y": "dense", "Ta": "dense"}
+    assert bench.dft_forms("spot_tc_bf16x3_N64", 64) == {"U": "dense", "Y": "dense", "Ta": "dense"}
+    assert bench.dft_forms("spot_n32_fp32_N32", N) == {"U": "r2", "Y": "r4", "Ta": "r4"}
     dense = bench.spot_flops(n, N, nd, True)
     u2 = 4 * N * n * n + 2 * N * n
     assert u2 == 13440
@@ -65,9 +65,14 @@ def test_cuda_core_and_tensor_split():
     assert tc == dense - 8 * N * n * n + u2 == 171204
     assert tc - on_tc("spot_tc_bf16x3_N32") == 48324
     assert bench.spot_flops(n, N, nd, True, "spot_tcu_bf16x3_N32") - on_tc("spot_tcu_bf16x3_N32") == 34884
+    # Y by quadruples: per lane 8 column groups x (10 complex MACs + a 4-point DFT of 8 complex adds)
+    y4 = 32 * 8 * (10 * 8 + 8 * 2)
+    assert y4 == 2 * N * N * n + 4 * N * N == 24576
+    # Ta by quadruples: per lane 8 groups x (6 adds + 5 even d x 4 flops + 5 odd d x 8 flops)
+    ta4 = 32 * 8 * (6 + 5 * 4 + 5 * 8)
+    assert ta4 == 16896
     fp = bench.spot_flops(n, N, nd, True, "spot_n32_fp32_N32")
-    y2, ta2 = 4 * N * N * n + 2 * N * N, 2 * N * N * n + N * N
-    assert fp == dense - (8 * N * n * n - u2) - (8 * N * N * n - y2) - (4 * N * N * n - ta2) == 112836
+    assert fp == dense - (8 * N * n * n - u2) - (8 * N * N * n - y4) - (4 * N * N * n - ta4) == 89796
     assert on_tc("spot_n32_fp32_N32") == 0
     assert bench.dft_useful_flops(n, N) == 107520
     # issued BF16 flops per subaperture of the two original MMA chains: 32 rows x (64 x 64 + 2 x 32 x 64)
